@@ -1,0 +1,493 @@
+"""Plain FP64 CPU oracle for the Repulsive Curves hot path (arXiv 2006.07859).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU-baseline
+leg may import this module; the CUDA library never does, and this module never touches
+the CUDA library.  The pair sums live in ``tpe_oracle.c`` (literal loops, FP64); this
+file adds the linear algebra on top of them with numpy, one library primitive per step
+(a dense solve, an FFT), in the order the paper states it:
+
+  * constraints Phi and their Jacobian C ........... Sec. 8.1 (barycenter, total length)
+  * gradient saddle-point problem .................. Sec. 5.3.1, Eq. 22 (dense solve)
+  * projected system P^T A P y = P^T a, x = P y .... App. B.3.3 (solved by CG)
+  * constraint projection via z = C^+ b, x = z - y . Sec. 5.3.2 Eq. 23, App. B.3.4
+  * descent step: normalised gradient, backtracking
+    from tau = 1 until Armijo holds and the
+    constraint projection succeeds ................. Sec. 5.4
+
+Readings taken where the paper is silent or garbled (each is listed with its reason in
+the design notes of the repository):
+  * P = I - C^T (C C^T)^{-1} C and C^+ = C^T (C C^T)^{-1} (the printed "P := C C^+" with
+    C^+ = (C C^T)^{-1} C^T does not type-check; this is the Euclidean projector onto
+    null(C)).
+  * A-bar in the constraint projection is the one of the pre-step curve; C is evaluated
+    at the current iterate.
+  * Armijo constant 1e-4, halving, at most 30 halvings; projection tolerance on
+    max|Phi| relative to max(1, L0).
+
+The Jacobi-scaled circulant ("spectral") preconditioner at the end is not from the
+paper; it is this library's preconditioner, and the oracle for it is written from its
+definition (eigen-decomposition of the Gram matrix of a regular polygon) with numpy.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tpe_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle_tpe.so")
+_lib = None
+
+
+def build_library(force: bool = False) -> str:
+    """Compile tpe_oracle.c with gcc (FP64, no fast-math, OpenMP over independent rows)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build_library()
+        L = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.POINTER
+        d, i = ctypes.c_double, ctypes.c_int
+        pd, pi = P(d), P(i)
+        L.orc_energy.argtypes = [i, pd, i, pi, d, d, pd, pd]
+        L.orc_energy_rows.argtypes = [i, pd, i, pi, d, d, i, pi, pd]
+        L.orc_differential.argtypes = [i, pd, i, pi, d, d, pd]
+        L.orc_differential_at.argtypes = [i, pd, i, pi, d, d, i, pi, pd]
+        L.orc_gram_dense.argtypes = [i, pd, i, pi, d, pd, pd]
+        L.orc_gram_apply.argtypes = [i, pd, i, pi, d, i, pd, pd]
+        L.orc_gram_apply_at.argtypes = [i, pd, i, pi, d, i, pd, i, pi, pd]
+        L.orc_bilinear.argtypes = [i, pd, i, pi, d, pd, pd, pd, pd]
+        L.orc_edge_quantities.argtypes = [i, pd, i, pi, pd, pd, pd]
+        L.orc_num_threads.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _pd(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _pi(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _geom(gamma, edges):
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    e = np.ascontiguousarray(edges, dtype=np.int32)
+    return g, e
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(st):
+    if st == 1:
+        raise OracleError("edge of zero length: tangent undefined")
+    if st != 0:
+        raise OracleError(f"oracle status {st}")
+
+
+def sigma_of(alpha: float, beta: float) -> float:
+    """sigma = s - 1 with s = (beta - 1)/alpha (Sec. 4.2.2)."""
+    return (beta - 1.0) / alpha - 1.0
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+# ----------------------------------------------------------------------------- pair sums (C)
+
+def edge_quantities(gamma, edges):
+    g, e = _geom(gamma, edges)
+    nE = e.shape[0]
+    ell, T, x = np.empty(nE), np.empty((nE, 3)), np.empty((nE, 3))
+    _check(lib().orc_edge_quantities(g.shape[0], _pd(g), nE, _pi(e), _pd(ell), _pd(T), _pd(x)))
+    return ell, T, x
+
+
+def energy(gamma, edges, alpha=2.0, beta=4.5, rows=False):
+    """Discrete energy, Eq. 17 (and the per-target-edge row sums if rows=True)."""
+    g, e = _geom(gamma, edges)
+    r = np.empty(e.shape[0])
+    tot = ctypes.c_double(0.0)
+    _check(lib().orc_energy(g.shape[0], _pd(g), e.shape[0], _pi(e), alpha, beta, _pd(r), ctypes.byref(tot)))
+    return (tot.value, r) if rows else tot.value
+
+
+def energy_rows(gamma, edges, idx, alpha=2.0, beta=4.5):
+    g, e = _geom(gamma, edges)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    out = np.empty(idx.shape[0])
+    _check(lib().orc_energy_rows(g.shape[0], _pd(g), e.shape[0], _pi(e), alpha, beta, idx.shape[0], _pi(idx),
+                                 _pd(out)))
+    return out
+
+
+def differential(gamma, edges, alpha=2.0, beta=4.5):
+    """d hat-E / d gamma, vertex-major [nV, 3] (Sec. 5.1)."""
+    g, e = _geom(gamma, edges)
+    out = np.zeros((g.shape[0], 3))
+    _check(lib().orc_differential(g.shape[0], _pd(g), e.shape[0], _pi(e), alpha, beta, _pd(out)))
+    return out
+
+
+def differential_at(gamma, edges, vidx, alpha=2.0, beta=4.5):
+    g, e = _geom(gamma, edges)
+    v = np.ascontiguousarray(vidx, dtype=np.int32)
+    out = np.zeros((v.shape[0], 3))
+    _check(lib().orc_differential_at(g.shape[0], _pd(g), e.shape[0], _pi(e), alpha, beta, v.shape[0], _pi(v),
+                                     _pd(out)))
+    return out
+
+
+def gram_dense(gamma, edges, sigma):
+    """(B, B0) built by the increment tables of Secs. 5.2.2-5.2.3 (row-major nV x nV)."""
+    g, e = _geom(gamma, edges)
+    n = g.shape[0]
+    B, B0 = np.zeros((n, n)), np.zeros((n, n))
+    _check(lib().orc_gram_dense(n, _pd(g), e.shape[0], _pi(e), sigma, _pd(B), _pd(B0)))
+    return B, B0
+
+
+def gram_apply(gamma, edges, sigma, u):
+    """(B + B0) u, matrix-free with the same increments; u is [nV] or [nV, m]."""
+    g, e = _geom(gamma, edges)
+    u = np.asarray(u, dtype=np.float64)
+    vec = u.ndim == 1
+    U = np.ascontiguousarray(u.reshape(u.shape[0], -1))
+    out = np.zeros_like(U)
+    _check(lib().orc_gram_apply(g.shape[0], _pd(g), e.shape[0], _pi(e), sigma, U.shape[1], _pd(U), _pd(out)))
+    return out[:, 0] if vec else out
+
+
+def gram_apply_at(gamma, edges, sigma, u, vidx):
+    g, e = _geom(gamma, edges)
+    U = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(g.shape[0], -1))
+    v = np.ascontiguousarray(vidx, dtype=np.int32)
+    out = np.zeros((v.shape[0], U.shape[1]))
+    _check(lib().orc_gram_apply_at(g.shape[0], _pd(g), e.shape[0], _pi(e), sigma, U.shape[1], _pd(U), v.shape[0],
+                                   _pi(v), _pd(out)))
+    return out
+
+
+def bilinear(gamma, edges, sigma, u, v):
+    """(u^T B v, u^T B0 v) evaluated from the bilinear forms of Eq. 21 and Sec. 5.2.3."""
+    g, e = _geom(gamma, edges)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib().orc_bilinear(g.shape[0], _pd(g), e.shape[0], _pi(e), sigma, _pd(u), _pd(v), ctypes.byref(a),
+                              ctypes.byref(b)))
+    return a.value, b.value
+
+
+# ----------------------------------------------------------------------------- constraints
+
+@dataclass
+class ConstraintGroup:
+    """Barycenter and total-length constraints (Sec. 8.1) over the edges [e0, e1)."""
+    e0: int
+    e1: int
+    x0: np.ndarray
+    L0: float
+
+
+def constraint_groups(gamma, edges, edge_offsets=None):
+    """x0 and L0 fixed at their values on the given curve; one group per curve if
+    edge_offsets is given, else one group for the whole graph."""
+    ell, T, x = edge_quantities(gamma, edges)
+    offs = [0, len(edges)] if edge_offsets is None else list(edge_offsets)
+    groups = []
+    for c in range(len(offs) - 1):
+        e0, e1 = offs[c], offs[c + 1]
+        L = ell[e0:e1].sum()
+        x0 = (ell[e0:e1, None] * x[e0:e1]).sum(0) / L
+        groups.append(ConstraintGroup(e0, e1, x0, L))
+    return groups
+
+
+def phi(gamma, edges, groups):
+    """Phi_barycenter = sum_I l_I (x_I - x0) (3 rows), Phi_length = L0 - sum_I l_I (1 row), per group."""
+    ell, T, x = edge_quantities(gamma, edges)
+    out = []
+    for gr in groups:
+        s = slice(gr.e0, gr.e1)
+        out.extend(list((ell[s, None] * (x[s] - gr.x0)).sum(0)))
+        out.append(gr.L0 - ell[s].sum())
+    return np.array(out)
+
+
+def jacobian(gamma, edges, groups):
+    """C = d Phi, shape [4 * groups, nV, 3] (vertex-major columns).
+    d l_I / d g_i2 = T_I = -d l_I / d g_i1 and d x_I / d g_ia = Id / 2."""
+    g, e = _geom(gamma, edges)
+    ell, T, x = edge_quantities(g, e)
+    C = np.zeros((4 * len(groups), g.shape[0], 3))
+    for q, gr in enumerate(groups):
+        for I in range(gr.e0, gr.e1):
+            i1, i2 = e[I]
+            for k in range(3):
+                r = 4 * q + k
+                C[r, i2] += T[I] * (x[I, k] - gr.x0[k])
+                C[r, i1] -= T[I] * (x[I, k] - gr.x0[k])
+                C[r, i1, k] += 0.5 * ell[I]
+                C[r, i2, k] += 0.5 * ell[I]
+            C[4 * q + 3, i2] -= T[I]
+            C[4 * q + 3, i1] += T[I]
+    return C
+
+
+# ----------------------------------------------------------------------------- saddle-point problems
+
+def to_cm(v):
+    """Vertex-major [nV, 3] -> component-major R^{3|V|} (all x, then y, then z), as in Eq. 19."""
+    return np.asarray(v).T.reshape(-1)
+
+
+def from_cm(v, nV):
+    return np.asarray(v).reshape(3, nV).T.copy()
+
+
+def abar_cm(A):
+    """A-bar = diag(A, A, A) in component-major order, Eq. 19."""
+    n = A.shape[0]
+    Ab = np.zeros((3 * n, 3 * n))
+    for k in range(3):
+        Ab[k * n:(k + 1) * n, k * n:(k + 1) * n] = A
+    return Ab
+
+
+def kkt_solve(A, C, rhs_top, rhs_bottom):
+    """Dense solve of [A-bar C^T; C 0][x; lambda] = [rhs_top; rhs_bottom] (Eqs. 22-23).
+    A is the scalar nV x nV Gram matrix; C is [k, nV, 3]; rhs_top is [nV, 3]."""
+    nV = A.shape[0]
+    k = C.shape[0]
+    Ab = abar_cm(A)
+    Ccm = np.stack([to_cm(C[r]) for r in range(k)])
+    K = np.zeros((3 * nV + k, 3 * nV + k))
+    K[:3 * nV, :3 * nV] = Ab
+    K[:3 * nV, 3 * nV:] = Ccm.T
+    K[3 * nV:, :3 * nV] = Ccm
+    rhs = np.concatenate([to_cm(rhs_top), np.asarray(rhs_bottom, dtype=np.float64)])
+    sol = np.linalg.solve(K, rhs)
+    return from_cm(sol[:3 * nV], nV), sol[3 * nV:]
+
+
+class Projector:
+    """P v = v - C^T (C C^T)^{-1} C v (App. B.3.3, read as the Euclidean projector onto null(C))."""
+
+    def __init__(self, C):
+        self.C = C.reshape(C.shape[0], -1)
+        self.G = self.C @ self.C.T
+
+    def __call__(self, v):
+        s = v.shape
+        f = v.reshape(-1)
+        return (f - self.C.T @ np.linalg.solve(self.G, self.C @ f)).reshape(s)
+
+    def pinv(self, b):
+        """C^+ b = C^T (C C^T)^{-1} b."""
+        return (self.C.T @ np.linalg.solve(self.G, b))
+
+
+@dataclass
+class CGResult:
+    x: np.ndarray
+    iters: int
+    rel_res: float
+    converged: bool
+    history: list = field(default_factory=list)
+
+
+def projected_cg(apply_abar, P, a, tol=1e-6, maxit=10000, precond=None, x0=None):
+    """CG on P A-bar P y = P a, returning x = P y (App. B.3.3).  apply_abar maps [nV,3] -> [nV,3];
+    precond (optional, SPD) maps [nV,3] -> [nV,3] and is used as P M^{-1} P."""
+    Pa = P(a)
+    nb = np.linalg.norm(Pa)
+    y = np.zeros_like(a) if x0 is None else P(x0)
+    r = Pa - P(apply_abar(P(y))) if x0 is not None else Pa.copy()
+    if nb == 0.0:
+        return CGResult(P(y), 0, 0.0, True)
+    z = P(precond(r)) if precond else r.copy()
+    p = z.copy()
+    rz = float(np.vdot(r, z))
+    hist = []
+    for it in range(1, maxit + 1):
+        q = P(apply_abar(P(p)))
+        pq = float(np.vdot(p, q))
+        if not pq > 0.0:
+            return CGResult(P(y), it, np.linalg.norm(r) / nb, False, hist)
+        al = rz / pq
+        y = y + al * p
+        r = r - al * q
+        rel = np.linalg.norm(r) / nb
+        hist.append(rel)
+        if rel <= tol:
+            return CGResult(P(y), it, rel, True, hist)
+        z = P(precond(r)) if precond else r
+        rz2 = float(np.vdot(r, z))
+        p = z + (rz2 / rz) * p
+        rz = rz2
+    return CGResult(P(y), maxit, np.linalg.norm(r) / nb, False, hist)
+
+
+# ----------------------------------------------------------------------------- descent
+
+@dataclass
+class Params:
+    alpha: float = 2.0
+    beta: float = 4.5
+    cg_tol: float = 1e-6
+    cg_maxit: int = 20000
+    proj_cg_tol: float = 1e-6
+    proj_tol: float = 1e-10
+    proj_maxit: int = 5
+    armijo_c: float = 1e-4
+    shrink: float = 0.5
+    max_halvings: int = 30
+
+    @property
+    def sigma(self):
+        return sigma_of(self.alpha, self.beta)
+
+
+def make_apply(gamma, edges, sigma):
+    """Matrix-free A-bar u for vertex-major u [nV, 3] (A-bar acts on each component, Eq. 19)."""
+    return lambda u: gram_apply(gamma, edges, sigma, u)
+
+
+def sobolev_gradient(gamma, edges, groups, dE, prm: Params, dense=False, precond=None):
+    """Projected H^s gradient g~ (Eq. 22).  dense=True: direct dense KKT solve; otherwise projected CG."""
+    C = jacobian(gamma, edges, groups)
+    if dense:
+        B, B0 = gram_dense(gamma, edges, prm.sigma)
+        g, lam = kkt_solve(B + B0, C, dE, np.zeros(C.shape[0]))
+        return g, None
+    P = Projector(C)
+    res = projected_cg(make_apply(gamma, edges, prm.sigma), P, dE, prm.cg_tol, prm.cg_maxit, precond)
+    return res.x, res
+
+
+def constraint_projection(gamma_t, edges, groups, apply_abar, prm: Params, precond=None):
+    """Sec. 5.3.2 via App. B.3.4: repeat b = -Phi(g~); z = C^+ b; solve P A P y = P A z; x = z - y;
+    g~ += x; until max|Phi| <= tol.  Returns (curve, iterations, success)."""
+    g = gamma_t.copy()
+    scale = max(1.0, max(gr.L0 for gr in groups))
+    for it in range(prm.proj_maxit + 1):
+        ph = phi(g, edges, groups)
+        if np.max(np.abs(ph)) <= prm.proj_tol * scale:
+            return g, it, True
+        if it == prm.proj_maxit:
+            break
+        C = jacobian(g, edges, groups)
+        P = Projector(C)
+        z = P.pinv(-ph).reshape(g.shape)
+        res = projected_cg(apply_abar, P, apply_abar(z), prm.proj_cg_tol, prm.cg_maxit, precond)
+        g = g + (z - res.x)
+    return g, prm.proj_maxit, False
+
+
+@dataclass
+class StepInfo:
+    E_before: float
+    E_after: float
+    tau: float
+    gnorm: float
+    halvings: int
+    proj_iters: int
+    cg_iters: int
+    accepted: bool
+
+
+def descent_step(gamma, edges, groups, prm: Params, dense=False, precond_factory=None):
+    """One H^s descent step with normalised-gradient backtracking from tau = 1 (Sec. 5.4)."""
+    E0 = energy(gamma, edges, prm.alpha, prm.beta)
+    dE = differential(gamma, edges, prm.alpha, prm.beta)
+    pc = precond_factory(gamma) if precond_factory else None
+    g, res = sobolev_gradient(gamma, edges, groups, dE, prm, dense=dense, precond=pc)
+    gn = float(np.linalg.norm(g))
+    if gn == 0.0:
+        return gamma.copy(), StepInfo(E0, E0, 0.0, 0.0, 0, 0, res.iters if res else 0, False)
+    d = g / gn
+    slope = float(np.vdot(dE, d))
+    apply_abar = make_apply(gamma, edges, prm.sigma)  # A-bar of the pre-step curve
+    tau = 1.0
+    for h in range(prm.max_halvings + 1):
+        cand = gamma - tau * d
+        cand, pit, ok = constraint_projection(cand, edges, groups, apply_abar, prm, pc)
+        if ok:
+            E1 = energy(cand, edges, prm.alpha, prm.beta)
+            if E1 <= E0 - prm.armijo_c * tau * slope:
+                return cand, StepInfo(E0, E1, tau, gn, h, pit, res.iters if res else 0, True)
+        tau *= prm.shrink
+    return gamma.copy(), StepInfo(E0, E0, 0.0, gn, prm.max_halvings, 0, res.iters if res else 0, False)
+
+
+# ----------------------------------------------------------------------------- spectral preconditioner
+
+def circle_symbol(n, sigma):
+    """Eigenvalues of the Gram matrix A = B + B0 of a regular n-gon, normalised by its diagonal.
+    The regular n-gon's A is circulant, so its eigenvalues are the DFT of its first column.
+    lambda_0 (the constant mode, 0) is replaced by lambda_1."""
+    g = np.stack([np.cos(2 * np.pi * np.arange(n) / n), np.sin(2 * np.pi * np.arange(n) / n), np.zeros(n)], 1)
+    e = np.stack([np.arange(n), (np.arange(n) + 1) % n], 1).astype(np.int32)
+    if n <= 1024:
+        B, B0 = gram_dense(g, e, sigma)
+        col = (B + B0)[:, 0]
+    else:
+        u = np.zeros(n)
+        u[0] = 1.0
+        col = gram_apply(g, e, sigma, u)
+    lam = np.real(np.fft.fft(col)) / col[0]
+    lam[0] = lam[1]
+    return lam
+
+
+def spectral_preconditioner(diagA, vertex_offsets, symbols):
+    """M^{-1} r = D^{-1/2} F^{-1} diag(1/lambda) F D^{-1/2} r on every closed curve (per component),
+    with D = diag(A) of the actual curve and lambda the normalised regular-polygon symbol."""
+    ds = np.sqrt(diagA)
+
+    def apply(r):
+        out = np.empty_like(r)
+        for c in range(len(vertex_offsets) - 1):
+            v0, v1 = vertex_offsets[c], vertex_offsets[c + 1]
+            s = r[v0:v1] / ds[v0:v1, None]
+            lam = symbols[v1 - v0]
+            y = np.real(np.fft.ifft(np.fft.fft(s, axis=0) / lam[:, None], axis=0))
+            out[v0:v1] = y / ds[v0:v1, None]
+        return out
+
+    return apply
+
+
+def gram_diagonal(gamma, edges, sigma):
+    """diag(A) by applying A to unit vectors would be O(n^3); instead read it off the dense build
+    for small n, or from rows of the matrix-free apply for selected vertices."""
+    n = gamma.shape[0]
+    B, B0 = gram_dense(gamma, edges, sigma)
+    return np.diag(B + B0).copy()
+
+
+def gram_diagonal_at(gamma, edges, sigma, vidx):
+    n = gamma.shape[0]
+    out = np.empty(len(vidx))
+    for k, v in enumerate(vidx):
+        u = np.zeros(n)
+        u[v] = 1.0
+        out[k] = gram_apply_at(gamma, edges, sigma, u, [v])[0, 0]
+    return out
