@@ -1,0 +1,662 @@
+// C ABI of the GB300 tangent-point library: context creation, the entry points of include/tpe.h,
+// and the host orchestration of a descent step (Sec. 5.4): gradient solve, normalised direction,
+// backtracking with constraint projection (Sec. 5.3.2 via App. B.3.4) and the Armijo test.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tpe_internal.cuh"
+
+using namespace tpe;
+
+namespace {
+
+tp_status fail(tp_ctx *ctx, tp_status st, const std::string &msg)
+{
+    if (ctx) ctx->c.err = msg;
+    return st;
+}
+
+tp_status cuda_fail(tp_ctx *ctx, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, TP_ERR_OOM, m);
+    return fail(ctx, TP_ERR_CUDA, m);
+}
+
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t e__ = (call);                           \
+        if (e__ != cudaSuccess) return cuda_fail(ctx, e__, #call); \
+    } while (0)
+
+bool params_ok(const tp_params *p, std::string &why)
+{
+    if (!(p->alpha > 1.0)) {
+        why = "alpha must be > 1";
+        return false;
+    }
+    if (!(p->beta >= p->alpha + 2.0 - 1e-12 && p->beta < 2.0 * p->alpha + 1.0)) {
+        why = "beta must lie in [alpha + 2, 2 alpha + 1)";
+        return false;
+    }
+    if (p->precision < TP_FP64 || p->precision > TP_MIXED) {
+        why = "bad precision";
+        return false;
+    }
+    if (p->precond < TP_PRECOND_NONE || p->precond > TP_PRECOND_SPECTRAL) {
+        why = "bad preconditioner";
+        return false;
+    }
+    if (!(p->cg_rtol > 0.0) || p->cg_maxit < 1 || !(p->shrink > 0.0 && p->shrink < 1.0) || p->max_halvings < 0 ||
+        p->proj_maxit < 0 || !(p->proj_tol > 0.0)) {
+        why = "bad solver or line-search parameter";
+        return false;
+    }
+    return true;
+}
+
+void set_kernel_params(Ctx &c)
+{
+    const tp_params &p = c.prm;
+    double sigma = std::isnan(p.sigma) ? (p.beta - 1.0) / p.alpha - 1.0 : p.sigma;
+    c.kp.alpha = p.alpha;
+    c.kp.beta = p.beta;
+    c.kp.p = 2.0 * sigma + 1.0;
+    c.kp.fast = (p.alpha == 2.0 && p.beta == 4.5 && c.kp.p == 2.5) ? 1 : 0;
+    double rn = p.near_cutoff * c.mean_ell;
+    c.kp.near2 = rn * rn;
+    c.kp.near2f = (float)(rn * rn);
+}
+
+// FP64 mean edge length of geometry `which` (host read; used to scale the near-pair cutoff).
+__global__ void k_sum_ell(int n, const double *ell, double *out)
+{
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += ell[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+tp_status check_err_word(tp_ctx *ctx, cudaStream_t s)
+{
+    Ctx &c = ctx->c;
+    int e = 0;
+    CK(cudaMemcpyAsync(c.h_pinned_i + 1, c.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    e = c.h_pinned_i[1];
+    if (e) {
+        CK(cudaMemsetAsync(c.d_err, 0, sizeof(int), s));
+        if (e == TP_ERR_DEGENERATE_EDGE) return fail(ctx, TP_ERR_DEGENERATE_EDGE, "an edge has zero length");
+        if (e == TP_ERR_NONFINITE) return fail(ctx, TP_ERR_NONFINITE, "non-finite vertex position");
+        return fail(ctx, (tp_status)e, "device error");
+    }
+    return TP_OK;
+}
+
+// Build the edge records of `gamma` into geometry slot `which`; on the first call also fix the
+// mean edge length that scales the near-pair cutoff.
+tp_status records(tp_ctx *ctx, const double *gamma, int which, cudaStream_t s)
+{
+    Ctx &c = ctx->c;
+    CK(build_records(c, gamma, which, s));
+    if (c.mean_ell == 0.0 && c.nE > 0) {
+        k_sum_ell<<<1, 256, 0, s>>>(c.nE, c.d_ellw[which], c.d_scal);
+        c.launches++;
+        CK(cudaMemcpyAsync(c.h_pinned, c.d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        c.mean_ell = c.h_pinned[0] / c.nE;
+        set_kernel_params(c);
+        tp_status st = check_err_word(ctx, s);
+        if (st != TP_OK) {
+            c.mean_ell = 0.0;
+            return st;
+        }
+    }
+    return TP_OK;
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    return cudaMalloc((void **)p, sizeof(T) * std::max<size_t>(1, n));
+}
+
+}  // namespace
+
+extern "C" {
+
+void tp_default_params(tp_params *p)
+{
+    if (!p) return;
+    p->alpha = 2.0;
+    p->beta = 4.5;
+    p->sigma = NAN;
+    p->precision = TP_FP32;
+    p->near_cutoff = 4.0;
+    p->cg_rtol = 1e-6;
+    p->cg_maxit = 20000;
+    p->cg_check_every = 8;
+    p->proj_cg_rtol = 1e-6;
+    p->precond = TP_PRECOND_SPECTRAL;
+    p->armijo_c = 1e-4;
+    p->shrink = 0.5;
+    p->max_halvings = 30;
+    p->proj_tol = 1e-10;
+    p->proj_maxit = 5;
+    p->independent = 0;
+}
+
+const char *tp_last_error(const tp_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
+
+int tp_num_problems(const tp_ctx *ctx) { return ctx ? ctx->c.nProb : 0; }
+
+int64_t tp_launch_count(const tp_ctx *ctx) { return ctx ? ctx->c.launches : 0; }
+
+void tp_destroy(tp_ctx *ctx)
+{
+    if (!ctx) return;
+    Ctx &c = ctx->c;
+    if (c.sol) solver_free(c);
+    void *ptrs[] = {c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_sym,
+                    c.d_curve_symoff, c.d_voff, c.d_twiddle, c.d_curve_twoff, c.d_fft_re, c.d_fft_im,
+                    c.plan_energy.d_items, c.plan_diff.d_items, c.plan_apply.d_items, c.plan_energy.d_eslots,
+                    c.plan_diff.d_eslots, c.plan_apply.d_eslots, c.d_counter, c.d_recF, c.d_recF2, c.d_recLo,
+                    c.d_recLo2, c.d_recD, c.d_recD2, c.d_ellw[0], c.d_ellw[1], c.d_Tw[0], c.d_Tw[1], c.d_xw[0],
+                    c.d_xw[1], c.d_urecF, c.d_urecD, c.d_part, c.d_rows, c.d_x0L0, c.d_Cv, c.d_G, c.d_Ginv,
+                    c.d_red, c.d_phi, c.d_y, c.d_r, c.d_z, c.d_p, c.d_q, c.d_diag, c.d_t1, c.d_t2, c.d_t3, c.d_t4,
+                    c.d_t5, c.d_t6, c.d_gam, c.d_best, c.d_E, c.d_scal, c.d_cg, c.d_err};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c.h_pinned) cudaFreeHost(c.h_pinned);
+    if (c.h_pinned_i) cudaFreeHost(c.h_pinned_i);
+    delete ctx;
+}
+
+tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int n_curves,
+                    const int32_t *voff_host, const int32_t *eoff_host, const tp_params *p)
+{
+    if (!out) return TP_ERR_INVALID_ARG;
+    *out = nullptr;
+    tp_ctx *ctx = new (std::nothrow) tp_ctx();
+    if (!ctx) return TP_ERR_OOM;
+    *out = ctx;
+    Ctx &c = ctx->c;
+    tp_params prm;
+    if (p)
+        prm = *p;
+    else
+        tp_default_params(&prm);
+    std::string why;
+    if (!params_ok(&prm, why)) return fail(ctx, TP_ERR_INVALID_ARG, why);
+    if (nV < 1 || nE < 0 || n_curves < 1 || (nE > 0 && !edges_host) || !voff_host || !eoff_host)
+        return fail(ctx, TP_ERR_INVALID_ARG, "bad graph sizes or null pointers");
+    if (voff_host[0] != 0 || eoff_host[0] != 0 || voff_host[n_curves] != nV || eoff_host[n_curves] != nE)
+        return fail(ctx, TP_ERR_INVALID_ARG, "curve offsets must start at 0 and end at n_vertices / n_edges");
+    for (int k = 0; k < n_curves; ++k)
+        if (voff_host[k + 1] < voff_host[k] || eoff_host[k + 1] < eoff_host[k])
+            return fail(ctx, TP_ERR_INVALID_ARG, "curve offsets must be non-decreasing");
+    c.prm = prm;
+    c.nV = nV;
+    c.nE = nE;
+    c.nCurves = n_curves;
+    c.independent = prm.independent ? 1 : 0;
+    c.h_edges.assign(edges_host, edges_host + 2 * (size_t)nE);
+    c.h_voff.assign(voff_host, voff_host + n_curves + 1);
+    c.h_eoff.assign(eoff_host, eoff_host + n_curves + 1);
+    // validate edges: in range, two distinct endpoints, inside their curve's vertex range
+    for (int k = 0; k < n_curves; ++k)
+        for (int I = eoff_host[k]; I < eoff_host[k + 1]; ++I) {
+            int a = edges_host[2 * I], b = edges_host[2 * I + 1];
+            if (a < voff_host[k] || a >= voff_host[k + 1] || b < voff_host[k] || b >= voff_host[k + 1] || a == b)
+                return fail(ctx, TP_ERR_INVALID_ARG, "edge " + std::to_string(I) + " is not a proper edge of its curve");
+        }
+    if (c.independent) {
+        c.nProb = n_curves;
+        c.h_prob_v = c.h_voff;
+        c.h_prob_e = c.h_eoff;
+    } else {
+        c.nProb = 1;
+        c.h_prob_v = {0, nV};
+        c.h_prob_e = {0, nE};
+    }
+    // closed-curve check for the spectral preconditioner: curve k's edges are (v0+i, v0+(i+1) mod n)
+    c.spectral_ok = 1;
+    c.h_curve_n.resize(n_curves);
+    for (int k = 0; k < n_curves; ++k) {
+        int v0 = voff_host[k], n = voff_host[k + 1] - v0, e0 = eoff_host[k], m = eoff_host[k + 1] - e0;
+        c.h_curve_n[k] = n;
+        c.max_curve_n = std::max(c.max_curve_n, n);
+        if (n != m || n < 4) {
+            c.spectral_ok = 0;
+            continue;
+        }
+        for (int i = 0; i < n; ++i)
+            if (edges_host[2 * (e0 + i)] != v0 + i || edges_host[2 * (e0 + i) + 1] != v0 + (i + 1) % n) {
+                c.spectral_ok = 0;
+                break;
+            }
+    }
+    if (prm.precond == TP_PRECOND_SPECTRAL && !c.spectral_ok)
+        return fail(ctx, TP_ERR_UNSUPPORTED,
+                    "the spectral preconditioner needs every curve to be a closed polygon (i, i+1 mod n) of >= 4 vertices");
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev));
+    // incidence lists
+    std::vector<int> deg(nV + 1, 0), inc(2 * (size_t)nE), vprob(nV), eprob(std::max(1, nE));
+    for (int I = 0; I < nE; ++I) {
+        deg[c.h_edges[2 * I] + 1]++;
+        deg[c.h_edges[2 * I + 1] + 1]++;
+    }
+    for (int v = 0; v < nV; ++v) deg[v + 1] += deg[v];
+    std::vector<int> fill(deg.begin(), deg.end() - 1);
+    for (int I = 0; I < nE; ++I)
+        for (int s = 0; s < 2; ++s) inc[fill[c.h_edges[2 * I + s]]++] = 2 * I + s;
+    for (int q = 0; q < c.nProb; ++q) {
+        for (int v = c.h_prob_v[q]; v < c.h_prob_v[q + 1]; ++v) vprob[v] = q;
+        for (int I = c.h_prob_e[q]; I < c.h_prob_e[q + 1]; ++I) eprob[I] = q;
+    }
+    const bool p64 = prm.precision == TP_FP64, mix = prm.precision == TP_MIXED;
+    CK(dalloc(&c.d_edges, 2 * (size_t)nE));
+    CK(cudaMemcpy(c.d_edges, c.h_edges.data(), sizeof(int) * 2 * nE, cudaMemcpyHostToDevice));
+    CK(dalloc(&c.d_inc_ptr, nV + 1));
+    CK(cudaMemcpy(c.d_inc_ptr, deg.data(), sizeof(int) * (nV + 1), cudaMemcpyHostToDevice));
+    CK(dalloc(&c.d_inc, 2 * (size_t)nE));
+    CK(cudaMemcpy(c.d_inc, inc.data(), sizeof(int) * 2 * nE, cudaMemcpyHostToDevice));
+    CK(dalloc(&c.d_vprob, nV));
+    CK(cudaMemcpy(c.d_vprob, vprob.data(), sizeof(int) * nV, cudaMemcpyHostToDevice));
+    CK(dalloc(&c.d_eprob, nE));
+    CK(cudaMemcpy(c.d_eprob, eprob.data(), sizeof(int) * std::max(1, nE), cudaMemcpyHostToDevice));
+    CK(dalloc(&c.d_prob_v, c.nProb + 1));
+    CK(cudaMemcpy(c.d_prob_v, c.h_prob_v.data(), sizeof(int) * (c.nProb + 1), cudaMemcpyHostToDevice));
+    CK(dalloc(&c.d_prob_e, c.nProb + 1));
+    CK(cudaMemcpy(c.d_prob_e, c.h_prob_e.data(), sizeof(int) * (c.nProb + 1), cudaMemcpyHostToDevice));
+    CK(dalloc(&c.d_voff, n_curves + 1));
+    CK(cudaMemcpy(c.d_voff, c.h_voff.data(), sizeof(int) * (n_curves + 1), cudaMemcpyHostToDevice));
+    for (int w = 0; w < 2; ++w) {
+        CK(dalloc(&c.d_ellw[w], nE));
+        CK(dalloc(&c.d_Tw[w], 3 * (size_t)nE));
+        CK(dalloc(&c.d_xw[w], 3 * (size_t)nE));
+    }
+    if (p64) {
+        CK(dalloc(&c.d_recD, nE));
+        CK(dalloc(&c.d_recD2, nE));
+        CK(dalloc(&c.d_urecD, nE));
+    } else {
+        CK(dalloc(&c.d_recF, nE));
+        CK(dalloc(&c.d_recF2, nE));
+        CK(dalloc(&c.d_urecF, nE));
+        if (mix) {
+            CK(dalloc(&c.d_recLo, nE));
+            CK(dalloc(&c.d_recLo2, nE));
+        }
+    }
+    CK(dalloc(&c.d_counter, 8));
+    CK(cudaMemset(c.d_counter, 0, sizeof(int) * 8));
+    set_kernel_params(c);
+    make_plans(c);
+    CK(cudaGetLastError());
+    int ms = std::max(std::max(c.plan_energy.max_slots, c.plan_diff.max_slots), c.plan_apply.max_slots);
+    c.part_elems = (size_t)ms * std::max(1, nE) * 6;
+    CK(dalloc(&c.d_part, c.part_elems));
+    CK(dalloc(&c.d_rows, nE));
+    CK(dalloc(&c.d_x0L0, 4 * (size_t)c.nProb));
+    CK(dalloc(&c.d_Cv, 12 * (size_t)nV));
+    CK(dalloc(&c.d_G, 16 * (size_t)c.nProb));
+    CK(dalloc(&c.d_Ginv, 16 * (size_t)c.nProb));
+    CK(dalloc(&c.d_red, 16 * (size_t)c.nProb));
+    CK(dalloc(&c.d_phi, 4 * (size_t)c.nProb));
+    double **vecs[] = {&c.d_y, &c.d_r, &c.d_z, &c.d_p, &c.d_q, &c.d_t1, &c.d_t2, &c.d_t3, &c.d_t4, &c.d_t5, &c.d_t6,
+                       &c.d_gam, &c.d_best};
+    for (double **v : vecs) CK(dalloc(v, 3 * (size_t)nV));
+    CK(cudaMemset(c.d_z, 0, sizeof(double) * 3 * nV));
+    CK(dalloc(&c.d_diag, nV));
+    CK(dalloc(&c.d_E, c.nProb));
+    CK(dalloc(&c.d_scal, 64 + 16 * (size_t)c.nProb));
+    CK(dalloc(&c.d_cg, c.nProb));
+    CK(dalloc(&c.d_err, 4));
+    CK(cudaMemset(c.d_err, 0, sizeof(int) * 4));
+    CK(cudaMallocHost(&c.h_pinned, sizeof(double) * (64 + 16 * (size_t)c.nProb)));
+    CK(cudaMallocHost(&c.h_pinned_i, sizeof(int) * 64));
+    CK(solver_setup(c));
+    if (prm.precond == TP_PRECOND_SPECTRAL) {
+        cudaError_t e = spectral_setup(c, 0);
+        if (e == cudaErrorNotSupported) return fail(ctx, TP_ERR_UNSUPPORTED, "spectral preconditioner not built");
+        CK(e);
+    }
+    CK(cudaDeviceSynchronize());
+    return TP_OK;
+}
+
+tp_status tp_set_params(tp_ctx *ctx, const tp_params *p)
+{
+    if (!ctx || !p) return TP_ERR_INVALID_ARG;
+    std::string why;
+    if (!params_ok(p, why)) return fail(ctx, TP_ERR_INVALID_ARG, why);
+    Ctx &c = ctx->c;
+    if (p->precision != c.prm.precision) return fail(ctx, TP_ERR_INVALID_ARG, "precision is fixed at creation");
+    if (p->precond == TP_PRECOND_SPECTRAL && !c.spectral_ok)
+        return fail(ctx, TP_ERR_UNSUPPORTED, "the spectral preconditioner needs closed polygons");
+    int indep = c.prm.independent;
+    int had_spectral = c.prm.precond == TP_PRECOND_SPECTRAL || c.d_sym != nullptr;
+    c.prm = *p;
+    c.prm.independent = indep;
+    set_kernel_params(c);
+    if (p->precond == TP_PRECOND_SPECTRAL && !had_spectral) {
+        cudaError_t e = spectral_setup(c, 0);
+        if (e == cudaErrorNotSupported) return fail(ctx, TP_ERR_UNSUPPORTED, "spectral preconditioner not built");
+        CK(e);
+        CK(cudaDeviceSynchronize());
+    }
+    return TP_OK;
+}
+
+tp_status tp_energy(tp_ctx *ctx, const double *gamma, double *E, double *rows, tp_stream stream)
+{
+    if (!ctx || !gamma) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    CK(pair_energy(ctx->c, gamma, 0, rows, E, s));
+    return TP_OK;
+}
+
+tp_status tp_differential(tp_ctx *ctx, const double *gamma, double *dE, double *E, tp_stream stream)
+{
+    if (!ctx || !gamma || !dE) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    CK(pair_diff(ctx->c, gamma, 0, dE, s));
+    if (E) CK(pair_energy(ctx->c, gamma, 0, nullptr, E, s));
+    return TP_OK;
+}
+
+tp_status sobolev_apply(tp_ctx *ctx, const double *gamma, const double *u, double *Au, tp_stream stream)
+{
+    if (!ctx || !gamma || !u || !Au) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    CK(pair_apply(ctx->c, gamma, 0, u, Au, s));
+    return TP_OK;
+}
+
+tp_status tp_gram_diagonal(tp_ctx *ctx, const double *gamma, double *diag, tp_stream stream)
+{
+    if (!ctx || !gamma || !diag) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    CK(pair_diag(ctx->c, gamma, 0, diag, s));
+    return TP_OK;
+}
+
+tp_status tp_set_constraints_from(tp_ctx *ctx, const double *gamma, tp_stream stream)
+{
+    if (!ctx || !gamma) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    CK(constraints_targets(ctx->c, 0, s));
+    ctx->c.constraints_set = 1;
+    return TP_OK;
+}
+
+tp_status tp_constraints(tp_ctx *ctx, const double *gamma, double *phi, tp_stream stream)
+{
+    if (!ctx || !gamma || !phi) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    if (!ctx->c.constraints_set) {
+        CK(constraints_targets(ctx->c, 0, s));
+        ctx->c.constraints_set = 1;
+    }
+    CK(constraints_eval(ctx->c, gamma, 0, phi, s));
+    return TP_OK;
+}
+
+tp_status tp_precond_apply(tp_ctx *ctx, const double *gamma, const double *r, double *z, tp_stream stream)
+{
+    if (!ctx || !gamma || !r || !z) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx &c = ctx->c;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    if (c.prm.precond != TP_PRECOND_NONE) CK(pair_diag(c, gamma, 0, c.d_diag, s));
+    CK(precond_apply(c, r, z, s, nullptr));
+    return TP_OK;
+}
+
+// Preconditioner set-up for the geometry in slot 0.
+static tp_status precond_setup(tp_ctx *ctx, const double *gamma, cudaStream_t s)
+{
+    Ctx &c = ctx->c;
+    if (c.prm.precond != TP_PRECOND_NONE) CK(pair_diag(c, gamma, 0, c.d_diag, s));
+    return TP_OK;
+}
+
+tp_status sobolev_gradient(tp_ctx *ctx, const double *gamma, const double *dE, double *g, tp_solve_info *info,
+                           tp_stream stream)
+{
+    if (!ctx || !gamma || !dE || !g) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx &c = ctx->c;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    if (!c.constraints_set) {
+        CK(constraints_targets(c, 0, s));
+        c.constraints_set = 1;
+    }
+    CK(constraints_jacobian(c, 0, s));
+    st = precond_setup(ctx, gamma, s);
+    if (st) return st;
+    int it = 0, conv = 0, bd = 0;
+    double rr = 0.0;
+    CK(cg_solve(c, gamma, 0, dE, g, c.prm.cg_rtol, c.prm.cg_maxit, &it, &rr, &conv, &bd, s));
+    if (info) {
+        info->iters = it;
+        info->rel_res = rr;
+        info->converged = conv;
+    }
+    st = check_err_word(ctx, s);
+    if (st) return st;
+    if (bd) return fail(ctx, TP_ERR_BREAKDOWN, "CG breakdown: p^T A p <= 0");
+    if (!conv) return fail(ctx, TP_ERR_NOT_CONVERGED, "CG did not reach cg_rtol within cg_maxit");
+    return TP_OK;
+}
+
+// gamma_out = gamma_in - tau_q d (per problem)
+__global__ void k_trial(int nV, const double *__restrict__ g, const double *__restrict__ d,
+                        const double *__restrict__ tau, const int *__restrict__ vprob, double *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    double t = tau[vprob[i]];
+    for (int k = 0; k < 3; ++k) out[3 * i + k] = g[3 * i + k] - t * d[3 * i + k];
+}
+
+// dst[v] = src[v] for the vertices of problems with mask[q] != 0
+__global__ void k_copy_masked(int nV, const double *__restrict__ src, const int *__restrict__ mask,
+                              const int *__restrict__ vprob, double *__restrict__ dst)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    if (!mask[vprob[i]]) return;
+    for (int k = 0; k < 3; ++k) dst[3 * i + k] = src[3 * i + k];
+}
+
+// x += a * y
+__global__ void k_add(int n, double *__restrict__ x, const double *__restrict__ a, const double *__restrict__ b)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] += a[i] - b[i];
+}
+
+tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream stream)
+{
+    if (!ctx || !gamma) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx &c = ctx->c;
+    const int nP = c.nProb, nV = c.nV;
+    const size_t vb = sizeof(double) * 3 * nV;
+    const int nb = (nV + 255) / 256;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    if (!c.constraints_set) {
+        CK(constraints_targets(c, 0, s));
+        c.constraints_set = 1;
+    }
+    // E(gamma), dE(gamma)
+    double *E0 = c.d_scal + 64, *E1 = c.d_scal + 64 + nP, *gg = c.d_scal + 64 + 2 * nP,
+           *slope = c.d_scal + 64 + 3 * nP, *tau_d = c.d_scal + 64 + 4 * nP;
+    double *dE = c.d_t1, *g = c.d_t2, *dir = c.d_t3, *z = c.d_t4, *rhs = c.d_t5, *x = c.d_t6;
+    CK(pair_energy(c, gamma, 0, nullptr, E0, s));
+    CK(pair_diff(c, gamma, 0, dE, s));
+    // g~ = projected H^s gradient
+    CK(constraints_jacobian(c, 0, s));
+    st = precond_setup(ctx, gamma, s);
+    if (st) return st;
+    int it = 0, conv = 0, bd = 0;
+    double rr = 0.0;
+    CK(cg_solve(c, gamma, 0, dE, g, c.prm.cg_rtol, c.prm.cg_maxit, &it, &rr, &conv, &bd, s));
+    if (bd) return fail(ctx, TP_ERR_BREAKDOWN, "CG breakdown in the gradient solve");
+    // d = g / |g| per problem, slope = <dE, d>
+    CK(vec_dot(c, g, g, gg, s));
+    CK(vec_scale_dev(c, g, gg, 1, dir, s));
+    CK(vec_dot(c, dE, dir, slope, s));
+    std::vector<double> hE0(nP), hgg(nP), hslope(nP), hE1(nP), hphi(4 * (size_t)nP), hx0L0(4 * (size_t)nP);
+    CK(cudaMemcpyAsync(hE0.data(), E0, sizeof(double) * nP, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hgg.data(), gg, sizeof(double) * nP, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hslope.data(), slope, sizeof(double) * nP, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hx0L0.data(), c.d_x0L0, sizeof(double) * 4 * nP, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st = check_err_word(ctx, s);
+    if (st) return st;
+    // per-problem line search state
+    std::vector<double> tau(nP, 1.0), acc_tau(nP, 0.0);
+    std::vector<int> pending(nP, 1), accepted(nP, 0), acc_halv(nP, 0), acc_pit(nP, 0);
+    for (int q = 0; q < nP; ++q)
+        if (!(hgg[q] > 0.0)) {
+            pending[q] = 0;
+            accepted[q] = 1;
+            hE1[q] = hE0[q];
+        }
+    int proj_cg_total = 0;
+    int *mask_dev = reinterpret_cast<int *>(c.d_scal + 64 + 5 * nP);  // nP ints fit in 8 nP doubles
+    CK(cudaMemcpyAsync(c.d_best, gamma, vb, cudaMemcpyDeviceToDevice, s));
+    for (int h = 0; h <= c.prm.max_halvings; ++h) {
+        int npend = 0;
+        for (int q = 0; q < nP; ++q) npend += pending[q];
+        if (npend == 0) break;
+        // trial = gamma - tau d (problems not pending use tau 0)
+        std::vector<double> tq(nP);
+        for (int q = 0; q < nP; ++q) tq[q] = pending[q] ? tau[q] : 0.0;
+        CK(cudaMemcpyAsync(tau_d, tq.data(), sizeof(double) * nP, cudaMemcpyHostToDevice, s));
+        k_trial<<<nb, 256, 0, s>>>(nV, gamma, dir, tau_d, c.d_vprob, c.d_gam);
+        c.launches++;
+        // constraint projection
+        std::vector<int> ok(nP, 0), pit(nP, 0);
+        for (int pi = 0;; ++pi) {
+            st = records(ctx, c.d_gam, 1, s);
+            if (st) return st;
+            CK(constraints_eval(c, c.d_gam, 1, c.d_phi, s));
+            CK(cudaMemcpyAsync(hphi.data(), c.d_phi, sizeof(double) * 4 * nP, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            st = check_err_word(ctx, s);
+            if (st) return st;
+            int all = 1;
+            for (int q = 0; q < nP; ++q) {
+                double m = 0.0;
+                for (int k = 0; k < 4; ++k) m = std::max(m, std::fabs(hphi[4 * q + k]));
+                ok[q] = std::isfinite(m) && m <= c.prm.proj_tol * std::max(1.0, hx0L0[4 * q + 3]);
+                if (pending[q] && !ok[q]) all = 0;
+            }
+            if (all || pi >= c.prm.proj_maxit) break;
+            for (int q = 0; q < nP; ++q)
+                if (pending[q] && !ok[q]) pit[q] = pi + 1;
+            // z = C^+ (-Phi) at the trial curve; rhs = A-bar(gamma) z; P A-bar P y = P rhs; trial += z - y
+            CK(constraints_jacobian(c, 1, s));
+            CK(pinv_apply(c, c.d_phi, -1.0, z, s));
+            CK(pair_apply(c, gamma, 0, z, rhs, s));
+            int pit_cg = 0, pconv = 0, pbd = 0;
+            double prr = 0.0;
+            CK(cg_solve(c, gamma, 0, rhs, x, c.prm.proj_cg_rtol, c.prm.cg_maxit, &pit_cg, &prr, &pconv, &pbd, s));
+            proj_cg_total += pit_cg;
+            k_add<<<(3 * nV + 255) / 256, 256, 0, s>>>(3 * nV, c.d_gam, z, x);
+            c.launches++;
+        }
+        // energy of the projected trial and the Armijo test
+        st = records(ctx, c.d_gam, 1, s);
+        if (st) return st;
+        CK(pair_energy(c, c.d_gam, 1, nullptr, E1, s));
+        std::vector<double> e1(nP);
+        CK(cudaMemcpyAsync(e1.data(), E1, sizeof(double) * nP, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        std::vector<int> acc_now(nP, 0);
+        for (int q = 0; q < nP; ++q) {
+            if (!pending[q]) continue;
+            if (ok[q] && std::isfinite(e1[q]) && e1[q] <= hE0[q] - c.prm.armijo_c * tau[q] * hslope[q]) {
+                acc_now[q] = 1;
+                accepted[q] = 1;
+                pending[q] = 0;
+                acc_tau[q] = tau[q];
+                acc_halv[q] = h;
+                acc_pit[q] = pit[q];
+                hE1[q] = e1[q];
+            } else {
+                tau[q] *= c.prm.shrink;
+            }
+        }
+        CK(cudaMemcpyAsync(mask_dev, acc_now.data(), sizeof(int) * nP, cudaMemcpyHostToDevice, s));
+        k_copy_masked<<<nb, 256, 0, s>>>(nV, c.d_gam, mask_dev, c.d_vprob, c.d_best);
+        c.launches++;
+    }
+    int nacc = 0;
+    for (int q = 0; q < nP; ++q) {
+        if (!accepted[q]) hE1[q] = hE0[q];
+        nacc += accepted[q];
+    }
+    CK(cudaMemcpyAsync(gamma, c.d_best, vb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    if (info) {
+        double a = 0, b = 0, gn = 0, tmax = 0;
+        int hmax = 0, pmax = 0;
+        for (int q = 0; q < nP; ++q) {
+            a += hE0[q];
+            b += hE1[q];
+            gn += hgg[q];
+            tmax = std::max(tmax, acc_tau[q]);
+            hmax = std::max(hmax, acc_halv[q]);
+            pmax = std::max(pmax, acc_pit[q]);
+        }
+        info->E_before = a;
+        info->E_after = b;
+        info->tau = tmax;
+        info->gnorm = std::sqrt(gn);
+        info->halvings = hmax;
+        info->proj_iters = pmax;
+        info->cg_iters = it;
+        info->proj_cg_iters = proj_cg_total;
+        info->accepted = nacc;
+        info->rel_res = rr;
+    }
+    if (nacc < nP) return fail(ctx, TP_ERR_LINESEARCH, "line search failed for some problem");
+    return TP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1122 @@
+// Pair passes of the tangent-point library: the O(|E|^2) loops over ordered pairs of edges that
+// share no vertex.  Every pass is a gather: one thread owns TPT target edges I and loops over all
+// source edges J staged through shared memory, so each output row is written by exactly one thread
+// (no atomics, deterministic).  A persistent grid pulls (target block, source chunk) items from a
+// queue; chunk results land in partial slots that a second kernel sums per row and gathers to the
+// vertices through the vertex->edge incidence lists.
+//
+//   energy  : E_I   = sum_J E_IJ,  E_IJ = (1/4) l_I l_J sum_{a,b} k(g_ia, g_jb, T_I)   (Eqs. 3, 17-18)
+//   diff    : d/d(g_i1, g_i2) of sum_J (E_IJ + E_JI)                                 (Sec. 5.1)
+//   apply   : h_I = sum_J 2 w_IJ (du_I - <T_I,T_J> du_J),  l_I = sum_J (w0_IJ + w0_JI)(ub_I - ub_J)
+//             (A u)_{i1,i2} = -/+ h_I / l_I + l_I / 2                                 (Secs. 5.2.2-5.2.3)
+//   diag    : diag(A)_v = sum_{I ni v} [2 sum_J w_IJ / l_I^2 + sum_J (w0_IJ + w0_JI) / 4]
+//
+// w_IJ = (1/4) l_I l_J sum_ab |d|^-p and w0_IJ = (1/4) l_I l_J sum_ab |T_I x d|^2 |d|^-(4+p) with
+// d = g_ia - g_jb and p = 2 sigma + 1.  The quadratic forms of Eq. 21 and Sec. 5.2.3 reduce to these
+// row sums because w_IJ is symmetric in (I, J) and only w0_IJ + w0_JI enters the low-order form.
+//
+// Precision (template PREC): P64 all FP64; P32 FP32 pair arithmetic with the partial sums of every
+// tile folded into FP64 accumulators; PMIX as P32 but positions are double-float (hi + lo) so that
+// d = g_ia - g_jb keeps full FP32 relative accuracy, and pairs with |g_i1 - g_j1| below the near
+// cutoff are evaluated in FP64 from the FP64 inputs instead.
+//
+// |T x d|^2 is formed as |d - (T.d) T|^2 (never as |d|^2 - (T.d)^2, which cancels for the nearly
+// parallel pairs along the curve).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tpe_internal.cuh"
+
+namespace tpe {
+
+#define TPE_CHECK(x)                          \
+    do {                                      \
+        cudaError_t e_ = (x);                 \
+        if (e_ != cudaSuccess) return e_;     \
+    } while (0)
+
+// ---------------------------------------------------------------------------------- K0: edge records
+
+__global__ void k_records(int nE, const double *__restrict__ g, const int *__restrict__ E, RecF *__restrict__ recF,
+                          RecLo *__restrict__ recLo, RecD *__restrict__ recD, double *__restrict__ ell,
+                          double *__restrict__ T, double *__restrict__ x, int *__restrict__ err)
+{
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nE) return;
+    int i1 = E[2 * I], i2 = E[2 * I + 1];
+    double p1[3], p2[3], e[3];
+    for (int k = 0; k < 3; ++k) {
+        p1[k] = g[3 * i1 + k];
+        p2[k] = g[3 * i2 + k];
+        e[k] = p2[k] - p1[k];
+    }
+    double l = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    bool fin = isfinite(l) && isfinite(p1[0] + p1[1] + p1[2]) && isfinite(p2[0] + p2[1] + p2[2]);
+    if (!fin) {
+        atomicCAS(err, 0, (int)TP_ERR_NONFINITE);
+        l = 1.0;
+    } else if (!(l > 0.0)) {
+        atomicCAS(err, 0, (int)TP_ERR_DEGENERATE_EDGE);
+        l = 1.0;
+    }
+    double t[3] = {e[0] / l, e[1] / l, e[2] / l};
+    ell[I] = l;
+    for (int k = 0; k < 3; ++k) {
+        T[3 * I + k] = t[k];
+        x[3 * I + k] = 0.5 * (p1[k] + p2[k]);
+    }
+    if (recF) {
+        float h1[3], h2[3];
+        for (int k = 0; k < 3; ++k) {
+            h1[k] = (float)p1[k];
+            h2[k] = (float)p2[k];
+        }
+        RecF r;
+        r.a = make_float4(h1[0], h1[1], h1[2], (float)l);
+        r.b = make_float4(h2[0], h2[1], h2[2], (float)t[0]);
+        r.c = make_float4((float)t[1], (float)t[2], __int_as_float(i1), __int_as_float(i2));
+        recF[I] = r;
+        if (recLo) {
+            RecLo q;
+            q.lo = make_float4((float)(p1[0] - (double)h1[0]), (float)(p1[1] - (double)h1[1]),
+                               (float)(p1[2] - (double)h1[2]), (float)(p2[0] - (double)h2[0]));
+            q.lo2 = make_float4((float)(p2[1] - (double)h2[1]), (float)(p2[2] - (double)h2[2]), 0.f, 0.f);
+            recLo[I] = q;
+        }
+    }
+    if (recD) {
+        RecD r;
+        r.a0 = make_double2(p1[0], p1[1]);
+        r.a1 = make_double2(p1[2], l);
+        r.b0 = make_double2(p2[0], p2[1]);
+        r.b1 = make_double2(p2[2], t[0]);
+        r.c0 = make_double2(t[1], t[2]);
+        r.i1 = i1;
+        r.i2 = i2;
+        r.pad0 = r.pad1 = 0;
+        recD[I] = r;
+    }
+}
+
+// Per-edge data of u for an apply: du = (u_j2 - u_j1)/l_J, ub = (u_j1 + u_j2)/2 (3 components).
+__global__ void k_urecs(int nE, const double *__restrict__ u, const int *__restrict__ E,
+                        const double *__restrict__ ell, URecF *__restrict__ uf, URecD *__restrict__ ud)
+{
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nE) return;
+    int i1 = E[2 * I], i2 = E[2 * I + 1];
+    double l = ell[I], du[3], ub[3];
+    for (int k = 0; k < 3; ++k) {
+        double a = u[3 * i1 + k], b = u[3 * i2 + k];
+        du[k] = (b - a) / l;
+        ub[k] = 0.5 * (a + b);
+    }
+    if (uf) {
+        float dh[3], uh[3], dl[3], ul[3];
+        for (int k = 0; k < 3; ++k) {
+            dh[k] = (float)du[k];
+            uh[k] = (float)ub[k];
+            dl[k] = (float)(du[k] - (double)dh[k]);
+            ul[k] = (float)(ub[k] - (double)uh[k]);
+        }
+        URecF r;
+        r.a = make_float4(dh[0], dh[1], dh[2], uh[0]);
+        r.b = make_float4(uh[1], uh[2], dl[0], dl[1]);
+        r.c = make_float4(dl[2], ul[0], ul[1], ul[2]);
+        uf[I] = r;
+    }
+    if (ud) {
+        URecD r;
+        r.du0 = make_double2(du[0], du[1]);
+        r.du1 = make_double2(du[2], 0.0);
+        r.ub0 = make_double2(ub[0], ub[1]);
+        r.ub1 = make_double2(ub[2], 0.0);
+        ud[I] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------------- powers
+
+// 1/d2 and |d|^-e from d2 = |d|^2.  Fast paths: e = 4.5 (energy, differential) and e = 2.5 (Gram
+// weights) from r = d2^-1/2 as r^4 sqrt(r) and r^2 sqrt(r), sqrt(r) = r rsqrt(r).
+template <class R, bool FAST, int WHICH>  // WHICH 0: beta (4.5 fast), 1: p (2.5 fast)
+__device__ __forceinline__ R inv_pow(R d2, R e, R &r2)
+{
+    if constexpr (FAST) {
+        if constexpr (sizeof(R) == 4) {
+            float r = rsqrtf(d2);
+            float sr = r * rsqrtf(r);
+            r2 = r * r;
+            return WHICH == 0 ? r2 * r2 * sr : r2 * sr;
+        } else {
+            double r = rsqrt(d2);
+            double sr = sqrt(r);
+            r2 = r * r;
+            return WHICH == 0 ? r2 * r2 * sr : r2 * sr;
+        }
+    } else {
+        if constexpr (sizeof(R) == 4) {
+            r2 = __frcp_rn(d2);
+            return exp2f(-0.5f * e * log2f(d2));
+        } else {
+            r2 = 1.0 / d2;
+            return pow(d2, -0.5 * e);
+        }
+    }
+}
+
+// |c|^alpha with c2 = |c|^2 (alpha = 2 in the fast path).
+template <class R, bool FAST>
+__device__ __forceinline__ R pow_c(R c2, R alpha)
+{
+    if constexpr (FAST) {
+        return c2;
+    } else {
+        if constexpr (sizeof(R) == 4)
+            return c2 > 0.f ? exp2f(0.5f * alpha * log2f(c2)) : 0.f;
+        else
+            return c2 > 0.0 ? pow(c2, 0.5 * alpha) : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------------- target / source views
+
+template <class R>
+struct V3 {
+    R x, y, z;
+};
+
+template <class R>
+__device__ __forceinline__ R dot3(V3<R> a, V3<R> b)
+{
+    return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+
+// Target edge data held in registers.
+template <class R>
+struct Tgt {
+    V3<R> p1, p2, T;   // hi parts (PMIX) or the values
+    V3<R> l1, l2;      // lo parts (PMIX only)
+    R ell;
+    int i1, i2;
+};
+
+template <int PREC>
+struct RealOf {
+    using type = float;
+};
+template <>
+struct RealOf<P64> {
+    using type = double;
+};
+
+// Shared-memory tile of source records.
+template <int PREC, bool NEEDU>
+struct Tile;
+template <bool NEEDU>
+struct Tile<P64, NEEDU> {
+    RecD r[kTile];
+    URecD u[NEEDU ? kTile : 1];
+};
+template <bool NEEDU>
+struct Tile<P32, NEEDU> {
+    RecF r[kTile];
+    URecF u[NEEDU ? kTile : 1];
+};
+template <bool NEEDU>
+struct Tile<PMIX, NEEDU> {
+    RecF r[kTile];
+    RecLo lo[kTile];
+    URecF u[NEEDU ? kTile : 1];
+};
+
+template <int PREC>
+__device__ __forceinline__ void load_target(Tgt<typename RealOf<PREC>::type> &t, int I, const RecF *recF,
+                                            const RecLo *recLo, const RecD *recD)
+{
+    if constexpr (PREC == P64) {
+        RecD r = recD[I];
+        t.p1 = {r.a0.x, r.a0.y, r.a1.x};
+        t.ell = r.a1.y;
+        t.p2 = {r.b0.x, r.b0.y, r.b1.x};
+        t.T = {r.b1.y, r.c0.x, r.c0.y};
+        t.i1 = r.i1;
+        t.i2 = r.i2;
+        t.l1 = {0, 0, 0};
+        t.l2 = {0, 0, 0};
+    } else {
+        RecF r = recF[I];
+        t.p1 = {r.a.x, r.a.y, r.a.z};
+        t.ell = r.a.w;
+        t.p2 = {r.b.x, r.b.y, r.b.z};
+        t.T = {r.b.w, r.c.x, r.c.y};
+        t.i1 = __float_as_int(r.c.z);
+        t.i2 = __float_as_int(r.c.w);
+        if constexpr (PREC == PMIX) {
+            RecLo q = recLo[I];
+            t.l1 = {q.lo.x, q.lo.y, q.lo.z};
+            t.l2 = {q.lo.w, q.lo2.x, q.lo2.y};
+        } else {
+            t.l1 = {0.f, 0.f, 0.f};
+            t.l2 = {0.f, 0.f, 0.f};
+        }
+    }
+}
+
+template <int PREC>
+struct Src {
+    using R = typename RealOf<PREC>::type;
+    V3<R> q1, q2, T, m1, m2;  // m = lo parts
+    R ell;
+    int j1, j2;
+};
+
+template <int PREC, bool NEEDU>
+__device__ __forceinline__ void load_source(Src<PREC> &s, const Tile<PREC, NEEDU> &tl, int j)
+{
+    if constexpr (PREC == P64) {
+        const RecD &r = tl.r[j];
+        const double2 a0 = r.a0, a1 = r.a1, b0 = r.b0, b1 = r.b1, c0 = r.c0;
+        s.q1 = V3<double>{a0.x, a0.y, a1.x};
+        s.ell = a1.y;
+        s.q2 = V3<double>{b0.x, b0.y, b1.x};
+        s.T = V3<double>{b1.y, c0.x, c0.y};
+        s.j1 = r.i1;
+        s.j2 = r.i2;
+    } else {
+        float4 a = tl.r[j].a, b = tl.r[j].b, c = tl.r[j].c;
+        s.q1 = {a.x, a.y, a.z};
+        s.ell = a.w;
+        s.q2 = {b.x, b.y, b.z};
+        s.T = {b.w, c.x, c.y};
+        s.j1 = __float_as_int(c.z);
+        s.j2 = __float_as_int(c.w);
+        if constexpr (PREC == PMIX) {
+            float4 l = tl.lo[j].lo, l2 = tl.lo[j].lo2;
+            s.m1 = {l.x, l.y, l.z};
+            s.m2 = {l.w, l2.x, l2.y};
+        }
+    }
+}
+
+// d = p - q (double-float positions in PMIX: hi difference plus lo difference).
+template <int PREC, class R>
+__device__ __forceinline__ V3<R> diff3(V3<R> p, V3<R> pl, V3<R> q, V3<R> ql)
+{
+    V3<R> d = {p.x - q.x, p.y - q.y, p.z - q.z};
+    if constexpr (PREC == PMIX) {
+        d.x += pl.x - ql.x;
+        d.y += pl.y - ql.y;
+        d.z += pl.z - ql.z;
+    }
+    return d;
+}
+
+// |d - (T.d) T|^2 = |T x d|^2 for unit T; also returns t = T.d.
+template <class R>
+__device__ __forceinline__ R perp2(V3<R> d, V3<R> T, R &t, V3<R> &dp)
+{
+    t = dot3(T, d);
+    dp = {d.x - t * T.x, d.y - t * T.y, d.z - t * T.z};
+    return dot3(dp, dp);
+}
+
+// ---------------------------------------------------------------------------------- FP64 near-pair paths
+
+struct NearArgs {
+    const double *g;    // [nV][3]
+    const int *E;       // [nE][2]
+    const double *ell;  // [nE]
+    const double *T;    // [nE][3]
+    const double *u;    // [nV][3] (apply)
+};
+
+__device__ __forceinline__ V3<double> ld3(const double *a, int i) { return {a[3 * i], a[3 * i + 1], a[3 * i + 2]}; }
+
+// l_J sum_ab k(g_ia, g_jb, T_I) in FP64.
+__device__ __noinline__ double near_energy(const NearArgs na, int I, int J, double alpha, double beta)
+{
+    V3<double> TI = ld3(na.T, I);
+    int ii[2] = {na.E[2 * I], na.E[2 * I + 1]}, jj[2] = {na.E[2 * J], na.E[2 * J + 1]};
+    double s = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            V3<double> p = ld3(na.g, ii[a]), q = ld3(na.g, jj[b]);
+            V3<double> d = {p.x - q.x, p.y - q.y, p.z - q.z}, dp;
+            double t, c2 = perp2(d, TI, t, dp), d2 = dot3(d, d);
+            s += pow(c2, 0.5 * alpha) * pow(d2, -0.5 * beta);
+        }
+    return na.ell[J] * s;
+}
+
+// Differential accumulators of one target against its sources (all scaled by l_J):
+//   S  = sum (fI + fJ);  G1, G2 = sum d/dp (fI + fJ) at p = g_i1, g_i2;  GT = sum d fI / d T_I
+struct DiffAcc64 {
+    double S, G1[3], G2[3], GT[3];
+};
+
+__device__ __noinline__ void near_diff(const NearArgs na, int I, int J, double alpha, double beta, DiffAcc64 &acc)
+{
+    V3<double> TI = ld3(na.T, I), TJ = ld3(na.T, J);
+    int ii[2] = {na.E[2 * I], na.E[2 * I + 1]}, jj[2] = {na.E[2 * J], na.E[2 * J + 1]};
+    double L = na.ell[J];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            V3<double> p = ld3(na.g, ii[a]), q = ld3(na.g, jj[b]);
+            V3<double> d = {p.x - q.x, p.y - q.y, p.z - q.z}, dpI, dpJ;
+            double tI, tJ;
+            double cI2 = perp2(d, TI, tI, dpI), cJ2 = perp2(d, TJ, tJ, dpJ), d2 = dot3(d, d);
+            double rb = pow(d2, -0.5 * beta);
+            double fI = pow(cI2, 0.5 * alpha) * rb, fJ = pow(cJ2, 0.5 * alpha) * rb;
+            double aI = cI2 > 0.0 ? alpha * fI / cI2 : 0.0, aJ = cJ2 > 0.0 ? alpha * fJ / cJ2 : 0.0;
+            double cb = beta * (fI + fJ) / d2;
+            double *G = a == 0 ? acc.G1 : acc.G2;
+            G[0] += L * (aI * dpI.x + aJ * dpJ.x - cb * d.x);
+            G[1] += L * (aI * dpI.y + aJ * dpJ.y - cb * d.y);
+            G[2] += L * (aI * dpI.z + aJ * dpJ.z - cb * d.z);
+            acc.GT[0] += -L * aI * tI * d.x;
+            acc.GT[1] += -L * aI * tI * d.y;
+            acc.GT[2] += -L * aI * tI * d.z;
+            acc.S += L * (fI + fJ);
+        }
+}
+
+// Apply accumulators (scaled by l_J), in the exact difference form
+//   du_I - <T_I,T_J> du_J = (du_I - du_J) + (|T_I - T_J|^2 / 2) du_J:
+//   A1 = sum W [(du_I - du_J) + (1 - t_IJ) du_J],  A2 = sum W0 (ub_I - ub_J),
+// with W = l_J sum_ab |d|^-p and W0 = l_J sum_ab (|T_I x d|^2 + |T_J x d|^2) |d|^-(4+p).
+// Sw, Sw0 are the u-independent row sums used for diag(A).
+struct ApplyAcc64 {
+    double Sw, A1[3], Sw0, A2[3];
+};
+
+__device__ __noinline__ void near_apply(const NearArgs na, int I, int J, double p, bool with_u, ApplyAcc64 &acc)
+{
+    V3<double> TI = ld3(na.T, I), TJ = ld3(na.T, J);
+    int ii[2] = {na.E[2 * I], na.E[2 * I + 1]}, jj[2] = {na.E[2 * J], na.E[2 * J + 1]};
+    double sw = 0.0, sw0 = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            V3<double> q = ld3(na.g, jj[b]), pp = ld3(na.g, ii[a]);
+            V3<double> d = {pp.x - q.x, pp.y - q.y, pp.z - q.z}, dpI, dpJ;
+            double tI, tJ;
+            double c2 = perp2(d, TI, tI, dpI) + perp2(d, TJ, tJ, dpJ), d2 = dot3(d, d);
+            double rp = pow(d2, -0.5 * p);
+            sw += rp;
+            sw0 += c2 * rp / (d2 * d2);
+        }
+    double L = na.ell[J];
+    double W = L * sw, W0 = L * sw0;
+    acc.Sw += W;
+    acc.Sw0 += W0;
+    if (with_u) {
+        double lI = na.ell[I];
+        V3<double> dT = {TI.x - TJ.x, TI.y - TJ.y, TI.z - TJ.z};
+        double omt = 0.5 * dot3(dT, dT);
+        for (int k = 0; k < 3; ++k) {
+            double duI = (na.u[3 * ii[1] + k] - na.u[3 * ii[0] + k]) / lI;
+            double duJ = (na.u[3 * jj[1] + k] - na.u[3 * jj[0] + k]) / L;
+            double ubI = 0.5 * (na.u[3 * ii[0] + k] + na.u[3 * ii[1] + k]);
+            double ubJ = 0.5 * (na.u[3 * jj[0] + k] + na.u[3 * jj[1] + k]);
+            acc.A1[k] += W * ((duI - duJ) + omt * duJ);
+            acc.A2[k] += W0 * (ubI - ubJ);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------- the pair kernel
+
+struct PairArgs {
+    const WorkItem *items;
+    int n_items;
+    int *counter;
+    const RecF *recF;
+    const RecLo *recLo;
+    const RecD *recD;
+    const URecF *urecF;
+    const URecD *urecD;
+    NearArgs na;
+    double *part;  // [slot][nE][stride]
+    int nE;
+    KernelParams kp;
+};
+
+template <int PREC, int OP>
+struct Acc32;  // per-target tile accumulators in the pair precision
+
+template <int PREC>
+struct Acc32<PREC, OP_ENERGY> {
+    static constexpr int op = OP_ENERGY;
+    typename RealOf<PREC>::type s;
+};
+template <int PREC>
+struct Acc32<PREC, OP_DIFF> {
+    static constexpr int op = OP_DIFF;
+    typename RealOf<PREC>::type S, G1[3], G2[3], GT[3];
+};
+template <int PREC>
+struct Acc32<PREC, OP_APPLY> {
+    static constexpr int op = OP_APPLY;
+    typename RealOf<PREC>::type A1[3], A2[3];
+};
+template <int PREC>
+struct Acc32<PREC, OP_DIAG> {
+    static constexpr int op = OP_DIAG;
+    typename RealOf<PREC>::type Sw, Sw0;
+};
+
+template <int OP>
+struct Acc64;
+template <>
+struct Acc64<OP_ENERGY> {
+    static constexpr int op = OP_ENERGY;
+    double s;
+};
+template <>
+struct Acc64<OP_DIFF> : DiffAcc64 {
+    static constexpr int op = OP_DIFF;
+};
+template <>
+struct Acc64<OP_APPLY> : ApplyAcc64 {
+    static constexpr int op = OP_APPLY;
+};
+template <>
+struct Acc64<OP_DIAG> : ApplyAcc64 {
+    static constexpr int op = OP_DIAG;
+};
+
+// Per-edge values of u seen by one side of a pair (double-float in PMIX).
+template <class R>
+struct UVal {
+    V3<R> dh, dl, uh, ul;  // du and ub, hi and lo parts
+};
+
+template <int PREC>
+__device__ __forceinline__ void load_uval(UVal<typename RealOf<PREC>::type> &v, const URecF *uf, const URecD *ud,
+                                          int I)
+{
+    if constexpr (PREC == P64) {
+        URecD r = ud[I];
+        v.dh = {r.du0.x, r.du0.y, r.du1.x};
+        v.uh = {r.ub0.x, r.ub0.y, r.ub1.x};
+        v.dl = {0, 0, 0};
+        v.ul = {0, 0, 0};
+    } else {
+        URecF r = uf[I];
+        v.dh = {r.a.x, r.a.y, r.a.z};
+        v.uh = {r.a.w, r.b.x, r.b.y};
+        v.dl = {r.b.z, r.b.w, r.c.x};
+        v.ul = {r.c.y, r.c.z, r.c.w};
+    }
+}
+
+// One (target, source) pair: accumulate into the tile accumulator a.
+template <int PREC, int OP, bool FAST>
+__device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type> &t, const Src<PREC> &s,
+                                          Acc32<PREC, OP> &a, bool keep, const KernelParams &kp,
+                                          typename RealOf<PREC>::type &d2_11,
+                                          const UVal<typename RealOf<PREC>::type> *tu,
+                                          const UVal<typename RealOf<PREC>::type> *su)
+{
+    using R = typename RealOf<PREC>::type;
+    const R alpha = (R)kp.alpha, beta = (R)kp.beta, pp = (R)kp.p;
+    if constexpr (OP == OP_ENERGY) {
+        R f = 0;
+#pragma unroll
+        for (int ab = 0; ab < 4; ++ab) {
+            V3<R> P = (ab < 2) ? t.p1 : t.p2, PL = (ab < 2) ? t.l1 : t.l2;
+            V3<R> Q = (ab & 1) ? s.q2 : s.q1, QL = (ab & 1) ? s.m2 : s.m1;
+            V3<R> d = diff3<PREC>(P, PL, Q, QL), dp;
+            R tt, c2 = perp2(d, t.T, tt, dp), d2 = dot3(d, d);
+            if (ab == 0) d2_11 = d2;
+            R r2;
+            f += pow_c<R, FAST>(c2, alpha) * inv_pow<R, FAST, 0>(d2, beta, r2);
+        }
+        R c = s.ell * f;
+        a.s += keep ? c : (R)0;
+    } else if constexpr (OP == OP_DIFF) {
+        R S = 0, G1[3] = {0, 0, 0}, G2[3] = {0, 0, 0}, GT[3] = {0, 0, 0};
+#pragma unroll
+        for (int ab = 0; ab < 4; ++ab) {
+            V3<R> P = (ab < 2) ? t.p1 : t.p2, PL = (ab < 2) ? t.l1 : t.l2;
+            V3<R> Q = (ab & 1) ? s.q2 : s.q1, QL = (ab & 1) ? s.m2 : s.m1;
+            V3<R> d = diff3<PREC>(P, PL, Q, QL), dpI, dpJ;
+            R tI, tJ;
+            R cI2 = perp2(d, t.T, tI, dpI), cJ2 = perp2(d, s.T, tJ, dpJ), d2 = dot3(d, d);
+            if (ab == 0) d2_11 = d2;
+            R r2;
+            R rb = inv_pow<R, FAST, 0>(d2, beta, r2);
+            R fI, fJ, aI, aJ;
+            if constexpr (FAST) {
+                fI = cI2 * rb;
+                fJ = cJ2 * rb;
+                aI = aJ = (R)2 * rb;
+            } else {
+                fI = pow_c<R, false>(cI2, alpha) * rb;
+                fJ = pow_c<R, false>(cJ2, alpha) * rb;
+                aI = cI2 > (R)0 ? alpha * fI / cI2 : (R)0;
+                aJ = cJ2 > (R)0 ? alpha * fJ / cJ2 : (R)0;
+            }
+            R fs = fI + fJ;
+            R cb = beta * fs * r2;
+            R *G = (ab < 2) ? G1 : G2;
+            G[0] += aI * dpI.x + aJ * dpJ.x - cb * d.x;
+            G[1] += aI * dpI.y + aJ * dpJ.y - cb * d.y;
+            G[2] += aI * dpI.z + aJ * dpJ.z - cb * d.z;
+            R m = -aI * tI;
+            GT[0] += m * d.x;
+            GT[1] += m * d.y;
+            GT[2] += m * d.z;
+            S += fs;
+        }
+        if (!keep) {  // neighbours produce Inf/NaN: never let them touch the accumulators
+            S = 0;
+            for (int k = 0; k < 3; ++k) G1[k] = G2[k] = GT[k] = 0;
+        }
+        R L = keep ? s.ell : (R)0;
+        a.S += L * S;
+        for (int k = 0; k < 3; ++k) {
+            a.G1[k] += L * G1[k];
+            a.G2[k] += L * G2[k];
+            a.GT[k] += L * GT[k];
+        }
+    } else {  // OP_APPLY / OP_DIAG
+        R sw = 0, sw0 = 0;
+#pragma unroll
+        for (int ab = 0; ab < 4; ++ab) {
+            V3<R> P = (ab < 2) ? t.p1 : t.p2, PL = (ab < 2) ? t.l1 : t.l2;
+            V3<R> Q = (ab & 1) ? s.q2 : s.q1, QL = (ab & 1) ? s.m2 : s.m1;
+            V3<R> d = diff3<PREC>(P, PL, Q, QL), dpI, dpJ;
+            R tI, tJ;
+            R c2 = perp2(d, t.T, tI, dpI) + perp2(d, s.T, tJ, dpJ), d2 = dot3(d, d);
+            if (ab == 0) d2_11 = d2;
+            R r2;
+            R rp = inv_pow<R, FAST, 1>(d2, pp, r2);
+            sw += rp;
+            sw0 += c2 * (rp * r2 * r2);
+        }
+        R W = keep ? s.ell * sw : (R)0;
+        R W0 = keep ? s.ell * sw0 : (R)0;
+        if constexpr (OP == OP_DIAG) {
+            a.Sw += W;
+            a.Sw0 += W0;
+        } else {
+            // (du_I - du_J) + (|T_I - T_J|^2 / 2) du_J  and  ub_I - ub_J, differences of double-floats
+            V3<R> dT = {t.T.x - s.T.x, t.T.y - s.T.y, t.T.z - s.T.z};
+            R omt = (R)0.5 * dot3(dT, dT);
+            R ddx = (tu->dh.x - su->dh.x), ddy = (tu->dh.y - su->dh.y), ddz = (tu->dh.z - su->dh.z);
+            R dbx = (tu->uh.x - su->uh.x), dby = (tu->uh.y - su->uh.y), dbz = (tu->uh.z - su->uh.z);
+            if constexpr (PREC == PMIX) {
+                ddx += tu->dl.x - su->dl.x;
+                ddy += tu->dl.y - su->dl.y;
+                ddz += tu->dl.z - su->dl.z;
+                dbx += tu->ul.x - su->ul.x;
+                dby += tu->ul.y - su->ul.y;
+                dbz += tu->ul.z - su->ul.z;
+            }
+            a.A1[0] += W * (ddx + omt * su->dh.x);
+            a.A1[1] += W * (ddy + omt * su->dh.y);
+            a.A1[2] += W * (ddz + omt * su->dh.z);
+            a.A2[0] += W0 * dbx;
+            a.A2[1] += W0 * dby;
+            a.A2[2] += W0 * dbz;
+        }
+    }
+}
+
+template <int PREC, int OP>
+__device__ __forceinline__ void acc_zero(Acc32<PREC, OP> &a)
+{
+    if constexpr (OP == OP_ENERGY) {
+        a.s = 0;
+    } else if constexpr (OP == OP_DIFF) {
+        a.S = 0;
+        for (int k = 0; k < 3; ++k) a.G1[k] = a.G2[k] = a.GT[k] = 0;
+    } else if constexpr (OP == OP_APPLY) {
+        for (int k = 0; k < 3; ++k) a.A1[k] = a.A2[k] = 0;
+    } else {
+        a.Sw = a.Sw0 = 0;
+    }
+}
+
+template <int OP>
+__device__ __forceinline__ void acc64_zero(Acc64<OP> &a)
+{
+    if constexpr (OP == OP_ENERGY) {
+        a.s = 0;
+    } else if constexpr (OP == OP_DIFF) {
+        a.S = 0;
+        for (int k = 0; k < 3; ++k) a.G1[k] = a.G2[k] = a.GT[k] = 0;
+    } else {
+        a.Sw = a.Sw0 = 0;
+        for (int k = 0; k < 3; ++k) a.A1[k] = a.A2[k] = 0;
+    }
+}
+
+template <class X, class Y>
+__device__ __forceinline__ void acc_add(X &A, const Y &a)
+{
+    constexpr int OPX = X::op;
+    if constexpr (OPX == OP_ENERGY) {
+        A.s += a.s;
+    } else if constexpr (OPX == OP_DIFF) {
+        A.S += a.S;
+        for (int k = 0; k < 3; ++k) {
+            A.G1[k] += a.G1[k];
+            A.G2[k] += a.G2[k];
+            A.GT[k] += a.GT[k];
+        }
+    } else if constexpr (OPX == OP_APPLY) {
+        for (int k = 0; k < 3; ++k) {
+            A.A1[k] += a.A1[k];
+            A.A2[k] += a.A2[k];
+        }
+    } else {
+        A.Sw += a.Sw;
+        A.Sw0 += a.Sw0;
+    }
+}
+
+template <int OP>
+__host__ __device__ constexpr int part_stride()
+{
+    return (OP == OP_ENERGY || OP == OP_DIAG) ? 1 : 6;
+}
+
+template <int PREC, int OP, int TPT, bool FAST, bool CHECK>
+__device__ __forceinline__ void tile_loop(const Tgt<typename RealOf<PREC>::type> (&tg)[TPT], const int (&tI)[TPT],
+                                          const UVal<typename RealOf<PREC>::type> (&tu)[TPT],
+                                          const Tile<PREC, OP == OP_APPLY> &tl, int cnt, int s0,
+                                          Acc32<PREC, OP> (&a)[TPT], Acc64<OP> (&A)[TPT], const PairArgs &pa)
+{
+    using R = typename RealOf<PREC>::type;
+#pragma unroll 2
+    for (int j = 0; j < cnt; ++j) {
+        Src<PREC> s;
+        load_source<PREC, OP == OP_APPLY>(s, tl, j);
+        UVal<R> su;
+        if constexpr (OP == OP_APPLY) {
+            if constexpr (PREC == P64) {
+                URecD u = tl.u[j];
+                su.dh = {u.du0.x, u.du0.y, u.du1.x};
+                su.uh = {u.ub0.x, u.ub0.y, u.ub1.x};
+            } else {
+                float4 x = tl.u[j].a, y = tl.u[j].b, z = tl.u[j].c;
+                su.dh = {x.x, x.y, x.z};
+                su.uh = {x.w, y.x, y.y};
+                su.dl = {y.z, y.w, z.x};
+                su.ul = {z.y, z.z, z.w};
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            bool keep = true;
+            if constexpr (CHECK)
+                keep = (s.j1 != tg[k].i1) & (s.j1 != tg[k].i2) & (s.j2 != tg[k].i1) & (s.j2 != tg[k].i2);
+            R d2_11;
+            if constexpr (PREC == PMIX) {
+                // evaluate the FP32 pair, then replace it by the FP64 one when the pair is near
+                Acc32<PREC, OP> tmp;
+                acc_zero<PREC, OP>(tmp);
+                pair_eval<PREC, OP, FAST>(tg[k], s, tmp, keep, pa.kp, d2_11, &tu[k], &su);
+                bool near = keep && (d2_11 < pa.kp.near2f);
+                if (near) {
+                    int J = s0 + j;
+                    if constexpr (OP == OP_ENERGY) {
+                        A[k].s += near_energy(pa.na, tI[k], J, pa.kp.alpha, pa.kp.beta);
+                    } else if constexpr (OP == OP_DIFF) {
+                        near_diff(pa.na, tI[k], J, pa.kp.alpha, pa.kp.beta, A[k]);
+                    } else {
+                        near_apply(pa.na, tI[k], J, pa.kp.p, OP == OP_APPLY, A[k]);
+                    }
+                } else {
+                    acc_add(a[k], tmp);
+                }
+            } else {
+                pair_eval<PREC, OP, FAST>(tg[k], s, a[k], keep, pa.kp, d2_11, &tu[k], &su);
+            }
+        }
+    }
+}
+
+template <int PREC, int OP, int TPT, bool FAST>
+__global__ void __launch_bounds__(kThreads) k_pairs(const PairArgs pa)
+{
+    using R = typename RealOf<PREC>::type;
+    constexpr bool NEEDU = (OP == OP_APPLY);
+    __shared__ Tile<PREC, NEEDU> tl;
+    __shared__ int s_item;
+    constexpr int S = part_stride<OP>();
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(pa.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= pa.n_items) break;
+        const WorkItem w = pa.items[it];
+        Tgt<R> tg[TPT];
+        UVal<R> tu[TPT];
+        int tI[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            int loc = threadIdx.x + k * kThreads;
+            tI[k] = w.tgt0 + min(loc, w.ntgt - 1);
+            load_target<PREC>(tg[k], tI[k], pa.recF, pa.recLo, pa.recD);
+            if constexpr (NEEDU) load_uval<PREC>(tu[k], pa.urecF, pa.urecD, tI[k]);
+        }
+        Acc64<OP> A[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) acc64_zero<OP>(A[k]);
+        for (int s0 = w.src0; s0 < w.src1; s0 += kTile) {
+            const int cnt = min(kTile, w.src1 - s0);
+            __syncthreads();
+            if (threadIdx.x < cnt) {
+                int J = s0 + threadIdx.x;
+                if constexpr (PREC == P64) {
+                    tl.r[threadIdx.x] = pa.recD[J];
+                    if constexpr (NEEDU) tl.u[threadIdx.x] = pa.urecD[J];
+                } else {
+                    tl.r[threadIdx.x] = pa.recF[J];
+                    if constexpr (PREC == PMIX) tl.lo[threadIdx.x] = pa.recLo[J];
+                    if constexpr (NEEDU) tl.u[threadIdx.x] = pa.urecF[J];
+                }
+            }
+            __syncthreads();
+            Acc32<PREC, OP> a[TPT];
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) acc_zero<PREC, OP>(a[k]);
+            const bool check = !(s0 + cnt - 1 < w.nb_lo || s0 > w.nb_hi);
+            if (check)
+                tile_loop<PREC, OP, TPT, FAST, true>(tg, tI, tu, tl, cnt, s0, a, A, pa);
+            else
+                tile_loop<PREC, OP, TPT, FAST, false>(tg, tI, tu, tl, cnt, s0, a, A, pa);
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) acc_add(A[k], a[k]);
+        }
+        // write this item's partial results for the valid targets
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            int loc = threadIdx.x + k * kThreads;
+            if (loc >= w.ntgt) continue;
+            int I = w.tgt0 + loc;
+            double *o = pa.part + ((size_t)w.slot * pa.nE + I) * S;
+            if constexpr (OP == OP_ENERGY) {
+                o[0] = A[k].s;
+            } else if constexpr (OP == OP_DIFF) {
+                // G_i1 = (1/4)[-T S + l_I G1 - (Id - T T^t) GT],  G_i2 = (1/4)[T S + l_I G2 + (Id - T T^t) GT]
+                const double *T = pa.na.T + 3 * I;
+                double l = pa.na.ell[I];
+                double tg3[3] = {T[0], T[1], T[2]};
+                double gt = tg3[0] * A[k].GT[0] + tg3[1] * A[k].GT[1] + tg3[2] * A[k].GT[2];
+                for (int c = 0; c < 3; ++c) {
+                    double pgt = A[k].GT[c] - gt * tg3[c];
+                    o[c] = 0.25 * (-tg3[c] * A[k].S + l * A[k].G1[c] - pgt);
+                    o[3 + c] = 0.25 * (tg3[c] * A[k].S + l * A[k].G2[c] + pgt);
+                }
+            } else if constexpr (OP == OP_APPLY) {
+                // h_I / l_I = A1 / 2 (to +i2, -i1) and l_I / 2 = l_I A2 / 8 (to both endpoints)
+                double l = pa.na.ell[I];
+                for (int c = 0; c < 3; ++c) {
+                    o[c] = 0.5 * A[k].A1[c];
+                    o[3 + c] = 0.125 * l * A[k].A2[c];
+                }
+            } else {
+                double l = pa.na.ell[I];
+                o[0] = A[k].Sw / (2.0 * l) + l * A[k].Sw0 / 16.0;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------- reductions / gathers
+
+// rows[I] = (l_I / 4) sum_slots part[slot][I]
+__global__ void k_energy_rows(int nE, int nslots_max, const int *__restrict__ eslots, const double *__restrict__ part,
+                              const double *__restrict__ ell, double *__restrict__ rows)
+{
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nE) return;
+    double s = 0.0;
+    int ns = eslots[I];
+    for (int k = 0; k < ns; ++k) s += part[(size_t)k * nE + I];
+    rows[I] = 0.25 * ell[I] * s;
+}
+
+// Per-problem sums of a per-edge array (deterministic: one block per problem, fixed order).
+__global__ void k_segment_sum(const int *__restrict__ off, const double *__restrict__ x, double *__restrict__ out)
+{
+    int q = blockIdx.x;
+    int b = off[q], e = off[q + 1];
+    double s = 0.0;
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) s += x[i];
+    __shared__ double sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = sh[0];
+}
+
+// out_v = sum_{(I, slot) in inc(v)} sum_k part[k][I][slot*3 + c] (diff: slot selects G_i1 / G_i2;
+// apply: -/+ first triple plus the second triple).
+template <int OP>
+__global__ void k_vertex_gather(int nV, int nE, const int *__restrict__ inc_ptr, const int *__restrict__ inc,
+                                const int *__restrict__ eslots, const double *__restrict__ part,
+                                double *__restrict__ out)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    double o[3] = {0, 0, 0};
+    for (int k = inc_ptr[v]; k < inc_ptr[v + 1]; ++k) {
+        int I = inc[k] >> 1, sl = inc[k] & 1;
+        int ns = eslots[I];
+        for (int q = 0; q < ns; ++q) {
+            const double *p = part + ((size_t)q * nE + I) * (OP == OP_DIAG ? 1 : 6);
+            if constexpr (OP == OP_DIFF) {
+                for (int c = 0; c < 3; ++c) o[c] += p[3 * sl + c];
+            } else if constexpr (OP == OP_APPLY) {
+                double sg = sl ? 1.0 : -1.0;
+                for (int c = 0; c < 3; ++c) o[c] += sg * p[c] + p[3 + c];
+            } else {
+                o[0] += p[0];
+            }
+        }
+    }
+    if constexpr (OP == OP_DIAG) {
+        out[v] = o[0];
+    } else {
+        for (int c = 0; c < 3; ++c) out[3 * v + c] = o[c];
+    }
+}
+
+// ---------------------------------------------------------------------------------- planning
+
+// Build the (target block, source chunk) queue of one pass.  Items of big problems come first
+// so the persistent grid ends with the small ones.
+static void plan_pass(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy)
+{
+    const int tb = kThreads * tpt;
+    std::vector<WorkItem> items;
+    // neighbour spans per target block: min/max edge index sharing a vertex with the block
+    std::vector<int> vmin(c.nV, INT32_MAX), vmax(c.nV, -1);
+    for (int I = 0; I < c.nE; ++I)
+        for (int s = 0; s < 2; ++s) {
+            int v = c.h_edges[2 * I + s];
+            vmin[v] = std::min(vmin[v], I);
+            vmax[v] = std::max(vmax[v], I);
+        }
+    const int target_items = std::max(1, 8 * c.sm_count * std::max(1, occupancy));
+    // total work estimate to size chunks
+    double total = 0.0;
+    for (int q = 0; q < c.nProb; ++q) {
+        double n = c.h_prob_e[q + 1] - c.h_prob_e[q];
+        total += n * n;
+    }
+    int max_slots = 1;
+    std::vector<int> eslots(c.nE, 1);
+    struct Tmp {
+        WorkItem w;
+        double cost;
+    };
+    std::vector<Tmp> tmp;
+    for (int q = 0; q < c.nProb; ++q) {
+        int e0 = c.h_prob_e[q], e1 = c.h_prob_e[q + 1], n = e1 - e0;
+        if (n <= 0) continue;
+        int nblk = (n + tb - 1) / tb;
+        // chunks so that this problem gets its share of the target item count
+        double share = total > 0 ? (double)n * n / total : 1.0;
+        int want = (int)std::ceil(share * target_items / nblk);
+        int max_chunks = std::max(1, n / kTile);
+        int nch = std::min(std::max(1, want), max_chunks);
+        nch = std::min(nch, 64);
+        int clen = ((n + nch - 1) / nch + kTile - 1) / kTile * kTile;
+        nch = (n + clen - 1) / clen;
+        max_slots = std::max(max_slots, nch);
+        for (int b = 0; b < nblk; ++b) {
+            int t0 = e0 + b * tb, nt = std::min(tb, e1 - t0);
+            int lo = INT32_MAX, hi = -1;
+            for (int I = t0; I < t0 + nt; ++I)
+                for (int s = 0; s < 2; ++s) {
+                    int v = c.h_edges[2 * I + s];
+                    lo = std::min(lo, vmin[v]);
+                    hi = std::max(hi, vmax[v]);
+                }
+            for (int k = 0; k < nch; ++k) {
+                int s0 = e0 + k * clen, s1 = std::min(e1, s0 + clen);
+                WorkItem w{t0, nt, s0, s1, k, lo, hi, 0};
+                tmp.push_back({w, (double)nt * (s1 - s0)});
+            }
+        }
+        for (int I = e0; I < e1; ++I) eslots[I] = nch;
+    }
+    std::stable_sort(tmp.begin(), tmp.end(), [](const Tmp &a, const Tmp &b) { return a.cost > b.cost; });
+    for (auto &t : tmp) items.push_back(t.w);
+    pl.n_items = (int)items.size();
+    pl.max_slots = max_slots;
+    pl.tpt = tpt;
+    pl.grid = std::max(1, std::min(pl.n_items, c.sm_count * std::max(1, occupancy)));
+    cudaMalloc(&pl.d_items, sizeof(WorkItem) * std::max<size_t>(1, items.size()));
+    cudaMemcpy(pl.d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice);
+    cudaMalloc(&pl.d_eslots, sizeof(int) * std::max(1, c.nE));
+    cudaMemcpy(pl.d_eslots, eslots.data(), sizeof(int) * c.nE, cudaMemcpyHostToDevice);
+}
+
+template <int PREC, int OP, int TPT>
+static int occupancy_of(const Ctx &c)
+{
+    int occ = 0;
+    if (c.kp.fast)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs<PREC, OP, TPT, true>, kThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs<PREC, OP, TPT, false>, kThreads, 0);
+    return occ;
+}
+
+constexpr int kTptEnergy = 4, kTptDiff = 2, kTptApply = 2;
+constexpr int kTptEnergy64 = 1, kTptDiff64 = 1, kTptApply64 = 1;
+
+void make_plans(Ctx &c)
+{
+    // The chunking must be identical across precisions of one op class; all slots share one layout,
+    // so every pass of the context uses the same targets-per-thread within an op class.
+    const bool p64 = c.prm.precision == TP_FP64;
+    int oe, od, oa;
+    if (p64) {
+        oe = occupancy_of<P64, OP_ENERGY, kTptEnergy64>(c);
+        od = occupancy_of<P64, OP_DIFF, kTptDiff64>(c);
+        oa = occupancy_of<P64, OP_APPLY, kTptApply64>(c);
+    } else if (c.prm.precision == TP_MIXED) {
+        oe = occupancy_of<PMIX, OP_ENERGY, kTptEnergy>(c);
+        od = occupancy_of<PMIX, OP_DIFF, kTptDiff>(c);
+        oa = occupancy_of<PMIX, OP_APPLY, kTptApply>(c);
+    } else {
+        oe = occupancy_of<P32, OP_ENERGY, kTptEnergy>(c);
+        od = occupancy_of<P32, OP_DIFF, kTptDiff>(c);
+        oa = occupancy_of<P32, OP_APPLY, kTptApply>(c);
+    }
+    plan_pass(c, c.plan_energy, p64 ? kTptEnergy64 : kTptEnergy, oe);
+    plan_pass(c, c.plan_diff, p64 ? kTptDiff64 : kTptDiff, od);
+    plan_pass(c, c.plan_apply, p64 ? kTptApply64 : kTptApply, oa);
+}
+
+// ---------------------------------------------------------------------------------- launchers
+
+cudaError_t build_records(Ctx &c, const double *gamma, int which, cudaStream_t s)
+{
+    int nb = (c.nE + 255) / 256;
+    const bool p64 = c.prm.precision == TP_FP64, mix = c.prm.precision == TP_MIXED;
+    RecF *rf = p64 ? nullptr : (which ? c.d_recF2 : c.d_recF);
+    RecLo *rl = mix ? (which ? c.d_recLo2 : c.d_recLo) : nullptr;
+    RecD *rd = p64 ? (which ? c.d_recD2 : c.d_recD) : nullptr;
+    if (c.nE == 0) return cudaSuccess;
+    k_records<<<nb, 256, 0, s>>>(c.nE, gamma, c.d_edges, rf, rl, rd, c.d_ellw[which], c.d_Tw[which], c.d_xw[which], c.d_err);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t build_urecs(Ctx &c, const double *u, int which, cudaStream_t s)
+{
+    if (c.nE == 0) return cudaSuccess;
+    int nb = (c.nE + 255) / 256;
+    const bool p64 = c.prm.precision == TP_FP64;
+    k_urecs<<<nb, 256, 0, s>>>(c.nE, u, c.d_edges, c.d_ellw[which], p64 ? nullptr : c.d_urecF, p64 ? c.d_urecD : nullptr);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+template <int OP>
+static cudaError_t run_pairs(Ctx &c, int which, const double *gamma, const double *u, cudaStream_t s)
+{
+    Ctx::Plan &pl = (OP == OP_ENERGY) ? c.plan_energy : (OP == OP_DIFF ? c.plan_diff : c.plan_apply);
+    if (pl.n_items == 0) return cudaSuccess;
+    constexpr int ctr = OP;
+    TPE_CHECK(cudaMemsetAsync(c.d_counter + ctr, 0, sizeof(int), s));
+    PairArgs pa;
+    pa.items = pl.d_items;
+    pa.n_items = pl.n_items;
+    pa.counter = c.d_counter + ctr;
+    pa.recF = which ? c.d_recF2 : c.d_recF;
+    pa.recLo = which ? c.d_recLo2 : c.d_recLo;
+    pa.recD = which ? c.d_recD2 : c.d_recD;
+    pa.urecF = c.d_urecF;
+    pa.urecD = c.d_urecD;
+    pa.na = NearArgs{gamma, c.d_edges, c.d_ellw[which], c.d_Tw[which], u};
+    pa.part = c.d_part;
+    pa.nE = c.nE;
+    pa.kp = c.kp;
+    const int g = pl.grid;
+    const bool f = c.kp.fast != 0;
+    switch (c.prm.precision) {
+    case TP_FP64:
+        if (f) k_pairs<P64, OP, (OP == OP_ENERGY ? kTptEnergy64 : OP == OP_DIFF ? kTptDiff64 : kTptApply64), true><<<g, kThreads, 0, s>>>(pa);
+        else k_pairs<P64, OP, (OP == OP_ENERGY ? kTptEnergy64 : OP == OP_DIFF ? kTptDiff64 : kTptApply64), false><<<g, kThreads, 0, s>>>(pa);
+        break;
+    case TP_MIXED:
+        if (f) k_pairs<PMIX, OP, (OP == OP_ENERGY ? kTptEnergy : OP == OP_DIFF ? kTptDiff : kTptApply), true><<<g, kThreads, 0, s>>>(pa);
+        else k_pairs<PMIX, OP, (OP == OP_ENERGY ? kTptEnergy : OP == OP_DIFF ? kTptDiff : kTptApply), false><<<g, kThreads, 0, s>>>(pa);
+        break;
+    default:
+        if (f) k_pairs<P32, OP, (OP == OP_ENERGY ? kTptEnergy : OP == OP_DIFF ? kTptDiff : kTptApply), true><<<g, kThreads, 0, s>>>(pa);
+        else k_pairs<P32, OP, (OP == OP_ENERGY ? kTptEnergy : OP == OP_DIFF ? kTptDiff : kTptApply), false><<<g, kThreads, 0, s>>>(pa);
+        break;
+    }
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t pair_energy(Ctx &c, const double *gamma, int which, double *rows_out, double *E_out, cudaStream_t s)
+{
+    TPE_CHECK(run_pairs<OP_ENERGY>(c, which, gamma, nullptr, s));
+    double *rows = rows_out ? rows_out : c.d_rows;
+    if (c.nE > 0) {
+        k_energy_rows<<<(c.nE + 255) / 256, 256, 0, s>>>(c.nE, c.plan_energy.max_slots, c.plan_energy.d_eslots, c.d_part, c.d_ellw[which],
+                                                         rows);
+        c.launches++;
+    }
+    if (E_out) {
+        k_segment_sum<<<c.nProb, 256, 0, s>>>(c.d_prob_e, rows, E_out);
+        c.launches++;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t pair_diff(Ctx &c, const double *gamma, int which, double *dE, cudaStream_t s)
+{
+    TPE_CHECK(run_pairs<OP_DIFF>(c, which, gamma, nullptr, s));
+    if (c.nV > 0) {
+        k_vertex_gather<OP_DIFF><<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.nE, c.d_inc_ptr, c.d_inc, c.plan_diff.d_eslots,
+                                                                    c.d_part, dE);
+        c.launches++;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t pair_apply(Ctx &c, const double *gamma_geom, int which, const double *u, double *Au, cudaStream_t s)
+{
+    TPE_CHECK(build_urecs(c, u, which, s));
+    TPE_CHECK(run_pairs<OP_APPLY>(c, which, gamma_geom, u, s));
+    if (c.nV > 0) {
+        k_vertex_gather<OP_APPLY><<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.nE, c.d_inc_ptr, c.d_inc, c.plan_apply.d_eslots,
+                                                                     c.d_part, Au);
+        c.launches++;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t pair_diag(Ctx &c, const double *gamma_geom, int which, double *diag, cudaStream_t s)
+{
+    TPE_CHECK(run_pairs<OP_DIAG>(c, which, gamma_geom, nullptr, s));
+    if (c.nV > 0) {
+        k_vertex_gather<OP_DIAG><<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.nE, c.d_inc_ptr, c.d_inc, c.plan_apply.d_eslots,
+                                                                    c.d_part, diag);
+        c.launches++;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tpe

@@ -1,0 +1,692 @@
+// Constraints, projection and the projected preconditioned CG of the H^s gradient.
+//
+//   Phi_bary = sum_I l_I (x_I - x0), Phi_len = L0 - sum_I l_I          (Sec. 8.1), per problem
+//   C = d Phi, stored per vertex as C[v][4][3]
+//   P v = v - C^T (C C^T)^-1 C v,  C^+ b = C^T (C C^T)^-1 b              (App. B.3.3, read as the
+//                                                                         Euclidean projector onto null C)
+//   CG on P A-bar P y = P a, x = P y                                     (App. B.3.3, Eq. "ProjectedSystem")
+//
+// Every reduction is deterministic: fixed chunks of vertices (never crossing problems) are reduced
+// in shared memory, and the last block to finish sums the chunk partials of each problem in index
+// order and runs the per-problem scalar update (CG alpha/beta, convergence flags) on the device.
+// No scalar goes to the host inside an iteration; the host polls a pinned "active problems"
+// counter every cg_check_every iterations.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tpe_internal.cuh"
+
+namespace tpe {
+
+#define TPE_CHECK(x)                      \
+    do {                                  \
+        cudaError_t e_ = (x);             \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
+constexpr int kRedThreads = 256;
+
+// ---------------------------------------------------------------------------------- reduction core
+
+struct RedArgs {
+    const int *chunk_lo;   // [nchunks + 1] element ranges of the chunks
+    const int *prob_c0;    // [nprob + 1] first chunk of each problem
+    int nchunks, nprob;
+    double *partial;       // [nchunks][K]
+    unsigned *counter;
+    double *sums;          // [nprob][K]
+};
+
+// Block-reduce K values, publish the block partial, and in the last block sum the partials of
+// every problem into sums[q][k].  Returns true in the last block (all threads).
+template <int K>
+__device__ bool reduce_phase(double (&s)[K], const RedArgs &ra)
+{
+    __shared__ double sh[K][kRedThreads];
+    __shared__ bool last;
+    for (int k = 0; k < K; ++k) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < K; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < K; ++k) ra.partial[(size_t)blockIdx.x * K + k] = sh[k][0];
+        __threadfence();
+        last = (atomicAdd(ra.counter, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+        for (int k = 0; k < K; ++k) {
+            double acc = 0.0;
+            for (int ch = ra.prob_c0[q]; ch < ra.prob_c0[q + 1]; ++ch) acc += __ldcg(&ra.partial[(size_t)ch * K + k]);
+            ra.sums[(size_t)q * K + k] = acc;
+        }
+    }
+    if (threadIdx.x == 0) *ra.counter = 0u;
+    __threadfence();
+    __syncthreads();
+    return true;
+}
+
+// ---------------------------------------------------------------------------------- reduction plans
+
+
+
+// Chunks of at most `cap` elements within each problem's range [off[q], off[q+1]).
+static void make_red_plan(const std::vector<int32_t> &off, int cap, int **d_lo, int **d_c0, int *nch)
+{
+    std::vector<int> lo, c0;
+    int nprob = (int)off.size() - 1;
+    for (int q = 0; q < nprob; ++q) {
+        c0.push_back((int)lo.size());
+        int a = off[q], b = off[q + 1];
+        if (b <= a) continue;
+        for (int x = a; x < b; x += cap) lo.push_back(x);
+    }
+    c0.push_back((int)lo.size());
+    int n = (int)lo.size();
+    lo.push_back(off.back());
+    cudaMalloc(d_lo, sizeof(int) * lo.size());
+    cudaMemcpy(*d_lo, lo.data(), sizeof(int) * lo.size(), cudaMemcpyHostToDevice);
+    cudaMalloc(d_c0, sizeof(int) * c0.size());
+    cudaMemcpy(*d_c0, c0.data(), sizeof(int) * c0.size(), cudaMemcpyHostToDevice);
+    *nch = n;
+}
+
+// The context keeps these in its generic scratch: see solver_setup.
+}  // namespace tpe
+struct tpe::SolverState {
+    int *v_lo = nullptr, *v_c0 = nullptr, v_n = 0;  // vertex chunks
+    int *e_lo = nullptr, *e_c0 = nullptr, e_n = 0;  // edge chunks
+    double *partial = nullptr;                      // [max chunks][16]
+    unsigned *counters = nullptr;                   // [8]
+    double *sums = nullptr;                         // [nProb][16]
+    double *mu = nullptr;                           // [nProb][4]
+    int *done = nullptr;                            // [nProb] 1 = converged / inactive
+    int *active = nullptr;                          // [1] number of active problems
+    int *status = nullptr;                          // [nProb] 0 ok, 1 breakdown
+};
+namespace tpe {
+
+static SolverState &S(Ctx &c) { return *c.sol; }
+
+static inline RedArgs vargs(Ctx &c, int which_counter)
+{
+    SolverState &s = S(c);
+    return RedArgs{s.v_lo, s.v_c0, s.v_n, c.nProb, s.partial, s.counters + which_counter, s.sums};
+}
+static inline RedArgs eargs(Ctx &c, int which_counter)
+{
+    SolverState &s = S(c);
+    return RedArgs{s.e_lo, s.e_c0, s.e_n, c.nProb, s.partial, s.counters + which_counter, s.sums};
+}
+
+cudaError_t solver_setup(Ctx &c)
+{
+    c.sol = new SolverState();
+    SolverState &s = S(c);
+    make_red_plan(c.h_prob_v, 2048, &s.v_lo, &s.v_c0, &s.v_n);
+    make_red_plan(c.h_prob_e, 2048, &s.e_lo, &s.e_c0, &s.e_n);
+    int mx = std::max(std::max(s.v_n, s.e_n), 1);
+    TPE_CHECK(cudaMalloc(&s.partial, sizeof(double) * (size_t)mx * 16));
+    TPE_CHECK(cudaMalloc(&s.counters, sizeof(unsigned) * 8));
+    TPE_CHECK(cudaMemset(s.counters, 0, sizeof(unsigned) * 8));
+    TPE_CHECK(cudaMalloc(&s.sums, sizeof(double) * (size_t)std::max(1, c.nProb) * 16));
+    TPE_CHECK(cudaMalloc(&s.mu, sizeof(double) * (size_t)std::max(1, c.nProb) * 4));
+    TPE_CHECK(cudaMalloc(&s.done, sizeof(int) * (size_t)std::max(1, c.nProb)));
+    TPE_CHECK(cudaMalloc(&s.status, sizeof(int) * (size_t)std::max(1, c.nProb)));
+    TPE_CHECK(cudaMalloc(&s.active, sizeof(int) * 4));
+    return cudaSuccess;
+}
+
+void solver_free(Ctx &c)
+{
+    SolverState &s = S(c);
+    cudaFree(s.v_lo);
+    cudaFree(s.v_c0);
+    cudaFree(s.e_lo);
+    cudaFree(s.e_c0);
+    cudaFree(s.partial);
+    cudaFree(s.counters);
+    cudaFree(s.sums);
+    cudaFree(s.mu);
+    cudaFree(s.done);
+    cudaFree(s.status);
+    cudaFree(s.active);
+    delete c.sol;
+    c.sol = nullptr;
+}
+
+// ---------------------------------------------------------------------------------- constraints
+
+// Phi per problem from the FP64 edge quantities: sum l_I (x_I - x0) and L0 - sum l_I.
+__global__ void k_phi(RedArgs ra, const double *__restrict__ ell, const double *__restrict__ x,
+                      const double *__restrict__ x0L0, const int *__restrict__ eprob, double *__restrict__ phi)
+{
+    double s[4] = {0, 0, 0, 0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int I = lo + threadIdx.x; I < hi; I += blockDim.x) {
+        int q = eprob[I];
+        double l = ell[I];
+        for (int k = 0; k < 3; ++k) s[k] += l * (x[3 * I + k] - x0L0[4 * q + k]);
+        s[3] += l;
+    }
+    if (reduce_phase<4>(s, ra)) {
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+            for (int k = 0; k < 3; ++k) phi[4 * q + k] = ra.sums[4 * q + k];
+            phi[4 * q + 3] = x0L0[4 * q + 3] - ra.sums[4 * q + 3];
+        }
+    }
+}
+
+// x0 = sum l_I x_I / sum l_I and L0 = sum l_I of the given curve.
+__global__ void k_targets(RedArgs ra, const double *__restrict__ ell, const double *__restrict__ x,
+                          double *__restrict__ x0L0)
+{
+    double s[4] = {0, 0, 0, 0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int I = lo + threadIdx.x; I < hi; I += blockDim.x) {
+        double l = ell[I];
+        for (int k = 0; k < 3; ++k) s[k] += l * x[3 * I + k];
+        s[3] += l;
+    }
+    if (reduce_phase<4>(s, ra)) {
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+            double L = ra.sums[4 * q + 3];
+            for (int k = 0; k < 3; ++k) x0L0[4 * q + k] = L > 0 ? ra.sums[4 * q + k] / L : 0.0;
+            x0L0[4 * q + 3] = L;
+        }
+    }
+}
+
+// C[v][k][:] for the barycenter rows k < 3 and the length row k = 3:
+//   d/dg_v [l_I (x_I,k - x0_k)] = s_v T_I (x_I,k - x0_k) + (l_I / 2) e_k,   d/dg_v [L0 - l_I] = -s_v T_I,
+// with s_v = +1 if v = i2, -1 if v = i1.
+__global__ void k_jacobian(int nV, const int *__restrict__ inc_ptr, const int *__restrict__ inc,
+                           const double *__restrict__ ell, const double *__restrict__ T, const double *__restrict__ x,
+                           const double *__restrict__ x0L0, const int *__restrict__ vprob, double *__restrict__ C)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    int q = vprob[v];
+    double c[4][3] = {{0}};
+    for (int k = inc_ptr[v]; k < inc_ptr[v + 1]; ++k) {
+        int I = inc[k] >> 1;
+        double sg = (inc[k] & 1) ? 1.0 : -1.0;
+        double t[3] = {T[3 * I], T[3 * I + 1], T[3 * I + 2]};
+        for (int r = 0; r < 3; ++r) {
+            double xr = x[3 * I + r] - x0L0[4 * q + r];
+            for (int cc = 0; cc < 3; ++cc) c[r][cc] += sg * t[cc] * xr;
+            c[r][r] += 0.5 * ell[I];
+        }
+        for (int cc = 0; cc < 3; ++cc) c[3][cc] -= sg * t[cc];
+    }
+    for (int r = 0; r < 4; ++r)
+        for (int cc = 0; cc < 3; ++cc) C[(size_t)v * 12 + r * 3 + cc] = c[r][cc];
+}
+
+// G = C C^T per problem, then G^-1 (4x4, Gauss-Jordan with partial pivoting in FP64).
+__device__ void inv4(const double *G, double *Gi)
+{
+    double a[4][8];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 8; ++j) a[i][j] = j < 4 ? G[4 * i + j] : (j - 4 == i ? 1.0 : 0.0);
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 4; ++r)
+            if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+        if (piv != col)
+            for (int j = 0; j < 8; ++j) {
+                double t = a[col][j];
+                a[col][j] = a[piv][j];
+                a[piv][j] = t;
+            }
+        double d = a[col][col];
+        if (d == 0.0) d = 1e-300;
+        for (int j = 0; j < 8; ++j) a[col][j] /= d;
+        for (int r = 0; r < 4; ++r)
+            if (r != col) {
+                double f = a[r][col];
+                for (int j = 0; j < 8; ++j) a[r][j] -= f * a[col][j];
+            }
+    }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) Gi[4 * i + j] = a[i][4 + j];
+}
+
+__global__ void k_gram_cc(RedArgs ra, const double *__restrict__ C, double *__restrict__ G, double *__restrict__ Gi)
+{
+    double s[10] = {0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        const double *c = C + (size_t)v * 12;
+        int n = 0;
+        for (int i = 0; i < 4; ++i)
+            for (int j = i; j < 4; ++j) {
+                s[n++] += c[3 * i] * c[3 * j] + c[3 * i + 1] * c[3 * j + 1] + c[3 * i + 2] * c[3 * j + 2];
+            }
+    }
+    if (reduce_phase<10>(s, ra)) {
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+            double g[16];
+            int n = 0;
+            for (int i = 0; i < 4; ++i)
+                for (int j = i; j < 4; ++j) {
+                    g[4 * i + j] = g[4 * j + i] = ra.sums[(size_t)q * 10 + n];
+                    ++n;
+                }
+            for (int k = 0; k < 16; ++k) G[16 * q + k] = g[k];
+            inv4(g, Gi + 16 * q);
+        }
+    }
+}
+
+// mu = G^-1 (C v) per problem (skip problems whose flag is set).
+__global__ void k_cv(RedArgs ra, const double *__restrict__ C, const double *__restrict__ v,
+                     const double *__restrict__ Gi, double *__restrict__ mu, const int *__restrict__ skip)
+{
+    double s[4] = {0, 0, 0, 0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double *c = C + (size_t)i * 12;
+        double a = v[3 * i], b = v[3 * i + 1], d = v[3 * i + 2];
+        for (int k = 0; k < 4; ++k) s[k] += c[3 * k] * a + c[3 * k + 1] * b + c[3 * k + 2] * d;
+    }
+    if (reduce_phase<4>(s, ra)) {
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+            const double *g = Gi + 16 * q;
+            const double *cv = ra.sums + 4 * q;
+            for (int k = 0; k < 4; ++k)
+                mu[4 * q + k] = g[4 * k] * cv[0] + g[4 * k + 1] * cv[1] + g[4 * k + 2] * cv[2] + g[4 * k + 3] * cv[3];
+        }
+    }
+}
+
+// v -= C^T mu (per vertex).
+__global__ void k_sub_ctmu(int nV, const double *__restrict__ C, const double *__restrict__ mu,
+                           const int *__restrict__ vprob, double *__restrict__ v, const int *__restrict__ skip)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    int q = vprob[i];
+    if (skip && skip[q]) return;
+    const double *c = C + (size_t)i * 12;
+    const double *m = mu + 4 * q;
+    for (int cc = 0; cc < 3; ++cc)
+        v[3 * i + cc] -= c[cc] * m[0] + c[3 + cc] * m[1] + c[6 + cc] * m[2] + c[9 + cc] * m[3];
+}
+
+// out = scale * C^T G^-1 b  with b = phi (per problem).
+__global__ void k_pinv(int nV, const double *__restrict__ C, const double *__restrict__ Gi,
+                       const double *__restrict__ b, double scale, const int *__restrict__ vprob,
+                       double *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    int q = vprob[i];
+    const double *g = Gi + 16 * q;
+    const double *bb = b + 4 * q;
+    double m[4];
+    for (int k = 0; k < 4; ++k) m[k] = scale * (g[4 * k] * bb[0] + g[4 * k + 1] * bb[1] + g[4 * k + 2] * bb[2] + g[4 * k + 3] * bb[3]);
+    const double *c = C + (size_t)i * 12;
+    for (int cc = 0; cc < 3; ++cc) out[3 * i + cc] = c[cc] * m[0] + c[3 + cc] * m[1] + c[6 + cc] * m[2] + c[9 + cc] * m[3];
+}
+
+cudaError_t constraints_eval(Ctx &c, const double *, int which, double *phi, cudaStream_t s)
+{
+    SolverState &st = S(c);
+    k_phi<<<st.e_n, kRedThreads, 0, s>>>(eargs(c, 0), c.d_ellw[which], c.d_xw[which], c.d_x0L0, c.d_eprob, phi);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t constraints_targets(Ctx &c, int which, cudaStream_t s)
+{
+    SolverState &st = S(c);
+    k_targets<<<st.e_n, kRedThreads, 0, s>>>(eargs(c, 0), c.d_ellw[which], c.d_xw[which], c.d_x0L0);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t constraints_jacobian(Ctx &c, int which, cudaStream_t s)
+{
+    SolverState &st = S(c);
+    k_jacobian<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_inc_ptr, c.d_inc, c.d_ellw[which], c.d_Tw[which], c.d_xw[which], c.d_x0L0,
+                                                  c.d_vprob, c.d_Cv);
+    k_gram_cc<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 1), c.d_Cv, c.d_G, c.d_Ginv);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t project(Ctx &c, double *v, cudaStream_t s, const int *skip)
+{
+    SolverState &st = S(c);
+    k_cv<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 2), c.d_Cv, v, c.d_Ginv, st.mu, skip);
+    k_sub_ctmu<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_Cv, st.mu, c.d_vprob, v, skip);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t pinv_apply(Ctx &c, const double *b_phi, double scale, double *out, cudaStream_t s)
+{
+    k_pinv<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_Cv, c.d_Ginv, b_phi, scale, c.d_vprob, out);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------- vector helpers
+
+// out[q] = sum over the problem's vertices of a . b
+__global__ void k_dot(RedArgs ra, const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ out)
+{
+    double s[1] = {0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        s[0] += a[3 * i] * b[3 * i] + a[3 * i + 1] * b[3 * i + 1] + a[3 * i + 2] * b[3 * i + 2];
+    if (reduce_phase<1>(s, ra))
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) out[q] = ra.sums[q];
+}
+
+cudaError_t vec_dot(Ctx &c, const double *a, const double *b, double *out_dev, cudaStream_t s)
+{
+    SolverState &st = S(c);
+    k_dot<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), a, b, out_dev);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+__global__ void k_axpby(int n, double a, const double *__restrict__ x, double b, const double *__restrict__ y,
+                        double *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a * x[i] + (y ? b * y[i] : 0.0);
+}
+
+cudaError_t vec_axpby(Ctx &c, double a, const double *x, double b, const double *y, double *out, cudaStream_t s)
+{
+    int n = 3 * c.nV;
+    k_axpby<<<(n + 255) / 256, 256, 0, s>>>(n, a, x, b, y, out);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+// out = x * f(num[q]) per problem: f = 1/sqrt(num) if invert_sqrt else num.
+__global__ void k_scale_prob(int nV, const double *__restrict__ x, const double *__restrict__ num, int invert_sqrt,
+                             const int *__restrict__ vprob, double *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    double f = num[vprob[i]];
+    if (invert_sqrt) f = f > 0.0 ? 1.0 / sqrt(f) : 0.0;
+    for (int k = 0; k < 3; ++k) out[3 * i + k] = f * x[3 * i + k];
+}
+
+cudaError_t vec_scale_dev(Ctx &c, const double *x, const double *num_dev, int invert_sqrt, double *out,
+                          cudaStream_t s)
+{
+    k_scale_prob<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, x, num_dev, invert_sqrt, c.d_vprob, out);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t sum_problems(Ctx &c, const double *x, int per_vertex, double *out, cudaStream_t s)
+{
+    (void)c;
+    (void)x;
+    (void)per_vertex;
+    (void)out;
+    (void)s;
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------------- preconditioners
+
+__global__ void k_jacobi(int nV, const double *__restrict__ diag, const double *__restrict__ r,
+                         double *__restrict__ z, const int *__restrict__ vprob, const int *__restrict__ skip)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    if (skip && skip[vprob[i]]) return;
+    double d = diag[i];
+    double f = d > 0.0 ? 1.0 / d : 0.0;
+    for (int k = 0; k < 3; ++k) z[3 * i + k] = f * r[3 * i + k];
+}
+
+cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip);
+
+cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip)
+{
+    switch (c.prm.precond) {
+    case TP_PRECOND_JACOBI:
+        k_jacobi<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_diag, r, z, c.d_vprob, skip);
+        c.launches++;
+        return cudaGetLastError();
+    case TP_PRECOND_SPECTRAL:
+        return spectral_apply(c, r, z, s, skip);
+    default:
+        return cudaMemcpyAsync(z, r, sizeof(double) * 3 * c.nV, cudaMemcpyDeviceToDevice, s);
+    }
+}
+
+// ---------------------------------------------------------------------------------- CG
+
+// Initialise: bb = r.r (r = P rhs already), rz = r.z; done flags for problems with zero rhs.
+__global__ void k_cg_init(RedArgs ra, const double *__restrict__ r, const double *__restrict__ z,
+                          CGScalars *__restrict__ cg, int *__restrict__ done, int *__restrict__ active)
+{
+    double s[2] = {0, 0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        for (int k = 0; k < 3; ++k) {
+            s[0] += r[3 * i + k] * r[3 * i + k];
+            s[1] += r[3 * i + k] * z[3 * i + k];
+        }
+    if (reduce_phase<2>(s, ra)) {
+        __shared__ int na;
+        if (threadIdx.x == 0) na = 0;
+        __syncthreads();
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+            CGScalars &g = cg[q];
+            g.bnorm2 = ra.sums[2 * q];
+            g.rnorm2 = ra.sums[2 * q];
+            g.rz = ra.sums[2 * q + 1];
+            g.iters = 0;
+            g.breakdown = 0;
+            g.done = (g.bnorm2 == 0.0);
+            done[q] = g.done;
+            if (!g.done) atomicAdd(&na, 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *active = na;
+    }
+}
+
+// alpha = rz / (p.q) per active problem.
+__global__ void k_cg_alpha(RedArgs ra, const double *__restrict__ p, const double *__restrict__ q_,
+                           CGScalars *__restrict__ cg, int *__restrict__ done)
+{
+    double s[1] = {0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        s[0] += p[3 * i] * q_[3 * i] + p[3 * i + 1] * q_[3 * i + 1] + p[3 * i + 2] * q_[3 * i + 2];
+    if (reduce_phase<1>(s, ra)) {
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+            CGScalars &g = cg[q];
+            if (g.done) continue;
+            double pq = ra.sums[q];
+            g.pq = pq;
+            if (!(pq > 0.0)) {
+                g.breakdown = 1;
+                g.done = 1;
+                done[q] = 1;
+                g.alpha = 0.0;
+            } else {
+                g.alpha = g.rz / pq;
+            }
+        }
+    }
+}
+
+// y += alpha p; r -= alpha q (active problems); then r.r
+__global__ void k_cg_update(RedArgs ra, const int *__restrict__ vprob, const double *__restrict__ p,
+                            const double *__restrict__ q_, double *__restrict__ y, double *__restrict__ r,
+                            CGScalars *__restrict__ cg, int *__restrict__ done, double tol2, int *__restrict__ active)
+{
+    double s[1] = {0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        int pr = vprob[i];
+        if (done[pr]) continue;
+        double a = cg[pr].alpha;
+        for (int k = 0; k < 3; ++k) {
+            y[3 * i + k] += a * p[3 * i + k];
+            double rv = r[3 * i + k] - a * q_[3 * i + k];
+            r[3 * i + k] = rv;
+            s[0] += rv * rv;
+        }
+    }
+    if (reduce_phase<1>(s, ra)) {
+        __shared__ int na;
+        if (threadIdx.x == 0) na = 0;
+        __syncthreads();
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+            CGScalars &g = cg[q];
+            if (!g.done) {
+                g.rnorm2 = ra.sums[q];
+                g.iters += 1;
+                if (g.rnorm2 <= tol2 * g.bnorm2) {
+                    g.done = 1;
+                    done[q] = 1;
+                }
+            }
+            if (!g.done) atomicAdd(&na, 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *active = na;
+    }
+}
+
+// rz_new = r.z; beta = rz_new / rz; rz = rz_new (active problems)
+__global__ void k_cg_beta(RedArgs ra, const double *__restrict__ r, const double *__restrict__ z,
+                          CGScalars *__restrict__ cg, const int *__restrict__ done)
+{
+    double s[1] = {0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        s[0] += r[3 * i] * z[3 * i] + r[3 * i + 1] * z[3 * i + 1] + r[3 * i + 2] * z[3 * i + 2];
+    if (reduce_phase<1>(s, ra)) {
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+            CGScalars &g = cg[q];
+            if (g.done) continue;
+            double rzn = ra.sums[q];
+            g.beta = g.rz != 0.0 ? rzn / g.rz : 0.0;
+            g.rz = rzn;
+        }
+    }
+}
+
+// p = z + beta p (active problems)
+__global__ void k_cg_p(int nV, const int *__restrict__ vprob, const double *__restrict__ z, double *__restrict__ p,
+                       const CGScalars *__restrict__ cg, const int *__restrict__ done)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    int q = vprob[i];
+    if (done[q]) return;
+    double b = cg[q].beta;
+    for (int k = 0; k < 3; ++k) p[3 * i + k] = z[3 * i + k] + b * p[3 * i + k];
+}
+
+// Relative residual per problem: out[q] = sqrt(|r_true|^2 / |P rhs|^2)
+__global__ void k_relres(RedArgs ra, const double *__restrict__ r, const CGScalars *__restrict__ cg,
+                         double *__restrict__ out)
+{
+    double s[1] = {0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        s[0] += r[3 * i] * r[3 * i] + r[3 * i + 1] * r[3 * i + 1] + r[3 * i + 2] * r[3 * i + 2];
+    if (reduce_phase<1>(s, ra))
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x)
+            out[q] = cg[q].bnorm2 > 0.0 ? sqrt(ra.sums[q] / cg[q].bnorm2) : 0.0;
+}
+
+// Solve P A-bar P y = P rhs (A-bar of the geometry `which`), x = P y.  The constraint Jacobian
+// (c.d_Cv, c.d_Ginv) must describe the projector to use.  rhs and x may not alias the CG scratch.
+cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
+                     int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s)
+{
+    SolverState &st = S(c);
+    const size_t vb = sizeof(double) * 3 * c.nV;
+    const int nb = (c.nV + 255) / 256;
+    double *r = c.d_r, *z = c.d_z, *p = c.d_p, *q = c.d_q, *y = c.d_y;
+    // r = P rhs, y = 0
+    TPE_CHECK(cudaMemcpyAsync(r, rhs, vb, cudaMemcpyDeviceToDevice, s));
+    TPE_CHECK(project(c, r, s, nullptr));
+    TPE_CHECK(cudaMemsetAsync(y, 0, vb, s));
+    TPE_CHECK(precond_apply(c, r, z, s, nullptr));
+    if (c.prm.precond != TP_PRECOND_NONE) TPE_CHECK(project(c, z, s, nullptr));
+    TPE_CHECK(cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, s));
+    k_cg_init<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 4), r, z, c.d_cg, st.done, st.active);
+    c.launches++;
+    const double tol2 = rtol * rtol;
+    const int every = std::max(1, c.prm.cg_check_every);
+    int it = 0;
+    int *h_active = c.h_pinned_i;
+    for (; it < maxit;) {
+        // q = P A-bar p
+        TPE_CHECK(pair_apply(c, gamma_geom, which, p, q, s));
+        TPE_CHECK(project(c, q, s, st.done));
+        k_cg_alpha<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 5), p, q, c.d_cg, st.done);
+        k_cg_update<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 6), c.d_vprob, p, q, y, r, c.d_cg, st.done, tol2,
+                                                   st.active);
+        c.launches += 2;
+        TPE_CHECK(precond_apply(c, r, z, s, st.done));
+        if (c.prm.precond != TP_PRECOND_NONE) TPE_CHECK(project(c, z, s, st.done));
+        k_cg_beta<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 7), r, c.prm.precond != TP_PRECOND_NONE ? z : r, c.d_cg,
+                                                 st.done);
+        k_cg_p<<<nb, 256, 0, s>>>(c.nV, c.d_vprob, c.prm.precond != TP_PRECOND_NONE ? z : r, p, c.d_cg, st.done);
+        c.launches += 2;
+        ++it;
+        if (it % every == 0 || it == maxit) {
+            TPE_CHECK(cudaMemcpyAsync(h_active, st.active, sizeof(int), cudaMemcpyDeviceToHost, s));
+            TPE_CHECK(cudaStreamSynchronize(s));
+            if (*h_active == 0) break;
+        }
+    }
+    // x = P y; true residual r = P (rhs - A-bar x) with the working-precision operator
+    TPE_CHECK(cudaMemcpyAsync(x, y, vb, cudaMemcpyDeviceToDevice, s));
+    TPE_CHECK(project(c, x, s, nullptr));
+    TPE_CHECK(pair_apply(c, gamma_geom, which, x, q, s));
+    TPE_CHECK(vec_axpby(c, 1.0, rhs, -1.0, q, r, s));
+    TPE_CHECK(project(c, r, s, nullptr));
+    double *rr = c.d_scal + 64 + 10 * (size_t)c.nProb;  // [nProb]
+    k_relres<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), r, c.d_cg, rr);
+    c.launches++;
+    std::vector<CGScalars> hcg(c.nProb);
+    std::vector<double> hrr(c.nProb);
+    TPE_CHECK(cudaMemcpyAsync(hcg.data(), c.d_cg, sizeof(CGScalars) * c.nProb, cudaMemcpyDeviceToHost, s));
+    TPE_CHECK(cudaMemcpyAsync(hrr.data(), rr, sizeof(double) * c.nProb, cudaMemcpyDeviceToHost, s));
+    TPE_CHECK(cudaStreamSynchronize(s));
+    int mx_it = 0, bd = 0, conv = 1;
+    double mx_rr = 0.0;
+    for (int qq = 0; qq < c.nProb; ++qq) {
+        mx_it = std::max(mx_it, hcg[qq].iters);
+        bd |= hcg[qq].breakdown;
+        conv &= (hcg[qq].done && !hcg[qq].breakdown) ? 1 : 0;
+        mx_rr = std::max(mx_rr, hrr[qq]);
+    }
+    if (iters) *iters = mx_it;
+    if (rel_res) *rel_res = mx_rr;
+    if (converged) *converged = conv;
+    if (breakdown) *breakdown = bd;
+    return cudaSuccess;
+}
+
+}  // namespace tpe

@@ -1,0 +1,178 @@
+// Internal declarations of the GB300 tangent-point library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tpe.h"
+
+namespace tpe {
+
+// Precision of the pair arithmetic.
+enum Prec { P64 = 0, P32 = 1, PMIX = 2 };
+
+// Which quantity a pair pass accumulates.
+enum PairOp { OP_ENERGY = 0, OP_DIFF = 1, OP_APPLY = 2, OP_DIAG = 3 };
+
+constexpr int kThreads = 128;  // threads per CTA of the pair passes
+constexpr int kTile = 128;     // source edges staged in shared memory per tile
+
+// One unit of the persistent pair-pass queue: targets [tgt0, tgt0 + ntgt) against sources
+// [src0, src1); results go to partial slot `slot`.  [nb_lo, nb_hi] spans every edge that
+// shares a vertex with some target of the item, so source tiles outside it skip the
+// disjointness test.
+struct WorkItem {
+    int tgt0, ntgt, src0, src1, slot, nb_lo, nb_hi, pad;
+};
+
+// FP32 edge record (48 B): a = (g_i1, l), b = (g_i2, T.x), c = (T.y, T.z, i1, i2 as bits);
+// lo = (low parts of g_i1 (3), low part of g_i2.x), lo2 = (g_i2.y low, g_i2.z low, 0, 0)
+// (double-float positions, used by the mixed-precision pass only).
+struct alignas(16) RecF {
+    float4 a, b, c;
+};
+struct alignas(16) RecLo {
+    float4 lo, lo2;
+};
+// FP64 edge record (96 B).
+struct alignas(16) RecD {
+    double2 a0, a1;  // g_i1.xy, (g_i1.z, l)
+    double2 b0, b1;  // g_i2.xy, (g_i2.z, T.x)
+    double2 c0;      // T.y, T.z
+    int i1, i2;
+    int pad0, pad1;
+};
+// Per-edge data of the vector u in an apply: du = (u_j2 - u_j1)/l_J (3 comps), ub = (u_j1 + u_j2)/2,
+// as double-float (hi + lo) so that the differences du_I - du_J, ub_I - ub_J are formed accurately.
+// a = (du_hi.xyz, ub_hi.x), b = (ub_hi.yz, du_lo.xy), c = (du_lo.z, ub_lo.xyz).
+struct alignas(16) URecF {
+    float4 a, b, c;
+};
+struct alignas(16) URecD {
+    double2 du0, du1, ub0, ub1;  // du.xy, (du.z, 0), ub.xy, (ub.z, 0)
+};
+
+struct KernelParams {
+    double alpha, beta, p;  // kernel exponents and p = 2 sigma + 1
+    int fast;               // (alpha, beta, p) == (2, 4.5, 2.5): specialised powers
+    double near2;           // squared near-pair cutoff (mixed precision)
+    float near2f;
+};
+
+// Device-side scalars of one CG solve (all FP64) - one block per problem.
+struct CGScalars {
+    double rz, rz_new, pq, alpha, beta, bnorm2, rnorm2;
+    int done, breakdown, iters;
+};
+
+struct Ctx {
+    // graph
+    int nV = 0, nE = 0, nCurves = 0, nProb = 0;
+    int independent = 0;
+    tp_params prm{};
+    KernelParams kp{};
+    std::vector<int32_t> h_edges, h_voff, h_eoff;
+    std::vector<int32_t> h_prob_v, h_prob_e;  // per-problem vertex / edge offsets [nProb + 1]
+    int32_t *d_edges = nullptr;                // [nE][2]
+    int32_t *d_inc_ptr = nullptr;              // [nV + 1] incidence CSR
+    int32_t *d_inc = nullptr;                  // [2 nE]: edge * 2 + slot (slot 1 <=> v is i2)
+    int32_t *d_vprob = nullptr;                // [nV] problem of each vertex
+    int32_t *d_eprob = nullptr;                // [nE] problem of each edge
+    int32_t *d_prob_v = nullptr, *d_prob_e = nullptr;
+    // spectral preconditioner: per closed curve
+    int spectral_ok = 0;
+    std::vector<int32_t> h_curve_n;            // vertices of each curve
+    std::vector<int> h_sym_sizes;              // distinct curve sizes
+    std::vector<int64_t> h_sym_off;            // offset of each distinct size in d_sym
+    double *d_sym = nullptr;                   // concatenated symbols
+    int64_t *d_curve_symoff = nullptr;         // [nCurves] offset of the curve's symbol
+    int32_t *d_voff = nullptr;                 // [nCurves + 1]
+    double2 *d_twiddle = nullptr;              // per distinct size: exp(-2 pi i k / n)
+    int64_t *d_curve_twoff = nullptr;
+    double *d_fft_re = nullptr, *d_fft_im = nullptr;  // [3][nV] spectral workspace
+    int max_curve_n = 0;
+    // pair-pass work lists, one per pair op class (blocking depends on targets per thread)
+    struct Plan {
+        WorkItem *d_items = nullptr;
+        int n_items = 0;
+        int max_slots = 0;
+        int grid = 0;
+        int tpt = 0;
+        int32_t *d_eslots = nullptr;  // [nE] number of partial slots of each target row
+    };
+    Plan plan_energy, plan_diff, plan_apply;
+    int *d_counter = nullptr;  // persistent-queue counters [8]
+    // edge records
+    RecF *d_recF = nullptr, *d_recF2 = nullptr;
+    RecLo *d_recLo = nullptr, *d_recLo2 = nullptr;
+    RecD *d_recD = nullptr, *d_recD2 = nullptr;
+    // FP64 edge quantities of the two geometries (0: base curve, 1: trial curve): [nE], [nE][3], [nE][3]
+    double *d_ellw[2] = {nullptr, nullptr}, *d_Tw[2] = {nullptr, nullptr}, *d_xw[2] = {nullptr, nullptr};
+    double mean_ell = 0.0;
+    URecF *d_urecF = nullptr;
+    URecD *d_urecD = nullptr;
+    // partial results [max_slots][nE][6] (FP64)
+    double *d_part = nullptr;
+    size_t part_elems = 0;
+    double *d_rows = nullptr;  // [nE]
+    // constraints: per problem x0 (3) and L0
+    double *d_x0L0 = nullptr;  // [nProb][4]
+    int constraints_set = 0;
+    double *d_Cv = nullptr;    // [nV][4][3] constraint Jacobian at the current curve
+    double *d_G = nullptr;     // [nProb][16] C C^T
+    double *d_Ginv = nullptr;  // [nProb][16]
+    double *d_red = nullptr;   // reduction scratch [nProb][16]
+    double *d_phi = nullptr;   // [nProb][4]
+    // CG vectors [nV][3]
+    double *d_y = nullptr, *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_q = nullptr, *d_diag = nullptr;
+    double *d_t1 = nullptr, *d_t2 = nullptr, *d_t3 = nullptr, *d_t4 = nullptr;  // temporaries [nV][3]
+    double *d_gam = nullptr;   // trial curve [nV][3]
+    double *d_E = nullptr;     // [nProb]
+    double *d_scal = nullptr;  // generic device scalars [64 + 8 nProb]
+    CGScalars *d_cg = nullptr; // [nProb]
+    int *d_err = nullptr;      // device error word
+    double *h_pinned = nullptr;  // pinned host staging [64 + 8 nProb]
+    int *h_pinned_i = nullptr;
+    int64_t launches = 0;
+    std::string err;
+    int sm_count = 0;
+    struct SolverState *sol = nullptr;
+    double *d_best = nullptr;  // [nV][3] line-search result
+    double *d_t5 = nullptr, *d_t6 = nullptr;
+};
+
+// ------------------------------------------------------------------ pair passes (pairs.cu)
+cudaError_t build_records(Ctx &c, const double *gamma, int which, cudaStream_t s);
+cudaError_t build_urecs(Ctx &c, const double *u, int which_geom, cudaStream_t s);
+cudaError_t pair_energy(Ctx &c, const double *gamma, int which, double *rows_out, double *E_out, cudaStream_t s);
+cudaError_t pair_diff(Ctx &c, const double *gamma, int which, double *dE, cudaStream_t s);
+cudaError_t pair_apply(Ctx &c, const double *gamma_geom, int which, const double *u, double *Au, cudaStream_t s);
+cudaError_t pair_diag(Ctx &c, const double *gamma_geom, int which, double *diag, cudaStream_t s);
+void make_plans(Ctx &c);
+
+// ------------------------------------------------------------------ solver pieces (solver.cu)
+cudaError_t constraints_eval(Ctx &c, const double *gamma, int which, double *phi, cudaStream_t s);
+cudaError_t constraints_jacobian(Ctx &c, int which, cudaStream_t s);
+cudaError_t constraints_targets(Ctx &c, int which, cudaStream_t s);
+cudaError_t project(Ctx &c, double *v, cudaStream_t s, const int *skip_flag);
+cudaError_t pinv_apply(Ctx &c, const double *b_phi, double scale, double *out, cudaStream_t s);
+cudaError_t spectral_setup(Ctx &c, cudaStream_t s);
+cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip_flag);
+cudaError_t solver_setup(Ctx &c);
+void solver_free(Ctx &c);
+cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
+                     int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s);
+cudaError_t vec_dot(Ctx &c, const double *a, const double *b, double *out_dev, cudaStream_t s);
+cudaError_t vec_axpby(Ctx &c, double a, const double *x, double b, const double *y, double *out, cudaStream_t s);
+cudaError_t vec_scale_dev(Ctx &c, const double *x, const double *num_dev, int invert_sqrt, double *out,
+                          cudaStream_t s);
+cudaError_t sum_problems(Ctx &c, const double *per_edge_or_vertex, int per_vertex, double *out, cudaStream_t s);
+
+}  // namespace tpe
+
+struct tp_ctx {
+    tpe::Ctx c;
+};

@@ -1,0 +1,238 @@
+"""Thin ctypes binding of include/tpe.h.  Argument marshalling only: every computation runs in
+libtpe.so.  Tensors must be CUDA float64 (vertex arrays [nV, 3], contiguous); the calls are enqueued
+on torch's current CUDA stream.  There is no CPU fallback: a missing library raises."""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtpe.so")
+
+TP_OK, TP_ERR_INVALID_ARG, TP_ERR_CUDA, TP_ERR_DEGENERATE_EDGE, TP_ERR_NONFINITE = 0, 1, 2, 3, 4
+TP_ERR_NOT_CONVERGED, TP_ERR_BREAKDOWN, TP_ERR_LINESEARCH, TP_ERR_PROJECTION, TP_ERR_OOM = 5, 6, 7, 8, 9
+TP_ERR_UNSUPPORTED = 10
+TP_FP64, TP_FP32, TP_MIXED = 0, 1, 2
+TP_PRECOND_NONE, TP_PRECOND_JACOBI, TP_PRECOND_SPECTRAL = 0, 1, 2
+
+STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ERR_DEGENERATE_EDGE",
+                4: "TP_ERR_NONFINITE", 5: "TP_ERR_NOT_CONVERGED", 6: "TP_ERR_BREAKDOWN", 7: "TP_ERR_LINESEARCH",
+                8: "TP_ERR_PROJECTION", 9: "TP_ERR_OOM", 10: "TP_ERR_UNSUPPORTED"}
+
+EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp_num_problems", "tp_set_params",
+            "tp_energy", "tp_differential", "sobolev_apply", "tp_gram_diagonal", "tp_precond_apply",
+            "tp_spectral_symbol", "tp_set_constraints_from", "tp_constraints", "sobolev_gradient", "descent_step",
+            "tp_launch_count"]
+
+
+class TpParams(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("precision", ctypes.c_int), ("near_cutoff", ctypes.c_double), ("cg_rtol", ctypes.c_double),
+                ("cg_maxit", ctypes.c_int), ("cg_check_every", ctypes.c_int), ("proj_cg_rtol", ctypes.c_double),
+                ("precond", ctypes.c_int), ("armijo_c", ctypes.c_double), ("shrink", ctypes.c_double),
+                ("max_halvings", ctypes.c_int), ("proj_tol", ctypes.c_double), ("proj_maxit", ctypes.c_int),
+                ("independent", ctypes.c_int)]
+
+
+class TpSolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double), ("converged", ctypes.c_int)]
+
+
+class TpStepInfo(ctypes.Structure):
+    _fields_ = [("E_before", ctypes.c_double), ("E_after", ctypes.c_double), ("tau", ctypes.c_double),
+                ("gnorm", ctypes.c_double), ("halvings", ctypes.c_int), ("proj_iters", ctypes.c_int),
+                ("cg_iters", ctypes.c_int), ("proj_cg_iters", ctypes.c_int), ("accepted", ctypes.c_int),
+                ("rel_res", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """Load libtpe.so (built by paper_2006_07859_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_2006_07859_gb300.build` first "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.tp_default_params.argtypes = [ctypes.POINTER(TpParams)]
+        L.tp_create.argtypes = [ctypes.POINTER(vp), i, i, vp, i, vp, vp, ctypes.POINTER(TpParams)]
+        L.tp_destroy.argtypes = [vp]
+        L.tp_last_error.argtypes = [vp]
+        L.tp_last_error.restype = ctypes.c_char_p
+        L.tp_num_problems.argtypes = [vp]
+        L.tp_set_params.argtypes = [vp, ctypes.POINTER(TpParams)]
+        L.tp_energy.argtypes = [vp, vp, vp, vp, vp]
+        L.tp_differential.argtypes = [vp, vp, vp, vp, vp]
+        L.sobolev_apply.argtypes = [vp, vp, vp, vp, vp]
+        L.tp_gram_diagonal.argtypes = [vp, vp, vp, vp]
+        L.tp_precond_apply.argtypes = [vp, vp, vp, vp, vp]
+        L.tp_spectral_symbol.argtypes = [vp, i, vp, vp]
+        L.tp_set_constraints_from.argtypes = [vp, vp, vp]
+        L.tp_constraints.argtypes = [vp, vp, vp, vp]
+        L.sobolev_gradient.argtypes = [vp, vp, vp, vp, ctypes.POINTER(TpSolveInfo), vp]
+        L.descent_step.argtypes = [vp, vp, ctypes.POINTER(TpStepInfo), vp]
+        L.tp_launch_count.argtypes = [vp]
+        L.tp_launch_count.restype = ctypes.c_int64
+        _lib = L
+    return _lib
+
+
+def default_params(**kw) -> TpParams:
+    p = TpParams()
+    library().tp_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """Owns a tp_ctx for one fixed graph (edges and curve offsets given on the host)."""
+
+    def __init__(self, edges, vertex_offsets, edge_offsets, n_vertices, params: TpParams | None = None, **kw):
+        L = library()
+        self._edges = np.ascontiguousarray(edges, dtype=np.int32)
+        self._voff = np.ascontiguousarray(vertex_offsets, dtype=np.int32)
+        self._eoff = np.ascontiguousarray(edge_offsets, dtype=np.int32)
+        self.params = params if params is not None else default_params(**kw)
+        self.n_vertices = int(n_vertices)
+        self.n_edges = int(self._edges.shape[0])
+        h = ctypes.c_void_p()
+        st = L.tp_create(ctypes.byref(h), self.n_vertices, self.n_edges, self._edges.ctypes.data, len(self._voff) - 1,
+                         self._voff.ctypes.data, self._eoff.ctypes.data, ctypes.byref(self.params))
+        self.handle = h
+        if st != TP_OK:
+            msg = L.tp_last_error(h).decode() if h.value else ""
+            if h.value:
+                L.tp_destroy(h)
+                self.handle = ctypes.c_void_p()
+            raise TpError(st, msg)
+        self.n_problems = L.tp_num_problems(h)
+
+    @classmethod
+    def from_curves(cls, curves, **kw):
+        return cls(curves.edges, curves.vertex_offsets, curves.edge_offsets, curves.n_vertices, **kw)
+
+    def close(self):
+        if self.handle and self.handle.value:
+            library().tp_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=()):
+        if st != TP_OK and st not in allow:
+            raise TpError(st, library().tp_last_error(self.handle).decode())
+        return st
+
+    def launch_count(self) -> int:
+        return int(library().tp_launch_count(self.handle))
+
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            setattr(self.params, k, v)
+        self._check(library().tp_set_params(self.handle, ctypes.byref(self.params)))
+
+
+# ---------------------------------------------------------------- entry points (same names as the C ABI)
+
+def _new(shape, like=None):
+    import torch
+    return torch.empty(shape, dtype=torch.float64, device="cuda")
+
+
+def tp_energy(ctx: Context, gamma, E=None, rows=None):
+    E = _new(ctx.n_problems) if E is None else E
+    ctx._check(library().tp_energy(ctx.handle, _ptr(gamma), _ptr(E), _ptr(rows), _stream()))
+    return E
+
+
+def tp_differential(ctx: Context, gamma, dE=None, E=None):
+    dE = _new((ctx.n_vertices, 3)) if dE is None else dE
+    ctx._check(library().tp_differential(ctx.handle, _ptr(gamma), _ptr(dE), _ptr(E), _stream()))
+    return dE
+
+
+def sobolev_apply(ctx: Context, gamma, u, Au=None):
+    Au = _new((ctx.n_vertices, 3)) if Au is None else Au
+    ctx._check(library().sobolev_apply(ctx.handle, _ptr(gamma), _ptr(u), _ptr(Au), _stream()))
+    return Au
+
+
+def tp_gram_diagonal(ctx: Context, gamma, diag=None):
+    diag = _new(ctx.n_vertices) if diag is None else diag
+    ctx._check(library().tp_gram_diagonal(ctx.handle, _ptr(gamma), _ptr(diag), _stream()))
+    return diag
+
+
+def tp_precond_apply(ctx: Context, gamma, r, z=None):
+    z = _new((ctx.n_vertices, 3)) if z is None else z
+    ctx._check(library().tp_precond_apply(ctx.handle, _ptr(gamma), _ptr(r), _ptr(z), _stream()))
+    return z
+
+
+def tp_spectral_symbol(ctx: Context, n: int, lam=None):
+    lam = _new(n) if lam is None else lam
+    ctx._check(library().tp_spectral_symbol(ctx.handle, int(n), _ptr(lam), _stream()))
+    return lam
+
+
+def tp_set_constraints_from(ctx: Context, gamma):
+    ctx._check(library().tp_set_constraints_from(ctx.handle, _ptr(gamma), _stream()))
+
+
+def tp_constraints(ctx: Context, gamma, phi=None):
+    phi = _new(4 * ctx.n_problems) if phi is None else phi
+    ctx._check(library().tp_constraints(ctx.handle, _ptr(gamma), _ptr(phi), _stream()))
+    return phi
+
+
+def sobolev_gradient(ctx: Context, gamma, dE, g=None, allow_not_converged=False):
+    g = _new((ctx.n_vertices, 3)) if g is None else g
+    info = TpSolveInfo()
+    allow = (TP_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    st = ctx._check(library().sobolev_gradient(ctx.handle, _ptr(gamma), _ptr(dE), _ptr(g), ctypes.byref(info),
+                                               _stream()), allow)
+    return g, {"iters": info.iters, "rel_res": info.rel_res, "converged": info.converged, "status": st}
+
+
+def descent_step(ctx: Context, gamma, allow=()):
+    info = TpStepInfo()
+    st = ctx._check(library().descent_step(ctx.handle, _ptr(gamma), ctypes.byref(info), _stream()), allow)
+    d = info.as_dict()
+    d["status"] = st
+    return d

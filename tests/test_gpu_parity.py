@@ -1,0 +1,120 @@
+"""GPU parity of the pair passes against the FP64 oracle on identical seeded inputs, through the
+C ABI.  FP64: relative 1e-10; FP32 / mixed: energy relative 1e-4, vectors cosine >= 0.9999."""
+import numpy as np
+import pytest
+
+import synth as S
+from tests.gpu_util import cosine, dev, host, make_ctx, need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+SIG = 0.75
+PRECS = [(0, 1e-10), (1, 1e-4), (2, 1e-4)]   # TP_FP64, TP_FP32, TP_MIXED
+
+
+def cases():
+    return {
+        "square": S.single(S.unit_square()),
+        "trefoil256": S.trefoil_256(),
+        "ragged300": S.single(S.fourier_knot(300, 5, 3)),
+        "scene3": S.scene([S.fourier_knot(70, 3, 1), S.fourier_knot(150, 4, 2), S.fourier_knot(201, 5, 3)]),
+        "open": S.single(S.fourier_knot(130, 3, 9), closed=False),
+    }
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    from oracle import oracle as O
+    O.build_library()
+    return O
+
+
+@pytest.mark.parametrize("prec,tol", PRECS)
+@pytest.mark.parametrize("name", ["square", "trefoil256", "ragged300", "scene3", "open"])
+def test_energy(torch, orc, name, prec, tol):
+    from paper_2006_07859_gb300 import tpe
+    c = cases()[name]
+    ctx = make_ctx(c, precision=prec, precond=1)
+    g = dev(c.gamma)
+    rows = torch.empty(c.n_edges, dtype=torch.float64, device="cuda")
+    E = host(tpe.tp_energy(ctx, g, rows=rows))
+    Eo, rows_o = orc.energy(c.gamma, c.edges, rows=True)
+    assert abs(E[0] - Eo) <= tol * abs(Eo)
+    assert rel(host(rows), rows_o) <= (tol if prec == 0 else 1e-3)
+
+
+@pytest.mark.parametrize("prec,tol", PRECS)
+@pytest.mark.parametrize("name", ["square", "trefoil256", "ragged300", "scene3", "open"])
+def test_differential(torch, orc, name, prec, tol):
+    from paper_2006_07859_gb300 import tpe
+    c = cases()[name]
+    ctx = make_ctx(c, precision=prec, precond=1)
+    dE = host(tpe.tp_differential(ctx, dev(c.gamma)))
+    dEo = orc.differential(c.gamma, c.edges)
+    if prec == 0:
+        assert rel(dE, dEo) <= 1e-10
+    else:
+        assert cosine(dE, dEo) >= 0.9999
+        assert rel(dE, dEo) <= 1e-3
+
+
+@pytest.mark.parametrize("prec,tol", PRECS)
+@pytest.mark.parametrize("name", ["square", "trefoil256", "ragged300", "scene3", "open"])
+def test_apply_and_diagonal(torch, orc, name, prec, tol):
+    from paper_2006_07859_gb300 import tpe
+    c = cases()[name]
+    ctx = make_ctx(c, precision=prec, precond=1)
+    U = np.random.default_rng(7).normal(size=(c.n_vertices, 3))
+    Au = host(tpe.sobolev_apply(ctx, dev(c.gamma), dev(U)))
+    Auo = orc.gram_apply(c.gamma, c.edges, SIG, U)
+    if prec == 0:
+        assert rel(Au, Auo) <= 1e-10
+    else:
+        assert cosine(Au, Auo) >= 0.9999
+        assert rel(Au, Auo) <= 1e-4
+    d = host(tpe.tp_gram_diagonal(ctx, dev(c.gamma)))
+    do = orc.gram_diagonal(c.gamma, c.edges, SIG)
+    assert rel(d, do) <= (1e-10 if prec == 0 else 1e-5)
+
+
+def test_smooth_vector_apply_accuracy(torch, orc):
+    """The difference form keeps the FP32 apply accurate on smooth vectors, where |A u| << |A||u|."""
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.fourier_knot(512, 6, 4))
+    t = np.linspace(0, 2 * np.pi, 512, endpoint=False)
+    U = np.stack([np.cos(t), np.sin(2 * t), np.cos(3 * t)], 1)
+    Auo = orc.gram_apply(c.gamma, c.edges, SIG, U)
+    for prec in (1, 2):
+        ctx = make_ctx(c, precision=prec, precond=1)
+        Au = host(tpe.sobolev_apply(ctx, dev(c.gamma), dev(U)))
+        assert rel(Au, Auo) <= 1e-4, prec
+
+
+def test_constraints(torch, orc):
+    from paper_2006_07859_gb300 import tpe
+    c = S.trefoil_256()
+    ctx = make_ctx(c, precision=0, precond=1)
+    g = dev(c.gamma)
+    tpe.tp_set_constraints_from(ctx, g)
+    moved = c.gamma + np.array([0.1, -0.2, 0.05]) + 0.01 * np.random.default_rng(1).normal(size=c.gamma.shape)
+    phi = host(tpe.tp_constraints(ctx, dev(moved)))
+    gr = orc.constraint_groups(c.gamma, c.edges)
+    assert rel(phi, orc.phi(moved, c.edges, gr)) <= 1e-10
+
+
+def test_degenerate_edge_is_reported(torch):
+    from paper_2006_07859_gb300 import tpe
+    g = S.unit_square()
+    g[2] = g[1]
+    c = S.single(g)
+    ctx = make_ctx(c, precision=1, precond=1)
+    with pytest.raises(tpe.TpError) as ei:
+        tpe.tp_energy(ctx, dev(g))
+        torch.cuda.synchronize()
+        tpe.tp_constraints(ctx, dev(g))
+    assert ei.value.status in (tpe.TP_ERR_DEGENERATE_EDGE,)
