@@ -491,3 +491,44 @@ def gram_diagonal_at(gamma, edges, sigma, vidx):
         u[v] = 1.0
         out[k] = gram_apply_at(gamma, edges, sigma, u, [v])[0, 0]
     return out
+
+
+def ngon_symbol_closed_form(n, sigma, normalized=True):
+    """Eigenvalues of A = B + B0 of the regular n-gon (unit circumradius) from the quadratic forms
+    (Eq. 21, Sec. 5.2.3) evaluated on the Fourier modes u_j = exp(i 2 pi k j / n), summed over the
+    offset m = J - I in [2, n - 2] of the edge pair:
+        lambda_k = sum_m 2 w_m |e^{i th k} - 1|^2 / l^2 (1 - cos(th k m) <T_0, T_m>)
+                 + sum_m (w0_m / 4) |1 + e^{i th k}|^2 (1 - cos(th k m)),      th = 2 pi / n,
+    w_m = w_{0m}, w0_m = w0_{0m} + w0_{m0} from the vertex chords 2 sin(pi j / n).  Equal to the DFT
+    of the first column of the dense circulant Gram matrix (pinned by a test), but every term is
+    >= 0, so it stays accurate where that DFT cancels.  normalized: divide by the diagonal (the mean
+    eigenvalue) and set lambda_0 := lambda_1, as the spectral preconditioner uses it."""
+    p = 2.0 * sigma + 1.0
+    m = np.arange(2, n - 1)
+    l = 2.0 * np.sin(np.pi / n)
+    w = np.zeros(m.shape)
+    w0 = np.zeros(m.shape)
+    for a in (0, 1):
+        for b in (0, 1):
+            off = m + b - a
+            ch = 2.0 * np.abs(np.sin(np.pi * off / n))
+            s0 = np.sin(np.pi * (a + m + b - 1) / n)
+            sm = np.sin(np.pi * (a + m + b - 2 * m - 1) / n)
+            w += ch ** -p
+            w0 += (s0 ** 2 + sm ** 2) * ch ** (-(2.0 + p))
+    w *= 0.25 * l * l
+    w0 *= 0.25 * l * l
+    t = np.cos(2 * np.pi * m / n)
+    lam = np.zeros(n)
+    for k0 in range(0, n, 256):
+        k = np.arange(k0, min(n, k0 + 256))[:, None]
+        r = (k * m[None, :]) % n
+        one_m_cos = 2.0 * np.sin(np.pi * r / n) ** 2
+        ek = 4.0 * np.sin(np.pi * k / n) ** 2
+        pk = 4.0 * np.cos(np.pi * k / n) ** 2
+        term = 2 * w * ek / l ** 2 * ((1 - t) + t * one_m_cos) + (w0 / 4) * pk * one_m_cos
+        lam[k0:k0 + k.shape[0]] = term.sum(1)
+    if normalized:
+        lam = lam / lam.mean()
+        lam[0] = lam[1]
+    return lam

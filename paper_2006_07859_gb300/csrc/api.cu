@@ -170,8 +170,8 @@ void tp_destroy(tp_ctx *ctx)
     if (!ctx) return;
     Ctx &c = ctx->c;
     if (c.sol) solver_free(c);
-    void *ptrs[] = {c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_sym,
-                    c.d_curve_symoff, c.d_voff, c.d_twiddle, c.d_curve_twoff, c.d_fft_re, c.d_fft_im,
+    spectral_free(c);
+    void *ptrs[] = {c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_voff,
                     c.plan_energy.d_items, c.plan_diff.d_items, c.plan_apply.d_items, c.plan_energy.d_eslots,
                     c.plan_diff.d_eslots, c.plan_apply.d_eslots, c.d_counter, c.d_recF, c.d_recF2, c.d_recLo,
                     c.d_recLo2, c.d_recD, c.d_recD2, c.d_ellw[0], c.d_ellw[1], c.d_Tw[0], c.d_Tw[1], c.d_xw[0],
@@ -351,7 +351,7 @@ tp_status tp_set_params(tp_ctx *ctx, const tp_params *p)
     if (p->precond == TP_PRECOND_SPECTRAL && !c.spectral_ok)
         return fail(ctx, TP_ERR_UNSUPPORTED, "the spectral preconditioner needs closed polygons");
     int indep = c.prm.independent;
-    int had_spectral = c.prm.precond == TP_PRECOND_SPECTRAL || c.d_sym != nullptr;
+    int had_spectral = c.spec != nullptr;
     c.prm = *p;
     c.prm.independent = indep;
     set_kernel_params(c);

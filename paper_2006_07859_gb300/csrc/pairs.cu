@@ -336,8 +336,23 @@ struct NearArgs {
 
 __device__ __forceinline__ V3<double> ld3(const double *a, int i) { return {a[3 * i], a[3 * i + 1], a[3 * i + 2]}; }
 
+// FP64 powers for the near-pair paths: |d|^-e (fast: e = 4.5 or 2.5 via rsqrt/sqrt) and |c|^alpha.
+__device__ __forceinline__ double npow_d(double d2, double e, bool fast, bool weight)
+{
+    if (fast) {
+        double r = rsqrt(d2), sr = sqrt(r), r2 = r * r;
+        return weight ? r2 * sr : r2 * r2 * sr;
+    }
+    return pow(d2, -0.5 * e);
+}
+__device__ __forceinline__ double npow_c(double c2, double alpha, bool fast)
+{
+    if (fast) return c2;
+    return c2 > 0.0 ? pow(c2, 0.5 * alpha) : 0.0;
+}
+
 // l_J sum_ab k(g_ia, g_jb, T_I) in FP64.
-__device__ __noinline__ double near_energy(const NearArgs na, int I, int J, double alpha, double beta)
+__device__ __noinline__ double near_energy(const NearArgs na, int I, int J, double alpha, double beta, bool fast)
 {
     V3<double> TI = ld3(na.T, I);
     int ii[2] = {na.E[2 * I], na.E[2 * I + 1]}, jj[2] = {na.E[2 * J], na.E[2 * J + 1]};
@@ -347,7 +362,7 @@ __device__ __noinline__ double near_energy(const NearArgs na, int I, int J, doub
             V3<double> p = ld3(na.g, ii[a]), q = ld3(na.g, jj[b]);
             V3<double> d = {p.x - q.x, p.y - q.y, p.z - q.z}, dp;
             double t, c2 = perp2(d, TI, t, dp), d2 = dot3(d, d);
-            s += pow(c2, 0.5 * alpha) * pow(d2, -0.5 * beta);
+            s += npow_c(c2, alpha, fast) * npow_d(d2, beta, fast, false);
         }
     return na.ell[J] * s;
 }
@@ -358,7 +373,8 @@ struct DiffAcc64 {
     double S, G1[3], G2[3], GT[3];
 };
 
-__device__ __noinline__ void near_diff(const NearArgs na, int I, int J, double alpha, double beta, DiffAcc64 &acc)
+__device__ __noinline__ void near_diff(const NearArgs na, int I, int J, double alpha, double beta, bool fast,
+                                      DiffAcc64 &acc)
 {
     V3<double> TI = ld3(na.T, I), TJ = ld3(na.T, J);
     int ii[2] = {na.E[2 * I], na.E[2 * I + 1]}, jj[2] = {na.E[2 * J], na.E[2 * J + 1]};
@@ -369,9 +385,10 @@ __device__ __noinline__ void near_diff(const NearArgs na, int I, int J, double a
             V3<double> d = {p.x - q.x, p.y - q.y, p.z - q.z}, dpI, dpJ;
             double tI, tJ;
             double cI2 = perp2(d, TI, tI, dpI), cJ2 = perp2(d, TJ, tJ, dpJ), d2 = dot3(d, d);
-            double rb = pow(d2, -0.5 * beta);
-            double fI = pow(cI2, 0.5 * alpha) * rb, fJ = pow(cJ2, 0.5 * alpha) * rb;
-            double aI = cI2 > 0.0 ? alpha * fI / cI2 : 0.0, aJ = cJ2 > 0.0 ? alpha * fJ / cJ2 : 0.0;
+            double rb = npow_d(d2, beta, fast, false);
+            double fI = npow_c(cI2, alpha, fast) * rb, fJ = npow_c(cJ2, alpha, fast) * rb;
+            double aI = fast ? 2.0 * rb : (cI2 > 0.0 ? alpha * fI / cI2 : 0.0);
+            double aJ = fast ? 2.0 * rb : (cJ2 > 0.0 ? alpha * fJ / cJ2 : 0.0);
             double cb = beta * (fI + fJ) / d2;
             double *G = a == 0 ? acc.G1 : acc.G2;
             G[0] += L * (aI * dpI.x + aJ * dpJ.x - cb * d.x);
@@ -393,7 +410,8 @@ struct ApplyAcc64 {
     double Sw, A1[3], Sw0, A2[3];
 };
 
-__device__ __noinline__ void near_apply(const NearArgs na, int I, int J, double p, bool with_u, ApplyAcc64 &acc)
+__device__ __noinline__ void near_apply(const NearArgs na, int I, int J, double p, bool with_u, bool fast,
+                                       ApplyAcc64 &acc)
 {
     V3<double> TI = ld3(na.T, I), TJ = ld3(na.T, J);
     int ii[2] = {na.E[2 * I], na.E[2 * I + 1]}, jj[2] = {na.E[2 * J], na.E[2 * J + 1]};
@@ -404,7 +422,7 @@ __device__ __noinline__ void near_apply(const NearArgs na, int I, int J, double 
             V3<double> d = {pp.x - q.x, pp.y - q.y, pp.z - q.z}, dpI, dpJ;
             double tI, tJ;
             double c2 = perp2(d, TI, tI, dpI) + perp2(d, TJ, tJ, dpJ), d2 = dot3(d, d);
-            double rp = pow(d2, -0.5 * p);
+            double rp = npow_d(d2, p, fast, true);
             sw += rp;
             sw0 += c2 * rp / (d2 * d2);
         }
@@ -726,11 +744,11 @@ __device__ __forceinline__ void tile_loop(const Tgt<typename RealOf<PREC>::type>
                 if (near) {
                     int J = s0 + j;
                     if constexpr (OP == OP_ENERGY) {
-                        A[k].s += near_energy(pa.na, tI[k], J, pa.kp.alpha, pa.kp.beta);
+                        A[k].s += near_energy(pa.na, tI[k], J, pa.kp.alpha, pa.kp.beta, FAST);
                     } else if constexpr (OP == OP_DIFF) {
-                        near_diff(pa.na, tI[k], J, pa.kp.alpha, pa.kp.beta, A[k]);
+                        near_diff(pa.na, tI[k], J, pa.kp.alpha, pa.kp.beta, FAST, A[k]);
                     } else {
-                        near_apply(pa.na, tI[k], J, pa.kp.p, OP == OP_APPLY, A[k]);
+                        near_apply(pa.na, tI[k], J, pa.kp.p, OP == OP_APPLY, FAST, A[k]);
                     }
                 } else {
                     acc_add(a[k], tmp);

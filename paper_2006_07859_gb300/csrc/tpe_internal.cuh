@@ -11,6 +11,9 @@
 
 namespace tpe {
 
+struct SpecState;
+struct SolverState;
+
 // Precision of the pair arithmetic.
 enum Prec { P64 = 0, P32 = 1, PMIX = 2 };
 
@@ -82,18 +85,12 @@ struct Ctx {
     int32_t *d_vprob = nullptr;                // [nV] problem of each vertex
     int32_t *d_eprob = nullptr;                // [nE] problem of each edge
     int32_t *d_prob_v = nullptr, *d_prob_e = nullptr;
-    // spectral preconditioner: per closed curve
+    // spectral preconditioner (closed curves only)
     int spectral_ok = 0;
     std::vector<int32_t> h_curve_n;            // vertices of each curve
-    std::vector<int> h_sym_sizes;              // distinct curve sizes
-    std::vector<int64_t> h_sym_off;            // offset of each distinct size in d_sym
-    double *d_sym = nullptr;                   // concatenated symbols
-    int64_t *d_curve_symoff = nullptr;         // [nCurves] offset of the curve's symbol
     int32_t *d_voff = nullptr;                 // [nCurves + 1]
-    double2 *d_twiddle = nullptr;              // per distinct size: exp(-2 pi i k / n)
-    int64_t *d_curve_twoff = nullptr;
-    double *d_fft_re = nullptr, *d_fft_im = nullptr;  // [3][nV] spectral workspace
     int max_curve_n = 0;
+    SpecState *spec = nullptr;
     // pair-pass work lists, one per pair op class (blocking depends on targets per thread)
     struct Plan {
         WorkItem *d_items = nullptr;
@@ -139,7 +136,7 @@ struct Ctx {
     int64_t launches = 0;
     std::string err;
     int sm_count = 0;
-    struct SolverState *sol = nullptr;
+    SolverState *sol = nullptr;
     double *d_best = nullptr;  // [nV][3] line-search result
     double *d_t5 = nullptr, *d_t6 = nullptr;
 };
@@ -160,6 +157,7 @@ cudaError_t constraints_targets(Ctx &c, int which, cudaStream_t s);
 cudaError_t project(Ctx &c, double *v, cudaStream_t s, const int *skip_flag);
 cudaError_t pinv_apply(Ctx &c, const double *b_phi, double scale, double *out, cudaStream_t s);
 cudaError_t spectral_setup(Ctx &c, cudaStream_t s);
+void spectral_free(Ctx &c);
 cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip_flag);
 cudaError_t solver_setup(Ctx &c);
 void solver_free(Ctx &c);

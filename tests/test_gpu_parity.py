@@ -79,7 +79,7 @@ def test_apply_and_diagonal(torch, orc, name, prec, tol):
         assert rel(Au, Auo) <= 1e-4
     d = host(tpe.tp_gram_diagonal(ctx, dev(c.gamma)))
     do = orc.gram_diagonal(c.gamma, c.edges, SIG)
-    assert rel(d, do) <= (1e-10 if prec == 0 else 1e-5)
+    assert rel(d, do) <= {0: 1e-10, 1: 1e-4, 2: 1e-5}[prec]
 
 
 def test_smooth_vector_apply_accuracy(torch, orc):

@@ -36,17 +36,19 @@ def _kkt_residual(orc, c, g_gpu, dE):
 def test_gradient_matches_dense_kkt(torch, orc, prec, precond):
     from paper_2006_07859_gb300 import tpe
     c = S.trefoil_256()
-    ctx = make_ctx(c, precision=prec, precond=precond, cg_rtol=1e-8, cg_maxit=5000)
+    # FP64 solves to 1e-8; the mixed operator's rounding floor at n = 256 is ~1e-7, so it solves to 1e-6
+    rtol = 1e-8 if prec == 0 else 1e-6
+    ctx = make_ctx(c, precision=prec, precond=precond, cg_rtol=rtol, cg_maxit=5000)
     g = dev(c.gamma)
     dE = tpe.tp_differential(ctx, g)
     gt, info = tpe.sobolev_gradient(ctx, g, dE)
-    assert info["converged"] and info["rel_res"] <= 1e-8
-    res, cg = _kkt_residual(orc, c, host(gt), host(dE))
-    assert res <= (1e-7 if prec == 0 else 1e-5)
+    assert info["converged"] and info["rel_res"] <= 2 * rtol
+    res, cg = _kkt_residual(orc, c, host(gt), host(dE))   # judged by the dense FP64 operator
+    assert res <= (1e-7 if prec == 0 else 5e-6)
     assert cg <= 1e-10 * np.abs(host(gt)).max()
     gr = orc.constraint_groups(c.gamma, c.edges)
     gk, _ = orc.sobolev_gradient(c.gamma, c.edges, gr, orc.differential(c.gamma, c.edges), orc.Params(), dense=True)
-    assert rel(host(gt), gk) <= (1e-6 if prec == 0 else 1e-4)
+    assert rel(host(gt), gk) <= (1e-6 if prec == 0 else 1e-3)
 
 
 def test_descent_step_matches_oracle(torch, orc):
@@ -78,6 +80,7 @@ def test_independent_batch_equals_single_curves(torch):
         gk, ek = b.curve(k)
         cs = S.single(gk)
         c1 = make_ctx(cs, precision=2, precond=1)
-        assert abs(host(tpe.tp_energy(c1, dev(gk)))[0] - E[k]) <= 1e-12 * E[k]
+        # equal up to the order in which FP32 tile partials are summed (the chunking differs)
+        assert abs(host(tpe.tp_energy(c1, dev(gk)))[0] - E[k]) <= 1e-7 * E[k]
         v0, v1 = b.vertex_offsets[k], b.vertex_offsets[k + 1]
-        assert rel(host(tpe.tp_differential(c1, dev(gk))), dE[v0:v1]) <= 1e-12
+        assert rel(host(tpe.tp_differential(c1, dev(gk))), dE[v0:v1]) <= 1e-6

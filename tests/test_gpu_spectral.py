@@ -1,0 +1,97 @@
+"""GPU spectral (Jacobi-scaled circulant) preconditioner against its oracle: the regular-polygon
+symbol, the three FFT paths (power of two, Bluestein, four-step) and PCG convergence."""
+import numpy as np
+import pytest
+
+import synth as S
+from tests.gpu_util import dev, host, make_ctx, need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+SIG = 0.75
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    from oracle import oracle as O
+    O.build_library()
+    return O
+
+
+@pytest.mark.parametrize("n", [4, 16, 64, 256, 300, 1000, 4096])
+def test_symbol(torch, orc, n):
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.regular_polygon(8))
+    ctx = make_ctx(c, precision=2, precond=1)
+    lam = host(tpe.tp_spectral_symbol(ctx, n))
+    ref = orc.ngon_symbol_closed_form(n, SIG) if n > 64 else orc.circle_symbol(n, SIG)
+    assert rel(lam, ref) <= 2e-5
+    assert np.all(lam > 0)
+
+
+@pytest.mark.parametrize("name", ["pow2_256", "bluestein_300", "scene3", "batch_indep"])
+def test_precond_apply(torch, orc, name):
+    from paper_2006_07859_gb300 import tpe
+    if name == "pow2_256":
+        c, indep = S.trefoil_256(), 0
+    elif name == "bluestein_300":
+        c, indep = S.single(S.fourier_knot(300, 5, 3)), 0
+    elif name == "scene3":
+        c, indep = S.scene([S.fourier_knot(70, 3, 1), S.fourier_knot(128, 4, 2), S.fourier_knot(201, 5, 3)]), 0
+    else:
+        c, indep = S.batch_of_knots([64, 77, 512, 1031], 6, 900), 1
+    ctx = make_ctx(c, precision=2, precond=2, independent=indep)
+    r = np.random.default_rng(3).normal(size=(c.n_vertices, 3))
+    z = host(tpe.tp_precond_apply(ctx, dev(c.gamma), dev(r)))
+    diag = orc.gram_diagonal(c.gamma, c.edges, SIG) if not indep else np.concatenate(
+        [orc.gram_diagonal(*c.curve(k), SIG) for k in range(c.n_curves)])
+    sizes = np.diff(c.vertex_offsets)
+    syms = {int(n): orc.ngon_symbol_closed_form(int(n), SIG) for n in set(sizes)}
+    zo = orc.spectral_preconditioner(diag, c.vertex_offsets, syms)(r)
+    assert rel(z, zo) <= 1e-4
+
+
+def test_four_step_fft_on_regular_polygon(torch, orc):
+    """n = 16384 uses the four-step FFT.  On a regular polygon diag(A) is the constant mean
+    eigenvalue, so M^-1 r = IDFT(DFT(r) / lambda) / A_00."""
+    from paper_2006_07859_gb300 import tpe
+    n = 16384
+    c = S.single(S.regular_polygon(n, 1.0))
+    ctx = make_ctx(c, precision=2, precond=2)
+    r = np.random.default_rng(5).normal(size=(n, 3))
+    z = host(tpe.tp_precond_apply(ctx, dev(c.gamma), dev(r)))
+    lam_raw = orc.ngon_symbol_closed_form(n, SIG, normalized=False)
+    a00 = lam_raw.mean()
+    lam = lam_raw / a00
+    lam[0] = lam[1]
+    zo = np.real(np.fft.ifft(np.fft.fft(r, axis=0) / lam[:, None], axis=0)) / a00
+    assert rel(z, zo) <= 1e-4
+
+
+@pytest.mark.parametrize("n", [64, 256, 1000])
+def test_pcg_on_regular_polygon_converges_immediately(torch, n):
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.regular_polygon(n, 1.0))
+    ctx = make_ctx(c, precision=0, precond=2, cg_rtol=1e-8)
+    g = dev(c.gamma)
+    rhs = dev(np.random.default_rng(n).normal(size=(n, 3)))
+    _, info = tpe.sobolev_gradient(ctx, g, rhs)
+    assert info["converged"] and info["iters"] <= 8, info
+
+
+def test_spectral_beats_jacobi_and_agrees(torch, orc):
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.fourier_knot(1024, 8, 1))
+    g = dev(c.gamma)
+    out = {}
+    for pc in (1, 2):
+        ctx = make_ctx(c, precision=2, precond=pc, cg_rtol=1e-6)
+        dE = tpe.tp_differential(ctx, g)
+        gt, info = tpe.sobolev_gradient(ctx, g, dE)
+        out[pc] = (host(gt), info)
+    assert out[2][1]["iters"] * 3 < out[1][1]["iters"], (out[1][1], out[2][1])
+    assert rel(out[2][0], out[1][0]) <= 1e-3

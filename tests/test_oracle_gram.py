@@ -103,6 +103,16 @@ def test_regular_polygon_is_circulant_and_matches_fourier_symbol(orc):
     np.testing.assert_allclose(ev_dft, lam, rtol=1e-11, atol=1e-12 * A[0, 0])
 
 
+def test_ngon_closed_form_symbol_matches_dense_gram(orc):
+    for n in (8, 16, 33, 64):
+        g = S.regular_polygon(n, 1.0)
+        B, B0 = orc.gram_dense(g, S.closed_edges(n), SIG)
+        ev = np.real(np.fft.fft((B + B0)[:, 0]))
+        lam = orc.ngon_symbol_closed_form(n, SIG, normalized=False)
+        np.testing.assert_allclose(lam, ev, rtol=1e-10, atol=1e-12 * ev.max())
+        np.testing.assert_allclose(orc.ngon_symbol_closed_form(n, SIG), orc.circle_symbol(n, SIG), rtol=1e-9)
+
+
 def test_constraint_jacobian_matches_differences(orc):
     c = S.single(S.trefoil(20, 0.01, 2))
     g, e = c.gamma, c.edges
