@@ -177,6 +177,21 @@ TPE_API tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, t
 /* Number of kernel launches this context has issued since creation (all entry points). */
 TPE_API int64_t tp_launch_count(const tp_ctx *ctx);
 
+/* Ordered disjoint edge pairs (I, J) one pair pass of this context visits (Eq. 17's index set,
+ * summed over problems): the algorithmic work unit of every pair kernel. */
+TPE_API int64_t tp_pairs_per_pass(const tp_ctx *ctx);
+
+/* Per-kernel timing with CUDA events recorded around every pair-kernel launch on its own stream.
+ * enable = 1 starts (and clears) the record; op: 0 energy, 1 differential, 2 apply, 3 diag.
+ * tp_profile_read synchronises the recorded events and returns the summed device time (ms) and
+ * the number of launches of that pair kernel since profiling was enabled. */
+TPE_API tp_status tp_profile(tp_ctx *ctx, int enable);
+TPE_API tp_status tp_profile_read(tp_ctx *ctx, int op, double *total_ms, int64_t *launches);
+
+/* Throughput microbenchmarks on the current device (no context needed): FP32 FMA FLOP/s, MUFU
+ * rsqrt op/s and FP64 FMA FLOP/s.  Returns 0 on success. */
+TPE_API int tp_measure_peaks(double *fp32_flops, double *mufu_ops, double *fp64_flops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -283,12 +283,14 @@ int orc_differential_at(int nV, const double *g, int nE, const int *E, double al
     for (int k = 0; k < nidx; ++k) {
         int v = vidx[k];
         double acc[3] = {0, 0, 0};
-        for (int I = 0; I < nE; ++I) {
-            int vinI = (E[2 * I] == v || E[2 * I + 1] == v);
-            for (int J = 0; J < nE; ++J) {
-                int vinJ = (E[2 * J] == v || E[2 * J + 1] == v);
-                if ((vinI || vinJ) && disjoint(&E[2 * I], &E[2 * J])) pair_energy_grad(&G, I, J, alpha, beta, acc, v);
-            }
+        /* the pairs that touch v: (X, Y) and (Y, X) for every edge X incident to v */
+        for (int X = 0; X < nE; ++X) {
+            if (E[2 * X] != v && E[2 * X + 1] != v) continue;
+            for (int Y = 0; Y < nE; ++Y)
+                if (disjoint(&E[2 * X], &E[2 * Y])) {
+                    pair_energy_grad(&G, X, Y, alpha, beta, acc, v);
+                    pair_energy_grad(&G, Y, X, alpha, beta, acc, v);
+                }
         }
         for (int c = 0; c < 3; ++c) out[3 * k + c] = acc[c];
     }
@@ -433,13 +435,14 @@ int orc_gram_apply_at(int nV, const double *g, int nE, const int *E, double sigm
         int v = vidx[k];
         apply_ctx ac = {u, &out[(size_t)k * m], m, v};
         for (int c = 0; c < m; ++c) out[(size_t)k * m + c] = 0.0;
-        for (int I = 0; I < nE; ++I) {
-            int vinI = (E[2 * I] == v || E[2 * I + 1] == v);
-            for (int J = 0; J < nE; ++J) {
-                int vinJ = (E[2 * J] == v || E[2 * J + 1] == v);
-                if ((vinI || vinJ) && disjoint(&E[2 * I], &E[2 * J]))
-                    pair_increments(&G, I, J, sigma, 1, 1, apply_incr, &ac);
-            }
+        /* increments with row v come from the ordered pairs (X, Y) and (Y, X), X incident to v */
+        for (int X = 0; X < nE; ++X) {
+            if (E[2 * X] != v && E[2 * X + 1] != v) continue;
+            for (int Y = 0; Y < nE; ++Y)
+                if (disjoint(&E[2 * X], &E[2 * Y])) {
+                    pair_increments(&G, X, Y, sigma, 1, 1, apply_incr, &ac);
+                    pair_increments(&G, Y, X, sigma, 1, 1, apply_incr, &ac);
+                }
         }
     }
     geom_free(&G);

@@ -165,6 +165,31 @@ int tp_num_problems(const tp_ctx *ctx) { return ctx ? ctx->c.nProb : 0; }
 
 int64_t tp_launch_count(const tp_ctx *ctx) { return ctx ? ctx->c.launches : 0; }
 
+int64_t tp_pairs_per_pass(const tp_ctx *ctx) { return ctx ? ctx->c.pairs_per_pass : 0; }
+
+tp_status tp_profile(tp_ctx *ctx, int enable)
+{
+    if (!ctx) return TP_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    prof_harvest(c);
+    for (int k = 0; k < 4; ++k) {
+        c.prof_ms[k] = 0.0;
+        c.prof_n[k] = 0;
+    }
+    c.profile = enable ? 1 : 0;
+    return TP_OK;
+}
+
+tp_status tp_profile_read(tp_ctx *ctx, int op, double *total_ms, int64_t *launches)
+{
+    if (!ctx || op < 0 || op > 3) return TP_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    prof_harvest(c);
+    if (total_ms) *total_ms = c.prof_ms[op];
+    if (launches) *launches = c.prof_n[op];
+    return TP_OK;
+}
+
 void tp_destroy(tp_ctx *ctx)
 {
     if (!ctx) return;
@@ -180,6 +205,8 @@ void tp_destroy(tp_ctx *ctx)
                     c.d_t5, c.d_t6, c.d_gam, c.d_best, c.d_E, c.d_scal, c.d_cg, c.d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    prof_harvest(c);
+    for (auto &e : c.prof_pool) cudaEventDestroy(e);
     if (c.h_pinned) cudaFreeHost(c.h_pinned);
     if (c.h_pinned_i) cudaFreeHost(c.h_pinned_i);
     delete ctx;
@@ -268,6 +295,22 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
     for (int q = 0; q < c.nProb; ++q) {
         for (int v = c.h_prob_v[q]; v < c.h_prob_v[q + 1]; ++v) vprob[v] = q;
         for (int I = c.h_prob_e[q]; I < c.h_prob_e[q + 1]; ++I) eprob[I] = q;
+    }
+    // ordered disjoint pairs per pass: n_q^2 minus, per edge, the edges sharing a vertex with it
+    c.pairs_per_pass = 0;
+    for (int q = 0; q < c.nProb; ++q) {
+        int64_t n = c.h_prob_e[q + 1] - c.h_prob_e[q];
+        int64_t excl = 0;
+        for (int I = c.h_prob_e[q]; I < c.h_prob_e[q + 1]; ++I) {
+            std::vector<int> nb;
+            for (int s = 0; s < 2; ++s) {
+                int v = c.h_edges[2 * I + s];
+                for (int k = deg[v]; k < deg[v + 1]; ++k) nb.push_back(inc[k] >> 1);
+            }
+            std::sort(nb.begin(), nb.end());
+            excl += std::unique(nb.begin(), nb.end()) - nb.begin();
+        }
+        c.pairs_per_pass += n * n - excl;
     }
     const bool p64 = prm.precision == TP_FP64, mix = prm.precision == TP_MIXED;
     CK(dalloc(&c.d_edges, 2 * (size_t)nE));
@@ -450,6 +493,28 @@ static tp_status precond_setup(tp_ctx *ctx, const double *gamma, cudaStream_t s)
     return TP_OK;
 }
 
+// H^s gradient of Eq. 22 by the mean-free route: y0 = A^+ dE, y1 = A^+ C_len^T (two CG solves on the
+// mean-free subspace), then the 4x4 correction (schur_gradient).  Needs the Jacobian of `gamma` in
+// c.d_Cv and the preconditioner set up.  Uses d_t3, d_t4, d_t6 as scratch.
+static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE, double *g, int *iters, double *rr,
+                                  int *conv, int *bd, cudaStream_t s)
+{
+    int i0 = 0, i1 = 0, c0 = 0, c1 = 0, b0 = 0, b1 = 0;
+    double r0 = 0, r1 = 0;
+    cudaError_t e = cg_solve(c, gamma, 0, dE, c.d_t3, c.prm.cg_rtol, c.prm.cg_maxit, &i0, &r0, &c0, &b0, s, 1);
+    if (e != cudaSuccess) return e;
+    e = clen_rhs(c, c.d_t6, s);
+    if (e != cudaSuccess) return e;
+    e = cg_solve(c, gamma, 0, c.d_t6, c.d_t4, c.prm.cg_rtol, c.prm.cg_maxit, &i1, &r1, &c1, &b1, s, 1);
+    if (e != cudaSuccess) return e;
+    e = schur_gradient(c, c.d_t3, c.d_t4, g, s);
+    *iters = i0 + i1;
+    *rr = std::max(r0, r1);
+    *conv = c0 && c1;
+    *bd = b0 || b1;
+    return e;
+}
+
 tp_status sobolev_gradient(tp_ctx *ctx, const double *gamma, const double *dE, double *g, tp_solve_info *info,
                            tp_stream stream)
 {
@@ -467,7 +532,7 @@ tp_status sobolev_gradient(tp_ctx *ctx, const double *gamma, const double *dE, d
     if (st) return st;
     int it = 0, conv = 0, bd = 0;
     double rr = 0.0;
-    CK(cg_solve(c, gamma, 0, dE, g, c.prm.cg_rtol, c.prm.cg_maxit, &it, &rr, &conv, &bd, s));
+    CK(gradient_solve(c, gamma, dE, g, &it, &rr, &conv, &bd, s));
     if (info) {
         info->iters = it;
         info->rel_res = rr;
@@ -500,11 +565,11 @@ __global__ void k_copy_masked(int nV, const double *__restrict__ src, const int 
     for (int k = 0; k < 3; ++k) dst[3 * i + k] = src[3 * i + k];
 }
 
-// x += a * y
+// x += a - b (b may be NULL)
 __global__ void k_add(int n, double *__restrict__ x, const double *__restrict__ a, const double *__restrict__ b)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x[i] += a[i] - b[i];
+    if (i < n) x[i] += a[i] - (b ? b[i] : 0.0);
 }
 
 tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream stream)
@@ -525,6 +590,7 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
     double *E0 = c.d_scal + 64, *E1 = c.d_scal + 64 + nP, *gg = c.d_scal + 64 + 2 * nP,
            *slope = c.d_scal + 64 + 3 * nP, *tau_d = c.d_scal + 64 + 4 * nP;
     double *dE = c.d_t1, *g = c.d_t2, *dir = c.d_t3, *z = c.d_t4, *rhs = c.d_t5, *x = c.d_t6;
+    // gradient_solve uses d_t3, d_t4, d_t6 as scratch before dir / z / x are written
     CK(pair_energy(c, gamma, 0, nullptr, E0, s));
     CK(pair_diff(c, gamma, 0, dE, s));
     // g~ = projected H^s gradient
@@ -533,7 +599,7 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
     if (st) return st;
     int it = 0, conv = 0, bd = 0;
     double rr = 0.0;
-    CK(cg_solve(c, gamma, 0, dE, g, c.prm.cg_rtol, c.prm.cg_maxit, &it, &rr, &conv, &bd, s));
+    CK(gradient_solve(c, gamma, dE, g, &it, &rr, &conv, &bd, s));
     if (bd) return fail(ctx, TP_ERR_BREAKDOWN, "CG breakdown in the gradient solve");
     // d = g / |g| per problem, slope = <dE, d>
     CK(vec_dot(c, g, g, gg, s));
@@ -589,15 +655,17 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
             if (all || pi >= c.prm.proj_maxit) break;
             for (int q = 0; q < nP; ++q)
                 if (pending[q] && !ok[q]) pit[q] = pi + 1;
-            // z = C^+ (-Phi) at the trial curve; rhs = A-bar(gamma) z; P A-bar P y = P rhs; trial += z - y
+            // x = argmin x^T A-bar(gamma) x / 2 s.t. C(trial) x = -Phi(trial) (Eq. 23) by the mean-free route:
+            // y1 = A-bar(gamma)^+ C_len(trial)^T, then x = mu y1 + N t; trial += x
             CK(constraints_jacobian(c, 1, s));
-            CK(pinv_apply(c, c.d_phi, -1.0, z, s));
-            CK(pair_apply(c, gamma, 0, z, rhs, s));
+            CK(clen_rhs(c, rhs, s));
             int pit_cg = 0, pconv = 0, pbd = 0;
             double prr = 0.0;
-            CK(cg_solve(c, gamma, 0, rhs, x, c.prm.proj_cg_rtol, c.prm.cg_maxit, &pit_cg, &prr, &pconv, &pbd, s));
+            CK(cg_solve(c, gamma, 0, rhs, z, c.prm.proj_cg_rtol, c.prm.cg_maxit, &pit_cg, &prr, &pconv, &pbd, s,
+                        1));
             proj_cg_total += pit_cg;
-            k_add<<<(3 * nV + 255) / 256, 256, 0, s>>>(3 * nV, c.d_gam, z, x);
+            CK(schur_projection(c, z, c.d_phi, -1.0, x, s));
+            k_add<<<(3 * nV + 255) / 256, 256, 0, s>>>(3 * nV, c.d_gam, x, nullptr);
             c.launches++;
         }
         // energy of the projected trial and the Armijo test

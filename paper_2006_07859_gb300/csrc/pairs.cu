@@ -998,6 +998,37 @@ static int occupancy_of(const Ctx &c)
 constexpr int kTptEnergy = 4, kTptDiff = 2, kTptApply = 2;
 constexpr int kTptEnergy64 = 1, kTptDiff64 = 1, kTptApply64 = 1;
 
+// ---------------------------------------------------------------------------------- profiling
+
+constexpr int kProfSlots = 1024;
+
+int prof_begin(Ctx &c, int op, cudaStream_t s)
+{
+    if (c.prof_pool.empty()) {
+        c.prof_pool.resize(2 * kProfSlots);
+        for (auto &e : c.prof_pool) cudaEventCreate(&e);
+    }
+    if ((int)c.prof_pending.size() == kProfSlots) prof_harvest(c);
+    int slot = (int)c.prof_pending.size();
+    c.prof_pending.push_back({op, slot});
+    cudaEventRecord(c.prof_pool[2 * slot], s);
+    return slot;
+}
+
+void prof_end(Ctx &c, int slot, cudaStream_t s) { cudaEventRecord(c.prof_pool[2 * slot + 1], s); }
+
+void prof_harvest(Ctx &c)
+{
+    for (auto &pe : c.prof_pending) {
+        cudaEventSynchronize(c.prof_pool[2 * pe.second + 1]);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c.prof_pool[2 * pe.second], c.prof_pool[2 * pe.second + 1]);
+        c.prof_ms[pe.first] += ms;
+        c.prof_n[pe.first] += 1;
+    }
+    c.prof_pending.clear();
+}
+
 void make_plans(Ctx &c)
 {
     // The chunking must be identical across precisions of one op class; all slots share one layout,
@@ -1069,6 +1100,7 @@ static cudaError_t run_pairs(Ctx &c, int which, const double *gamma, const doubl
     pa.kp = c.kp;
     const int g = pl.grid;
     const bool f = c.kp.fast != 0;
+    const int slot = c.profile ? prof_begin(c, OP, s) : -1;
     switch (c.prm.precision) {
     case TP_FP64:
         if (f) k_pairs<P64, OP, (OP == OP_ENERGY ? kTptEnergy64 : OP == OP_DIFF ? kTptDiff64 : kTptApply64), true><<<g, kThreads, 0, s>>>(pa);
@@ -1083,6 +1115,7 @@ static cudaError_t run_pairs(Ctx &c, int which, const double *gamma, const doubl
         else k_pairs<P32, OP, (OP == OP_ENERGY ? kTptEnergy : OP == OP_DIFF ? kTptDiff : kTptApply), false><<<g, kThreads, 0, s>>>(pa);
         break;
     }
+    if (slot >= 0) prof_end(c, slot, s);
     c.launches++;
     return cudaGetLastError();
 }

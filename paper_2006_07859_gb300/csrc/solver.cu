@@ -619,8 +619,17 @@ __global__ void k_relres(RedArgs ra, const double *__restrict__ r, const CGScala
 
 // Solve P A-bar P y = P rhs (A-bar of the geometry `which`), x = P y.  The constraint Jacobian
 // (c.d_Cv, c.d_Ginv) must describe the projector to use.  rhs and x may not alias the CG scratch.
+cudaError_t project_mean(Ctx &c, double *v, cudaStream_t s, const int *skip);
+
+// proj_mode 0: P = I - C^T (C C^T)^-1 C (constraint projector); 1: P = subtract the per-problem mean.
+static cudaError_t projector(Ctx &c, int mode, double *v, cudaStream_t s, const int *skip)
+{
+    return mode ? project_mean(c, v, s, skip) : project(c, v, s, skip);
+}
+
 cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
-                     int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s)
+                     int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s,
+                     int proj_mode)
 {
     SolverState &st = S(c);
     const size_t vb = sizeof(double) * 3 * c.nV;
@@ -628,10 +637,10 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
     double *r = c.d_r, *z = c.d_z, *p = c.d_p, *q = c.d_q, *y = c.d_y;
     // r = P rhs, y = 0
     TPE_CHECK(cudaMemcpyAsync(r, rhs, vb, cudaMemcpyDeviceToDevice, s));
-    TPE_CHECK(project(c, r, s, nullptr));
+    TPE_CHECK(projector(c, proj_mode, r, s, nullptr));
     TPE_CHECK(cudaMemsetAsync(y, 0, vb, s));
     TPE_CHECK(precond_apply(c, r, z, s, nullptr));
-    if (c.prm.precond != TP_PRECOND_NONE) TPE_CHECK(project(c, z, s, nullptr));
+    if (c.prm.precond != TP_PRECOND_NONE) TPE_CHECK(projector(c, proj_mode, z, s, nullptr));
     TPE_CHECK(cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, s));
     k_cg_init<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 4), r, z, c.d_cg, st.done, st.active);
     c.launches++;
@@ -642,13 +651,13 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
     for (; it < maxit;) {
         // q = P A-bar p
         TPE_CHECK(pair_apply(c, gamma_geom, which, p, q, s));
-        TPE_CHECK(project(c, q, s, st.done));
+        TPE_CHECK(projector(c, proj_mode, q, s, st.done));
         k_cg_alpha<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 5), p, q, c.d_cg, st.done);
         k_cg_update<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 6), c.d_vprob, p, q, y, r, c.d_cg, st.done, tol2,
                                                    st.active);
         c.launches += 2;
         TPE_CHECK(precond_apply(c, r, z, s, st.done));
-        if (c.prm.precond != TP_PRECOND_NONE) TPE_CHECK(project(c, z, s, st.done));
+        if (c.prm.precond != TP_PRECOND_NONE) TPE_CHECK(projector(c, proj_mode, z, s, st.done));
         k_cg_beta<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 7), r, c.prm.precond != TP_PRECOND_NONE ? z : r, c.d_cg,
                                                  st.done);
         k_cg_p<<<nb, 256, 0, s>>>(c.nV, c.d_vprob, c.prm.precond != TP_PRECOND_NONE ? z : r, p, c.d_cg, st.done);
@@ -662,10 +671,10 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
     }
     // x = P y; true residual r = P (rhs - A-bar x) with the working-precision operator
     TPE_CHECK(cudaMemcpyAsync(x, y, vb, cudaMemcpyDeviceToDevice, s));
-    TPE_CHECK(project(c, x, s, nullptr));
+    TPE_CHECK(projector(c, proj_mode, x, s, nullptr));
     TPE_CHECK(pair_apply(c, gamma_geom, which, x, q, s));
     TPE_CHECK(vec_axpby(c, 1.0, rhs, -1.0, q, r, s));
-    TPE_CHECK(project(c, r, s, nullptr));
+    TPE_CHECK(projector(c, proj_mode, r, s, nullptr));
     double *rr = c.d_scal + 64 + 10 * (size_t)c.nProb;  // [nProb]
     k_relres<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), r, c.d_cg, rr);
     c.launches++;
@@ -687,6 +696,173 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
     if (converged) *converged = conv;
     if (breakdown) *breakdown = bd;
     return cudaSuccess;
+}
+
+}  // namespace tpe
+
+namespace tpe {
+
+// ---------------------------------------------------------------------------------- mean-free route
+//
+// For the barycenter + total-length constraint set the KKT systems of Eqs. 22-23 reduce to solves
+// on the mean-free subspace.  null(A-bar) = span{e_x, e_y, e_z} (translations), and C_bary N = L Id,
+// C_len N = 0 (N: the translation basis).  Solvability of A-bar g + C^T lambda = dE needs
+// N^T C^T lambda = 0, i.e. lambda_bary = 0, hence
+//   g = A^+ dE - lambda_len A^+ C_len^T + N t,   lambda_len = <C_len, A^+ dE> / <C_len, A^+ C_len^T>,
+//   t = -(C_bary N)^-1 C_bary (A^+ dE - lambda_len A^+ C_len^T),
+// and the constraint projection min x^T A-bar x / 2 s.t. C x = b has x = mu A^+ C_len^T + N t with
+// mu = b_len / <C_len, A^+ C_len^T>, t = (C_bary N)^-1 (b_bary - mu C_bary A^+ C_len^T).
+// A^+ is applied by CG on the mean-free subspace (projector: subtract the per-problem mean).
+
+// per-problem mean of each component
+__global__ void k_mean(RedArgs ra, const double *__restrict__ v, const int *__restrict__ prob_v,
+                       double *__restrict__ mean)
+{
+    double s[3] = {0, 0, 0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        for (int k = 0; k < 3; ++k) s[k] += v[3 * i + k];
+    if (reduce_phase<3>(s, ra))
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+            double n = (double)(prob_v[q + 1] - prob_v[q]);
+            for (int k = 0; k < 3; ++k) mean[3 * q + k] = n > 0 ? ra.sums[3 * q + k] / n : 0.0;
+        }
+}
+
+__global__ void k_sub_mean(int nV, const double *__restrict__ mean, const int *__restrict__ vprob,
+                           double *__restrict__ v, const int *__restrict__ skip)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    int q = vprob[i];
+    if (skip && skip[q]) return;
+    for (int k = 0; k < 3; ++k) v[3 * i + k] -= mean[3 * q + k];
+}
+
+cudaError_t project_mean(Ctx &c, double *v, cudaStream_t s, const int *skip)
+{
+    SolverState &st = S(c);
+    k_mean<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 2), v, c.d_prob_v, st.mu);
+    k_sub_mean<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, st.mu, c.d_vprob, v, skip);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
+// out[v] = C_len row (row 3 of C) at vertex v
+__global__ void k_clen(int nV, const double *__restrict__ C, double *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    for (int k = 0; k < 3; ++k) out[3 * i + k] = C[(size_t)i * 12 + 9 + k];
+}
+
+cudaError_t clen_rhs(Ctx &c, double *out, cudaStream_t s)
+{
+    k_clen<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_Cv, out);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+// Reductions per problem: s[0] = <C_len, a>, s[1] = <C_len, b>, s[2..4] = C_bary_k . b,
+// s[5..13] = (C_bary N)_kj = sum_v C[v][k][j].
+__global__ void k_schur_red(RedArgs ra, const double *__restrict__ C, const double *__restrict__ a,
+                            const double *__restrict__ b, double *__restrict__ out)
+{
+    double s[14] = {0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double *cv = C + (size_t)i * 12;
+        for (int j = 0; j < 3; ++j) {
+            double av = a ? a[3 * i + j] : 0.0, bv = b[3 * i + j];
+            s[0] += cv[9 + j] * av;
+            s[1] += cv[9 + j] * bv;
+            for (int k = 0; k < 3; ++k) {
+                s[2 + k] += cv[3 * k + j] * bv;
+                s[5 + 3 * k + j] += cv[3 * k + j];
+            }
+        }
+    }
+    if (reduce_phase<14>(s, ra))
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x)
+            for (int k = 0; k < 14; ++k) out[14 * q + k] = ra.sums[14 * q + k];
+}
+
+__device__ void solve3(const double *M, const double *r, double *x)
+{
+    double a = M[0], b = M[1], c = M[2], d = M[3], e = M[4], f = M[5], g = M[6], h = M[7], k = M[8];
+    double det = a * (e * k - f * h) - b * (d * k - f * g) + c * (d * h - e * g);
+    if (det == 0.0) det = 1e-300;
+    double inv[9] = {(e * k - f * h), -(b * k - c * h), (b * f - c * e), -(d * k - f * g), (a * k - c * g),
+                     -(a * f - c * d), (d * h - e * g), -(a * h - b * g), (a * e - b * d)};
+    for (int i = 0; i < 3; ++i) x[i] = (inv[3 * i] * r[0] + inv[3 * i + 1] * r[1] + inv[3 * i + 2] * r[2]) / det;
+}
+
+// g' = y0 - lambda y1 with lambda = s0 / s1 (per problem), written to out.
+__global__ void k_schur_lin(int nV, const double *__restrict__ red, const double *__restrict__ y0,
+                            const double *__restrict__ y1, const int *__restrict__ vprob, double *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    const double *r = red + 14 * vprob[i];
+    double lam = r[1] != 0.0 ? r[0] / r[1] : 0.0;
+    for (int k = 0; k < 3; ++k) out[3 * i + k] = y0[3 * i + k] - lam * y1[3 * i + k];
+}
+
+// out += t with (C_bary N) t = target - C_bary out  (target: -phi_bary scaled, or 0)
+__global__ void k_schur_shift(int nV, const double *__restrict__ red, const double *__restrict__ phi, double phi_scale,
+                              const int *__restrict__ vprob, double *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    int q = vprob[i];
+    const double *r = red + 14 * q;
+    double rhs[3], t[3];
+    for (int k = 0; k < 3; ++k) rhs[k] = (phi ? phi_scale * phi[4 * q + k] : 0.0) - r[2 + k];
+    solve3(r + 5, rhs, t);
+    for (int k = 0; k < 3; ++k) out[3 * i + k] += t[k];
+}
+
+// x = mu y1 with mu = b_len / <C_len, y1>, b = phi_scale * phi (per problem).
+__global__ void k_proj_lin(int nV, const double *__restrict__ red, const double *__restrict__ phi, double phi_scale,
+                           const double *__restrict__ y1, const int *__restrict__ vprob, double *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    int q = vprob[i];
+    const double *r = red + 14 * q;
+    double mu = r[1] != 0.0 ? phi_scale * phi[4 * q + 3] / r[1] : 0.0;
+    for (int k = 0; k < 3; ++k) out[3 * i + k] = mu * y1[3 * i + k];
+}
+
+// g = A^+ dE - lambda A^+ C_len^T + N t from y0 = A^+ dE and y1 = A^+ C_len^T (Jacobian in c.d_Cv).
+cudaError_t schur_gradient(Ctx &c, const double *y0, const double *y1, double *g, cudaStream_t s)
+{
+    SolverState &st = S(c);
+    double *red = st.sums + 0;  // scratch reused below
+    double *red_out = c.d_red;  // [nProb][14] (d_red holds 16 per problem)
+    (void)red;
+    const int nb = (c.nV + 255) / 256;
+    k_schur_red<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_Cv, y0, y1, red_out);
+    k_schur_lin<<<nb, 256, 0, s>>>(c.nV, red_out, y0, y1, c.d_vprob, g);
+    k_schur_red<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_Cv, nullptr, g, red_out);
+    k_schur_shift<<<nb, 256, 0, s>>>(c.nV, red_out, nullptr, 0.0, c.d_vprob, g);
+    c.launches += 4;
+    return cudaGetLastError();
+}
+
+// x = mu y1 + N t solving C x = phi_scale * phi with y1 = A^+ C_len^T (Jacobian in c.d_Cv).
+cudaError_t schur_projection(Ctx &c, const double *y1, const double *phi, double phi_scale, double *x,
+                             cudaStream_t s)
+{
+    SolverState &st = S(c);
+    double *red_out = c.d_red;
+    const int nb = (c.nV + 255) / 256;
+    k_schur_red<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_Cv, nullptr, y1, red_out);
+    k_proj_lin<<<nb, 256, 0, s>>>(c.nV, red_out, phi, phi_scale, y1, c.d_vprob, x);
+    k_schur_red<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_Cv, nullptr, x, red_out);
+    k_schur_shift<<<nb, 256, 0, s>>>(c.nV, red_out, phi, phi_scale, c.d_vprob, x);
+    c.launches += 4;
+    return cudaGetLastError();
 }
 
 }  // namespace tpe

@@ -139,7 +139,18 @@ struct Ctx {
     SolverState *sol = nullptr;
     double *d_best = nullptr;  // [nV][3] line-search result
     double *d_t5 = nullptr, *d_t6 = nullptr;
+    int64_t pairs_per_pass = 0;
+    // per-kernel event timing (tp_profile)
+    int profile = 0;
+    std::vector<cudaEvent_t> prof_pool;
+    std::vector<std::pair<int, int>> prof_pending;  // (op, slot)
+    double prof_ms[4] = {0, 0, 0, 0};
+    int64_t prof_n[4] = {0, 0, 0, 0};
 };
+
+int prof_begin(Ctx &c, int op, cudaStream_t s);
+void prof_end(Ctx &c, int slot, cudaStream_t s);
+void prof_harvest(Ctx &c);
 
 // ------------------------------------------------------------------ pair passes (pairs.cu)
 cudaError_t build_records(Ctx &c, const double *gamma, int which, cudaStream_t s);
@@ -162,7 +173,13 @@ cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, co
 cudaError_t solver_setup(Ctx &c);
 void solver_free(Ctx &c);
 cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
-                     int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s);
+                     int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s,
+                     int proj_mode);
+cudaError_t project_mean(Ctx &c, double *v, cudaStream_t s, const int *skip);
+cudaError_t clen_rhs(Ctx &c, double *out, cudaStream_t s);
+cudaError_t schur_gradient(Ctx &c, const double *y0, const double *y1, double *g, cudaStream_t s);
+cudaError_t schur_projection(Ctx &c, const double *y1, const double *phi, double phi_scale, double *x,
+                             cudaStream_t s);
 cudaError_t vec_dot(Ctx &c, const double *a, const double *b, double *out_dev, cudaStream_t s);
 cudaError_t vec_axpby(Ctx &c, double a, const double *x, double b, const double *y, double *out, cudaStream_t s);
 cudaError_t vec_scale_dev(Ctx &c, const double *x, const double *num_dev, int invert_sqrt, double *out,

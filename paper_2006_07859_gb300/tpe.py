@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ER
 EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp_num_problems", "tp_set_params",
             "tp_energy", "tp_differential", "sobolev_apply", "tp_gram_diagonal", "tp_precond_apply",
             "tp_spectral_symbol", "tp_set_constraints_from", "tp_constraints", "sobolev_gradient", "descent_step",
-            "tp_launch_count"]
+            "tp_launch_count", "tp_pairs_per_pass", "tp_profile", "tp_profile_read", "tp_measure_peaks"]
 
 
 class TpParams(ctypes.Structure):
@@ -88,6 +88,12 @@ def library() -> ctypes.CDLL:
         L.descent_step.argtypes = [vp, vp, ctypes.POINTER(TpStepInfo), vp]
         L.tp_launch_count.argtypes = [vp]
         L.tp_launch_count.restype = ctypes.c_int64
+        L.tp_pairs_per_pass.argtypes = [vp]
+        L.tp_pairs_per_pass.restype = ctypes.c_int64
+        L.tp_profile.argtypes = [vp, i]
+        L.tp_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64)]
+        pdd = ctypes.POINTER(d)
+        L.tp_measure_peaks.argtypes = [pdd, pdd, pdd]
         _lib = L
     return _lib
 
@@ -161,6 +167,17 @@ class Context:
 
     def launch_count(self) -> int:
         return int(library().tp_launch_count(self.handle))
+
+    def pairs_per_pass(self) -> int:
+        return int(library().tp_pairs_per_pass(self.handle))
+
+    def profile(self, enable=True):
+        self._check(library().tp_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self, op: int):
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        self._check(library().tp_profile_read(self.handle, op, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def set_params(self, **kw):
         for k, v in kw.items():
@@ -236,3 +253,11 @@ def descent_step(ctx: Context, gamma, allow=()):
     d = info.as_dict()
     d["status"] = st
     return d
+
+
+def tp_measure_peaks():
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = library().tp_measure_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    if st != 0:
+        raise TpError(TP_ERR_CUDA, "tp_measure_peaks failed")
+    return {"fp32_flops": a.value, "mufu_ops": b.value, "fp64_flops": c.value}
