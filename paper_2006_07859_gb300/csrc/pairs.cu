@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "tpe_internal.cuh"
@@ -83,7 +84,10 @@ __global__ void k_records(int nE, const double *__restrict__ g, const int *__res
             RecLo q;
             q.lo = make_float4((float)(p1[0] - (double)h1[0]), (float)(p1[1] - (double)h1[1]),
                                (float)(p1[2] - (double)h1[2]), (float)(p2[0] - (double)h2[0]));
-            q.lo2 = make_float4((float)(p2[1] - (double)h2[1]), (float)(p2[2] - (double)h2[2]), 0.f, 0.f);
+            float th[3] = {(float)t[0], (float)t[1], (float)t[2]};
+            q.lo2 = make_float4((float)(p2[1] - (double)h2[1]), (float)(p2[2] - (double)h2[2]),
+                                (float)(t[0] - (double)th[0]), (float)(t[1] - (double)th[1]));
+            q.lo3 = make_float4((float)(t[2] - (double)th[2]), 0.f, 0.f, 0.f);
             recLo[I] = q;
         }
     }
@@ -199,7 +203,7 @@ __device__ __forceinline__ R dot3(V3<R> a, V3<R> b)
 template <class R>
 struct Tgt {
     V3<R> p1, p2, T;   // hi parts (PMIX) or the values
-    V3<R> l1, l2;      // lo parts (PMIX only)
+    V3<R> l1, l2, Tl;  // lo parts (PMIX only)
     R ell;
     int i1, i2;
 };
@@ -247,6 +251,7 @@ __device__ __forceinline__ void load_target(Tgt<typename RealOf<PREC>::type> &t,
         t.i2 = r.i2;
         t.l1 = {0, 0, 0};
         t.l2 = {0, 0, 0};
+        t.Tl = {0, 0, 0};
     } else {
         RecF r = recF[I];
         t.p1 = {r.a.x, r.a.y, r.a.z};
@@ -259,9 +264,11 @@ __device__ __forceinline__ void load_target(Tgt<typename RealOf<PREC>::type> &t,
             RecLo q = recLo[I];
             t.l1 = {q.lo.x, q.lo.y, q.lo.z};
             t.l2 = {q.lo.w, q.lo2.x, q.lo2.y};
+            t.Tl = {q.lo2.z, q.lo2.w, q.lo3.x};
         } else {
             t.l1 = {0.f, 0.f, 0.f};
             t.l2 = {0.f, 0.f, 0.f};
+            t.Tl = {0.f, 0.f, 0.f};
         }
     }
 }
@@ -269,7 +276,7 @@ __device__ __forceinline__ void load_target(Tgt<typename RealOf<PREC>::type> &t,
 template <int PREC>
 struct Src {
     using R = typename RealOf<PREC>::type;
-    V3<R> q1, q2, T, m1, m2;  // m = lo parts
+    V3<R> q1, q2, T, m1, m2, Tm;  // m = lo parts
     R ell;
     int j1, j2;
 };
@@ -298,6 +305,10 @@ __device__ __forceinline__ void load_source(Src<PREC> &s, const Tile<PREC, NEEDU
             float4 l = tl.lo[j].lo, l2 = tl.lo[j].lo2;
             s.m1 = {l.x, l.y, l.z};
             s.m2 = {l.w, l2.x, l2.y};
+            if constexpr (NEEDU) {
+                float l3 = tl.lo[j].lo3.x;
+                s.Tm = {l2.z, l2.w, l3};
+            }
         }
     }
 }
@@ -478,8 +489,18 @@ struct Acc32<PREC, OP_DIFF> {
 template <int PREC>
 struct Acc32<PREC, OP_APPLY> {
     static constexpr int op = OP_APPLY;
-    typename RealOf<PREC>::type A1[3], A2[3];
+    typename RealOf<PREC>::type A1[3], A2[3], C1[3], C2[3];  // C: Kahan compensations
 };
+
+// Kahan-compensated accumulation acc += x (c carries the lost low-order part, to be subtracted).
+template <class R>
+__device__ __forceinline__ void kahan_add(R &acc, R &c, R x)
+{
+    R y = x - c;
+    R t = acc + y;
+    c = (t - acc) - y;
+    acc = t;
+}
 template <int PREC>
 struct Acc32<PREC, OP_DIAG> {
     static constexpr int op = OP_DIAG;
@@ -624,6 +645,11 @@ __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type>
         } else {
             // (du_I - du_J) + (|T_I - T_J|^2 / 2) du_J  and  ub_I - ub_J, differences of double-floats
             V3<R> dT = {t.T.x - s.T.x, t.T.y - s.T.y, t.T.z - s.T.z};
+            if constexpr (PREC == PMIX) {
+                dT.x += t.Tl.x - s.Tm.x;
+                dT.y += t.Tl.y - s.Tm.y;
+                dT.z += t.Tl.z - s.Tm.z;
+            }
             R omt = (R)0.5 * dot3(dT, dT);
             R ddx = (tu->dh.x - su->dh.x), ddy = (tu->dh.y - su->dh.y), ddz = (tu->dh.z - su->dh.z);
             R dbx = (tu->uh.x - su->uh.x), dby = (tu->uh.y - su->uh.y), dbz = (tu->uh.z - su->uh.z);
@@ -635,12 +661,12 @@ __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type>
                 dby += tu->ul.y - su->ul.y;
                 dbz += tu->ul.z - su->ul.z;
             }
-            a.A1[0] += W * (ddx + omt * su->dh.x);
-            a.A1[1] += W * (ddy + omt * su->dh.y);
-            a.A1[2] += W * (ddz + omt * su->dh.z);
-            a.A2[0] += W0 * dbx;
-            a.A2[1] += W0 * dby;
-            a.A2[2] += W0 * dbz;
+            kahan_add(a.A1[0], a.C1[0], W * (ddx + omt * su->dh.x));
+            kahan_add(a.A1[1], a.C1[1], W * (ddy + omt * su->dh.y));
+            kahan_add(a.A1[2], a.C1[2], W * (ddz + omt * su->dh.z));
+            kahan_add(a.A2[0], a.C2[0], W0 * dbx);
+            kahan_add(a.A2[1], a.C2[1], W0 * dby);
+            kahan_add(a.A2[2], a.C2[2], W0 * dbz);
         }
     }
 }
@@ -654,7 +680,7 @@ __device__ __forceinline__ void acc_zero(Acc32<PREC, OP> &a)
         a.S = 0;
         for (int k = 0; k < 3; ++k) a.G1[k] = a.G2[k] = a.GT[k] = 0;
     } else if constexpr (OP == OP_APPLY) {
-        for (int k = 0; k < 3; ++k) a.A1[k] = a.A2[k] = 0;
+        for (int k = 0; k < 3; ++k) a.A1[k] = a.A2[k] = a.C1[k] = a.C2[k] = 0;
     } else {
         a.Sw = a.Sw0 = 0;
     }
@@ -688,9 +714,18 @@ __device__ __forceinline__ void acc_add(X &A, const Y &a)
             A.GT[k] += a.GT[k];
         }
     } else if constexpr (OPX == OP_APPLY) {
-        for (int k = 0; k < 3; ++k) {
-            A.A1[k] += a.A1[k];
-            A.A2[k] += a.A2[k];
+        if constexpr (std::is_same_v<X, Acc64<OP_APPLY>>) {
+            // tile fold into FP64: value minus its compensation
+            for (int k = 0; k < 3; ++k) {
+                A.A1[k] += (double)a.A1[k] - (double)a.C1[k];
+                A.A2[k] += (double)a.A2[k] - (double)a.C2[k];
+            }
+        } else {
+            // one pair's accumulator into the tile accumulator (mixed path), compensated
+            for (int k = 0; k < 3; ++k) {
+                kahan_add(A.A1[k], A.C1[k], a.A1[k] - a.C1[k]);
+                kahan_add(A.A2[k], A.C2[k], a.A2[k] - a.C2[k]);
+            }
         }
     } else {
         A.Sw += a.Sw;
@@ -928,7 +963,7 @@ static void plan_pass(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy)
             vmin[v] = std::min(vmin[v], I);
             vmax[v] = std::max(vmax[v], I);
         }
-    const int target_items = std::max(1, 8 * c.sm_count * std::max(1, occupancy));
+    const int target_items = std::max(1, 3 * c.sm_count * std::max(1, occupancy));
     // total work estimate to size chunks
     double total = 0.0;
     for (int q = 0; q < c.nProb; ++q) {
@@ -949,7 +984,7 @@ static void plan_pass(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy)
         // chunks so that this problem gets its share of the target item count
         double share = total > 0 ? (double)n * n / total : 1.0;
         int want = (int)std::ceil(share * target_items / nblk);
-        int max_chunks = std::max(1, n / kTile);
+        int max_chunks = std::max(1, n / (8 * kTile));  // at least 8 source tiles per item
         int nch = std::min(std::max(1, want), max_chunks);
         nch = std::min(nch, 64);
         int clen = ((n + nch - 1) / nch + kTile - 1) / kTile * kTile;

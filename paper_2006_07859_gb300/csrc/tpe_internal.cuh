@@ -38,7 +38,7 @@ struct alignas(16) RecF {
     float4 a, b, c;
 };
 struct alignas(16) RecLo {
-    float4 lo, lo2;
+    float4 lo, lo2, lo3;  // lo2 = (g_i2.y lo, g_i2.z lo, T.x lo, T.y lo), lo3 = (T.z lo, 0, 0, 0)
 };
 // FP64 edge record (96 B).
 struct alignas(16) RecD {
