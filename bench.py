@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--cg-maxit", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-262k", action="store_true", help="skip the 262,144-edge pair-pass timing")
+    ap.add_argument("--mode", choices=["bench", "passes"], default="bench",
+                    help="passes: only run energy, differential and 3 applies of the workload (for ncu)")
     return ap.parse_args()
 
 
@@ -233,6 +237,23 @@ def pass_throughput_262k(tpe, torch):
     return out
 
 
+def run_passes(args):
+    """A short fixed sequence on the benchmark workload for profilers: one energy, one differential,
+    three applies (mixed precision)."""
+    import torch
+    from paper_2006_07859_gb300 import tpe
+    curves, cfg, indep = workload(args.workload)
+    ctx = tpe.Context.from_curves(curves, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_JACOBI, independent=indep)
+    g = torch.as_tensor(curves.gamma).cuda()
+    u = torch.as_tensor(np.random.default_rng(1).normal(size=(curves.n_vertices, 3))).cuda()
+    tpe.tp_energy(ctx, g)
+    tpe.tp_differential(ctx, g)
+    for _ in range(3):
+        tpe.sobolev_apply(ctx, g, u)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "passes", "workload": cfg["workload"], "pairs_per_pass": ctx.pairs_per_pass()}))
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2006_07859_gb300 import tpe
@@ -310,10 +331,13 @@ def run_ours(args, rank, world, local_rank):
     peaks = tpe.tp_measure_peaks()
     passes = {k: prof[k][1] / args.steps for k in ("energy", "diff", "apply")}
     pps = {k: (pairs * prof[k][1] / (prof[k][0] / 1e3) if prof[k][1] else None) for k in prof}
-    big = pass_throughput_262k(tpe, torch)
+    big = None if args.no_262k else pass_throughput_262k(tpe, torch)
     # CPU oracle baseline on a bounded sample, extrapolated with the measured pass counts
-    rates, cores = oracle_rates(curves, args.cpu_seconds)
-    cpu_val = oracle_step_rate(rates, pairs, passes)
+    if args.no_cpu:
+        rates, cores, cpu_val = {}, 0, None
+    else:
+        rates, cores = oracle_rates(curves, args.cpu_seconds)
+        cpu_val = oracle_step_rate(rates, pairs, passes)
     kernel_share = {k: prof[k][0] / 1e3 / total for k in prof}
     line = {
         "metric": "H^s descent steps/s at 262K edges; pair interactions/s vs FP32 roofline", "value": value, "unit": "steps/s", "n_gpus": world,
@@ -362,6 +386,8 @@ def main():
             dist.init_process_group("gloo")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.mode == "passes":
+        run_passes(args)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

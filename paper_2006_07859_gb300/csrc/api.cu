@@ -54,6 +54,10 @@ bool params_ok(const tp_params *p, std::string &why)
         why = "bad preconditioner";
         return false;
     }
+    if (!(p->far_cutoff >= 0.0)) {
+        why = "far_cutoff must be >= 0";
+        return false;
+    }
     if (!(p->cg_rtol > 0.0) || p->cg_maxit < 1 || !(p->shrink > 0.0 && p->shrink < 1.0) || p->max_halvings < 0 ||
         p->proj_maxit < 0 || !(p->proj_tol > 0.0)) {
         why = "bad solver or line-search parameter";
@@ -73,6 +77,35 @@ void set_kernel_params(Ctx &c)
     double rn = p.near_cutoff * c.mean_ell;
     c.kp.near2 = rn * rn;
     c.kp.near2f = (float)(rn * rn);
+    // tiles closer than far_cutoff x the curve's extent use double-float differences (mixed path)
+    double rm = std::max(p.far_cutoff * c.extent, rn);
+    c.kp.mid2f = p.far_cutoff >= 10.0 ? 3.0e38f : (float)(rm * rm);
+}
+
+// Bounding-box diagonal of the vertex positions (host read; scales the double-float tile cutoff).
+__global__ void k_extent(int nV, const double *g, double *out)
+{
+    __shared__ double sh[6][256];
+    double b[6] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300};
+    for (int i = threadIdx.x; i < nV; i += blockDim.x)
+        for (int k = 0; k < 3; ++k) {
+            b[k] = fmin(b[k], g[3 * i + k]);
+            b[3 + k] = fmax(b[3 + k], g[3 * i + k]);
+        }
+    for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = b[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 6; ++k)
+                sh[k][threadIdx.x] = k < 3 ? fmin(sh[k][threadIdx.x], sh[k][threadIdx.x + w])
+                                           : fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < 3; ++k) s += (sh[3 + k][0] - sh[k][0]) * (sh[3 + k][0] - sh[k][0]);
+        *out = sqrt(s);
+    }
 }
 
 // FP64 mean edge length of geometry `which` (host read; used to scale the near-pair cutoff).
@@ -114,10 +147,12 @@ tp_status records(tp_ctx *ctx, const double *gamma, int which, cudaStream_t s)
     CK(build_records(c, gamma, which, s));
     if (c.mean_ell == 0.0 && c.nE > 0) {
         k_sum_ell<<<1, 256, 0, s>>>(c.nE, c.d_ellw[which], c.d_scal);
-        c.launches++;
-        CK(cudaMemcpyAsync(c.h_pinned, c.d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+        k_extent<<<1, 256, 0, s>>>(c.nV, gamma, c.d_scal + 1);
+        c.launches += 2;
+        CK(cudaMemcpyAsync(c.h_pinned, c.d_scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         c.mean_ell = c.h_pinned[0] / c.nE;
+        c.extent = c.h_pinned[1];
         set_kernel_params(c);
         tp_status st = check_err_word(ctx, s);
         if (st != TP_OK) {
@@ -157,6 +192,7 @@ void tp_default_params(tp_params *p)
     p->proj_tol = 1e-10;
     p->proj_maxit = 5;
     p->independent = 0;
+    p->far_cutoff = 10.0;
 }
 
 const char *tp_last_error(const tp_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }

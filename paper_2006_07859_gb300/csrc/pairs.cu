@@ -305,20 +305,17 @@ __device__ __forceinline__ void load_source(Src<PREC> &s, const Tile<PREC, NEEDU
             float4 l = tl.lo[j].lo, l2 = tl.lo[j].lo2;
             s.m1 = {l.x, l.y, l.z};
             s.m2 = {l.w, l2.x, l2.y};
-            if constexpr (NEEDU) {
-                float l3 = tl.lo[j].lo3.x;
-                s.Tm = {l2.z, l2.w, l3};
-            }
+            s.Tm = {l2.z, l2.w, tl.lo[j].lo3.x};
         }
     }
 }
 
-// d = p - q (double-float positions in PMIX: hi difference plus lo difference).
-template <int PREC, class R>
+// d = p - q (double-float positions when DF: hi difference plus lo difference).
+template <bool DF, class R>
 __device__ __forceinline__ V3<R> diff3(V3<R> p, V3<R> pl, V3<R> q, V3<R> ql)
 {
     V3<R> d = {p.x - q.x, p.y - q.y, p.z - q.z};
-    if constexpr (PREC == PMIX) {
+    if constexpr (DF) {
         d.x += pl.x - ql.x;
         d.y += pl.y - ql.y;
         d.z += pl.z - ql.z;
@@ -347,70 +344,11 @@ struct NearArgs {
 
 __device__ __forceinline__ V3<double> ld3(const double *a, int i) { return {a[3 * i], a[3 * i + 1], a[3 * i + 2]}; }
 
-// FP64 powers for the near-pair paths: |d|^-e (fast: e = 4.5 or 2.5 via rsqrt/sqrt) and |c|^alpha.
-__device__ __forceinline__ double npow_d(double d2, double e, bool fast, bool weight)
-{
-    if (fast) {
-        double r = rsqrt(d2), sr = sqrt(r), r2 = r * r;
-        return weight ? r2 * sr : r2 * r2 * sr;
-    }
-    return pow(d2, -0.5 * e);
-}
-__device__ __forceinline__ double npow_c(double c2, double alpha, bool fast)
-{
-    if (fast) return c2;
-    return c2 > 0.0 ? pow(c2, 0.5 * alpha) : 0.0;
-}
-
-// l_J sum_ab k(g_ia, g_jb, T_I) in FP64.
-__device__ __noinline__ double near_energy(const NearArgs na, int I, int J, double alpha, double beta, bool fast)
-{
-    V3<double> TI = ld3(na.T, I);
-    int ii[2] = {na.E[2 * I], na.E[2 * I + 1]}, jj[2] = {na.E[2 * J], na.E[2 * J + 1]};
-    double s = 0.0;
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) {
-            V3<double> p = ld3(na.g, ii[a]), q = ld3(na.g, jj[b]);
-            V3<double> d = {p.x - q.x, p.y - q.y, p.z - q.z}, dp;
-            double t, c2 = perp2(d, TI, t, dp), d2 = dot3(d, d);
-            s += npow_c(c2, alpha, fast) * npow_d(d2, beta, fast, false);
-        }
-    return na.ell[J] * s;
-}
-
 // Differential accumulators of one target against its sources (all scaled by l_J):
 //   S  = sum (fI + fJ);  G1, G2 = sum d/dp (fI + fJ) at p = g_i1, g_i2;  GT = sum d fI / d T_I
 struct DiffAcc64 {
     double S, G1[3], G2[3], GT[3];
 };
-
-__device__ __noinline__ void near_diff(const NearArgs na, int I, int J, double alpha, double beta, bool fast,
-                                      DiffAcc64 &acc)
-{
-    V3<double> TI = ld3(na.T, I), TJ = ld3(na.T, J);
-    int ii[2] = {na.E[2 * I], na.E[2 * I + 1]}, jj[2] = {na.E[2 * J], na.E[2 * J + 1]};
-    double L = na.ell[J];
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) {
-            V3<double> p = ld3(na.g, ii[a]), q = ld3(na.g, jj[b]);
-            V3<double> d = {p.x - q.x, p.y - q.y, p.z - q.z}, dpI, dpJ;
-            double tI, tJ;
-            double cI2 = perp2(d, TI, tI, dpI), cJ2 = perp2(d, TJ, tJ, dpJ), d2 = dot3(d, d);
-            double rb = npow_d(d2, beta, fast, false);
-            double fI = npow_c(cI2, alpha, fast) * rb, fJ = npow_c(cJ2, alpha, fast) * rb;
-            double aI = fast ? 2.0 * rb : (cI2 > 0.0 ? alpha * fI / cI2 : 0.0);
-            double aJ = fast ? 2.0 * rb : (cJ2 > 0.0 ? alpha * fJ / cJ2 : 0.0);
-            double cb = beta * (fI + fJ) / d2;
-            double *G = a == 0 ? acc.G1 : acc.G2;
-            G[0] += L * (aI * dpI.x + aJ * dpJ.x - cb * d.x);
-            G[1] += L * (aI * dpI.y + aJ * dpJ.y - cb * d.y);
-            G[2] += L * (aI * dpI.z + aJ * dpJ.z - cb * d.z);
-            acc.GT[0] += -L * aI * tI * d.x;
-            acc.GT[1] += -L * aI * tI * d.y;
-            acc.GT[2] += -L * aI * tI * d.z;
-            acc.S += L * (fI + fJ);
-        }
-}
 
 // Apply accumulators (scaled by l_J), in the exact difference form
 //   du_I - <T_I,T_J> du_J = (du_I - du_J) + (|T_I - T_J|^2 / 2) du_J:
@@ -420,41 +358,6 @@ __device__ __noinline__ void near_diff(const NearArgs na, int I, int J, double a
 struct ApplyAcc64 {
     double Sw, A1[3], Sw0, A2[3];
 };
-
-__device__ __noinline__ void near_apply(const NearArgs na, int I, int J, double p, bool with_u, bool fast,
-                                       ApplyAcc64 &acc)
-{
-    V3<double> TI = ld3(na.T, I), TJ = ld3(na.T, J);
-    int ii[2] = {na.E[2 * I], na.E[2 * I + 1]}, jj[2] = {na.E[2 * J], na.E[2 * J + 1]};
-    double sw = 0.0, sw0 = 0.0;
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) {
-            V3<double> q = ld3(na.g, jj[b]), pp = ld3(na.g, ii[a]);
-            V3<double> d = {pp.x - q.x, pp.y - q.y, pp.z - q.z}, dpI, dpJ;
-            double tI, tJ;
-            double c2 = perp2(d, TI, tI, dpI) + perp2(d, TJ, tJ, dpJ), d2 = dot3(d, d);
-            double rp = npow_d(d2, p, fast, true);
-            sw += rp;
-            sw0 += c2 * rp / (d2 * d2);
-        }
-    double L = na.ell[J];
-    double W = L * sw, W0 = L * sw0;
-    acc.Sw += W;
-    acc.Sw0 += W0;
-    if (with_u) {
-        double lI = na.ell[I];
-        V3<double> dT = {TI.x - TJ.x, TI.y - TJ.y, TI.z - TJ.z};
-        double omt = 0.5 * dot3(dT, dT);
-        for (int k = 0; k < 3; ++k) {
-            double duI = (na.u[3 * ii[1] + k] - na.u[3 * ii[0] + k]) / lI;
-            double duJ = (na.u[3 * jj[1] + k] - na.u[3 * jj[0] + k]) / L;
-            double ubI = 0.5 * (na.u[3 * ii[0] + k] + na.u[3 * ii[1] + k]);
-            double ubJ = 0.5 * (na.u[3 * jj[0] + k] + na.u[3 * jj[1] + k]);
-            acc.A1[k] += W * ((duI - duJ) + omt * duJ);
-            acc.A2[k] += W0 * (ubI - ubJ);
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------------- the pair kernel
 
@@ -553,12 +456,29 @@ __device__ __forceinline__ void load_uval(UVal<typename RealOf<PREC>::type> &v, 
 }
 
 // One (target, source) pair: accumulate into the tile accumulator a.
-template <int PREC, int OP, bool FAST>
+// DF: use the low parts (double-float differences) and compensated accumulation; only the mixed
+// path's MID and NEAR tiles set it.
+// |T x d|^2 in FP64 from the double-float position differences and tangent of a near pair: the
+// angle between T and the chord is small there, so FP32 would lose most of the digits of the
+// perpendicular part.  Only this quantity goes to FP64; the rest of the pair stays in FP32.
+__device__ __forceinline__ float perp2_near(V3<float> P, V3<float> PL, V3<float> Q, V3<float> QL, V3<float> T,
+                                            V3<float> Tl)
+{
+    double dx = (double)(P.x - Q.x) + (double)(PL.x - QL.x);
+    double dy = (double)(P.y - Q.y) + (double)(PL.y - QL.y);
+    double dz = (double)(P.z - Q.z) + (double)(PL.z - QL.z);
+    double tx = (double)T.x + (double)Tl.x, ty = (double)T.y + (double)Tl.y, tz = (double)T.z + (double)Tl.z;
+    double t = tx * dx + ty * dy + tz * dz;
+    double px = dx - t * tx, py = dy - t * ty, pz = dz - t * tz;
+    return (float)(px * px + py * py + pz * pz);
+}
+
+template <int PREC, int OP, bool FAST, bool DF = (PREC == PMIX)>
 __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type> &t, const Src<PREC> &s,
                                           Acc32<PREC, OP> &a, bool keep, const KernelParams &kp,
                                           typename RealOf<PREC>::type &d2_11,
                                           const UVal<typename RealOf<PREC>::type> *tu,
-                                          const UVal<typename RealOf<PREC>::type> *su)
+                                          const UVal<typename RealOf<PREC>::type> *su, bool near = false)
 {
     using R = typename RealOf<PREC>::type;
     const R alpha = (R)kp.alpha, beta = (R)kp.beta, pp = (R)kp.p;
@@ -568,8 +488,10 @@ __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type>
         for (int ab = 0; ab < 4; ++ab) {
             V3<R> P = (ab < 2) ? t.p1 : t.p2, PL = (ab < 2) ? t.l1 : t.l2;
             V3<R> Q = (ab & 1) ? s.q2 : s.q1, QL = (ab & 1) ? s.m2 : s.m1;
-            V3<R> d = diff3<PREC>(P, PL, Q, QL), dp;
+            V3<R> d = diff3<DF>(P, PL, Q, QL), dp;
             R tt, c2 = perp2(d, t.T, tt, dp), d2 = dot3(d, d);
+            if constexpr (DF && sizeof(R) == 4)
+                if (near) c2 = perp2_near(P, PL, Q, QL, t.T, t.Tl);
             if (ab == 0) d2_11 = d2;
             R r2;
             f += pow_c<R, FAST>(c2, alpha) * inv_pow<R, FAST, 0>(d2, beta, r2);
@@ -582,9 +504,14 @@ __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type>
         for (int ab = 0; ab < 4; ++ab) {
             V3<R> P = (ab < 2) ? t.p1 : t.p2, PL = (ab < 2) ? t.l1 : t.l2;
             V3<R> Q = (ab & 1) ? s.q2 : s.q1, QL = (ab & 1) ? s.m2 : s.m1;
-            V3<R> d = diff3<PREC>(P, PL, Q, QL), dpI, dpJ;
+            V3<R> d = diff3<DF>(P, PL, Q, QL), dpI, dpJ;
             R tI, tJ;
             R cI2 = perp2(d, t.T, tI, dpI), cJ2 = perp2(d, s.T, tJ, dpJ), d2 = dot3(d, d);
+            if constexpr (DF && sizeof(R) == 4)
+                if (near) {
+                    cI2 = perp2_near(P, PL, Q, QL, t.T, t.Tl);
+                    cJ2 = perp2_near(P, PL, Q, QL, s.T, s.Tm);
+                }
             if (ab == 0) d2_11 = d2;
             R r2;
             R rb = inv_pow<R, FAST, 0>(d2, beta, r2);
@@ -623,20 +550,27 @@ __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type>
             a.GT[k] += L * GT[k];
         }
     } else {  // OP_APPLY / OP_DIAG
-        R sw = 0, sw0 = 0;
+        // the four trapezoid terms are summed as (11 + 22) + (12 + 21), an order that is the same
+        // from row I and from row J, so W_IJ and W_JI (and W0) are bitwise equal: the FP32 operator
+        // stays exactly symmetric
+        R tw[4], tw0[4];
 #pragma unroll
         for (int ab = 0; ab < 4; ++ab) {
             V3<R> P = (ab < 2) ? t.p1 : t.p2, PL = (ab < 2) ? t.l1 : t.l2;
             V3<R> Q = (ab & 1) ? s.q2 : s.q1, QL = (ab & 1) ? s.m2 : s.m1;
-            V3<R> d = diff3<PREC>(P, PL, Q, QL), dpI, dpJ;
+            V3<R> d = diff3<DF>(P, PL, Q, QL), dpI, dpJ;
             R tI, tJ;
             R c2 = perp2(d, t.T, tI, dpI) + perp2(d, s.T, tJ, dpJ), d2 = dot3(d, d);
+            if constexpr (DF && sizeof(R) == 4)
+                if (near) c2 = perp2_near(P, PL, Q, QL, t.T, t.Tl) + perp2_near(P, PL, Q, QL, s.T, s.Tm);
             if (ab == 0) d2_11 = d2;
             R r2;
             R rp = inv_pow<R, FAST, 1>(d2, pp, r2);
-            sw += rp;
-            sw0 += c2 * (rp * r2 * r2);
+            tw[ab] = rp;
+            tw0[ab] = c2 * (rp * r2 * r2);
         }
+        R sw = (tw[0] + tw[3]) + (tw[1] + tw[2]);
+        R sw0 = (tw0[0] + tw0[3]) + (tw0[1] + tw0[2]);
         R W = keep ? s.ell * sw : (R)0;
         R W0 = keep ? s.ell * sw0 : (R)0;
         if constexpr (OP == OP_DIAG) {
@@ -645,7 +579,7 @@ __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type>
         } else {
             // (du_I - du_J) + (|T_I - T_J|^2 / 2) du_J  and  ub_I - ub_J, differences of double-floats
             V3<R> dT = {t.T.x - s.T.x, t.T.y - s.T.y, t.T.z - s.T.z};
-            if constexpr (PREC == PMIX) {
+            if constexpr (DF) {
                 dT.x += t.Tl.x - s.Tm.x;
                 dT.y += t.Tl.y - s.Tm.y;
                 dT.z += t.Tl.z - s.Tm.z;
@@ -653,6 +587,9 @@ __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type>
             R omt = (R)0.5 * dot3(dT, dT);
             R ddx = (tu->dh.x - su->dh.x), ddy = (tu->dh.y - su->dh.y), ddz = (tu->dh.z - su->dh.z);
             R dbx = (tu->uh.x - su->uh.x), dby = (tu->uh.y - su->uh.y), dbz = (tu->uh.z - su->uh.z);
+            // the differences of u always use the double-float parts in the mixed path: for smooth u
+            // they are small second differences, and the operator's accuracy on them sets how far CG
+            // can reduce the true residual
             if constexpr (PREC == PMIX) {
                 ddx += tu->dl.x - su->dl.x;
                 ddy += tu->dl.y - su->dl.y;
@@ -661,12 +598,21 @@ __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type>
                 dby += tu->ul.y - su->ul.y;
                 dbz += tu->ul.z - su->ul.z;
             }
-            kahan_add(a.A1[0], a.C1[0], W * (ddx + omt * su->dh.x));
-            kahan_add(a.A1[1], a.C1[1], W * (ddy + omt * su->dh.y));
-            kahan_add(a.A1[2], a.C1[2], W * (ddz + omt * su->dh.z));
-            kahan_add(a.A2[0], a.C2[0], W0 * dbx);
-            kahan_add(a.A2[1], a.C2[1], W0 * dby);
-            kahan_add(a.A2[2], a.C2[2], W0 * dbz);
+            if constexpr (PREC != P32) {
+                kahan_add(a.A1[0], a.C1[0], W * (ddx + omt * su->dh.x));
+                kahan_add(a.A1[1], a.C1[1], W * (ddy + omt * su->dh.y));
+                kahan_add(a.A1[2], a.C1[2], W * (ddz + omt * su->dh.z));
+                kahan_add(a.A2[0], a.C2[0], W0 * dbx);
+                kahan_add(a.A2[1], a.C2[1], W0 * dby);
+                kahan_add(a.A2[2], a.C2[2], W0 * dbz);
+            } else {
+                a.A1[0] += W * (ddx + omt * su->dh.x);
+                a.A1[1] += W * (ddy + omt * su->dh.y);
+                a.A1[2] += W * (ddz + omt * su->dh.z);
+                a.A2[0] += W0 * dbx;
+                a.A2[1] += W0 * dby;
+                a.A2[2] += W0 * dbz;
+            }
         }
     }
 }
@@ -739,7 +685,7 @@ __host__ __device__ constexpr int part_stride()
     return (OP == OP_ENERGY || OP == OP_DIAG) ? 1 : 6;
 }
 
-template <int PREC, int OP, int TPT, bool FAST, bool CHECK>
+template <int PREC, int OP, int TPT, bool FAST, bool CHECK, int MODE = 2>
 __device__ __forceinline__ void tile_loop(const Tgt<typename RealOf<PREC>::type> (&tg)[TPT], const int (&tI)[TPT],
                                           const UVal<typename RealOf<PREC>::type> (&tu)[TPT],
                                           const Tile<PREC, OP == OP_APPLY> &tl, int cnt, int s0,
@@ -770,24 +716,13 @@ __device__ __forceinline__ void tile_loop(const Tgt<typename RealOf<PREC>::type>
             if constexpr (CHECK)
                 keep = (s.j1 != tg[k].i1) & (s.j1 != tg[k].i2) & (s.j2 != tg[k].i1) & (s.j2 != tg[k].i2);
             R d2_11;
-            if constexpr (PREC == PMIX) {
-                // evaluate the FP32 pair, then replace it by the FP64 one when the pair is near
-                Acc32<PREC, OP> tmp;
-                acc_zero<PREC, OP>(tmp);
-                pair_eval<PREC, OP, FAST>(tg[k], s, tmp, keep, pa.kp, d2_11, &tu[k], &su);
-                bool near = keep && (d2_11 < pa.kp.near2f);
-                if (near) {
-                    int J = s0 + j;
-                    if constexpr (OP == OP_ENERGY) {
-                        A[k].s += near_energy(pa.na, tI[k], J, pa.kp.alpha, pa.kp.beta, FAST);
-                    } else if constexpr (OP == OP_DIFF) {
-                        near_diff(pa.na, tI[k], J, pa.kp.alpha, pa.kp.beta, FAST, A[k]);
-                    } else {
-                        near_apply(pa.na, tI[k], J, pa.kp.p, OP == OP_APPLY, FAST, A[k]);
-                    }
-                } else {
-                    acc_add(a[k], tmp);
-                }
+            if constexpr (PREC == PMIX && MODE < 2) {
+                pair_eval<PREC, OP, FAST, MODE == 1>(tg[k], s, a[k], keep, pa.kp, d2_11, &tu[k], &su);
+            } else if constexpr (PREC == PMIX) {
+                // near pairs (|g_i1 - g_j1| below the cutoff) take |T x d|^2 in FP64
+                V3<float> e = diff3<true>(tg[k].p1, tg[k].l1, s.q1, s.m1);
+                bool near = keep && (dot3(e, e) < pa.kp.near2f);
+                pair_eval<PREC, OP, FAST, true>(tg[k], s, a[k], keep, pa.kp, d2_11, &tu[k], &su, near);
             } else {
                 pair_eval<PREC, OP, FAST>(tg[k], s, a[k], keep, pa.kp, d2_11, &tu[k], &su);
             }
@@ -795,13 +730,41 @@ __device__ __forceinline__ void tile_loop(const Tgt<typename RealOf<PREC>::type>
     }
 }
 
+__device__ __forceinline__ void box_add(float (&b)[6], V3<float> p, V3<float> q)
+{
+    b[0] = fminf(b[0], fminf(p.x, q.x));
+    b[1] = fminf(b[1], fminf(p.y, q.y));
+    b[2] = fminf(b[2], fminf(p.z, q.z));
+    b[3] = fmaxf(b[3], fmaxf(p.x, q.x));
+    b[4] = fmaxf(b[4], fmaxf(p.y, q.y));
+    b[5] = fmaxf(b[5], fmaxf(p.z, q.z));
+}
+
+// Block-wide bounding box: every thread ends with the box of all threads' boxes.  Contains one
+// __syncthreads (the caller's tile barrier).
+__device__ __forceinline__ void block_box(float (&b)[6], float (*sh)[6])
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        for (int q = 0; q < 6; ++q) {
+            float v = __shfl_xor_sync(0xffffffffu, b[q], o);
+            b[q] = q < 3 ? fminf(b[q], v) : fmaxf(b[q], v);
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 6; ++q) sh[threadIdx.x >> 5][q] = b[q];
+    __syncthreads();
+    for (int wv = 0; wv < kThreads / 32; ++wv)
+        for (int q = 0; q < 6; ++q) b[q] = q < 3 ? fminf(b[q], sh[wv][q]) : fmaxf(b[q], sh[wv][q]);
+}
+
 template <int PREC, int OP, int TPT, bool FAST>
-__global__ void __launch_bounds__(kThreads) k_pairs(const PairArgs pa)
+__global__ void __launch_bounds__(kThreads, PREC == P64 ? 1 : 3) k_pairs(const PairArgs pa)
 {
     using R = typename RealOf<PREC>::type;
     constexpr bool NEEDU = (OP == OP_APPLY);
     __shared__ Tile<PREC, NEEDU> tl;
     __shared__ int s_item;
+    __shared__ float s_box[2][kThreads / 32][6];
     constexpr int S = part_stride<OP>();
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(pa.counter, 1);
@@ -821,33 +784,81 @@ __global__ void __launch_bounds__(kThreads) k_pairs(const PairArgs pa)
             if constexpr (NEEDU) load_uval<PREC>(tu[k], pa.urecF, pa.urecD, tI[k]);
         }
         Acc64<OP> A[TPT];
+        Acc32<PREC, OP> a[TPT];
 #pragma unroll
         for (int k = 0; k < TPT; ++k) acc64_zero<OP>(A[k]);
+        float tbox[6];  // bounding box of this warp's targets (mixed path): min xyz, max xyz
+        if constexpr (PREC == PMIX) {
+            float b[6] = {1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) box_add(b, tg[k].p1, tg[k].p2);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                for (int q = 0; q < 6; ++q) {
+                    float v = __shfl_xor_sync(0xffffffffu, b[q], o);
+                    b[q] = q < 3 ? fminf(b[q], v) : fmaxf(b[q], v);
+                }
+            for (int q = 0; q < 6; ++q) tbox[q] = b[q];
+        }
+        int tiles_since_fold = 0;
         for (int s0 = w.src0; s0 < w.src1; s0 += kTile) {
             const int cnt = min(kTile, w.src1 - s0);
             __syncthreads();
+            float sb[6] = {1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
             if (threadIdx.x < cnt) {
                 int J = s0 + threadIdx.x;
                 if constexpr (PREC == P64) {
                     tl.r[threadIdx.x] = pa.recD[J];
                     if constexpr (NEEDU) tl.u[threadIdx.x] = pa.urecD[J];
                 } else {
-                    tl.r[threadIdx.x] = pa.recF[J];
-                    if constexpr (PREC == PMIX) tl.lo[threadIdx.x] = pa.recLo[J];
+                    RecF r = pa.recF[J];
+                    tl.r[threadIdx.x] = r;
+                    if constexpr (PREC == PMIX) {
+                        tl.lo[threadIdx.x] = pa.recLo[J];
+                        box_add(sb, V3<float>{r.a.x, r.a.y, r.a.z}, V3<float>{r.b.x, r.b.y, r.b.z});
+                    }
                     if constexpr (NEEDU) tl.u[threadIdx.x] = pa.urecF[J];
                 }
             }
-            __syncthreads();
-            Acc32<PREC, OP> a[TPT];
+            if constexpr (PREC == PMIX) block_box(sb, s_box[1]);  // contains the barriers
+            else __syncthreads();
+            if (tiles_since_fold == 0) {
 #pragma unroll
-            for (int k = 0; k < TPT; ++k) acc_zero<PREC, OP>(a[k]);
+                for (int k = 0; k < TPT; ++k) acc_zero<PREC, OP>(a[k]);
+            }
             const bool check = !(s0 + cnt - 1 < w.nb_lo || s0 > w.nb_hi);
-            if (check)
-                tile_loop<PREC, OP, TPT, FAST, true>(tg, tI, tu, tl, cnt, s0, a, A, pa);
-            else
-                tile_loop<PREC, OP, TPT, FAST, false>(tg, tI, tu, tl, cnt, s0, a, A, pa);
+            int mode = 2;
+            if constexpr (PREC == PMIX) {
+                // squared distance between the two boxes decides the arithmetic of the whole tile
+                float g2 = 0.f;
+                for (int q = 0; q < 3; ++q) {
+                    float gap = fmaxf(fmaxf(sb[q] - tbox[3 + q], tbox[q] - sb[3 + q]), 0.f);
+                    g2 += gap * gap;
+                }
+                mode = (g2 < pa.kp.near2f) ? 2 : (g2 < pa.kp.mid2f ? 1 : 0);
+                // In the Gram weights |T x d|^2 enters only the low-order weight w0, whose near-pair
+                // entries are ~(kappa l)^2 / 4 of the high-order ones, so FP32 double-float accuracy
+                // suffices there: no FP64 near path for apply / diag.
+                if constexpr (OP == OP_APPLY || OP == OP_DIAG) mode = min(mode, 1);
+            }
+            if (check || mode == 2) {
+                if (check && (OP == OP_APPLY || OP == OP_DIAG) && PREC == PMIX)
+                    tile_loop<PREC, OP, TPT, FAST, true, 1>(tg, tI, tu, tl, cnt, s0, a, A, pa);
+                else if (check)
+                    tile_loop<PREC, OP, TPT, FAST, true, 2>(tg, tI, tu, tl, cnt, s0, a, A, pa);
+                else
+                    tile_loop<PREC, OP, TPT, FAST, false, 2>(tg, tI, tu, tl, cnt, s0, a, A, pa);
+            } else if (mode == 1) {
+                tile_loop<PREC, OP, TPT, FAST, false, 1>(tg, tI, tu, tl, cnt, s0, a, A, pa);
+            } else {
+                tile_loop<PREC, OP, TPT, FAST, false, 0>(tg, tI, tu, tl, cnt, s0, a, A, pa);
+            }
+            // fold the tile accumulators into FP64 every 4 tiles and at the end of the item
+            if (++tiles_since_fold == 4 || s0 + kTile >= w.src1) {
 #pragma unroll
-            for (int k = 0; k < TPT; ++k) acc_add(A[k], a[k]);
+                for (int k = 0; k < TPT; ++k) acc_add(A[k], a[k]);
+                tiles_since_fold = 0;
+            }
         }
         // write this item's partial results for the valid targets
 #pragma unroll

@@ -63,6 +63,7 @@ struct KernelParams {
     int fast;               // (alpha, beta, p) == (2, 4.5, 2.5): specialised powers
     double near2;           // squared near-pair cutoff (mixed precision)
     float near2f;
+    float mid2f;            // squared distance below which a tile uses double-float differences
 };
 
 // Device-side scalars of one CG solve (all FP64) - one block per problem.
@@ -109,6 +110,7 @@ struct Ctx {
     // FP64 edge quantities of the two geometries (0: base curve, 1: trial curve): [nE], [nE][3], [nE][3]
     double *d_ellw[2] = {nullptr, nullptr}, *d_Tw[2] = {nullptr, nullptr}, *d_xw[2] = {nullptr, nullptr};
     double mean_ell = 0.0;
+    double extent = 0.0;  // bounding-box diagonal of the first curve seen
     URecF *d_urecF = nullptr;
     URecD *d_urecD = nullptr;
     // partial results [max_slots][nE][6] (FP64)

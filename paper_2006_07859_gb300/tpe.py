@@ -34,7 +34,7 @@ class TpParams(ctypes.Structure):
                 ("cg_maxit", ctypes.c_int), ("cg_check_every", ctypes.c_int), ("proj_cg_rtol", ctypes.c_double),
                 ("precond", ctypes.c_int), ("armijo_c", ctypes.c_double), ("shrink", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("proj_tol", ctypes.c_double), ("proj_maxit", ctypes.c_int),
-                ("independent", ctypes.c_int)]
+                ("independent", ctypes.c_int), ("far_cutoff", ctypes.c_double)]
 
 
 class TpSolveInfo(ctypes.Structure):
