@@ -54,8 +54,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-262k", action="store_true", help="skip the 262,144-edge pair-pass timing")
-    ap.add_argument("--mode", choices=["bench", "passes"], default="bench",
-                    help="passes: only run energy, differential and 3 applies of the workload (for ncu)")
+    ap.add_argument("--mode", choices=["bench", "passes", "precision", "batch"], default="bench",
+                    help="passes: energy, differential and 3 applies of the workload (for ncu); "
+                         "precision: per-result error of the 262,144-edge passes against the FP64 oracle on "
+                         "a sample; batch: 1,024 independent knots of log-uniform size")
+    ap.add_argument("--rows", type=int, default=1024, help="precision mode: sampled rows / vertices")
+    ap.add_argument("--with-fp64", action="store_true", help="precision mode: also run the FP64 GPU passes")
     return ap.parse_args()
 
 
@@ -254,6 +258,85 @@ def run_passes(args):
     print(json.dumps({"mode": "passes", "workload": cfg["workload"], "pairs_per_pass": ctx.pairs_per_pass()}))
 
 
+def run_precision(args):
+    """Config 3: one 262,144-edge knot (K = 16, seed 100).  Energy rows, differential and apply of the
+    GPU passes in FP32, mixed (and optionally FP64) against the FP64 oracle on `rows` sampled target
+    edges / vertices (seed 101)."""
+    import torch
+    import synth as S
+    from oracle import oracle as O
+    from paper_2006_07859_gb300 import tpe
+    c = S.knot_262144()
+    g = torch.as_tensor(c.gamma).cuda()
+    rng = np.random.default_rng(101)
+    rows_idx = np.sort(rng.choice(c.n_edges, size=args.rows, replace=False)).astype(np.int32)
+    v_idx = np.sort(rng.choice(c.n_vertices, size=max(16, args.rows // 4), replace=False)).astype(np.int32)
+    u = np.random.default_rng(102).normal(size=(c.n_vertices, 3))
+    t0 = time.perf_counter()
+    ref_rows = O.energy_rows(c.gamma, c.edges, rows_idx)
+    ref_dE = O.differential_at(c.gamma, c.edges, v_idx)
+    ref_Au = O.gram_apply_at(c.gamma, c.edges, O.sigma_of(2.0, 4.5), u, v_idx)
+    t_oracle = time.perf_counter() - t0
+    out = {"mode": "precision", "workload": "fourier_knot_K16_n262144_seed100", "rows": int(len(rows_idx)),
+           "vertices": int(len(v_idx)), "oracle_seconds": t_oracle, "oracle_cores": O.num_threads(), "results": {}}
+    precs = [("fp32", tpe.TP_FP32), ("mixed", tpe.TP_MIXED)] + ([("fp64", tpe.TP_FP64)] if args.with_fp64 else [])
+
+    def err(a, b):
+        a, b = np.asarray(a), np.asarray(b)
+        r = np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+        return {"max_rel": float(r.max()), "median_rel": float(np.median(r)),
+                "max_rel_of_max": float(np.abs(a - b).max() / np.abs(b).max())}
+
+    for name, prec in precs:
+        ctx = tpe.Context.from_curves(c, precision=prec, precond=tpe.TP_PRECOND_JACOBI)
+        rows = torch.empty(c.n_edges, dtype=torch.float64, device="cuda")
+        t1 = time.perf_counter()
+        E = tpe.tp_energy(ctx, g, rows=rows).cpu().numpy()[0]
+        dE = tpe.tp_differential(ctx, g).cpu().numpy()
+        Au = tpe.sobolev_apply(ctx, g, torch.as_tensor(u).cuda()).cpu().numpy()
+        torch.cuda.synchronize()
+        out["results"][name] = {"energy_total": float(E), "seconds": time.perf_counter() - t1,
+                                "energy_rows": err(rows.cpu().numpy()[rows_idx], ref_rows),
+                                "differential": err(dE[v_idx], ref_dE), "apply": err(Au[v_idx], ref_Au)}
+        ctx.close()
+    print(json.dumps(out), flush=True)
+
+
+def run_batch(args):
+    """Config 4: 1,024 independent closed Fourier knots (K = 8) with n log-uniform in [64, 4096]
+    (seed 1000), all in one persistent launch per pass; energy, differential and one descent step."""
+    import torch
+    import synth as S
+    from paper_2006_07859_gb300 import tpe
+    sizes = S.batch_sizes(1024, 64, 4096, 1000)
+    b = S.batch_of_knots(sizes, 8, 1000)
+    ctx = tpe.Context.from_curves(b, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_SPECTRAL, independent=1,
+                                  cg_rtol=1e-6, cg_maxit=2000, proj_cg_rtol=1e-3)
+    g = torch.as_tensor(b.gamma).cuda()
+    pairs = ctx.pairs_per_pass()
+    tpe.tp_energy(ctx, g)
+    torch.cuda.synchronize()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    res = {"mode": "batch", "workload": "1024_fourier_knots_K8_n_loguniform_64_4096_seed1000",
+           "n_vertices": int(b.n_vertices), "pairs_per_pass": pairs}
+    for name, fn in (("energy", lambda: tpe.tp_energy(ctx, g)), ("diff", lambda: tpe.tp_differential(ctx, g))):
+        a, z = ev(), ev()
+        a.record()
+        for _ in range(3):
+            fn()
+        z.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(z) / 3 / 1e3
+        res[name] = {"ms": t * 1e3, "pairs_per_s": pairs / t}
+    a, z = ev(), ev()
+    a.record()
+    info = tpe.descent_step(ctx, g, allow=(tpe.TP_ERR_NOT_CONVERGED, tpe.TP_ERR_LINESEARCH))
+    z.record()
+    torch.cuda.synchronize()
+    res["descent_step"] = dict(info, seconds=a.elapsed_time(z) / 1e3)
+    print(json.dumps(res), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2006_07859_gb300 import tpe
@@ -388,6 +471,10 @@ def main():
         run_reference(args, rank, world)
     elif args.mode == "passes":
         run_passes(args)
+    elif args.mode == "precision":
+        run_precision(args)
+    elif args.mode == "batch":
+        run_batch(args)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -191,6 +191,24 @@ TPE_API int64_t tp_pairs_per_pass(const tp_ctx *ctx);
 TPE_API tp_status tp_profile(tp_ctx *ctx, int enable);
 TPE_API tp_status tp_profile_read(tp_ctx *ctx, int op, double *total_ms, int64_t *launches);
 
+/* Discrete energy (Eq. 17) of one curve network without any device allocation, for callers that
+ * cannot call cudaMalloc (inside a region where allocation is forbidden, or with all free memory
+ * handed to their own pool).  The paper has no counterpart: this is a variant of tp_energy's mixed
+ * precision pair pass whose scratch (edge records, work items, partial sums; about 20 MB) lives in
+ * fixed-size file-scope __device__ arrays that every GPU which loads the library keeps until exit.
+ *   gamma  DEVICE double [n_vertices][3];  edges DEVICE int32 [n_edges][2] with indices in
+ *          [0, n_vertices) (not checked: they are device data);  E DEVICE double [1].
+ *   n_edges <= 65536, else TP_ERR_INVALID_ARG (the scratch has a fixed size).
+ *   All pairs of disjoint edges of the whole graph form one problem (as independent = 0).
+ * The first call on a device looks up the arrays' device addresses (cudaGetSymbolAddress); make
+ * it before any stream capture.  Every call synchronises `stream` once (to read the edge-length
+ * statistics that set the near-pair cutoff) and then enqueues the pair pass.  All calls share the
+ * same scratch and it keeps the last call's contents: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Errors: TP_ERR_INVALID_ARG, TP_ERR_DEGENERATE_EDGE, TP_ERR_NONFINITE, TP_ERR_CUDA. */
+TPE_API tp_status tp_energy_static(const double *gamma, const int32_t *edges, int n_vertices, int n_edges,
+                                   double alpha, double beta, double *E, tp_stream stream);
+
 /* Throughput microbenchmarks on the current device (no context needed): FP32 FMA FLOP/s, MUFU
  * rsqrt op/s and FP64 FMA FLOP/s.  Returns 0 on success. */
 TPE_API int tp_measure_peaks(double *fp32_flops, double *mufu_ops, double *fp64_flops);

@@ -1099,6 +1099,127 @@ void make_plans(Ctx &c)
     plan_pass(c, c.plan_apply, p64 ? kTptApply64 : kTptApply, oa);
 }
 
+// ---------------------------------------------------------------------------------- no-allocation energy
+
+// Items of one problem spanning all edges (target blocks x source chunks); every tile checks
+// disjointness (the neighbour span is the whole range) because no incidence lists are built.
+__global__ void k_static_items(int nE, int tb, int clen, int nch, WorkItem *items, int *eslots, int *off)
+{
+    int it = blockIdx.x * blockDim.x + threadIdx.x;
+    int nblk = (nE + tb - 1) / tb;
+    if (it < nblk * nch) {
+        int b = it / nch, k = it % nch;
+        int t0 = b * tb, s0 = k * clen;
+        items[it] = WorkItem{t0, min(tb, nE - t0), s0, min(nE, s0 + clen), k, 0, nE - 1, 0};
+    }
+    if (it < nE) eslots[it] = nch;
+    if (it == 0) {
+        off[0] = 0;
+        off[1] = nE;
+    }
+}
+
+__global__ void k_static_stats(int nV, int nE, const double *__restrict__ g, const double *__restrict__ ell,
+                               double *__restrict__ out)
+{
+    __shared__ double sh[7][256];
+    double b[7] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300, 0.0};
+    for (int i = threadIdx.x; i < nV; i += blockDim.x)
+        for (int k = 0; k < 3; ++k) {
+            b[k] = fmin(b[k], g[3 * i + k]);
+            b[3 + k] = fmax(b[3 + k], g[3 * i + k]);
+        }
+    for (int I = threadIdx.x; I < nE; I += blockDim.x) b[6] += ell[I];
+    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = b[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 7; ++k)
+                sh[k][threadIdx.x] = k < 3 ? fmin(sh[k][threadIdx.x], sh[k][threadIdx.x + w])
+                                           : (k < 6 ? fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + w])
+                                                    : sh[k][threadIdx.x] + sh[k][threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < 3; ++k) s += (sh[3 + k][0] - sh[k][0]) * (sh[3 + k][0] - sh[k][0]);
+        out[0] = sh[6][0] / (nE > 0 ? nE : 1);  // mean edge length
+        out[1] = sqrt(s);                       // bounding-box diagonal
+    }
+}
+
+cudaError_t static_energy_launch(const double *gamma, const int *edges, int nV, int nE, double alpha, double beta,
+                                 double near_cutoff, RecF *recF, RecLo *recLo, double *ell, double *T, double *x,
+                                 WorkItem *items, int *eslots, double *part, double *rows, int *counter, int *err,
+                                 double *scal, int *off, int max_items, int max_slots, double *E, cudaStream_t s,
+                                 int *status)
+{
+    *status = 0;
+    if (nE == 0) return cudaMemsetAsync(E, 0, sizeof(double), s);
+    TPE_CHECK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    k_records<<<(nE + 255) / 256, 256, 0, s>>>(nE, gamma, edges, recF, recLo, nullptr, ell, T, x, err);
+    k_static_stats<<<1, 256, 0, s>>>(nV, nE, gamma, ell, scal);
+    TPE_CHECK(cudaGetLastError());
+    // the cutoffs are kernel arguments: read the two statistics and the error word (synchronises)
+    double st[2] = {0.0, 0.0};
+    int e = 0;
+    TPE_CHECK(cudaMemcpyAsync(st, scal, sizeof(st), cudaMemcpyDeviceToHost, s));
+    TPE_CHECK(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TPE_CHECK(cudaStreamSynchronize(s));
+    if (e) {
+        *status = e;
+        return cudaSuccess;
+    }
+    KernelParams kp{};
+    kp.alpha = alpha;
+    kp.beta = beta;
+    kp.p = 2.0 * ((beta - 1.0) / alpha - 1.0) + 1.0;
+    kp.fast = (alpha == 2.0 && beta == 4.5) ? 1 : 0;
+    double rn = near_cutoff * st[0];
+    kp.near2 = rn * rn;
+    kp.near2f = (float)(rn * rn);
+    kp.mid2f = 3.0e38f;  // double-float positions in every tile (the context's default)
+    // blocking: targets per item = kThreads * kTptEnergy, at least 8 source tiles per item
+    int dev = 0, sms = 0, occ = 0;
+    TPE_CHECK(cudaGetDevice(&dev));
+    TPE_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (kp.fast)
+        TPE_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs<PMIX, OP_ENERGY, kTptEnergy, true>, kThreads, 0));
+    else
+        TPE_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs<PMIX, OP_ENERGY, kTptEnergy, false>, kThreads, 0));
+    const int tb = kThreads * kTptEnergy;
+    const int nblk = (nE + tb - 1) / tb;
+    int want = (3 * sms * std::max(1, occ) + nblk - 1) / nblk;
+    int nch = std::min(std::min(std::max(1, want), std::max(1, nE / (8 * kTile))), max_slots);
+    int clen = ((nE + nch - 1) / nch + kTile - 1) / kTile * kTile;
+    nch = (nE + clen - 1) / clen;
+    if (nblk * nch > max_items || nch > max_slots) return cudaErrorInvalidValue;
+    const int nit = nblk * nch;
+    k_static_items<<<(std::max(nit, nE) + 255) / 256, 256, 0, s>>>(nE, tb, clen, nch, items, eslots, off);
+    TPE_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), s));
+    PairArgs pa;
+    pa.items = items;
+    pa.n_items = nit;
+    pa.counter = counter;
+    pa.recF = recF;
+    pa.recLo = recLo;
+    pa.recD = nullptr;
+    pa.urecF = nullptr;
+    pa.urecD = nullptr;
+    pa.na = NearArgs{gamma, edges, ell, T, nullptr};
+    pa.part = part;
+    pa.nE = nE;
+    pa.kp = kp;
+    const int grid = std::max(1, std::min(nit, sms * std::max(1, occ)));
+    if (kp.fast)
+        k_pairs<PMIX, OP_ENERGY, kTptEnergy, true><<<grid, kThreads, 0, s>>>(pa);
+    else
+        k_pairs<PMIX, OP_ENERGY, kTptEnergy, false><<<grid, kThreads, 0, s>>>(pa);
+    k_energy_rows<<<(nE + 255) / 256, 256, 0, s>>>(nE, nch, eslots, part, ell, rows);
+    k_segment_sum<<<1, 256, 0, s>>>(off, rows, E);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------- launchers
 
 cudaError_t build_records(Ctx &c, const double *gamma, int which, cudaStream_t s)

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ER
 EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp_num_problems", "tp_set_params",
             "tp_energy", "tp_differential", "sobolev_apply", "tp_gram_diagonal", "tp_precond_apply",
             "tp_spectral_symbol", "tp_set_constraints_from", "tp_constraints", "sobolev_gradient", "descent_step",
-            "tp_launch_count", "tp_pairs_per_pass", "tp_profile", "tp_profile_read", "tp_measure_peaks"]
+            "tp_launch_count", "tp_pairs_per_pass", "tp_profile", "tp_profile_read", "tp_measure_peaks", "tp_energy_static"]
 
 
 class TpParams(ctypes.Structure):
@@ -94,6 +94,7 @@ def library() -> ctypes.CDLL:
         L.tp_profile_read.argtypes = [vp, i, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_int64)]
         pdd = ctypes.POINTER(d)
         L.tp_measure_peaks.argtypes = [pdd, pdd, pdd]
+        L.tp_energy_static.argtypes = [vp, vp, i, i, d, d, vp, vp]
         _lib = L
     return _lib
 
@@ -261,3 +262,16 @@ def tp_measure_peaks():
     if st != 0:
         raise TpError(TP_ERR_CUDA, "tp_measure_peaks failed")
     return {"fp32_flops": a.value, "mufu_ops": b.value, "fp64_flops": c.value}
+
+
+def tp_energy_static(gamma, edges, alpha=2.0, beta=4.5, E=None):
+    """Energy without device allocation inside the library (edges: CUDA int32 [nE, 2])."""
+    import torch
+    if not (edges.is_cuda and edges.dtype == torch.int32 and edges.is_contiguous()):
+        raise ValueError("edges must be a contiguous CUDA int32 tensor")
+    E = _new(1) if E is None else E
+    st = library().tp_energy_static(_ptr(gamma), ctypes.c_void_p(edges.data_ptr()), int(gamma.shape[0]),
+                                    int(edges.shape[0]), float(alpha), float(beta), _ptr(E), _stream())
+    if st != TP_OK:
+        raise TpError(st, "tp_energy_static failed")
+    return E
