@@ -54,12 +54,17 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-262k", action="store_true", help="skip the 262,144-edge pair-pass timing")
-    ap.add_argument("--mode", choices=["bench", "passes", "precision", "batch"], default="bench",
+    ap.add_argument("--mode", choices=["bench", "passes", "precision", "batch", "learned"], default="bench",
                     help="passes: energy, differential and 3 applies of the workload (for ncu); "
                          "precision: per-result error of the 262,144-edge passes against the FP64 oracle on "
-                         "a sample; batch: 1,024 independent knots of log-uniform size")
+                         "a sample; batch: 1,024 independent knots of log-uniform size; learned: train the "
+                         "learned preconditioner and compare times to 1e-6 against plain FP64 CG")
     ap.add_argument("--rows", type=int, default=1024, help="precision mode: sampled rows / vertices")
     ap.add_argument("--with-fp64", action="store_true", help="precision mode: also run the FP64 GPU passes")
+    ap.add_argument("--train-steps", type=int, default=300, help="learned mode: Adam steps")
+    ap.add_argument("--train-descent", type=int, default=6, help="learned mode: descent steps harvested")
+    ap.add_argument("--fp64-maxit", type=int, default=600, help="learned mode: cap of the plain FP64 CG solves")
+    ap.add_argument("--eval-262k", action="store_true", help="learned mode: also compare on the 262,144-vertex knot")
     return ap.parse_args()
 
 
@@ -310,8 +315,8 @@ def run_batch(args):
     from paper_2006_07859_gb300 import tpe
     sizes = S.batch_sizes(1024, 64, 4096, 1000)
     b = S.batch_of_knots(sizes, 8, 1000)
-    ctx = tpe.Context.from_curves(b, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_SPECTRAL, independent=1,
-                                  cg_rtol=1e-6, cg_maxit=2000, proj_cg_rtol=1e-3)
+    ctx = tpe.Context.from_curves(b, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_TWOLEVEL, independent=1,
+                                  cg_rtol=1e-6, cg_maxit=500, proj_cg_rtol=1e-3)
     g = torch.as_tensor(b.gamma).cuda()
     pairs = ctx.pairs_per_pass()
     tpe.tp_energy(ctx, g)
@@ -337,6 +342,97 @@ def run_batch(args):
     print(json.dumps(res), flush=True)
 
 
+def timed_solve(tpe, torch, ctx, g, rhs):
+    """Wall time (CUDA events around the call) and info of one preconditioned CG solve of
+    A-bar y = P rhs on the mean-free subspace, preconditioner set-up included."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    R = torch.empty((0, ctx.n_vertices, 3), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    ev[0].record()
+    _, info = tpe.tp_cg_harvest(ctx, g, rhs, 1, R, R)
+    ev[1].record()
+    torch.cuda.synchronize()
+    return dict(info, seconds=ev[0].elapsed_time(ev[1]) / 1e3)
+
+
+def run_learned(args):
+    """Learned preconditioner (config 5 at reduced scale, see the training set below): harvest
+    (residual, correction) pairs from the descent of 8 training knots (K = 8, n log-uniform in
+    [4096, 16384], seed 500), train the network with the library's kernels, then time the gradient
+    solve A-bar y = P dE to 1e-6 on the 8 x 4096 benchmark knots (unseen): plain FP64 CG, FP64 Jacobi,
+    FP64 two-level, mixed two-level and mixed two-level + learned term."""
+    import torch
+    import synth as S
+    from paper_2006_07859_gb300 import learned, tpe
+    out = {"mode": "learned"}
+    sizes = S.batch_sizes(8, 4096, 16384, 500)
+    tr = S.batch_of_knots(sizes, 8, 500)
+    ctx = tpe.Context.from_curves(tr, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_LEARNED, independent=1,
+                                  cg_rtol=1e-6, cg_maxit=2000, proj_cg_rtol=1e-3)
+    ctx.set_params(precond=tpe.TP_PRECOND_TWOLEVEL)
+    g = torch.as_tensor(tr.gamma).cuda()
+    t0 = time.perf_counter()
+    sets = learned.harvest_descent(ctx, g, steps=args.train_descent, every=1, max_pairs=400)
+    torch.cuda.synchronize()
+    t_h = time.perf_counter() - t0
+    npairs = sum(s.n for s in sets)
+    th0 = torch.as_tensor(learned.init_params(0)).cuda()
+    loss0 = learned.evaluate_loss(ctx, sets, th0)
+    t0 = time.perf_counter()
+    res = learned.train(ctx, sets, steps=args.train_steps, lr=3e-3, batch=4, seed=0)
+    torch.cuda.synchronize()
+    t_t = time.perf_counter() - t0
+    loss1 = learned.evaluate_loss(ctx, sets, res["theta"])
+    theta = res["theta"].clone()
+    out["training"] = {"curves": "8_fourier_knots_K8_n_loguniform_4096_16384_seed500", "sizes": [int(x) for x in sizes],
+                       "descent_steps_harvested": args.train_descent, "pair_vectors": npairs,
+                       "per_curve_pairs": npairs * len(sizes), "harvest_seconds": t_h, "adam_steps": args.train_steps,
+                       "train_seconds": t_t, "loss_init": loss0, "loss_trained": loss1,
+                       "loss_first": res["losses"][0], "loss_last10": float(np.mean(res["losses"][-10:]))}
+    ctx.close()
+    del sets
+    torch.cuda.empty_cache()
+
+    def compare(curves, label, arms):
+        rows = {}
+        for name, prec, pc, maxit in arms:
+            c = tpe.Context.from_curves(curves, precision=prec, precond=pc, independent=1, cg_rtol=1e-6,
+                                        cg_maxit=maxit, cg_check_every=8)
+            gg = torch.as_tensor(curves.gamma).cuda()
+            dE = tpe.tp_differential(c, gg)
+            if pc == tpe.TP_PRECOND_LEARNED:
+                tpe.tp_gnn_set_params(c, theta)
+            if pc >= tpe.TP_PRECOND_SPECTRAL:
+                timed_solve(tpe, torch, c, gg, dE)   # warm-up of the short solves (first-launch costs)
+            rows[name] = timed_solve(tpe, torch, c, gg, dE)
+            c.close()
+        return {"workload": label, "rtol": 1e-6, "solves": rows}
+
+    arms = [("fp64_none", tpe.TP_FP64, tpe.TP_PRECOND_NONE, args.fp64_maxit),
+            ("fp64_jacobi", tpe.TP_FP64, tpe.TP_PRECOND_JACOBI, args.fp64_maxit),
+            ("fp64_twolevel", tpe.TP_FP64, tpe.TP_PRECOND_TWOLEVEL, 2000),
+            ("mixed_none", tpe.TP_MIXED, tpe.TP_PRECOND_NONE, 20000),
+            ("mixed_jacobi", tpe.TP_MIXED, tpe.TP_PRECOND_JACOBI, 20000),
+            ("mixed_twolevel", tpe.TP_MIXED, tpe.TP_PRECOND_TWOLEVEL, 2000),
+            ("mixed_learned", tpe.TP_MIXED, tpe.TP_PRECOND_LEARNED, 2000)]
+    curves, cfg, _ = workload("knots8x4096")
+    out["eval_8x4096"] = compare(curves, cfg["workload"], arms)
+    r = out["eval_8x4096"]["solves"]
+    # plain FP64 CG capped: estimated time to 1e-6 = its time per iteration x the iterations the same
+    # unpreconditioned CG needs with the mixed operator (labelled as an estimate)
+    for a, b in (("fp64_none", "mixed_none"), ("fp64_jacobi", "mixed_jacobi")):
+        if not r[a]["converged"] and r[b]["converged"]:
+            r[a]["estimated_seconds_to_rtol"] = r[a]["seconds"] / r[a]["iters"] * r[b]["iters"]
+    if args.eval_262k:
+        big = S.knot_262144()
+        arms2 = [("mixed_none_capped100", tpe.TP_MIXED, tpe.TP_PRECOND_NONE, 100),
+                 ("mixed_jacobi_capped100", tpe.TP_MIXED, tpe.TP_PRECOND_JACOBI, 100),
+                 ("mixed_twolevel", tpe.TP_MIXED, tpe.TP_PRECOND_TWOLEVEL, 2000),
+                 ("mixed_learned", tpe.TP_MIXED, tpe.TP_PRECOND_LEARNED, 2000)]
+        out["eval_262144"] = compare(big, "fourier_knot_K16_n262144_seed100", arms2)
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2006_07859_gb300 import tpe
@@ -347,7 +443,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
     curves, cfg, indep = workload(args.workload)
     sp = solver_params(args.workload, args)
-    ctx = tpe.Context.from_curves(curves, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_SPECTRAL,
+    ctx = tpe.Context.from_curves(curves, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_TWOLEVEL,
                                   independent=indep, **sp)
     gamma = torch.as_tensor(curves.gamma).cuda()
     pairs = ctx.pairs_per_pass()
@@ -376,7 +472,7 @@ def run_ours(args, rank, world, local_rank):
         total += a.elapsed_time(b) / 1e3
     clk = clocks.stop() if clocks else None
     launches = ctx.launch_count() - l0
-    prof = {op: ctx.profile_read(i) for i, op in enumerate(["energy", "diff", "apply", "diag"])}
+    prof = {op: ctx.profile_read(i) for i, op in enumerate(["energy", "diff", "apply", "diag", "apply_cg"])}
     ctx.profile(False)
     t = torch.tensor([total], dtype=torch.float64, device="cuda")
     if dist:
@@ -413,7 +509,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = pairs * FLOP_PER_PAIR["apply"] / avg_s if n_a else None
     peaks = tpe.tp_measure_peaks()
     passes = {k: prof[k][1] / args.steps for k in ("energy", "diff", "apply")}
-    pps = {k: (pairs * prof[k][1] / (prof[k][0] / 1e3) if prof[k][1] else None) for k in prof}
+    passes["apply"] += prof["apply_cg"][1] / args.steps   # every apply launch (the CG ones may skip converged curves)
+    pps = {k: (pairs * prof[k][1] / (prof[k][0] / 1e3) if prof[k][1] else None) for k in prof if k != "apply_cg"}
     big = None if args.no_262k else pass_throughput_262k(tpe, torch)
     # CPU oracle baseline on a bounded sample, extrapolated with the measured pass counts
     if args.no_cpu:
@@ -427,7 +524,7 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
         "data": "synthetic",
-        "config": dict(cfg, alpha=2.0, beta=4.5, precision="mixed", precond="spectral", **sp,
+        "config": dict(cfg, alpha=2.0, beta=4.5, precision="mixed", precond="twolevel (spectral RQ + 64 coarse hats)", **sp,
                        l2="flushed between timed steps (256 MiB write)", parallelism=f"replicas x{world}"),
         "pair_interactions_per_s": pps,
         "pair_pass_throughput_262144": big,
@@ -475,6 +572,8 @@ def main():
         run_precision(args)
     elif args.mode == "batch":
         run_batch(args)
+    elif args.mode == "learned":
+        run_learned(args)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -68,8 +68,18 @@ typedef enum {
 typedef enum {
     TP_PRECOND_NONE = 0,
     TP_PRECOND_JACOBI = 1,   /* diag(A)^-1 */
-    TP_PRECOND_SPECTRAL = 2  /* Jacobi-scaled circulant inverse per closed curve (not in the paper) */
+    TP_PRECOND_SPECTRAL = 2, /* Jacobi-scaled circulant inverse per closed curve (not in the paper) */
+    TP_PRECOND_SPECTRAL_RQ = 3, /* the same with the symbol corrected by Rayleigh quotients of the actual
+                                   operator at sampled frequencies, rebuilt at every set-up (not in the paper) */
+    TP_PRECOND_TWOLEVEL = 4,    /* TP_PRECOND_SPECTRAL_RQ plus an additive coarse-space correction
+                                   Z (Z^T A Z)^-1 Z^T with coarse_dim periodic hat functions per curve */
+    TP_PRECOND_LEARNED = 5      /* TP_PRECOND_TWOLEVEL plus a learned SPD local term G_theta (tp_gnn_*);
+                                   only for contexts created with it (not in the paper) */
 } tp_precond;
+
+/* Shape of the learned preconditioner's edge-graph network (see tp_gnn_set_params). */
+#define TP_GNN_HIDDEN 64
+#define TP_GNN_FEATURES 8
 
 typedef struct {
     double alpha, beta;   /* kernel exponents of Eq. 3; Lemma 1 needs alpha > 1, beta in [alpha+2, 2 alpha+1) */
@@ -88,15 +98,17 @@ typedef struct {
     int proj_maxit;
     int independent;      /* 1: every curve is its own problem (no cross-curve pairs, constraints per curve);
                              0: the whole graph is one problem (one barycenter + one total length) */
+    int coarse_dim;       /* TP_PRECOND_TWOLEVEL: hat functions per closed curve (<= 64, at most n / 4) */
     double far_cutoff;    /* TP_MIXED: source tiles farther than far_cutoff * (extent of the curve) from a
                              warp's targets use single-float positions (faster, less accurate); >= 10
                              keeps double-float positions everywhere */
 } tp_params;
 
 typedef struct {
-    int iters;          /* CG iterations of the gradient solve */
-    double rel_res;     /* final ||P(a - A-bar x)|| / ||P a||, recomputed with the exact operator */
-    int converged;
+    int iters;          /* CG iterations of the gradient solve (largest over problems, summed over the solves) */
+    double rel_res;     /* final relative residual, recomputed with the working-precision operator (largest over problems) */
+    int converged;      /* all problems reached cg_rtol */
+    int n_converged;    /* problems whose solves all reached cg_rtol */
 } tp_solve_info;
 
 typedef struct {
@@ -107,8 +119,9 @@ typedef struct {
     int proj_iters;           /* projection iterations of the accepted trial */
     int cg_iters;             /* gradient-solve CG iterations */
     int proj_cg_iters;        /* all CG iterations spent in constraint projections */
-    int accepted;
+    int accepted;             /* problems whose step was accepted */
     double rel_res;           /* gradient-solve relative residual */
+    int n_converged;          /* problems whose gradient solves reached cg_rtol */
 } tp_step_info;
 
 typedef struct tp_ctx tp_ctx;
@@ -150,6 +163,12 @@ TPE_API tp_status tp_gram_diagonal(tp_ctx *ctx, const double *gamma, double *dia
 /* Apply the configured preconditioner M^-1 (for the curve gamma) to r: z = M^-1 r, device [nV][3]. */
 TPE_API tp_status tp_precond_apply(tp_ctx *ctx, const double *gamma, const double *r, double *z, tp_stream stream);
 
+/* Symbols the spectral preconditioner currently divides by, for every curve at its vertex offset:
+ * out DEVICE double [n_vertices].  rq = 0: regular-polygon symbols; rq = 1: the Rayleigh-quotient
+ * corrected symbols of the last set-up (TP_PRECOND_SPECTRAL_RQ), which tp_precond_apply and the
+ * solves rebuild for their curve. */
+TPE_API tp_status tp_spectral_symbols(tp_ctx *ctx, int rq, double *out, tp_stream stream);
+
 /* Regular-polygon symbol of the spectral preconditioner for a closed curve of n vertices
  * (eigenvalues of A of the regular n-gon divided by its diagonal, lambda_0 := lambda_1),
  * into lam (device [n]). */
@@ -185,7 +204,8 @@ TPE_API int64_t tp_launch_count(const tp_ctx *ctx);
 TPE_API int64_t tp_pairs_per_pass(const tp_ctx *ctx);
 
 /* Per-kernel timing with CUDA events recorded around every pair-kernel launch on its own stream.
- * enable = 1 starts (and clears) the record; op: 0 energy, 1 differential, 2 apply, 3 diag.
+ * enable = 1 starts (and clears) the record; op: 0 energy, 1 differential, 2 apply (full passes),
+ * 3 diag, 4 apply inside CG solves (items of already converged problems skipped).
  * tp_profile_read synchronises the recorded events and returns the summed device time (ms) and
  * the number of launches of that pair kernel since profiling was enabled. */
 TPE_API tp_status tp_profile(tp_ctx *ctx, int enable);
@@ -208,6 +228,81 @@ TPE_API tp_status tp_profile_read(tp_ctx *ctx, int op, double *total_ms, int64_t
  * Errors: TP_ERR_INVALID_ARG, TP_ERR_DEGENERATE_EDGE, TP_ERR_NONFINITE, TP_ERR_CUDA. */
 TPE_API tp_status tp_energy_static(const double *gamma, const int32_t *edges, int n_vertices, int n_edges,
                                    double alpha, double beta, double *E, tp_stream stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Learned preconditioner (TP_PRECOND_LEARNED).  Not part of the paper: a 3-layer network on the
+ * edge graph of the closed curves predicts per-edge log-weights (a_I, b_I) of an SPD local term
+ *   G = D^-1/2 (D_delta^T diag(e^{2a}) D_delta + D_sigma^T diag(e^{2b}) D_sigma) D^-1/2,
+ * D = diag(A), (D_delta r)_I = r_i2 - r_i1, (D_sigma r)_I = r_i1 + r_i2, that is added to the
+ * two-level preconditioner: M^-1 r = M_2L^-1 r + G r.  It stays SPD for any parameters, so CG with
+ * the exact operator remains the judge of the residual.
+ * Network (per edge I, neighbours I-1 and I+1 along its curve; FP32 activations, BF16 weights):
+ *   f_I = [log(l_I / mean l), 1 - T_{I-1}.T_I, 1 - T_I.T_{I+1}, log(d_i1 / mean d), log(d_i2 / mean d),
+ *          log(l_{I-1} / l_I), log(l_{I+1} / l_I), 1]     (means over the edge's curve)
+ *   h1 = relu(W1 f + b1),  h2 = relu(W2s h1 + W2n (h1[I-1] + h1[I+1]) / 2 + b2),
+ *   h3 = relu(W3s h2 + W3n (h2[I-1] + h2[I+1]) / 2 + b3),  (a, b) = W4 h3 + b4.
+ * Parameter vector theta: FP32, DEVICE, tp_gnn_num_params() values in the order
+ *   W1 [64][8], b1 [64], W2s [64][64], W2n [64][64], b2, W3s, W3n, b3, W4 [2][64], b4 [2] (row-major).
+ * Training: (r, e = A^+ r) pairs from the context's own CG solves (tp_cg_harvest), prepared once
+ * (tp_gnn_prepare_pairs), then Adam steps on L = (z^T A z - 2 z^T r + e^T r) / e^T r with
+ * z = M_2L^-1 r + G r (tp_gnn_train_step), the A-norm error of z relative to that of z = 0.
+ * Every tp_gnn_* call fails with TP_ERR_UNSUPPORTED on a context not created with
+ * TP_PRECOND_LEARNED (only those hold the network's scratch, about 1.6 KB per edge). */
+TPE_API int tp_gnn_num_params(void);
+
+/* Load theta (DEVICE float [P]) as the FP32 master parameters and refresh their BF16 copy;
+ * reset_optimizer = 1 also zeroes Adam's moments and step count. */
+TPE_API tp_status tp_gnn_set_params(tp_ctx *ctx, const float *theta, int reset_optimizer, tp_stream stream);
+/* Copy the FP32 master parameters into theta (DEVICE float [P]). */
+TPE_API tp_status tp_gnn_get_params(tp_ctx *ctx, float *theta, tp_stream stream);
+
+/* Bind the curve gamma: diag(A) by one pair pass and the edge features, kept for the forward,
+ * backward, G-term and training calls until the next bind or preconditioner set-up. */
+TPE_API tp_status tp_gnn_bind(tp_ctx *ctx, const double *gamma, tp_stream stream);
+
+/* Network forward on the bound curve with the current BF16 weights.  features (DEVICE float
+ * [n_edges][8]) and out (DEVICE float [n_edges][2]: a, b) may each be NULL. */
+TPE_API tp_status tp_gnn_forward(tp_ctx *ctx, float *features, float *out, tp_stream stream);
+
+/* Parameter gradient grad (DEVICE float [P]) of a scalar whose derivative with respect to the
+ * outputs of the last forward pass is dout (DEVICE float [n_edges][2]).  The chain uses the BF16
+ * weights the forward pass used; the sums are deterministic. */
+TPE_API tp_status tp_gnn_backward(tp_ctx *ctx, const float *dout, float *grad, tp_stream stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the FP32 masters with gradient grad
+ * (DEVICE float [P]) and learning rate lr; refreshes the BF16 copy. */
+TPE_API tp_status tp_gnn_adam(tp_ctx *ctx, const float *grad, float lr, tp_stream stream);
+
+/* z = G r (accumulate = 0) or z += G r (accumulate = 1) with the last forward's outputs and the
+ * bound diag(A); r, z DEVICE double [nV][3]. */
+TPE_API tp_status tp_gnn_g_apply(tp_ctx *ctx, const double *r, double *z, int accumulate, tp_stream stream);
+
+/* dout (=, or += with accumulate = 1) the derivative of gz . (G r) with respect to the network
+ * outputs (a, b): DEVICE float [n_edges][2]; r, gz DEVICE double [nV][3]. */
+TPE_API tp_status tp_gnn_out_grad(tp_ctx *ctx, const double *r, const double *gz, float *dout, int accumulate,
+                                  tp_stream stream);
+
+/* Solve A-bar y = P rhs by the configured preconditioned CG on the mean-free subspace (the solve
+ * inside sobolev_gradient) and capture, every `every` iterations and at most max_pairs times, the
+ * residual r_k into R[k] and the exact correction e_k = y* - y_k (y*: the final iterate) into E[k].
+ * R, E: DEVICE double [max_pairs][nV][3].  *n_pairs (host) = pairs captured.  info (host, may be
+ * NULL) as for sobolev_gradient.  Synchronises the stream. */
+TPE_API tp_status tp_cg_harvest(tp_ctx *ctx, const double *gamma, const double *rhs, int every, int max_pairs,
+                                double *R, double *E, int *n_pairs, tp_solve_info *info, tp_stream stream);
+
+/* For n harvested pairs of the curve gamma: ER[k] (DEVICE double [n][n_problems]) = e_k . r_k per
+ * problem, B[k] = P M_2L^-1 r_k (the preconditioner without the learned term) and AB[k] = A-bar B[k].
+ * R, E, B, AB DEVICE double [n][nV][3]; B may be the same buffer as E (ER is taken first). */
+TPE_API tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, const double *R, double *E,
+                                       double *B, double *AB, double *ER, tp_stream stream);
+
+/* One training step on n prepared pairs of the bound curve gamma: the loss at the current parameters,
+ * averaged over pairs and problems, into *loss (host), the parameter gradient into grad (DEVICE float
+ * [P], may be NULL), then one Adam step when lr > 0 (lr = 0: gradient only).  Costs one A-bar apply
+ * per pair.  Synchronises the stream. */
+TPE_API tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, const double *R, const double *B,
+                                    const double *AB, const double *ER, float lr, double *loss, float *grad,
+                                    tp_stream stream);
 
 /* Throughput microbenchmarks on the current device (no context needed): FP32 FMA FLOP/s, MUFU
  * rsqrt op/s and FP64 FMA FLOP/s.  Returns 0 on success. */

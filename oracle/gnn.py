@@ -1,0 +1,161 @@
+"""FP64 numpy oracle of the learned preconditioner term (test infrastructure only).
+
+The learned term is this library's extension, not part of the paper.  Every step is written out
+from its definition; the CUDA kernels (BF16 weights, FP32 accumulation) are checked against it.
+
+Edge features (closed curves; I-1 and I+1 are the neighbours of edge I on its curve; d = diag(A)):
+    f = [log(l_I / mean l), 1 - T_{I-1}.T_I, 1 - T_I.T_{I+1}, log(d_i1 / mean d), log(d_i2 / mean d),
+         log(l_{I-1} / l_I), log(l_{I+1} / l_I), 1]
+Network (3 layers of width 64 on the edge graph, then a linear read-out of 2 values per edge):
+    h1 = relu(W1 f + b1)
+    h2 = relu(W2s h1 + W2n (h1[I-1] + h1[I+1]) / 2 + b2)
+    h3 = relu(W3s h2 + W3n (h2[I-1] + h2[I+1]) / 2 + b3)
+    (a, b) = W4 h3 + b4
+Preconditioner term (SPD by construction), for r with 3 components and r~ = r / sqrt(d):
+    delta_I = r~_i2 - r~_i1, sigma_I = r~_i1 + r~_i2, ea = exp(2 a_I), eb = exp(2 b_I)
+    (G r)_i2 += (ea delta_I + eb sigma_I) / sqrt(d_i2),  (G r)_i1 += (-ea delta_I + eb sigma_I) / sqrt(d_i1)
+Training loss of one pair (r, e = A^+ r): the A-norm error of z = M^-1 r + G r relative to e,
+    L = (z^T A z - 2 z^T r + e^T r) / (e^T r),   dL/dz = 2 (A z - r) / (e^T r).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+H = 64
+F = 8
+SHAPES = [("W1", (H, F)), ("b1", (H,)), ("W2s", (H, H)), ("W2n", (H, H)), ("b2", (H,)),
+          ("W3s", (H, H)), ("W3n", (H, H)), ("b3", (H,)), ("W4", (2, H)), ("b4", (2,))]
+
+
+def n_params():
+    return sum(int(np.prod(s)) for _, s in SHAPES)
+
+
+def unpack(theta):
+    out, o = {}, 0
+    for name, s in SHAPES:
+        k = int(np.prod(s))
+        out[name] = np.asarray(theta[o:o + k], dtype=np.float64).reshape(s)
+        o += k
+    return out
+
+
+def init_params(seed=0, out_bias=-2.0):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, s in SHAPES:
+        if name.startswith("W"):
+            fan_in = s[1]
+            w = rng.normal(0.0, 1.0 / np.sqrt(fan_in), size=s)
+            if name == "W4":
+                w *= 0.1
+            parts.append(w.ravel())
+        elif name == "b4":
+            parts.append(np.full(s, out_bias))
+        else:
+            parts.append(np.zeros(s))
+    return np.concatenate(parts)
+
+
+def neighbours(n):
+    I = np.arange(n)
+    return (I - 1) % n, (I + 1) % n
+
+
+def features(gamma, diag):
+    """Edge features of one closed curve (vertex i, edge i = (i, i+1 mod n))."""
+    n = gamma.shape[0]
+    e = np.roll(gamma, -1, axis=0) - gamma
+    l = np.linalg.norm(e, axis=1)
+    T = e / l[:, None]
+    prv, nxt = neighbours(n)
+    d1, d2 = diag, np.roll(diag, -1)
+    dm = diag.mean()
+    return np.stack([np.log(l / l.mean()), 1 - (T[prv] * T).sum(1), 1 - (T * T[nxt]).sum(1), np.log(d1 / dm),
+                     np.log(d2 / dm), np.log(l[prv] / l), np.log(l[nxt] / l), np.ones(n)], axis=1)
+
+
+def forward(theta, f):
+    p = unpack(theta)
+    n = f.shape[0]
+    prv, nxt = neighbours(n)
+    z1 = f @ p["W1"].T + p["b1"]
+    h1 = np.maximum(z1, 0)
+    m1 = 0.5 * (h1[prv] + h1[nxt])
+    z2 = h1 @ p["W2s"].T + m1 @ p["W2n"].T + p["b2"]
+    h2 = np.maximum(z2, 0)
+    m2 = 0.5 * (h2[prv] + h2[nxt])
+    z3 = h2 @ p["W3s"].T + m2 @ p["W3n"].T + p["b3"]
+    h3 = np.maximum(z3, 0)
+    out = h3 @ p["W4"].T + p["b4"]
+    return out, dict(f=f, z1=z1, h1=h1, m1=m1, z2=z2, h2=h2, m2=m2, z3=z3, h3=h3)
+
+
+def backward(theta, cache, dout):
+    """Gradient of a scalar whose derivative w.r.t. the network outputs is dout [n, 2]."""
+    p = unpack(theta)
+    f = cache["f"]
+    n = f.shape[0]
+    prv, nxt = neighbours(n)
+    g = {}
+    g["W4"] = dout.T @ cache["h3"]
+    g["b4"] = dout.sum(0)
+    dh3 = dout @ p["W4"]
+    dz3 = dh3 * (cache["z3"] > 0)
+    g["W3s"] = dz3.T @ cache["h2"]
+    g["W3n"] = dz3.T @ cache["m2"]
+    g["b3"] = dz3.sum(0)
+    dh2 = dz3 @ p["W3s"]
+    dm2 = dz3 @ p["W3n"]
+    dh2 = dh2 + 0.5 * (dm2[nxt] + dm2[prv])   # m2[I] = (h2[I-1] + h2[I+1]) / 2
+    dz2 = dh2 * (cache["z2"] > 0)
+    g["W2s"] = dz2.T @ cache["h1"]
+    g["W2n"] = dz2.T @ cache["m1"]
+    g["b2"] = dz2.sum(0)
+    dh1 = dz2 @ p["W2s"]
+    dm1 = dz2 @ p["W2n"]
+    dh1 = dh1 + 0.5 * (dm1[nxt] + dm1[prv])
+    dz1 = dh1 * (cache["z1"] > 0)
+    g["W1"] = dz1.T @ f
+    g["b1"] = dz1.sum(0)
+    return np.concatenate([g[name].ravel() for name, _ in SHAPES])
+
+
+def g_apply(out, diag, r):
+    """(G r) for the per-edge outputs out = (a, b) of one closed curve; r [n, 3]."""
+    n = r.shape[0]
+    sd = np.sqrt(diag)
+    rt = r / sd[:, None]
+    r1, r2 = rt, np.roll(rt, -1, axis=0)      # values at i1 = I and i2 = I + 1
+    ea, eb = np.exp(2 * out[:, 0]), np.exp(2 * out[:, 1])
+    delta, sig = r2 - r1, r1 + r2
+    c2 = ea[:, None] * delta + eb[:, None] * sig
+    c1 = -ea[:, None] * delta + eb[:, None] * sig
+    gr = c1 / sd[:, None] + np.roll(c2, 1, axis=0) / sd[:, None]   # vertex i receives c1 of edge i, c2 of edge i-1
+    return gr
+
+
+def g_out_grad(out, diag, r, gz):
+    """d(gz . G r) / d out: per edge [dL/da, dL/db] with gz = dL/d(G r)."""
+    sd = np.sqrt(diag)
+    rt = r / sd[:, None]
+    gt = gz / sd[:, None]
+    r1, r2 = rt, np.roll(rt, -1, axis=0)
+    g1, g2 = gt, np.roll(gt, -1, axis=0)
+    ea, eb = np.exp(2 * out[:, 0]), np.exp(2 * out[:, 1])
+    delta, sig = r2 - r1, r1 + r2
+    dea = ((g2 - g1) * delta).sum(1)
+    deb = ((g1 + g2) * sig).sum(1)
+    return np.stack([2 * ea * dea, 2 * eb * deb], axis=1)
+
+
+def loss_and_grad(theta, f, diag, A, r, e, base_z):
+    """Loss of one pair and its parameter gradient. base_z = M^-1 r of the fixed preconditioner."""
+    out, cache = forward(theta, f)
+    z = base_z + g_apply(out, diag, r)
+    Az = A @ z
+    er = float((e * r).sum())
+    L = (float((z * Az).sum()) - 2 * float((z * r).sum()) + er) / er
+    gz = 2 * (Az - r) / er
+    dout = g_out_grad(out, diag, r, gz)
+    return L, backward(theta, cache, dout)

@@ -532,3 +532,65 @@ def ngon_symbol_closed_form(n, sigma, normalized=True):
         lam = lam / lam.mean()
         lam[0] = lam[1]
     return lam
+
+
+def rq_frequencies(n):
+    """Sampled frequencies of the Rayleigh-quotient symbol correction: 1..8 and 14 values spaced
+    evenly in log between 9 and n/2 (rounded), unique, at most n/2."""
+    ks = list(range(1, 9))
+    lo, hi = math.log(9.0), math.log(max(9.0, n / 2.0))
+    ks += [int(round(math.exp(lo + (hi - lo) * j / 13.0))) for j in range(14)]
+    return sorted(k for k in set(ks) if 1 <= k <= n // 2)
+
+
+def spectral_rq_symbol(A, n, sigma):
+    """Rayleigh-quotient corrected symbol of one closed curve with Gram matrix A (n x n): the
+    eigenvalues of T. Chan's optimal circulant approximation of S = D^-1/2 A D^-1/2,
+    lambda_opt(k) = (c_k^T S c_k + s_k^T S s_k) / n with c_k, s_k the cosine and sine modes, are taken
+    at the sampled frequencies; rho = lambda_opt / lambda_ngon is interpolated linearly in
+    (log k, log rho) and the symbol is lambda_ngon * rho (lambda_0 := the corrected lambda_1)."""
+    d = np.diag(A)
+    ds = np.sqrt(d)
+    lam = ngon_symbol_closed_form(n, sigma)
+    i = np.arange(n)
+    ks = rq_frequencies(n)
+    lk, lr = [], []
+    for k in ks:
+        c = np.cos(2 * np.pi * ((k * i) % n) / n) / ds
+        s = np.sin(2 * np.pi * ((k * i) % n) / n) / ds
+        q = (c @ A @ c + s @ A @ s) / n
+        lk.append(math.log(k))
+        lr.append(math.log(q / lam[k]))
+    out = np.empty(n)
+    for k in range(n):
+        kf = k if k <= n // 2 else n - k
+        if kf <= 1:
+            r = lr[0]
+        else:
+            r = float(np.interp(math.log(kf), lk, lr))
+        out[k] = lam[1 if k == 0 else k] * math.exp(r)
+    return out
+
+
+def coarse_hats(n, m):
+    """The first m - 1 of m periodic hat functions on a closed curve of n vertices: hat j is
+    max(0, 1 - |i m / n - j|) (distance taken modulo m).  Columns of an n x (m - 1) matrix."""
+    t = np.arange(n) * m / n
+    Z = np.zeros((n, m - 1))
+    for j in range(m - 1):
+        d = np.abs(t - j)
+        d = np.minimum(d, m - d)
+        Z[:, j] = np.maximum(0.0, 1.0 - d)
+    return Z
+
+
+def twolevel_apply(A, n, sigma, m, r):
+    """Two-level preconditioner of one closed curve: the Rayleigh-quotient corrected spectral term
+    plus the additive coarse term Z (Z^T A Z)^-1 Z^T r with m periodic hats (m <= n / 4).
+    r: [n, 3]; returns [n, 3] (before the mean-free projection)."""
+    ds = np.sqrt(np.diag(A))
+    lam = spectral_rq_symbol(A, n, sigma)
+    z = np.real(np.fft.ifft(np.fft.fft(r / ds[:, None], axis=0) / lam[:, None], axis=0)) / ds[:, None]
+    Z = coarse_hats(n, m)
+    Ac = Z.T @ A @ Z
+    return z + Z @ np.linalg.solve(Ac, Z.T @ r)

@@ -50,8 +50,12 @@ bool params_ok(const tp_params *p, std::string &why)
         why = "bad precision";
         return false;
     }
-    if (p->precond < TP_PRECOND_NONE || p->precond > TP_PRECOND_SPECTRAL) {
+    if (p->precond < TP_PRECOND_NONE || p->precond > TP_PRECOND_LEARNED) {
         why = "bad preconditioner";
+        return false;
+    }
+    if (p->coarse_dim < 2) {
+        why = "coarse_dim must be >= 2";
         return false;
     }
     if (!(p->far_cutoff >= 0.0)) {
@@ -77,6 +81,9 @@ void set_kernel_params(Ctx &c)
     double rn = p.near_cutoff * c.mean_ell;
     c.kp.near2 = rn * rn;
     c.kp.near2f = (float)(rn * rn);
+    // the differential's near-pair gradient terms are large and cancel between the two sides of a
+    // vertex, so they get FP64 over a 4x wider band than the energy
+    c.kp.near2f_diff = (float)(16.0 * rn * rn);
     // tiles closer than far_cutoff x the curve's extent use double-float differences (mixed path)
     double rm = std::max(p.far_cutoff * c.extent, rn);
     c.kp.mid2f = p.far_cutoff >= 10.0 ? 3.0e38f : (float)(rm * rm);
@@ -193,6 +200,7 @@ void tp_default_params(tp_params *p)
     p->proj_maxit = 5;
     p->independent = 0;
     p->far_cutoff = 10.0;
+    p->coarse_dim = 64;
 }
 
 const char *tp_last_error(const tp_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
@@ -208,7 +216,7 @@ tp_status tp_profile(tp_ctx *ctx, int enable)
     if (!ctx) return TP_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     prof_harvest(c);
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         c.prof_ms[k] = 0.0;
         c.prof_n[k] = 0;
     }
@@ -218,7 +226,7 @@ tp_status tp_profile(tp_ctx *ctx, int enable)
 
 tp_status tp_profile_read(tp_ctx *ctx, int op, double *total_ms, int64_t *launches)
 {
-    if (!ctx || op < 0 || op > 3) return TP_ERR_INVALID_ARG;
+    if (!ctx || op < 0 || op > 4) return TP_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     prof_harvest(c);
     if (total_ms) *total_ms = c.prof_ms[op];
@@ -232,6 +240,8 @@ void tp_destroy(tp_ctx *ctx)
     Ctx &c = ctx->c;
     if (c.sol) solver_free(c);
     spectral_free(c);
+    coarse_free(c);
+    gnn_free(c);
     void *ptrs[] = {c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_voff,
                     c.plan_energy.d_items, c.plan_diff.d_items, c.plan_apply.d_items, c.plan_energy.d_eslots,
                     c.plan_diff.d_eslots, c.plan_apply.d_eslots, c.d_counter, c.d_recF, c.d_recF2, c.d_recLo,
@@ -312,7 +322,7 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
                 break;
             }
     }
-    if (prm.precond == TP_PRECOND_SPECTRAL && !c.spectral_ok)
+    if ((prm.precond >= TP_PRECOND_SPECTRAL) && !c.spectral_ok)
         return fail(ctx, TP_ERR_UNSUPPORTED,
                     "the spectral preconditioner needs every curve to be a closed polygon (i, i+1 mod n) of >= 4 vertices");
     int dev = 0;
@@ -411,11 +421,13 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
     CK(cudaMallocHost(&c.h_pinned, sizeof(double) * (64 + 16 * (size_t)c.nProb)));
     CK(cudaMallocHost(&c.h_pinned_i, sizeof(int) * 64));
     CK(solver_setup(c));
-    if (prm.precond == TP_PRECOND_SPECTRAL) {
+    if (prm.precond >= TP_PRECOND_SPECTRAL) {
         cudaError_t e = spectral_setup(c, 0);
         if (e == cudaErrorNotSupported) return fail(ctx, TP_ERR_UNSUPPORTED, "spectral preconditioner not built");
         CK(e);
     }
+    if (prm.precond >= TP_PRECOND_TWOLEVEL) CK(coarse_init(c));
+    if (prm.precond == TP_PRECOND_LEARNED) CK(gnn_alloc(c));
     CK(cudaDeviceSynchronize());
     return TP_OK;
 }
@@ -427,19 +439,22 @@ tp_status tp_set_params(tp_ctx *ctx, const tp_params *p)
     if (!params_ok(p, why)) return fail(ctx, TP_ERR_INVALID_ARG, why);
     Ctx &c = ctx->c;
     if (p->precision != c.prm.precision) return fail(ctx, TP_ERR_INVALID_ARG, "precision is fixed at creation");
-    if (p->precond == TP_PRECOND_SPECTRAL && !c.spectral_ok)
+    if ((p->precond >= TP_PRECOND_SPECTRAL) && !c.spectral_ok)
         return fail(ctx, TP_ERR_UNSUPPORTED, "the spectral preconditioner needs closed polygons");
+    if (p->precond == TP_PRECOND_LEARNED && !c.gnn)
+        return fail(ctx, TP_ERR_UNSUPPORTED, "TP_PRECOND_LEARNED needs a context created with it");
     int indep = c.prm.independent;
     int had_spectral = c.spec != nullptr;
     c.prm = *p;
     c.prm.independent = indep;
     set_kernel_params(c);
-    if (p->precond == TP_PRECOND_SPECTRAL && !had_spectral) {
+    if ((p->precond >= TP_PRECOND_SPECTRAL) && !had_spectral) {
         cudaError_t e = spectral_setup(c, 0);
         if (e == cudaErrorNotSupported) return fail(ctx, TP_ERR_UNSUPPORTED, "spectral preconditioner not built");
         CK(e);
         CK(cudaDeviceSynchronize());
     }
+    if (p->precond >= TP_PRECOND_TWOLEVEL) CK(coarse_init(c));
     return TP_OK;
 }
 
@@ -509,6 +524,24 @@ tp_status tp_constraints(tp_ctx *ctx, const double *gamma, double *phi, tp_strea
     return TP_OK;
 }
 
+// Preconditioner set-up for the geometry in slot 0: diag(A); the Rayleigh-quotient corrected
+// symbols (TP_PRECOND_SPECTRAL_RQ and up); the coarse space (TP_PRECOND_TWOLEVEL and up); the
+// learned term's features and network outputs (TP_PRECOND_LEARNED).
+static tp_status precond_setup(tp_ctx *ctx, const double *gamma, cudaStream_t s)
+{
+    Ctx &c = ctx->c;
+    if (c.prm.precond == TP_PRECOND_LEARNED && !gnn_ready(c))
+        return fail(ctx, TP_ERR_INVALID_ARG, "TP_PRECOND_LEARNED: no network parameters loaded (tp_gnn_set_params)");
+    if (c.prm.precond != TP_PRECOND_NONE) CK(pair_diag(c, gamma, 0, c.d_diag, s));
+    if (c.prm.precond >= TP_PRECOND_SPECTRAL_RQ) CK(spectral_rq_setup(c, gamma, 0, s));
+    if (c.prm.precond >= TP_PRECOND_TWOLEVEL) CK(coarse_setup(c, gamma, 0, s));
+    if (c.prm.precond == TP_PRECOND_LEARNED) {
+        CK(gnn_bind(c, 0, c.d_diag, s));
+        CK(gnn_forward(c, s));
+    }
+    return TP_OK;
+}
+
 tp_status tp_precond_apply(tp_ctx *ctx, const double *gamma, const double *r, double *z, tp_stream stream)
 {
     if (!ctx || !gamma || !r || !z) return TP_ERR_INVALID_ARG;
@@ -516,32 +549,40 @@ tp_status tp_precond_apply(tp_ctx *ctx, const double *gamma, const double *r, do
     Ctx &c = ctx->c;
     tp_status st = records(ctx, gamma, 0, s);
     if (st) return st;
-    if (c.prm.precond != TP_PRECOND_NONE) CK(pair_diag(c, gamma, 0, c.d_diag, s));
+    st = precond_setup(ctx, gamma, s);
+    if (st) return st;
     CK(precond_apply(c, r, z, s, nullptr));
     return TP_OK;
 }
 
-// Preconditioner set-up for the geometry in slot 0.
-static tp_status precond_setup(tp_ctx *ctx, const double *gamma, cudaStream_t s)
+tp_status tp_spectral_symbols(tp_ctx *ctx, int rq, double *out, tp_stream stream)
 {
-    Ctx &c = ctx->c;
-    if (c.prm.precond != TP_PRECOND_NONE) CK(pair_diag(c, gamma, 0, c.d_diag, s));
+    if (!ctx || !out) return TP_ERR_INVALID_ARG;
+    if (!ctx->c.spec) return fail(ctx, TP_ERR_UNSUPPORTED, "no spectral preconditioner in this context");
+    CK(spectral_symbol_copy(ctx->c, rq, out, (cudaStream_t)stream));
     return TP_OK;
 }
+
 
 // H^s gradient of Eq. 22 by the mean-free route: y0 = A^+ dE, y1 = A^+ C_len^T (two CG solves on the
 // mean-free subspace), then the 4x4 correction (schur_gradient).  Needs the Jacobian of `gamma` in
 // c.d_Cv and the preconditioner set up.  Uses d_t3, d_t4, d_t6 as scratch.
 static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE, double *g, int *iters, double *rr,
-                                  int *conv, int *bd, cudaStream_t s)
+                                  int *conv, int *bd, cudaStream_t s, int *n_conv = nullptr)
 {
     int i0 = 0, i1 = 0, c0 = 0, c1 = 0, b0 = 0, b1 = 0;
     double r0 = 0, r1 = 0;
-    cudaError_t e = cg_solve(c, gamma, 0, dE, c.d_t3, c.prm.cg_rtol, c.prm.cg_maxit, &i0, &r0, &c0, &b0, s, 1);
+    std::vector<int> flags(c.nProb, 1);
+    cudaError_t e = cg_solve(c, gamma, 0, dE, c.d_t3, c.prm.cg_rtol, c.prm.cg_maxit, &i0, &r0, &c0, &b0, s, 1,
+                             flags.data());
     if (e != cudaSuccess) return e;
     e = clen_rhs(c, c.d_t6, s);
     if (e != cudaSuccess) return e;
-    e = cg_solve(c, gamma, 0, c.d_t6, c.d_t4, c.prm.cg_rtol, c.prm.cg_maxit, &i1, &r1, &c1, &b1, s, 1);
+    e = cg_solve(c, gamma, 0, c.d_t6, c.d_t4, c.prm.cg_rtol, c.prm.cg_maxit, &i1, &r1, &c1, &b1, s, 1, flags.data());
+    if (n_conv) {
+        *n_conv = 0;
+        for (int f : flags) *n_conv += f;
+    }
     if (e != cudaSuccess) return e;
     e = schur_gradient(c, c.d_t3, c.d_t4, g, s);
     *iters = i0 + i1;
@@ -566,13 +607,14 @@ tp_status sobolev_gradient(tp_ctx *ctx, const double *gamma, const double *dE, d
     CK(constraints_jacobian(c, 0, s));
     st = precond_setup(ctx, gamma, s);
     if (st) return st;
-    int it = 0, conv = 0, bd = 0;
+    int it = 0, conv = 0, bd = 0, nconv = 0;
     double rr = 0.0;
-    CK(gradient_solve(c, gamma, dE, g, &it, &rr, &conv, &bd, s));
+    CK(gradient_solve(c, gamma, dE, g, &it, &rr, &conv, &bd, s, &nconv));
     if (info) {
         info->iters = it;
         info->rel_res = rr;
         info->converged = conv;
+        info->n_converged = nconv;
     }
     st = check_err_word(ctx, s);
     if (st) return st;
@@ -633,9 +675,9 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
     CK(constraints_jacobian(c, 0, s));
     st = precond_setup(ctx, gamma, s);
     if (st) return st;
-    int it = 0, conv = 0, bd = 0;
+    int it = 0, conv = 0, bd = 0, nconv = 0;
     double rr = 0.0;
-    CK(gradient_solve(c, gamma, dE, g, &it, &rr, &conv, &bd, s));
+    CK(gradient_solve(c, gamma, dE, g, &it, &rr, &conv, &bd, s, &nconv));
     if (bd) return fail(ctx, TP_ERR_BREAKDOWN, "CG breakdown in the gradient solve");
     // d = g / |g| per problem, slope = <dE, d>
     CK(vec_dot(c, g, g, gg, s));
@@ -758,9 +800,191 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
         info->proj_cg_iters = proj_cg_total;
         info->accepted = nacc;
         info->rel_res = rr;
+        info->n_converged = nconv;
     }
     if (nacc < nP) return fail(ctx, TP_ERR_LINESEARCH, "line search failed for some problem");
     return TP_OK;
+}
+
+// ---------------------------------------------------------------------------------- learned preconditioner
+
+int tp_gnn_num_params(void) { return gnn_num_params(); }
+
+static tp_status need_gnn(tp_ctx *ctx)
+{
+    if (!ctx) return TP_ERR_INVALID_ARG;
+    if (!ctx->c.gnn) return fail(ctx, TP_ERR_UNSUPPORTED, "the context was not created with TP_PRECOND_LEARNED");
+    return TP_OK;
+}
+
+tp_status tp_gnn_set_params(tp_ctx *ctx, const float *theta, int reset_optimizer, tp_stream stream)
+{
+    tp_status st = need_gnn(ctx);
+    if (st) return st;
+    if (!theta) return fail(ctx, TP_ERR_INVALID_ARG, "null parameter vector");
+    CK(gnn_set_params(ctx->c, theta, reset_optimizer, (cudaStream_t)stream));
+    return TP_OK;
+}
+
+tp_status tp_gnn_get_params(tp_ctx *ctx, float *theta, tp_stream stream)
+{
+    tp_status st = need_gnn(ctx);
+    if (st) return st;
+    if (!theta) return fail(ctx, TP_ERR_INVALID_ARG, "null parameter vector");
+    if (!gnn_ready(ctx->c)) return fail(ctx, TP_ERR_INVALID_ARG, "no parameters loaded");
+    CK(gnn_get_params(ctx->c, theta, (cudaStream_t)stream));
+    return TP_OK;
+}
+
+tp_status tp_gnn_bind(tp_ctx *ctx, const double *gamma, tp_stream stream)
+{
+    tp_status st = need_gnn(ctx);
+    if (st) return st;
+    if (!gamma) return fail(ctx, TP_ERR_INVALID_ARG, "null curve");
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx &c = ctx->c;
+    st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    CK(pair_diag(c, gamma, 0, gnn_diag_buffer(c), s));
+    CK(gnn_bind(c, 0, gnn_diag_buffer(c), s));
+    return TP_OK;
+}
+
+tp_status tp_gnn_forward(tp_ctx *ctx, float *features, float *out, tp_stream stream)
+{
+    tp_status st = need_gnn(ctx);
+    if (st) return st;
+    Ctx &c = ctx->c;
+    if (!gnn_ready(c) || !gnn_bound(c)) return fail(ctx, TP_ERR_INVALID_ARG, "parameters or geometry missing");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(gnn_forward(c, s));
+    if (features) CK(cudaMemcpyAsync(features, gnn_features(c), sizeof(float) * TP_GNN_FEATURES * c.nE,
+                                     cudaMemcpyDeviceToDevice, s));
+    if (out) CK(cudaMemcpyAsync(out, gnn_outputs(c), sizeof(float) * 2 * c.nE, cudaMemcpyDeviceToDevice, s));
+    return TP_OK;
+}
+
+tp_status tp_gnn_backward(tp_ctx *ctx, const float *dout, float *grad, tp_stream stream)
+{
+    tp_status st = need_gnn(ctx);
+    if (st) return st;
+    if (!dout || !grad) return fail(ctx, TP_ERR_INVALID_ARG, "null pointer");
+    if (!gnn_ready(ctx->c) || !gnn_bound(ctx->c)) return fail(ctx, TP_ERR_INVALID_ARG, "parameters or geometry missing");
+    CK(gnn_backward(ctx->c, dout, grad, (cudaStream_t)stream));
+    return TP_OK;
+}
+
+tp_status tp_gnn_adam(tp_ctx *ctx, const float *grad, float lr, tp_stream stream)
+{
+    tp_status st = need_gnn(ctx);
+    if (st) return st;
+    if (!grad || !(lr >= 0.f)) return fail(ctx, TP_ERR_INVALID_ARG, "null gradient or bad learning rate");
+    if (!gnn_ready(ctx->c)) return fail(ctx, TP_ERR_INVALID_ARG, "no parameters loaded");
+    CK(gnn_adam(ctx->c, grad, lr, (cudaStream_t)stream));
+    return TP_OK;
+}
+
+tp_status tp_gnn_g_apply(tp_ctx *ctx, const double *r, double *z, int accumulate, tp_stream stream)
+{
+    tp_status st = need_gnn(ctx);
+    if (st) return st;
+    if (!r || !z) return fail(ctx, TP_ERR_INVALID_ARG, "null pointer");
+    if (!gnn_ready(ctx->c) || !gnn_bound(ctx->c)) return fail(ctx, TP_ERR_INVALID_ARG, "parameters or geometry missing");
+    CK(gnn_gapply(ctx->c, r, z, accumulate, (cudaStream_t)stream, nullptr));
+    return TP_OK;
+}
+
+tp_status tp_gnn_out_grad(tp_ctx *ctx, const double *r, const double *gz, float *dout, int accumulate,
+                          tp_stream stream)
+{
+    tp_status st = need_gnn(ctx);
+    if (st) return st;
+    if (!r || !gz || !dout) return fail(ctx, TP_ERR_INVALID_ARG, "null pointer");
+    if (!gnn_ready(ctx->c) || !gnn_bound(ctx->c)) return fail(ctx, TP_ERR_INVALID_ARG, "parameters or geometry missing");
+    CK(gnn_out_grad(ctx->c, r, gz, 1.0, accumulate, dout, (cudaStream_t)stream));
+    return TP_OK;
+}
+
+tp_status tp_cg_harvest(tp_ctx *ctx, const double *gamma, const double *rhs, int every, int max_pairs, double *R,
+                        double *E, int *n_pairs, tp_solve_info *info, tp_stream stream)
+{
+    if (!ctx || !gamma || !rhs || !n_pairs || every < 1 || max_pairs < 0 || (max_pairs > 0 && (!R || !E)))
+        return fail(ctx, TP_ERR_INVALID_ARG, "bad harvest arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx &c = ctx->c;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    st = precond_setup(ctx, gamma, s);
+    if (st) return st;
+    c.hv.R = max_pairs > 0 ? R : nullptr;
+    c.hv.Y = E;
+    c.hv.every = every;
+    c.hv.max = max_pairs;
+    c.hv.n = 0;
+    int it = 0, conv = 0, bd = 0;
+    double rr = 0.0;
+    cudaError_t e = cg_solve(c, gamma, 0, rhs, c.d_t3, c.prm.cg_rtol, c.prm.cg_maxit, &it, &rr, &conv, &bd, s, 1);
+    const int n = c.hv.n;
+    c.hv = Ctx::Harvest{};
+    CK(e);
+    // exact corrections: e_k = y* - y_k (every iterate lies in the mean-free subspace)
+    const size_t nv3 = 3 * (size_t)c.nV;
+    for (int k = 0; k < n; ++k) CK(vec_axpby(c, 1.0, c.d_t3, -1.0, E + k * nv3, E + k * nv3, s));
+    *n_pairs = n;
+    if (info) {
+        info->iters = it;
+        info->rel_res = rr;
+        info->converged = conv;
+        info->n_converged = conv ? c.nProb : 0;
+    }
+    st = check_err_word(ctx, s);
+    if (st) return st;
+    if (bd) return fail(ctx, TP_ERR_BREAKDOWN, "CG breakdown: p^T A p <= 0");
+    return TP_OK;
+}
+
+tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, const double *R, double *E, double *B,
+                               double *AB, double *ER, tp_stream stream)
+{
+    if (!ctx || !gamma || n < 0 || (n > 0 && (!R || !E || !B || !AB || !ER)))
+        return fail(ctx, TP_ERR_INVALID_ARG, "bad pair arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx &c = ctx->c;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    st = precond_setup(ctx, gamma, s);
+    if (st) return st;
+    const size_t nv3 = 3 * (size_t)c.nV;
+    for (int k = 0; k < n; ++k) {
+        const double *r = R + k * nv3;
+        double *b = B + k * nv3;
+        CK(gnn_problem_dot(c, E + k * nv3, r, ER + (size_t)k * c.nProb, s));  // before B may overwrite E
+        CK(precond_apply_base(c, r, b, s, nullptr));
+        if (c.prm.precond != TP_PRECOND_NONE) CK(project_mean(c, b, s, nullptr));
+        CK(pair_apply(c, gamma, 0, b, AB + k * nv3, s));
+    }
+    return TP_OK;
+}
+
+tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, const double *R, const double *B,
+                            const double *AB, const double *ER, float lr, double *loss, float *grad,
+                            tp_stream stream)
+{
+    tp_status st = need_gnn(ctx);
+    if (st) return st;
+    if (!gamma || n < 1 || !R || !B || !AB || !ER || !(lr >= 0.f))
+        return fail(ctx, TP_ERR_INVALID_ARG, "bad training arguments");
+    Ctx &c = ctx->c;
+    if (!gnn_ready(c) || !gnn_bound(c)) return fail(ctx, TP_ERR_INVALID_ARG, "parameters or geometry missing");
+    cudaStream_t s = (cudaStream_t)stream;
+    st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    CK(gnn_train_step(c, gamma, n, R, B, AB, ER, lr, c.d_scal, s));
+    if (grad) CK(cudaMemcpyAsync(grad, gnn_last_grad(c), sizeof(float) * gnn_num_params(), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c.h_pinned, c.d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (loss) *loss = c.h_pinned[0];
+    return check_err_word(ctx, s);
 }
 
 }  // extern "C"

@@ -1,0 +1,285 @@
+// Coarse-space correction of the spectral preconditioner (TP_PRECOND_TWOLEVEL; not from the paper).
+//
+// The Rayleigh-quotient corrected circulant fixes the spectrum of A mode by mode, but A is not
+// circulant: its slowest modes on a knotted curve are global low-frequency deformations whose
+// stiffness depends on where the curve comes close to itself.  An additive two-level term fixes them:
+//
+//   M^-1 = M_spectral^-1 + Z (Z^T A Z)^-1 Z^T,
+//
+// Z = the m - 1 first of m periodic hat functions per closed curve (centres i = j n / m, support of
+// two hat widths; the m hats sum to 1, so the dropped one is implied on the mean-free subspace).
+// Z^T A Z is assembled with (m - 1) / 3 applies of the pair kernel (three hats per apply, one per
+// component) and Cholesky-factored per curve in FP64.  Per CG iteration the term costs three O(n)
+// kernels: restriction Z^T r, the (m - 1) x (m - 1) triangular solves, prolongation Z y.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "tpe_internal.cuh"
+
+namespace tpe {
+
+#define TPE_CHECK(x)                      \
+    do {                                  \
+        cudaError_t e_ = (x);             \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
+constexpr int kMaxCoarse = 64;
+
+struct CoarseCurve {
+    int v0, n, m;  // hats j = 0 .. m-2 are the basis
+    int pad;
+    long long aoff, woff;  // offsets of the factor [(m-1)^2] and of the coarse vectors [(m-1) x 3]
+};
+
+}  // namespace tpe
+
+struct tpe::CoarseState {
+    std::vector<CoarseCurve> curves;
+    CoarseCurve *d_curves = nullptr;
+    int *d_vcurve = nullptr;
+    double *d_L = nullptr;  // Cholesky factors (lower, row-major) per curve
+    double *d_w = nullptr;  // coarse vectors
+    int max_m = 0;
+    int ready = 0;
+};
+
+namespace tpe {
+
+// hat j of a curve with n vertices and m hats at local vertex i (periodic)
+__device__ __forceinline__ double hat(int i, int j, int n, int m)
+{
+    double t = (double)i * m / n;
+    double d = fabs(t - j);
+    d = fmin(d, m - d);
+    return fmax(0.0, 1.0 - d);
+}
+
+// local index range [lo, lo + len) (mod n) covering the support of hat j
+__device__ __forceinline__ void hat_support(int j, int n, int m, int &lo, int &len)
+{
+    lo = (int)floor((double)(j - 1) * n / m) - 1;
+    len = (int)ceil(2.0 * n / m) + 3;
+    if (len > n) {
+        lo = 0;
+        len = n;
+    }
+}
+
+__global__ void k_coarse_probe(int nV, int b, const CoarseCurve *__restrict__ cc, const int *__restrict__ vcurve,
+                               double *__restrict__ y)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    const CoarseCurve C = cc[vcurve[v]];
+    int i = v - C.v0;
+    for (int q = 0; q < 3; ++q) {
+        int l = 3 * b + q;
+        y[3 * v + q] = (l < C.m - 1) ? hat(i, l, C.n, C.m) : 0.0;
+    }
+}
+
+// Ac[j][3b + q] = Z_j^T (A Z_{3b+q}): one block per (curve, j)
+__global__ void k_coarse_gram(int b, const CoarseCurve *__restrict__ cc, const double *__restrict__ AZ,
+                              double *__restrict__ L)
+{
+    const CoarseCurve C = cc[blockIdx.x];
+    const int j = blockIdx.y;
+    const int mm = C.m - 1;
+    if (j >= mm) return;
+    int lo, len;
+    hat_support(j, C.n, C.m, lo, len);
+    __shared__ double sh[3][128];
+    double s[3] = {0, 0, 0};
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+        int i = ((lo + k) % C.n + C.n) % C.n;
+        double z = hat(i, j, C.n, C.m);
+        for (int q = 0; q < 3; ++q) s[q] += z * AZ[3 * (C.v0 + i) + q];
+    }
+    for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 3; ++q) {
+            int l = 3 * b + q;
+            if (l < mm) L[C.aoff + (long long)j * mm + l] = sh[q][0];
+        }
+}
+
+// symmetrise and Cholesky-factor every curve's coarse matrix in place (one block per curve)
+__global__ void k_coarse_factor(const CoarseCurve *__restrict__ cc, double *__restrict__ L)
+{
+    const CoarseCurve C = cc[blockIdx.x];
+    const int mm = C.m - 1;
+    __shared__ double a[kMaxCoarse * kMaxCoarse];
+    double *g = L + C.aoff;
+    for (int t = threadIdx.x; t < mm * mm; t += blockDim.x) {
+        int r = t / mm, col = t % mm;
+        a[r * mm + col] = 0.5 * (g[r * mm + col] + g[col * mm + r]);
+    }
+    __syncthreads();
+    for (int k = 0; k < mm; ++k) {
+        if (threadIdx.x == 0) {
+            double d = a[k * mm + k];
+            a[k * mm + k] = d > 0.0 ? sqrt(d) : 1e-150;
+        }
+        __syncthreads();
+        double dk = a[k * mm + k];
+        for (int r = k + 1 + threadIdx.x; r < mm; r += blockDim.x) a[r * mm + k] /= dk;
+        __syncthreads();
+        for (int t = threadIdx.x; t < (mm - k - 1) * (mm - k - 1); t += blockDim.x) {
+            int r = k + 1 + t / (mm - k - 1), col = k + 1 + t % (mm - k - 1);
+            if (col <= r) a[r * mm + col] -= a[r * mm + k] * a[col * mm + k];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < mm * mm; t += blockDim.x) g[t] = a[t];
+}
+
+// w[j][q] = Z_j^T r: one block per (curve, j)
+__global__ void k_coarse_restrict(const CoarseCurve *__restrict__ cc, const double *__restrict__ r,
+                                  double *__restrict__ w)
+{
+    const CoarseCurve C = cc[blockIdx.x];
+    const int j = blockIdx.y;
+    if (j >= C.m - 1) return;
+    int lo, len;
+    hat_support(j, C.n, C.m, lo, len);
+    __shared__ double sh[3][128];
+    double s[3] = {0, 0, 0};
+    for (int k = threadIdx.x; k < len; k += blockDim.x) {
+        int i = ((lo + k) % C.n + C.n) % C.n;
+        double z = hat(i, j, C.n, C.m);
+        for (int q = 0; q < 3; ++q) s[q] += z * r[3 * (C.v0 + i) + q];
+    }
+    for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int wv = 64; wv > 0; wv >>= 1) {
+        if (threadIdx.x < wv)
+            for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + wv];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 3; ++q) w[C.woff + 3 * j + q] = sh[q][0];
+}
+
+// y = (L L^T)^-1 w per curve and component (three threads per curve block, one per component)
+__global__ void k_coarse_solve(const CoarseCurve *__restrict__ cc, const double *__restrict__ L, double *__restrict__ w)
+{
+    const CoarseCurve C = cc[blockIdx.x];
+    const int q = threadIdx.x;
+    if (q >= 3) return;
+    const int mm = C.m - 1;
+    const double *a = L + C.aoff;
+    double *y = w + C.woff;
+    for (int r = 0; r < mm; ++r) {  // L z = w
+        double s = y[3 * r + q];
+        for (int k = 0; k < r; ++k) s -= a[r * mm + k] * y[3 * k + q];
+        y[3 * r + q] = s / a[r * mm + r];
+    }
+    for (int r = mm - 1; r >= 0; --r) {  // L^T y = z
+        double s = y[3 * r + q];
+        for (int k = r + 1; k < mm; ++k) s -= a[k * mm + r] * y[3 * k + q];
+        y[3 * r + q] = s / a[r * mm + r];
+    }
+}
+
+// z[v] += sum_j Z_j(i) y_j (each vertex lies in at most two hats)
+__global__ void k_coarse_prolong(int nV, const CoarseCurve *__restrict__ cc, const int *__restrict__ vcurve,
+                                 const double *__restrict__ w, double *__restrict__ z)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    const CoarseCurve C = cc[vcurve[v]];
+    int i = v - C.v0;
+    double t = (double)i * C.m / C.n;
+    int j0 = (int)floor(t);
+    double acc[3] = {0, 0, 0};
+    for (int dj = 0; dj <= 1; ++dj) {
+        int j = (j0 + dj) % C.m;
+        if (j >= C.m - 1) continue;
+        double h = hat(i, j, C.n, C.m);
+        for (int q = 0; q < 3; ++q) acc[q] += h * w[C.woff + 3 * j + q];
+    }
+    for (int q = 0; q < 3; ++q) z[3 * v + q] += acc[q];
+}
+
+cudaError_t coarse_init(Ctx &c)
+{
+    if (c.coarse) return cudaSuccess;
+    c.coarse = new CoarseState();
+    CoarseState &S = *c.coarse;
+    long long aoff = 0, woff = 0;
+    std::vector<int> vc(c.nV);
+    for (int k = 0; k < c.nCurves; ++k) {
+        CoarseCurve C{};
+        C.v0 = c.h_voff[k];
+        C.n = c.h_voff[k + 1] - C.v0;
+        C.m = std::max(2, std::min(std::min(c.prm.coarse_dim, kMaxCoarse), C.n / 4));
+        C.aoff = aoff;
+        C.woff = woff;
+        aoff += (long long)(C.m - 1) * (C.m - 1);
+        woff += 3LL * (C.m - 1);
+        S.max_m = std::max(S.max_m, C.m);
+        S.curves.push_back(C);
+        for (int v = C.v0; v < C.v0 + C.n; ++v) vc[v] = k;
+    }
+    TPE_CHECK(cudaMalloc(&S.d_curves, sizeof(CoarseCurve) * S.curves.size()));
+    TPE_CHECK(cudaMemcpy(S.d_curves, S.curves.data(), sizeof(CoarseCurve) * S.curves.size(), cudaMemcpyHostToDevice));
+    TPE_CHECK(cudaMalloc(&S.d_vcurve, sizeof(int) * c.nV));
+    TPE_CHECK(cudaMemcpy(S.d_vcurve, vc.data(), sizeof(int) * c.nV, cudaMemcpyHostToDevice));
+    TPE_CHECK(cudaMalloc(&S.d_L, sizeof(double) * std::max<long long>(1, aoff)));
+    TPE_CHECK(cudaMalloc(&S.d_w, sizeof(double) * std::max<long long>(1, woff)));
+    return cudaSuccess;
+}
+
+void coarse_free(Ctx &c)
+{
+    if (!c.coarse) return;
+    cudaFree(c.coarse->d_curves);
+    cudaFree(c.coarse->d_vcurve);
+    cudaFree(c.coarse->d_L);
+    cudaFree(c.coarse->d_w);
+    delete c.coarse;
+    c.coarse = nullptr;
+}
+
+// Z^T A Z of the curve `gamma_geom` (geometry slot `which`) and its factors; uses c.d_y, c.d_q.
+cudaError_t coarse_setup(Ctx &c, const double *gamma_geom, int which, cudaStream_t s)
+{
+    TPE_CHECK(coarse_init(c));
+    CoarseState &S = *c.coarse;
+    const int nb = (c.nV + 255) / 256;
+    const int nbatch = (S.max_m - 1 + 2) / 3;
+    for (int b = 0; b < nbatch; ++b) {
+        k_coarse_probe<<<nb, 256, 0, s>>>(c.nV, b, S.d_curves, S.d_vcurve, c.d_y);
+        c.launches++;
+        TPE_CHECK(pair_apply(c, gamma_geom, which, c.d_y, c.d_q, s));
+        k_coarse_gram<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(b, S.d_curves, c.d_q, S.d_L);
+        c.launches++;
+    }
+    k_coarse_factor<<<c.nCurves, 256, 0, s>>>(S.d_curves, S.d_L);
+    c.launches++;
+    S.ready = 1;
+    return cudaGetLastError();
+}
+
+// z += Z (Z^T A Z)^-1 Z^T r
+cudaError_t coarse_apply(Ctx &c, const double *r, double *z, cudaStream_t s)
+{
+    if (!c.coarse || !c.coarse->ready) return cudaSuccess;
+    CoarseState &S = *c.coarse;
+    k_coarse_restrict<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(S.d_curves, r, S.d_w);
+    k_coarse_solve<<<c.nCurves, 32, 0, s>>>(S.d_curves, S.d_L, S.d_w);
+    k_coarse_prolong<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_w, z);
+    c.launches += 3;
+    return cudaGetLastError();
+}
+
+}  // namespace tpe

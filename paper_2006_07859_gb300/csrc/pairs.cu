@@ -374,6 +374,7 @@ struct PairArgs {
     double *part;  // [slot][nE][stride]
     int nE;
     KernelParams kp;
+    const int *skip;  // per-problem flags: items of flagged problems are skipped (may be NULL)
 };
 
 template <int PREC, int OP>
@@ -388,6 +389,7 @@ template <int PREC>
 struct Acc32<PREC, OP_DIFF> {
     static constexpr int op = OP_DIFF;
     typename RealOf<PREC>::type S, G1[3], G2[3], GT[3];
+    typename RealOf<PREC>::type cS, c1[3], c2[3], cT[3];  // Kahan compensations (mixed path)
 };
 template <int PREC>
 struct Acc32<PREC, OP_APPLY> {
@@ -455,6 +457,55 @@ __device__ __forceinline__ void load_uval(UVal<typename RealOf<PREC>::type> &v, 
     }
 }
 
+
+// Differential of one near pair in FP64 from the double-float positions and tangents, accumulated
+// straight into the FP64 accumulators: along the curve the near-pair gradient terms are large and
+// cancel between neighbours, so they need FP64 both in the arithmetic and in the sum.
+__device__ __noinline__ void near_diff_df(const Tgt<float> &t, const Src<PMIX> &s, double alpha, double beta,
+                                          bool fast, DiffAcc64 &acc)
+{
+    double TI[3] = {(double)t.T.x + t.Tl.x, (double)t.T.y + t.Tl.y, (double)t.T.z + t.Tl.z};
+    double TJ[3] = {(double)s.T.x + s.Tm.x, (double)s.T.y + s.Tm.y, (double)s.T.z + s.Tm.z};
+    double L = s.ell;
+    for (int ab = 0; ab < 4; ++ab) {
+        V3<float> P = (ab < 2) ? t.p1 : t.p2, PL = (ab < 2) ? t.l1 : t.l2;
+        V3<float> Q = (ab & 1) ? s.q2 : s.q1, QL = (ab & 1) ? s.m2 : s.m1;
+        double d[3] = {(double)(P.x - Q.x) + (double)(PL.x - QL.x), (double)(P.y - Q.y) + (double)(PL.y - QL.y),
+                       (double)(P.z - Q.z) + (double)(PL.z - QL.z)};
+        double tI = TI[0] * d[0] + TI[1] * d[1] + TI[2] * d[2];
+        double tJ = TJ[0] * d[0] + TJ[1] * d[1] + TJ[2] * d[2];
+        double dpI[3], dpJ[3];
+        for (int k = 0; k < 3; ++k) {
+            dpI[k] = d[k] - tI * TI[k];
+            dpJ[k] = d[k] - tJ * TJ[k];
+        }
+        double cI2 = dpI[0] * dpI[0] + dpI[1] * dpI[1] + dpI[2] * dpI[2];
+        double cJ2 = dpJ[0] * dpJ[0] + dpJ[1] * dpJ[1] + dpJ[2] * dpJ[2];
+        double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double rb, fI, fJ, aI, aJ;
+        if (fast) {
+            double r = rsqrt(d2), r2 = r * r;
+            rb = r2 * r2 * sqrt(r);
+            fI = cI2 * rb;
+            fJ = cJ2 * rb;
+            aI = aJ = 2.0 * rb;
+        } else {
+            rb = pow(d2, -0.5 * beta);
+            fI = (cI2 > 0.0 ? pow(cI2, 0.5 * alpha) : 0.0) * rb;
+            fJ = (cJ2 > 0.0 ? pow(cJ2, 0.5 * alpha) : 0.0) * rb;
+            aI = cI2 > 0.0 ? alpha * fI / cI2 : 0.0;
+            aJ = cJ2 > 0.0 ? alpha * fJ / cJ2 : 0.0;
+        }
+        double cb = beta * (fI + fJ) / d2;
+        double *G = ab < 2 ? acc.G1 : acc.G2;
+        for (int k = 0; k < 3; ++k) {
+            G[k] += L * (aI * dpI[k] + aJ * dpJ[k] - cb * d[k]);
+            acc.GT[k] += -L * aI * tI * d[k];
+        }
+        acc.S += L * (fI + fJ);
+    }
+}
+
 // One (target, source) pair: accumulate into the tile accumulator a.
 // DF: use the low parts (double-float differences) and compensated accumulation; only the mixed
 // path's MID and NEAR tiles set it.
@@ -471,6 +522,17 @@ __device__ __forceinline__ float perp2_near(V3<float> P, V3<float> PL, V3<float>
     double t = tx * dx + ty * dy + tz * dz;
     double px = dx - t * tx, py = dy - t * ty, pz = dz - t * tz;
     return (float)(px * px + py * py + pz * pz);
+}
+
+// Target-side |T x d|^2 with the double-float tangent T + Tl: a rounding error of T_I is the same for
+// every source J, so it does not average out, and the vertex gather of the differential amplifies it
+// by ~1 / (kappa l).  The source-side tangent's rounding is shared by the two edges at a vertex and
+// cancels there.
+__device__ __forceinline__ float perp2_df(V3<float> d, V3<float> T, V3<float> Tl, float &t, V3<float> &dp)
+{
+    t = fmaf(T.x, d.x, fmaf(T.y, d.y, fmaf(T.z, d.z, dot3(Tl, d))));
+    dp = {fmaf(-t, T.x, fmaf(-t, Tl.x, d.x)), fmaf(-t, T.y, fmaf(-t, Tl.y, d.y)), fmaf(-t, T.z, fmaf(-t, Tl.z, d.z))};
+    return dot3(dp, dp);
 }
 
 template <int PREC, int OP, bool FAST, bool DF = (PREC == PMIX)>
@@ -506,7 +568,11 @@ __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type>
             V3<R> Q = (ab & 1) ? s.q2 : s.q1, QL = (ab & 1) ? s.m2 : s.m1;
             V3<R> d = diff3<DF>(P, PL, Q, QL), dpI, dpJ;
             R tI, tJ;
-            R cI2 = perp2(d, t.T, tI, dpI), cJ2 = perp2(d, s.T, tJ, dpJ), d2 = dot3(d, d);
+            R cI2, cJ2 = perp2(d, s.T, tJ, dpJ), d2 = dot3(d, d);
+            if constexpr (DF && sizeof(R) == 4)
+                cI2 = perp2_df(d, t.T, t.Tl, tI, dpI);
+            else
+                cI2 = perp2(d, t.T, tI, dpI);
             if constexpr (DF && sizeof(R) == 4)
                 if (near) {
                     cI2 = perp2_near(P, PL, Q, QL, t.T, t.Tl);
@@ -543,11 +609,22 @@ __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type>
             for (int k = 0; k < 3; ++k) G1[k] = G2[k] = GT[k] = 0;
         }
         R L = keep ? s.ell : (R)0;
-        a.S += L * S;
-        for (int k = 0; k < 3; ++k) {
-            a.G1[k] += L * G1[k];
-            a.G2[k] += L * G2[k];
-            a.GT[k] += L * GT[k];
+        if constexpr (PREC == PMIX) {
+            // compensated: the vertex gather takes differences of neighbouring edges' rows, which
+            // cancel by ~1 / (kappa l), so the rows need more than FP32 summation accuracy
+            kahan_add(a.S, a.cS, L * S);
+            for (int k = 0; k < 3; ++k) {
+                kahan_add(a.G1[k], a.c1[k], L * G1[k]);
+                kahan_add(a.G2[k], a.c2[k], L * G2[k]);
+                kahan_add(a.GT[k], a.cT[k], L * GT[k]);
+            }
+        } else {
+            a.S += L * S;
+            for (int k = 0; k < 3; ++k) {
+                a.G1[k] += L * G1[k];
+                a.G2[k] += L * G2[k];
+                a.GT[k] += L * GT[k];
+            }
         }
     } else {  // OP_APPLY / OP_DIAG
         // the four trapezoid terms are summed as (11 + 22) + (12 + 21), an order that is the same
@@ -623,8 +700,8 @@ __device__ __forceinline__ void acc_zero(Acc32<PREC, OP> &a)
     if constexpr (OP == OP_ENERGY) {
         a.s = 0;
     } else if constexpr (OP == OP_DIFF) {
-        a.S = 0;
-        for (int k = 0; k < 3; ++k) a.G1[k] = a.G2[k] = a.GT[k] = 0;
+        a.S = a.cS = 0;
+        for (int k = 0; k < 3; ++k) a.G1[k] = a.G2[k] = a.GT[k] = a.c1[k] = a.c2[k] = a.cT[k] = 0;
     } else if constexpr (OP == OP_APPLY) {
         for (int k = 0; k < 3; ++k) a.A1[k] = a.A2[k] = a.C1[k] = a.C2[k] = 0;
     } else {
@@ -653,11 +730,12 @@ __device__ __forceinline__ void acc_add(X &A, const Y &a)
     if constexpr (OPX == OP_ENERGY) {
         A.s += a.s;
     } else if constexpr (OPX == OP_DIFF) {
-        A.S += a.S;
+        // tile fold into FP64: value minus its compensation
+        A.S += (double)a.S - (double)a.cS;
         for (int k = 0; k < 3; ++k) {
-            A.G1[k] += a.G1[k];
-            A.G2[k] += a.G2[k];
-            A.GT[k] += a.GT[k];
+            A.G1[k] += (double)a.G1[k] - (double)a.c1[k];
+            A.G2[k] += (double)a.G2[k] - (double)a.c2[k];
+            A.GT[k] += (double)a.GT[k] - (double)a.cT[k];
         }
     } else if constexpr (OPX == OP_APPLY) {
         if constexpr (std::is_same_v<X, Acc64<OP_APPLY>>) {
@@ -719,10 +797,18 @@ __device__ __forceinline__ void tile_loop(const Tgt<typename RealOf<PREC>::type>
             if constexpr (PREC == PMIX && MODE < 2) {
                 pair_eval<PREC, OP, FAST, MODE == 1>(tg[k], s, a[k], keep, pa.kp, d2_11, &tu[k], &su);
             } else if constexpr (PREC == PMIX) {
-                // near pairs (|g_i1 - g_j1| below the cutoff) take |T x d|^2 in FP64
+                // near pairs (|g_i1 - g_j1| below the cutoff) take |T x d|^2 in FP64; the differential
+                // evaluates and accumulates the whole near pair in FP64
                 V3<float> e = diff3<true>(tg[k].p1, tg[k].l1, s.q1, s.m1);
-                bool near = keep && (dot3(e, e) < pa.kp.near2f);
-                pair_eval<PREC, OP, FAST, true>(tg[k], s, a[k], keep, pa.kp, d2_11, &tu[k], &su, near);
+                bool near = keep && (dot3(e, e) < (OP == OP_DIFF ? pa.kp.near2f_diff : pa.kp.near2f));
+                if constexpr (OP == OP_DIFF) {
+                    if (near)
+                        near_diff_df(tg[k], s, pa.kp.alpha, pa.kp.beta, FAST, A[k]);
+                    else
+                        pair_eval<PREC, OP, FAST, true>(tg[k], s, a[k], keep, pa.kp, d2_11, &tu[k], &su, false);
+                } else {
+                    pair_eval<PREC, OP, FAST, true>(tg[k], s, a[k], keep, pa.kp, d2_11, &tu[k], &su, near);
+                }
             } else {
                 pair_eval<PREC, OP, FAST>(tg[k], s, a[k], keep, pa.kp, d2_11, &tu[k], &su);
             }
@@ -773,6 +859,7 @@ __global__ void __launch_bounds__(kThreads, PREC == P64 ? 1 : 3) k_pairs(const P
         __syncthreads();
         if (it >= pa.n_items) break;
         const WorkItem w = pa.items[it];
+        if (pa.skip && pa.skip[w.pad]) continue;  // problem already converged: its output is not used
         Tgt<R> tg[TPT];
         UVal<R> tu[TPT];
         int tI[TPT];
@@ -835,7 +922,8 @@ __global__ void __launch_bounds__(kThreads, PREC == P64 ? 1 : 3) k_pairs(const P
                     float gap = fmaxf(fmaxf(sb[q] - tbox[3 + q], tbox[q] - sb[3 + q]), 0.f);
                     g2 += gap * gap;
                 }
-                mode = (g2 < pa.kp.near2f) ? 2 : (g2 < pa.kp.mid2f ? 1 : 0);
+                const float nr2 = (OP == OP_DIFF) ? pa.kp.near2f_diff : pa.kp.near2f;
+                mode = (g2 < nr2) ? 2 : (g2 < pa.kp.mid2f ? 1 : 0);
                 // In the Gram weights |T x d|^2 enters only the low-order weight w0, whose near-pair
                 // entries are ~(kappa l)^2 / 4 of the high-order ones, so FP32 double-float accuracy
                 // suffices there: no FP64 near path for apply / diag.
@@ -1012,7 +1100,7 @@ static void plan_pass(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy)
                 }
             for (int k = 0; k < nch; ++k) {
                 int s0 = e0 + k * clen, s1 = std::min(e1, s0 + clen);
-                WorkItem w{t0, nt, s0, s1, k, lo, hi, 0};
+                WorkItem w{t0, nt, s0, s1, k, lo, hi, q};
                 tmp.push_back({w, (double)nt * (s1 - s0)});
             }
         }
@@ -1178,6 +1266,7 @@ cudaError_t static_energy_launch(const double *gamma, const int *edges, int nV, 
     double rn = near_cutoff * st[0];
     kp.near2 = rn * rn;
     kp.near2f = (float)(rn * rn);
+    kp.near2f_diff = (float)(16.0 * rn * rn);
     kp.mid2f = 3.0e38f;  // double-float positions in every tile (the context's default)
     // blocking: targets per item = kThreads * kTptEnergy, at least 8 source tiles per item
     int dev = 0, sms = 0, occ = 0;
@@ -1210,6 +1299,7 @@ cudaError_t static_energy_launch(const double *gamma, const int *edges, int nV, 
     pa.part = part;
     pa.nE = nE;
     pa.kp = kp;
+    pa.skip = nullptr;
     const int grid = std::max(1, std::min(nit, sms * std::max(1, occ)));
     if (kp.fast)
         k_pairs<PMIX, OP_ENERGY, kTptEnergy, true><<<grid, kThreads, 0, s>>>(pa);
@@ -1265,9 +1355,12 @@ static cudaError_t run_pairs(Ctx &c, int which, const double *gamma, const doubl
     pa.part = c.d_part;
     pa.nE = c.nE;
     pa.kp = c.kp;
+    pa.skip = (OP == OP_APPLY) ? c.d_skip : nullptr;
     const int g = pl.grid;
     const bool f = c.kp.fast != 0;
-    const int slot = c.profile ? prof_begin(c, OP, s) : -1;
+    // profiling: applies that skip converged problems are recorded apart (op 4), so op 2 always
+    // times full passes of pairs_per_pass pairs
+    const int slot = c.profile ? prof_begin(c, (OP == OP_APPLY && c.d_skip) ? 4 : OP, s) : -1;
     switch (c.prm.precision) {
     case TP_FP64:
         if (f) k_pairs<P64, OP, (OP == OP_ENERGY ? kTptEnergy64 : OP == OP_DIFF ? kTptDiff64 : kTptApply64), true><<<g, kThreads, 0, s>>>(pa);

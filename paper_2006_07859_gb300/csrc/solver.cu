@@ -461,7 +461,8 @@ __global__ void k_jacobi(int nV, const double *__restrict__ diag, const double *
 
 cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip);
 
-cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip)
+// M^-1 r without the learned term (TP_PRECOND_LEARNED: the two-level part).
+cudaError_t precond_apply_base(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip)
 {
     switch (c.prm.precond) {
     case TP_PRECOND_JACOBI:
@@ -469,10 +470,26 @@ cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, co
         c.launches++;
         return cudaGetLastError();
     case TP_PRECOND_SPECTRAL:
+    case TP_PRECOND_SPECTRAL_RQ:
         return spectral_apply(c, r, z, s, skip);
+    case TP_PRECOND_TWOLEVEL:
+    case TP_PRECOND_LEARNED: {
+        cudaError_t e = spectral_apply(c, r, z, s, skip);
+        if (e != cudaSuccess) return e;
+        return coarse_apply(c, r, z, s);
+    }
     default:
         return cudaMemcpyAsync(z, r, sizeof(double) * 3 * c.nV, cudaMemcpyDeviceToDevice, s);
     }
+}
+
+// M^-1 r of the configured preconditioner; TP_PRECOND_LEARNED adds the learned term G r.
+cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip)
+{
+    cudaError_t e = precond_apply_base(c, r, z, s, skip);
+    if (e != cudaSuccess || c.prm.precond != TP_PRECOND_LEARNED) return e;
+    if (!gnn_ready(c) || !gnn_bound(c)) return cudaErrorNotReady;
+    return gnn_gapply(c, r, z, 1, s, skip);
 }
 
 // ---------------------------------------------------------------------------------- CG
@@ -629,7 +646,7 @@ static cudaError_t projector(Ctx &c, int mode, double *v, cudaStream_t s, const 
 
 cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
                      int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s,
-                     int proj_mode)
+                     int proj_mode, int *conv_flags)
 {
     SolverState &st = S(c);
     const size_t vb = sizeof(double) * 3 * c.nV;
@@ -649,8 +666,11 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
     int it = 0;
     int *h_active = c.h_pinned_i;
     for (; it < maxit;) {
-        // q = P A-bar p
-        TPE_CHECK(pair_apply(c, gamma_geom, which, p, q, s));
+        // q = P A-bar p (work items of converged problems are skipped)
+        c.d_skip = st.done;
+        cudaError_t ea = pair_apply(c, gamma_geom, which, p, q, s);
+        c.d_skip = nullptr;
+        TPE_CHECK(ea);
         TPE_CHECK(projector(c, proj_mode, q, s, st.done));
         k_cg_alpha<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 5), p, q, c.d_cg, st.done);
         k_cg_update<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 6), c.d_vprob, p, q, y, r, c.d_cg, st.done, tol2,
@@ -663,6 +683,12 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
         k_cg_p<<<nb, 256, 0, s>>>(c.nV, c.d_vprob, c.prm.precond != TP_PRECOND_NONE ? z : r, p, c.d_cg, st.done);
         c.launches += 2;
         ++it;
+        if (c.hv.R && c.hv.n < c.hv.max && it % c.hv.every == 0) {
+            const size_t off = (size_t)c.hv.n * 3 * c.nV;
+            TPE_CHECK(cudaMemcpyAsync(c.hv.R + off, r, vb, cudaMemcpyDeviceToDevice, s));
+            TPE_CHECK(cudaMemcpyAsync(c.hv.Y + off, y, vb, cudaMemcpyDeviceToDevice, s));
+            c.hv.n++;
+        }
         if (it % every == 0 || it == maxit) {
             TPE_CHECK(cudaMemcpyAsync(h_active, st.active, sizeof(int), cudaMemcpyDeviceToHost, s));
             TPE_CHECK(cudaStreamSynchronize(s));
@@ -688,7 +714,9 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
     for (int qq = 0; qq < c.nProb; ++qq) {
         mx_it = std::max(mx_it, hcg[qq].iters);
         bd |= hcg[qq].breakdown;
-        conv &= (hcg[qq].done && !hcg[qq].breakdown) ? 1 : 0;
+        int ok = (hcg[qq].done && !hcg[qq].breakdown) ? 1 : 0;
+        conv &= ok;
+        if (conv_flags) conv_flags[qq] &= ok;
         mx_rr = std::max(mx_rr, hrr[qq]);
     }
     if (iters) *iters = mx_it;

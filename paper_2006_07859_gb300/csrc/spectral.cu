@@ -41,9 +41,11 @@ enum SpecKind { SK_POW2 = 0, SK_BLUESTEIN = 1, SK_FOURSTEP = 2 };
 
 struct SpecCurve {
     int v0, n, M, logM;  // M: FFT size (pow2: n; Bluestein: pow2 >= 2n-1; four-step: N1)
-    int kind, N2, logN2, pad;
+    int kind, N2, logN2, nk;  // nk: number of sampled frequencies of the Rayleigh-quotient correction
     long long sym_off, chirp_off, bhat_off;  // offsets into the symbol / chirp / B-hat tables
 };
+
+constexpr int kMaxRQ = 24;  // sampled frequencies per curve for the Rayleigh-quotient symbol
 
 }  // namespace tpe
 
@@ -60,6 +62,13 @@ struct tpe::SpecState {
     double2 *d_buf0 = nullptr, *d_buf1 = nullptr;  // four-step workspace [3][n_large]
     double *d_dinv = nullptr;    // [nV] D^-1/2
     std::map<int, long long> sym_of_n;
+    // Rayleigh-quotient corrected symbols (precond TP_PRECOND_SPECTRAL_RQ), one per curve at its vertex offset
+    double *d_sym_rq = nullptr;  // [nV]
+    int *d_klist = nullptr;      // [nCurves][kMaxRQ] sampled frequencies
+    double *d_rq = nullptr;      // [nCurves][2 kMaxRQ] Rayleigh numerators (cos, sin)
+    int *d_vcurve = nullptr;     // [nV] curve of each vertex
+    int max_nk = 0;
+    int rq_ready = 0;
 };
 
 namespace tpe {
@@ -129,15 +138,19 @@ __global__ void __launch_bounds__(kFFTThreads) k_spec_small(const SpecCurve *__r
                                                             const double *__restrict__ sym,
                                                             const double2 *__restrict__ chirp,
                                                             const double2 *__restrict__ bhat,
-                                                            const double2 *__restrict__ tw)
+                                                            const double2 *__restrict__ tw,
+                                                            const double *__restrict__ sym_rq,
+                                                            const int *__restrict__ skip, int indep)
 {
     extern __shared__ double2 sa[];
-    const SpecCurve C = curves[idx[blockIdx.x / 3]];
+    const int cidx = idx[blockIdx.x / 3];
+    if (skip && skip[indep ? cidx : 0]) return;  // converged problem: its z is not used
+    const SpecCurve C = curves[cidx];
     const int comp = blockIdx.x % 3, n = C.n;
     for (int m = threadIdx.x; m < n; m += blockDim.x)
         sa[m] = make_double2(r[3 * (C.v0 + m) + comp] * dinv[C.v0 + m], 0.0);
     __syncthreads();
-    const double *lam = sym + C.sym_off;
+    const double *lam = sym_rq ? sym_rq + C.v0 : sym + C.sym_off;
     if (C.kind == SK_POW2) {
         fft_batch(sa, 1, n, C.logM, tw, false);
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -391,6 +404,7 @@ cudaError_t spectral_setup(Ctx &c, cudaStream_t s)
     long long sym_total = 0, chirp_total = 0, bhat_total = 0;
     std::map<int, long long> chirp_of, bhat_of;
     size_t large_max = 0;
+    std::vector<int> klist;
     for (int k = 0; k < c.nCurves; ++k) {
         int n = c.h_curve_n[k];
         SpecCurve C{};
@@ -433,6 +447,23 @@ cudaError_t spectral_setup(Ctx &c, cudaStream_t s)
             C.chirp_off = chirp_of[n];
             C.bhat_off = bhat_of[n];
         }
+        // sampled frequencies of the Rayleigh-quotient correction: 1..8, then 14 log-spaced up to n/2
+        {
+            std::vector<int> ks;
+            for (int k = 1; k <= 8; ++k) ks.push_back(k);
+            for (int j = 0; j < 14; ++j) {
+                double x = std::exp(std::log(9.0) + (std::log(std::max(9.0, n / 2.0)) - std::log(9.0)) * j / 13.0);
+                ks.push_back((int)std::lround(x));
+            }
+            std::sort(ks.begin(), ks.end());
+            ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+            std::vector<int> kk;
+            for (int k : ks)
+                if (k >= 1 && k <= n / 2) kk.push_back(k);
+            C.nk = (int)kk.size();
+            S.max_nk = std::max(S.max_nk, C.nk);
+            for (int j = 0; j < kMaxRQ; ++j) klist.push_back(j < C.nk ? kk[j] : 0);
+        }
         S.curves.push_back(C);
         if (C.kind == SK_FOURSTEP)
             S.large_idx.push_back(k);
@@ -452,6 +483,17 @@ cudaError_t spectral_setup(Ctx &c, cudaStream_t s)
     TPE_CHECK(cudaMalloc(&S.d_chirp, sizeof(double2) * std::max<long long>(1, chirp_total)));
     TPE_CHECK(cudaMalloc(&S.d_bhat, sizeof(double2) * std::max<long long>(1, bhat_total)));
     TPE_CHECK(cudaMalloc(&S.d_dinv, sizeof(double) * c.nV));
+    TPE_CHECK(cudaMalloc(&S.d_sym_rq, sizeof(double) * c.nV));
+    TPE_CHECK(cudaMalloc(&S.d_klist, sizeof(int) * klist.size()));
+    TPE_CHECK(cudaMemcpy(S.d_klist, klist.data(), sizeof(int) * klist.size(), cudaMemcpyHostToDevice));
+    TPE_CHECK(cudaMalloc(&S.d_rq, sizeof(double) * 2 * kMaxRQ * c.nCurves));
+    {
+        std::vector<int> vc(c.nV);
+        for (int k = 0; k < c.nCurves; ++k)
+            for (int v = c.h_voff[k]; v < c.h_voff[k + 1]; ++v) vc[v] = k;
+        TPE_CHECK(cudaMalloc(&S.d_vcurve, sizeof(int) * c.nV));
+        TPE_CHECK(cudaMemcpy(S.d_vcurve, vc.data(), sizeof(int) * c.nV, cudaMemcpyHostToDevice));
+    }
     if (large_max) {
         TPE_CHECK(cudaMalloc(&S.d_buf0, sizeof(double2) * 3 * large_max));
         TPE_CHECK(cudaMalloc(&S.d_buf1, sizeof(double2) * 3 * large_max));
@@ -478,23 +520,25 @@ void spectral_free(Ctx &c)
 {
     if (!c.spec) return;
     SpecState &S = *c.spec;
-    void *p[] = {S.d_curves, S.d_small_idx, S.d_sym, S.d_tw, S.d_chirp, S.d_bhat, S.d_buf0, S.d_buf1, S.d_dinv};
+    void *p[] = {S.d_curves, S.d_small_idx, S.d_sym, S.d_tw, S.d_chirp, S.d_bhat, S.d_buf0, S.d_buf1, S.d_dinv,
+                 S.d_sym_rq, S.d_klist, S.d_rq, S.d_vcurve};
     for (void *q : p)
         if (q) cudaFree(q);
     delete c.spec;
     c.spec = nullptr;
 }
 
-cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *)
+cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip)
 {
     if (!c.spec) return cudaErrorNotSupported;
     SpecState &S = *c.spec;
+    const double *rq = (c.prm.precond >= TP_PRECOND_SPECTRAL_RQ && S.rq_ready) ? S.d_sym_rq : nullptr;
     k_dinv<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_diag, S.d_dinv);
     c.launches++;
     if (!S.small_idx.empty()) {
         int M = S.max_small_M;
         k_spec_small<<<(int)S.small_idx.size() * 3, kFFTThreads, sizeof(double2) * M, s>>>(
-            S.d_curves, S.d_small_idx, r, z, S.d_dinv, S.d_sym, S.d_chirp, S.d_bhat, S.d_tw);
+            S.d_curves, S.d_small_idx, r, z, S.d_dinv, S.d_sym, S.d_chirp, S.d_bhat, S.d_tw, rq, skip, c.independent);
         c.launches++;
     }
     for (int k : S.large_idx) {
@@ -508,13 +552,144 @@ cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, c
         k_four_prep<<<nb, 256, 0, s>>>(C.v0, n, r, S.d_dinv, S.d_buf0);
         k_four_a<<<dim3(N1 / GA, 3), kFFTThreads, smA, s>>>(S.d_buf0, n, N1, N2, C.logN2, GA, S.d_tw, 0);
         k_four_c<<<dim3(N2 / GC, 3), kFFTThreads, smC, s>>>(S.d_buf0, S.d_buf1, n, N1, N2, C.logM, GC, S.d_tw, 0);
-        k_four_div<<<nb, 256, 0, s>>>(n, S.d_sym + C.sym_off, S.d_buf1);
+        k_four_div<<<nb, 256, 0, s>>>(n, rq ? rq + C.v0 : S.d_sym + C.sym_off, S.d_buf1);
         k_four_a<<<dim3(N1 / GA, 3), kFFTThreads, smA, s>>>(S.d_buf1, n, N1, N2, C.logN2, GA, S.d_tw, 1);
         k_four_c<<<dim3(N2 / GC, 3), kFFTThreads, smC, s>>>(S.d_buf1, S.d_buf0, n, N1, N2, C.logM, GC, S.d_tw, 1);
         k_four_out<<<nb, 256, 0, s>>>(C.v0, n, S.d_buf0, S.d_dinv, z);
         c.launches += 7;
     }
     return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------------- Rayleigh-quotient symbol
+//
+// T. Chan's optimal circulant approximation of S = D^-1/2 A D^-1/2 has the eigenvalues
+// lambda_opt(k) = f_k^H S f_k / n (the Rayleigh quotients of S on the Fourier modes).  They are
+// sampled at <= 24 frequencies per curve with the apply kernel (cos and sin probes scaled by
+// D^-1/2), the ratio rho(k) = lambda_opt(k) / lambda_ngon(k) is interpolated linearly in
+// (log k, log rho), and the preconditioner divides by lambda_ngon(k) rho(k).  On a regular polygon
+// rho = 1.  On knotted curves the low modes are far stiffer than the polygon's (rho up to ~1e4 at
+// k = 1), which is what the polygon symbol misses.
+
+// probe batch b: component q of vertex v holds vector t = 3 b + q = (frequency index t/2, cos or sin)
+__global__ void k_rq_probe(int nV, int b, const SpecCurve *__restrict__ curves, const int *__restrict__ vcurve,
+                           const int *__restrict__ klist, const double *__restrict__ diag, double *__restrict__ y)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    int c = vcurve[v];
+    const SpecCurve C = curves[c];
+    int i = v - C.v0;
+    double dv = diag[v] > 0.0 ? 1.0 / sqrt(diag[v]) : 0.0;
+    for (int q = 0; q < 3; ++q) {
+        int t = 3 * b + q, kk = t >> 1;
+        double val = 0.0;
+        if (kk < C.nk) {
+            long long e = ((long long)klist[c * kMaxRQ + kk] * i) % C.n;
+            double sn, cs;
+            sincospi(2.0 * (double)e / C.n, &sn, &cs);
+            val = ((t & 1) ? sn : cs) * dv;
+        }
+        y[3 * v + q] = val;
+    }
+}
+
+// rq[c][t] = sum over the curve of y . Ay for the three probes of batch b (one block per curve)
+__global__ void k_rq_reduce(int b, const SpecCurve *__restrict__ curves, const double *__restrict__ y,
+                            const double *__restrict__ Ay, double *__restrict__ rq)
+{
+    const SpecCurve C = curves[blockIdx.x];
+    __shared__ double sh[3][256];
+    double s[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < C.n; i += blockDim.x) {
+        int v = C.v0 + i;
+        for (int q = 0; q < 3; ++q) s[q] += y[3 * v + q] * Ay[3 * v + q];
+    }
+    for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 3; ++q) {
+            int t = 3 * b + q;
+            if (t < 2 * kMaxRQ) rq[blockIdx.x * 2 * kMaxRQ + t] = sh[q][0];
+        }
+}
+
+// corrected symbol of every curve (one block per curve)
+__global__ void k_rq_symbol(const SpecCurve *__restrict__ curves, const int *__restrict__ klist,
+                            const double *__restrict__ rq, const double *__restrict__ sym,
+                            double *__restrict__ sym_rq)
+{
+    const SpecCurve C = curves[blockIdx.x];
+    const double *lam = sym + C.sym_off;
+    __shared__ double lk[kMaxRQ], lr[kMaxRQ];
+    if (threadIdx.x < C.nk) {
+        int k = klist[blockIdx.x * kMaxRQ + threadIdx.x];
+        double q = (rq[blockIdx.x * 2 * kMaxRQ + 2 * threadIdx.x] + rq[blockIdx.x * 2 * kMaxRQ + 2 * threadIdx.x + 1]) / C.n;
+        double rho = (q > 0.0 && lam[k] > 0.0) ? q / lam[k] : 1.0;
+        lk[threadIdx.x] = log((double)k);
+        lr[threadIdx.x] = log(rho);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < C.n; k += blockDim.x) {
+        int kf = k <= C.n / 2 ? k : C.n - k;  // lambda_{n-k} = lambda_k
+        double r;
+        if (C.nk == 0) {
+            r = 0.0;
+        } else if (kf <= 1) {
+            r = lr[0];
+        } else {
+            double x = log((double)kf);
+            int j = 0;
+            while (j + 1 < C.nk && lk[j + 1] < x) ++j;
+            if (j + 1 >= C.nk)
+                r = lr[C.nk - 1];
+            else {
+                double f = (x - lk[j]) / (lk[j + 1] - lk[j]);
+                r = lr[j] + f * (lr[j + 1] - lr[j]);
+            }
+        }
+        int kl = (k == 0) ? 1 : k;  // lambda_0 := corrected lambda_1
+        sym_rq[C.v0 + k] = lam[kl] * exp(r);
+    }
+}
+
+// Builds the corrected symbols of the curve `gamma_geom` (geometry slot `which`); needs diag(A) in
+// c.d_diag.  Uses c.d_y and c.d_q as scratch (free outside a CG solve).
+cudaError_t spectral_rq_setup(Ctx &c, const double *gamma_geom, int which, cudaStream_t s)
+{
+    if (!c.spec) return cudaErrorNotSupported;
+    SpecState &S = *c.spec;
+    const int nb = (c.nV + 255) / 256;
+    const int nbatch = (2 * S.max_nk + 2) / 3;
+    for (int b = 0; b < nbatch; ++b) {
+        k_rq_probe<<<nb, 256, 0, s>>>(c.nV, b, S.d_curves, S.d_vcurve, S.d_klist, c.d_diag, c.d_y);
+        c.launches++;
+        TPE_CHECK(pair_apply(c, gamma_geom, which, c.d_y, c.d_q, s));
+        k_rq_reduce<<<c.nCurves, 256, 0, s>>>(b, S.d_curves, c.d_y, c.d_q, S.d_rq);
+        c.launches++;
+    }
+    k_rq_symbol<<<c.nCurves, 256, 0, s>>>(S.d_curves, S.d_klist, S.d_rq, S.d_sym, S.d_sym_rq);
+    c.launches++;
+    S.rq_ready = 1;
+    return cudaGetLastError();
+}
+
+cudaError_t spectral_symbol_copy(Ctx &c, int rq, double *out, cudaStream_t s)
+{
+    if (!c.spec) return cudaErrorNotSupported;
+    SpecState &S = *c.spec;
+    if (rq) return cudaMemcpyAsync(out, S.d_sym_rq, sizeof(double) * c.nV, cudaMemcpyDeviceToDevice, s);
+    for (int k = 0; k < c.nCurves; ++k) {
+        const SpecCurve &C = S.curves[k];
+        TPE_CHECK(cudaMemcpyAsync(out + C.v0, S.d_sym + C.sym_off, sizeof(double) * C.n, cudaMemcpyDeviceToDevice, s));
+    }
+    return cudaSuccess;
 }
 
 cudaError_t spectral_symbol_of(Ctx &c, int n, double *lam, cudaStream_t s)

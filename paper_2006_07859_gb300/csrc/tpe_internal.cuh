@@ -13,6 +13,8 @@ namespace tpe {
 
 struct SpecState;
 struct SolverState;
+struct CoarseState;
+struct GnnState;
 
 // Precision of the pair arithmetic.
 enum Prec { P64 = 0, P32 = 1, PMIX = 2 };
@@ -28,7 +30,7 @@ constexpr int kTile = 128;     // source edges staged in shared memory per tile
 // shares a vertex with some target of the item, so source tiles outside it skip the
 // disjointness test.
 struct WorkItem {
-    int tgt0, ntgt, src0, src1, slot, nb_lo, nb_hi, pad;
+    int tgt0, ntgt, src0, src1, slot, nb_lo, nb_hi, pad;  // pad: problem index
 };
 
 // FP32 edge record (48 B): a = (g_i1, l), b = (g_i2, T.x), c = (T.y, T.z, i1, i2 as bits);
@@ -63,6 +65,7 @@ struct KernelParams {
     int fast;               // (alpha, beta, p) == (2, 4.5, 2.5): specialised powers
     double near2;           // squared near-pair cutoff (mixed precision)
     float near2f;
+    float near2f_diff;      // squared near cutoff of the differential (wider: its near terms cancel)
     float mid2f;            // squared distance below which a tile uses double-float differences
 };
 
@@ -92,6 +95,7 @@ struct Ctx {
     int32_t *d_voff = nullptr;                 // [nCurves + 1]
     int max_curve_n = 0;
     SpecState *spec = nullptr;
+    CoarseState *coarse = nullptr;
     // pair-pass work lists, one per pair op class (blocking depends on targets per thread)
     struct Plan {
         WorkItem *d_items = nullptr;
@@ -142,12 +146,19 @@ struct Ctx {
     double *d_best = nullptr;  // [nV][3] line-search result
     double *d_t5 = nullptr, *d_t6 = nullptr;
     int64_t pairs_per_pass = 0;
+    const int *d_skip = nullptr;  // during a CG solve: per-problem converged flags (apply skips them)
+    GnnState *gnn = nullptr;      // learned preconditioner term (contexts created with TP_PRECOND_LEARNED)
+    // (residual, iterate) capture of a CG solve: every `every` iterations r -> R[n], y -> Y[n]
+    struct Harvest {
+        double *R = nullptr, *Y = nullptr;
+        int every = 1, max = 0, n = 0;
+    } hv;
     // per-kernel event timing (tp_profile)
     int profile = 0;
     std::vector<cudaEvent_t> prof_pool;
     std::vector<std::pair<int, int>> prof_pending;  // (op, slot)
-    double prof_ms[4] = {0, 0, 0, 0};
-    int64_t prof_n[4] = {0, 0, 0, 0};
+    double prof_ms[5] = {0, 0, 0, 0, 0};
+    int64_t prof_n[5] = {0, 0, 0, 0, 0};
 };
 
 int prof_begin(Ctx &c, int op, cudaStream_t s);
@@ -170,13 +181,20 @@ cudaError_t constraints_targets(Ctx &c, int which, cudaStream_t s);
 cudaError_t project(Ctx &c, double *v, cudaStream_t s, const int *skip_flag);
 cudaError_t pinv_apply(Ctx &c, const double *b_phi, double scale, double *out, cudaStream_t s);
 cudaError_t spectral_setup(Ctx &c, cudaStream_t s);
+cudaError_t spectral_rq_setup(Ctx &c, const double *gamma_geom, int which, cudaStream_t s);
+cudaError_t coarse_setup(Ctx &c, const double *gamma_geom, int which, cudaStream_t s);
+cudaError_t coarse_apply(Ctx &c, const double *r, double *z, cudaStream_t s);
+void coarse_free(Ctx &c);
+cudaError_t spectral_symbol_copy(Ctx &c, int rq, double *out, cudaStream_t s);
 void spectral_free(Ctx &c);
 cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip_flag);
+cudaError_t precond_apply_base(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip_flag);
+cudaError_t coarse_init(Ctx &c);
 cudaError_t solver_setup(Ctx &c);
 void solver_free(Ctx &c);
 cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
                      int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s,
-                     int proj_mode);
+                     int proj_mode, int *conv_flags = nullptr);
 cudaError_t project_mean(Ctx &c, double *v, cudaStream_t s, const int *skip);
 cudaError_t clen_rhs(Ctx &c, double *out, cudaStream_t s);
 cudaError_t schur_gradient(Ctx &c, const double *y0, const double *y1, double *g, cudaStream_t s);
@@ -187,6 +205,29 @@ cudaError_t vec_axpby(Ctx &c, double a, const double *x, double b, const double 
 cudaError_t vec_scale_dev(Ctx &c, const double *x, const double *num_dev, int invert_sqrt, double *out,
                           cudaStream_t s);
 cudaError_t sum_problems(Ctx &c, const double *per_edge_or_vertex, int per_vertex, double *out, cudaStream_t s);
+
+// ------------------------------------------------------------------ learned preconditioner (gnn.cu)
+int gnn_num_params();
+cudaError_t gnn_alloc(Ctx &c);
+void gnn_free(Ctx &c);
+int gnn_ready(const Ctx &c);
+int gnn_bound(const Ctx &c);
+cudaError_t gnn_set_params(Ctx &c, const float *theta, int reset_adam, cudaStream_t s);
+cudaError_t gnn_get_params(Ctx &c, float *theta, cudaStream_t s);
+cudaError_t gnn_bind(Ctx &c, int which, const double *diag, cudaStream_t s);
+double *gnn_diag_buffer(Ctx &c);
+const float *gnn_features(const Ctx &c);
+const float *gnn_outputs(const Ctx &c);
+const float *gnn_last_grad(const Ctx &c);
+cudaError_t gnn_forward(Ctx &c, cudaStream_t s);
+cudaError_t gnn_backward(Ctx &c, const float *dout, float *grad, cudaStream_t s);
+cudaError_t gnn_adam(Ctx &c, const float *grad, float lr, cudaStream_t s);
+cudaError_t gnn_gapply(Ctx &c, const double *r, double *z, int accumulate, cudaStream_t s, const int *skip);
+cudaError_t gnn_out_grad(Ctx &c, const double *r, const double *gz, double scale, int accumulate, float *dout,
+                         cudaStream_t s);
+cudaError_t gnn_problem_dot(Ctx &c, const double *a, const double *b, double *out, cudaStream_t s);
+cudaError_t gnn_train_step(Ctx &c, const double *gamma, int n_pairs, const double *R, const double *B,
+                           const double *AB, const double *ER, float lr, double *loss_dev, cudaStream_t s);
 
 }  // namespace tpe
 

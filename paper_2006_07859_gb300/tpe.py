@@ -16,7 +16,9 @@ TP_OK, TP_ERR_INVALID_ARG, TP_ERR_CUDA, TP_ERR_DEGENERATE_EDGE, TP_ERR_NONFINITE
 TP_ERR_NOT_CONVERGED, TP_ERR_BREAKDOWN, TP_ERR_LINESEARCH, TP_ERR_PROJECTION, TP_ERR_OOM = 5, 6, 7, 8, 9
 TP_ERR_UNSUPPORTED = 10
 TP_FP64, TP_FP32, TP_MIXED = 0, 1, 2
-TP_PRECOND_NONE, TP_PRECOND_JACOBI, TP_PRECOND_SPECTRAL = 0, 1, 2
+TP_PRECOND_NONE, TP_PRECOND_JACOBI, TP_PRECOND_SPECTRAL, TP_PRECOND_SPECTRAL_RQ, TP_PRECOND_TWOLEVEL = 0, 1, 2, 3, 4
+TP_PRECOND_LEARNED = 5
+TP_GNN_HIDDEN, TP_GNN_FEATURES = 64, 8
 
 STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ERR_DEGENERATE_EDGE",
                 4: "TP_ERR_NONFINITE", 5: "TP_ERR_NOT_CONVERGED", 6: "TP_ERR_BREAKDOWN", 7: "TP_ERR_LINESEARCH",
@@ -25,7 +27,10 @@ STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ER
 EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp_num_problems", "tp_set_params",
             "tp_energy", "tp_differential", "sobolev_apply", "tp_gram_diagonal", "tp_precond_apply",
             "tp_spectral_symbol", "tp_set_constraints_from", "tp_constraints", "sobolev_gradient", "descent_step",
-            "tp_launch_count", "tp_pairs_per_pass", "tp_profile", "tp_profile_read", "tp_measure_peaks", "tp_energy_static"]
+            "tp_launch_count", "tp_pairs_per_pass", "tp_profile", "tp_profile_read", "tp_measure_peaks", "tp_energy_static",
+            "tp_spectral_symbols", "tp_gnn_num_params", "tp_gnn_set_params", "tp_gnn_get_params", "tp_gnn_bind",
+            "tp_gnn_forward", "tp_gnn_backward", "tp_gnn_adam", "tp_gnn_g_apply", "tp_gnn_out_grad", "tp_cg_harvest",
+            "tp_gnn_prepare_pairs", "tp_gnn_train_step"]
 
 
 class TpParams(ctypes.Structure):
@@ -34,18 +39,19 @@ class TpParams(ctypes.Structure):
                 ("cg_maxit", ctypes.c_int), ("cg_check_every", ctypes.c_int), ("proj_cg_rtol", ctypes.c_double),
                 ("precond", ctypes.c_int), ("armijo_c", ctypes.c_double), ("shrink", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("proj_tol", ctypes.c_double), ("proj_maxit", ctypes.c_int),
-                ("independent", ctypes.c_int), ("far_cutoff", ctypes.c_double)]
+                ("independent", ctypes.c_int), ("coarse_dim", ctypes.c_int), ("far_cutoff", ctypes.c_double)]
 
 
 class TpSolveInfo(ctypes.Structure):
-    _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double), ("converged", ctypes.c_int)]
+    _fields_ = [("iters", ctypes.c_int), ("rel_res", ctypes.c_double), ("converged", ctypes.c_int),
+                ("n_converged", ctypes.c_int)]
 
 
 class TpStepInfo(ctypes.Structure):
     _fields_ = [("E_before", ctypes.c_double), ("E_after", ctypes.c_double), ("tau", ctypes.c_double),
                 ("gnorm", ctypes.c_double), ("halvings", ctypes.c_int), ("proj_iters", ctypes.c_int),
                 ("cg_iters", ctypes.c_int), ("proj_cg_iters", ctypes.c_int), ("accepted", ctypes.c_int),
-                ("rel_res", ctypes.c_double)]
+                ("rel_res", ctypes.c_double), ("n_converged", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,6 +101,19 @@ def library() -> ctypes.CDLL:
         pdd = ctypes.POINTER(d)
         L.tp_measure_peaks.argtypes = [pdd, pdd, pdd]
         L.tp_energy_static.argtypes = [vp, vp, i, i, d, d, vp, vp]
+        L.tp_spectral_symbols.argtypes = [vp, i, vp, vp]
+        L.tp_gnn_num_params.argtypes = []
+        L.tp_gnn_set_params.argtypes = [vp, vp, i, vp]
+        L.tp_gnn_get_params.argtypes = [vp, vp, vp]
+        L.tp_gnn_bind.argtypes = [vp, vp, vp]
+        L.tp_gnn_forward.argtypes = [vp, vp, vp, vp]
+        L.tp_gnn_backward.argtypes = [vp, vp, vp, vp]
+        L.tp_gnn_adam.argtypes = [vp, vp, ctypes.c_float, vp]
+        L.tp_gnn_g_apply.argtypes = [vp, vp, vp, i, vp]
+        L.tp_gnn_out_grad.argtypes = [vp, vp, vp, vp, i, vp]
+        L.tp_cg_harvest.argtypes = [vp, vp, vp, i, i, vp, vp, ctypes.POINTER(i), ctypes.POINTER(TpSolveInfo), vp]
+        L.tp_gnn_prepare_pairs.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp]
+        L.tp_gnn_train_step.argtypes = [vp, vp, i, vp, vp, vp, vp, ctypes.c_float, pdd, vp, vp]
         _lib = L
     return _lib
 
@@ -115,6 +134,15 @@ def _ptr(t):
     import torch
     if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise ValueError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _fptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float32 tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -245,7 +273,8 @@ def sobolev_gradient(ctx: Context, gamma, dE, g=None, allow_not_converged=False)
     allow = (TP_ERR_NOT_CONVERGED,) if allow_not_converged else ()
     st = ctx._check(library().sobolev_gradient(ctx.handle, _ptr(gamma), _ptr(dE), _ptr(g), ctypes.byref(info),
                                                _stream()), allow)
-    return g, {"iters": info.iters, "rel_res": info.rel_res, "converged": info.converged, "status": st}
+    return g, {"iters": info.iters, "rel_res": info.rel_res, "converged": info.converged,
+               "n_converged": info.n_converged, "status": st}
 
 
 def descent_step(ctx: Context, gamma, allow=()):
@@ -275,3 +304,87 @@ def tp_energy_static(gamma, edges, alpha=2.0, beta=4.5, E=None):
     if st != TP_OK:
         raise TpError(st, "tp_energy_static failed")
     return E
+
+
+def tp_spectral_symbols(ctx: Context, rq: int, out=None):
+    out = _new(ctx.n_vertices) if out is None else out
+    ctx._check(library().tp_spectral_symbols(ctx.handle, int(rq), _ptr(out), _stream()))
+    return out
+
+
+# ---------------------------------------------------------------- learned preconditioner
+
+def tp_gnn_num_params() -> int:
+    return int(library().tp_gnn_num_params())
+
+
+def tp_gnn_set_params(ctx: Context, theta, reset_optimizer=True):
+    ctx._check(library().tp_gnn_set_params(ctx.handle, _fptr(theta), 1 if reset_optimizer else 0, _stream()))
+
+
+def tp_gnn_get_params(ctx: Context, theta=None):
+    import torch
+    theta = torch.empty(tp_gnn_num_params(), dtype=torch.float32, device="cuda") if theta is None else theta
+    ctx._check(library().tp_gnn_get_params(ctx.handle, _fptr(theta), _stream()))
+    return theta
+
+
+def tp_gnn_bind(ctx: Context, gamma):
+    ctx._check(library().tp_gnn_bind(ctx.handle, _ptr(gamma), _stream()))
+
+
+def tp_gnn_forward(ctx: Context, features=None, out=None):
+    """Returns (features [nE, 8], outputs [nE, 2]) as float32 CUDA tensors."""
+    import torch
+    features = torch.empty((ctx.n_edges, TP_GNN_FEATURES), dtype=torch.float32, device="cuda") \
+        if features is None else features
+    out = torch.empty((ctx.n_edges, 2), dtype=torch.float32, device="cuda") if out is None else out
+    ctx._check(library().tp_gnn_forward(ctx.handle, _fptr(features), _fptr(out), _stream()))
+    return features, out
+
+
+def tp_gnn_backward(ctx: Context, dout, grad=None):
+    import torch
+    grad = torch.empty(tp_gnn_num_params(), dtype=torch.float32, device="cuda") if grad is None else grad
+    ctx._check(library().tp_gnn_backward(ctx.handle, _fptr(dout), _fptr(grad), _stream()))
+    return grad
+
+
+def tp_gnn_adam(ctx: Context, grad, lr: float):
+    ctx._check(library().tp_gnn_adam(ctx.handle, _fptr(grad), ctypes.c_float(lr), _stream()))
+
+
+def tp_gnn_g_apply(ctx: Context, r, z=None, accumulate=False):
+    z = _new((ctx.n_vertices, 3)) if z is None else z
+    ctx._check(library().tp_gnn_g_apply(ctx.handle, _ptr(r), _ptr(z), 1 if accumulate else 0, _stream()))
+    return z
+
+
+def tp_gnn_out_grad(ctx: Context, r, gz, dout=None, accumulate=False):
+    import torch
+    dout = torch.empty((ctx.n_edges, 2), dtype=torch.float32, device="cuda") if dout is None else dout
+    ctx._check(library().tp_gnn_out_grad(ctx.handle, _ptr(r), _ptr(gz), _fptr(dout), 1 if accumulate else 0,
+                                         _stream()))
+    return dout
+
+
+def tp_cg_harvest(ctx: Context, gamma, rhs, every: int, R, E):
+    """R, E: CUDA float64 [max_pairs, nV, 3].  Returns (n_pairs, solve info dict)."""
+    n = ctypes.c_int()
+    info = TpSolveInfo()
+    ctx._check(library().tp_cg_harvest(ctx.handle, _ptr(gamma), _ptr(rhs), int(every), int(R.shape[0]), _ptr(R),
+                                       _ptr(E), ctypes.byref(n), ctypes.byref(info), _stream()))
+    return n.value, {"iters": info.iters, "rel_res": info.rel_res, "converged": info.converged}
+
+
+def tp_gnn_prepare_pairs(ctx: Context, gamma, R, E, B, AB, ER):
+    """ER: CUDA float64 [n, n_problems]; B may be E (in place)."""
+    ctx._check(library().tp_gnn_prepare_pairs(ctx.handle, _ptr(gamma), int(R.shape[0]), _ptr(R), _ptr(E), _ptr(B),
+                                              _ptr(AB), _ptr(ER), _stream()))
+
+
+def tp_gnn_train_step(ctx: Context, gamma, R, B, AB, ER, lr: float, grad=None) -> float:
+    loss = ctypes.c_double()
+    ctx._check(library().tp_gnn_train_step(ctx.handle, _ptr(gamma), int(R.shape[0]), _ptr(R), _ptr(B), _ptr(AB),
+                                           _ptr(ER), ctypes.c_float(lr), ctypes.byref(loss), _fptr(grad), _stream()))
+    return loss.value

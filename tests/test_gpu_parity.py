@@ -118,3 +118,23 @@ def test_degenerate_edge_is_reported(torch):
         torch.cuda.synchronize()
         tpe.tp_constraints(ctx, dev(g))
     assert ei.value.status in (tpe.TP_ERR_DEGENERATE_EDGE,)
+
+
+def test_mixed_precision_at_scale(torch, orc):
+    """65,536-edge knot (K = 16): mixed-precision energy rows, differential and apply on sampled
+    rows against the FP64 oracle.  At this size plain FP32 loses the near pairs entirely."""
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.fourier_knot(65536, 16, 100))
+    rng = np.random.default_rng(101)
+    rows_i = np.sort(rng.choice(c.n_edges, 64, replace=False)).astype(np.int32)
+    v_i = np.sort(rng.choice(c.n_vertices, 24, replace=False)).astype(np.int32)
+    u = np.random.default_rng(102).normal(size=(c.n_vertices, 3))
+    ctx = make_ctx(c, precision=2, precond=1)
+    g = dev(c.gamma)
+    rows = torch.empty(c.n_edges, dtype=torch.float64, device="cuda")
+    tpe.tp_energy(ctx, g, rows=rows)
+    dE = host(tpe.tp_differential(ctx, g))
+    Au = host(tpe.sobolev_apply(ctx, g, dev(u)))
+    assert rel(host(rows)[rows_i], orc.energy_rows(c.gamma, c.edges, rows_i)) <= 1e-6
+    assert rel(dE[v_i], orc.differential_at(c.gamma, c.edges, v_i)) <= 1e-6
+    assert rel(Au[v_i], orc.gram_apply_at(c.gamma, c.edges, SIG, u, v_i)) <= 1e-6

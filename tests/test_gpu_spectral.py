@@ -95,3 +95,98 @@ def test_spectral_beats_jacobi_and_agrees(torch, orc):
         out[pc] = (host(gt), info)
     assert out[2][1]["iters"] * 3 < out[1][1]["iters"], (out[1][1], out[2][1])
     assert rel(out[2][0], out[1][0]) <= 1e-3
+
+
+@pytest.mark.parametrize("name", ["ngon64", "trefoil256", "knot300", "batch3"])
+def test_rq_symbol_and_apply(torch, orc, name):
+    """Rayleigh-quotient corrected symbol (TP_PRECOND_SPECTRAL_RQ) against the oracle built from the
+    dense Gram matrix, and the preconditioner applied with it."""
+    from paper_2006_07859_gb300 import tpe
+    if name == "ngon64":
+        c, indep = S.single(S.regular_polygon(64, 1.0)), 0
+    elif name == "trefoil256":
+        c, indep = S.trefoil_256(), 0
+    elif name == "knot300":
+        c, indep = S.single(S.fourier_knot(300, 5, 3)), 0
+    else:
+        c, indep = S.batch_of_knots([64, 129, 256], 5, 700), 1
+    ctx = make_ctx(c, precision=0, precond=3, independent=indep)
+    r = np.random.default_rng(4).normal(size=(c.n_vertices, 3))
+    z = host(tpe.tp_precond_apply(ctx, dev(c.gamma), dev(r)))     # also builds the corrected symbols
+    sym = host(tpe.tp_spectral_symbols(ctx, 1))
+    ref, diag = [], []
+    for k in range(c.n_curves):
+        gk, ek = c.curve(k)
+        B, B0 = orc.gram_dense(gk, ek, SIG)
+        ref.append(orc.spectral_rq_symbol(B + B0, gk.shape[0], SIG))
+        diag.append(np.diag(B + B0))
+    ref = np.concatenate(ref)
+    assert rel(sym, ref) <= 1e-5
+    if name == "ngon64":   # on a regular polygon the correction is the identity
+        assert rel(sym, host(tpe.tp_spectral_symbols(ctx, 0))) <= 1e-6
+    syms = {}
+    ds = np.sqrt(np.concatenate(diag))
+    zo = np.empty_like(r)
+    for k in range(c.n_curves):
+        v0, v1 = c.vertex_offsets[k], c.vertex_offsets[k + 1]
+        s_ = r[v0:v1] / ds[v0:v1, None]
+        y = np.real(np.fft.ifft(np.fft.fft(s_, axis=0) / ref[v0:v1, None], axis=0))
+        zo[v0:v1] = y / ds[v0:v1, None]
+    assert rel(z, zo) <= 1e-5
+
+
+def test_rq_symbol_halves_iterations(torch):
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.fourier_knot(1024, 8, 1))
+    g = dev(c.gamma)
+    its = {}
+    for pc in (2, 3):
+        ctx = make_ctx(c, precision=0, precond=pc, cg_rtol=1e-6)
+        dE = tpe.tp_differential(ctx, g)
+        _, info = tpe.sobolev_gradient(ctx, g, dE)
+        assert info["converged"]
+        its[pc] = info["iters"]
+    assert its[3] < 0.75 * its[2], its
+
+
+@pytest.mark.parametrize("name", ["trefoil256", "knot300", "batch3"])
+def test_twolevel_apply(torch, orc, name):
+    """Two-level preconditioner (spectral RQ + coarse hats) against the oracle built from the dense
+    Gram matrix."""
+    from paper_2006_07859_gb300 import tpe
+    if name == "trefoil256":
+        c, indep = S.trefoil_256(), 0
+    elif name == "knot300":
+        c, indep = S.single(S.fourier_knot(300, 5, 3)), 0
+    else:
+        c, indep = S.batch_of_knots([64, 129, 256], 5, 700), 1
+    ctx = make_ctx(c, precision=0, precond=4, independent=indep, coarse_dim=32)
+    r = np.random.default_rng(6).normal(size=(c.n_vertices, 3))
+    r -= r.mean(0)
+    z = host(tpe.tp_precond_apply(ctx, dev(c.gamma), dev(r)))
+    zo = np.empty_like(r)
+    for k in range(c.n_curves):
+        gk, ek = c.curve(k)
+        n = gk.shape[0]
+        B, B0 = orc.gram_dense(gk, ek, SIG)
+        v0, v1 = c.vertex_offsets[k], c.vertex_offsets[k + 1]
+        zo[v0:v1] = orc.twolevel_apply(B + B0, n, SIG, min(32, n // 4), r[v0:v1])
+    # compare modulo the constant the mean-free projection removes (per curve)
+    for k in range(c.n_curves):
+        v0, v1 = c.vertex_offsets[k], c.vertex_offsets[k + 1]
+        a, b = z[v0:v1] - z[v0:v1].mean(0), zo[v0:v1] - zo[v0:v1].mean(0)
+        assert rel(a, b) <= 1e-6, k
+
+
+def test_twolevel_cuts_iterations(torch):
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.fourier_knot(1024, 8, 1))
+    g = dev(c.gamma)
+    its = {}
+    for pc in (3, 4):
+        ctx = make_ctx(c, precision=0, precond=pc, cg_rtol=1e-6)
+        dE = tpe.tp_differential(ctx, g)
+        _, info = tpe.sobolev_gradient(ctx, g, dE)
+        assert info["converged"]
+        its[pc] = info["iters"]
+    assert its[4] < 0.6 * its[3], its

@@ -1,0 +1,64 @@
+"""Pins of the learned-preconditioner oracle (oracle/gnn.py): finite differences of the loss
+with respect to the parameters, symmetry and positivity of the learned term.  CPU only."""
+import numpy as np
+import pytest
+
+import synth as S
+from oracle import gnn
+
+
+@pytest.fixture(scope="module")
+def setup(orc):
+    n = 24
+    c = S.single(S.fourier_knot(n, 3, 5))
+    B, B0 = orc.gram_dense(c.gamma, c.edges, 0.75)
+    A = B + B0
+    diag = np.diag(A).copy()
+    rng = np.random.default_rng(0)
+    e = rng.normal(size=(n, 3))
+    e -= e.mean(0)
+    r = A @ e
+    base_z = r / diag[:, None]
+    return c, A, diag, r, e, base_z
+
+
+def test_g_term_is_symmetric_positive(setup):
+    c, A, diag, r, e, base_z = setup
+    theta = gnn.init_params(3, out_bias=-0.5)
+    out, _ = gnn.forward(theta, gnn.features(c.gamma, diag))
+    n = c.n_vertices
+    G = np.zeros((n, n))
+    for k in range(n):
+        u = np.zeros((n, 3))
+        u[k, 0] = 1.0
+        G[:, k] = gnn.g_apply(out, diag, u)[:, 0]
+    assert np.abs(G - G.T).max() <= 1e-12 * np.abs(G).max()
+    assert np.linalg.eigvalsh(G).min() >= -1e-12 * np.abs(G).max()
+
+
+def test_loss_gradient_matches_central_differences(setup):
+    c, A, diag, r, e, base_z = setup
+    theta = gnn.init_params(1, out_bias=-0.5)
+    f = gnn.features(c.gamma, diag)
+    L, g = gnn.loss_and_grad(theta, f, diag, A, r, e, base_z)
+    rng = np.random.default_rng(2)
+    idx = rng.choice(theta.size, 40, replace=False)
+    h = 1e-6
+    for k in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (gnn.loss_and_grad(tp, f, diag, A, r, e, base_z)[0] - gnn.loss_and_grad(tm, f, diag, A, r, e, base_z)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g).max()), (k, fd, g[k])
+
+
+def test_loss_is_the_a_norm_error(setup):
+    """L = (z - e)^T A (z - e) / e^T A e with A e = r."""
+    c, A, diag, r, e, base_z = setup
+    theta = gnn.init_params(4, out_bias=-1.0)
+    f = gnn.features(c.gamma, diag)
+    out, _ = gnn.forward(theta, f)
+    z = base_z + gnn.g_apply(out, diag, r)
+    L, _ = gnn.loss_and_grad(theta, f, diag, A, r, e, base_z)
+    d = z - e
+    assert abs(L - (d * (A @ d)).sum() / (e * (A @ e)).sum()) <= 1e-10

@@ -205,3 +205,13 @@ def test_spectral_preconditioner_is_exact_on_regular_polygon(orc):
         assert res.converged and res.iters <= 6
         assert plain.iters > 4 * res.iters
         assert np.abs(res.x - plain.x).max() <= 1e-7 * np.abs(plain.x).max()
+
+
+def test_rq_symbol_is_exact_on_regular_polygon(orc):
+    """On a regular polygon A is circulant with a constant diagonal, so the Rayleigh quotients on the
+    Fourier modes are its normalised eigenvalues and the correction is the identity."""
+    for n in (40, 64, 100):
+        g = S.regular_polygon(n, 1.7)
+        B, B0 = orc.gram_dense(g, S.closed_edges(n), SIG)
+        np.testing.assert_allclose(orc.spectral_rq_symbol(B + B0, n, SIG), orc.ngon_symbol_closed_form(n, SIG),
+                                   rtol=1e-10)
