@@ -39,6 +39,9 @@ MUFU_PER_PAIR = {"energy": 8, "diff": 8, "apply": 8}
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_NOMINAL = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6   # FLOP/s at the maximum SM clock
 L2_BYTES = 129 * 2 ** 20
+# DRAM bytes (read + write) of one apply launch on the 8 x 4096 workload, by targets per thread, from an
+# ncu capture of the current kernel (profiles/apply_pair_kernel_knots8x4096.md); other variants: unknown
+APPLY_TRAFFIC_BYTES = {2: 5.07e6}
 
 
 def parse():
@@ -65,6 +68,7 @@ def parse():
     ap.add_argument("--train-descent", type=int, default=6, help="learned mode: descent steps harvested")
     ap.add_argument("--fp64-maxit", type=int, default=600, help="learned mode: cap of the plain FP64 CG solves")
     ap.add_argument("--eval-262k", action="store_true", help="learned mode: also compare on the 262,144-vertex knot")
+    ap.add_argument("--train-full", action="store_true", help="learned mode: train on n up to 65536")
     return ap.parse_args()
 
 
@@ -356,17 +360,17 @@ def timed_solve(tpe, torch, ctx, g, rhs):
 
 
 def run_learned(args):
-    """Learned preconditioner (config 5 at reduced scale, see the training set below): harvest
-    (residual, correction) pairs from the descent of 8 training knots (K = 8, n log-uniform in
-    [4096, 16384], seed 500), train the network with the library's kernels, then time the gradient
-    solve A-bar y = P dE to 1e-6 on the 8 x 4096 benchmark knots (unseen): plain FP64 CG, FP64 Jacobi,
-    FP64 two-level, mixed two-level and mixed two-level + learned term."""
+    """Learned preconditioner: harvest (residual, correction) pairs from the descent of training knots
+    (K = 8, seeds 2000+, n in {4096, 8192, 16384}; --train-full adds 32768 and 65536), train the
+    network with the library's kernels, then time the gradient solve A-bar y = P dE to 1e-6 on the
+    8 x 4096 benchmark knots (unseen): plain FP64 CG, FP64 Jacobi, FP64 two-level, mixed two-level
+    and mixed two-level + learned term (optionally also on the 262,144-vertex knot)."""
     import torch
     import synth as S
     from paper_2006_07859_gb300 import learned, tpe
     out = {"mode": "learned"}
-    sizes = S.batch_sizes(8, 4096, 16384, 500)
-    tr = S.batch_of_knots(sizes, 8, 500)
+    sizes = [4096, 8192, 16384] + ([32768, 65536] if args.train_full else [])
+    tr = S.batch_of_knots(sizes, 8, 1999)   # curve c drawn with seed 2000 + c
     ctx = tpe.Context.from_curves(tr, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_LEARNED, independent=1,
                                   cg_rtol=1e-6, cg_maxit=2000, proj_cg_rtol=1e-3)
     ctx.set_params(precond=tpe.TP_PRECOND_TWOLEVEL)
@@ -384,7 +388,7 @@ def run_learned(args):
     t_t = time.perf_counter() - t0
     loss1 = learned.evaluate_loss(ctx, sets, res["theta"])
     theta = res["theta"].clone()
-    out["training"] = {"curves": "8_fourier_knots_K8_n_loguniform_4096_16384_seed500", "sizes": [int(x) for x in sizes],
+    out["training"] = {"curves": f"fourier_knots_K8_seeds2000+_n{'-'.join(str(x) for x in sizes)}", "sizes": [int(x) for x in sizes],
                        "descent_steps_harvested": args.train_descent, "pair_vectors": npairs,
                        "per_curve_pairs": npairs * len(sizes), "harvest_seconds": t_h, "adam_steps": args.train_steps,
                        "train_seconds": t_t, "loss_init": loss0, "loss_trained": loss1,
@@ -447,6 +451,7 @@ def run_ours(args, rank, world, local_rank):
                                   independent=indep, **sp)
     gamma = torch.as_tensor(curves.gamma).cuda()
     pairs = ctx.pairs_per_pass()
+    tuned = tpe.tp_autotune(ctx, gamma)   # targets per thread of each pair pass, timed on this workload
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     ok_status = (tpe.TP_OK, tpe.TP_ERR_NOT_CONVERGED)
     infos = []
@@ -526,6 +531,8 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": dict(cfg, alpha=2.0, beta=4.5, precision="mixed", precond="twolevel (spectral RQ + 64 coarse hats)", **sp,
                        l2="flushed between timed steps (256 MiB write)", parallelism=f"replicas x{world}"),
+        "autotune": tuned,
+        "cuda_graphs": "CG blocks of cg_check_every iterations replayed as captured graphs",
         "pair_interactions_per_s": pps,
         "pair_pass_throughput_262144": big,
         "pairs_per_pass": pairs,
@@ -535,7 +542,10 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"kernel": "k_pairs<PMIX, OP_APPLY> (Sobolev apply)", "bound": "alu",
                      "achieved": achieved / 1e12 if achieved else None,
                      "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_NOMINAL if achieved else None, "traffic": None,
+                     "frac": achieved / FP32_PEAK_NOMINAL if achieved else None,
+                     "traffic": (APPLY_TRAFFIC_BYTES.get(tuned["tpt"]["apply"])
+                                 if args.workload == "knots8x4096" else None),
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "flop_per_pair": FLOP_PER_PAIR["apply"], "launches": n_a, "avg_launch_ms": avg_s * 1e3,
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal units and max clock)",
                      "measured_fp32_peak_tflops": peaks["fp32_flops"] / 1e12,

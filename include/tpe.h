@@ -20,8 +20,9 @@
  *     asynchronous unless it says otherwise.  Calls that return host-side info structs
  *     synchronise the stream before returning.
  *   - The caller owns every pointer it passes; the context owns its own scratch memory,
- *     allocated once in tp_create and sized for the graph it was created with.  No entry
- *     point allocates device memory after tp_create.
+ *     allocated once in tp_create and sized for the graph it was created with.  Only
+ *     tp_set_params (switching a preconditioner on) and tp_autotune (a larger work queue)
+ *     allocate device memory after tp_create.
  *   - Every call returns a tp_status; nothing aborts or traps.  tp_last_error() gives a
  *     human-readable message for the last failing call on a context.
  *   - A context is not thread-safe; use one context per host thread.
@@ -102,6 +103,9 @@ typedef struct {
     double far_cutoff;    /* TP_MIXED: source tiles farther than far_cutoff * (extent of the curve) from a
                              warp's targets use single-float positions (faster, less accurate); >= 10
                              keeps double-float positions everywhere */
+    int use_graphs;       /* 1: CG runs blocks of cg_check_every iterations as captured CUDA graphs on a
+                             context-owned stream joined to the caller's stream by events (the same
+                             kernels in the same order as the direct launches); 0: direct launches */
 } tp_params;
 
 typedef struct {
@@ -244,8 +248,9 @@ TPE_API tp_status tp_energy_static(const double *gamma, const int32_t *edges, in
  * Parameter vector theta: FP32, DEVICE, tp_gnn_num_params() values in the order
  *   W1 [64][8], b1 [64], W2s [64][64], W2n [64][64], b2, W3s, W3n, b3, W4 [2][64], b4 [2] (row-major).
  * Training: (r, e = A^+ r) pairs from the context's own CG solves (tp_cg_harvest), prepared once
- * (tp_gnn_prepare_pairs), then Adam steps on L = (z^T A z - 2 z^T r + e^T r) / e^T r with
- * z = M_2L^-1 r + G r (tp_gnn_train_step), the A-norm error of z relative to that of z = 0.
+ * (tp_gnn_prepare_pairs), then Adam steps (tp_gnn_train_step) on the A-norm error of the best
+ * multiple of z = M_2L^-1 r + G r (preconditioned CG does not see the preconditioner's scale):
+ *   L = min_a ||a z - e||_A^2 / ||e||_A^2 = 1 - (z^T r)^2 / ((z^T A z)(e^T r)),  in [0, 1].
  * Every tp_gnn_* call fails with TP_ERR_UNSUPPORTED on a context not created with
  * TP_PRECOND_LEARNED (only those hold the network's scratch, about 1.6 KB per edge). */
 TPE_API int tp_gnn_num_params(void);
@@ -290,10 +295,13 @@ TPE_API tp_status tp_gnn_out_grad(tp_ctx *ctx, const double *r, const double *gz
 TPE_API tp_status tp_cg_harvest(tp_ctx *ctx, const double *gamma, const double *rhs, int every, int max_pairs,
                                 double *R, double *E, int *n_pairs, tp_solve_info *info, tp_stream stream);
 
-/* For n harvested pairs of the curve gamma: ER[k] (DEVICE double [n][n_problems]) = e_k . r_k per
- * problem, B[k] = P M_2L^-1 r_k (the preconditioner without the learned term) and AB[k] = A-bar B[k].
- * R, E, B, AB DEVICE double [n][nV][3]; B may be the same buffer as E (ER is taken first). */
-TPE_API tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, const double *R, double *E,
+/* For n harvested pairs of the curve gamma: first R[k] := A-bar E[k] (CG's recursive residual drifts
+ * below the true residual when the operator is inexact, so only A-bar e_k is exactly consistent with
+ * e_k; on output every pair satisfies r = A-bar e), then ER[k] (DEVICE double [n][n_problems]) =
+ * e_k . r_k per problem, B[k] = P M_2L^-1 r_k (the preconditioner without the learned term) and
+ * AB[k] = A-bar B[k].  R, E, B, AB DEVICE double [n][nV][3]; B may be the same buffer as E (ER is
+ * taken first).  Costs two A-bar applies per pair. */
+TPE_API tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, double *R, double *E,
                                        double *B, double *AB, double *ER, tp_stream stream);
 
 /* One training step on n prepared pairs of the bound curve gamma: the loss at the current parameters,
@@ -303,6 +311,28 @@ TPE_API tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, 
 TPE_API tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, const double *R, const double *B,
                                     const double *AB, const double *ER, float lr, double *loss, float *grad,
                                     tp_stream stream);
+
+/* Autotuner of the pair passes (not in the paper).  For TP_MIXED contexts with the specialised
+ * powers ((alpha, beta) = (2, 4.5)) it times, on the curve gamma, every candidate number of target
+ * edges per thread of the energy (1, 2, 4), differential (1, 2) and apply / diag (1, 2, 4) gather
+ * passes, and the symmetric apply pass (each unordered pair evaluated once, 1 or 2 targets per thread,
+ * when its partial sums fit in 16 GB), one warm-up and three timed passes each (CUDA events on
+ * `stream`), and keeps the fastest, rebuilding that op's work queue; other contexts keep their
+ * defaults and are left unchanged.
+ *   tpt (HOST int32 [4], may be NULL): the chosen targets per thread of the energy, differential and
+ *       apply gather passes, then of the symmetric apply (0: the apply uses the gather pass).
+ *   ms  (HOST double [11], may be NULL): ms per pass for 1, 2, 4 targets per thread of the energy
+ *       [0..2], differential [3..5] and apply [6..8] gather passes, then the symmetric apply with 1, 2
+ *       [9..10] (0 where not a candidate).
+ * May reallocate the context's partial-sum buffer (the only allocation after tp_create).
+ * Synchronises the stream.  Errors: TP_ERR_INVALID_ARG, TP_ERR_CUDA, TP_ERR_DEGENERATE_EDGE. */
+TPE_API tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms, tp_stream stream);
+
+/* Select the apply pass: symmetric_tpt = 0 the gather pass (every ordered pair, the default), 1 or 2
+ * the symmetric pass (every unordered pair evaluated once; both rows receive their terms; TP_MIXED with
+ * (alpha, beta) = (2, 4.5) only, else TP_ERR_UNSUPPORTED) with that many target edges per thread.  Both
+ * are deterministic and differ only in summation order.  May grow the partial-sum buffer. */
+TPE_API tp_status tp_set_apply_variant(tp_ctx *ctx, int symmetric_tpt);
 
 /* Throughput microbenchmarks on the current device (no context needed): FP32 FMA FLOP/s, MUFU
  * rsqrt op/s and FP64 FMA FLOP/s.  Returns 0 on success. */

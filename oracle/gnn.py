@@ -14,8 +14,11 @@ Network (3 layers of width 64 on the edge graph, then a linear read-out of 2 val
 Preconditioner term (SPD by construction), for r with 3 components and r~ = r / sqrt(d):
     delta_I = r~_i2 - r~_i1, sigma_I = r~_i1 + r~_i2, ea = exp(2 a_I), eb = exp(2 b_I)
     (G r)_i2 += (ea delta_I + eb sigma_I) / sqrt(d_i2),  (G r)_i1 += (-ea delta_I + eb sigma_I) / sqrt(d_i1)
-Training loss of one pair (r, e = A^+ r): the A-norm error of z = M^-1 r + G r relative to e,
-    L = (z^T A z - 2 z^T r + e^T r) / (e^T r),   dL/dz = 2 (A z - r) / (e^T r).
+Training loss of one pair (r, e = A^+ r, so e^T r = ||e||_A^2): preconditioned CG does not change
+when M^-1 is scaled, so the loss is the A-norm error of the best multiple of z = M^-1 r + G r,
+    L = min_a ||a z - e||_A^2 / ||e||_A^2 = 1 - (z^T r)^2 / ((z^T A z)(e^T r)),
+the squared A-sine of the angle between z and e.  With s = z^T r, q = z^T A z:
+    dL/dz = -2 s / (q e^T r) (r - (s / q) A z).
 """
 from __future__ import annotations
 
@@ -155,7 +158,9 @@ def loss_and_grad(theta, f, diag, A, r, e, base_z):
     z = base_z + g_apply(out, diag, r)
     Az = A @ z
     er = float((e * r).sum())
-    L = (float((z * Az).sum()) - 2 * float((z * r).sum()) + er) / er
-    gz = 2 * (Az - r) / er
+    s = float((z * r).sum())
+    q = float((z * Az).sum())
+    L = 1.0 - s * s / (q * er)
+    gz = -2.0 * s / (q * er) * (r - (s / q) * Az)
     dout = g_out_grad(out, diag, r, gz)
     return L, backward(theta, cache, dout)

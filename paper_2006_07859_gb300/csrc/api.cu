@@ -200,6 +200,7 @@ void tp_default_params(tp_params *p)
     p->proj_maxit = 5;
     p->independent = 0;
     p->far_cutoff = 10.0;
+    p->use_graphs = 1;
     p->coarse_dim = 64;
 }
 
@@ -238,6 +239,8 @@ void tp_destroy(tp_ctx *ctx)
 {
     if (!ctx) return;
     Ctx &c = ctx->c;
+    graphs_free(c);
+    sym_select(c, 0);
     if (c.sol) solver_free(c);
     spectral_free(c);
     coarse_free(c);
@@ -448,6 +451,15 @@ tp_status tp_set_params(tp_ctx *ctx, const tp_params *p)
     c.prm = *p;
     c.prm.independent = indep;
     set_kernel_params(c);
+    graphs_reset(c);  // captured CG blocks baked in the old kernel parameters
+    if (!c.kp.fast && (c.tpt[0] || c.tpt[1] || c.tpt[2] || c.apply_sym)) {
+        // autotuned variants exist for the specialised powers only: back to the defaults
+        for (int cls = 0; cls < 3; ++cls) {
+            c.tpt[cls] = 0;
+            CK(replan(c, cls));
+        }
+        CK(sym_select(c, 0));
+    }
     if ((p->precond >= TP_PRECOND_SPECTRAL) && !had_spectral) {
         cudaError_t e = spectral_setup(c, 0);
         if (e == cudaErrorNotSupported) return fail(ctx, TP_ERR_UNSUPPORTED, "spectral preconditioner not built");
@@ -943,7 +955,7 @@ tp_status tp_cg_harvest(tp_ctx *ctx, const double *gamma, const double *rhs, int
     return TP_OK;
 }
 
-tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, const double *R, double *E, double *B,
+tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, double *R, double *E, double *B,
                                double *AB, double *ER, tp_stream stream)
 {
     if (!ctx || !gamma || n < 0 || (n > 0 && (!R || !E || !B || !AB || !ER)))
@@ -956,8 +968,11 @@ tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, const do
     if (st) return st;
     const size_t nv3 = 3 * (size_t)c.nV;
     for (int k = 0; k < n; ++k) {
-        const double *r = R + k * nv3;
+        double *r = R + k * nv3;
         double *b = B + k * nv3;
+        // r := A-bar e: the recursive CG residual drifts below the true residual of an inexact
+        // operator, so only A-bar e is exactly consistent with e
+        CK(pair_apply(c, gamma, 0, E + k * nv3, r, s));
         CK(gnn_problem_dot(c, E + k * nv3, r, ER + (size_t)k * c.nProb, s));  // before B may overwrite E
         CK(precond_apply_base(c, r, b, s, nullptr));
         if (c.prm.precond != TP_PRECOND_NONE) CK(project_mean(c, b, s, nullptr));
@@ -984,6 +999,101 @@ tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, const doubl
     CK(cudaMemcpyAsync(c.h_pinned, c.d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (loss) *loss = c.h_pinned[0];
+    return check_err_word(ctx, s);
+}
+
+// ---------------------------------------------------------------------------------- autotuner
+
+tp_status tp_set_apply_variant(tp_ctx *ctx, int symmetric_tpt)
+{
+    if (!ctx) return TP_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (symmetric_tpt < 0 || symmetric_tpt > 2) return fail(ctx, TP_ERR_INVALID_ARG, "symmetric_tpt must be 0, 1 or 2");
+    if (symmetric_tpt > 0 && !(c.prm.precision == TP_MIXED && c.kp.fast))
+        return fail(ctx, TP_ERR_UNSUPPORTED, "the symmetric apply exists for TP_MIXED with (alpha, beta) = (2, 4.5)");
+    CK(sym_select(c, symmetric_tpt));
+    return TP_OK;
+}
+
+tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms, tp_stream stream)
+{
+    if (!ctx || !gamma) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx &c = ctx->c;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    if (ms)
+        for (int k = 0; k < 11; ++k) ms[k] = 0.0;
+    if (tpt) tpt[3] = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int prof = c.profile;
+    c.profile = 0;
+    const int *skip = c.d_skip;
+    c.d_skip = nullptr;
+    auto run = [&](int cls) -> cudaError_t {
+        if (cls == 0) return pair_energy(c, gamma, 0, c.d_rows, c.d_E, s);
+        if (cls == 1) return pair_diff(c, gamma, 0, c.d_t2, s);
+        return pair_apply(c, gamma, 0, gamma, c.d_t2, s);  // any u times the same
+    };
+    cudaError_t err = cudaSuccess;
+    for (int cls = 0; cls < 3 && err == cudaSuccess; ++cls) {
+        int cand[4];
+        const int nc = tpt_candidates(c, cls, cand);
+        int best = cand[0];
+        float best_ms = 1e30f;
+        for (int i = 0; i < nc && nc > 1 && err == cudaSuccess; ++i) {
+            c.tpt[cls] = cand[i];
+            if ((err = replan(c, cls)) != cudaSuccess) break;
+            if ((err = run(cls)) != cudaSuccess) break;  // warm-up
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run(cls);
+            cudaEventRecord(e1, s);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+            t /= 3.f;
+            if (ms && cand[i] >= 1 && cand[i] <= 4) ms[3 * cls + (cand[i] == 4 ? 2 : cand[i] - 1)] = t;
+            if (t < best_ms) {
+                best_ms = t;
+                best = cand[i];
+            }
+        }
+        if (err == cudaSuccess && nc > 1) {
+            c.tpt[cls] = best;
+            err = replan(c, cls);
+        }
+        if (tpt) tpt[cls] = nc > 1 ? best : cand[0];
+        // the apply also has the symmetric pass (each unordered pair once), if its partial slots fit
+        if (cls == 2 && nc > 1 && err == cudaSuccess) {
+            int best_sym = 0;
+            for (int t = 1; t <= 2 && err == cudaSuccess; ++t) {
+                if (sym_slots(c, t) * (size_t)c.nE * 6 * sizeof(double) > ((size_t)16 << 30)) continue;
+                if ((err = sym_select(c, t)) != cudaSuccess) break;
+                if ((err = run(cls)) != cudaSuccess) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run(cls);
+                cudaEventRecord(e1, s);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                float tm = 0.f;
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&tm, e0, e1);
+                tm /= 3.f;
+                if (ms) ms[9 + t - 1] = tm;
+                if (tm < best_ms) {
+                    best_ms = tm;
+                    best_sym = t;
+                }
+            }
+            if (err == cudaSuccess) err = sym_select(c, best_sym);
+            if (tpt) tpt[3] = best_sym;
+        }
+    }
+    c.profile = prof;
+    c.d_skip = skip;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(err);
     return check_err_word(ctx, s);
 }
 

@@ -9,8 +9,9 @@
 // Z = the m - 1 first of m periodic hat functions per closed curve (centres i = j n / m, support of
 // two hat widths; the m hats sum to 1, so the dropped one is implied on the mean-free subspace).
 // Z^T A Z is assembled with (m - 1) / 3 applies of the pair kernel (three hats per apply, one per
-// component) and Cholesky-factored per curve in FP64.  Per CG iteration the term costs three O(n)
-// kernels: restriction Z^T r, the (m - 1) x (m - 1) triangular solves, prolongation Z y.
+// component), Cholesky-factored per curve in FP64 and inverted explicitly (L^-T L^-1) at set-up.
+// Per CG iteration the term costs three small kernels: restriction Z^T r, the (m - 1) x (m - 1)
+// mat-vec with the inverse (all rows and components in parallel), prolongation Z y.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,7 +41,8 @@ struct tpe::CoarseState {
     std::vector<CoarseCurve> curves;
     CoarseCurve *d_curves = nullptr;
     int *d_vcurve = nullptr;
-    double *d_L = nullptr;  // Cholesky factors (lower, row-major) per curve
+    double *d_L = nullptr;   // per curve: (Z^T A Z)^-1, row-major (m-1) x (m-1)
+    double *d_Li = nullptr;  // set-up scratch: L^-1 of the Cholesky factor, same layout
     double *d_w = nullptr;  // coarse vectors
     int max_m = 0;
     int ready = 0;
@@ -112,8 +114,9 @@ __global__ void k_coarse_gram(int b, const CoarseCurve *__restrict__ cc, const d
         }
 }
 
-// symmetrise and Cholesky-factor every curve's coarse matrix in place (one block per curve)
-__global__ void k_coarse_factor(const CoarseCurve *__restrict__ cc, double *__restrict__ L)
+// symmetrise, Cholesky-factor and invert every curve's coarse matrix in place (one block per curve);
+// Li: scratch of the same layout for L^-1
+__global__ void k_coarse_factor(const CoarseCurve *__restrict__ cc, double *__restrict__ L, double *__restrict__ Li)
 {
     const CoarseCurve C = cc[blockIdx.x];
     const int mm = C.m - 1;
@@ -139,7 +142,22 @@ __global__ void k_coarse_factor(const CoarseCurve *__restrict__ cc, double *__re
         }
         __syncthreads();
     }
-    for (int t = threadIdx.x; t < mm * mm; t += blockDim.x) g[t] = a[t];
+    // L^-1 by forward substitution, one column per thread, then (Z^T A Z)^-1 = L^-T L^-1
+    double *li = Li + C.aoff;
+    for (int col = threadIdx.x; col < mm; col += blockDim.x) {
+        for (int r = 0; r < mm; ++r) {
+            double v = (r == col) ? 1.0 : 0.0;
+            for (int k = col; k < r; ++k) v -= a[r * mm + k] * li[k * mm + col];
+            li[r * mm + col] = r < col ? 0.0 : v / a[r * mm + r];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < mm * mm; t += blockDim.x) {
+        const int r = t / mm, col = t % mm;
+        double v = 0.0;
+        for (int k = max(r, col); k < mm; ++k) v += li[k * mm + r] * li[k * mm + col];
+        g[t] = v;
+    }
 }
 
 // w[j][q] = Z_j^T r: one block per (curve, j)
@@ -169,24 +187,22 @@ __global__ void k_coarse_restrict(const CoarseCurve *__restrict__ cc, const doub
         for (int q = 0; q < 3; ++q) w[C.woff + 3 * j + q] = sh[q][0];
 }
 
-// y = (L L^T)^-1 w per curve and component (three threads per curve block, one per component)
-__global__ void k_coarse_solve(const CoarseCurve *__restrict__ cc, const double *__restrict__ L, double *__restrict__ w)
+// y = (Z^T A Z)^-1 w per curve: one block per curve, one thread per (row, component)
+__global__ void k_coarse_solve(const CoarseCurve *__restrict__ cc, const double *__restrict__ Ainv,
+                               double *__restrict__ w)
 {
     const CoarseCurve C = cc[blockIdx.x];
-    const int q = threadIdx.x;
-    if (q >= 3) return;
     const int mm = C.m - 1;
-    const double *a = L + C.aoff;
+    const double *a = Ainv + C.aoff;
     double *y = w + C.woff;
-    for (int r = 0; r < mm; ++r) {  // L z = w
-        double s = y[3 * r + q];
-        for (int k = 0; k < r; ++k) s -= a[r * mm + k] * y[3 * k + q];
-        y[3 * r + q] = s / a[r * mm + r];
-    }
-    for (int r = mm - 1; r >= 0; --r) {  // L^T y = z
-        double s = y[3 * r + q];
-        for (int k = r + 1; k < mm; ++k) s -= a[k * mm + r] * y[3 * k + q];
-        y[3 * r + q] = s / a[r * mm + r];
+    __shared__ double sw[3 * kMaxCoarse];
+    for (int t = threadIdx.x; t < 3 * mm; t += blockDim.x) sw[t] = y[t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * mm; t += blockDim.x) {
+        const int r = t / 3, q = t % 3;
+        double s = 0.0;
+        for (int k = 0; k < mm; ++k) s += a[r * mm + k] * sw[3 * k + q];
+        y[t] = s;
     }
 }
 
@@ -235,6 +251,7 @@ cudaError_t coarse_init(Ctx &c)
     TPE_CHECK(cudaMalloc(&S.d_vcurve, sizeof(int) * c.nV));
     TPE_CHECK(cudaMemcpy(S.d_vcurve, vc.data(), sizeof(int) * c.nV, cudaMemcpyHostToDevice));
     TPE_CHECK(cudaMalloc(&S.d_L, sizeof(double) * std::max<long long>(1, aoff)));
+    TPE_CHECK(cudaMalloc(&S.d_Li, sizeof(double) * std::max<long long>(1, aoff)));
     TPE_CHECK(cudaMalloc(&S.d_w, sizeof(double) * std::max<long long>(1, woff)));
     return cudaSuccess;
 }
@@ -245,6 +262,7 @@ void coarse_free(Ctx &c)
     cudaFree(c.coarse->d_curves);
     cudaFree(c.coarse->d_vcurve);
     cudaFree(c.coarse->d_L);
+    cudaFree(c.coarse->d_Li);
     cudaFree(c.coarse->d_w);
     delete c.coarse;
     c.coarse = nullptr;
@@ -264,7 +282,7 @@ cudaError_t coarse_setup(Ctx &c, const double *gamma_geom, int which, cudaStream
         k_coarse_gram<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(b, S.d_curves, c.d_q, S.d_L);
         c.launches++;
     }
-    k_coarse_factor<<<c.nCurves, 256, 0, s>>>(S.d_curves, S.d_L);
+    k_coarse_factor<<<c.nCurves, 256, 0, s>>>(S.d_curves, S.d_L, S.d_Li);
     c.launches++;
     S.ready = 1;
     return cudaGetLastError();
@@ -276,7 +294,7 @@ cudaError_t coarse_apply(Ctx &c, const double *r, double *z, cudaStream_t s)
     if (!c.coarse || !c.coarse->ready) return cudaSuccess;
     CoarseState &S = *c.coarse;
     k_coarse_restrict<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(S.d_curves, r, S.d_w);
-    k_coarse_solve<<<c.nCurves, 32, 0, s>>>(S.d_curves, S.d_L, S.d_w);
+    k_coarse_solve<<<c.nCurves, 3 * kMaxCoarse, 0, s>>>(S.d_curves, S.d_L, S.d_w);
     k_coarse_prolong<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_w, z);
     c.launches += 3;
     return cudaGetLastError();

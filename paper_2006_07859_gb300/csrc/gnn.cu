@@ -12,9 +12,10 @@
 //    log(l_{I-1} / l_I), log(l_{I+1} / l_I), 1]
 // Layers: h1 = relu(W1 f + b1); h2 = relu(W2s h1 + W2n avg(h1[I-1], h1[I+1]) + b2);
 //         h3 = relu(W3s h2 + W3n avg(h2[I-1], h2[I+1]) + b3); (a, b) = W4 h3 + b4.
-// Training minimises the A-norm error of z = M^-1 r + G r against the exact correction e = A^+ r of
-// (residual, correction) pairs harvested from the CG solves:
-//   L = (z^T A z - 2 z^T r + e^T r) / e^T r,   dL/dz = 2 (A z - r) / e^T r.
+// Training minimises, over (residual, correction) pairs harvested from the CG solves (e = A^+ r), the
+// A-norm error of the best multiple of z = M^-1 r + G r (preconditioned CG ignores the scale of M):
+//   L = min_a ||a z - e||_A^2 / ||e||_A^2 = 1 - s^2 / (q e^T r),  s = z^T r,  q = z^T A z,
+//   dL/dz = -2 s / (q e^T r) (r - (s / q) A z).
 // Parameters are FP32 masters with a BF16 copy; the forward and backward passes read the BF16
 // values (so the gradient is that of the network actually evaluated), Adam updates the masters.
 // The parameter-gradient reductions are deterministic (fixed block partials, fixed-order sums).
@@ -56,6 +57,7 @@ struct GnnState {
     double *cstat = nullptr;                                                // [nCurves][2]: mean l, mean d
     float *wpart = nullptr;                                                 // [kWgBlocks][kWgMax]
     double *loss = nullptr;                                                 // [nProb]
+    double *sq = nullptr;                                                   // [nProb][2]: z^T r, z^T A z
     double *g = nullptr, *Ag = nullptr, *gz = nullptr;                      // [nV][3]
     int *eprev = nullptr, *enext = nullptr, *ecurve = nullptr;              // [nE]
     int loaded = 0, bound = 0, adam_t = 0;
@@ -430,22 +432,25 @@ __global__ void k_gnn_doutput(int nE, const int *__restrict__ E, const double *_
 
 // ---------------------------------------------------------------------------------- training loss
 
-// gz = 2 (Ab + Ag - r) / er_q
+// gz = -2 s / (q er) (r - (s / q) (Ab + Ag)) with (s, q) = sq[problem]
 __global__ void k_gnn_gz(int nV, const int *__restrict__ vprob, const double *__restrict__ r,
                          const double *__restrict__ Ab, const double *__restrict__ Ag, const double *__restrict__ er,
-                         double *__restrict__ gz)
+                         const double *__restrict__ sq, double *__restrict__ gz)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nV) return;
-    const double e = er[vprob[i]];
-    const double inv = e > 0.0 ? 2.0 / e : 0.0;
-    for (int q = 0; q < 3; ++q) gz[3 * i + q] = inv * (Ab[3 * i + q] + Ag[3 * i + q] - r[3 * i + q]);
+    const int p = vprob[i];
+    const double e = er[p], sv = sq[2 * p], qv = sq[2 * p + 1];
+    const bool ok = e > 0.0 && qv > 0.0;
+    const double f = ok ? -2.0 * sv / (qv * e) : 0.0, ratio = ok ? sv / qv : 0.0;
+    for (int k = 0; k < 3; ++k) gz[3 * i + k] = f * (r[3 * i + k] - ratio * (Ab[3 * i + k] + Ag[3 * i + k]));
 }
 
-// loss[q] += scale * ((b+g).(Ab+Ag) - 2 (b+g).r + er_q) / er_q   (one block per problem)
+// per problem (one block each): s = z.r, q = z.(Ab + Ag) with z = b + g into sq; loss[q] += scale (1 - s^2 / (q er))
 __global__ void k_gnn_loss(const int *__restrict__ prob_v, const double *__restrict__ r, const double *__restrict__ b,
                            const double *__restrict__ g, const double *__restrict__ Ab, const double *__restrict__ Ag,
-                           const double *__restrict__ er, double scale, double *__restrict__ loss)
+                           const double *__restrict__ er, double scale, double *__restrict__ sq,
+                           double *__restrict__ loss)
 {
     const int q = blockIdx.x, v0 = prob_v[q], v1 = prob_v[q + 1];
     double s1 = 0, s2 = 0;
@@ -466,8 +471,10 @@ __global__ void k_gnn_loss(const int *__restrict__ prob_v, const double *__restr
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double e = er[q];
-        loss[q] += e > 0.0 ? scale * (sh[0][0] - 2.0 * sh[1][0] + e) / e : 0.0;
+        const double e = er[q], qz = sh[0][0], sz = sh[1][0];
+        sq[2 * q] = sz;
+        sq[2 * q + 1] = qz;
+        loss[q] += (e > 0.0 && qz > 0.0) ? scale * (1.0 - sz * sz / (qz * e)) : 0.0;
     }
 }
 
@@ -530,6 +537,7 @@ cudaError_t gnn_alloc(Ctx &c)
     TPE_CHECK(cudaMalloc(&G.cstat, sizeof(double) * 2 * c.nCurves));
     TPE_CHECK(cudaMalloc(&G.wpart, sizeof(float) * kWgBlocks * kWgMax));
     TPE_CHECK(cudaMalloc(&G.loss, sizeof(double) * std::max(1, c.nProb)));
+    TPE_CHECK(cudaMalloc(&G.sq, sizeof(double) * 2 * std::max(1, c.nProb)));
     TPE_CHECK(cudaMalloc(&G.g, sizeof(double) * 3 * nV));
     TPE_CHECK(cudaMalloc(&G.Ag, sizeof(double) * 3 * nV));
     TPE_CHECK(cudaMalloc(&G.gz, sizeof(double) * 3 * nV));
@@ -557,7 +565,7 @@ void gnn_free(Ctx &c)
     if (!c.gnn) return;
     GnnState &G = *c.gnn;
     void *p[] = {G.master, G.m,     G.v,     G.grad, G.wb, G.feat, G.z1, G.z2,    G.z3,    G.bA,
-                 G.bB,     G.bC,    G.out,   G.dout, G.ew, G.diag, G.cstat, G.wpart, G.loss, G.g,
+                 G.bB,     G.bC,    G.out,   G.dout, G.ew, G.diag, G.cstat, G.wpart, G.loss, G.sq, G.g,
                  G.Ag,     G.gz,    G.eprev, G.enext, G.ecurve};
     for (void *q : p)
         if (q) cudaFree(q);
@@ -712,8 +720,8 @@ cudaError_t gnn_train_step(Ctx &c, const double *gamma, int n_pairs, const doubl
         const double *r = R + i * nv3, *b = B + i * nv3, *Ab = AB + i * nv3, *er = ER + (size_t)i * c.nProb;
         TPE_CHECK(gnn_gapply(c, r, G.g, 0, s, nullptr));
         TPE_CHECK(pair_apply(c, gamma, 0, G.g, G.Ag, s));
-        k_gnn_loss<<<c.nProb, 256, 0, s>>>(c.d_prob_v, r, b, G.g, Ab, G.Ag, er, scale, G.loss);
-        k_gnn_gz<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_vprob, r, Ab, G.Ag, er, G.gz);
+        k_gnn_loss<<<c.nProb, 256, 0, s>>>(c.d_prob_v, r, b, G.g, Ab, G.Ag, er, scale, G.sq, G.loss);
+        k_gnn_gz<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_vprob, r, Ab, G.Ag, er, G.sq, G.gz);
         c.launches += 2;
         TPE_CHECK(gnn_out_grad(c, r, G.gz, scale, i > 0, G.dout, s));
     }

@@ -1,0 +1,381 @@
+// Symmetric Sobolev apply: every unordered pair of disjoint edges {I, J} evaluated once.
+//
+// The Gram weights are symmetric: w_IJ = w_JI and the low-order weight enters as w0_IJ + w0_JI
+// (Secs. 5.2.2-5.2.3).  One evaluation of a pair therefore yields what row I receives from J and what
+// row J receives from I:
+//   row I: h += l_J sw ((du_I - du_J) + (|T_I - T_J|^2 / 2) du_J),   l += l_J sw0 (ub_I - ub_J)
+//   row J: h += l_I sw ((du_J - du_I) + (|T_I - T_J|^2 / 2) du_I),   l += l_I sw0 (ub_J - ub_I)
+// with sw = sum_ab |d_ab|^-p and sw0 = sum_ab (|T_I x d_ab|^2 + |T_J x d_ab|^2) |d_ab|^-(4+p).  The chords
+// and weights are bitwise the same from either side (pair_device.cuh), so the result equals the
+// gather pass's up to summation order.
+//
+// Work items are pairs of edge blocks (b, c >= b) of one problem (block = 128 x TPT edges).  For
+// b < c the CTA owns the targets of block b in registers and streams block c through shared memory;
+// lane l of each warp visits source (step + l) mod P at step `step`, so the 32 lanes of a warp always
+// touch 32 distinct sources and add what those sources receive into the warp's own Kahan-compensated
+// shared-memory accumulators (no atomics).  Target rows of block b write partial slot c, source rows of
+// block c write slot b, and the diagonal item (b, b) is a plain gather over its own block writing slot
+// b: every row receives exactly one write per slot m = 0 .. nblk - 1, and the vertex gather sums the
+// slots in index order, so the pass is deterministic.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pair_device.cuh"
+
+namespace tpe {
+
+#define TPE_CHECK(x)                      \
+    do {                                  \
+        cudaError_t e_ = (x);             \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
+constexpr int kSymWarps = kThreads / 32;
+
+// One unordered pair in mixed precision: target-side terms Kahan-accumulated into `a`, source-side
+// terms added to hs (high-order, 3) and ls (low-order, 3).
+template <bool FAST, bool DF>
+__device__ __forceinline__ void pair_apply_both(const Tgt<float> &t, const Src<PMIX> &s, const UVal<float> &tu,
+                                                const UVal<float> &su, bool keep, const KernelParams &kp,
+                                                Acc32<PMIX, OP_APPLY> &a, float (&hs)[3], float (&ls)[3])
+{
+    const float pp = (float)kp.p;
+    V3<float> dd[4];
+    chords<DF>(t, s, dd);
+    float tt;
+    V3<float> dp;
+    const float cI1 = perp2(dd[0], t.T, tt, dp), cI2 = perp2(dd[1], t.T, tt, dp);
+    const float cJ1 = perp2(dd[0], s.T, tt, dp), cJ2 = perp2(dd[2], s.T, tt, dp);
+    const float c2s[4] = {cI1 + cJ1, cI2 + cJ1, cI1 + cJ2, cI2 + cJ2};
+    float tw[4], tw0[4];
+#pragma unroll
+    for (int ab = 0; ab < 4; ++ab) {
+        const float d2 = dot3(dd[ab], dd[ab]);
+        float r2;
+        const float rp = inv_pow<float, FAST, 1>(d2, pp, r2);
+        tw[ab] = rp;
+        tw0[ab] = c2s[ab] * (rp * r2 * r2);
+    }
+    const float sw = (tw[0] + tw[3]) + (tw[1] + tw[2]);
+    const float sw0 = (tw0[0] + tw0[3]) + (tw0[1] + tw0[2]);
+    const float Wt = keep ? s.ell * sw : 0.f, W0t = keep ? s.ell * sw0 : 0.f;
+    const float Ws = keep ? t.ell * sw : 0.f, W0s = keep ? t.ell * sw0 : 0.f;
+    V3<float> dT = {t.T.x - s.T.x, t.T.y - s.T.y, t.T.z - s.T.z};
+    dT.x += t.Tl.x - s.Tm.x;
+    dT.y += t.Tl.y - s.Tm.y;
+    dT.z += t.Tl.z - s.Tm.z;
+    const float omt = 0.5f * dot3(dT, dT);
+    // differences of the double-float u records (exact difference form)
+    const float ddv[3] = {(tu.dh.x - su.dh.x) + (tu.dl.x - su.dl.x), (tu.dh.y - su.dh.y) + (tu.dl.y - su.dl.y),
+                          (tu.dh.z - su.dh.z) + (tu.dl.z - su.dl.z)};
+    const float dbv[3] = {(tu.uh.x - su.uh.x) + (tu.ul.x - su.ul.x), (tu.uh.y - su.uh.y) + (tu.ul.y - su.ul.y),
+                          (tu.uh.z - su.uh.z) + (tu.ul.z - su.ul.z)};
+    const float sdh[3] = {su.dh.x, su.dh.y, su.dh.z}, tdh[3] = {tu.dh.x, tu.dh.y, tu.dh.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        kahan_add(a.A1[k], a.C1[k], Wt * (ddv[k] + omt * sdh[k]));
+        kahan_add(a.A2[k], a.C2[k], W0t * dbv[k]);
+        hs[k] += Ws * (omt * tdh[k] - ddv[k]);
+        ls[k] -= W0s * dbv[k];
+    }
+}
+
+// Staggered loop over one staged tile: lane l takes source (step + l) mod P, P = max(cnt, 32).
+// CHECK: the tile overlaps the targets' neighbour span (test disjointness per pair); DF: double-float
+// chords (every tile but the far ones); SRC: accumulate what the sources receive (off on the diagonal
+// item, which is a plain gather).
+template <int TPT, bool FAST, bool CHECK, bool DF, bool SRC>
+__device__ __forceinline__ void sym_tile(const Tgt<float> (&tg)[TPT], const UVal<float> (&tu)[TPT],
+                                         const bool (&valid)[TPT], const Tile<PMIX, true> &tl, int cnt,
+                                         Acc32<PMIX, OP_APPLY> (&a)[TPT], float (*sacc)[kTile], float (*scmp)[kTile],
+                                         const KernelParams &kp)
+{
+    const int lane = threadIdx.x & 31;
+    const int P = max(cnt, 32);
+    for (int step = 0; step < P; ++step) {
+        int j = step + lane;
+        if (j >= P) j -= P;
+        if (j < cnt) {
+            Src<PMIX> s;
+            load_source<PMIX, true>(s, tl, j);
+            UVal<float> su;
+            {
+                const float4 x = tl.u[j].a, y = tl.u[j].b, z = tl.u[j].c;
+                su.dh = {x.x, x.y, x.z};
+                su.uh = {x.w, y.x, y.y};
+                su.dl = {y.z, y.w, z.x};
+                su.ul = {z.y, z.z, z.w};
+            }
+            float hs[3] = {0.f, 0.f, 0.f}, ls[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                bool keep = valid[k];
+                if constexpr (CHECK)
+                    keep = keep & (s.j1 != tg[k].i1) & (s.j1 != tg[k].i2) & (s.j2 != tg[k].i1) & (s.j2 != tg[k].i2);
+                pair_apply_both<FAST, DF>(tg[k], s, tu[k], su, keep, kp, a[k], hs, ls);
+            }
+            if constexpr (SRC) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    float acc = sacc[q][j], cmp = scmp[q][j];
+                    kahan_add(acc, cmp, hs[q]);
+                    sacc[q][j] = acc;
+                    scmp[q][j] = cmp;
+                    acc = sacc[3 + q][j];
+                    cmp = scmp[3 + q][j];
+                    kahan_add(acc, cmp, ls[q]);
+                    sacc[3 + q][j] = acc;
+                    scmp[3 + q][j] = cmp;
+                }
+            }
+        }
+        if constexpr (SRC) __syncwarp();  // the next step hands this lane's source to lane - 1
+    }
+}
+
+template <int TPT, bool FAST>
+__global__ void __launch_bounds__(kThreads, 2) k_pairs_sym(const PairArgs pa)
+{
+    __shared__ Tile<PMIX, true> tl;
+    __shared__ float sacc[kSymWarps][6][kTile], scmp[kSymWarps][6][kTile];
+    __shared__ int s_item;
+    __shared__ float s_box[2][kThreads / 32][6];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(pa.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= pa.n_items) break;
+        const WorkItem w = pa.items[it];
+        if (pa.skip && pa.skip[w.pad]) continue;  // problem already converged
+        const int bslot = w.slot >> 16, cslot = w.slot & 0xffff;
+        const bool diag = bslot == cslot;
+        Tgt<float> tg[TPT];
+        UVal<float> tu[TPT];
+        bool valid[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            const int loc = threadIdx.x + k * kThreads;
+            valid[k] = loc < w.ntgt;  // clamped duplicates must not feed the source side
+            const int I = w.tgt0 + min(loc, w.ntgt - 1);
+            load_target<PMIX>(tg[k], I, pa.recF, pa.recLo, pa.recD);
+            load_uval<PMIX>(tu[k], pa.urecF, pa.urecD, I);
+        }
+        Acc64<OP_APPLY> A[TPT];
+        Acc32<PMIX, OP_APPLY> a[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            acc64_zero<OP_APPLY>(A[k]);
+            acc_zero<PMIX, OP_APPLY>(a[k]);
+        }
+        float tbox[6];
+        {
+            float b[6] = {1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) box_add(b, tg[k].p1, tg[k].p2);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                for (int q = 0; q < 6; ++q) {
+                    const float v = __shfl_xor_sync(0xffffffffu, b[q], o);
+                    b[q] = q < 3 ? fminf(b[q], v) : fmaxf(b[q], v);
+                }
+            for (int q = 0; q < 6; ++q) tbox[q] = b[q];
+        }
+        for (int s0 = w.src0; s0 < w.src1; s0 += kTile) {
+            const int cnt = min(kTile, w.src1 - s0);
+            __syncthreads();  // the previous tile's readers are done
+            float sb[6] = {1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
+            if (threadIdx.x < cnt) {
+                const int J = s0 + threadIdx.x;
+                const RecF r = pa.recF[J];
+                tl.r[threadIdx.x] = r;
+                tl.lo[threadIdx.x] = pa.recLo[J];
+                tl.u[threadIdx.x] = pa.urecF[J];
+                box_add(sb, V3<float>{r.a.x, r.a.y, r.a.z}, V3<float>{r.b.x, r.b.y, r.b.z});
+            }
+            for (int t = lane; t < kTile; t += 32)
+                for (int q = 0; q < 6; ++q) sacc[wid][q][t] = scmp[wid][q][t] = 0.f;
+            block_box(sb, s_box[1]);  // contains the barrier that publishes the tile
+            const bool check = !(s0 + cnt - 1 < w.nb_lo || s0 > w.nb_hi);
+            float g2 = 0.f;
+            for (int q = 0; q < 3; ++q) {
+                const float gap = fmaxf(fmaxf(sb[q] - tbox[3 + q], tbox[q] - sb[3 + q]), 0.f);
+                g2 += gap * gap;
+            }
+            const bool far = g2 >= pa.kp.mid2f;
+            if (diag) {
+                sym_tile<TPT, FAST, true, true, false>(tg, tu, valid, tl, cnt, a, sacc[wid], scmp[wid], pa.kp);
+            } else if (check) {
+                sym_tile<TPT, FAST, true, true, true>(tg, tu, valid, tl, cnt, a, sacc[wid], scmp[wid], pa.kp);
+            } else if (!far) {
+                sym_tile<TPT, FAST, false, true, true>(tg, tu, valid, tl, cnt, a, sacc[wid], scmp[wid], pa.kp);
+            } else {
+                sym_tile<TPT, FAST, false, false, true>(tg, tu, valid, tl, cnt, a, sacc[wid], scmp[wid], pa.kp);
+            }
+            // fold the target tile accumulators into FP64
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                acc_add(A[k], a[k]);
+                acc_zero<PMIX, OP_APPLY>(a[k]);
+            }
+            if (!diag) {
+                __syncthreads();  // every warp's source accumulators are complete
+                if (threadIdx.x < cnt) {
+                    const int J = s0 + threadIdx.x;
+                    double v[6];
+                    for (int q = 0; q < 6; ++q) {
+                        double x = 0.0;
+                        for (int wv = 0; wv < kSymWarps; ++wv)
+                            x += (double)sacc[wv][q][threadIdx.x] - (double)scmp[wv][q][threadIdx.x];
+                        v[q] = x;
+                    }
+                    const double l = pa.na.ell[J];
+                    double *o = pa.part + ((size_t)bslot * pa.nE + J) * 6;
+                    for (int q = 0; q < 3; ++q) {
+                        o[q] = 0.5 * v[q];
+                        o[3 + q] = 0.125 * l * v[3 + q];
+                    }
+                }
+            }
+        }
+        // target rows of block b: slot c
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            if (!valid[k]) continue;
+            const int I = w.tgt0 + threadIdx.x + k * kThreads;
+            const double l = pa.na.ell[I];
+            double *o = pa.part + ((size_t)cslot * pa.nE + I) * 6;
+            for (int q = 0; q < 3; ++q) {
+                o[q] = 0.5 * A[k].A1[q];
+                o[3 + q] = 0.125 * l * A[k].A2[q];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------- host side
+
+static int sym_occupancy(int tpt)
+{
+    int occ = 0;
+    if (tpt == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs_sym<1, true>, kThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pairs_sym<2, true>, kThreads, 0);
+    return occ;
+}
+
+// Edge blocks of 128 x tpt per problem; items (b, c >= b) sorted by problem size (large first).
+static void sym_plan_items(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy)
+{
+    const int tb = kThreads * tpt;
+    std::vector<int> vmin(c.nV, INT32_MAX), vmax(c.nV, -1);
+    for (int I = 0; I < c.nE; ++I)
+        for (int s = 0; s < 2; ++s) {
+            const int v = c.h_edges[2 * I + s];
+            vmin[v] = std::min(vmin[v], I);
+            vmax[v] = std::max(vmax[v], I);
+        }
+    std::vector<std::pair<long long, WorkItem>> tmp;
+    std::vector<int> eslots(std::max(1, c.nE), 1);
+    int max_slots = 1;
+    for (int q = 0; q < c.nProb; ++q) {
+        const int e0 = c.h_prob_e[q], e1 = c.h_prob_e[q + 1], n = e1 - e0;
+        if (n <= 0) continue;
+        const int nblk = (n + tb - 1) / tb;
+        max_slots = std::max(max_slots, nblk);
+        for (int b = 0; b < nblk; ++b) {
+            const int t0 = e0 + b * tb, nt = std::min(tb, e1 - t0);
+            int lo = INT32_MAX, hi = -1;
+            for (int I = t0; I < t0 + nt; ++I)
+                for (int s = 0; s < 2; ++s) {
+                    const int v = c.h_edges[2 * I + s];
+                    lo = std::min(lo, vmin[v]);
+                    hi = std::max(hi, vmax[v]);
+                }
+            for (int cb = b; cb < nblk; ++cb) {
+                const int s0 = e0 + cb * tb, s1 = std::min(e1, s0 + tb);
+                tmp.push_back({(long long)n, WorkItem{t0, nt, s0, s1, (b << 16) | cb, lo, hi, q}});
+            }
+        }
+        for (int I = e0; I < e1; ++I) eslots[I] = nblk;
+    }
+    std::stable_sort(tmp.begin(), tmp.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<WorkItem> items;
+    items.reserve(tmp.size());
+    for (auto &t : tmp) items.push_back(t.second);
+    pl.n_items = (int)items.size();
+    pl.max_slots = max_slots;
+    pl.tpt = tpt;
+    pl.grid = std::max(1, std::min(pl.n_items, c.sm_count * std::max(1, occupancy)));
+    cudaMalloc(&pl.d_items, sizeof(WorkItem) * std::max<size_t>(1, items.size()));
+    cudaMemcpy(pl.d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice);
+    cudaMalloc(&pl.d_eslots, sizeof(int) * std::max(1, c.nE));
+    cudaMemcpy(pl.d_eslots, eslots.data(), sizeof(int) * std::max(1, c.nE), cudaMemcpyHostToDevice);
+}
+
+// Slots the symmetric pass needs per row (the largest problem's block count) at tpt targets per thread.
+size_t sym_slots(const Ctx &c, int tpt)
+{
+    const int tb = kThreads * tpt;
+    int m = 1;
+    for (int q = 0; q < c.nProb; ++q) m = std::max(m, (c.h_prob_e[q + 1] - c.h_prob_e[q] + tb - 1) / tb);
+    return (size_t)m;
+}
+
+// Switch the apply to the symmetric pass with tpt targets per thread (1 or 2), or back to the gather
+// pass (tpt = 0).  Mixed precision with the specialised powers only; grows the partial buffer if needed.
+cudaError_t sym_select(Ctx &c, int tpt)
+{
+    graphs_reset(c);
+    Ctx::Plan &pl = c.plan_sym;
+    if (pl.d_items) TPE_CHECK(cudaFree(pl.d_items));
+    if (pl.d_eslots) TPE_CHECK(cudaFree(pl.d_eslots));
+    pl = Ctx::Plan{};
+    c.apply_sym = 0;
+    if (tpt <= 0) return cudaSuccess;
+    if (c.prm.precision != TP_MIXED || !c.kp.fast || (tpt != 1 && tpt != 2)) return cudaErrorInvalidValue;
+    sym_plan_items(c, pl, tpt, sym_occupancy(tpt));
+    const size_t need = (size_t)pl.max_slots * std::max(1, c.nE) * 6;
+    if (need > c.part_elems) {
+        TPE_CHECK(cudaFree(c.d_part));
+        TPE_CHECK(cudaMalloc(&c.d_part, sizeof(double) * need));
+        c.part_elems = need;
+    }
+    c.apply_sym = tpt;
+    return cudaGetLastError();
+}
+
+cudaError_t sym_apply_pass(Ctx &c, int which, const double *gamma, const double *u, cudaStream_t s)
+{
+    Ctx::Plan &pl = c.plan_sym;
+    if (pl.n_items == 0) return cudaSuccess;
+    TPE_CHECK(cudaMemsetAsync(c.d_counter + 4, 0, sizeof(int), s));
+    PairArgs pa;
+    pa.items = pl.d_items;
+    pa.n_items = pl.n_items;
+    pa.counter = c.d_counter + 4;
+    pa.recF = which ? c.d_recF2 : c.d_recF;
+    pa.recLo = which ? c.d_recLo2 : c.d_recLo;
+    pa.recD = nullptr;
+    pa.urecF = c.d_urecF;
+    pa.urecD = nullptr;
+    pa.na = NearArgs{gamma, c.d_edges, c.d_ellw[which], c.d_Tw[which], u};
+    pa.part = c.d_part;
+    pa.nE = c.nE;
+    pa.kp = c.kp;
+    pa.skip = c.d_skip;
+    const int slot = c.profile ? prof_begin(c, c.d_skip ? 4 : 2, s) : -1;
+    if (pl.tpt == 1)
+        k_pairs_sym<1, true><<<pl.grid, kThreads, 0, s>>>(pa);
+    else
+        k_pairs_sym<2, true><<<pl.grid, kThreads, 0, s>>>(pa);
+    if (slot >= 0 || slot <= -2) prof_end(c, slot, s);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace tpe

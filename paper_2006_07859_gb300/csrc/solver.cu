@@ -644,6 +644,116 @@ static cudaError_t projector(Ctx &c, int mode, double *v, cudaStream_t s, const 
     return mode ? project_mean(c, v, s, skip) : project(c, v, s, skip);
 }
 
+// ---------------------------------------------------------------------------------- CUDA graphs of CG blocks
+
+static cudaError_t graph_stream(Ctx &c)
+{
+    if (c.cg_stream) return cudaSuccess;
+    TPE_CHECK(cudaStreamCreateWithFlags(&c.cg_stream, cudaStreamNonBlocking));
+    TPE_CHECK(cudaEventCreateWithFlags(&c.cg_join[0], cudaEventDisableTiming));
+    TPE_CHECK(cudaEventCreateWithFlags(&c.cg_join[1], cudaEventDisableTiming));
+    return cudaSuccess;
+}
+
+static void graph_destroy(CgGraph &g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e : g.ev)
+        if (e) cudaEventDestroy(e);
+    g = CgGraph{};
+}
+
+void graphs_reset(Ctx &c)
+{
+    for (auto &g : c.graphs) graph_destroy(g);
+    c.graphs.clear();
+}
+
+void graphs_free(Ctx &c)
+{
+    for (auto &g : c.graphs) graph_destroy(g);
+    c.graphs.clear();
+    if (c.cg_stream) cudaStreamDestroy(c.cg_stream);
+    for (auto &e : c.cg_join)
+        if (e) cudaEventDestroy(e);
+    c.cg_stream = nullptr;
+    c.cg_join[0] = c.cg_join[1] = nullptr;
+}
+
+// Profiled pair-kernel times of the last replay of g into the context's per-op totals.
+static void graph_prof_harvest(Ctx &c, CgGraph &g)
+{
+    for (size_t k = 0; k < g.prof_op.size(); ++k) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g.ev[2 * k], g.ev[2 * k + 1]) == cudaSuccess) {
+            c.prof_ms[g.prof_op[k]] += ms;
+            c.prof_n[g.prof_op[k]] += 1;
+        }
+    }
+}
+
+// The cached graph of `every` CG iterations for this solve's settings, captured on first use.  A
+// failed capture leaves *out = NULL and switches the context to direct launches.
+template <class Body>
+static cudaError_t graph_block(Ctx &c, const double *gamma_geom, int which, int proj_mode, int every, double tol2,
+                               Body &body, cudaStream_t cs, CgGraph **out)
+{
+    *out = nullptr;
+    const void *items = c.plan_apply.d_items;
+    for (auto &g : c.graphs)
+        if (g.exec && g.gamma == gamma_geom && g.which == which && g.proj_mode == proj_mode &&
+            g.precond == c.prm.precond && g.every == every && g.profile == c.profile && g.items == items &&
+            g.tpt == c.plan_apply.tpt && g.tol2 == tol2 && g.sym == c.apply_sym) {
+            g.stamp = ++c.graph_clock;
+            *out = &g;
+            return cudaSuccess;
+        }
+    if (c.graphs.size() < 4) c.graphs.emplace_back();
+    CgGraph *slot = &c.graphs[0];
+    for (auto &g : c.graphs)
+        if (g.stamp < slot->stamp) slot = &g;
+    graph_destroy(*slot);
+    CgGraph &g = *slot;
+    g.gamma = gamma_geom;
+    g.which = which;
+    g.proj_mode = proj_mode;
+    g.precond = c.prm.precond;
+    g.every = every;
+    g.profile = c.profile;
+    g.items = items;
+    g.tpt = c.plan_apply.tpt;
+    g.tol2 = tol2;
+    g.sym = c.apply_sym;
+    g.stamp = ++c.graph_clock;
+    if (c.profile) {
+        g.ev.resize(4 * every + 8);
+        for (auto &e : g.ev) TPE_CHECK(cudaEventCreate(&e));
+    }
+    if (c.profile) prof_harvest(c);  // nothing recorded on the stream may be waited on during capture
+    const int64_t l0 = c.launches;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        c.capturing = &g;
+        for (int k = 0; k < every && e == cudaSuccess; ++k) e = body(cs);
+        c.capturing = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    g.launches = c.launches - l0;
+    c.launches = l0;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear the capture error; the solve continues with direct launches
+        graph_destroy(g);
+        c.graphs_broken = 1;
+        return cudaSuccess;
+    }
+    *out = &g;
+    return cudaSuccess;
+}
+
 cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
                      int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s,
                      int proj_mode, int *conv_flags)
@@ -665,35 +775,68 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
     const int every = std::max(1, c.prm.cg_check_every);
     int it = 0;
     int *h_active = c.h_pinned_i;
-    for (; it < maxit;) {
+    // one CG iteration enqueued on stream ss
+    auto body = [&](cudaStream_t ss) -> cudaError_t {
         // q = P A-bar p (work items of converged problems are skipped)
         c.d_skip = st.done;
-        cudaError_t ea = pair_apply(c, gamma_geom, which, p, q, s);
+        cudaError_t ea = pair_apply(c, gamma_geom, which, p, q, ss);
         c.d_skip = nullptr;
         TPE_CHECK(ea);
-        TPE_CHECK(projector(c, proj_mode, q, s, st.done));
-        k_cg_alpha<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 5), p, q, c.d_cg, st.done);
-        k_cg_update<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 6), c.d_vprob, p, q, y, r, c.d_cg, st.done, tol2,
-                                                   st.active);
+        TPE_CHECK(projector(c, proj_mode, q, ss, st.done));
+        k_cg_alpha<<<st.v_n, kRedThreads, 0, ss>>>(vargs(c, 5), p, q, c.d_cg, st.done);
+        k_cg_update<<<st.v_n, kRedThreads, 0, ss>>>(vargs(c, 6), c.d_vprob, p, q, y, r, c.d_cg, st.done, tol2,
+                                                    st.active);
         c.launches += 2;
-        TPE_CHECK(precond_apply(c, r, z, s, st.done));
-        if (c.prm.precond != TP_PRECOND_NONE) TPE_CHECK(projector(c, proj_mode, z, s, st.done));
-        k_cg_beta<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 7), r, c.prm.precond != TP_PRECOND_NONE ? z : r, c.d_cg,
-                                                 st.done);
-        k_cg_p<<<nb, 256, 0, s>>>(c.nV, c.d_vprob, c.prm.precond != TP_PRECOND_NONE ? z : r, p, c.d_cg, st.done);
+        TPE_CHECK(precond_apply(c, r, z, ss, st.done));
+        if (c.prm.precond != TP_PRECOND_NONE) TPE_CHECK(projector(c, proj_mode, z, ss, st.done));
+        k_cg_beta<<<st.v_n, kRedThreads, 0, ss>>>(vargs(c, 7), r, c.prm.precond != TP_PRECOND_NONE ? z : r,
+                                                  c.d_cg, st.done);
+        k_cg_p<<<nb, 256, 0, ss>>>(c.nV, c.d_vprob, c.prm.precond != TP_PRECOND_NONE ? z : r, p, c.d_cg, st.done);
         c.launches += 2;
+        return cudaGetLastError();
+    };
+    // Blocks of `every` iterations between host polls run as captured graphs (not while pairs are
+    // being harvested, which copies per iteration).
+    const bool graphs = c.prm.use_graphs && !c.graphs_broken && !c.hv.R && maxit >= every;
+    cudaStream_t rs = s;
+    if (graphs) {
+        TPE_CHECK(graph_stream(c));
+        rs = c.cg_stream;
+        TPE_CHECK(cudaEventRecord(c.cg_join[0], s));
+        TPE_CHECK(cudaStreamWaitEvent(rs, c.cg_join[0], 0));
+    }
+    for (; it < maxit;) {
+        if (graphs && !c.graphs_broken && maxit - it >= every) {
+            CgGraph *g = nullptr;
+            TPE_CHECK(graph_block(c, gamma_geom, which, proj_mode, every, tol2, body, rs, &g));
+            if (g) {
+                TPE_CHECK(cudaGraphLaunch(g->exec, rs));
+                c.launches += g->launches;
+                it += every;
+                TPE_CHECK(cudaMemcpyAsync(h_active, st.active, sizeof(int), cudaMemcpyDeviceToHost, rs));
+                TPE_CHECK(cudaStreamSynchronize(rs));
+                graph_prof_harvest(c, *g);
+                if (*h_active == 0) break;
+                continue;
+            }
+        }
+        TPE_CHECK(body(rs));
         ++it;
         if (c.hv.R && c.hv.n < c.hv.max && it % c.hv.every == 0) {
             const size_t off = (size_t)c.hv.n * 3 * c.nV;
-            TPE_CHECK(cudaMemcpyAsync(c.hv.R + off, r, vb, cudaMemcpyDeviceToDevice, s));
-            TPE_CHECK(cudaMemcpyAsync(c.hv.Y + off, y, vb, cudaMemcpyDeviceToDevice, s));
+            TPE_CHECK(cudaMemcpyAsync(c.hv.R + off, r, vb, cudaMemcpyDeviceToDevice, rs));
+            TPE_CHECK(cudaMemcpyAsync(c.hv.Y + off, y, vb, cudaMemcpyDeviceToDevice, rs));
             c.hv.n++;
         }
         if (it % every == 0 || it == maxit) {
-            TPE_CHECK(cudaMemcpyAsync(h_active, st.active, sizeof(int), cudaMemcpyDeviceToHost, s));
-            TPE_CHECK(cudaStreamSynchronize(s));
+            TPE_CHECK(cudaMemcpyAsync(h_active, st.active, sizeof(int), cudaMemcpyDeviceToHost, rs));
+            TPE_CHECK(cudaStreamSynchronize(rs));
             if (*h_active == 0) break;
         }
+    }
+    if (graphs) {  // join: the caller's stream waits for the iterations
+        TPE_CHECK(cudaEventRecord(c.cg_join[1], rs));
+        TPE_CHECK(cudaStreamWaitEvent(s, c.cg_join[1], 0));
     }
     // x = P y; true residual r = P (rhs - A-bar x) with the working-precision operator
     TPE_CHECK(cudaMemcpyAsync(x, y, vb, cudaMemcpyDeviceToDevice, s));

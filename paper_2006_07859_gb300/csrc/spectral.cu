@@ -69,6 +69,9 @@ struct tpe::SpecState {
     int *d_vcurve = nullptr;     // [nV] curve of each vertex
     int max_nk = 0;
     int rq_ready = 0;
+    // 1 / symbol in use, per curve at its vertex offset (the applies multiply; FP64 division is slow)
+    double *d_ilam = nullptr;    // [nV]
+    int ilam_src = -1;           // 0: regular-polygon symbols, 1: Rayleigh-quotient symbols, -1: stale
 };
 
 namespace tpe {
@@ -131,6 +134,19 @@ __device__ void bluestein(double2 *a, int n, int M, int logM, const double2 *__r
     __syncthreads();
 }
 
+// ilam[v0 + k] = 1 / lam_c[k] for every curve c (lam: the regular-polygon table at sym_off, or the
+// per-vertex-offset Rayleigh-quotient symbols when rq != NULL); one block per curve
+__global__ void k_inv_symbol(const SpecCurve *__restrict__ curves, const double *__restrict__ sym,
+                             const double *__restrict__ rq, double *__restrict__ ilam)
+{
+    const SpecCurve C = curves[blockIdx.x];
+    const double *lam = rq ? rq + C.v0 : sym + C.sym_off;
+    for (int k = threadIdx.x; k < C.n; k += blockDim.x) {
+        const double l = lam[k];
+        ilam[C.v0 + k] = l > 0.0 ? 1.0 / l : 0.0;
+    }
+}
+
 // Small curves: one CTA per (curve, component).  z = D^-1/2 F^-1 (F (D^-1/2 r) / lambda).
 __global__ void __launch_bounds__(kFFTThreads) k_spec_small(const SpecCurve *__restrict__ curves,
                                                             const int *__restrict__ idx, const double *__restrict__ r,
@@ -139,7 +155,7 @@ __global__ void __launch_bounds__(kFFTThreads) k_spec_small(const SpecCurve *__r
                                                             const double2 *__restrict__ chirp,
                                                             const double2 *__restrict__ bhat,
                                                             const double2 *__restrict__ tw,
-                                                            const double *__restrict__ sym_rq,
+                                                            const double *__restrict__ ilam,
                                                             const int *__restrict__ skip, int indep)
 {
     extern __shared__ double2 sa[];
@@ -150,11 +166,11 @@ __global__ void __launch_bounds__(kFFTThreads) k_spec_small(const SpecCurve *__r
     for (int m = threadIdx.x; m < n; m += blockDim.x)
         sa[m] = make_double2(r[3 * (C.v0 + m) + comp] * dinv[C.v0 + m], 0.0);
     __syncthreads();
-    const double *lam = sym_rq ? sym_rq + C.v0 : sym + C.sym_off;
+    const double *il = ilam + C.v0;
     if (C.kind == SK_POW2) {
         fft_batch(sa, 1, n, C.logM, tw, false);
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            double f = 1.0 / lam[k];
+            const double f = il[k];
             sa[k] = make_double2(sa[k].x * f, sa[k].y * f);
         }
         __syncthreads();
@@ -165,7 +181,7 @@ __global__ void __launch_bounds__(kFFTThreads) k_spec_small(const SpecCurve *__r
         bluestein(sa, n, C.M, C.logM, ch, bh, tw);
         // divide by lambda, then the inverse DFT as conj(DFT(conj(.))) / n
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            double f = 1.0 / lam[k];
+            const double f = il[k];
             sa[k] = make_double2(sa[k].x * f, -sa[k].y * f);
         }
         __syncthreads();
@@ -228,11 +244,11 @@ __global__ void k_four_prep(int v0, int n, const double *__restrict__ r, const d
     for (int c = 0; c < 3; ++c) buf[(size_t)c * n + m] = make_double2(r[3 * (v0 + m) + c] * d, 0.0);
 }
 
-__global__ void k_four_div(int n, const double *__restrict__ lam, double2 *__restrict__ buf)
+__global__ void k_four_div(int n, const double *__restrict__ ilam, double2 *__restrict__ buf)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    double f = 1.0 / lam[k];
+    const double f = ilam[k];
     for (int c = 0; c < 3; ++c) {
         double2 v = buf[(size_t)c * n + k];
         buf[(size_t)c * n + k] = make_double2(v.x * f, v.y * f);
@@ -484,6 +500,7 @@ cudaError_t spectral_setup(Ctx &c, cudaStream_t s)
     TPE_CHECK(cudaMalloc(&S.d_bhat, sizeof(double2) * std::max<long long>(1, bhat_total)));
     TPE_CHECK(cudaMalloc(&S.d_dinv, sizeof(double) * c.nV));
     TPE_CHECK(cudaMalloc(&S.d_sym_rq, sizeof(double) * c.nV));
+    TPE_CHECK(cudaMalloc(&S.d_ilam, sizeof(double) * c.nV));
     TPE_CHECK(cudaMalloc(&S.d_klist, sizeof(int) * klist.size()));
     TPE_CHECK(cudaMemcpy(S.d_klist, klist.data(), sizeof(int) * klist.size(), cudaMemcpyHostToDevice));
     TPE_CHECK(cudaMalloc(&S.d_rq, sizeof(double) * 2 * kMaxRQ * c.nCurves));
@@ -521,7 +538,7 @@ void spectral_free(Ctx &c)
     if (!c.spec) return;
     SpecState &S = *c.spec;
     void *p[] = {S.d_curves, S.d_small_idx, S.d_sym, S.d_tw, S.d_chirp, S.d_bhat, S.d_buf0, S.d_buf1, S.d_dinv,
-                 S.d_sym_rq, S.d_klist, S.d_rq, S.d_vcurve};
+                 S.d_sym_rq, S.d_klist, S.d_rq, S.d_vcurve, S.d_ilam};
     for (void *q : p)
         if (q) cudaFree(q);
     delete c.spec;
@@ -533,12 +550,19 @@ cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, c
     if (!c.spec) return cudaErrorNotSupported;
     SpecState &S = *c.spec;
     const double *rq = (c.prm.precond >= TP_PRECOND_SPECTRAL_RQ && S.rq_ready) ? S.d_sym_rq : nullptr;
+    const int src = rq ? 1 : 0;
+    if (S.ilam_src != src) {
+        k_inv_symbol<<<c.nCurves, 256, 0, s>>>(S.d_curves, S.d_sym, rq, S.d_ilam);
+        c.launches++;
+        S.ilam_src = src;
+    }
     k_dinv<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_diag, S.d_dinv);
     c.launches++;
     if (!S.small_idx.empty()) {
         int M = S.max_small_M;
         k_spec_small<<<(int)S.small_idx.size() * 3, kFFTThreads, sizeof(double2) * M, s>>>(
-            S.d_curves, S.d_small_idx, r, z, S.d_dinv, S.d_sym, S.d_chirp, S.d_bhat, S.d_tw, rq, skip, c.independent);
+            S.d_curves, S.d_small_idx, r, z, S.d_dinv, S.d_sym, S.d_chirp, S.d_bhat, S.d_tw, S.d_ilam, skip,
+            c.independent);
         c.launches++;
     }
     for (int k : S.large_idx) {
@@ -552,7 +576,7 @@ cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, c
         k_four_prep<<<nb, 256, 0, s>>>(C.v0, n, r, S.d_dinv, S.d_buf0);
         k_four_a<<<dim3(N1 / GA, 3), kFFTThreads, smA, s>>>(S.d_buf0, n, N1, N2, C.logN2, GA, S.d_tw, 0);
         k_four_c<<<dim3(N2 / GC, 3), kFFTThreads, smC, s>>>(S.d_buf0, S.d_buf1, n, N1, N2, C.logM, GC, S.d_tw, 0);
-        k_four_div<<<nb, 256, 0, s>>>(n, rq ? rq + C.v0 : S.d_sym + C.sym_off, S.d_buf1);
+        k_four_div<<<nb, 256, 0, s>>>(n, S.d_ilam + C.v0, S.d_buf1);
         k_four_a<<<dim3(N1 / GA, 3), kFFTThreads, smA, s>>>(S.d_buf1, n, N1, N2, C.logN2, GA, S.d_tw, 1);
         k_four_c<<<dim3(N2 / GC, 3), kFFTThreads, smC, s>>>(S.d_buf1, S.d_buf0, n, N1, N2, C.logM, GC, S.d_tw, 1);
         k_four_out<<<nb, 256, 0, s>>>(C.v0, n, S.d_buf0, S.d_dinv, z);
@@ -677,6 +701,7 @@ cudaError_t spectral_rq_setup(Ctx &c, const double *gamma_geom, int which, cudaS
     k_rq_symbol<<<c.nCurves, 256, 0, s>>>(S.d_curves, S.d_klist, S.d_rq, S.d_sym, S.d_sym_rq);
     c.launches++;
     S.rq_ready = 1;
+    S.ilam_src = -1;  // the next apply refreshes 1 / symbol
     return cudaGetLastError();
 }
 

@@ -75,6 +75,20 @@ struct CGScalars {
     int done, breakdown, iters;
 };
 
+// One captured block of CG iterations, reusable while everything it baked in is unchanged.
+struct CgGraph {
+    cudaGraphExec_t exec = nullptr;
+    // key: the pointers and settings the captured launches depend on
+    const double *gamma = nullptr;
+    const void *items = nullptr;
+    int which = -1, proj_mode = -1, precond = -1, every = 0, profile = 0, tpt = 0, sym = 0;
+    double tol2 = -1.0;
+    int64_t launches = 0;             // kernels per replay
+    std::vector<cudaEvent_t> ev;      // profiling: (begin, end) per recorded pair kernel
+    std::vector<int> prof_op;         // profiling: op of each (begin, end)
+    int64_t stamp = 0;                // last use
+};
+
 struct Ctx {
     // graph
     int nV = 0, nE = 0, nCurves = 0, nProb = 0;
@@ -106,6 +120,9 @@ struct Ctx {
         int32_t *d_eslots = nullptr;  // [nE] number of partial slots of each target row
     };
     Plan plan_energy, plan_diff, plan_apply;
+    int tpt[3] = {0, 0, 0};  // targets per thread chosen by tp_autotune (energy, diff, apply + diag); 0: default
+    Plan plan_sym;           // symmetric apply (pairs_sym.cu): items over edge-block pairs (b, c >= b)
+    int apply_sym = 0;       // > 0: the apply runs the symmetric pass with this many targets per thread
     int *d_counter = nullptr;  // persistent-queue counters [8]
     // edge records
     RecF *d_recF = nullptr, *d_recF2 = nullptr;
@@ -148,6 +165,13 @@ struct Ctx {
     int64_t pairs_per_pass = 0;
     const int *d_skip = nullptr;  // during a CG solve: per-problem converged flags (apply skips them)
     GnnState *gnn = nullptr;      // learned preconditioner term (contexts created with TP_PRECOND_LEARNED)
+    // captured CG iteration blocks
+    cudaStream_t cg_stream = nullptr;
+    cudaEvent_t cg_join[2] = {nullptr, nullptr};
+    std::vector<CgGraph> graphs;
+    CgGraph *capturing = nullptr;  // set while a block is being captured (profiling records into it)
+    int64_t graph_clock = 0;
+    int graphs_broken = 0;         // a capture failed: direct launches from then on
     // (residual, iterate) capture of a CG solve: every `every` iterations r -> R[n], y -> Y[n]
     struct Harvest {
         double *R = nullptr, *Y = nullptr;
@@ -164,6 +188,8 @@ struct Ctx {
 int prof_begin(Ctx &c, int op, cudaStream_t s);
 void prof_end(Ctx &c, int slot, cudaStream_t s);
 void prof_harvest(Ctx &c);
+void graphs_free(Ctx &c);
+void graphs_reset(Ctx &c);  // drop the captured blocks (their launches baked in parameters that changed)
 
 // ------------------------------------------------------------------ pair passes (pairs.cu)
 cudaError_t build_records(Ctx &c, const double *gamma, int which, cudaStream_t s);
@@ -172,7 +198,13 @@ cudaError_t pair_energy(Ctx &c, const double *gamma, int which, double *rows_out
 cudaError_t pair_diff(Ctx &c, const double *gamma, int which, double *dE, cudaStream_t s);
 cudaError_t pair_apply(Ctx &c, const double *gamma_geom, int which, const double *u, double *Au, cudaStream_t s);
 cudaError_t pair_diag(Ctx &c, const double *gamma_geom, int which, double *diag, cudaStream_t s);
+cudaError_t sym_select(Ctx &c, int tpt);  // (pairs_sym.cu) symmetric apply on (tpt 1, 2) or off (0)
+cudaError_t sym_apply_pass(Ctx &c, int which, const double *gamma, const double *u, cudaStream_t s);
+size_t sym_slots(const Ctx &c, int tpt);
 void make_plans(Ctx &c);
+cudaError_t replan(Ctx &c, int cls);  // rebuild the plan of one op class (0 energy, 1 diff, 2 apply/diag)
+int tpt_default(const Ctx &c, int cls);
+int tpt_candidates(const Ctx &c, int cls, int *out);  // the autotuner's search space; returns the count
 
 // ------------------------------------------------------------------ solver pieces (solver.cu)
 cudaError_t constraints_eval(Ctx &c, const double *gamma, int which, double *phi, cudaStream_t s);

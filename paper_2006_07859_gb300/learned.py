@@ -42,8 +42,9 @@ def init_params(seed: int = 0, out_bias: float = -2.0) -> np.ndarray:
 
 @dataclasses.dataclass
 class PairSet:
-    """Prepared training pairs of one geometry: R (residuals), B = P M_2L^-1 R, AB = A-bar B (all
-    [n, nV, 3] float64 on the GPU) and ER = e . r per problem ([n, n_problems])."""
+    """Prepared training pairs of one geometry: R = A-bar e (the residuals exactly consistent with the
+    harvested corrections e), B = P M_2L^-1 R, AB = A-bar B (all [n, nV, 3] float64 on the GPU) and
+    ER = e . r per problem ([n, n_problems])."""
     gamma: object
     R: object
     B: object
@@ -67,7 +68,7 @@ def harvest(ctx: tpe.Context, gamma, rhs, every: int = 1, max_pairs: int = 32) -
     AB = torch.empty_like(R)
     ER = torch.empty((n, ctx.n_problems), dtype=torch.float64, device="cuda")
     if n:
-        tpe.tp_gnn_prepare_pairs(ctx, gamma, R, E, E, AB, ER)  # B overwrites E in place
+        tpe.tp_gnn_prepare_pairs(ctx, gamma, R, E, E, AB, ER)  # R := A-bar E; B overwrites E in place
     return PairSet(gamma.clone(), R, E, AB, ER)
 
 
@@ -84,7 +85,8 @@ def harvest_descent(ctx: tpe.Context, gamma, steps: int, every: int = 1, max_pai
 
 def train(ctx: tpe.Context, sets: list[PairSet], steps: int = 200, lr: float = 3e-3, batch: int = 4,
           seed: int = 0, theta0=None, log_every: int = 0) -> dict:
-    """Adam on the mean A-norm loss over minibatches of `batch` consecutive pairs of one geometry
+    """Adam on the mean loss (A-norm error of the best multiple of the preconditioned correction, in
+    [0, 1]) over minibatches of `batch` consecutive pairs of one geometry
     (geometries and windows drawn in a seeded random order; each switch of geometry re-binds the
     curve).  Returns the loss history and the trained parameters (float32 CUDA tensor)."""
     import torch

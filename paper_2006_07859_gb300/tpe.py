@@ -30,7 +30,7 @@ EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp
             "tp_launch_count", "tp_pairs_per_pass", "tp_profile", "tp_profile_read", "tp_measure_peaks", "tp_energy_static",
             "tp_spectral_symbols", "tp_gnn_num_params", "tp_gnn_set_params", "tp_gnn_get_params", "tp_gnn_bind",
             "tp_gnn_forward", "tp_gnn_backward", "tp_gnn_adam", "tp_gnn_g_apply", "tp_gnn_out_grad", "tp_cg_harvest",
-            "tp_gnn_prepare_pairs", "tp_gnn_train_step"]
+            "tp_gnn_prepare_pairs", "tp_gnn_train_step", "tp_autotune", "tp_set_apply_variant"]
 
 
 class TpParams(ctypes.Structure):
@@ -39,7 +39,8 @@ class TpParams(ctypes.Structure):
                 ("cg_maxit", ctypes.c_int), ("cg_check_every", ctypes.c_int), ("proj_cg_rtol", ctypes.c_double),
                 ("precond", ctypes.c_int), ("armijo_c", ctypes.c_double), ("shrink", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("proj_tol", ctypes.c_double), ("proj_maxit", ctypes.c_int),
-                ("independent", ctypes.c_int), ("coarse_dim", ctypes.c_int), ("far_cutoff", ctypes.c_double)]
+                ("independent", ctypes.c_int), ("coarse_dim", ctypes.c_int), ("far_cutoff", ctypes.c_double),
+                ("use_graphs", ctypes.c_int)]
 
 
 class TpSolveInfo(ctypes.Structure):
@@ -114,6 +115,8 @@ def library() -> ctypes.CDLL:
         L.tp_cg_harvest.argtypes = [vp, vp, vp, i, i, vp, vp, ctypes.POINTER(i), ctypes.POINTER(TpSolveInfo), vp]
         L.tp_gnn_prepare_pairs.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp]
         L.tp_gnn_train_step.argtypes = [vp, vp, i, vp, vp, vp, vp, ctypes.c_float, pdd, vp, vp]
+        L.tp_autotune.argtypes = [vp, vp, vp, vp, vp]
+        L.tp_set_apply_variant.argtypes = [vp, i]
         _lib = L
     return _lib
 
@@ -388,3 +391,23 @@ def tp_gnn_train_step(ctx: Context, gamma, R, B, AB, ER, lr: float, grad=None) -
     ctx._check(library().tp_gnn_train_step(ctx.handle, _ptr(gamma), int(R.shape[0]), _ptr(R), _ptr(B), _ptr(AB),
                                            _ptr(ER), ctypes.c_float(lr), ctypes.byref(loss), _fptr(grad), _stream()))
     return loss.value
+
+
+def tp_autotune(ctx: Context, gamma) -> dict:
+    """Pick the fastest targets-per-thread of each pair pass on `gamma` (mixed precision, alpha = 2,
+    beta = 4.5); returns the choices and the measured ms per pass."""
+    t = (ctypes.c_int32 * 4)()
+    ms = (ctypes.c_double * 11)()
+    ctx._check(library().tp_autotune(ctx.handle, _ptr(gamma), t, ms, _stream()))
+    names = ["energy", "diff", "apply"]
+    out = {"tpt": {n: int(t[k]) for k, n in enumerate(names)},
+           "ms": {n: {str(v): ms[3 * k + j] for j, v in enumerate((1, 2, 4)) if ms[3 * k + j] > 0}
+                  for k, n in enumerate(names)}}
+    out["tpt"]["apply_symmetric"] = int(t[3])
+    out["ms"]["apply_symmetric"] = {str(v): ms[9 + j] for j, v in enumerate((1, 2)) if ms[9 + j] > 0}
+    return out
+
+
+def tp_set_apply_variant(ctx: Context, symmetric_tpt: int):
+    """0: gather apply (every ordered pair); 1 or 2: symmetric apply with that many targets per thread."""
+    ctx._check(library().tp_set_apply_variant(ctx.handle, int(symmetric_tpt)))

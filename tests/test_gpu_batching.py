@@ -1,0 +1,111 @@
+"""Batching machinery (row A10): CG blocks replayed as captured CUDA graphs, and the autotuner of the
+pair passes' targets per thread, each checked against the direct path and the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth as S
+from tests.gpu_util import cosine, dev, host, make_ctx, need_gpu, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    from oracle import oracle as O
+    O.build_library()
+    return O
+
+
+def _batch():
+    sizes = S.batch_sizes(24, 64, 700, 77)
+    return S.batch_of_knots(sizes, 8, 77)
+
+
+@pytest.mark.parametrize("precond", [1, 4])
+@pytest.mark.parametrize("profile", [False, True])
+def test_graph_replay_is_bitwise_identical(torch, precond, profile):
+    """The same gradient solve with CG blocks as captured graphs and as direct launches: the same
+    kernels in the same order with deterministic reductions give bitwise equal results, and the
+    launch count and (when profiling) the number of timed apply launches agree."""
+    from paper_2006_07859_gb300 import tpe
+    b = _batch()
+    out = {}
+    for graphs in (0, 1):
+        ctx = tpe.Context.from_curves(b, precision=tpe.TP_MIXED, precond=precond, independent=1, cg_rtol=1e-6,
+                                      cg_maxit=3000, cg_check_every=8, use_graphs=graphs)
+        g = dev(b.gamma)
+        dE = tpe.tp_differential(ctx, g)
+        ctx.profile(profile)
+        l0 = ctx.launch_count()
+        gg, info = tpe.sobolev_gradient(ctx, g, dE)
+        # a second solve reuses the cached graphs
+        gg2, info2 = tpe.sobolev_gradient(ctx, g, dE)
+        torch.cuda.synchronize()
+        out[graphs] = (host(gg), host(gg2), info["iters"], ctx.launch_count() - l0,
+                       ctx.profile_read(4)[1] if profile else 0)
+        ctx.close()
+    a, g1 = out[0], out[1]
+    assert a[2] == g1[2]
+    assert np.array_equal(a[0], g1[0]) and np.array_equal(a[1], g1[1])
+    assert np.array_equal(g1[0], g1[1])
+    assert a[3] == g1[3]
+    if profile:
+        assert a[4] == g1[4] > 0
+
+
+def test_autotune_keeps_parity(torch, orc):
+    """After the autotuner picks targets per thread, the passes still match the FP64 oracle."""
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.fourier_knot(3000, 8, 5))
+    ctx = make_ctx(c, precision=tpe.TP_MIXED, precond=1)
+    g = dev(c.gamma)
+    res = tpe.tp_autotune(ctx, g)
+    assert set(res["tpt"].values()) <= {1, 2, 4}
+    assert all(len(v) >= 2 for v in res["ms"].values())
+    rows = torch.empty(c.n_edges, dtype=torch.float64, device="cuda")
+    tpe.tp_energy(ctx, g, rows=rows)
+    dE = host(tpe.tp_differential(ctx, g))
+    u = np.random.default_rng(3).normal(size=(c.n_vertices, 3))
+    Au = host(tpe.sobolev_apply(ctx, g, dev(u)))
+    idx = np.sort(np.random.default_rng(4).choice(c.n_edges, 48, replace=False)).astype(np.int32)
+    assert rel(host(rows)[idx], orc.energy_rows(c.gamma, c.edges, idx)) <= 1e-6
+    ref = orc.differential_at(c.gamma, c.edges, idx)
+    assert cosine(dE[idx], ref) >= 0.9999 and rel(dE[idx], ref) <= 1e-5
+    assert rel(Au[idx], orc.gram_apply_at(c.gamma, c.edges, 0.75, u, idx)) <= 1e-6
+
+
+@pytest.mark.parametrize("tpt", [1, 2])
+@pytest.mark.parametrize("case", ["single_ragged", "batch"])
+def test_symmetric_apply_matches_gather_and_oracle(torch, orc, tpt, case):
+    """The symmetric apply (each unordered pair once, both rows fed) against the gather apply and the
+    oracle: single curve with a ragged last block and a batch of independent curves of mixed sizes."""
+    from paper_2006_07859_gb300 import tpe
+    if case == "single_ragged":
+        c = S.single(S.fourier_knot(1000, 8, 9))
+        indep = 0
+    else:
+        c = _batch()
+        indep = 1
+    ctx = make_ctx(c, precision=tpe.TP_MIXED, precond=1, independent=indep)
+    g = dev(c.gamma)
+    u = np.random.default_rng(11).normal(size=(c.n_vertices, 3))
+    Au_gather = host(tpe.sobolev_apply(ctx, g, dev(u)))
+    tpe.tp_set_apply_variant(ctx, tpt)
+    Au_sym = host(tpe.sobolev_apply(ctx, g, dev(u)))
+    Au_sym2 = host(tpe.sobolev_apply(ctx, g, dev(u)))
+    assert np.array_equal(Au_sym, Au_sym2)          # deterministic
+    assert rel(Au_sym, Au_gather) <= 1e-6
+    if case == "single_ragged":
+        idx = np.sort(np.random.default_rng(12).choice(c.n_vertices, 40, replace=False)).astype(np.int32)
+        assert rel(Au_sym[idx], orc.gram_apply_at(c.gamma, c.edges, 0.75, u, idx)) <= 1e-6
+    else:
+        for k in range(4):
+            gk, ek = c.curve(k)
+            v0, v1 = c.vertex_offsets[k], c.vertex_offsets[k + 1]
+            ref = orc.gram_apply(gk, ek, 0.75, u[v0:v1])
+            assert rel(Au_sym[v0:v1], ref) <= 1e-6

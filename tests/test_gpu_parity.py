@@ -136,5 +136,11 @@ def test_mixed_precision_at_scale(torch, orc):
     dE = host(tpe.tp_differential(ctx, g))
     Au = host(tpe.sobolev_apply(ctx, g, dev(u)))
     assert rel(host(rows)[rows_i], orc.energy_rows(c.gamma, c.edges, rows_i)) <= 1e-6
-    assert rel(dE[v_i], orc.differential_at(c.gamma, c.edges, v_i)) <= 1e-6
+    # The differential at a vertex is the difference of its two edges' gathered rows, which cancel by
+    # ~1 / (kappa l) ~ 1e3 here: the FP32 rounding of the individual pair terms (about 1e-7 each,
+    # independent between the two edges) is amplified by that factor.  Bound: the gradient criterion
+    # of the FP32 contract (cosine >= 0.9999) and a 1e-5 relative error against the largest entry.
+    ref = orc.differential_at(c.gamma, c.edges, v_i)
+    assert cosine(dE[v_i], ref) >= 0.9999
+    assert rel(dE[v_i], ref) <= 1e-5
     assert rel(Au[v_i], orc.gram_apply_at(c.gamma, c.edges, SIG, u, v_i)) <= 1e-6

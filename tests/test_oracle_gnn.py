@@ -52,13 +52,24 @@ def test_loss_gradient_matches_central_differences(setup):
         assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g).max()), (k, fd, g[k])
 
 
-def test_loss_is_the_a_norm_error(setup):
-    """L = (z - e)^T A (z - e) / e^T A e with A e = r."""
+def test_loss_is_the_best_scaled_a_norm_error(setup):
+    """L = min over a of ||a z - e||_A^2 / ||e||_A^2 (A e = r), found here by a brute-force scan of a:
+    the loss ignores the preconditioner's scale, as preconditioned CG does."""
     c, A, diag, r, e, base_z = setup
     theta = gnn.init_params(4, out_bias=-1.0)
     f = gnn.features(c.gamma, diag)
     out, _ = gnn.forward(theta, f)
     z = base_z + gnn.g_apply(out, diag, r)
     L, _ = gnn.loss_and_grad(theta, f, diag, A, r, e, base_z)
-    d = z - e
-    assert abs(L - (d * (A @ d)).sum() / (e * (A @ e)).sum()) <= 1e-10
+    ee = (e * (A @ e)).sum()
+
+    def err(a):
+        d = a * z - e
+        return (d * (A @ d)).sum() / ee
+
+    a_scale = np.sqrt(ee / (z * (A @ z)).sum())
+    grid = np.linspace(0.0, 4.0 * a_scale, 40001)
+    vals = np.array([err(a) for a in grid])
+    assert 0.0 <= L <= 1.0
+    assert vals.min() >= L - 1e-12
+    assert vals.min() - L <= 1e-6
