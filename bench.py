@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--workload", choices=["knots8x4096", "scene8x4096", "knot262144"], default="knots8x4096")
     ap.add_argument("--cg-rtol", type=float, default=None)
     ap.add_argument("--cg-maxit", type=int, default=None)
+    ap.add_argument("--precond-refresh", type=int, default=1,
+                    help="rebuild the fitted symbols and coarse space every k-th solve set-up")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -90,7 +92,8 @@ def solver_params(name, args):
     # rounding floor at that size is above 1e-6); the 8 x 4096 scene solves to 1e-6.
     rtol = args.cg_rtol if args.cg_rtol is not None else 1e-6
     maxit = args.cg_maxit if args.cg_maxit is not None else 2000
-    return dict(cg_rtol=rtol, cg_maxit=maxit, proj_cg_rtol=1e-3, cg_check_every=8)
+    return dict(cg_rtol=rtol, cg_maxit=maxit, proj_cg_rtol=1e-3, cg_check_every=8,
+                precond_refresh=max(1, args.precond_refresh))
 
 
 # ------------------------------------------------------------------------------- clocks

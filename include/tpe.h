@@ -106,6 +106,9 @@ typedef struct {
     int use_graphs;       /* 1: CG runs blocks of cg_check_every iterations as captured CUDA graphs on a
                              context-owned stream joined to the caller's stream by events (the same
                              kernels in the same order as the direct launches); 0: direct launches */
+    int precond_refresh;  /* rebuild the Rayleigh-quotient symbols and the coarse space every k-th
+                             preconditioner set-up (1: every set-up); diag(A) and the learned term's
+                             features are always rebuilt for the current curve */
 } tp_params;
 
 typedef struct {

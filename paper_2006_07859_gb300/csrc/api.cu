@@ -58,6 +58,10 @@ bool params_ok(const tp_params *p, std::string &why)
         why = "coarse_dim must be >= 2";
         return false;
     }
+    if (p->precond_refresh < 1) {
+        why = "precond_refresh must be >= 1";
+        return false;
+    }
     if (!(p->far_cutoff >= 0.0)) {
         why = "far_cutoff must be >= 0";
         return false;
@@ -201,6 +205,7 @@ void tp_default_params(tp_params *p)
     p->independent = 0;
     p->far_cutoff = 10.0;
     p->use_graphs = 1;
+    p->precond_refresh = 1;
     p->coarse_dim = 64;
 }
 
@@ -452,6 +457,7 @@ tp_status tp_set_params(tp_ctx *ctx, const tp_params *p)
     c.prm.independent = indep;
     set_kernel_params(c);
     graphs_reset(c);  // captured CG blocks baked in the old kernel parameters
+    c.setups_since_full = -1;  // the next preconditioner set-up is a full one
     if (!c.kp.fast && (c.tpt[0] || c.tpt[1] || c.tpt[2] || c.apply_sym)) {
         // autotuned variants exist for the specialised powers only: back to the defaults
         for (int cls = 0; cls < 3; ++cls) {
@@ -545,8 +551,12 @@ static tp_status precond_setup(tp_ctx *ctx, const double *gamma, cudaStream_t s)
     if (c.prm.precond == TP_PRECOND_LEARNED && !gnn_ready(c))
         return fail(ctx, TP_ERR_INVALID_ARG, "TP_PRECOND_LEARNED: no network parameters loaded (tp_gnn_set_params)");
     if (c.prm.precond != TP_PRECOND_NONE) CK(pair_diag(c, gamma, 0, c.d_diag, s));
-    if (c.prm.precond >= TP_PRECOND_SPECTRAL_RQ) CK(spectral_rq_setup(c, gamma, 0, s));
-    if (c.prm.precond >= TP_PRECOND_TWOLEVEL) CK(coarse_setup(c, gamma, 0, s));
+    // the fitted symbols and the coarse space are rebuilt every precond_refresh-th set-up (any SPD
+    // preconditioner keeps PCG exact; the curve moves little between consecutive descent steps)
+    const bool full = c.setups_since_full < 0 || c.setups_since_full + 1 >= std::max(1, c.prm.precond_refresh);
+    c.setups_since_full = full ? 0 : c.setups_since_full + 1;
+    if (full && c.prm.precond >= TP_PRECOND_SPECTRAL_RQ) CK(spectral_rq_setup(c, gamma, 0, s));
+    if (full && c.prm.precond >= TP_PRECOND_TWOLEVEL) CK(coarse_setup(c, gamma, 0, s));
     if (c.prm.precond == TP_PRECOND_LEARNED) {
         CK(gnn_bind(c, 0, c.d_diag, s));
         CK(gnn_forward(c, s));

@@ -172,6 +172,7 @@ struct Ctx {
     CgGraph *capturing = nullptr;  // set while a block is being captured (profiling records into it)
     int64_t graph_clock = 0;
     int graphs_broken = 0;         // a capture failed: direct launches from then on
+    int setups_since_full = -1;    // preconditioner set-ups since the last full one (-1: none yet)
     // (residual, iterate) capture of a CG solve: every `every` iterations r -> R[n], y -> Y[n]
     struct Harvest {
         double *R = nullptr, *Y = nullptr;

@@ -40,7 +40,7 @@ class TpParams(ctypes.Structure):
                 ("precond", ctypes.c_int), ("armijo_c", ctypes.c_double), ("shrink", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("proj_tol", ctypes.c_double), ("proj_maxit", ctypes.c_int),
                 ("independent", ctypes.c_int), ("coarse_dim", ctypes.c_int), ("far_cutoff", ctypes.c_double),
-                ("use_graphs", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("precond_refresh", ctypes.c_int)]
 
 
 class TpSolveInfo(ctypes.Structure):
