@@ -154,8 +154,9 @@ def trefoil_256() -> Curves:
     return single(trefoil(256, 0.01, 0))
 
 
-def eight_knots_4096(as_scene: bool = True) -> Curves:
-    ks = [fourier_knot(4096, 8, s) for s in range(1, 9)]
+def eight_knots_4096(as_scene: bool = True, first_seed: int = 1) -> Curves:
+    """Eight closed Fourier knots (K = 8, 4,096 vertices, seeds first_seed .. first_seed + 7)."""
+    ks = [fourier_knot(4096, 8, s) for s in range(first_seed, first_seed + 8)]
     if as_scene:
         return scene(ks)
     gs, es, vo, eo = [], [], [0], [0]
