@@ -251,6 +251,7 @@ def pass_throughput_262k(tpe, torch):
     ctx = tpe.Context.from_curves(c, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_JACOBI)
     g = torch.as_tensor(c.gamma).cuda()
     u = torch.as_tensor(np.random.default_rng(1).normal(size=(c.n_vertices, 3))).cuda()
+    tuned = tpe.tp_autotune(ctx, g)
     tpe.tp_energy(ctx, g)
     torch.cuda.synchronize()
     ctx.profile(True)
@@ -260,7 +261,7 @@ def pass_throughput_262k(tpe, torch):
     tpe.sobolev_apply(ctx, g, u)
     torch.cuda.synchronize()
     pairs = ctx.pairs_per_pass()
-    out = {"pairs_per_pass": pairs}
+    out = {"pairs_per_pass": pairs, "autotune": tuned["tpt"]}
     for i, op in enumerate(["energy", "diff", "apply"]):
         ms, n = ctx.profile_read(i)
         out[op] = {"pairs_per_s": pairs * n / (ms / 1e3), "ms_per_launch": ms / n,
@@ -363,6 +364,14 @@ def run_batch(args):
     z.record()
     torch.cuda.synchronize()
     res["descent_step"] = dict(info, seconds=a.elapsed_time(z) / 1e3)
+    # per-curve view of the last solve: distribution of the true residual and the worst curves
+    rr, its = tpe.tp_last_solve(ctx)
+    order = np.argsort(-rr)
+    res["last_solve_per_curve"] = {
+        "rel_res_quantiles": {q: float(np.quantile(rr, q)) for q in (0.5, 0.9, 0.99, 1.0)},
+        "iters_quantiles": {q: float(np.quantile(its, q)) for q in (0.5, 0.9, 0.99, 1.0)},
+        "worst": [{"curve": int(k), "n": int(sizes[k]), "rel_res": float(rr[k]), "iters": int(its[k])}
+                  for k in order[:5]]}
     print(json.dumps(res), flush=True)
 
 

@@ -203,6 +203,11 @@ TPE_API tp_status sobolev_gradient(tp_ctx *ctx, const double *gamma, const doubl
  * (the line search reads scalars on the host).  On TP_ERR_LINESEARCH gamma is unchanged. */
 TPE_API tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream stream);
 
+/* Per-problem result of the context's last CG solve (the last one inside the last call that solved):
+ * rel_res (HOST double [n_problems], may be NULL) the true relative residual recomputed with the
+ * working-precision operator, iters (HOST int32 [n_problems], may be NULL) the iterations. */
+TPE_API tp_status tp_last_solve(const tp_ctx *ctx, double *rel_res, int32_t *iters);
+
 /* Number of kernel launches this context has issued since creation (all entry points). */
 TPE_API int64_t tp_launch_count(const tp_ctx *ctx);
 
@@ -238,21 +243,23 @@ TPE_API tp_status tp_energy_static(const double *gamma, const int32_t *edges, in
 
 /* ------------------------------------------------------------------------------------------
  * Learned preconditioner (TP_PRECOND_LEARNED).  Not part of the paper: a 3-layer network on the
- * edge graph of the closed curves predicts per-edge log-weights (a_I, b_I) of an SPD local term
+ * edge graph of the closed curves predicts three values (a_I, b_I, c_I) per edge that shape
+ *   M^-1 r = W S W r + Z (Z^T A Z)^-1 Z^T r + G r,
+ * W = D^-1/2 diag(exp(c_v)) with c_v the mean of c over the edges at vertex v (a learned rescaling of
+ * the Jacobi-scaled circulant S of TP_PRECOND_TWOLEVEL, which c = 0 gives back), Z the coarse space,
  *   G = D^-1/2 (D_delta^T diag(e^{2a}) D_delta + D_sigma^T diag(e^{2b}) D_sigma) D^-1/2,
- * D = diag(A), (D_delta r)_I = r_i2 - r_i1, (D_sigma r)_I = r_i1 + r_i2, that is added to the
- * two-level preconditioner: M^-1 r = M_2L^-1 r + G r.  It stays SPD for any parameters, so CG with
- * the exact operator remains the judge of the residual.
+ * D = diag(A), (D_delta r)_I = r_i2 - r_i1, (D_sigma r)_I = r_i1 + r_i2.  M stays SPD for any
+ * parameters, so CG with the exact operator remains the judge of the residual.
  * Network (per edge I, neighbours I-1 and I+1 along its curve; FP32 activations, BF16 weights):
  *   f_I = [log(l_I / mean l), 1 - T_{I-1}.T_I, 1 - T_I.T_{I+1}, log(d_i1 / mean d), log(d_i2 / mean d),
  *          log(l_{I-1} / l_I), log(l_{I+1} / l_I), 1]     (means over the edge's curve)
  *   h1 = relu(W1 f + b1),  h2 = relu(W2s h1 + W2n (h1[I-1] + h1[I+1]) / 2 + b2),
- *   h3 = relu(W3s h2 + W3n (h2[I-1] + h2[I+1]) / 2 + b3),  (a, b) = W4 h3 + b4.
+ *   h3 = relu(W3s h2 + W3n (h2[I-1] + h2[I+1]) / 2 + b3),  (a, b, c) = W4 h3 + b4.
  * Parameter vector theta: FP32, DEVICE, tp_gnn_num_params() values in the order
- *   W1 [64][8], b1 [64], W2s [64][64], W2n [64][64], b2, W3s, W3n, b3, W4 [2][64], b4 [2] (row-major).
+ *   W1 [64][8], b1 [64], W2s [64][64], W2n [64][64], b2, W3s, W3n, b3, W4 [3][64], b4 [3] (row-major).
  * Training: (r, e = A^+ r) pairs from the context's own CG solves (tp_cg_harvest), prepared once
  * (tp_gnn_prepare_pairs), then Adam steps (tp_gnn_train_step) on the A-norm error of the best
- * multiple of z = M_2L^-1 r + G r (preconditioned CG does not see the preconditioner's scale):
+ * multiple of z = M^-1 r (preconditioned CG does not see the preconditioner's scale):
  *   L = min_a ||a z - e||_A^2 / ||e||_A^2 = 1 - (z^T r)^2 / ((z^T A z)(e^T r)),  in [0, 1].
  * Every tp_gnn_* call fails with TP_ERR_UNSUPPORTED on a context not created with
  * TP_PRECOND_LEARNED (only those hold the network's scratch, about 1.6 KB per edge). */
@@ -269,11 +276,11 @@ TPE_API tp_status tp_gnn_get_params(tp_ctx *ctx, float *theta, tp_stream stream)
 TPE_API tp_status tp_gnn_bind(tp_ctx *ctx, const double *gamma, tp_stream stream);
 
 /* Network forward on the bound curve with the current BF16 weights.  features (DEVICE float
- * [n_edges][8]) and out (DEVICE float [n_edges][2]: a, b) may each be NULL. */
+ * [n_edges][8]) and out (DEVICE float [n_edges][3]: a, b, c) may each be NULL. */
 TPE_API tp_status tp_gnn_forward(tp_ctx *ctx, float *features, float *out, tp_stream stream);
 
 /* Parameter gradient grad (DEVICE float [P]) of a scalar whose derivative with respect to the
- * outputs of the last forward pass is dout (DEVICE float [n_edges][2]).  The chain uses the BF16
+ * outputs of the last forward pass is dout (DEVICE float [n_edges][3]).  The chain uses the BF16
  * weights the forward pass used; the sums are deterministic. */
 TPE_API tp_status tp_gnn_backward(tp_ctx *ctx, const float *dout, float *grad, tp_stream stream);
 
@@ -286,7 +293,8 @@ TPE_API tp_status tp_gnn_adam(tp_ctx *ctx, const float *grad, float lr, tp_strea
 TPE_API tp_status tp_gnn_g_apply(tp_ctx *ctx, const double *r, double *z, int accumulate, tp_stream stream);
 
 /* dout (=, or += with accumulate = 1) the derivative of gz . (G r) with respect to the network
- * outputs (a, b): DEVICE float [n_edges][2]; r, gz DEVICE double [nV][3]. */
+ * outputs (a, b): DEVICE float [n_edges][3] (the c column is set to 0, or left as it is when
+ * accumulating); r, gz DEVICE double [nV][3]. */
 TPE_API tp_status tp_gnn_out_grad(tp_ctx *ctx, const double *r, const double *gz, float *dout, int accumulate,
                                   tp_stream stream);
 
@@ -301,32 +309,37 @@ TPE_API tp_status tp_cg_harvest(tp_ctx *ctx, const double *gamma, const double *
 /* For n harvested pairs of the curve gamma: first R[k] := A-bar E[k] (CG's recursive residual drifts
  * below the true residual when the operator is inexact, so only A-bar e_k is exactly consistent with
  * e_k; on output every pair satisfies r = A-bar e), then ER[k] (DEVICE double [n][n_problems]) =
- * e_k . r_k per problem, B[k] = P M_2L^-1 r_k (the preconditioner without the learned term) and
- * AB[k] = A-bar B[k].  R, E, B, AB DEVICE double [n][nV][3]; B may be the same buffer as E (ER is
- * taken first).  Costs two A-bar applies per pair. */
+ * e_k . r_k per problem, B[k] = the part of the preconditioner that the parameters do not change,
+ * applied to r_k and mean-projected, and AB[k] = A-bar B[k].  With ILAM (DEVICE double [nV], may be
+ * NULL) the circulant is left to training (its scaling is learned): B[k] is the coarse term alone and
+ * ILAM receives this curve's inverse circulant symbols; without it, B[k] is the whole two-level
+ * preconditioner.  R, E, B, AB DEVICE double [n][nV][3]; B may be the same buffer as E (ER is taken
+ * first).  Costs two A-bar applies per pair. */
 TPE_API tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, double *R, double *E,
-                                       double *B, double *AB, double *ER, tp_stream stream);
+                                       double *B, double *AB, double *ER, double *ILAM, tp_stream stream);
 
-/* One training step on n prepared pairs of the bound curve gamma: the loss at the current parameters,
- * averaged over pairs and problems, into *loss (host), the parameter gradient into grad (DEVICE float
- * [P], may be NULL), then one Adam step when lr > 0 (lr = 0: gradient only).  Costs one A-bar apply
- * per pair.  Synchronises the stream. */
+/* One training step on n prepared pairs of the bound curve gamma, with the inverse symbols ILAM that
+ * tp_gnn_prepare_pairs returned for it (NULL: the prepared B already holds the whole circulant):
+ * z = B + W S W r + G r per pair, the loss at the current parameters, averaged over pairs and problems,
+ * into *loss (host), the parameter gradient into grad (DEVICE float [P], may be NULL), then one Adam
+ * step when lr > 0 (lr = 0: gradient only).  Costs one A-bar apply and two circulant applies per pair.
+ * Synchronises the stream. */
 TPE_API tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, const double *R, const double *B,
-                                    const double *AB, const double *ER, float lr, double *loss, float *grad,
-                                    tp_stream stream);
+                                    const double *AB, const double *ER, const double *ILAM, float lr,
+                                    double *loss, float *grad, tp_stream stream);
 
 /* Autotuner of the pair passes (not in the paper).  For TP_MIXED contexts with the specialised
  * powers ((alpha, beta) = (2, 4.5)) it times, on the curve gamma, every candidate number of target
  * edges per thread of the energy (1, 2, 4), differential (1, 2) and apply / diag (1, 2, 4) gather
- * passes, and the symmetric apply pass (each unordered pair evaluated once, 1 or 2 targets per thread,
- * when its partial sums fit in 16 GB), one warm-up and three timed passes each (CUDA events on
- * `stream`), and keeps the fastest, rebuilding that op's work queue; other contexts keep their
- * defaults and are left unchanged.
- *   tpt (HOST int32 [4], may be NULL): the chosen targets per thread of the energy, differential and
- *       apply gather passes, then of the symmetric apply (0: the apply uses the gather pass).
- *   ms  (HOST double [11], may be NULL): ms per pass for 1, 2, 4 targets per thread of the energy
+ * passes, and the symmetric energy and apply passes (each unordered pair evaluated once, 1 or 2
+ * targets per thread, when their partial sums fit in 16 GB), one warm-up and three timed passes each
+ * (CUDA events on `stream`), and keeps the fastest, rebuilding that op's work queue; other contexts
+ * keep their defaults and are left unchanged.
+ *   tpt (HOST int32 [5], may be NULL): the chosen targets per thread of the energy, differential and
+ *       apply gather passes, then of the symmetric apply and the symmetric energy (0: gather pass).
+ *   ms  (HOST double [13], may be NULL): ms per pass for 1, 2, 4 targets per thread of the energy
  *       [0..2], differential [3..5] and apply [6..8] gather passes, then the symmetric apply with 1, 2
- *       [9..10] (0 where not a candidate).
+ *       [9..10] and the symmetric energy with 1, 2 [11..12] (0 where not a candidate).
  * May reallocate the context's partial-sum buffer (the only allocation after tp_create).
  * Synchronises the stream.  Errors: TP_ERR_INVALID_ARG, TP_ERR_CUDA, TP_ERR_DEGENERATE_EDGE. */
 TPE_API tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms, tp_stream stream);
@@ -336,6 +349,10 @@ TPE_API tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, do
  * (alpha, beta) = (2, 4.5) only, else TP_ERR_UNSUPPORTED) with that many target edges per thread.  Both
  * are deterministic and differ only in summation order.  May grow the partial-sum buffer. */
 TPE_API tp_status tp_set_apply_variant(tp_ctx *ctx, int symmetric_tpt);
+
+/* The same choice for the energy pass (0: gather, 1 or 2: symmetric; the rows E_I are the same
+ * sums in another order). */
+TPE_API tp_status tp_set_energy_variant(tp_ctx *ctx, int symmetric_tpt);
 
 /* Throughput microbenchmarks on the current device (no context needed): FP32 FMA FLOP/s, MUFU
  * rsqrt op/s and FP64 FMA FLOP/s.  Returns 0 on success. */

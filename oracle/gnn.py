@@ -6,19 +6,26 @@ from its definition; the CUDA kernels (BF16 weights, FP32 accumulation) are chec
 Edge features (closed curves; I-1 and I+1 are the neighbours of edge I on its curve; d = diag(A)):
     f = [log(l_I / mean l), 1 - T_{I-1}.T_I, 1 - T_I.T_{I+1}, log(d_i1 / mean d), log(d_i2 / mean d),
          log(l_{I-1} / l_I), log(l_{I+1} / l_I), 1]
-Network (3 layers of width 64 on the edge graph, then a linear read-out of 2 values per edge):
+Network (3 layers of width 64 on the edge graph, then a linear read-out of 3 values per edge):
     h1 = relu(W1 f + b1)
     h2 = relu(W2s h1 + W2n (h1[I-1] + h1[I+1]) / 2 + b2)
     h3 = relu(W3s h2 + W3n (h2[I-1] + h2[I+1]) / 2 + b3)
-    (a, b) = W4 h3 + b4
-Preconditioner term (SPD by construction), for r with 3 components and r~ = r / sqrt(d):
+    (a, b, c) = W4 h3 + b4
+Preconditioner (SPD for every parameter value):
+    M^-1 r = W S W r + Z (Z^T A Z)^-1 Z^T r + G r,
+  * W = D^-1/2 diag(exp(c_v)), c_v = (c_{I-1} + c_I) / 2 the mean of the outputs of the two edges at
+    vertex v, S = F^-1 diag(1 / lambda) F the circulant of each closed curve (per component): a learned
+    rescaling of the Jacobi-scaled circulant (c = 0 gives the two-level preconditioner back);
+  * G: for r with 3 components and r~ = r / sqrt(d),
     delta_I = r~_i2 - r~_i1, sigma_I = r~_i1 + r~_i2, ea = exp(2 a_I), eb = exp(2 b_I)
-    (G r)_i2 += (ea delta_I + eb sigma_I) / sqrt(d_i2),  (G r)_i1 += (-ea delta_I + eb sigma_I) / sqrt(d_i1)
+    (G r)_i2 += (ea delta_I + eb sigma_I) / sqrt(d_i2),  (G r)_i1 += (-ea delta_I + eb sigma_I) / sqrt(d_i1).
 Training loss of one pair (r, e = A^+ r, so e^T r = ||e||_A^2): preconditioned CG does not change
-when M^-1 is scaled, so the loss is the A-norm error of the best multiple of z = M^-1 r + G r,
+when M^-1 is scaled, so the loss is the A-norm error of the best multiple of z = M^-1 r,
     L = min_a ||a z - e||_A^2 / ||e||_A^2 = 1 - (z^T r)^2 / ((z^T A z)(e^T r)),
 the squared A-sine of the angle between z and e.  With s = z^T r, q = z^T A z:
-    dL/dz = -2 s / (q e^T r) (r - (s / q) A z).
+    dL/dz = -2 s / (q e^T r) (r - (s / q) A z),
+and through the rescaling, with z_S = W S W r and z2 = W S W (dL/dz) (S is symmetric):
+    dL/dc_v = sum over components of ((dL/dz)_v (z_S)_v + r_v (z2)_v).
 """
 from __future__ import annotations
 
@@ -27,7 +34,7 @@ import numpy as np
 H = 64
 F = 8
 SHAPES = [("W1", (H, F)), ("b1", (H,)), ("W2s", (H, H)), ("W2n", (H, H)), ("b2", (H,)),
-          ("W3s", (H, H)), ("W3n", (H, H)), ("b3", (H,)), ("W4", (2, H)), ("b4", (2,))]
+          ("W3s", (H, H)), ("W3n", (H, H)), ("b3", (H,)), ("W4", (3, H)), ("b4", (3,))]
 
 
 def n_params():
@@ -54,7 +61,7 @@ def init_params(seed=0, out_bias=-2.0):
                 w *= 0.1
             parts.append(w.ravel())
         elif name == "b4":
-            parts.append(np.full(s, out_bias))
+            parts.append(np.array([out_bias, out_bias, 0.0]))   # c = 0: the plain Jacobi scaling
         else:
             parts.append(np.zeros(s))
     return np.concatenate(parts)
@@ -139,7 +146,7 @@ def g_apply(out, diag, r):
 
 
 def g_out_grad(out, diag, r, gz):
-    """d(gz . G r) / d out: per edge [dL/da, dL/db] with gz = dL/d(G r)."""
+    """d(gz . G r) / d out: per edge [dL/da, dL/db, 0] with gz = dL/d(G r)."""
     sd = np.sqrt(diag)
     rt = r / sd[:, None]
     gt = gz / sd[:, None]
@@ -149,13 +156,32 @@ def g_out_grad(out, diag, r, gz):
     delta, sig = r2 - r1, r1 + r2
     dea = ((g2 - g1) * delta).sum(1)
     deb = ((g1 + g2) * sig).sum(1)
-    return np.stack([2 * ea * dea, 2 * eb * deb], axis=1)
+    return np.stack([2 * ea * dea, 2 * eb * deb, np.zeros_like(dea)], axis=1)
 
 
-def loss_and_grad(theta, f, diag, A, r, e, base_z):
-    """Loss of one pair and its parameter gradient. base_z = M^-1 r of the fixed preconditioner."""
+def vertex_log_scale(out):
+    """c_v = (c_{I-1} + c_I) / 2: vertex v is the second endpoint of edge v-1 and the first of edge v."""
+    c = out[:, 2]
+    return 0.5 * (np.roll(c, 1) + c)
+
+
+def scaled_spectral(diag, vlog, lam, r):
+    """W S W r with W = D^-1/2 diag(exp(vlog)), S = F^-1 diag(1 / lam) F per component (one closed curve)."""
+    w = np.exp(vlog) / np.sqrt(diag)
+    y = np.real(np.fft.ifft(np.fft.fft(w[:, None] * r, axis=0) / lam[:, None], axis=0))
+    return w[:, None] * y
+
+
+def loss_and_grad(theta, f, diag, A, r, e, base_z, lam=None):
+    """Loss of one pair and its parameter gradient.  base_z: the part of M^-1 r that does not depend
+    on the parameters (the coarse term; with lam = None, the whole fixed preconditioner).  lam: the
+    circulant symbol of the curve, which switches the learned rescaling W S W r on."""
     out, cache = forward(theta, f)
     z = base_z + g_apply(out, diag, r)
+    zs = None
+    if lam is not None:
+        zs = scaled_spectral(diag, vertex_log_scale(out), lam, r)
+        z = z + zs
     Az = A @ z
     er = float((e * r).sum())
     s = float((z * r).sum())
@@ -163,4 +189,8 @@ def loss_and_grad(theta, f, diag, A, r, e, base_z):
     L = 1.0 - s * s / (q * er)
     gz = -2.0 * s / (q * er) * (r - (s / q) * Az)
     dout = g_out_grad(out, diag, r, gz)
+    if lam is not None:
+        z2 = scaled_spectral(diag, vertex_log_scale(out), lam, gz)
+        dc_v = (gz * zs).sum(1) + (r * z2).sum(1)
+        dout[:, 2] = 0.5 * (dc_v + np.roll(dc_v, -1))   # edge I feeds vertices I and I+1
     return L, backward(theta, cache, dout)

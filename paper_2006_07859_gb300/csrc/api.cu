@@ -246,6 +246,7 @@ void tp_destroy(tp_ctx *ctx)
     Ctx &c = ctx->c;
     graphs_free(c);
     sym_select(c, 0);
+    sym_select_energy(c, 0);
     if (c.sol) solver_free(c);
     spectral_free(c);
     coarse_free(c);
@@ -465,6 +466,7 @@ tp_status tp_set_params(tp_ctx *ctx, const tp_params *p)
             CK(replan(c, cls));
         }
         CK(sym_select(c, 0));
+        CK(sym_select_energy(c, 0));
     }
     if ((p->precond >= TP_PRECOND_SPECTRAL) && !had_spectral) {
         cudaError_t e = spectral_setup(c, 0);
@@ -882,7 +884,7 @@ tp_status tp_gnn_forward(tp_ctx *ctx, float *features, float *out, tp_stream str
     CK(gnn_forward(c, s));
     if (features) CK(cudaMemcpyAsync(features, gnn_features(c), sizeof(float) * TP_GNN_FEATURES * c.nE,
                                      cudaMemcpyDeviceToDevice, s));
-    if (out) CK(cudaMemcpyAsync(out, gnn_outputs(c), sizeof(float) * 2 * c.nE, cudaMemcpyDeviceToDevice, s));
+    if (out) CK(cudaMemcpyAsync(out, gnn_outputs(c), sizeof(float) * 3 * c.nE, cudaMemcpyDeviceToDevice, s));
     return TP_OK;
 }
 
@@ -966,7 +968,7 @@ tp_status tp_cg_harvest(tp_ctx *ctx, const double *gamma, const double *rhs, int
 }
 
 tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, double *R, double *E, double *B,
-                               double *AB, double *ER, tp_stream stream)
+                               double *AB, double *ER, double *ILAM, tp_stream stream)
 {
     if (!ctx || !gamma || n < 0 || (n > 0 && (!R || !E || !B || !AB || !ER)))
         return fail(ctx, TP_ERR_INVALID_ARG, "bad pair arguments");
@@ -976,6 +978,11 @@ tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, double *
     if (st) return st;
     st = precond_setup(ctx, gamma, s);
     if (st) return st;
+    // with ILAM the circulant is left to the training step (its scaling is learned): B is the coarse
+    // term alone and ILAM receives this geometry's inverse symbols
+    const bool rescale = ILAM && c.spec;
+    if (ILAM && !c.spec) return fail(ctx, TP_ERR_UNSUPPORTED, "no circulant preconditioner in this context");
+    if (rescale) CK(cudaMemcpyAsync(ILAM, spectral_ilam(c, s), sizeof(double) * c.nV, cudaMemcpyDeviceToDevice, s));
     const size_t nv3 = 3 * (size_t)c.nV;
     for (int k = 0; k < n; ++k) {
         double *r = R + k * nv3;
@@ -984,7 +991,12 @@ tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, double *
         // operator, so only A-bar e is exactly consistent with e
         CK(pair_apply(c, gamma, 0, E + k * nv3, r, s));
         CK(gnn_problem_dot(c, E + k * nv3, r, ER + (size_t)k * c.nProb, s));  // before B may overwrite E
-        CK(precond_apply_base(c, r, b, s, nullptr));
+        if (rescale) {
+            CK(cudaMemsetAsync(b, 0, sizeof(double) * nv3, s));
+            if (c.prm.precond >= TP_PRECOND_TWOLEVEL) CK(coarse_apply(c, r, b, s));
+        } else {
+            CK(precond_apply_base(c, r, b, s, nullptr));
+        }
         if (c.prm.precond != TP_PRECOND_NONE) CK(project_mean(c, b, s, nullptr));
         CK(pair_apply(c, gamma, 0, b, AB + k * nv3, s));
     }
@@ -992,8 +1004,8 @@ tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, double *
 }
 
 tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, const double *R, const double *B,
-                            const double *AB, const double *ER, float lr, double *loss, float *grad,
-                            tp_stream stream)
+                            const double *AB, const double *ER, const double *ILAM, float lr, double *loss,
+                            float *grad, tp_stream stream)
 {
     tp_status st = need_gnn(ctx);
     if (st) return st;
@@ -1004,7 +1016,8 @@ tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, const doubl
     cudaStream_t s = (cudaStream_t)stream;
     st = records(ctx, gamma, 0, s);
     if (st) return st;
-    CK(gnn_train_step(c, gamma, n, R, B, AB, ER, lr, c.d_scal, s));
+    if (ILAM && !c.spec) return fail(ctx, TP_ERR_UNSUPPORTED, "no circulant preconditioner in this context");
+    CK(gnn_train_step(c, gamma, n, R, B, AB, ER, ILAM, lr, c.d_scal, s));
     if (grad) CK(cudaMemcpyAsync(grad, gnn_last_grad(c), sizeof(float) * gnn_num_params(), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(c.h_pinned, c.d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1012,7 +1025,29 @@ tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, const doubl
     return check_err_word(ctx, s);
 }
 
+tp_status tp_last_solve(const tp_ctx *ctx, double *rel_res, int32_t *iters)
+{
+    if (!ctx) return TP_ERR_INVALID_ARG;
+    const Ctx &c = ctx->c;
+    for (int q = 0; q < c.nProb; ++q) {
+        if (rel_res) rel_res[q] = q < (int)c.last_rr.size() ? c.last_rr[q] : 0.0;
+        if (iters) iters[q] = q < (int)c.last_iters.size() ? c.last_iters[q] : 0;
+    }
+    return TP_OK;
+}
+
 // ---------------------------------------------------------------------------------- autotuner
+
+tp_status tp_set_energy_variant(tp_ctx *ctx, int symmetric_tpt)
+{
+    if (!ctx) return TP_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (symmetric_tpt < 0 || symmetric_tpt > 2) return fail(ctx, TP_ERR_INVALID_ARG, "symmetric_tpt must be 0, 1 or 2");
+    if (symmetric_tpt > 0 && !(c.prm.precision == TP_MIXED && c.kp.fast))
+        return fail(ctx, TP_ERR_UNSUPPORTED, "the symmetric energy exists for TP_MIXED with (alpha, beta) = (2, 4.5)");
+    CK(sym_select_energy(c, symmetric_tpt));
+    return TP_OK;
+}
 
 tp_status tp_set_apply_variant(tp_ctx *ctx, int symmetric_tpt)
 {
@@ -1033,8 +1068,8 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
     tp_status st = records(ctx, gamma, 0, s);
     if (st) return st;
     if (ms)
-        for (int k = 0; k < 11; ++k) ms[k] = 0.0;
-    if (tpt) tpt[3] = 0;
+        for (int k = 0; k < 13; ++k) ms[k] = 0.0;
+    if (tpt) tpt[3] = tpt[4] = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1075,6 +1110,29 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
             err = replan(c, cls);
         }
         if (tpt) tpt[cls] = nc > 1 ? best : cand[0];
+        // the energy also has the symmetric pass (its rows are one double per edge and slot)
+        if (cls == 0 && nc > 1 && err == cudaSuccess) {
+            int best_sym = 0;
+            for (int t = 1; t <= 2 && err == cudaSuccess; ++t) {
+                if (sym_slots(c, t) * (size_t)c.nE * sizeof(double) > ((size_t)16 << 30)) continue;
+                if ((err = sym_select_energy(c, t)) != cudaSuccess) break;
+                if ((err = run(cls)) != cudaSuccess) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run(cls);
+                cudaEventRecord(e1, s);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                float tm = 0.f;
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&tm, e0, e1);
+                tm /= 3.f;
+                if (ms) ms[11 + t - 1] = tm;
+                if (tm < best_ms) {
+                    best_ms = tm;
+                    best_sym = t;
+                }
+            }
+            if (err == cudaSuccess) err = sym_select_energy(c, best_sym);
+            if (tpt) tpt[4] = best_sym;
+        }
         // the apply also has the symmetric pass (each unordered pair once), if its partial slots fit
         if (cls == 2 && nc > 1 && err == cudaSuccess) {
             int best_sym = 0;

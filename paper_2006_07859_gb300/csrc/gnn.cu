@@ -1,8 +1,11 @@
 // Learned preconditioner term (TP_PRECOND_LEARNED; this library's extension, not in the paper).
 //
 // A 3-layer network on the edge graph of the closed curves (width 64, BF16 weights, FP32
-// accumulation) maps local geometry to two log-weights (a_I, b_I) per edge.  They define an SPD
-// local term that is added to the two-level preconditioner:
+// accumulation) maps local geometry to three values (a_I, b_I, c_I) per edge that shape an SPD
+// preconditioner around the two-level one:
+//   M^-1 r = W S W r + Z (Z^T A Z)^-1 Z^T r + G r,
+//   W = D^-1/2 diag(exp(c_v)), c_v = mean of c over the two edges at vertex v, S the circulant of the
+//   Rayleigh-quotient symbol (c = 0: the two-level preconditioner), and the local term
 //   r~ = r / sqrt(d),  delta_I = r~_i2 - r~_i1,  sigma_I = r~_i1 + r~_i2,
 //   (G r)_i2 += (e^{2a} delta_I + e^{2b} sigma_I) / sqrt(d_i2),
 //   (G r)_i1 += (-e^{2a} delta_I + e^{2b} sigma_I) / sqrt(d_i1),
@@ -11,11 +14,13 @@
 //   [log(l / mean l), 1 - T_{I-1}.T_I, 1 - T_I.T_{I+1}, log(d_i1 / mean d), log(d_i2 / mean d),
 //    log(l_{I-1} / l_I), log(l_{I+1} / l_I), 1]
 // Layers: h1 = relu(W1 f + b1); h2 = relu(W2s h1 + W2n avg(h1[I-1], h1[I+1]) + b2);
-//         h3 = relu(W3s h2 + W3n avg(h2[I-1], h2[I+1]) + b3); (a, b) = W4 h3 + b4.
+//         h3 = relu(W3s h2 + W3n avg(h2[I-1], h2[I+1]) + b3); (a, b, c) = W4 h3 + b4.
 // Training minimises, over (residual, correction) pairs harvested from the CG solves (e = A^+ r), the
 // A-norm error of the best multiple of z = M^-1 r + G r (preconditioned CG ignores the scale of M):
 //   L = min_a ||a z - e||_A^2 / ||e||_A^2 = 1 - s^2 / (q e^T r),  s = z^T r,  q = z^T A z,
-//   dL/dz = -2 s / (q e^T r) (r - (s / q) A z).
+//   dL/dz = -2 s / (q e^T r) (r - (s / q) A z),
+// and through the rescaling (S symmetric), with z_S = W S W r and z2 = W S W (dL/dz):
+//   dL/dc_v = sum over components of ((dL/dz)_v (z_S)_v + r_v (z2)_v).
 // Parameters are FP32 masters with a BF16 copy; the forward and backward passes read the BF16
 // values (so the gradient is that of the network actually evaluated), Adam updates the masters.
 // The parameter-gradient reductions are deterministic (fixed block partials, fixed-order sums).
@@ -36,11 +41,11 @@ namespace tpe {
         if (e_ != cudaSuccess) return e_; \
     } while (0)
 
-constexpr int kH = TP_GNN_HIDDEN, kF = TP_GNN_FEATURES;
-// parameter layout: W1 [64][8], b1, W2s [64][64], W2n, b2, W3s, W3n, b3, W4 [2][64], b4 [2]
+constexpr int kH = TP_GNN_HIDDEN, kF = TP_GNN_FEATURES, kO = 3;
+// parameter layout: W1 [64][8], b1, W2s [64][64], W2n, b2, W3s, W3n, b3, W4 [3][64], b4 [3]
 constexpr int oW1 = 0, ob1 = oW1 + kH * kF, oW2s = ob1 + kH, oW2n = oW2s + kH * kH, ob2 = oW2n + kH * kH,
-              oW3s = ob2 + kH, oW3n = oW3s + kH * kH, ob3 = oW3n + kH * kH, oW4 = ob3 + kH, ob4 = oW4 + 2 * kH,
-              kNParams = ob4 + 2;
+              oW3s = ob2 + kH, oW3n = oW3s + kH * kH, ob3 = oW3n + kH * kH, oW4 = ob3 + kH, ob4 = oW4 + kO * kH,
+              kNParams = ob4 + kO;
 constexpr int kWgBlocks = 256;  // blocks of the weight-gradient kernels (fixed: deterministic sums)
 constexpr int kWgSub = 32;      // edges staged per sub-tile
 constexpr int kWgMax = kH * kH + kH;
@@ -51,7 +56,9 @@ struct GnnState {
     float *feat = nullptr;                                                  // [nE][8]
     float *z1 = nullptr, *z2 = nullptr, *z3 = nullptr;                      // pre-activations [nE][64]
     float *bA = nullptr, *bB = nullptr, *bC = nullptr;                      // backward scratch [nE][64]
-    float *out = nullptr, *dout = nullptr;                                  // [nE][2]
+    float *out = nullptr, *dout = nullptr;                                  // [nE][3]: a, b, c
+    double *vlog = nullptr;                                                 // [nV] c_v
+    double *zs = nullptr, *zg = nullptr, *w = nullptr, *dcv = nullptr;      // [nV][3], [nV][3], [nV][3], [nV]
     double *ew = nullptr;                                                   // [nE][2]: e^{2a}, e^{2b}
     double *diag = nullptr;                                                 // [nV] diag(A) of the bound curve
     double *cstat = nullptr;                                                // [nCurves][2]: mean l, mean d
@@ -189,31 +196,43 @@ __global__ void __launch_bounds__(128) k_gnn_lmp(int nE, const int *__restrict__
     }
 }
 
-// (a, b) = W4 relu(z3) + b4; also e^{2a}, e^{2b} in FP64 for the G term
+// (a, b, c) = W4 relu(z3) + b4; also e^{2a}, e^{2b} in FP64 for the G term
 __global__ void k_gnn_out(int nE, const float *__restrict__ z3, const __nv_bfloat16 *__restrict__ w,
                           float *__restrict__ out, double *__restrict__ ew)
 {
-    __shared__ float W[2 * kH + 2];
-    for (int t = threadIdx.x; t < 2 * kH + 2; t += blockDim.x) W[t] = bf(w, oW4 + t);
+    __shared__ float W[kO * kH + kO];
+    for (int t = threadIdx.x; t < kO * kH + kO; t += blockDim.x) W[t] = bf(w, oW4 + t);
     __syncthreads();
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nE) return;
-    float a = W[2 * kH], b = W[2 * kH + 1];
+    float o[kO];
+#pragma unroll
+    for (int q = 0; q < kO; ++q) o[q] = W[kO * kH + q];
     const float4 *z = reinterpret_cast<const float4 *>(z3 + (size_t)I * kH);
 #pragma unroll
     for (int k = 0; k < kH / 4; ++k) {
         const float4 v = z[k];
         const float hv[4] = {fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f)};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            a = fmaf(W[4 * k + q], hv[q], a);
-            b = fmaf(W[kH + 4 * k + q], hv[q], b);
-        }
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int c = 0; c < kO; ++c) o[c] = fmaf(W[c * kH + 4 * k + q], hv[q], o[c]);
     }
-    out[2 * I] = a;
-    out[2 * I + 1] = b;
-    ew[2 * I] = exp(2.0 * (double)a);
-    ew[2 * I + 1] = exp(2.0 * (double)b);
+    for (int c = 0; c < kO; ++c) out[kO * I + c] = o[c];
+    ew[2 * I] = exp(2.0 * (double)o[0]);
+    ew[2 * I + 1] = exp(2.0 * (double)o[1]);
+}
+
+// c_v = mean over the edges incident to v of their output c
+__global__ void k_gnn_vlog(int nV, const int *__restrict__ inc_ptr, const int *__restrict__ inc,
+                           const float *__restrict__ out, double *__restrict__ vlog)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    double s = 0.0;
+    const int k0 = inc_ptr[v], k1 = inc_ptr[v + 1];
+    for (int k = k0; k < k1; ++k) s += (double)out[kO * (inc[k] >> 1) + 2];
+    vlog[v] = k1 > k0 ? s / (k1 - k0) : 0.0;
 }
 
 // ---------------------------------------------------------------------------------- backward
@@ -222,15 +241,15 @@ __global__ void k_gnn_out(int nE, const float *__restrict__ z3, const __nv_bfloa
 __global__ void k_gnn_bout(int nE, const float *__restrict__ dout, const float *__restrict__ z3,
                            const __nv_bfloat16 *__restrict__ w, float *__restrict__ dz3)
 {
-    __shared__ float W[2 * kH];
-    for (int t = threadIdx.x; t < 2 * kH; t += blockDim.x) W[t] = bf(w, oW4 + t);
+    __shared__ float W[kO * kH];
+    for (int t = threadIdx.x; t < kO * kH; t += blockDim.x) W[t] = bf(w, oW4 + t);
     __syncthreads();
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nE) return;
-    const float da = dout[2 * I], db = dout[2 * I + 1];
+    const float da = dout[kO * I], db = dout[kO * I + 1], dc = dout[kO * I + 2];
     for (int k = 0; k < kH; ++k) {
         const float z = z3[(size_t)I * kH + k];
-        dz3[(size_t)I * kH + k] = z > 0.f ? fmaf(da, W[k], db * W[kH + k]) : 0.f;
+        dz3[(size_t)I * kH + k] = z > 0.f ? fmaf(da, W[k], fmaf(db, W[kH + k], dc * W[2 * kH + k])) : 0.f;
     }
 }
 
@@ -422,12 +441,40 @@ __global__ void k_gnn_doutput(int nE, const int *__restrict__ E, const double *_
     }
     const float da = (float)(scale * 2.0 * ew[2 * I] * dea), db = (float)(scale * 2.0 * ew[2 * I + 1] * deb);
     if (accumulate) {
-        dout[2 * I] += da;
-        dout[2 * I + 1] += db;
+        dout[kO * I] += da;
+        dout[kO * I + 1] += db;
     } else {
-        dout[2 * I] = da;
-        dout[2 * I + 1] = db;
+        dout[kO * I] = da;
+        dout[kO * I + 1] = db;
+        dout[kO * I + 2] = 0.f;
     }
+}
+
+// dc_v = sum over components of gz_v . zs_v + r_v . z2_v (the rescaling's gradient at vertex v)
+__global__ void k_gnn_dcv(int nV, const double *__restrict__ gz, const double *__restrict__ zs,
+                          const double *__restrict__ r, const double *__restrict__ z2, double *__restrict__ dcv)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    double s = 0.0;
+    for (int q = 0; q < 3; ++q) s += gz[3 * v + q] * zs[3 * v + q] + r[3 * v + q] * z2[3 * v + q];
+    dcv[v] = s;
+}
+
+// dout_c[I] += scale * (dc_{i1} + dc_{i2}) / 2   (c_v averages the two edges at v; closed curves)
+__global__ void k_gnn_dc_edges(int nE, const int *__restrict__ E, const double *__restrict__ dcv, double scale,
+                               float *__restrict__ dout)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nE) return;
+    dout[kO * I + 2] += (float)(scale * 0.5 * (dcv[E[2 * I]] + dcv[E[2 * I + 1]]));
+}
+
+// w = a + b
+__global__ void k_gnn_add(int n, const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ w)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] = a[i] + b[i];
 }
 
 // ---------------------------------------------------------------------------------- training loss
@@ -530,8 +577,14 @@ cudaError_t gnn_alloc(Ctx &c)
     TPE_CHECK(cudaMalloc(&G.feat, sizeof(float) * nE * kF));
     float **acts[] = {&G.z1, &G.z2, &G.z3, &G.bA, &G.bB, &G.bC};
     for (float **p : acts) TPE_CHECK(cudaMalloc(p, sizeof(float) * nE * kH));
-    TPE_CHECK(cudaMalloc(&G.out, sizeof(float) * nE * 2));
-    TPE_CHECK(cudaMalloc(&G.dout, sizeof(float) * nE * 2));
+    TPE_CHECK(cudaMalloc(&G.out, sizeof(float) * nE * kO));
+    TPE_CHECK(cudaMalloc(&G.dout, sizeof(float) * nE * kO));
+    TPE_CHECK(cudaMalloc(&G.vlog, sizeof(double) * nV));
+    TPE_CHECK(cudaMemset(G.vlog, 0, sizeof(double) * nV));
+    TPE_CHECK(cudaMalloc(&G.zs, sizeof(double) * 3 * nV));
+    TPE_CHECK(cudaMalloc(&G.zg, sizeof(double) * 3 * nV));
+    TPE_CHECK(cudaMalloc(&G.w, sizeof(double) * 3 * nV));
+    TPE_CHECK(cudaMalloc(&G.dcv, sizeof(double) * nV));
     TPE_CHECK(cudaMalloc(&G.ew, sizeof(double) * nE * 2));
     TPE_CHECK(cudaMalloc(&G.diag, sizeof(double) * nV));
     TPE_CHECK(cudaMalloc(&G.cstat, sizeof(double) * 2 * c.nCurves));
@@ -565,7 +618,7 @@ void gnn_free(Ctx &c)
     if (!c.gnn) return;
     GnnState &G = *c.gnn;
     void *p[] = {G.master, G.m,     G.v,     G.grad, G.wb, G.feat, G.z1, G.z2,    G.z3,    G.bA,
-                 G.bB,     G.bC,    G.out,   G.dout, G.ew, G.diag, G.cstat, G.wpart, G.loss, G.sq, G.g,
+                 G.bB,     G.bC,    G.out,   G.dout, G.ew, G.diag, G.cstat, G.wpart, G.loss, G.sq, G.vlog, G.zs, G.zg, G.w, G.dcv, G.g,
                  G.Ag,     G.gz,    G.eprev, G.enext, G.ecurve};
     for (void *q : p)
         if (q) cudaFree(q);
@@ -613,6 +666,7 @@ cudaError_t gnn_bind(Ctx &c, int which, const double *diag, cudaStream_t s)
 double *gnn_diag_buffer(Ctx &c) { return c.gnn->diag; }
 const float *gnn_features(const Ctx &c) { return c.gnn->feat; }
 const float *gnn_outputs(const Ctx &c) { return c.gnn->out; }
+const double *gnn_vlog(const Ctx &c) { return c.gnn->vlog; }
 
 // Network forward on the bound features with the current BF16 weights: outputs and e^{2a}, e^{2b}.
 cudaError_t gnn_forward(Ctx &c, cudaStream_t s)
@@ -623,7 +677,8 @@ cudaError_t gnn_forward(Ctx &c, cudaStream_t s)
     k_gnn_lmp<<<nb, 128, 0, s>>>(c.nE, G.eprev, G.enext, G.z1, G.wb, oW2s, oW2n, ob2, G.z2);
     k_gnn_lmp<<<nb, 128, 0, s>>>(c.nE, G.eprev, G.enext, G.z2, G.wb, oW3s, oW3n, ob3, G.z3);
     k_gnn_out<<<nb, 128, 0, s>>>(c.nE, G.z3, G.wb, G.out, G.ew);
-    c.launches += 4;
+    k_gnn_vlog<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_inc_ptr, c.d_inc, G.out, G.vlog);
+    c.launches += 5;
     return cudaGetLastError();
 }
 
@@ -647,7 +702,7 @@ cudaError_t gnn_backward(Ctx &c, const float *dout, float *grad, cudaStream_t s)
     GnnState &G = *c.gnn;
     const int nb = (c.nE + 127) / 128;
     // read-out: W4, b4, then dz3 into bA
-    TPE_CHECK((wgrad<2, kH>(c, dout, G.z3, 0, oW4, ob4, grad, s)));
+    TPE_CHECK((wgrad<kO, kH>(c, dout, G.z3, 0, oW4, ob4, grad, s)));
     k_gnn_bout<<<nb, 128, 0, s>>>(c.nE, dout, G.z3, G.wb, G.bA);
     c.launches++;
     // layer 3: x = h2 (self) and avg h2 (neighbours)
@@ -704,26 +759,43 @@ cudaError_t gnn_problem_dot(Ctx &c, const double *a, const double *b, double *ou
     return cudaGetLastError();
 }
 
-// One training step over n_pairs prepared pairs (r_i, b_i = M^-1 r_i, Ab_i = A b_i and, per problem,
-// er_i = e_i . r_i) on the bound geometry, whose edge records are in slot 0.  The loss at the
-// current parameters (mean over pairs and problems) goes to loss_dev (device double [1]); then, for
-// lr > 0, one Adam step.  The parameter gradient is left in the context (gnn_last_grad).
+// One training step over n_pairs prepared pairs of the bound geometry (edge records in slot 0):
+// r_i, b_i (the parameter-independent part of M^-1 r_i: the coarse term), Ab_i = A b_i, er_i = e_i . r_i
+// per problem, and ilam (the inverse circulant symbols of the geometry, [nV]; NULL: no rescaled
+// circulant).  Per pair: z = b + W S W r + G r, one A apply of the parameter-dependent part, the loss,
+// dL/dz, the output gradients of G and, through one more circulant apply, of the rescaling.  The loss
+// at the current parameters (mean over pairs and problems) goes to loss_dev; then, for lr > 0, one
+// Adam step.  The parameter gradient is left in the context (gnn_last_grad).
 cudaError_t gnn_train_step(Ctx &c, const double *gamma, int n_pairs, const double *R, const double *B,
-                           const double *AB, const double *ER, float lr, double *loss_dev, cudaStream_t s)
+                           const double *AB, const double *ER, const double *ilam, float lr, double *loss_dev,
+                           cudaStream_t s)
 {
     GnnState &G = *c.gnn;
     const size_t nv3 = 3 * (size_t)c.nV;
     const double scale = 1.0 / ((double)n_pairs * c.nProb);
+    const int nbv = (int)((nv3 + 255) / 256);
     TPE_CHECK(gnn_forward(c, s));
     TPE_CHECK(cudaMemsetAsync(G.loss, 0, sizeof(double) * c.nProb, s));
     for (int i = 0; i < n_pairs; ++i) {
         const double *r = R + i * nv3, *b = B + i * nv3, *Ab = AB + i * nv3, *er = ER + (size_t)i * c.nProb;
         TPE_CHECK(gnn_gapply(c, r, G.g, 0, s, nullptr));
-        TPE_CHECK(pair_apply(c, gamma, 0, G.g, G.Ag, s));
-        k_gnn_loss<<<c.nProb, 256, 0, s>>>(c.d_prob_v, r, b, G.g, Ab, G.Ag, er, scale, G.sq, G.loss);
+        if (ilam) {
+            TPE_CHECK(spectral_apply_ex(c, r, G.zs, s, nullptr, G.diag, ilam, G.vlog));
+            k_gnn_add<<<nbv, 256, 0, s>>>((int)nv3, G.g, G.zs, G.w);
+            c.launches++;
+        }
+        const double *w = ilam ? G.w : G.g;
+        TPE_CHECK(pair_apply(c, gamma, 0, w, G.Ag, s));
+        k_gnn_loss<<<c.nProb, 256, 0, s>>>(c.d_prob_v, r, b, w, Ab, G.Ag, er, scale, G.sq, G.loss);
         k_gnn_gz<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_vprob, r, Ab, G.Ag, er, G.sq, G.gz);
         c.launches += 2;
         TPE_CHECK(gnn_out_grad(c, r, G.gz, scale, i > 0, G.dout, s));
+        if (ilam) {
+            TPE_CHECK(spectral_apply_ex(c, G.gz, G.zg, s, nullptr, G.diag, ilam, G.vlog));
+            k_gnn_dcv<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, G.gz, G.zs, r, G.zg, G.dcv);
+            k_gnn_dc_edges<<<(c.nE + 127) / 128, 128, 0, s>>>(c.nE, c.d_edges, G.dcv, scale, G.dout);
+            c.launches += 2;
+        }
     }
     TPE_CHECK(gnn_backward(c, G.dout, G.grad, s));
     if (lr > 0.f) TPE_CHECK(gnn_adam(c, G.grad, lr, s));

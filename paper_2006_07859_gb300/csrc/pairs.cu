@@ -805,10 +805,15 @@ static cudaError_t run_pairs(Ctx &c, int which, const double *gamma, const doubl
 
 cudaError_t pair_energy(Ctx &c, const double *gamma, int which, double *rows_out, double *E_out, cudaStream_t s)
 {
-    TPE_CHECK(run_pairs<OP_ENERGY>(c, which, gamma, nullptr, s));
+    const bool sym = c.energy_sym > 0;
+    if (sym)
+        TPE_CHECK(sym_energy_pass(c, which, gamma, s));
+    else
+        TPE_CHECK(run_pairs<OP_ENERGY>(c, which, gamma, nullptr, s));
+    const Ctx::Plan &pl = sym ? c.plan_sym_e : c.plan_energy;
     double *rows = rows_out ? rows_out : c.d_rows;
     if (c.nE > 0) {
-        k_energy_rows<<<(c.nE + 255) / 256, 256, 0, s>>>(c.nE, c.plan_energy.max_slots, c.plan_energy.d_eslots, c.d_part, c.d_ellw[which],
+        k_energy_rows<<<(c.nE + 255) / 256, 256, 0, s>>>(c.nE, pl.max_slots, pl.d_eslots, c.d_part, c.d_ellw[which],
                                                          rows);
         c.launches++;
     }

@@ -256,6 +256,172 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs_sym(const PairArgs pa)
     }
 }
 
+// ---------------------------------------------------------------------------------- symmetric energy
+
+// One unordered pair of the energy: the target row receives l_J sum_ab |T_I x d_ab|^alpha |d_ab|^-beta,
+// the source row l_I sum_ab |T_J x d_ab|^alpha |d_ab|^-beta (Eqs. 17-18; the factor l_I / 4 of a row
+// is applied when the rows are summed).  Near pairs take both |T x d|^2 in FP64.
+template <bool FAST, bool DF>
+__device__ __forceinline__ void pair_energy_both(const Tgt<float> &t, const Src<PMIX> &s, bool keep, bool near,
+                                                 const KernelParams &kp, float &at, float &as)
+{
+    const float alpha = (float)kp.alpha, beta = (float)kp.beta;
+    V3<float> dd[4];
+    chords<DF>(t, s, dd);
+    float tt;
+    V3<float> dp;
+    float cI[2] = {perp2(dd[0], t.T, tt, dp), perp2(dd[1], t.T, tt, dp)};  // depends on b only
+    float cJ[2] = {perp2(dd[0], s.T, tt, dp), perp2(dd[2], s.T, tt, dp)};  // depends on a only
+    if constexpr (DF)
+        if (near) {
+            cI[0] = perp2_near(t.p1, t.l1, s.q1, s.m1, t.T, t.Tl);
+            cI[1] = perp2_near(t.p1, t.l1, s.q2, s.m2, t.T, t.Tl);
+            cJ[0] = perp2_near(t.p1, t.l1, s.q1, s.m1, s.T, s.Tm);
+            cJ[1] = perp2_near(t.p2, t.l2, s.q1, s.m1, s.T, s.Tm);
+        }
+    const float pI[2] = {pow_c<float, FAST>(cI[0], alpha), pow_c<float, FAST>(cI[1], alpha)};
+    const float pJ[2] = {pow_c<float, FAST>(cJ[0], alpha), pow_c<float, FAST>(cJ[1], alpha)};
+    float fI = 0.f, fJ = 0.f;
+#pragma unroll
+    for (int ab = 0; ab < 4; ++ab) {
+        const float d2 = dot3(dd[ab], dd[ab]);
+        float r2;
+        const float rb = inv_pow<float, FAST, 0>(d2, beta, r2);
+        fI += pI[ab & 1] * rb;
+        fJ += pJ[ab >> 1] * rb;
+    }
+    at += keep ? s.ell * fI : 0.f;
+    as += keep ? t.ell * fJ : 0.f;
+}
+
+// MODE 2: near pairs possible (|g_i1 - g_j1|^2 < near cutoff^2 take FP64 cross products); 1: double-float
+// chords; 0: single-float chords (far tiles).
+template <int TPT, bool FAST, bool CHECK, int MODE, bool SRC>
+__device__ __forceinline__ void sym_energy_tile(const Tgt<float> (&tg)[TPT], const bool (&valid)[TPT],
+                                                const Tile<PMIX, false> &tl, int cnt, float (&at)[TPT],
+                                                float *sacc, float *scmp, const KernelParams &kp)
+{
+    const int lane = threadIdx.x & 31;
+    const int P = max(cnt, 32);
+    for (int step = 0; step < P; ++step) {
+        int j = step + lane;
+        if (j >= P) j -= P;
+        if (j < cnt) {
+            Src<PMIX> s;
+            load_source<PMIX, false>(s, tl, j);
+            float as = 0.f;
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                bool keep = valid[k];
+                if constexpr (CHECK)
+                    keep = keep & (s.j1 != tg[k].i1) & (s.j1 != tg[k].i2) & (s.j2 != tg[k].i1) & (s.j2 != tg[k].i2);
+                bool near = false;
+                if constexpr (MODE == 2) {
+                    const V3<float> e = diff3<true>(tg[k].p1, tg[k].l1, s.q1, s.m1);
+                    near = keep && dot3(e, e) < kp.near2f;
+                }
+                pair_energy_both<FAST, (MODE >= 1)>(tg[k], s, keep, near, kp, at[k], as);
+            }
+            if constexpr (SRC) {
+                float acc = sacc[j], cmp = scmp[j];
+                kahan_add(acc, cmp, as);
+                sacc[j] = acc;
+                scmp[j] = cmp;
+            }
+        }
+        if constexpr (SRC) __syncwarp();
+    }
+}
+
+template <int TPT, bool FAST>
+__global__ void __launch_bounds__(kThreads, 3) k_energy_sym(const PairArgs pa)
+{
+    __shared__ Tile<PMIX, false> tl;
+    __shared__ float sacc[kSymWarps][kTile], scmp[kSymWarps][kTile];
+    __shared__ int s_item;
+    __shared__ float s_box[2][kThreads / 32][6];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(pa.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= pa.n_items) break;
+        const WorkItem w = pa.items[it];
+        const int bslot = w.slot >> 16, cslot = w.slot & 0xffff;
+        const bool diag = bslot == cslot;
+        Tgt<float> tg[TPT];
+        bool valid[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            const int loc = threadIdx.x + k * kThreads;
+            valid[k] = loc < w.ntgt;
+            load_target<PMIX>(tg[k], w.tgt0 + min(loc, w.ntgt - 1), pa.recF, pa.recLo, pa.recD);
+        }
+        double A[TPT];
+        float at[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) A[k] = 0.0;
+        float tbox[6];
+        {
+            float b[6] = {1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) box_add(b, tg[k].p1, tg[k].p2);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                for (int q = 0; q < 6; ++q) {
+                    const float v = __shfl_xor_sync(0xffffffffu, b[q], o);
+                    b[q] = q < 3 ? fminf(b[q], v) : fmaxf(b[q], v);
+                }
+            for (int q = 0; q < 6; ++q) tbox[q] = b[q];
+        }
+        for (int s0 = w.src0; s0 < w.src1; s0 += kTile) {
+            const int cnt = min(kTile, w.src1 - s0);
+            __syncthreads();
+            float sb[6] = {1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
+            if (threadIdx.x < cnt) {
+                const int J = s0 + threadIdx.x;
+                const RecF r = pa.recF[J];
+                tl.r[threadIdx.x] = r;
+                tl.lo[threadIdx.x] = pa.recLo[J];
+                box_add(sb, V3<float>{r.a.x, r.a.y, r.a.z}, V3<float>{r.b.x, r.b.y, r.b.z});
+            }
+            for (int t = lane; t < kTile; t += 32) sacc[wid][t] = scmp[wid][t] = 0.f;
+            block_box(sb, s_box[1]);
+            const bool check = !(s0 + cnt - 1 < w.nb_lo || s0 > w.nb_hi);
+            float g2 = 0.f;
+            for (int q = 0; q < 3; ++q) {
+                const float gap = fmaxf(fmaxf(sb[q] - tbox[3 + q], tbox[q] - sb[3 + q]), 0.f);
+                g2 += gap * gap;
+            }
+            const int mode = g2 < pa.kp.near2f ? 2 : (g2 < pa.kp.mid2f ? 1 : 0);
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) at[k] = 0.f;
+            if (diag)
+                sym_energy_tile<TPT, FAST, true, 2, false>(tg, valid, tl, cnt, at, sacc[wid], scmp[wid], pa.kp);
+            else if (check || mode == 2)
+                sym_energy_tile<TPT, FAST, true, 2, true>(tg, valid, tl, cnt, at, sacc[wid], scmp[wid], pa.kp);
+            else if (mode == 1)
+                sym_energy_tile<TPT, FAST, false, 1, true>(tg, valid, tl, cnt, at, sacc[wid], scmp[wid], pa.kp);
+            else
+                sym_energy_tile<TPT, FAST, false, 0, true>(tg, valid, tl, cnt, at, sacc[wid], scmp[wid], pa.kp);
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) A[k] += (double)at[k];
+            if (!diag) {
+                __syncthreads();
+                if (threadIdx.x < cnt) {
+                    double x = 0.0;
+                    for (int wv = 0; wv < kSymWarps; ++wv) x += (double)sacc[wv][threadIdx.x] - (double)scmp[wv][threadIdx.x];
+                    pa.part[(size_t)bslot * pa.nE + s0 + threadIdx.x] = x;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < TPT; ++k)
+            if (valid[k]) pa.part[(size_t)cslot * pa.nE + w.tgt0 + threadIdx.x + k * kThreads] = A[k];
+    }
+}
+
 // ---------------------------------------------------------------------------------- host side
 
 static int sym_occupancy(int tpt)
@@ -346,6 +512,66 @@ cudaError_t sym_select(Ctx &c, int tpt)
         c.part_elems = need;
     }
     c.apply_sym = tpt;
+    return cudaGetLastError();
+}
+
+static int sym_energy_occupancy(int tpt)
+{
+    int occ = 0;
+    if (tpt == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_energy_sym<1, true>, kThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_energy_sym<2, true>, kThreads, 0);
+    return occ;
+}
+
+// The energy's symmetric pass on (tpt 1, 2) or off (0); same conditions as sym_select.
+cudaError_t sym_select_energy(Ctx &c, int tpt)
+{
+    Ctx::Plan &pl = c.plan_sym_e;
+    if (pl.d_items) TPE_CHECK(cudaFree(pl.d_items));
+    if (pl.d_eslots) TPE_CHECK(cudaFree(pl.d_eslots));
+    pl = Ctx::Plan{};
+    c.energy_sym = 0;
+    if (tpt <= 0) return cudaSuccess;
+    if (c.prm.precision != TP_MIXED || !c.kp.fast || (tpt != 1 && tpt != 2)) return cudaErrorInvalidValue;
+    sym_plan_items(c, pl, tpt, sym_energy_occupancy(tpt));
+    const size_t need = (size_t)pl.max_slots * std::max(1, c.nE);
+    if (need > c.part_elems) {
+        TPE_CHECK(cudaFree(c.d_part));
+        TPE_CHECK(cudaMalloc(&c.d_part, sizeof(double) * need));
+        c.part_elems = need;
+    }
+    c.energy_sym = tpt;
+    return cudaGetLastError();
+}
+
+cudaError_t sym_energy_pass(Ctx &c, int which, const double *gamma, cudaStream_t s)
+{
+    Ctx::Plan &pl = c.plan_sym_e;
+    if (pl.n_items == 0) return cudaSuccess;
+    TPE_CHECK(cudaMemsetAsync(c.d_counter + 5, 0, sizeof(int), s));
+    PairArgs pa;
+    pa.items = pl.d_items;
+    pa.n_items = pl.n_items;
+    pa.counter = c.d_counter + 5;
+    pa.recF = which ? c.d_recF2 : c.d_recF;
+    pa.recLo = which ? c.d_recLo2 : c.d_recLo;
+    pa.recD = nullptr;
+    pa.urecF = nullptr;
+    pa.urecD = nullptr;
+    pa.na = NearArgs{gamma, c.d_edges, c.d_ellw[which], c.d_Tw[which], nullptr};
+    pa.part = c.d_part;
+    pa.nE = c.nE;
+    pa.kp = c.kp;
+    pa.skip = nullptr;
+    const int slot = c.profile ? prof_begin(c, OP_ENERGY, s) : -1;
+    if (pl.tpt == 1)
+        k_energy_sym<1, true><<<pl.grid, kThreads, 0, s>>>(pa);
+    else
+        k_energy_sym<2, true><<<pl.grid, kThreads, 0, s>>>(pa);
+    if (slot >= 0 || slot <= -2) prof_end(c, slot, s);
+    c.launches++;
     return cudaGetLastError();
 }
 

@@ -483,12 +483,15 @@ cudaError_t precond_apply_base(Ctx &c, const double *r, double *z, cudaStream_t 
     }
 }
 
-// M^-1 r of the configured preconditioner; TP_PRECOND_LEARNED adds the learned term G r.
+// M^-1 r of the configured preconditioner.  TP_PRECOND_LEARNED: the circulant with the learned
+// per-vertex rescaling, the coarse term and the learned local term G r.
 cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip)
 {
-    cudaError_t e = precond_apply_base(c, r, z, s, skip);
-    if (e != cudaSuccess || c.prm.precond != TP_PRECOND_LEARNED) return e;
+    if (c.prm.precond != TP_PRECOND_LEARNED) return precond_apply_base(c, r, z, s, skip);
     if (!gnn_ready(c) || !gnn_bound(c)) return cudaErrorNotReady;
+    cudaError_t e = spectral_apply_ex(c, r, z, s, skip, c.d_diag, spectral_ilam(c, s), gnn_vlog(c));
+    if (e != cudaSuccess) return e;
+    if ((e = coarse_apply(c, r, z, s)) != cudaSuccess) return e;
     return gnn_gapply(c, r, z, 1, s, skip);
 }
 
@@ -852,6 +855,9 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
     TPE_CHECK(cudaMemcpyAsync(hcg.data(), c.d_cg, sizeof(CGScalars) * c.nProb, cudaMemcpyDeviceToHost, s));
     TPE_CHECK(cudaMemcpyAsync(hrr.data(), rr, sizeof(double) * c.nProb, cudaMemcpyDeviceToHost, s));
     TPE_CHECK(cudaStreamSynchronize(s));
+    c.last_rr = hrr;
+    c.last_iters.resize(c.nProb);
+    for (int qq = 0; qq < c.nProb; ++qq) c.last_iters[qq] = hcg[qq].iters;
     int mx_it = 0, bd = 0, conv = 1;
     double mx_rr = 0.0;
     for (int qq = 0; qq < c.nProb; ++qq) {

@@ -264,10 +264,13 @@ __global__ void k_four_out(int v0, int n, const double2 *__restrict__ buf, const
     for (int c = 0; c < 3; ++c) z[3 * (v0 + m) + c] = buf[(size_t)c * n + m].x * d;
 }
 
-__global__ void k_dinv(int nV, const double *__restrict__ diag, double *__restrict__ dinv)
+// dinv = exp(vlog) / sqrt(diag): the Jacobi scaling of the circulant, optionally rescaled per vertex
+// (the learned preconditioner's log-scale; vlog may be NULL)
+__global__ void k_dinv(int nV, const double *__restrict__ diag, const double *__restrict__ vlog,
+                       double *__restrict__ dinv)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nV) dinv[i] = diag[i] > 0.0 ? 1.0 / sqrt(diag[i]) : 0.0;
+    if (i < nV) dinv[i] = diag[i] > 0.0 ? (vlog ? exp(vlog[i]) : 1.0) / sqrt(diag[i]) : 0.0;
 }
 
 // ---------------------------------------------------------------------------------- set-up kernels
@@ -545,9 +548,10 @@ void spectral_free(Ctx &c)
     c.spec = nullptr;
 }
 
-cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip)
+// The inverse symbols the applies currently divide by (refreshed after a Rayleigh-quotient set-up).
+const double *spectral_ilam(Ctx &c, cudaStream_t s)
 {
-    if (!c.spec) return cudaErrorNotSupported;
+    if (!c.spec) return nullptr;
     SpecState &S = *c.spec;
     const double *rq = (c.prm.precond >= TP_PRECOND_SPECTRAL_RQ && S.rq_ready) ? S.d_sym_rq : nullptr;
     const int src = rq ? 1 : 0;
@@ -556,12 +560,28 @@ cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, c
         c.launches++;
         S.ilam_src = src;
     }
-    k_dinv<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_diag, S.d_dinv);
+    return S.d_ilam;
+}
+
+cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip)
+{
+    if (!c.spec) return cudaErrorNotSupported;
+    const double *il = spectral_ilam(c, s);
+    return spectral_apply_ex(c, r, z, s, skip, c.d_diag, il, nullptr);
+}
+
+// z = W F^-1 diag(ilam) F W r per closed curve and component, W = diag(exp(vlog) / sqrt(diag)).
+cudaError_t spectral_apply_ex(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip,
+                              const double *diag, const double *ilam, const double *vlog)
+{
+    if (!c.spec) return cudaErrorNotSupported;
+    SpecState &S = *c.spec;
+    k_dinv<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, diag, vlog, S.d_dinv);
     c.launches++;
     if (!S.small_idx.empty()) {
         int M = S.max_small_M;
         k_spec_small<<<(int)S.small_idx.size() * 3, kFFTThreads, sizeof(double2) * M, s>>>(
-            S.d_curves, S.d_small_idx, r, z, S.d_dinv, S.d_sym, S.d_chirp, S.d_bhat, S.d_tw, S.d_ilam, skip,
+            S.d_curves, S.d_small_idx, r, z, S.d_dinv, S.d_sym, S.d_chirp, S.d_bhat, S.d_tw, ilam, skip,
             c.independent);
         c.launches++;
     }
@@ -576,7 +596,7 @@ cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, c
         k_four_prep<<<nb, 256, 0, s>>>(C.v0, n, r, S.d_dinv, S.d_buf0);
         k_four_a<<<dim3(N1 / GA, 3), kFFTThreads, smA, s>>>(S.d_buf0, n, N1, N2, C.logN2, GA, S.d_tw, 0);
         k_four_c<<<dim3(N2 / GC, 3), kFFTThreads, smC, s>>>(S.d_buf0, S.d_buf1, n, N1, N2, C.logM, GC, S.d_tw, 0);
-        k_four_div<<<nb, 256, 0, s>>>(n, S.d_ilam + C.v0, S.d_buf1);
+        k_four_div<<<nb, 256, 0, s>>>(n, ilam + C.v0, S.d_buf1);
         k_four_a<<<dim3(N1 / GA, 3), kFFTThreads, smA, s>>>(S.d_buf1, n, N1, N2, C.logN2, GA, S.d_tw, 1);
         k_four_c<<<dim3(N2 / GC, 3), kFFTThreads, smC, s>>>(S.d_buf1, S.d_buf0, n, N1, N2, C.logM, GC, S.d_tw, 1);
         k_four_out<<<nb, 256, 0, s>>>(C.v0, n, S.d_buf0, S.d_dinv, z);

@@ -123,6 +123,8 @@ struct Ctx {
     int tpt[3] = {0, 0, 0};  // targets per thread chosen by tp_autotune (energy, diff, apply + diag); 0: default
     Plan plan_sym;           // symmetric apply (pairs_sym.cu): items over edge-block pairs (b, c >= b)
     int apply_sym = 0;       // > 0: the apply runs the symmetric pass with this many targets per thread
+    Plan plan_sym_e;         // symmetric energy (pairs_sym.cu)
+    int energy_sym = 0;      // > 0: the energy runs the symmetric pass with this many targets per thread
     int *d_counter = nullptr;  // persistent-queue counters [8]
     // edge records
     RecF *d_recF = nullptr, *d_recF2 = nullptr;
@@ -173,6 +175,8 @@ struct Ctx {
     int64_t graph_clock = 0;
     int graphs_broken = 0;         // a capture failed: direct launches from then on
     int setups_since_full = -1;    // preconditioner set-ups since the last full one (-1: none yet)
+    std::vector<double> last_rr;   // per problem: true relative residual of the last CG solve
+    std::vector<int> last_iters;   // per problem: its iterations
     // (residual, iterate) capture of a CG solve: every `every` iterations r -> R[n], y -> Y[n]
     struct Harvest {
         double *R = nullptr, *Y = nullptr;
@@ -202,6 +206,8 @@ cudaError_t pair_diag(Ctx &c, const double *gamma_geom, int which, double *diag,
 cudaError_t sym_select(Ctx &c, int tpt);  // (pairs_sym.cu) symmetric apply on (tpt 1, 2) or off (0)
 cudaError_t sym_apply_pass(Ctx &c, int which, const double *gamma, const double *u, cudaStream_t s);
 size_t sym_slots(const Ctx &c, int tpt);
+cudaError_t sym_select_energy(Ctx &c, int tpt);
+cudaError_t sym_energy_pass(Ctx &c, int which, const double *gamma, cudaStream_t s);
 void make_plans(Ctx &c);
 cudaError_t replan(Ctx &c, int cls);  // rebuild the plan of one op class (0 energy, 1 diff, 2 apply/diag)
 int tpt_default(const Ctx &c, int cls);
@@ -221,6 +227,9 @@ void coarse_free(Ctx &c);
 cudaError_t spectral_symbol_copy(Ctx &c, int rq, double *out, cudaStream_t s);
 void spectral_free(Ctx &c);
 cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip_flag);
+cudaError_t spectral_apply_ex(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip,
+                              const double *diag, const double *ilam, const double *vlog);
+const double *spectral_ilam(Ctx &c, cudaStream_t s);
 cudaError_t precond_apply_base(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip_flag);
 cudaError_t coarse_init(Ctx &c);
 cudaError_t solver_setup(Ctx &c);
@@ -260,7 +269,9 @@ cudaError_t gnn_out_grad(Ctx &c, const double *r, const double *gz, double scale
                          cudaStream_t s);
 cudaError_t gnn_problem_dot(Ctx &c, const double *a, const double *b, double *out, cudaStream_t s);
 cudaError_t gnn_train_step(Ctx &c, const double *gamma, int n_pairs, const double *R, const double *B,
-                           const double *AB, const double *ER, float lr, double *loss_dev, cudaStream_t s);
+                           const double *AB, const double *ER, const double *ilam, float lr, double *loss_dev,
+                           cudaStream_t s);
+const double *gnn_vlog(const Ctx &c);
 
 }  // namespace tpe
 

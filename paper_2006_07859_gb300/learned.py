@@ -18,13 +18,13 @@ HIDDEN, FEATURES = tpe.TP_GNN_HIDDEN, tpe.TP_GNN_FEATURES
 # parameter blocks in the order of the C ABI (row-major matrices)
 SHAPES = [("W1", (HIDDEN, FEATURES)), ("b1", (HIDDEN,)), ("W2s", (HIDDEN, HIDDEN)), ("W2n", (HIDDEN, HIDDEN)),
           ("b2", (HIDDEN,)), ("W3s", (HIDDEN, HIDDEN)), ("W3n", (HIDDEN, HIDDEN)), ("b3", (HIDDEN,)),
-          ("W4", (2, HIDDEN)), ("b4", (2,))]
+          ("W4", (3, HIDDEN)), ("b4", (3,))]
 
 
 def init_params(seed: int = 0, out_bias: float = -2.0) -> np.ndarray:
     """He-style initial parameters (float32): weights N(0, 1 / fan_in), read-out weights scaled by 0.1,
-    hidden biases 0, read-out biases `out_bias` (so G starts as a small multiple of the Jacobi-scaled
-    stencils, e^{2 out_bias})."""
+    hidden biases 0, read-out biases `out_bias` for (a, b) (so G starts as a small multiple of the
+    Jacobi-scaled stencils, e^{2 out_bias}) and 0 for c (the circulant starts unscaled)."""
     rng = np.random.default_rng(seed)
     parts = []
     for name, s in SHAPES:
@@ -32,7 +32,7 @@ def init_params(seed: int = 0, out_bias: float = -2.0) -> np.ndarray:
             w = rng.normal(0.0, 1.0 / np.sqrt(s[1]), size=s)
             parts.append((0.1 * w if name == "W4" else w).ravel())
         elif name == "b4":
-            parts.append(np.full(s, out_bias))
+            parts.append(np.array([out_bias, out_bias, 0.0]))
         else:
             parts.append(np.zeros(s))
     theta = np.concatenate(parts).astype(np.float32)
@@ -43,13 +43,14 @@ def init_params(seed: int = 0, out_bias: float = -2.0) -> np.ndarray:
 @dataclasses.dataclass
 class PairSet:
     """Prepared training pairs of one geometry: R = A-bar e (the residuals exactly consistent with the
-    harvested corrections e), B = P M_2L^-1 R, AB = A-bar B (all [n, nV, 3] float64 on the GPU) and
-    ER = e . r per problem ([n, n_problems])."""
+    harvested corrections e), B = the coarse term of R, AB = A-bar B (all [n, nV, 3] float64 on the GPU),
+    ER = e . r per problem ([n, n_problems]) and ILAM, the geometry's inverse circulant symbols ([nV])."""
     gamma: object
     R: object
     B: object
     AB: object
     ER: object
+    ILAM: object = None
 
     @property
     def n(self) -> int:
@@ -67,9 +68,10 @@ def harvest(ctx: tpe.Context, gamma, rhs, every: int = 1, max_pairs: int = 32) -
     R, E = R[:n].contiguous(), E[:n].contiguous()
     AB = torch.empty_like(R)
     ER = torch.empty((n, ctx.n_problems), dtype=torch.float64, device="cuda")
+    ILAM = torch.empty(nV, dtype=torch.float64, device="cuda")
     if n:
-        tpe.tp_gnn_prepare_pairs(ctx, gamma, R, E, E, AB, ER)  # R := A-bar E; B overwrites E in place
-    return PairSet(gamma.clone(), R, E, AB, ER)
+        tpe.tp_gnn_prepare_pairs(ctx, gamma, R, E, E, AB, ER, ILAM)  # R := A-bar E; B overwrites E in place
+    return PairSet(gamma.clone(), R, E, AB, ER, ILAM)
 
 
 def harvest_descent(ctx: tpe.Context, gamma, steps: int, every: int = 1, max_pairs: int = 32) -> list[PairSet]:
@@ -107,7 +109,7 @@ def train(ctx: tpe.Context, sets: list[PairSet], steps: int = 200, lr: float = 3
         b = min(batch, ps.n)
         j = int(rng.integers(ps.n - b + 1))          # a contiguous window of pairs: views, no copies
         loss = tpe.tp_gnn_train_step(ctx, ps.gamma, ps.R[j:j + b], ps.B[j:j + b], ps.AB[j:j + b],
-                                     ps.ER[j:j + b], lr)
+                                     ps.ER[j:j + b], lr, ILAM=ps.ILAM)
         losses.append(loss)
         if log_every and (it % log_every == 0 or it == steps - 1):
             print(f"step {it:5d}  loss {loss:.6f}", flush=True)
@@ -122,6 +124,6 @@ def evaluate_loss(ctx: tpe.Context, sets: list[PairSet], theta) -> float:
         if ps.n == 0:
             continue
         tpe.tp_gnn_bind(ctx, ps.gamma)
-        tot += tpe.tp_gnn_train_step(ctx, ps.gamma, ps.R, ps.B, ps.AB, ps.ER, 0.0) * ps.n
+        tot += tpe.tp_gnn_train_step(ctx, ps.gamma, ps.R, ps.B, ps.AB, ps.ER, 0.0, ILAM=ps.ILAM) * ps.n
         cnt += ps.n
     return tot / max(1, cnt)

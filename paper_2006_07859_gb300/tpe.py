@@ -30,7 +30,8 @@ EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp
             "tp_launch_count", "tp_pairs_per_pass", "tp_profile", "tp_profile_read", "tp_measure_peaks", "tp_energy_static",
             "tp_spectral_symbols", "tp_gnn_num_params", "tp_gnn_set_params", "tp_gnn_get_params", "tp_gnn_bind",
             "tp_gnn_forward", "tp_gnn_backward", "tp_gnn_adam", "tp_gnn_g_apply", "tp_gnn_out_grad", "tp_cg_harvest",
-            "tp_gnn_prepare_pairs", "tp_gnn_train_step", "tp_autotune", "tp_set_apply_variant"]
+            "tp_gnn_prepare_pairs", "tp_gnn_train_step", "tp_autotune", "tp_set_apply_variant",
+            "tp_set_energy_variant", "tp_last_solve"]
 
 
 class TpParams(ctypes.Structure):
@@ -113,10 +114,12 @@ def library() -> ctypes.CDLL:
         L.tp_gnn_g_apply.argtypes = [vp, vp, vp, i, vp]
         L.tp_gnn_out_grad.argtypes = [vp, vp, vp, vp, i, vp]
         L.tp_cg_harvest.argtypes = [vp, vp, vp, i, i, vp, vp, ctypes.POINTER(i), ctypes.POINTER(TpSolveInfo), vp]
-        L.tp_gnn_prepare_pairs.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp]
-        L.tp_gnn_train_step.argtypes = [vp, vp, i, vp, vp, vp, vp, ctypes.c_float, pdd, vp, vp]
+        L.tp_gnn_prepare_pairs.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp]
+        L.tp_gnn_train_step.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, ctypes.c_float, pdd, vp, vp]
         L.tp_autotune.argtypes = [vp, vp, vp, vp, vp]
         L.tp_set_apply_variant.argtypes = [vp, i]
+        L.tp_set_energy_variant.argtypes = [vp, i]
+        L.tp_last_solve.argtypes = [vp, vp, vp]
         _lib = L
     return _lib
 
@@ -337,11 +340,11 @@ def tp_gnn_bind(ctx: Context, gamma):
 
 
 def tp_gnn_forward(ctx: Context, features=None, out=None):
-    """Returns (features [nE, 8], outputs [nE, 2]) as float32 CUDA tensors."""
+    """Returns (features [nE, 8], outputs [nE, 3]: a, b, c) as float32 CUDA tensors."""
     import torch
     features = torch.empty((ctx.n_edges, TP_GNN_FEATURES), dtype=torch.float32, device="cuda") \
         if features is None else features
-    out = torch.empty((ctx.n_edges, 2), dtype=torch.float32, device="cuda") if out is None else out
+    out = torch.empty((ctx.n_edges, 3), dtype=torch.float32, device="cuda") if out is None else out
     ctx._check(library().tp_gnn_forward(ctx.handle, _fptr(features), _fptr(out), _stream()))
     return features, out
 
@@ -365,7 +368,7 @@ def tp_gnn_g_apply(ctx: Context, r, z=None, accumulate=False):
 
 def tp_gnn_out_grad(ctx: Context, r, gz, dout=None, accumulate=False):
     import torch
-    dout = torch.empty((ctx.n_edges, 2), dtype=torch.float32, device="cuda") if dout is None else dout
+    dout = torch.empty((ctx.n_edges, 3), dtype=torch.float32, device="cuda") if dout is None else dout
     ctx._check(library().tp_gnn_out_grad(ctx.handle, _ptr(r), _ptr(gz), _fptr(dout), 1 if accumulate else 0,
                                          _stream()))
     return dout
@@ -380,34 +383,51 @@ def tp_cg_harvest(ctx: Context, gamma, rhs, every: int, R, E):
     return n.value, {"iters": info.iters, "rel_res": info.rel_res, "converged": info.converged}
 
 
-def tp_gnn_prepare_pairs(ctx: Context, gamma, R, E, B, AB, ER):
-    """ER: CUDA float64 [n, n_problems]; B may be E (in place)."""
+def tp_gnn_prepare_pairs(ctx: Context, gamma, R, E, B, AB, ER, ILAM=None):
+    """ER: CUDA float64 [n, n_problems]; B may be E (in place); ILAM (CUDA float64 [nV] or None)
+    receives the curve's inverse circulant symbols and leaves the circulant to training."""
     ctx._check(library().tp_gnn_prepare_pairs(ctx.handle, _ptr(gamma), int(R.shape[0]), _ptr(R), _ptr(E), _ptr(B),
-                                              _ptr(AB), _ptr(ER), _stream()))
+                                              _ptr(AB), _ptr(ER), _ptr(ILAM), _stream()))
 
 
-def tp_gnn_train_step(ctx: Context, gamma, R, B, AB, ER, lr: float, grad=None) -> float:
+def tp_gnn_train_step(ctx: Context, gamma, R, B, AB, ER, lr: float, grad=None, ILAM=None) -> float:
     loss = ctypes.c_double()
     ctx._check(library().tp_gnn_train_step(ctx.handle, _ptr(gamma), int(R.shape[0]), _ptr(R), _ptr(B), _ptr(AB),
-                                           _ptr(ER), ctypes.c_float(lr), ctypes.byref(loss), _fptr(grad), _stream()))
+                                           _ptr(ER), _ptr(ILAM), ctypes.c_float(lr), ctypes.byref(loss), _fptr(grad),
+                                           _stream()))
     return loss.value
 
 
 def tp_autotune(ctx: Context, gamma) -> dict:
     """Pick the fastest targets-per-thread of each pair pass on `gamma` (mixed precision, alpha = 2,
     beta = 4.5); returns the choices and the measured ms per pass."""
-    t = (ctypes.c_int32 * 4)()
-    ms = (ctypes.c_double * 11)()
+    t = (ctypes.c_int32 * 5)()
+    ms = (ctypes.c_double * 13)()
     ctx._check(library().tp_autotune(ctx.handle, _ptr(gamma), t, ms, _stream()))
     names = ["energy", "diff", "apply"]
     out = {"tpt": {n: int(t[k]) for k, n in enumerate(names)},
            "ms": {n: {str(v): ms[3 * k + j] for j, v in enumerate((1, 2, 4)) if ms[3 * k + j] > 0}
                   for k, n in enumerate(names)}}
     out["tpt"]["apply_symmetric"] = int(t[3])
+    out["tpt"]["energy_symmetric"] = int(t[4])
     out["ms"]["apply_symmetric"] = {str(v): ms[9 + j] for j, v in enumerate((1, 2)) if ms[9 + j] > 0}
+    out["ms"]["energy_symmetric"] = {str(v): ms[11 + j] for j, v in enumerate((1, 2)) if ms[11 + j] > 0}
     return out
 
 
 def tp_set_apply_variant(ctx: Context, symmetric_tpt: int):
     """0: gather apply (every ordered pair); 1 or 2: symmetric apply with that many targets per thread."""
     ctx._check(library().tp_set_apply_variant(ctx.handle, int(symmetric_tpt)))
+
+
+def tp_set_energy_variant(ctx: Context, symmetric_tpt: int):
+    """0: gather energy pass (every ordered pair); 1 or 2: symmetric pass with that many targets per thread."""
+    ctx._check(library().tp_set_energy_variant(ctx.handle, int(symmetric_tpt)))
+
+
+def tp_last_solve(ctx: Context):
+    """(true relative residual, iterations) per problem of the context's last CG solve, as numpy arrays."""
+    rr = np.zeros(ctx.n_problems)
+    it = np.zeros(ctx.n_problems, dtype=np.int32)
+    ctx._check(library().tp_last_solve(ctx.handle, rr.ctypes.data, it.ctypes.data))
+    return rr, it

@@ -115,7 +115,8 @@ def test_g_apply_and_output_gradient(torch, orc, G):
 
 def test_training_step_gradient_matches_oracle(torch, orc, G):
     """Loss and parameter gradient of one training step (one harvested pair, FP64 pair kernels)
-    against the oracle's loss_and_grad with the dense Gram matrix."""
+    against the oracle's loss_and_grad with the dense Gram matrix: the learned rescaling of the
+    circulant (with the symbol the GPU set up), the G term and the prepared coarse term."""
     from paper_2006_07859_gb300 import tpe
     ctx, cs, gam, voff = setup(torch, orc, [120])
     x = cs[0]
@@ -132,13 +133,15 @@ def test_training_step_gradient_matches_oracle(torch, orc, G):
     Ecopy = E.clone()
     B, AB = torch.empty_like(R), torch.empty_like(R)
     ER = torch.empty((n, 1), dtype=torch.float64, device="cuda")
-    tpe.tp_gnn_prepare_pairs(ctx, g, R, E, B, AB, ER)
+    ILAM = torch.empty(gam.shape[0], dtype=torch.float64, device="cuda")
+    tpe.tp_gnn_prepare_pairs(ctx, g, R, E, B, AB, ER, ILAM)
     ctx.set_params(precond=tpe.TP_PRECOND_LEARNED)
     tpe.tp_gnn_set_params(ctx, torch.as_tensor(th).cuda())
     tpe.tp_gnn_bind(ctx, g)
     grad = torch.empty(tpe.tp_gnn_num_params(), dtype=torch.float32, device="cuda")
     k = 1
-    loss = tpe.tp_gnn_train_step(ctx, g, R[k:k + 1], B[k:k + 1], AB[k:k + 1], ER[k:k + 1], 0.0, grad=grad)
+    loss = tpe.tp_gnn_train_step(ctx, g, R[k:k + 1], B[k:k + 1], AB[k:k + 1], ER[k:k + 1], 0.0, grad=grad,
+                                 ILAM=ILAM)
     Bm, B0m = orc.gram_dense(x, e, SIG)
     A = Bm + B0m
     diag = np.diag(A).copy()
@@ -147,7 +150,8 @@ def test_training_step_gradient_matches_oracle(torch, orc, G):
     # prepared pairs are exactly consistent: r = A e, so e . r = ||e||_A^2 > 0 and the loss is >= 0
     assert rel(r, A @ ee) <= 1e-9
     assert abs(float((ee * r).sum()) - float(host(ER[k])[0])) <= 1e-12 * abs(float((ee * r).sum()))
-    L, gref = G.loss_and_grad(bf16_round(th), f, diag, A, r, ee, bz)
+    lam = 1.0 / host(ILAM)      # the circulant symbol the GPU set up for this curve
+    L, gref = G.loss_and_grad(bf16_round(th), f, diag, A, r, ee, bz, lam)
     assert L >= 0.0
     assert abs(loss - L) <= 1e-6 * max(1.0, abs(L))
     assert rel(host(grad), gref) <= 1e-3

@@ -73,3 +73,38 @@ def test_loss_is_the_best_scaled_a_norm_error(setup):
     assert 0.0 <= L <= 1.0
     assert vals.min() >= L - 1e-12
     assert vals.min() - L <= 1e-6
+
+
+def test_rescaled_spectral_gradient_matches_central_differences(setup, orc):
+    """The full learned preconditioner (rescaled circulant + G term + a fixed part): parameter gradient
+    of the loss against central differences, with the regular-polygon symbol as the circulant."""
+    c, A, diag, r, e, base_z = setup
+    n = c.n_vertices
+    lam = orc.ngon_symbol_closed_form(n, 0.75)
+    theta = gnn.init_params(6, out_bias=-1.0)
+    f = gnn.features(c.gamma, diag)
+    zc = 0.3 * base_z
+    L, g = gnn.loss_and_grad(theta, f, diag, A, r, e, zc, lam)
+    rng = np.random.default_rng(9)
+    o = sum(int(np.prod(s)) for name, s in gnn.SHAPES[:-2])   # start of W4
+    idx = np.concatenate([rng.choice(theta.size, 30, replace=False), o + 2 * gnn.H + np.arange(0, gnn.H, 8),
+                          [theta.size - 1]])                  # include the c row of W4 and its bias
+    h = 1e-6
+    for k in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (gnn.loss_and_grad(tp, f, diag, A, r, e, zc, lam)[0]
+              - gnn.loss_and_grad(tm, f, diag, A, r, e, zc, lam)[0]) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * max(1.0, abs(g).max()), (k, fd, g[k])
+
+
+def test_zero_log_scale_is_the_jacobi_scaled_circulant(setup, orc):
+    """With c = 0 the rescaled circulant is the plain D^-1/2 F^-1 diag(1/lambda) F D^-1/2 of the
+    spectral preconditioner (computed by the oracle's own routine)."""
+    c, A, diag, r, e, base_z = setup
+    n = c.n_vertices
+    lam = orc.ngon_symbol_closed_form(n, 0.75)
+    z = gnn.scaled_spectral(diag, np.zeros(n), lam, r)
+    ref = orc.spectral_preconditioner(diag, [0, n], {n: lam})(r)
+    assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max()
