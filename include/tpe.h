@@ -331,15 +331,15 @@ TPE_API tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, con
 /* Autotuner of the pair passes (not in the paper).  For TP_MIXED contexts with the specialised
  * powers ((alpha, beta) = (2, 4.5)) it times, on the curve gamma, every candidate number of target
  * edges per thread of the energy (1, 2, 4), differential (1, 2) and apply / diag (1, 2, 4) gather
- * passes, and the symmetric energy and apply passes (each unordered pair evaluated once, 1 or 2
+ * passes, and the symmetric energy, differential and apply passes (each unordered pair evaluated once, 1 or 2
  * targets per thread, when their partial sums fit in 16 GB), one warm-up and three timed passes each
  * (CUDA events on `stream`), and keeps the fastest, rebuilding that op's work queue; other contexts
  * keep their defaults and are left unchanged.
- *   tpt (HOST int32 [5], may be NULL): the chosen targets per thread of the energy, differential and
- *       apply gather passes, then of the symmetric apply and the symmetric energy (0: gather pass).
- *   ms  (HOST double [13], may be NULL): ms per pass for 1, 2, 4 targets per thread of the energy
- *       [0..2], differential [3..5] and apply [6..8] gather passes, then the symmetric apply with 1, 2
- *       [9..10] and the symmetric energy with 1, 2 [11..12] (0 where not a candidate).
+ *   tpt (HOST int32 [6], may be NULL): the chosen targets per thread of the energy, differential and
+ *       apply gather passes, then of the symmetric apply, energy and differential (0: gather pass).
+ *   ms  (HOST double [15], may be NULL): ms per pass for 1, 2, 4 targets per thread of the energy
+ *       [0..2], differential [3..5] and apply [6..8] gather passes, then the symmetric apply [9..10],
+ *       energy [11..12] and differential [13..14] with 1, 2 (0 where not a candidate).
  * May reallocate the context's partial-sum buffer (the only allocation after tp_create).
  * Synchronises the stream.  Errors: TP_ERR_INVALID_ARG, TP_ERR_CUDA, TP_ERR_DEGENERATE_EDGE. */
 TPE_API tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms, tp_stream stream);
@@ -353,6 +353,10 @@ TPE_API tp_status tp_set_apply_variant(tp_ctx *ctx, int symmetric_tpt);
 /* The same choice for the energy pass (0: gather, 1 or 2: symmetric; the rows E_I are the same
  * sums in another order). */
 TPE_API tp_status tp_set_energy_variant(tp_ctx *ctx, int symmetric_tpt);
+
+/* The same choice for the differential pass (0: gather, 1 or 2: symmetric; row J's terms of a pair
+ * are the mirror of row I's, near pairs are FP64 on both sides). */
+TPE_API tp_status tp_set_diff_variant(tp_ctx *ctx, int symmetric_tpt);
 
 /* Throughput microbenchmarks on the current device (no context needed): FP32 FMA FLOP/s, MUFU
  * rsqrt op/s and FP64 FMA FLOP/s.  Returns 0 on success. */

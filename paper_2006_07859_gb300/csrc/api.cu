@@ -247,6 +247,7 @@ void tp_destroy(tp_ctx *ctx)
     graphs_free(c);
     sym_select(c, 0);
     sym_select_energy(c, 0);
+    sym_select_diff(c, 0);
     if (c.sol) solver_free(c);
     spectral_free(c);
     coarse_free(c);
@@ -459,7 +460,7 @@ tp_status tp_set_params(tp_ctx *ctx, const tp_params *p)
     set_kernel_params(c);
     graphs_reset(c);  // captured CG blocks baked in the old kernel parameters
     c.setups_since_full = -1;  // the next preconditioner set-up is a full one
-    if (!c.kp.fast && (c.tpt[0] || c.tpt[1] || c.tpt[2] || c.apply_sym)) {
+    if (!c.kp.fast && (c.tpt[0] || c.tpt[1] || c.tpt[2] || c.apply_sym || c.energy_sym || c.diff_sym)) {
         // autotuned variants exist for the specialised powers only: back to the defaults
         for (int cls = 0; cls < 3; ++cls) {
             c.tpt[cls] = 0;
@@ -467,6 +468,7 @@ tp_status tp_set_params(tp_ctx *ctx, const tp_params *p)
         }
         CK(sym_select(c, 0));
         CK(sym_select_energy(c, 0));
+        CK(sym_select_diff(c, 0));
     }
     if ((p->precond >= TP_PRECOND_SPECTRAL) && !had_spectral) {
         cudaError_t e = spectral_setup(c, 0);
@@ -1038,6 +1040,17 @@ tp_status tp_last_solve(const tp_ctx *ctx, double *rel_res, int32_t *iters)
 
 // ---------------------------------------------------------------------------------- autotuner
 
+tp_status tp_set_diff_variant(tp_ctx *ctx, int symmetric_tpt)
+{
+    if (!ctx) return TP_ERR_INVALID_ARG;
+    Ctx &c = ctx->c;
+    if (symmetric_tpt < 0 || symmetric_tpt > 2) return fail(ctx, TP_ERR_INVALID_ARG, "symmetric_tpt must be 0, 1 or 2");
+    if (symmetric_tpt > 0 && !(c.prm.precision == TP_MIXED && c.kp.fast))
+        return fail(ctx, TP_ERR_UNSUPPORTED, "the symmetric differential exists for TP_MIXED with (alpha, beta) = (2, 4.5)");
+    CK(sym_select_diff(c, symmetric_tpt));
+    return TP_OK;
+}
+
 tp_status tp_set_energy_variant(tp_ctx *ctx, int symmetric_tpt)
 {
     if (!ctx) return TP_ERR_INVALID_ARG;
@@ -1068,8 +1081,8 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
     tp_status st = records(ctx, gamma, 0, s);
     if (st) return st;
     if (ms)
-        for (int k = 0; k < 13; ++k) ms[k] = 0.0;
-    if (tpt) tpt[3] = tpt[4] = 0;
+        for (int k = 0; k < 15; ++k) ms[k] = 0.0;
+    if (tpt) tpt[3] = tpt[4] = tpt[5] = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1110,6 +1123,29 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
             err = replan(c, cls);
         }
         if (tpt) tpt[cls] = nc > 1 ? best : cand[0];
+        // the differential also has the symmetric pass
+        if (cls == 1 && nc > 1 && err == cudaSuccess) {
+            int best_sym = 0;
+            for (int t = 1; t <= 2 && err == cudaSuccess; ++t) {
+                if (sym_slots(c, t) * (size_t)c.nE * 6 * sizeof(double) > ((size_t)16 << 30)) continue;
+                if ((err = sym_select_diff(c, t)) != cudaSuccess) break;
+                if ((err = run(cls)) != cudaSuccess) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run(cls);
+                cudaEventRecord(e1, s);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                float tm = 0.f;
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&tm, e0, e1);
+                tm /= 3.f;
+                if (ms) ms[13 + t - 1] = tm;
+                if (tm < best_ms) {
+                    best_ms = tm;
+                    best_sym = t;
+                }
+            }
+            if (err == cudaSuccess) err = sym_select_diff(c, best_sym);
+            if (tpt) tpt[5] = best_sym;
+        }
         // the energy also has the symmetric pass (its rows are one double per edge and slot)
         if (cls == 0 && nc > 1 && err == cudaSuccess) {
             int best_sym = 0;

@@ -826,10 +826,14 @@ cudaError_t pair_energy(Ctx &c, const double *gamma, int which, double *rows_out
 
 cudaError_t pair_diff(Ctx &c, const double *gamma, int which, double *dE, cudaStream_t s)
 {
-    TPE_CHECK(run_pairs<OP_DIFF>(c, which, gamma, nullptr, s));
+    const bool sym = c.diff_sym > 0;
+    if (sym)
+        TPE_CHECK(sym_diff_pass(c, which, gamma, s));
+    else
+        TPE_CHECK(run_pairs<OP_DIFF>(c, which, gamma, nullptr, s));
     if (c.nV > 0) {
-        k_vertex_gather<OP_DIFF><<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.nE, c.d_inc_ptr, c.d_inc, c.plan_diff.d_eslots,
-                                                                    c.d_part, dE);
+        k_vertex_gather<OP_DIFF><<<(c.nV + 255) / 256, 256, 0, s>>>(
+            c.nV, c.nE, c.d_inc_ptr, c.d_inc, sym ? c.plan_sym_d.d_eslots : c.plan_diff.d_eslots, c.d_part, dE);
         c.launches++;
     }
     return cudaGetLastError();

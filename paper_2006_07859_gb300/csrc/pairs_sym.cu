@@ -422,6 +422,326 @@ __global__ void __launch_bounds__(kThreads, 3) k_energy_sym(const PairArgs pa)
     }
 }
 
+// ---------------------------------------------------------------------------------- symmetric differential
+//
+// Row I accumulates (scaled by l_J) S = sum (f_I + f_J), G_a += v_ab, GT += -a_I (T_I . d_ab) d_ab, with
+// v_ab = d(f_I + f_J)/dd at d_ab = g_ia - g_jb.  Row J sees d' = -d and accumulates (scaled by l_I) the
+// same S, G_b -= v_ab (its endpoint b) and GT += -a_J (T_J . d_ab) d_ab.  Both tangents are double-float
+// in |T x d|^2 and T . d (each is the target tangent of one of the two rows).
+
+// source-side accumulator slots: 0 S, 1-3 G1, 4-6 G2, 7-9 GT
+constexpr int kDS = 10;
+
+template <bool FAST, bool DF>
+__device__ __forceinline__ void pair_diff_both(const Tgt<float> &t, const Src<PMIX> &s, bool keep,
+                                               const KernelParams &kp, Acc32<PMIX, OP_DIFF> &a,
+                                               float (&src)[kDS])
+{
+    const float alpha = (float)kp.alpha, beta = (float)kp.beta;
+    V3<float> dd[4];
+    chords<DF>(t, s, dd);
+    float tI[2], tJ[2], cI[2], cJ[2];
+    V3<float> dpI[2], dpJ[2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        cI[b] = perp2_df(dd[b], t.T, t.Tl, tI[b], dpI[b]);
+        cJ[b] = perp2_df(dd[2 * b], s.T, s.Tm, tJ[b], dpJ[b]);
+    }
+    float S = 0.f, G1[3] = {0, 0, 0}, G2[3] = {0, 0, 0}, GT[3] = {0, 0, 0};
+    float H1[3] = {0, 0, 0}, H2[3] = {0, 0, 0}, HT[3] = {0, 0, 0};
+#pragma unroll
+    for (int ab = 0; ab < 4; ++ab) {
+        const int ia = ab >> 1, jb = ab & 1;
+        const V3<float> d = dd[ab];
+        const float d2 = dot3(d, d);
+        float r2;
+        const float rb = inv_pow<float, FAST, 0>(d2, beta, r2);
+        float fI, fJ, aI, aJ;
+        if constexpr (FAST) {
+            fI = cI[jb] * rb;
+            fJ = cJ[ia] * rb;
+            aI = aJ = 2.f * rb;
+        } else {
+            fI = pow_c<float, false>(cI[jb], alpha) * rb;
+            fJ = pow_c<float, false>(cJ[ia], alpha) * rb;
+            aI = cI[jb] > 0.f ? alpha * fI / cI[jb] : 0.f;
+            aJ = cJ[ia] > 0.f ? alpha * fJ / cJ[ia] : 0.f;
+        }
+        const float fs = fI + fJ, cb = beta * fs * r2;
+        const float v[3] = {aI * dpI[jb].x + aJ * dpJ[ia].x - cb * d.x, aI * dpI[jb].y + aJ * dpJ[ia].y - cb * d.y,
+                            aI * dpI[jb].z + aJ * dpJ[ia].z - cb * d.z};
+        float *G = ia ? G2 : G1, *H = jb ? H2 : H1;
+        const float mI = -aI * (ia ? tI[jb] + t.ell : tI[jb]);
+        const float mJ = -aJ * (jb ? tJ[ia] - s.ell : tJ[ia]);
+        const float dv[3] = {d.x, d.y, d.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            G[k] += v[k];
+            H[k] -= v[k];
+            GT[k] += mI * dv[k];
+            HT[k] += mJ * dv[k];
+        }
+        S += fs;
+    }
+    const float L = keep ? s.ell : 0.f, Ls = keep ? t.ell : 0.f;
+    kahan_add(a.S, a.cS, keep ? L * S : 0.f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        kahan_add(a.G1[k], a.c1[k], keep ? L * G1[k] : 0.f);
+        kahan_add(a.G2[k], a.c2[k], keep ? L * G2[k] : 0.f);
+        kahan_add(a.GT[k], a.cT[k], keep ? L * GT[k] : 0.f);
+    }
+    if (keep) {
+        src[0] += Ls * S;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            src[1 + k] += Ls * H1[k];
+            src[4 + k] += Ls * H2[k];
+            src[7 + k] += Ls * HT[k];
+        }
+    }
+}
+
+// A near pair entirely in FP64 from the double-float positions and tangents: row I's terms into tgt,
+// row J's into src (both FP64).
+static __device__ __noinline__ void near_diff_both_df(const Tgt<float> &t, const Src<PMIX> &s, double alpha,
+                                                      double beta, bool fast, DiffAcc64 &tgt, double (&src)[kDS])
+{
+    const double TI[3] = {(double)t.T.x + t.Tl.x, (double)t.T.y + t.Tl.y, (double)t.T.z + t.Tl.z};
+    const double TJ[3] = {(double)s.T.x + s.Tm.x, (double)s.T.y + s.Tm.y, (double)s.T.z + s.Tm.z};
+    const double L = s.ell, Ls = t.ell;
+    for (int ab = 0; ab < 4; ++ab) {
+        const V3<float> P = (ab < 2) ? t.p1 : t.p2, PL = (ab < 2) ? t.l1 : t.l2;
+        const V3<float> Q = (ab & 1) ? s.q2 : s.q1, QL = (ab & 1) ? s.m2 : s.m1;
+        const double d[3] = {(double)(P.x - Q.x) + (double)(PL.x - QL.x), (double)(P.y - Q.y) + (double)(PL.y - QL.y),
+                             (double)(P.z - Q.z) + (double)(PL.z - QL.z)};
+        const double tI = TI[0] * d[0] + TI[1] * d[1] + TI[2] * d[2];
+        const double tJ = TJ[0] * d[0] + TJ[1] * d[1] + TJ[2] * d[2];
+        double dpI[3], dpJ[3];
+        for (int k = 0; k < 3; ++k) {
+            dpI[k] = d[k] - tI * TI[k];
+            dpJ[k] = d[k] - tJ * TJ[k];
+        }
+        const double cI2 = dpI[0] * dpI[0] + dpI[1] * dpI[1] + dpI[2] * dpI[2];
+        const double cJ2 = dpJ[0] * dpJ[0] + dpJ[1] * dpJ[1] + dpJ[2] * dpJ[2];
+        const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double rb, fI, fJ, aI, aJ;
+        if (fast) {
+            const double r = rsqrt(d2), r2 = r * r;
+            rb = r2 * r2 * sqrt(r);
+            fI = cI2 * rb;
+            fJ = cJ2 * rb;
+            aI = aJ = 2.0 * rb;
+        } else {
+            rb = pow(d2, -0.5 * beta);
+            fI = (cI2 > 0.0 ? pow(cI2, 0.5 * alpha) : 0.0) * rb;
+            fJ = (cJ2 > 0.0 ? pow(cJ2, 0.5 * alpha) : 0.0) * rb;
+            aI = cI2 > 0.0 ? alpha * fI / cI2 : 0.0;
+            aJ = cJ2 > 0.0 ? alpha * fJ / cJ2 : 0.0;
+        }
+        const double cb = beta * (fI + fJ) / d2;
+        double *G = ab < 2 ? tgt.G1 : tgt.G2;
+        const int hb = (ab & 1) ? 4 : 1;
+        for (int k = 0; k < 3; ++k) {
+            const double v = aI * dpI[k] + aJ * dpJ[k] - cb * d[k];
+            G[k] += L * v;
+            tgt.GT[k] += -L * aI * tI * d[k];
+            src[hb + k] -= Ls * v;
+            src[7 + k] += -Ls * aJ * tJ * d[k];
+        }
+        tgt.S += L * (fI + fJ);
+        src[0] += Ls * (fI + fJ);
+    }
+}
+
+// Row output of the differential from its accumulators (Sec. 5.1 by the chain rule through l_I and T_I):
+// G_i1 = (1/4)[-T S + l G1 - (Id - T T^t) GT],  G_i2 = (1/4)[T S + l G2 + (Id - T T^t) GT]
+__device__ __forceinline__ void diff_row_out(const double *T, double l, double S, const double *G1,
+                                             const double *G2, const double *GT, double *o)
+{
+    const double gt = T[0] * GT[0] + T[1] * GT[1] + T[2] * GT[2];
+    for (int c = 0; c < 3; ++c) {
+        const double pgt = GT[c] - gt * T[c];
+        o[c] = 0.25 * (-T[c] * S + l * G1[c] - pgt);
+        o[3 + c] = 0.25 * (T[c] * S + l * G2[c] + pgt);
+    }
+}
+
+// MODE 2: near pairs (|g_i1 - g_j1| inside the differential's FP64 band) possible; 1 / 0 as in the energy.
+template <int TPT, bool FAST, bool CHECK, int MODE, bool SRC>
+__device__ __forceinline__ void sym_diff_tile(const Tgt<float> (&tg)[TPT], const bool (&valid)[TPT],
+                                              const Tile<PMIX, false> &tl, int cnt, Acc32<PMIX, OP_DIFF> (&a)[TPT],
+                                              Acc64<OP_DIFF> (&A)[TPT], float *sacc, float *scmp,
+                                              const KernelParams &kp)
+{
+    const int lane = threadIdx.x & 31;
+    const int P = max(cnt, 32);
+    for (int step = 0; step < P; ++step) {
+        int j = step + lane;
+        if (j >= P) j -= P;
+        if (j < cnt) {
+            Src<PMIX> s;
+            load_source<PMIX, false>(s, tl, j);
+            float src[kDS];
+#pragma unroll
+            for (int q = 0; q < kDS; ++q) src[q] = 0.f;
+            double srcd[kDS];
+            bool anynear = false;
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                bool keep = valid[k];
+                if constexpr (CHECK)
+                    keep = keep & (s.j1 != tg[k].i1) & (s.j1 != tg[k].i2) & (s.j2 != tg[k].i1) & (s.j2 != tg[k].i2);
+                bool near = false;
+                if constexpr (MODE == 2) {
+                    const V3<float> e = diff3<true>(tg[k].p1, tg[k].l1, s.q1, s.m1);
+                    near = keep && dot3(e, e) < kp.near2f_diff;
+                }
+                if (near) {
+                    if (!anynear) {
+#pragma unroll
+                        for (int q = 0; q < kDS; ++q) srcd[q] = 0.0;
+                        anynear = true;
+                    }
+                    if constexpr (SRC)
+                        near_diff_both_df(tg[k], s, kp.alpha, kp.beta, FAST, A[k], srcd);
+                    else
+                        near_diff_df(tg[k], s, kp.alpha, kp.beta, FAST, A[k]);
+                } else {
+                    pair_diff_both<FAST, (MODE >= 1)>(tg[k], s, keep, kp, a[k], src);
+                }
+            }
+            if constexpr (SRC) {
+#pragma unroll
+                for (int q = 0; q < kDS; ++q) {
+                    float acc = sacc[q * kTile + j], cmp = scmp[q * kTile + j];
+                    if (anynear) {
+                        // FP64 near terms as hi + lo so the compensated sum keeps their digits
+                        const double tot = (double)src[q] + srcd[q];
+                        const float hi = (float)tot;
+                        kahan_add(acc, cmp, hi);
+                        kahan_add(acc, cmp, (float)(tot - (double)hi));
+                    } else {
+                        kahan_add(acc, cmp, src[q]);
+                    }
+                    sacc[q * kTile + j] = acc;
+                    scmp[q * kTile + j] = cmp;
+                }
+            }
+        }
+        if constexpr (SRC) __syncwarp();
+    }
+}
+
+constexpr size_t kDiffSymDynSmem = sizeof(float) * 2 * kSymWarps * kDS * kTile;
+
+template <int TPT, bool FAST>
+__global__ void __launch_bounds__(kThreads, 2) k_diff_sym(const PairArgs pa)
+{
+    __shared__ Tile<PMIX, false> tl;
+    __shared__ int s_item;
+    __shared__ float s_box[2][kThreads / 32][6];
+    extern __shared__ float dyn[];  // [kSymWarps][kDS][kTile] accumulators, then their compensations
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *sacc = dyn + (size_t)wid * kDS * kTile, *scmp = dyn + (size_t)(kSymWarps + wid) * kDS * kTile;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(pa.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= pa.n_items) break;
+        const WorkItem w = pa.items[it];
+        const int bslot = w.slot >> 16, cslot = w.slot & 0xffff;
+        const bool diag = bslot == cslot;
+        Tgt<float> tg[TPT];
+        bool valid[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            const int loc = threadIdx.x + k * kThreads;
+            valid[k] = loc < w.ntgt;
+            load_target<PMIX>(tg[k], w.tgt0 + min(loc, w.ntgt - 1), pa.recF, pa.recLo, pa.recD);
+        }
+        Acc64<OP_DIFF> A[TPT];
+        Acc32<PMIX, OP_DIFF> a[TPT];
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            acc64_zero<OP_DIFF>(A[k]);
+            acc_zero<PMIX, OP_DIFF>(a[k]);
+        }
+        float tbox[6];
+        {
+            float b[6] = {1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) box_add(b, tg[k].p1, tg[k].p2);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                for (int q = 0; q < 6; ++q) {
+                    const float v = __shfl_xor_sync(0xffffffffu, b[q], o);
+                    b[q] = q < 3 ? fminf(b[q], v) : fmaxf(b[q], v);
+                }
+            for (int q = 0; q < 6; ++q) tbox[q] = b[q];
+        }
+        for (int s0 = w.src0; s0 < w.src1; s0 += kTile) {
+            const int cnt = min(kTile, w.src1 - s0);
+            __syncthreads();
+            float sb[6] = {1e30f, 1e30f, 1e30f, -1e30f, -1e30f, -1e30f};
+            if (threadIdx.x < cnt) {
+                const int J = s0 + threadIdx.x;
+                const RecF r = pa.recF[J];
+                tl.r[threadIdx.x] = r;
+                tl.lo[threadIdx.x] = pa.recLo[J];
+                box_add(sb, V3<float>{r.a.x, r.a.y, r.a.z}, V3<float>{r.b.x, r.b.y, r.b.z});
+            }
+            for (int t = lane; t < kDS * kTile; t += 32) sacc[t] = scmp[t] = 0.f;
+            block_box(sb, s_box[1]);
+            const bool check = !(s0 + cnt - 1 < w.nb_lo || s0 > w.nb_hi);
+            float g2 = 0.f;
+            for (int q = 0; q < 3; ++q) {
+                const float gap = fmaxf(fmaxf(sb[q] - tbox[3 + q], tbox[q] - sb[3 + q]), 0.f);
+                g2 += gap * gap;
+            }
+            const int mode = g2 < pa.kp.near2f_diff ? 2 : (g2 < pa.kp.mid2f ? 1 : 0);
+            if (diag)
+                sym_diff_tile<TPT, FAST, true, 2, false>(tg, valid, tl, cnt, a, A, sacc, scmp, pa.kp);
+            else if (check || mode == 2)
+                sym_diff_tile<TPT, FAST, true, 2, true>(tg, valid, tl, cnt, a, A, sacc, scmp, pa.kp);
+            else if (mode == 1)
+                sym_diff_tile<TPT, FAST, false, 1, true>(tg, valid, tl, cnt, a, A, sacc, scmp, pa.kp);
+            else
+                sym_diff_tile<TPT, FAST, false, 0, true>(tg, valid, tl, cnt, a, A, sacc, scmp, pa.kp);
+#pragma unroll
+            for (int k = 0; k < TPT; ++k) {
+                acc_add(A[k], a[k]);
+                acc_zero<PMIX, OP_DIFF>(a[k]);
+            }
+            if (!diag) {
+                __syncthreads();
+                if (threadIdx.x < cnt) {
+                    const int J = s0 + threadIdx.x;
+                    double v[kDS];
+                    for (int q = 0; q < kDS; ++q) {
+                        double x = 0.0;
+                        for (int wv = 0; wv < kSymWarps; ++wv) {
+                            const float *ac = dyn + (size_t)wv * kDS * kTile, *cm = dyn + (size_t)(kSymWarps + wv) * kDS * kTile;
+                            x += (double)ac[q * kTile + threadIdx.x] - (double)cm[q * kTile + threadIdx.x];
+                        }
+                        v[q] = x;
+                    }
+                    diff_row_out(pa.na.T + 3 * J, pa.na.ell[J], v[0], v + 1, v + 4, v + 7,
+                                 pa.part + ((size_t)bslot * pa.nE + J) * 6);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) {
+            if (!valid[k]) continue;
+            const int I = w.tgt0 + threadIdx.x + k * kThreads;
+            diff_row_out(pa.na.T + 3 * I, pa.na.ell[I], A[k].S, A[k].G1, A[k].G2, A[k].GT,
+                         pa.part + ((size_t)cslot * pa.nE + I) * 6);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------- host side
 
 static int sym_occupancy(int tpt)
@@ -570,6 +890,69 @@ cudaError_t sym_energy_pass(Ctx &c, int which, const double *gamma, cudaStream_t
         k_energy_sym<1, true><<<pl.grid, kThreads, 0, s>>>(pa);
     else
         k_energy_sym<2, true><<<pl.grid, kThreads, 0, s>>>(pa);
+    if (slot >= 0 || slot <= -2) prof_end(c, slot, s);
+    c.launches++;
+    return cudaGetLastError();
+}
+
+static int sym_diff_occupancy(int tpt)
+{
+    int occ = 0;
+    if (tpt == 1) {
+        cudaFuncSetAttribute(k_diff_sym<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiffSymDynSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_diff_sym<1, true>, kThreads, kDiffSymDynSmem);
+    } else {
+        cudaFuncSetAttribute(k_diff_sym<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiffSymDynSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_diff_sym<2, true>, kThreads, kDiffSymDynSmem);
+    }
+    return occ;
+}
+
+// The differential's symmetric pass on (tpt 1, 2) or off (0); same conditions as sym_select.
+cudaError_t sym_select_diff(Ctx &c, int tpt)
+{
+    Ctx::Plan &pl = c.plan_sym_d;
+    if (pl.d_items) TPE_CHECK(cudaFree(pl.d_items));
+    if (pl.d_eslots) TPE_CHECK(cudaFree(pl.d_eslots));
+    pl = Ctx::Plan{};
+    c.diff_sym = 0;
+    if (tpt <= 0) return cudaSuccess;
+    if (c.prm.precision != TP_MIXED || !c.kp.fast || (tpt != 1 && tpt != 2)) return cudaErrorInvalidValue;
+    sym_plan_items(c, pl, tpt, sym_diff_occupancy(tpt));
+    const size_t need = (size_t)pl.max_slots * std::max(1, c.nE) * 6;
+    if (need > c.part_elems) {
+        TPE_CHECK(cudaFree(c.d_part));
+        TPE_CHECK(cudaMalloc(&c.d_part, sizeof(double) * need));
+        c.part_elems = need;
+    }
+    c.diff_sym = tpt;
+    return cudaGetLastError();
+}
+
+cudaError_t sym_diff_pass(Ctx &c, int which, const double *gamma, cudaStream_t s)
+{
+    Ctx::Plan &pl = c.plan_sym_d;
+    if (pl.n_items == 0) return cudaSuccess;
+    TPE_CHECK(cudaMemsetAsync(c.d_counter + 6, 0, sizeof(int), s));
+    PairArgs pa;
+    pa.items = pl.d_items;
+    pa.n_items = pl.n_items;
+    pa.counter = c.d_counter + 6;
+    pa.recF = which ? c.d_recF2 : c.d_recF;
+    pa.recLo = which ? c.d_recLo2 : c.d_recLo;
+    pa.recD = nullptr;
+    pa.urecF = nullptr;
+    pa.urecD = nullptr;
+    pa.na = NearArgs{gamma, c.d_edges, c.d_ellw[which], c.d_Tw[which], nullptr};
+    pa.part = c.d_part;
+    pa.nE = c.nE;
+    pa.kp = c.kp;
+    pa.skip = nullptr;
+    const int slot = c.profile ? prof_begin(c, OP_DIFF, s) : -1;
+    if (pl.tpt == 1)
+        k_diff_sym<1, true><<<pl.grid, kThreads, kDiffSymDynSmem, s>>>(pa);
+    else
+        k_diff_sym<2, true><<<pl.grid, kThreads, kDiffSymDynSmem, s>>>(pa);
     if (slot >= 0 || slot <= -2) prof_end(c, slot, s);
     c.launches++;
     return cudaGetLastError();

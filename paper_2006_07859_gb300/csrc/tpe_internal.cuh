@@ -125,6 +125,8 @@ struct Ctx {
     int apply_sym = 0;       // > 0: the apply runs the symmetric pass with this many targets per thread
     Plan plan_sym_e;         // symmetric energy (pairs_sym.cu)
     int energy_sym = 0;      // > 0: the energy runs the symmetric pass with this many targets per thread
+    Plan plan_sym_d;         // symmetric differential (pairs_sym.cu)
+    int diff_sym = 0;        // > 0: the differential runs the symmetric pass
     int *d_counter = nullptr;  // persistent-queue counters [8]
     // edge records
     RecF *d_recF = nullptr, *d_recF2 = nullptr;
@@ -208,6 +210,8 @@ cudaError_t sym_apply_pass(Ctx &c, int which, const double *gamma, const double 
 size_t sym_slots(const Ctx &c, int tpt);
 cudaError_t sym_select_energy(Ctx &c, int tpt);
 cudaError_t sym_energy_pass(Ctx &c, int which, const double *gamma, cudaStream_t s);
+cudaError_t sym_select_diff(Ctx &c, int tpt);
+cudaError_t sym_diff_pass(Ctx &c, int which, const double *gamma, cudaStream_t s);
 void make_plans(Ctx &c);
 cudaError_t replan(Ctx &c, int cls);  // rebuild the plan of one op class (0 energy, 1 diff, 2 apply/diag)
 int tpt_default(const Ctx &c, int cls);

@@ -31,7 +31,7 @@ EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp
             "tp_spectral_symbols", "tp_gnn_num_params", "tp_gnn_set_params", "tp_gnn_get_params", "tp_gnn_bind",
             "tp_gnn_forward", "tp_gnn_backward", "tp_gnn_adam", "tp_gnn_g_apply", "tp_gnn_out_grad", "tp_cg_harvest",
             "tp_gnn_prepare_pairs", "tp_gnn_train_step", "tp_autotune", "tp_set_apply_variant",
-            "tp_set_energy_variant", "tp_last_solve"]
+            "tp_set_energy_variant", "tp_last_solve", "tp_set_diff_variant"]
 
 
 class TpParams(ctypes.Structure):
@@ -120,6 +120,7 @@ def library() -> ctypes.CDLL:
         L.tp_set_apply_variant.argtypes = [vp, i]
         L.tp_set_energy_variant.argtypes = [vp, i]
         L.tp_last_solve.argtypes = [vp, vp, vp]
+        L.tp_set_diff_variant.argtypes = [vp, i]
         _lib = L
     return _lib
 
@@ -401,8 +402,8 @@ def tp_gnn_train_step(ctx: Context, gamma, R, B, AB, ER, lr: float, grad=None, I
 def tp_autotune(ctx: Context, gamma) -> dict:
     """Pick the fastest targets-per-thread of each pair pass on `gamma` (mixed precision, alpha = 2,
     beta = 4.5); returns the choices and the measured ms per pass."""
-    t = (ctypes.c_int32 * 5)()
-    ms = (ctypes.c_double * 13)()
+    t = (ctypes.c_int32 * 6)()
+    ms = (ctypes.c_double * 15)()
     ctx._check(library().tp_autotune(ctx.handle, _ptr(gamma), t, ms, _stream()))
     names = ["energy", "diff", "apply"]
     out = {"tpt": {n: int(t[k]) for k, n in enumerate(names)},
@@ -412,6 +413,8 @@ def tp_autotune(ctx: Context, gamma) -> dict:
     out["tpt"]["energy_symmetric"] = int(t[4])
     out["ms"]["apply_symmetric"] = {str(v): ms[9 + j] for j, v in enumerate((1, 2)) if ms[9 + j] > 0}
     out["ms"]["energy_symmetric"] = {str(v): ms[11 + j] for j, v in enumerate((1, 2)) if ms[11 + j] > 0}
+    out["tpt"]["diff_symmetric"] = int(t[5])
+    out["ms"]["diff_symmetric"] = {str(v): ms[13 + j] for j, v in enumerate((1, 2)) if ms[13 + j] > 0}
     return out
 
 
@@ -431,3 +434,8 @@ def tp_last_solve(ctx: Context):
     it = np.zeros(ctx.n_problems, dtype=np.int32)
     ctx._check(library().tp_last_solve(ctx.handle, rr.ctypes.data, it.ctypes.data))
     return rr, it
+
+
+def tp_set_diff_variant(ctx: Context, symmetric_tpt: int):
+    """0: gather differential (every ordered pair); 1 or 2: symmetric pass with that many targets per thread."""
+    ctx._check(library().tp_set_diff_variant(ctx.handle, int(symmetric_tpt)))

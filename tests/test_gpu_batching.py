@@ -138,3 +138,35 @@ def test_symmetric_energy_matches_gather_and_oracle(torch, orc, tpt, case):
     idx = np.sort(np.random.default_rng(13).choice(c.n_edges, 48, replace=False)).astype(np.int32)
     if case != "batch":
         assert rel(host(rows_s)[idx], orc.energy_rows(c.gamma, c.edges, idx)) <= 1e-6
+
+
+@pytest.mark.parametrize("tpt", [1, 2])
+@pytest.mark.parametrize("case", ["single_ragged", "batch", "near"])
+def test_symmetric_differential_matches_gather_and_oracle(torch, orc, tpt, case):
+    """The symmetric differential (row J's terms of a pair mirrored from row I's; near pairs FP64 on both
+    sides) against the gather pass and the oracle; translation invariance sum_v dE_v = 0 per curve."""
+    from paper_2006_07859_gb300 import tpe
+    if case == "single_ragged":
+        c = S.single(S.fourier_knot(1000, 8, 9))
+    elif case == "near":
+        c = S.single(S.fourier_knot(3000, 16, 4))
+    else:
+        c = _batch()
+    indep = 1 if case == "batch" else 0
+    ctx = make_ctx(c, precision=tpe.TP_MIXED, precond=1, independent=indep)
+    g = dev(c.gamma)
+    dE_g = host(tpe.tp_differential(ctx, g))
+    tpe.tp_set_diff_variant(ctx, tpt)
+    dE_s = host(tpe.tp_differential(ctx, g))
+    dE_s2 = host(tpe.tp_differential(ctx, g))
+    assert np.array_equal(dE_s, dE_s2)
+    assert rel(dE_s, dE_g) <= 1e-5
+    assert cosine(dE_s, dE_g) >= 1 - 1e-10
+    for k in range(min(4, len(c.vertex_offsets) - 1)):
+        v0, v1 = c.vertex_offsets[k], c.vertex_offsets[k + 1]
+        assert np.abs(dE_s[v0:v1].sum(0)).max() <= 1e-4 * np.abs(dE_s[v0:v1]).max()
+    if case != "batch":
+        idx = np.sort(np.random.default_rng(14).choice(c.n_vertices, 32, replace=False)).astype(np.int32)
+        ref = orc.differential_at(c.gamma, c.edges, idx)
+        assert cosine(dE_s[idx], ref) >= 0.9999
+        assert rel(dE_s[idx], ref) <= 1e-5
