@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--workload", choices=["knots8x4096", "scene8x4096", "knot262144"], default="knots8x4096")
     ap.add_argument("--cg-rtol", type=float, default=None)
     ap.add_argument("--cg-maxit", type=int, default=None)
-    ap.add_argument("--precond-refresh", type=int, default=1,
+    ap.add_argument("--precond-refresh", type=int, default=4,
                     help="rebuild the fitted symbols and coarse space every k-th solve set-up")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
