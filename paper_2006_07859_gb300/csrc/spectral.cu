@@ -17,6 +17,7 @@
 //   n a power of two <= 8192 : radix-2 FFT in shared memory
 //   other n <= 4096          : Bluestein (chirp-z) through a power-of-two FFT of size >= 2n - 1
 //   n a power of two > 8192  : four-step FFT, n = N1 N2, batched shared-memory FFTs of N1 and N2
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -52,8 +53,9 @@ constexpr int kMaxRQ = 24;  // sampled frequencies per curve for the Rayleigh-qu
 struct tpe::SpecState {
     std::vector<SpecCurve> curves;
     SpecCurve *d_curves = nullptr;
-    std::vector<int> small_idx, large_idx;  // curve indices per path
+    std::vector<int> small_idx, large_idx, cluster_idx;  // curve indices per path
     int *d_small_idx = nullptr;
+    int *d_cluster_idx = nullptr;
     int max_small_M = 0;
     double *d_sym = nullptr;     // normalised symbols
     double2 *d_tw = nullptr;     // exp(-2 pi i k / kMaxFFT), k < kMaxFFT / 2
@@ -188,6 +190,93 @@ __global__ void __launch_bounds__(kFFTThreads) k_spec_small(const SpecCurve *__r
         bluestein(sa, n, C.M, C.logM, ch, bh, tw);
         for (int m = threadIdx.x; m < n; m += blockDim.x) z[3 * (C.v0 + m) + comp] = sa[m].x / n * dinv[C.v0 + m];
     }
+}
+
+// Powers of two 1024 <= n <= 8192: one transform per cluster of 8 CTAs (four-step with n = 8 N2 through
+// distributed shared memory), so that the FP64 work of a few curves spreads over many SMs.
+namespace cg = cooperative_groups;
+constexpr int kClusterFFT = 8;                       // CTAs per transform (portable cluster size)
+constexpr int kClusterMaxN2 = kMaxFFT / kClusterFFT;  // 1024
+constexpr int kClusterThreads = 256;
+constexpr int kClusterMinN = 1024;
+
+// exp(-/+ 2 pi i j / kMaxFFT) for j in [0, kMaxFFT) from the half table
+__device__ __forceinline__ double2 twiddle_full(const double2 *__restrict__ tw, int j, bool inv)
+{
+    double2 w = j < kMaxFFT / 2 ? tw[j] : make_double2(-tw[j - kMaxFFT / 2].x, -tw[j - kMaxFFT / 2].y);
+    if (inv) w.y = -w.y;
+    return w;
+}
+
+// z = D^-1/2 F^-1 diag(ilam) F D^-1/2 r for one (curve, component) per cluster.  Index m = m1 + 8 m2,
+// k = k2 + N2 k1.  Rank m1 transforms its column over m2 and twists by W_n^{m1 k2}; rank q then owns
+// rows k2 in [q N2/8, (q+1) N2/8): an 8-point DFT over m1 gathered from the cluster, the division by the
+// symbol, the 8-point inverse DFT over k1 and the twist W_n^{-m1 k2}; finally rank m1 gathers row m1 of
+// every k2 and transforms back over k2.
+__global__ void __cluster_dims__(kClusterFFT, 1, 1) __launch_bounds__(kClusterThreads)
+    k_spec_cluster(const SpecCurve *__restrict__ curves, const int *__restrict__ idx, const double *__restrict__ r,
+                   double *__restrict__ z, const double *__restrict__ dinv, const double2 *__restrict__ tw,
+                   const double *__restrict__ ilam, const int *__restrict__ skip, int indep)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int tr = blockIdx.x / kClusterFFT;
+    const int cidx = idx[tr / 3], comp = tr % 3;
+    if (skip && skip[indep ? cidx : 0]) return;  // converged problem: the whole cluster leaves
+    const SpecCurve C = curves[cidx];
+    const int n = C.n, N2 = n / kClusterFFT, logN2 = C.logM - 3, per = N2 / kClusterFFT;
+    const int sN = kMaxFFT / n, s8 = kMaxFFT / kClusterFFT;
+    __shared__ double2 Y[kClusterMaxN2];
+    __shared__ double2 V[kClusterMaxN2];
+    for (int m2 = threadIdx.x; m2 < N2; m2 += blockDim.x) {
+        const int v = C.v0 + rank + kClusterFFT * m2;
+        Y[m2] = make_double2(r[3 * v + comp] * dinv[v], 0.0);
+    }
+    __syncthreads();
+    fft_batch(Y, 1, N2, logN2, tw, false);
+    for (int k2 = threadIdx.x; k2 < N2; k2 += blockDim.x)
+        Y[k2] = cmul(Y[k2], twiddle_full(tw, ((rank * k2) % n) * sN, false));
+    cl.sync();
+    for (int t = threadIdx.x; t < per; t += blockDim.x) {
+        const int k2 = rank * per + t;
+        double2 a[kClusterFFT], X[kClusterFFT];
+#pragma unroll
+        for (int m1 = 0; m1 < kClusterFFT; ++m1) a[m1] = cl.map_shared_rank(Y, m1)[k2];
+#pragma unroll
+        for (int k1 = 0; k1 < kClusterFFT; ++k1) {
+            double2 sacc = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int m1 = 0; m1 < kClusterFFT; ++m1) {
+                const double2 p = cmul(a[m1], twiddle_full(tw, ((m1 * k1) % kClusterFFT) * s8, false));
+                sacc.x += p.x;
+                sacc.y += p.y;
+            }
+            const double f = ilam[C.v0 + k2 + N2 * k1];
+            X[k1] = make_double2(sacc.x * f, sacc.y * f);
+        }
+#pragma unroll
+        for (int m1 = 0; m1 < kClusterFFT; ++m1) {
+            double2 sacc = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int k1 = 0; k1 < kClusterFFT; ++k1) {
+                const double2 p = cmul(X[k1], twiddle_full(tw, ((m1 * k1) % kClusterFFT) * s8, true));
+                sacc.x += p.x;
+                sacc.y += p.y;
+            }
+            V[t * kClusterFFT + m1] = cmul(sacc, twiddle_full(tw, ((m1 * k2) % n) * sN, true));
+        }
+    }
+    cl.sync();  // every rank's V is complete; nobody reads Y any more
+    for (int k2 = threadIdx.x; k2 < N2; k2 += blockDim.x)
+        Y[k2] = cl.map_shared_rank(V, k2 / per)[(k2 % per) * kClusterFFT + rank];
+    __syncthreads();
+    fft_batch(Y, 1, N2, logN2, tw, true);
+    const double sc = 1.0 / n;
+    for (int m2 = threadIdx.x; m2 < N2; m2 += blockDim.x) {
+        const int v = C.v0 + rank + kClusterFFT * m2;
+        z[3 * v + comp] = Y[m2].x * sc * dinv[v];
+    }
+    cl.sync();  // the other ranks may still read this rank's V
 }
 
 // Four-step pieces for n = N1 N2 (powers of two): index m = m1 + N1 m2, k = k2 + N2 k1.
@@ -486,6 +575,8 @@ cudaError_t spectral_setup(Ctx &c, cudaStream_t s)
         S.curves.push_back(C);
         if (C.kind == SK_FOURSTEP)
             S.large_idx.push_back(k);
+        else if (C.kind == SK_POW2 && n >= kClusterMinN)
+            S.cluster_idx.push_back(k);
         else {
             S.small_idx.push_back(k);
             S.max_small_M = std::max(S.max_small_M, C.M);
@@ -493,6 +584,10 @@ cudaError_t spectral_setup(Ctx &c, cudaStream_t s)
     }
     TPE_CHECK(cudaMalloc(&S.d_curves, sizeof(SpecCurve) * S.curves.size()));
     TPE_CHECK(cudaMemcpy(S.d_curves, S.curves.data(), sizeof(SpecCurve) * S.curves.size(), cudaMemcpyHostToDevice));
+    TPE_CHECK(cudaMalloc(&S.d_cluster_idx, sizeof(int) * std::max<size_t>(1, S.cluster_idx.size())));
+    if (!S.cluster_idx.empty())
+        TPE_CHECK(cudaMemcpy(S.d_cluster_idx, S.cluster_idx.data(), sizeof(int) * S.cluster_idx.size(),
+                             cudaMemcpyHostToDevice));
     TPE_CHECK(cudaMalloc(&S.d_small_idx, sizeof(int) * std::max<size_t>(1, S.small_idx.size())));
     if (!S.small_idx.empty())
         TPE_CHECK(cudaMemcpy(S.d_small_idx, S.small_idx.data(), sizeof(int) * S.small_idx.size(),
@@ -541,7 +636,7 @@ void spectral_free(Ctx &c)
     if (!c.spec) return;
     SpecState &S = *c.spec;
     void *p[] = {S.d_curves, S.d_small_idx, S.d_sym, S.d_tw, S.d_chirp, S.d_bhat, S.d_buf0, S.d_buf1, S.d_dinv,
-                 S.d_sym_rq, S.d_klist, S.d_rq, S.d_vcurve, S.d_ilam};
+                 S.d_sym_rq, S.d_klist, S.d_rq, S.d_vcurve, S.d_ilam, S.d_cluster_idx};
     for (void *q : p)
         if (q) cudaFree(q);
     delete c.spec;
@@ -578,6 +673,11 @@ cudaError_t spectral_apply_ex(Ctx &c, const double *r, double *z, cudaStream_t s
     SpecState &S = *c.spec;
     k_dinv<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, diag, vlog, S.d_dinv);
     c.launches++;
+    if (!S.cluster_idx.empty()) {
+        k_spec_cluster<<<(int)S.cluster_idx.size() * 3 * kClusterFFT, kClusterThreads, 0, s>>>(
+            S.d_curves, S.d_cluster_idx, r, z, S.d_dinv, S.d_tw, ilam, skip, c.independent);
+        c.launches++;
+    }
     if (!S.small_idx.empty()) {
         int M = S.max_small_M;
         k_spec_small<<<(int)S.small_idx.size() * 3, kFFTThreads, sizeof(double2) * M, s>>>(

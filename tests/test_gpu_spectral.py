@@ -190,3 +190,35 @@ def test_twolevel_cuts_iterations(torch):
         assert info["converged"]
         its[pc] = info["iters"]
     assert its[4] < 0.6 * its[3], its
+
+
+@pytest.mark.parametrize("n", [1024, 2048, 4096, 8192])
+def test_cluster_fft_on_regular_polygon(torch, orc, n):
+    """Powers of two 1024 .. 8192 run one transform per cluster of 8 CTAs (four-step through
+    distributed shared memory).  On a regular polygon M^-1 r = IDFT(DFT(r) / lambda) / A_00."""
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.regular_polygon(n, 1.0))
+    ctx = make_ctx(c, precision=2, precond=2)
+    r = np.random.default_rng(6).normal(size=(n, 3))
+    z = host(tpe.tp_precond_apply(ctx, dev(c.gamma), dev(r)))
+    lam_raw = orc.ngon_symbol_closed_form(n, SIG, normalized=False)
+    a00 = lam_raw.mean()
+    lam = lam_raw / a00
+    lam[0] = lam[1]
+    zo = np.real(np.fft.ifft(np.fft.fft(r, axis=0) / lam[:, None], axis=0)) / a00
+    assert rel(z, zo) <= 1e-4
+
+
+def test_cluster_fft_in_a_mixed_batch(torch, orc):
+    """A batch whose curves take the cluster path (1024), the Bluestein path (300) and the one-CTA
+    power-of-two path (64) in one apply, against the oracle's spectral preconditioner."""
+    from paper_2006_07859_gb300 import tpe
+    c = S.batch_of_knots([1024, 300, 64], 6, 910)
+    ctx = make_ctx(c, precision=2, precond=2, independent=1)
+    r = np.random.default_rng(7).normal(size=(c.n_vertices, 3))
+    z = host(tpe.tp_precond_apply(ctx, dev(c.gamma), dev(r)))
+    diag = np.concatenate([orc.gram_diagonal(*c.curve(k), SIG) for k in range(c.n_curves)])
+    sizes = np.diff(c.vertex_offsets)
+    syms = {int(n): orc.ngon_symbol_closed_form(int(n), SIG) for n in set(sizes)}
+    zo = orc.spectral_preconditioner(diag, c.vertex_offsets, syms)(r)
+    assert rel(z, zo) <= 1e-4
