@@ -6,7 +6,8 @@ the CUDA library.  The pair sums live in ``tpe_oracle.c`` (literal loops, FP64);
 file adds the linear algebra on top of them with numpy, one library primitive per step
 (a dense solve, an FFT), in the order the paper states it:
 
-  * constraints Phi and their Jacobian C ........... Sec. 8.1 (barycenter, total length)
+  * constraints Phi and their Jacobian C ........... Sec. 8.1 (barycenter; total length or
+                                                     every edge length)
   * gradient saddle-point problem .................. Sec. 5.3.1, Eq. 22 (dense solve)
   * projected system P^T A P y = P^T a, x = P y .... App. B.3.3 (solved by CG)
   * constraint projection via z = C^+ b, x = z - y . Sec. 5.3.2 Eq. 23, App. B.3.4
@@ -35,6 +36,7 @@ import math
 import os
 import subprocess
 from dataclasses import dataclass, field
+from typing import Optional
 
 import numpy as np
 
@@ -199,16 +201,23 @@ def bilinear(gamma, edges, sigma, u, v):
 
 @dataclass
 class ConstraintGroup:
-    """Barycenter and total-length constraints (Sec. 8.1) over the edges [e0, e1)."""
+    """Constraints of Sec. 8.1 over the edges [e0, e1): the barycenter (3 rows) and either the total
+    length (1 row) or, when l0 is given, one edge-length row per edge (Phi_I = l0_I - l_I).  The
+    total-length row is the sum of the edge-length rows, so the two are never combined."""
     e0: int
     e1: int
     x0: np.ndarray
     L0: float
+    l0: Optional[np.ndarray] = None
+
+    @property
+    def n_rows(self) -> int:
+        return 4 if self.l0 is None else 3 + (self.e1 - self.e0)
 
 
-def constraint_groups(gamma, edges, edge_offsets=None):
-    """x0 and L0 fixed at their values on the given curve; one group per curve if
-    edge_offsets is given, else one group for the whole graph."""
+def constraint_groups(gamma, edges, edge_offsets=None, edge_lengths=False):
+    """x0, L0 (and, with edge_lengths, every l0_I) fixed at their values on the given curve; one
+    group per curve if edge_offsets is given, else one group for the whole graph."""
     ell, T, x = edge_quantities(gamma, edges)
     offs = [0, len(edges)] if edge_offsets is None else list(edge_offsets)
     groups = []
@@ -216,38 +225,45 @@ def constraint_groups(gamma, edges, edge_offsets=None):
         e0, e1 = offs[c], offs[c + 1]
         L = ell[e0:e1].sum()
         x0 = (ell[e0:e1, None] * x[e0:e1]).sum(0) / L
-        groups.append(ConstraintGroup(e0, e1, x0, L))
+        groups.append(ConstraintGroup(e0, e1, x0, L, ell[e0:e1].copy() if edge_lengths else None))
     return groups
 
 
 def phi(gamma, edges, groups):
-    """Phi_barycenter = sum_I l_I (x_I - x0) (3 rows), Phi_length = L0 - sum_I l_I (1 row), per group."""
+    """Per group: Phi_barycenter = sum_I l_I (x_I - x0) (3 rows), then Phi_length = L0 - sum_I l_I
+    (1 row) or Phi_length,I = l0_I - l_I (one row per edge, in edge order)."""
     ell, T, x = edge_quantities(gamma, edges)
     out = []
     for gr in groups:
         s = slice(gr.e0, gr.e1)
         out.extend(list((ell[s, None] * (x[s] - gr.x0)).sum(0)))
-        out.append(gr.L0 - ell[s].sum())
+        if gr.l0 is None:
+            out.append(gr.L0 - ell[s].sum())
+        else:
+            out.extend(list(gr.l0 - ell[s]))
     return np.array(out)
 
 
 def jacobian(gamma, edges, groups):
-    """C = d Phi, shape [4 * groups, nV, 3] (vertex-major columns).
+    """C = d Phi, shape [total rows, nV, 3] (vertex-major columns), rows in the order of phi.
     d l_I / d g_i2 = T_I = -d l_I / d g_i1 and d x_I / d g_ia = Id / 2."""
     g, e = _geom(gamma, edges)
     ell, T, x = edge_quantities(g, e)
-    C = np.zeros((4 * len(groups), g.shape[0], 3))
-    for q, gr in enumerate(groups):
+    C = np.zeros((sum(gr.n_rows for gr in groups), g.shape[0], 3))
+    r0 = 0
+    for gr in groups:
         for I in range(gr.e0, gr.e1):
             i1, i2 = e[I]
             for k in range(3):
-                r = 4 * q + k
+                r = r0 + k
                 C[r, i2] += T[I] * (x[I, k] - gr.x0[k])
                 C[r, i1] -= T[I] * (x[I, k] - gr.x0[k])
                 C[r, i1, k] += 0.5 * ell[I]
                 C[r, i2, k] += 0.5 * ell[I]
-            C[4 * q + 3, i2] -= T[I]
-            C[4 * q + 3, i1] += T[I]
+            r = r0 + 3 + (0 if gr.l0 is None else I - gr.e0)
+            C[r, i2] -= T[I]
+            C[r, i1] += T[I]
+        r0 += gr.n_rows
     return C
 
 

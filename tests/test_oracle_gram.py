@@ -215,3 +215,77 @@ def test_rq_symbol_is_exact_on_regular_polygon(orc):
         B, B0 = orc.gram_dense(g, S.closed_edges(n), SIG)
         np.testing.assert_allclose(orc.spectral_rq_symbol(B + B0, n, SIG), orc.ngon_symbol_closed_form(n, SIG),
                                    rtol=1e-10)
+
+
+def test_edge_length_jacobian_matches_differences(orc):
+    """Edge-length rows (Sec. 8.1, Phi_I = l0_I - l_I) against central differences of phi: pins the
+    sign and the endpoint of every row."""
+    c = S.single(S.trefoil(16, 0.01, 5))
+    g, e = c.gamma, c.edges
+    gr = orc.constraint_groups(g, e, edge_lengths=True)
+    assert gr[0].n_rows == 3 + 16
+    assert np.abs(orc.phi(g, e, gr)).max() <= 1e-13
+    C = orc.jacobian(g, e, gr)
+    h = 1e-6
+    J = np.zeros_like(C)
+    for v in range(16):
+        for k in range(3):
+            gp, gm = g.copy(), g.copy()
+            gp[v, k] += h
+            gm[v, k] -= h
+            J[:, v, k] = (orc.phi(gp, e, gr) - orc.phi(gm, e, gr)) / (2 * h)
+    assert np.abs(J - C).max() <= 1e-8
+
+
+def test_edge_length_rows_annihilate_rigid_motions(orc):
+    """Every edge length is invariant under rigid motions, so the edge rows vanish on translations
+    and on infinitesimal rotations v = w x gamma; a radial scaling is not isometric."""
+    c = S.single(S.trefoil(24, 0.01, 6))
+    g, e = c.gamma, c.edges
+    gr = orc.constraint_groups(g, e, edge_lengths=True)
+    C = orc.jacobian(g, e, gr)[3:].reshape(24, -1)
+    w = np.array([0.3, -1.1, 0.7])
+    for v in (np.tile([1.0, 2.0, -0.5], (24, 1)), np.cross(w, g)):
+        assert np.abs(C @ v.reshape(-1)).max() <= 1e-13 * np.abs(v).max()
+    ell = orc.edge_quantities(g, e)[0]
+    # d/dt (l0 - l(g + t g)) = -l, row by row
+    np.testing.assert_allclose(C @ g.reshape(-1), -ell, rtol=1e-12)
+
+
+def test_edge_length_gradient_kkt_vs_projected_cg(orc):
+    """With barycenter + edge-length rows the projected CG solution matches the dense KKT solve; the
+    gradient is tangent to every constraint (C g = 0), and the projected operator has exactly one
+    zero eigenvalue per constraint row."""
+    n = 40
+    c = S.single(S.trefoil(n, 0.01, 7))
+    g, e = c.gamma, c.edges
+    gr = orc.constraint_groups(g, e, edge_lengths=True)
+    dE = orc.differential(g, e)
+    prm = orc.Params(cg_tol=1e-12)
+    gk, lam = orc.sobolev_gradient(g, e, gr, dE, prm, dense=True)
+    gc, res = orc.sobolev_gradient(g, e, gr, dE, prm)
+    assert res.converged
+    assert np.abs(gk - gc).max() <= 1e-8 * np.abs(gk).max()
+    C = orc.jacobian(g, e, gr).reshape(3 + n, -1)
+    assert np.abs(C @ gk.reshape(-1)).max() <= 1e-12 * np.abs(gk).max()
+    B, B0 = orc.gram_dense(g, e, prm.sigma)
+    Ab = np.kron(B + B0, np.eye(3))
+    P = np.eye(3 * n) - C.T @ np.linalg.solve(C @ C.T, C)
+    ev = np.linalg.eigvalsh(P @ Ab @ P)
+    assert np.sum(np.abs(ev) <= 1e-10 * ev[-1]) == 3 + n
+    # the edge-length set is stricter than the total length: its gradient differs
+    g4, _ = orc.sobolev_gradient(g, e, orc.constraint_groups(g, e), dE, prm, dense=True)
+    assert np.abs(g4 - gk).max() >= 1e-3 * np.abs(gk).max()
+
+
+def test_edge_length_descent_step_keeps_every_edge_length(orc):
+    c = S.single(S.trefoil(36, 0.01, 8))
+    g, e = c.gamma, c.edges
+    gr = orc.constraint_groups(g, e, edge_lengths=True)
+    prm = orc.Params()
+    g1, info = orc.descent_step(g, e, gr, prm)
+    assert info.accepted and info.E_after < info.E_before
+    ell0 = orc.edge_quantities(g, e)[0]
+    ell1 = orc.edge_quantities(g1, e)[0]
+    assert np.abs(ell1 - ell0).max() <= prm.proj_tol * max(1.0, gr[0].L0)
+    assert np.abs(orc.phi(g1, e, gr)).max() <= prm.proj_tol * max(1.0, gr[0].L0)
