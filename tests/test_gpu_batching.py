@@ -133,11 +133,18 @@ def test_symmetric_energy_matches_gather_and_oracle(torch, orc, tpt, case):
     E_s = host(tpe.tp_energy(ctx, g, rows=rows_s))
     E_s2 = host(tpe.tp_energy(ctx, g))
     assert np.array_equal(E_s, E_s2)
-    assert rel(host(rows_s), host(rows_g)) <= 1e-6
-    assert rel(E_s, E_g) <= 1e-7
+    # Both passes add a tile's pair terms in plain FP32 (128 sources here, up to 512 in the gather)
+    # before folding into FP64, so they differ by the rounding of those partial sums: a few 1e-6 of
+    # the largest row at n = 1000.  The oracle decides.
+    assert rel(host(rows_s), host(rows_g)) <= 2e-5
+    assert rel(E_s, E_g) <= 1e-6
     idx = np.sort(np.random.default_rng(13).choice(c.n_edges, 48, replace=False)).astype(np.int32)
     if case != "batch":
         assert rel(host(rows_s)[idx], orc.energy_rows(c.gamma, c.edges, idx)) <= 1e-6
+    else:
+        for k in range(3):
+            gk, ek = c.curve(k)
+            assert abs(E_s[k] - orc.energy(gk, ek)) <= 1e-6 * abs(E_s[k])
 
 
 @pytest.mark.parametrize("tpt", [1, 2])
