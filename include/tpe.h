@@ -11,7 +11,8 @@
  *   - the projected H^s gradient g~ of Eq. 22, solved as P A-bar P y = P dE, g~ = P y (App. B.3.3);
  *   - one descent step with normalised gradient, backtracking from tau = 1 and constraint
  *     projection (Secs. 5.3.2 and 5.4, App. B.3.4).
- * Constraints are the barycenter and total-length constraints of Sec. 8.1.
+ * Constraints are those of Sec. 8.1: the barycenter with either the total length or every edge length
+ * (tp_params.constraint_set).
  *
  * Conventions shared by every entry point
  *   - Vertex arrays (gamma, dE, u, ...) are DEVICE pointers to double, vertex-major [nV][3].
@@ -78,6 +79,16 @@ typedef enum {
                                    only for contexts created with it (not in the paper) */
 } tp_precond;
 
+/* Constraint sets of Sec. 8.1 (Phi of the descent step; targets fixed by tp_set_constraints_from or at
+ * the first call). */
+typedef enum {
+    TP_CONSTRAINTS_TOTAL_LENGTH = 0, /* barycenter (3 rows) + total length L0 - sum_I l_I (1 row) per problem */
+    TP_CONSTRAINTS_EDGE_LENGTHS = 1  /* barycenter + one row l0_I - l_I per edge (isometric motions only).
+                                        Every curve's edges must be one simple chain in storage order
+                                        (i1 of edge I + 1 = i2 of edge I; closed when the last edge ends at
+                                        the first one's start) and curves may not share vertices */
+} tp_constraint_set;
+
 /* Shape of the learned preconditioner's edge-graph network (see tp_gnn_set_params). */
 #define TP_GNN_HIDDEN 64
 #define TP_GNN_FEATURES 8
@@ -109,6 +120,7 @@ typedef struct {
     int precond_refresh;  /* rebuild the Rayleigh-quotient symbols and the coarse space every k-th
                              preconditioner set-up (1: every set-up); diag(A) and the learned term's
                              features are always rebuilt for the current curve */
+    int constraint_set;   /* tp_constraint_set (default TP_CONSTRAINTS_TOTAL_LENGTH) */
 } tp_params;
 
 typedef struct {
@@ -181,17 +193,21 @@ TPE_API tp_status tp_spectral_symbols(tp_ctx *ctx, int rq, double *out, tp_strea
  * into lam (device [n]). */
 TPE_API tp_status tp_spectral_symbol(tp_ctx *ctx, int n, double *lam, tp_stream stream);
 
-/* Fix the constraint targets x0 (barycenter) and L0 (total length) of every problem at their
- * values on the curve gamma (Sec. 8.1).  Called implicitly by the first sobolev_gradient or
- * descent_step on a context. */
+/* Fix the constraint targets x0 (barycenter), L0 (total length) and, once the edge-length set has
+ * been selected, every l0_I of every problem at their values on the curve gamma (Sec. 8.1).  Called
+ * implicitly by the first sobolev_gradient or descent_step on a context. */
 TPE_API tp_status tp_set_constraints_from(tp_ctx *ctx, const double *gamma, tp_stream stream);
 
 /* Constraint values Phi (Sec. 8.1) of gamma into phi (device [4 * n_problems]):
- * rows 4q..4q+2 barycenter, row 4q+3 length of problem q. */
+ * rows 4q..4q+2 barycenter, row 4q+3 length of problem q: L0 - sum_I l_I, or with
+ * TP_CONSTRAINTS_EDGE_LENGTHS max_I |l0_I - l_I| over the problem's edges. */
 TPE_API tp_status tp_constraints(tp_ctx *ctx, const double *gamma, double *phi, tp_stream stream);
 
 /* Projected H^s gradient (Eq. 22 via the projected system of App. B.3.3): g = P y with
  * P A-bar P y = P dE, by preconditioned CG with device-resident scalars.  dE, g device [nV][3].
+ * With TP_CONSTRAINTS_EDGE_LENGTHS, P is the orthogonal projector onto the mean-free velocities that
+ * keep every edge length (one tridiagonal solve per curve and iteration), and a translation then
+ * restores the barycenter row; the result is the same KKT solution of Eq. 22.
  * info (host, may be NULL) is filled after a stream synchronisation.
  * Returns TP_ERR_NOT_CONVERGED (g holds the last iterate) or TP_ERR_BREAKDOWN on failure. */
 TPE_API tp_status sobolev_gradient(tp_ctx *ctx, const double *gamma, const double *dE, double *g, tp_solve_info *info,

@@ -58,6 +58,10 @@ bool params_ok(const tp_params *p, std::string &why)
         why = "coarse_dim must be >= 2";
         return false;
     }
+    if (p->constraint_set != TP_CONSTRAINTS_TOTAL_LENGTH && p->constraint_set != TP_CONSTRAINTS_EDGE_LENGTHS) {
+        why = "bad constraint_set";
+        return false;
+    }
     if (p->precond_refresh < 1) {
         why = "precond_refresh must be >= 1";
         return false;
@@ -206,6 +210,7 @@ void tp_default_params(tp_params *p)
     p->far_cutoff = 10.0;
     p->use_graphs = 1;
     p->precond_refresh = 1;
+    p->constraint_set = TP_CONSTRAINTS_TOTAL_LENGTH;
     p->coarse_dim = 64;
 }
 
@@ -252,6 +257,7 @@ void tp_destroy(tp_ctx *ctx)
     spectral_free(c);
     coarse_free(c);
     gnn_free(c);
+    edges_free(c);
     void *ptrs[] = {c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_voff,
                     c.plan_energy.d_items, c.plan_diff.d_items, c.plan_apply.d_items, c.plan_energy.d_eslots,
                     c.plan_diff.d_eslots, c.plan_apply.d_eslots, c.d_counter, c.d_recF, c.d_recF2, c.d_recLo,
@@ -438,6 +444,10 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
     }
     if (prm.precond >= TP_PRECOND_TWOLEVEL) CK(coarse_init(c));
     if (prm.precond == TP_PRECOND_LEARNED) CK(gnn_alloc(c));
+    if (prm.constraint_set == TP_CONSTRAINTS_EDGE_LENGTHS) {
+        if (!edges_chains_ok(c, why)) return fail(ctx, TP_ERR_INVALID_ARG, why);
+        CK(edges_init(c));
+    }
     CK(cudaDeviceSynchronize());
     return TP_OK;
 }
@@ -453,6 +463,13 @@ tp_status tp_set_params(tp_ctx *ctx, const tp_params *p)
         return fail(ctx, TP_ERR_UNSUPPORTED, "the spectral preconditioner needs closed polygons");
     if (p->precond == TP_PRECOND_LEARNED && !c.gnn)
         return fail(ctx, TP_ERR_UNSUPPORTED, "TP_PRECOND_LEARNED needs a context created with it");
+    if (p->constraint_set == TP_CONSTRAINTS_EDGE_LENGTHS && !c.edges) {
+        if (!edges_chains_ok(c, why)) return fail(ctx, TP_ERR_INVALID_ARG, why);
+        CK(edges_init(c));
+        CK(cudaDeviceSynchronize());
+    }
+    // a new constraint set takes its targets from the next curve solved, as on a fresh context
+    if (p->constraint_set != c.prm.constraint_set) c.constraints_set = 0;
     int indep = c.prm.independent;
     int had_spectral = c.spec != nullptr;
     c.prm = *p;
@@ -596,9 +613,21 @@ tp_status tp_spectral_symbols(tp_ctx *ctx, int rq, double *out, tp_stream stream
 static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE, double *g, int *iters, double *rr,
                                   int *conv, int *bd, cudaStream_t s, int *n_conv = nullptr)
 {
+    std::vector<int> flags(c.nProb, 1);
+    if (edge_constraints(c)) {
+        // y on null(R) cap N-perp (projector mode 2), then the translation that restores the barycenter
+        cudaError_t e = edges_setup(c, 0, s);
+        if (e != cudaSuccess) return e;
+        e = cg_solve(c, gamma, 0, dE, g, c.prm.cg_rtol, c.prm.cg_maxit, iters, rr, conv, bd, s, 2, flags.data());
+        if (e != cudaSuccess) return e;
+        if (n_conv) {
+            *n_conv = 0;
+            for (int f : flags) *n_conv += f;
+        }
+        return schur_shift(c, g, nullptr, 0.0, s);
+    }
     int i0 = 0, i1 = 0, c0 = 0, c1 = 0, b0 = 0, b1 = 0;
     double r0 = 0, r1 = 0;
-    std::vector<int> flags(c.nProb, 1);
     cudaError_t e = cg_solve(c, gamma, 0, dE, c.d_t3, c.prm.cg_rtol, c.prm.cg_maxit, &i0, &r0, &c0, &b0, s, 1,
                              flags.data());
     if (e != cudaSuccess) return e;
@@ -762,13 +791,26 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
             // x = argmin x^T A-bar(gamma) x / 2 s.t. C(trial) x = -Phi(trial) (Eq. 23) by the mean-free route:
             // y1 = A-bar(gamma)^+ C_len(trial)^T, then x = mu y1 + N t; trial += x
             CK(constraints_jacobian(c, 1, s));
-            CK(clen_rhs(c, rhs, s));
             int pit_cg = 0, pconv = 0, pbd = 0;
             double prr = 0.0;
-            CK(cg_solve(c, gamma, 0, rhs, z, c.prm.proj_cg_rtol, c.prm.cg_maxit, &pit_cg, &prr, &pconv, &pbd, s,
-                        1));
+            if (edge_constraints(c)) {
+                // App. B.3.4 with the edge rows R(trial): z0 = R^T (R R^T)^-1 (l0 - l) (so R z0 = l0 - l),
+                // y = argmin |z0 - y|_A over null(R) cap N-perp, x = z0 - y, then the barycenter shift
+                double *z0 = g;  // free after the direction was formed
+                CK(edges_setup(c, 1, s));
+                CK(edges_pinv(c, z0, s));
+                CK(pair_apply(c, gamma, 0, z0, rhs, s));
+                CK(cg_solve(c, gamma, 0, rhs, z, c.prm.proj_cg_rtol, c.prm.cg_maxit, &pit_cg, &prr, &pconv, &pbd,
+                            s, 2));
+                CK(vec_axpby(c, 1.0, z0, -1.0, z, x, s));
+                CK(schur_shift(c, x, c.d_phi, -1.0, s));
+            } else {
+                CK(clen_rhs(c, rhs, s));
+                CK(cg_solve(c, gamma, 0, rhs, z, c.prm.proj_cg_rtol, c.prm.cg_maxit, &pit_cg, &prr, &pconv, &pbd,
+                            s, 1));
+                CK(schur_projection(c, z, c.d_phi, -1.0, x, s));
+            }
             proj_cg_total += pit_cg;
-            CK(schur_projection(c, z, c.d_phi, -1.0, x, s));
             k_add<<<(3 * nV + 255) / 256, 256, 0, s>>>(3 * nV, c.d_gam, x, nullptr);
             c.launches++;
         }

@@ -339,12 +339,16 @@ __global__ void k_pinv(int nV, const double *__restrict__ C, const double *__res
     for (int cc = 0; cc < 3; ++cc) out[3 * i + cc] = c[cc] * m[0] + c[3 + cc] * m[1] + c[6 + cc] * m[2] + c[9 + cc] * m[3];
 }
 
+// With TP_CONSTRAINTS_EDGE_LENGTHS the slot of the total-length row holds max_I |l0_I - l_I| over the
+// problem's edges (edges.cu), so that one max over the four slots decides the projection's success.
 cudaError_t constraints_eval(Ctx &c, const double *, int which, double *phi, cudaStream_t s)
 {
     SolverState &st = S(c);
     k_phi<<<st.e_n, kRedThreads, 0, s>>>(eargs(c, 0), c.d_ellw[which], c.d_xw[which], c.d_x0L0, c.d_eprob, phi);
     c.launches++;
-    return cudaGetLastError();
+    TPE_CHECK(cudaGetLastError());
+    if (edge_constraints(c)) TPE_CHECK(edges_phi(c, which, phi, s));
+    return cudaSuccess;
 }
 
 cudaError_t constraints_targets(Ctx &c, int which, cudaStream_t s)
@@ -352,7 +356,9 @@ cudaError_t constraints_targets(Ctx &c, int which, cudaStream_t s)
     SolverState &st = S(c);
     k_targets<<<st.e_n, kRedThreads, 0, s>>>(eargs(c, 0), c.d_ellw[which], c.d_xw[which], c.d_x0L0);
     c.launches++;
-    return cudaGetLastError();
+    TPE_CHECK(cudaGetLastError());
+    if (c.edges) TPE_CHECK(edges_targets(c, which, s));
+    return cudaSuccess;
 }
 
 cudaError_t constraints_jacobian(Ctx &c, int which, cudaStream_t s)
@@ -641,9 +647,14 @@ __global__ void k_relres(RedArgs ra, const double *__restrict__ r, const CGScala
 // (c.d_Cv, c.d_Ginv) must describe the projector to use.  rhs and x may not alias the CG scratch.
 cudaError_t project_mean(Ctx &c, double *v, cudaStream_t s, const int *skip);
 
-// proj_mode 0: P = I - C^T (C C^T)^-1 C (constraint projector); 1: P = subtract the per-problem mean.
+// proj_mode 0: P = I - C^T (C C^T)^-1 C (constraint projector); 1: P = subtract the per-problem mean;
+// 2: the mean, then the edge-length rows (P = P_E P_N, the two commute; edges.cu, set up by edges_setup).
 static cudaError_t projector(Ctx &c, int mode, double *v, cudaStream_t s, const int *skip)
 {
+    if (mode == 2) {
+        TPE_CHECK(project_mean(c, v, s, skip));
+        return edges_project(c, v, s, skip);
+    }
     return mode ? project_mean(c, v, s, skip) : project(c, v, s, skip);
 }
 
@@ -1024,6 +1035,18 @@ cudaError_t schur_gradient(Ctx &c, const double *y0, const double *y1, double *g
     k_schur_red<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_Cv, nullptr, g, red_out);
     k_schur_shift<<<nb, 256, 0, s>>>(c.nV, red_out, nullptr, 0.0, c.d_vprob, g);
     c.launches += 4;
+    return cudaGetLastError();
+}
+
+// out += N t with C_bary (out + N t) = phi_scale * phi_bary (phi null: 0); the barycenter step of the
+// edge-length route, where the edge rows are already satisfied by out.
+cudaError_t schur_shift(Ctx &c, double *out, const double *phi, double phi_scale, cudaStream_t s)
+{
+    SolverState &st = S(c);
+    const int nb = (c.nV + 255) / 256;
+    k_schur_red<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_Cv, nullptr, out, c.d_red);
+    k_schur_shift<<<nb, 256, 0, s>>>(c.nV, c.d_red, phi, phi_scale, c.d_vprob, out);
+    c.launches += 2;
     return cudaGetLastError();
 }
 

@@ -15,6 +15,7 @@ struct SpecState;
 struct SolverState;
 struct CoarseState;
 struct GnnState;
+struct EdgeState;
 
 // Precision of the pair arithmetic.
 enum Prec { P64 = 0, P32 = 1, PMIX = 2 };
@@ -169,6 +170,7 @@ struct Ctx {
     int64_t pairs_per_pass = 0;
     const int *d_skip = nullptr;  // during a CG solve: per-problem converged flags (apply skips them)
     GnnState *gnn = nullptr;      // learned preconditioner term (contexts created with TP_PRECOND_LEARNED)
+    EdgeState *edges = nullptr;   // edge-length constraint rows (edges.cu), allocated when first selected
     // captured CG iteration blocks
     cudaStream_t cg_stream = nullptr;
     cudaEvent_t cg_join[2] = {nullptr, nullptr};
@@ -242,6 +244,20 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
                      int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s,
                      int proj_mode, int *conv_flags = nullptr);
 cudaError_t project_mean(Ctx &c, double *v, cudaStream_t s, const int *skip);
+cudaError_t schur_shift(Ctx &c, double *out, const double *phi, double phi_scale, cudaStream_t s);
+// edge-length constraints (edges.cu)
+bool edges_chains_ok(const Ctx &c, std::string &why);
+cudaError_t edges_init(Ctx &c);
+void edges_free(Ctx &c);
+cudaError_t edges_targets(Ctx &c, int which, cudaStream_t s);
+cudaError_t edges_setup(Ctx &c, int which, cudaStream_t s);
+cudaError_t edges_project(Ctx &c, double *v, cudaStream_t s, const int *skip);
+cudaError_t edges_pinv(Ctx &c, double *out, cudaStream_t s);
+cudaError_t edges_phi(Ctx &c, int which, double *phi, cudaStream_t s);
+inline bool edge_constraints(const Ctx &c)
+{
+    return c.edges && c.prm.constraint_set == TP_CONSTRAINTS_EDGE_LENGTHS;
+}
 cudaError_t clen_rhs(Ctx &c, double *out, cudaStream_t s);
 cudaError_t schur_gradient(Ctx &c, const double *y0, const double *y1, double *g, cudaStream_t s);
 cudaError_t schur_projection(Ctx &c, const double *y1, const double *phi, double phi_scale, double *x,

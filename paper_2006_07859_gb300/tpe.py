@@ -19,6 +19,7 @@ TP_FP64, TP_FP32, TP_MIXED = 0, 1, 2
 TP_PRECOND_NONE, TP_PRECOND_JACOBI, TP_PRECOND_SPECTRAL, TP_PRECOND_SPECTRAL_RQ, TP_PRECOND_TWOLEVEL = 0, 1, 2, 3, 4
 TP_PRECOND_LEARNED = 5
 TP_GNN_HIDDEN, TP_GNN_FEATURES = 64, 8
+TP_CONSTRAINTS_TOTAL_LENGTH, TP_CONSTRAINTS_EDGE_LENGTHS = 0, 1
 
 STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ERR_DEGENERATE_EDGE",
                 4: "TP_ERR_NONFINITE", 5: "TP_ERR_NOT_CONVERGED", 6: "TP_ERR_BREAKDOWN", 7: "TP_ERR_LINESEARCH",
@@ -41,7 +42,7 @@ class TpParams(ctypes.Structure):
                 ("precond", ctypes.c_int), ("armijo_c", ctypes.c_double), ("shrink", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("proj_tol", ctypes.c_double), ("proj_maxit", ctypes.c_int),
                 ("independent", ctypes.c_int), ("coarse_dim", ctypes.c_int), ("far_cutoff", ctypes.c_double),
-                ("use_graphs", ctypes.c_int), ("precond_refresh", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("precond_refresh", ctypes.c_int), ("constraint_set", ctypes.c_int)]
 
 
 class TpSolveInfo(ctypes.Structure):
