@@ -64,6 +64,9 @@ def parse():
                          "precision: per-result error of the 262,144-edge passes against the FP64 oracle on "
                          "a sample; batch: 1,024 independent knots of log-uniform size; learned: train the "
                          "learned preconditioner and compare times to 1e-6 against plain FP64 CG")
+    ap.add_argument("--sym-tpt", type=int, default=0,
+                    help="passes mode: run the symmetric energy / differential / apply passes with this many "
+                         "targets per thread (0: the gather passes)")
     ap.add_argument("--rows", type=int, default=1024, help="precision mode: sampled rows / vertices")
     ap.add_argument("--with-fp64", action="store_true", help="precision mode: also run the FP64 GPU passes")
     ap.add_argument("--train-steps", type=int, default=300, help="learned mode: Adam steps")
@@ -273,11 +276,15 @@ def pass_throughput_262k(tpe, torch):
 
 def run_passes(args):
     """A short fixed sequence on the benchmark workload for profilers: one energy, one differential,
-    three applies (mixed precision)."""
+    three applies (mixed precision); --sym-tpt selects the symmetric passes."""
     import torch
     from paper_2006_07859_gb300 import tpe
     curves, cfg, indep = workload(args.workload)
     ctx = tpe.Context.from_curves(curves, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_JACOBI, independent=indep)
+    if args.sym_tpt:
+        tpe.tp_set_energy_variant(ctx, args.sym_tpt)
+        tpe.tp_set_diff_variant(ctx, args.sym_tpt)
+        tpe.tp_set_apply_variant(ctx, args.sym_tpt)
     g = torch.as_tensor(curves.gamma).cuda()
     u = torch.as_tensor(np.random.default_rng(1).normal(size=(curves.n_vertices, 3))).cuda()
     tpe.tp_energy(ctx, g)
