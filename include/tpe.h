@@ -352,10 +352,12 @@ TPE_API tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, con
  * (CUDA events on `stream`), and keeps the fastest, rebuilding that op's work queue; other contexts
  * keep their defaults and are left unchanged.
  *   tpt (HOST int32 [6], may be NULL): the chosen targets per thread of the energy, differential and
- *       apply gather passes, then of the symmetric apply, energy and differential (0: gather pass).
- *   ms  (HOST double [15], may be NULL): ms per pass for 1, 2, 4 targets per thread of the energy
+ *       apply gather passes, then of the symmetric apply and energy, then the symmetric differential's
+ *       variant (tp_set_diff_variant; 0: gather pass).
+ *   ms  (HOST double [17], may be NULL): ms per pass for 1, 2, 4 targets per thread of the energy
  *       [0..2], differential [3..5] and apply [6..8] gather passes, then the symmetric apply [9..10],
- *       energy [11..12] and differential [13..14] with 1, 2 (0 where not a candidate).
+ *       energy [11..12] with 1, 2, and the symmetric differential variants 1, 2 [13..14] and 3, 4
+ *       [15..16] (0 where not a candidate).
  * May reallocate the context's partial-sum buffer (the only allocation after tp_create).
  * Synchronises the stream.  Errors: TP_ERR_INVALID_ARG, TP_ERR_CUDA, TP_ERR_DEGENERATE_EDGE. */
 TPE_API tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms, tp_stream stream);
@@ -370,8 +372,10 @@ TPE_API tp_status tp_set_apply_variant(tp_ctx *ctx, int symmetric_tpt);
  * sums in another order). */
 TPE_API tp_status tp_set_energy_variant(tp_ctx *ctx, int symmetric_tpt);
 
-/* The same choice for the differential pass (0: gather, 1 or 2: symmetric; row J's terms of a pair
- * are the mirror of row I's, near pairs are FP64 on both sides). */
+/* The same choice for the differential pass (0: gather; 1 or 2: symmetric with that many targets per
+ * thread; 3: symmetric, one target per thread with registers held to 4 resident CTAs per SM; 4: two
+ * targets per thread held to 3 CTAs per SM.  Row J's terms of a pair are the mirror of row I's; near
+ * pairs are FP64 on both sides). */
 TPE_API tp_status tp_set_diff_variant(tp_ctx *ctx, int symmetric_tpt);
 
 /* Throughput microbenchmarks on the current device (no context needed): FP32 FMA FLOP/s, MUFU

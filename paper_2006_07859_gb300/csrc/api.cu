@@ -1086,7 +1086,7 @@ tp_status tp_set_diff_variant(tp_ctx *ctx, int symmetric_tpt)
 {
     if (!ctx) return TP_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
-    if (symmetric_tpt < 0 || symmetric_tpt > 2) return fail(ctx, TP_ERR_INVALID_ARG, "symmetric_tpt must be 0, 1 or 2");
+    if (symmetric_tpt < 0 || symmetric_tpt > 4) return fail(ctx, TP_ERR_INVALID_ARG, "the differential variant must be 0 .. 4");
     if (symmetric_tpt > 0 && !(c.prm.precision == TP_MIXED && c.kp.fast))
         return fail(ctx, TP_ERR_UNSUPPORTED, "the symmetric differential exists for TP_MIXED with (alpha, beta) = (2, 4.5)");
     CK(sym_select_diff(c, symmetric_tpt));
@@ -1123,7 +1123,7 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
     tp_status st = records(ctx, gamma, 0, s);
     if (st) return st;
     if (ms)
-        for (int k = 0; k < 15; ++k) ms[k] = 0.0;
+        for (int k = 0; k < 17; ++k) ms[k] = 0.0;
     if (tpt) tpt[3] = tpt[4] = tpt[5] = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
@@ -1168,8 +1168,9 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
         // the differential also has the symmetric pass
         if (cls == 1 && nc > 1 && err == cudaSuccess) {
             int best_sym = 0;
-            for (int t = 1; t <= 2 && err == cudaSuccess; ++t) {
-                if (sym_slots(c, t) * (size_t)c.nE * 6 * sizeof(double) > ((size_t)16 << 30)) continue;
+            for (int t = 1; t <= 4 && err == cudaSuccess; ++t) {
+                const int tpt_t = (t == 2 || t == 4) ? 2 : 1;
+                if (sym_slots(c, tpt_t) * (size_t)c.nE * 6 * sizeof(double) > ((size_t)16 << 30)) continue;
                 if ((err = sym_select_diff(c, t)) != cudaSuccess) break;
                 if ((err = run(cls)) != cudaSuccess) break;
                 cudaEventRecord(e0, s);
@@ -1179,7 +1180,7 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
                 float tm = 0.f;
                 if (err == cudaSuccess) err = cudaEventElapsedTime(&tm, e0, e1);
                 tm /= 3.f;
-                if (ms) ms[13 + t - 1] = tm;
+                if (ms) ms[t <= 2 ? 13 + t - 1 : 15 + t - 3] = tm;
                 if (tm < best_ms) {
                     best_ms = tm;
                     best_sym = t;

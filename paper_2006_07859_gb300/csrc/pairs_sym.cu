@@ -635,8 +635,10 @@ __device__ __forceinline__ void sym_diff_tile(const Tgt<float> (&tg)[TPT], const
 
 constexpr size_t kDiffSymDynSmem = sizeof(float) * 2 * kSymWarps * kDS * kTile;
 
-template <int TPT, bool FAST>
-__global__ void __launch_bounds__(kThreads, 2) k_diff_sym(const PairArgs pa)
+// MB: resident CTAs per SM the register allocation is held to (2 needs no spills at either TPT; the
+// variants with 3 / 4 trade a few spilled registers for more warps to hide latency).
+template <int TPT, bool FAST, int MB>
+__global__ void __launch_bounds__(kThreads, MB) k_diff_sym(const PairArgs pa)
 {
     __shared__ Tile<PMIX, false> tl;
     __shared__ int s_item;
@@ -895,16 +897,31 @@ cudaError_t sym_energy_pass(Ctx &c, int which, const double *gamma, cudaStream_t
     return cudaGetLastError();
 }
 
-static int sym_diff_occupancy(int tpt)
+// Symmetric differential variants: 1 / 2 targets per thread at 2 CTAs per SM, 3: one target at 4 CTAs
+// per SM, 4: two targets at 3 CTAs per SM.
+static int diff_variant_tpt(int v)
+{
+    return (v == 2 || v == 4) ? 2 : 1;
+}
+
+template <class F>
+static void with_diff_kernel(int v, F f)
+{
+    switch (v) {
+        case 1: f(k_diff_sym<1, true, 2>); break;
+        case 2: f(k_diff_sym<2, true, 2>); break;
+        case 3: f(k_diff_sym<1, true, 4>); break;
+        default: f(k_diff_sym<2, true, 3>); break;
+    }
+}
+
+static int sym_diff_occupancy(int v)
 {
     int occ = 0;
-    if (tpt == 1) {
-        cudaFuncSetAttribute(k_diff_sym<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiffSymDynSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_diff_sym<1, true>, kThreads, kDiffSymDynSmem);
-    } else {
-        cudaFuncSetAttribute(k_diff_sym<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiffSymDynSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_diff_sym<2, true>, kThreads, kDiffSymDynSmem);
-    }
+    with_diff_kernel(v, [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiffSymDynSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, kDiffSymDynSmem);
+    });
     return occ;
 }
 
@@ -917,8 +934,9 @@ cudaError_t sym_select_diff(Ctx &c, int tpt)
     pl = Ctx::Plan{};
     c.diff_sym = 0;
     if (tpt <= 0) return cudaSuccess;
-    if (c.prm.precision != TP_MIXED || !c.kp.fast || (tpt != 1 && tpt != 2)) return cudaErrorInvalidValue;
-    sym_plan_items(c, pl, tpt, sym_diff_occupancy(tpt));
+    if (c.prm.precision != TP_MIXED || !c.kp.fast || tpt > 4) return cudaErrorInvalidValue;
+    sym_plan_items(c, pl, diff_variant_tpt(tpt), sym_diff_occupancy(tpt));
+    pl.tpt = tpt;  // the variant (the plan's blocking follows its targets per thread)
     const size_t need = (size_t)pl.max_slots * std::max(1, c.nE) * 6;
     if (need > c.part_elems) {
         TPE_CHECK(cudaFree(c.d_part));
@@ -949,10 +967,7 @@ cudaError_t sym_diff_pass(Ctx &c, int which, const double *gamma, cudaStream_t s
     pa.kp = c.kp;
     pa.skip = nullptr;
     const int slot = c.profile ? prof_begin(c, OP_DIFF, s) : -1;
-    if (pl.tpt == 1)
-        k_diff_sym<1, true><<<pl.grid, kThreads, kDiffSymDynSmem, s>>>(pa);
-    else
-        k_diff_sym<2, true><<<pl.grid, kThreads, kDiffSymDynSmem, s>>>(pa);
+    with_diff_kernel(pl.tpt, [&](auto kern) { kern<<<pl.grid, kThreads, kDiffSymDynSmem, s>>>(pa); });
     if (slot >= 0 || slot <= -2) prof_end(c, slot, s);
     c.launches++;
     return cudaGetLastError();

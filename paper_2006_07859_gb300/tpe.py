@@ -404,7 +404,7 @@ def tp_autotune(ctx: Context, gamma) -> dict:
     """Pick the fastest targets-per-thread of each pair pass on `gamma` (mixed precision, alpha = 2,
     beta = 4.5); returns the choices and the measured ms per pass."""
     t = (ctypes.c_int32 * 6)()
-    ms = (ctypes.c_double * 15)()
+    ms = (ctypes.c_double * 17)()
     ctx._check(library().tp_autotune(ctx.handle, _ptr(gamma), t, ms, _stream()))
     names = ["energy", "diff", "apply"]
     out = {"tpt": {n: int(t[k]) for k, n in enumerate(names)},
@@ -415,7 +415,7 @@ def tp_autotune(ctx: Context, gamma) -> dict:
     out["ms"]["apply_symmetric"] = {str(v): ms[9 + j] for j, v in enumerate((1, 2)) if ms[9 + j] > 0}
     out["ms"]["energy_symmetric"] = {str(v): ms[11 + j] for j, v in enumerate((1, 2)) if ms[11 + j] > 0}
     out["tpt"]["diff_symmetric"] = int(t[5])
-    out["ms"]["diff_symmetric"] = {str(v): ms[13 + j] for j, v in enumerate((1, 2)) if ms[13 + j] > 0}
+    out["ms"]["diff_symmetric"] = {str(v): ms[i] for v, i in ((1, 13), (2, 14), (3, 15), (4, 16)) if ms[i] > 0}
     return out
 
 

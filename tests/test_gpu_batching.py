@@ -147,7 +147,7 @@ def test_symmetric_energy_matches_gather_and_oracle(torch, orc, tpt, case):
             assert abs(E_s[k] - orc.energy(gk, ek)) <= 1e-6 * abs(E_s[k])
 
 
-@pytest.mark.parametrize("tpt", [1, 2])
+@pytest.mark.parametrize("tpt", [1, 2, 3, 4])
 @pytest.mark.parametrize("case", ["single_ragged", "batch", "near"])
 def test_symmetric_differential_matches_gather_and_oracle(torch, orc, tpt, case):
     """The symmetric differential (row J's terms of a pair mirrored from row I's; near pairs FP64 on both

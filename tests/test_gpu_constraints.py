@@ -65,6 +65,8 @@ def test_edge_gradient_matches_dense_kkt(torch, orc, name):
             grk = orc.constraint_groups(gk, ek, edge_lengths=True)
             dk = orc.differential(gk, ek)
             parts.append(orc.sobolev_gradient(gk, ek, grk, dk, orc.Params(), dense=True)[0])
+            v0, v1 = c.vertex_offsets[k], c.vertex_offsets[k + 1]
+            assert rel(dEh[v0:v1], dk) <= 1e-10   # independent curves: no cross-curve pairs
         gk_all = np.concatenate(parts)
         assert len(groups) == c.n_curves
     else:
@@ -73,7 +75,7 @@ def test_edge_gradient_matches_dense_kkt(torch, orc, name):
                                       dense=True)[0]
         C = orc.jacobian(c.gamma, c.edges, gr).reshape(gr[0].n_rows, -1)
         assert np.abs(C @ gt.reshape(-1)).max() <= 1e-10 * np.abs(gt).max()
-    assert rel(dEh, orc.differential(c.gamma, c.edges)) <= 1e-10
+        assert rel(dEh, orc.differential(c.gamma, c.edges)) <= 1e-10
     assert rel(gt, gk_all) <= 1e-7
 
 
