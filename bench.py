@@ -59,11 +59,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-262k", action="store_true", help="skip the 262,144-edge pair-pass timing")
-    ap.add_argument("--mode", choices=["bench", "passes", "precision", "batch", "learned"], default="bench",
+    ap.add_argument("--mode", choices=["bench", "passes", "precision", "batch", "learned", "constraints"],
+                    default="bench",
                     help="passes: energy, differential and 3 applies of the workload (for ncu); "
                          "precision: per-result error of the 262,144-edge passes against the FP64 oracle on "
                          "a sample; batch: 1,024 independent knots of log-uniform size; learned: train the "
-                         "learned preconditioner and compare times to 1e-6 against plain FP64 CG")
+                         "learned preconditioner and compare times to 1e-6 against plain FP64 CG; "
+                         "constraints: descent steps with the total-length and the edge-length constraint sets")
     ap.add_argument("--sym-tpt", type=int, default=0,
                     help="passes mode: run the symmetric energy / differential / apply passes with this many "
                          "targets per thread (0: the gather passes)")
@@ -382,6 +384,45 @@ def run_batch(args):
     print(json.dumps(res), flush=True)
 
 
+def run_constraints(args):
+    """Descent steps under the two constraint sets of Sec. 8.1 on the 8 x 4096 benchmark knots (mixed
+    precision, two-level preconditioner): barycenter + total length against barycenter + every edge
+    length.  Reports steps/s, CG iterations and the largest edge-length drift after the steps."""
+    import torch
+    import synth as S
+    from paper_2006_07859_gb300 import tpe
+    curves = S.eight_knots_4096(as_scene=False)
+    res = {"mode": "constraints", "workload": "8_independent_fourier_knots_K8_n4096_seeds1-8", "steps": args.steps,
+           "warmup": args.warmup}
+    for name, cs in (("total_length", tpe.TP_CONSTRAINTS_TOTAL_LENGTH), ("edge_lengths", tpe.TP_CONSTRAINTS_EDGE_LENGTHS)):
+        ctx = tpe.Context.from_curves(curves, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_TWOLEVEL, independent=1,
+                                      cg_rtol=1e-6, cg_maxit=2000, proj_cg_rtol=1e-3, constraint_set=cs,
+                                      precond_refresh=args.precond_refresh)
+        tpe.tp_autotune(ctx, torch.as_tensor(curves.gamma).cuda())
+        g = torch.as_tensor(curves.gamma).cuda()
+        ell0 = np.linalg.norm(curves.gamma[curves.edges[:, 1]] - curves.gamma[curves.edges[:, 0]], axis=1)
+        allow = (tpe.TP_ERR_NOT_CONVERGED, tpe.TP_ERR_LINESEARCH)
+        for _ in range(args.warmup):
+            tpe.descent_step(ctx, g, allow=allow)
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        infos = []
+        a.record()
+        for _ in range(args.steps):
+            infos.append(tpe.descent_step(ctx, g, allow=allow))
+        z.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(z) / 1e3 / args.steps
+        gh = g.cpu().numpy()
+        ell = np.linalg.norm(gh[curves.edges[:, 1]] - gh[curves.edges[:, 0]], axis=1)
+        res[name] = {"steps_per_s": 1.0 / t, "ms_per_step": 1e3 * t,
+                     "cg_iters": [i["cg_iters"] for i in infos], "proj_cg_iters": [i["proj_cg_iters"] for i in infos],
+                     "E_after": infos[-1]["E_after"], "accepted": infos[-1]["accepted"],
+                     "max_rel_edge_length_drift": float(np.max(np.abs(ell / ell0 - 1.0)))}
+        ctx.close()
+    print(json.dumps(res), flush=True)
+
+
 def timed_solve(tpe, torch, ctx, g, rhs):
     """Wall time (CUDA events around the call) and info of one preconditioned CG solve of
     A-bar y = P rhs on the mean-free subspace, preconditioner set-up included."""
@@ -611,6 +652,8 @@ def main():
         run_passes(args)
     elif args.mode == "precision":
         run_precision(args)
+    elif args.mode == "constraints":
+        run_constraints(args)
     elif args.mode == "batch":
         run_batch(args)
     elif args.mode == "learned":
