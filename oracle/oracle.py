@@ -361,6 +361,119 @@ def projected_cg(apply_abar, P, a, tol=1e-6, maxit=10000, precond=None, x0=None)
     return CGResult(P(y), maxit, np.linalg.norm(r) / nb, False, hist)
 
 
+# ----------------------------------------------------------------------------- collision time (Sec. 5.4)
+#
+# The isotopy-safe start of the line search: tau_max is the first tau > 0 at which the moving curve
+# gamma - tau d brings two disjoint edges into contact; the backtracking starts at 2/3 tau_max.
+# Contact of two segments moving linearly in time needs their four endpoints coplanar, a cubic in tau
+# (the determinant of three edge vectors that are each linear in tau), and, at that root, the
+# segments must actually touch (distance zero, up to TOUCH_REL times the two lengths).  When every
+# coefficient of the cubic vanishes the motion is coplanar, and the first contact is a vertex of one
+# segment meeting the other segment: a quadratic in tau for each of the four vertex-segment choices.
+
+TOUCH_REL = 1e-8
+
+
+def segment_distance(p1, p2, q1, q2):
+    """Smallest |P(s) - Q(u)| over s, u in [0, 1]: the stationary point of the quadratic if it lies
+    in the square, else the best of the four edges of the square (each a clamped 1-D minimum)."""
+    d1, d2, r = p2 - p1, q2 - q1, p1 - q1
+    a, b, e = d1 @ d1, d1 @ d2, d2 @ d2
+    c, f = d1 @ r, d2 @ r
+    cand = []
+    den = a * e - b * b
+    if den > 1e-14 * a * e:
+        s, u = (b * f - c * e) / den, (a * f - b * c) / den
+        if 0.0 <= s <= 1.0 and 0.0 <= u <= 1.0:
+            cand.append((s, u))
+    for s in (0.0, 1.0):
+        cand.append((s, min(1.0, max(0.0, (b * s + f) / e)) if e > 0 else 0.0))
+    for u in (0.0, 1.0):
+        cand.append((min(1.0, max(0.0, (b * u - c) / a)) if a > 0 else 0.0, u))
+    return min(float(np.linalg.norm(p1 + s * d1 - q1 - u * d2)) for s, u in cand)
+
+
+def _det3(u, v, w):
+    return float(np.dot(u, np.cross(v, w)))
+
+
+def _real_roots(coef, T):
+    """Real roots in (0, T] of sum_k coef[k] t^k (numpy.roots on the trimmed polynomial)."""
+    c = list(coef)
+    while c and c[-1] == 0.0:
+        c.pop()
+    if len(c) <= 1:
+        return []
+    r = np.roots(c[::-1])
+    out = []
+    for z in r:
+        if abs(z.imag) <= 1e-9 * max(1.0, abs(z.real)) and 0.0 < z.real <= T:
+            out.append(float(z.real))
+    return sorted(out)
+
+
+def pair_collision_time(a, b, da, db, c, e, dc, de, T):
+    """First tau in (0, T] at which segment [a - tau da, b - tau db] touches [c - tau dc, e - tau de],
+    or inf."""
+    a, b, da, db, c, e, dc, de = (np.asarray(x, dtype=np.float64) for x in (a, b, da, db, c, e, dc, de))
+    tol = TOUCH_REL * (np.linalg.norm(b - a) + np.linalg.norm(e - c))
+    at = lambda p, dp, t: p - t * dp
+    # edge vectors relative to a, each linear in tau: X(t) = X0 + t X1
+    U0, U1 = b - a, -(db - da)
+    V0, V1 = c - a, -(dc - da)
+    W0, W1 = e - a, -(de - da)
+    coef = [_det3(U0, V0, W0),
+            _det3(U1, V0, W0) + _det3(U0, V1, W0) + _det3(U0, V0, W1),
+            _det3(U1, V1, W0) + _det3(U1, V0, W1) + _det3(U0, V1, W1),
+            _det3(U1, V1, W1)]
+    scale = max(np.linalg.norm(U0) + T * np.linalg.norm(U1), np.linalg.norm(V0) + T * np.linalg.norm(V1),
+                np.linalg.norm(W0) + T * np.linalg.norm(W1)) ** 3
+    if max(abs(coef[k]) * T ** k for k in range(4)) > 1e-13 * scale:
+        for t in _real_roots(coef, T):
+            if segment_distance(at(a, da, t), at(b, db, t), at(c, dc, t), at(e, de, t)) <= tol:
+                return t
+        return np.inf
+    # coplanar motion: vertex-segment contacts
+    best = np.inf
+    for p, dp, q1, dq1, q2, dq2 in ((a, da, c, dc, e, de), (b, db, c, dc, e, de),
+                                    (c, dc, a, da, b, db), (e, de, a, da, b, db)):
+        # (q2 - q1) x (p - q1) = 0 along the plane normal: a quadratic in tau
+        S0, S1 = q2 - q1, -(dq2 - dq1)
+        R0, R1 = p - q1, -(dp - dq1)
+        nrm = np.cross(U0 + 0.5 * T * U1, V0 + 0.5 * T * V1)
+        if np.linalg.norm(nrm) == 0.0:
+            nrm = np.cross(U0 + 0.5 * T * U1, W0 + 0.5 * T * W1)
+        if np.linalg.norm(nrm) == 0.0:
+            continue
+        q = [np.cross(S0, R0) @ nrm, (np.cross(S1, R0) + np.cross(S0, R1)) @ nrm, np.cross(S1, R1) @ nrm]
+        for t in _real_roots(q, T):
+            if segment_distance(at(a, da, t), at(b, db, t), at(c, dc, t), at(e, de, t)) <= tol:
+                best = min(best, t)
+                break
+    return best
+
+
+def first_collision_time(gamma, edges, d, T, edge_offsets=None):
+    """Sec. 5.4: the first tau in (0, T] at which two disjoint edges of gamma - tau d touch, per group of
+    edges (one per curve if edge_offsets is given, else the whole graph); T where none touch."""
+    g, e = _geom(gamma, edges)
+    d = np.asarray(d, dtype=np.float64).reshape(g.shape)
+    offs = [0, len(e)] if edge_offsets is None else list(edge_offsets)
+    out = []
+    for k in range(len(offs) - 1):
+        best = np.inf
+        for I in range(offs[k], offs[k + 1]):
+            a, b = e[I]
+            for J in range(I + 1, offs[k + 1]):
+                c, f = e[J]
+                if len({a, b, c, f}) < 4:
+                    continue
+                t = pair_collision_time(g[a], g[b], d[a], d[b], g[c], g[f], d[c], d[f], T)
+                best = min(best, t)
+        out.append(min(best, T))
+    return np.array(out)
+
+
 # ----------------------------------------------------------------------------- descent
 
 @dataclass
@@ -375,6 +488,8 @@ class Params:
     armijo_c: float = 1e-4
     shrink: float = 0.5
     max_halvings: int = 30
+    isotopy_safe: bool = False   # Sec. 5.4's first strategy: start at 2/3 of the first collision time
+    ccd_horizon: float = 1.5     # collision times are searched in (0, ccd_horizon]
 
     @property
     def sigma(self):
@@ -430,7 +545,9 @@ class StepInfo:
 
 
 def descent_step(gamma, edges, groups, prm: Params, dense=False, precond_factory=None):
-    """One H^s descent step with normalised-gradient backtracking from tau = 1 (Sec. 5.4)."""
+    """One H^s descent step with normalised-gradient backtracking (Sec. 5.4) from tau = 1, or with
+    prm.isotopy_safe from 2/3 of the first collision time along gamma - tau d (searched up to
+    ccd_horizon; ccd_horizon itself when no collision comes first)."""
     E0 = energy(gamma, edges, prm.alpha, prm.beta)
     dE = differential(gamma, edges, prm.alpha, prm.beta)
     pc = precond_factory(gamma) if precond_factory else None
@@ -442,6 +559,8 @@ def descent_step(gamma, edges, groups, prm: Params, dense=False, precond_factory
     slope = float(np.vdot(dE, d))
     apply_abar = make_apply(gamma, edges, prm.sigma)  # A-bar of the pre-step curve
     tau = 1.0
+    if prm.isotopy_safe:
+        tau = 2.0 / 3.0 * float(first_collision_time(gamma, edges, d, prm.ccd_horizon)[0])
     for h in range(prm.max_halvings + 1):
         cand = gamma - tau * d
         cand, pit, ok = constraint_projection(cand, edges, groups, apply_abar, prm, pc)
