@@ -22,8 +22,9 @@
  *     synchronise the stream before returning.
  *   - The caller owns every pointer it passes; the context owns its own scratch memory,
  *     allocated once in tp_create and sized for the graph it was created with.  Only
- *     tp_set_params (switching a preconditioner on) and tp_autotune (a larger work queue)
- *     allocate device memory after tp_create.
+ *     tp_set_params (switching a preconditioner, a constraint set or the line search on),
+ *     tp_autotune (a larger work queue) and the first tp_collision_time allocate device memory
+ *     after tp_create.
  *   - Every call returns a tp_status; nothing aborts or traps.  tp_last_error() gives a
  *     human-readable message for the last failing call on a context.
  *   - A context is not thread-safe; use one context per host thread.
@@ -89,6 +90,14 @@ typedef enum {
                                         the first one's start) and curves may not share vertices */
 } tp_constraint_set;
 
+/* Start of the backtracking line search (Sec. 5.4). */
+typedef enum {
+    TP_LINESEARCH_UNIT = 0,    /* normalised gradient, tau = 1 (the paper's strategy for its applications) */
+    TP_LINESEARCH_ISOTOPY = 1  /* tau = 2/3 tau_max, tau_max the first collision time of gamma - tau d in
+                                  (0, ccd_horizon] (ccd_horizon when none comes first); every accepted
+                                  step stays below the first collision along the straight path */
+} tp_line_search;
+
 /* Shape of the learned preconditioner's edge-graph network (see tp_gnn_set_params). */
 #define TP_GNN_HIDDEN 64
 #define TP_GNN_FEATURES 8
@@ -121,6 +130,9 @@ typedef struct {
                              preconditioner set-up (1: every set-up); diag(A) and the learned term's
                              features are always rebuilt for the current curve */
     int constraint_set;   /* tp_constraint_set (default TP_CONSTRAINTS_TOTAL_LENGTH) */
+    int line_search;      /* tp_line_search (default TP_LINESEARCH_UNIT) */
+    double ccd_horizon;   /* TP_LINESEARCH_ISOTOPY: collision times are searched in (0, ccd_horizon]
+                             (default 1.5, so that the start never exceeds tau = 1) */
 } tp_params;
 
 typedef struct {
@@ -203,6 +215,15 @@ TPE_API tp_status tp_set_constraints_from(tp_ctx *ctx, const double *gamma, tp_s
  * TP_CONSTRAINTS_EDGE_LENGTHS max_I |l0_I - l_I| over the problem's edges. */
 TPE_API tp_status tp_constraints(tp_ctx *ctx, const double *gamma, double *phi, tp_stream stream);
 
+/* First collision time (Sec. 5.4): t (DEVICE double [n_problems]) receives, per problem, the first
+ * tau in (0, horizon] at which two disjoint edges of gamma - tau d touch (segment distance at most
+ * 1e-8 times the sum of their lengths), or horizon where none do.  gamma, d: DEVICE [nV][3].  Pairs
+ * whose boxes swept over [0, horizon] are apart are skipped; the others solve the coplanarity cubic in
+ * FP64.  The first call allocates the context's block-pair work list.  Errors: TP_ERR_INVALID_ARG
+ * (horizon <= 0), TP_ERR_CUDA. */
+TPE_API tp_status tp_collision_time(tp_ctx *ctx, const double *gamma, const double *d, double horizon, double *t,
+                                    tp_stream stream);
+
 /* Projected H^s gradient (Eq. 22 via the projected system of App. B.3.3): g = P y with
  * P A-bar P y = P dE, by preconditioned CG with device-resident scalars.  dE, g device [nV][3].
  * With TP_CONSTRAINTS_EDGE_LENGTHS, P is the orthogonal projector onto the mean-free velocities that
@@ -214,7 +235,8 @@ TPE_API tp_status sobolev_gradient(tp_ctx *ctx, const double *gamma, const doubl
                            tp_stream stream);
 
 /* One descent step in place on gamma (device [nV][3]) (Sec. 5.4): g~ by sobolev_gradient,
- * d = g~ / ||g~||_2, then tau = 1, shrink, ... until the constraint projection of gamma - tau d
+ * d = g~ / ||g~||_2, then tau = 1 (or 2/3 of the first collision time with TP_LINESEARCH_ISOTOPY),
+ * shrink, ... until the constraint projection of gamma - tau d
  * (Sec. 5.3.2, App. B.3.4) succeeds and the Armijo condition holds.  Synchronises the stream
  * (the line search reads scalars on the host).  On TP_ERR_LINESEARCH gamma is unchanged. */
 TPE_API tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream stream);

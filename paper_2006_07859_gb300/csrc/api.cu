@@ -62,6 +62,10 @@ bool params_ok(const tp_params *p, std::string &why)
         why = "bad constraint_set";
         return false;
     }
+    if ((p->line_search != TP_LINESEARCH_UNIT && p->line_search != TP_LINESEARCH_ISOTOPY) || !(p->ccd_horizon > 0.0)) {
+        why = "bad line_search or ccd_horizon";
+        return false;
+    }
     if (p->precond_refresh < 1) {
         why = "precond_refresh must be >= 1";
         return false;
@@ -211,6 +215,8 @@ void tp_default_params(tp_params *p)
     p->use_graphs = 1;
     p->precond_refresh = 1;
     p->constraint_set = TP_CONSTRAINTS_TOTAL_LENGTH;
+    p->line_search = TP_LINESEARCH_UNIT;
+    p->ccd_horizon = 1.5;
     p->coarse_dim = 64;
 }
 
@@ -258,6 +264,7 @@ void tp_destroy(tp_ctx *ctx)
     coarse_free(c);
     gnn_free(c);
     edges_free(c);
+    ccd_free(c);
     void *ptrs[] = {c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_voff,
                     c.plan_energy.d_items, c.plan_diff.d_items, c.plan_apply.d_items, c.plan_energy.d_eslots,
                     c.plan_diff.d_eslots, c.plan_apply.d_eslots, c.d_counter, c.d_recF, c.d_recF2, c.d_recLo,
@@ -448,6 +455,7 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
         if (!edges_chains_ok(c, why)) return fail(ctx, TP_ERR_INVALID_ARG, why);
         CK(edges_init(c));
     }
+    if (prm.line_search == TP_LINESEARCH_ISOTOPY) CK(ccd_init(c));
     CK(cudaDeviceSynchronize());
     return TP_OK;
 }
@@ -466,6 +474,10 @@ tp_status tp_set_params(tp_ctx *ctx, const tp_params *p)
     if (p->constraint_set == TP_CONSTRAINTS_EDGE_LENGTHS && !c.edges) {
         if (!edges_chains_ok(c, why)) return fail(ctx, TP_ERR_INVALID_ARG, why);
         CK(edges_init(c));
+        CK(cudaDeviceSynchronize());
+    }
+    if (p->line_search == TP_LINESEARCH_ISOTOPY && !c.ccd) {
+        CK(ccd_init(c));
         CK(cudaDeviceSynchronize());
     }
     // a new constraint set takes its targets from the next curve solved, as on a fresh context
@@ -560,6 +572,18 @@ tp_status tp_constraints(tp_ctx *ctx, const double *gamma, double *phi, tp_strea
         ctx->c.constraints_set = 1;
     }
     CK(constraints_eval(ctx->c, gamma, 0, phi, s));
+    return TP_OK;
+}
+
+tp_status tp_collision_time(tp_ctx *ctx, const double *gamma, const double *d, double horizon, double *t,
+                            tp_stream stream)
+{
+    if (!ctx || !gamma || !d || !t) return TP_ERR_INVALID_ARG;
+    if (!(horizon > 0.0)) return fail(ctx, TP_ERR_INVALID_ARG, "horizon must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    tp_status st = records(ctx, gamma, 0, s);  // mean edge length (the box padding) and the degenerate-edge check
+    if (st) return st;
+    CK(ccd_time(ctx->c, gamma, d, horizon, t, s));
     return TP_OK;
 }
 
@@ -748,6 +772,15 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
     if (st) return st;
     // per-problem line search state
     std::vector<double> tau(nP, 1.0), acc_tau(nP, 0.0);
+    if (c.prm.line_search == TP_LINESEARCH_ISOTOPY) {
+        // Sec. 5.4: start at 2/3 of the first collision time along gamma - tau d
+        double *tcol = c.d_scal + 64 + 6 * nP;
+        CK(ccd_time(c, gamma, dir, c.prm.ccd_horizon, tcol, s));
+        std::vector<double> ht(nP);
+        CK(cudaMemcpyAsync(ht.data(), tcol, sizeof(double) * nP, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int q = 0; q < nP; ++q) tau[q] = 2.0 / 3.0 * ht[q];
+    }
     std::vector<int> pending(nP, 1), accepted(nP, 0), acc_halv(nP, 0), acc_pit(nP, 0);
     for (int q = 0; q < nP; ++q)
         if (!(hgg[q] > 0.0)) {

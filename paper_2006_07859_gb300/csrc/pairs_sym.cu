@@ -571,7 +571,7 @@ __device__ __forceinline__ void diff_row_out(const double *T, double l, double S
 template <int TPT, bool FAST, bool CHECK, int MODE, bool SRC>
 __device__ __forceinline__ void sym_diff_tile(const Tgt<float> (&tg)[TPT], const bool (&valid)[TPT],
                                               const Tile<PMIX, false> &tl, int cnt, Acc32<PMIX, OP_DIFF> (&a)[TPT],
-                                              Acc64<OP_DIFF> (&A)[TPT], float *sacc, float *scmp,
+                                              Acc64<OP_DIFF> (&A)[TPT], float2 *sac,
                                               const KernelParams &kp)
 {
     const int lane = threadIdx.x & 31;
@@ -614,7 +614,8 @@ __device__ __forceinline__ void sym_diff_tile(const Tgt<float> (&tg)[TPT], const
             if constexpr (SRC) {
 #pragma unroll
                 for (int q = 0; q < kDS; ++q) {
-                    float acc = sacc[q * kTile + j], cmp = scmp[q * kTile + j];
+                    const float2 ac = sac[q * kTile + j];  // (sum, Kahan compensation)
+                    float acc = ac.x, cmp = ac.y;
                     if (anynear) {
                         // FP64 near terms as hi + lo so the compensated sum keeps their digits
                         const double tot = (double)src[q] + srcd[q];
@@ -624,8 +625,7 @@ __device__ __forceinline__ void sym_diff_tile(const Tgt<float> (&tg)[TPT], const
                     } else {
                         kahan_add(acc, cmp, src[q]);
                     }
-                    sacc[q * kTile + j] = acc;
-                    scmp[q * kTile + j] = cmp;
+                    sac[q * kTile + j] = make_float2(acc, cmp);
                 }
             }
         }
@@ -643,9 +643,9 @@ __global__ void __launch_bounds__(kThreads, MB) k_diff_sym(const PairArgs pa)
     __shared__ Tile<PMIX, false> tl;
     __shared__ int s_item;
     __shared__ float s_box[2][kThreads / 32][6];
-    extern __shared__ float dyn[];  // [kSymWarps][kDS][kTile] accumulators, then their compensations
+    extern __shared__ float dyn[];  // [kSymWarps][kDS][kTile] float2 (sum, Kahan compensation) per source
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *sacc = dyn + (size_t)wid * kDS * kTile, *scmp = dyn + (size_t)(kSymWarps + wid) * kDS * kTile;
+    float2 *sac = reinterpret_cast<float2 *>(dyn) + (size_t)wid * kDS * kTile;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(pa.counter, 1);
         __syncthreads();
@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(kThreads, MB) k_diff_sym(const PairArgs pa)
                 tl.lo[threadIdx.x] = pa.recLo[J];
                 box_add(sb, V3<float>{r.a.x, r.a.y, r.a.z}, V3<float>{r.b.x, r.b.y, r.b.z});
             }
-            for (int t = lane; t < kDS * kTile; t += 32) sacc[t] = scmp[t] = 0.f;
+            for (int t = lane; t < kDS * kTile; t += 32) sac[t] = make_float2(0.f, 0.f);
             block_box(sb, s_box[1]);
             const bool check = !(s0 + cnt - 1 < w.nb_lo || s0 > w.nb_hi);
             float g2 = 0.f;
@@ -704,13 +704,13 @@ __global__ void __launch_bounds__(kThreads, MB) k_diff_sym(const PairArgs pa)
             }
             const int mode = g2 < pa.kp.near2f_diff ? 2 : (g2 < pa.kp.mid2f ? 1 : 0);
             if (diag)
-                sym_diff_tile<TPT, FAST, true, 2, false>(tg, valid, tl, cnt, a, A, sacc, scmp, pa.kp);
+                sym_diff_tile<TPT, FAST, true, 2, false>(tg, valid, tl, cnt, a, A, sac, pa.kp);
             else if (check || mode == 2)
-                sym_diff_tile<TPT, FAST, true, 2, true>(tg, valid, tl, cnt, a, A, sacc, scmp, pa.kp);
+                sym_diff_tile<TPT, FAST, true, 2, true>(tg, valid, tl, cnt, a, A, sac, pa.kp);
             else if (mode == 1)
-                sym_diff_tile<TPT, FAST, false, 1, true>(tg, valid, tl, cnt, a, A, sacc, scmp, pa.kp);
+                sym_diff_tile<TPT, FAST, false, 1, true>(tg, valid, tl, cnt, a, A, sac, pa.kp);
             else
-                sym_diff_tile<TPT, FAST, false, 0, true>(tg, valid, tl, cnt, a, A, sacc, scmp, pa.kp);
+                sym_diff_tile<TPT, FAST, false, 0, true>(tg, valid, tl, cnt, a, A, sac, pa.kp);
 #pragma unroll
             for (int k = 0; k < TPT; ++k) {
                 acc_add(A[k], a[k]);
@@ -724,8 +724,8 @@ __global__ void __launch_bounds__(kThreads, MB) k_diff_sym(const PairArgs pa)
                     for (int q = 0; q < kDS; ++q) {
                         double x = 0.0;
                         for (int wv = 0; wv < kSymWarps; ++wv) {
-                            const float *ac = dyn + (size_t)wv * kDS * kTile, *cm = dyn + (size_t)(kSymWarps + wv) * kDS * kTile;
-                            x += (double)ac[q * kTile + threadIdx.x] - (double)cm[q * kTile + threadIdx.x];
+                            const float2 ac = reinterpret_cast<const float2 *>(dyn)[((size_t)wv * kDS + q) * kTile + threadIdx.x];
+                            x += (double)ac.x - (double)ac.y;
                         }
                         v[q] = x;
                     }

@@ -16,6 +16,7 @@ struct SolverState;
 struct CoarseState;
 struct GnnState;
 struct EdgeState;
+struct CcdState;
 
 // Precision of the pair arithmetic.
 enum Prec { P64 = 0, P32 = 1, PMIX = 2 };
@@ -171,6 +172,7 @@ struct Ctx {
     const int *d_skip = nullptr;  // during a CG solve: per-problem converged flags (apply skips them)
     GnnState *gnn = nullptr;      // learned preconditioner term (contexts created with TP_PRECOND_LEARNED)
     EdgeState *edges = nullptr;   // edge-length constraint rows (edges.cu), allocated when first selected
+    CcdState *ccd = nullptr;      // collision-time work list (ccd.cu), allocated when first used
     // captured CG iteration blocks
     cudaStream_t cg_stream = nullptr;
     cudaEvent_t cg_join[2] = {nullptr, nullptr};
@@ -254,6 +256,10 @@ cudaError_t edges_setup(Ctx &c, int which, cudaStream_t s);
 cudaError_t edges_project(Ctx &c, double *v, cudaStream_t s, const int *skip);
 cudaError_t edges_pinv(Ctx &c, double *out, cudaStream_t s);
 cudaError_t edges_phi(Ctx &c, int which, double *phi, cudaStream_t s);
+// first collision time along a direction (ccd.cu)
+cudaError_t ccd_init(Ctx &c);
+void ccd_free(Ctx &c);
+cudaError_t ccd_time(Ctx &c, const double *gamma, const double *d, double T, double *tmin, cudaStream_t s);
 inline bool edge_constraints(const Ctx &c)
 {
     return c.edges && c.prm.constraint_set == TP_CONSTRAINTS_EDGE_LENGTHS;

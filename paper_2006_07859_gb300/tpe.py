@@ -20,6 +20,7 @@ TP_PRECOND_NONE, TP_PRECOND_JACOBI, TP_PRECOND_SPECTRAL, TP_PRECOND_SPECTRAL_RQ,
 TP_PRECOND_LEARNED = 5
 TP_GNN_HIDDEN, TP_GNN_FEATURES = 64, 8
 TP_CONSTRAINTS_TOTAL_LENGTH, TP_CONSTRAINTS_EDGE_LENGTHS = 0, 1
+TP_LINESEARCH_UNIT, TP_LINESEARCH_ISOTOPY = 0, 1
 
 STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ERR_DEGENERATE_EDGE",
                 4: "TP_ERR_NONFINITE", 5: "TP_ERR_NOT_CONVERGED", 6: "TP_ERR_BREAKDOWN", 7: "TP_ERR_LINESEARCH",
@@ -32,7 +33,7 @@ EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp
             "tp_spectral_symbols", "tp_gnn_num_params", "tp_gnn_set_params", "tp_gnn_get_params", "tp_gnn_bind",
             "tp_gnn_forward", "tp_gnn_backward", "tp_gnn_adam", "tp_gnn_g_apply", "tp_gnn_out_grad", "tp_cg_harvest",
             "tp_gnn_prepare_pairs", "tp_gnn_train_step", "tp_autotune", "tp_set_apply_variant",
-            "tp_set_energy_variant", "tp_last_solve", "tp_set_diff_variant"]
+            "tp_set_energy_variant", "tp_last_solve", "tp_set_diff_variant", "tp_collision_time"]
 
 
 class TpParams(ctypes.Structure):
@@ -42,7 +43,8 @@ class TpParams(ctypes.Structure):
                 ("precond", ctypes.c_int), ("armijo_c", ctypes.c_double), ("shrink", ctypes.c_double),
                 ("max_halvings", ctypes.c_int), ("proj_tol", ctypes.c_double), ("proj_maxit", ctypes.c_int),
                 ("independent", ctypes.c_int), ("coarse_dim", ctypes.c_int), ("far_cutoff", ctypes.c_double),
-                ("use_graphs", ctypes.c_int), ("precond_refresh", ctypes.c_int), ("constraint_set", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("precond_refresh", ctypes.c_int), ("constraint_set", ctypes.c_int),
+                ("line_search", ctypes.c_int), ("ccd_horizon", ctypes.c_double)]
 
 
 class TpSolveInfo(ctypes.Structure):
@@ -94,6 +96,7 @@ def library() -> ctypes.CDLL:
         L.tp_set_constraints_from.argtypes = [vp, vp, vp]
         L.tp_constraints.argtypes = [vp, vp, vp, vp]
         L.sobolev_gradient.argtypes = [vp, vp, vp, vp, ctypes.POINTER(TpSolveInfo), vp]
+        L.tp_collision_time.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp]
         L.descent_step.argtypes = [vp, vp, ctypes.POINTER(TpStepInfo), vp]
         L.tp_launch_count.argtypes = [vp]
         L.tp_launch_count.restype = ctypes.c_int64
@@ -273,6 +276,15 @@ def tp_constraints(ctx: Context, gamma, phi=None):
     phi = _new(4 * ctx.n_problems) if phi is None else phi
     ctx._check(library().tp_constraints(ctx.handle, _ptr(gamma), _ptr(phi), _stream()))
     return phi
+
+
+def tp_collision_time(ctx: Context, gamma, d, horizon: float, t=None):
+    """Per problem, the first tau in (0, horizon] at which two disjoint edges of gamma - tau d touch
+    (horizon where none do); a device tensor [n_problems]."""
+    t = _new(ctx.n_problems) if t is None else t
+    ctx._check(library().tp_collision_time(ctx.handle, _ptr(gamma), _ptr(d), ctypes.c_double(horizon), _ptr(t),
+                                           _stream()))
+    return t
 
 
 def sobolev_gradient(ctx: Context, gamma, dE, g=None, allow_not_converged=False):
