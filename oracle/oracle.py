@@ -361,6 +361,82 @@ def projected_cg(apply_abar, P, a, tol=1e-6, maxit=10000, precond=None, x0=None)
     return CGResult(P(y), maxit, np.linalg.norm(r) / nb, False, hist)
 
 
+# ----------------------------------------------------------------------------- penalties (Sec. 8.1)
+#
+# Soft terms added to the tangent-point energy: the total length sum_I l_I; the length difference
+# sum over vertices of degree 2 of (l_I - l_J)^2 (I, J the two edges at the vertex); and the field
+# potential sum_I l_I |T_I x X(x_I)|^2 for a unit vector field X, here X(x) = u / |u| with
+# u = M x + b (a constant field when M = 0; X = 0 where u = 0).
+
+
+@dataclass
+class Penalties:
+    w_length: float = 0.0
+    w_length_diff: float = 0.0
+    w_field: float = 0.0
+    field_M: np.ndarray = field(default_factory=lambda: np.zeros((3, 3)))
+    field_b: np.ndarray = field(default_factory=lambda: np.array([0.0, 0.0, 1.0]))
+
+
+def _field(pen, x):
+    u = pen.field_M @ x + pen.field_b
+    nu = np.linalg.norm(u)
+    return (u / nu, nu) if nu > 0 else (np.zeros(3), 0.0)
+
+
+def penalty_energy(gamma, edges, pen: Penalties):
+    """w_length sum l_I + w_length_diff sum_v (l_I - l_J)^2 + w_field sum_I l_I |T_I x X(x_I)|^2."""
+    g, e = _geom(gamma, edges)
+    ell, T, x = edge_quantities(g, e)
+    E = pen.w_length * ell.sum()
+    inc = [[] for _ in range(g.shape[0])]
+    for I, (a, b) in enumerate(e):
+        inc[a].append(I)
+        inc[b].append(I)
+    for v in range(g.shape[0]):
+        if len(inc[v]) == 2:
+            E += pen.w_length_diff * (ell[inc[v][0]] - ell[inc[v][1]]) ** 2
+    for I in range(len(e)):
+        X, _ = _field(pen, x[I])
+        E += pen.w_field * ell[I] * float(np.cross(T[I], X) @ np.cross(T[I], X))
+    return float(E)
+
+
+def penalty_gradient(gamma, edges, pen: Penalties):
+    """Gradient of penalty_energy with respect to the vertices ([nV, 3]), by the chain rule:
+    d l_I / d g_i2 = T_I = -d l_I / d g_i1, d x_I / d g_ia = Id / 2 and, for the field term with
+    e = g_i2 - g_i1, l (1 - (T.X)^2) = l - (e.X)^2 / l:
+      d/de = T - 2 (T.X) X + (T.X)^2 T,   d/dx = -2 (T.X) M^T (e - (e.X) X) / |u|."""
+    g, e = _geom(gamma, edges)
+    ell, T, x = edge_quantities(g, e)
+    G = np.zeros_like(g)
+    dl = np.full(len(e), pen.w_length)      # dE / d l_I of the length terms
+    inc = [[] for _ in range(g.shape[0])]
+    for I, (a, b) in enumerate(e):
+        inc[a].append(I)
+        inc[b].append(I)
+    for v in range(g.shape[0]):
+        if len(inc[v]) == 2:
+            I, J = inc[v]
+            w = 2.0 * pen.w_length_diff * (ell[I] - ell[J])
+            dl[I] += w
+            dl[J] -= w
+    for I, (a, b) in enumerate(e):
+        G[b] += dl[I] * T[I]
+        G[a] -= dl[I] * T[I]
+        if pen.w_field != 0.0:
+            X, nu = _field(pen, x[I])
+            tx = float(T[I] @ X)
+            de = T[I] - 2.0 * tx * X + tx * tx * T[I]
+            dx = np.zeros(3)
+            if nu > 0:
+                ev = ell[I] * T[I]
+                dx = -2.0 * tx * (pen.field_M.T @ (ev - (ev @ X) * X)) / nu
+            G[b] += pen.w_field * (de + 0.5 * dx)
+            G[a] += pen.w_field * (-de + 0.5 * dx)
+    return G
+
+
 # ----------------------------------------------------------------------------- collision time (Sec. 5.4)
 #
 # The isotopy-safe start of the line search: tau_max is the first tau > 0 at which the moving curve
