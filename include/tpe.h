@@ -23,8 +23,8 @@
  *   - The caller owns every pointer it passes; the context owns its own scratch memory,
  *     allocated once in tp_create and sized for the graph it was created with.  Only
  *     tp_set_params (switching a preconditioner, a constraint set or the line search on),
- *     tp_autotune (a larger work queue) and the first tp_collision_time allocate device memory
- *     after tp_create.
+ *     tp_autotune (a larger work queue), the first tp_set_penalties and the first
+ *     tp_collision_time allocate device memory after tp_create.
  *   - Every call returns a tp_status; nothing aborts or traps.  tp_last_error() gives a
  *     human-readable message for the last failing call on a context.
  *   - A context is not thread-safe; use one context per host thread.
@@ -97,6 +97,16 @@ typedef enum {
                                   (0, ccd_horizon] (ccd_horizon when none comes first); every accepted
                                   step stays below the first collision along the straight path */
 } tp_line_search;
+
+/* Penalties of Sec. 8.1, added by descent_step to the energy and differential of the curve (tp_energy and
+ * tp_differential stay the tangent-point energy alone; tp_penalty evaluates the penalties by themselves). */
+typedef struct {
+    double w_length;       /* weight of the total length sum_I l_I */
+    double w_length_diff;  /* weight of sum over vertices of degree 2 of (l_I - l_J)^2, I, J its two edges */
+    double w_field;        /* weight of the field potential sum_I l_I |T_I x X(x_I)|^2 */
+    double field_M[9];     /* X(x) = u / |u| with u = M x + b (M row-major); X = 0 where u = 0 */
+    double field_b[3];
+} tp_penalties;
 
 /* Shape of the learned preconditioner's edge-graph network (see tp_gnn_set_params). */
 #define TP_GNN_HIDDEN 64
@@ -215,6 +225,14 @@ TPE_API tp_status tp_set_constraints_from(tp_ctx *ctx, const double *gamma, tp_s
  * TP_CONSTRAINTS_EDGE_LENGTHS max_I |l0_I - l_I| over the problem's edges. */
 TPE_API tp_status tp_constraints(tp_ctx *ctx, const double *gamma, double *phi, tp_stream stream);
 
+/* Set (pen non-NULL, copied) or clear (NULL) the penalties the descent step adds (Sec. 8.1).  The first
+ * call allocates their scratch.  Errors: TP_ERR_INVALID_ARG (a non-finite weight). */
+TPE_API tp_status tp_set_penalties(tp_ctx *ctx, const tp_penalties *pen);
+
+/* The penalties alone at gamma: E (DEVICE double [n_problems], may be NULL) and their gradient dE (DEVICE
+ * [nV][3], may be NULL), both overwritten; zeros when none are set. */
+TPE_API tp_status tp_penalty(tp_ctx *ctx, const double *gamma, double *E, double *dE, tp_stream stream);
+
 /* First collision time (Sec. 5.4): t (DEVICE double [n_problems]) receives, per problem, the first
  * tau in (0, horizon] at which two disjoint edges of gamma - tau d touch (segment distance at most
  * 1e-8 times the sum of their lengths), or horizon where none do.  gamma, d: DEVICE [nV][3].  Pairs
@@ -234,7 +252,8 @@ TPE_API tp_status tp_collision_time(tp_ctx *ctx, const double *gamma, const doub
 TPE_API tp_status sobolev_gradient(tp_ctx *ctx, const double *gamma, const double *dE, double *g, tp_solve_info *info,
                            tp_stream stream);
 
-/* One descent step in place on gamma (device [nV][3]) (Sec. 5.4): g~ by sobolev_gradient,
+/* One descent step in place on gamma (device [nV][3]) (Sec. 5.4) on the energy plus the penalties set
+ * by tp_set_penalties: g~ by sobolev_gradient,
  * d = g~ / ||g~||_2, then tau = 1 (or 2/3 of the first collision time with TP_LINESEARCH_ISOTOPY),
  * shrink, ... until the constraint projection of gamma - tau d
  * (Sec. 5.3.2, App. B.3.4) succeeds and the Armijo condition holds.  Synchronises the stream

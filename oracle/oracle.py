@@ -566,6 +566,7 @@ class Params:
     max_halvings: int = 30
     isotopy_safe: bool = False   # Sec. 5.4's first strategy: start at 2/3 of the first collision time
     ccd_horizon: float = 1.5     # collision times are searched in (0, ccd_horizon]
+    penalties: object = None     # Penalties (Sec. 8.1) added to the energy and its differential
 
     @property
     def sigma(self):
@@ -624,8 +625,12 @@ def descent_step(gamma, edges, groups, prm: Params, dense=False, precond_factory
     """One H^s descent step with normalised-gradient backtracking (Sec. 5.4) from tau = 1, or with
     prm.isotopy_safe from 2/3 of the first collision time along gamma - tau d (searched up to
     ccd_horizon; ccd_horizon itself when no collision comes first)."""
-    E0 = energy(gamma, edges, prm.alpha, prm.beta)
+    pen = prm.penalties
+    total = lambda gg: energy(gg, edges, prm.alpha, prm.beta) + (penalty_energy(gg, edges, pen) if pen else 0.0)
+    E0 = total(gamma)
     dE = differential(gamma, edges, prm.alpha, prm.beta)
+    if pen:
+        dE = dE + penalty_gradient(gamma, edges, pen)
     pc = precond_factory(gamma) if precond_factory else None
     g, res = sobolev_gradient(gamma, edges, groups, dE, prm, dense=dense, precond=pc)
     gn = float(np.linalg.norm(g))
@@ -641,7 +646,7 @@ def descent_step(gamma, edges, groups, prm: Params, dense=False, precond_factory
         cand = gamma - tau * d
         cand, pit, ok = constraint_projection(cand, edges, groups, apply_abar, prm, pc)
         if ok:
-            E1 = energy(cand, edges, prm.alpha, prm.beta)
+            E1 = total(cand)
             if E1 <= E0 - prm.armijo_c * tau * slope:
                 return cand, StepInfo(E0, E1, tau, gn, h, pit, res.iters if res else 0, True)
         tau *= prm.shrink

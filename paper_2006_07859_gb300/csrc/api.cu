@@ -265,6 +265,7 @@ void tp_destroy(tp_ctx *ctx)
     gnn_free(c);
     edges_free(c);
     ccd_free(c);
+    penalties_free(c);
     void *ptrs[] = {c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_voff,
                     c.plan_energy.d_items, c.plan_diff.d_items, c.plan_apply.d_items, c.plan_energy.d_eslots,
                     c.plan_diff.d_eslots, c.plan_apply.d_eslots, c.d_counter, c.d_recF, c.d_recF2, c.d_recLo,
@@ -575,6 +576,32 @@ tp_status tp_constraints(tp_ctx *ctx, const double *gamma, double *phi, tp_strea
     return TP_OK;
 }
 
+tp_status tp_set_penalties(tp_ctx *ctx, const tp_penalties *pen)
+{
+    if (!ctx) return TP_ERR_INVALID_ARG;
+    if (pen) {
+        bool ok = std::isfinite(pen->w_length) && std::isfinite(pen->w_length_diff) && std::isfinite(pen->w_field);
+        for (int k = 0; k < 9; ++k) ok = ok && std::isfinite(pen->field_M[k]);
+        for (int k = 0; k < 3; ++k) ok = ok && std::isfinite(pen->field_b[k]);
+        if (!ok) return fail(ctx, TP_ERR_INVALID_ARG, "penalty weights and field must be finite");
+    }
+    CK(penalties_set(ctx->c, pen));
+    return TP_OK;
+}
+
+tp_status tp_penalty(tp_ctx *ctx, const double *gamma, double *E, double *dE, tp_stream stream)
+{
+    if (!ctx || !gamma) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx &c = ctx->c;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    if (E) CK(cudaMemsetAsync(E, 0, sizeof(double) * c.nProb, s));
+    if (dE) CK(cudaMemsetAsync(dE, 0, sizeof(double) * 3 * (size_t)c.nV, s));
+    CK(penalties_add(c, 0, E, dE, s));
+    return TP_OK;
+}
+
 tp_status tp_collision_time(tp_ctx *ctx, const double *gamma, const double *d, double horizon, double *t,
                             tp_stream stream)
 {
@@ -632,12 +659,18 @@ tp_status tp_spectral_symbols(tp_ctx *ctx, int rq, double *out, tp_stream stream
 
 
 // H^s gradient of Eq. 22 by the mean-free route: y0 = A^+ dE, y1 = A^+ C_len^T (two CG solves on the
-// mean-free subspace), then the 4x4 correction (schur_gradient).  Needs the Jacobian of `gamma` in
-// c.d_Cv and the preconditioner set up.  Uses d_t3, d_t4, d_t6 as scratch.
-static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE, double *g, int *iters, double *rr,
+// mean-free subspace), then the 4x4 correction (schur_gradient).  dE first loses C_bary^T lambda_bary,
+// the barycenter multiplier (zero for a translation-invariant dE).  Needs the Jacobian of `gamma` in
+// c.d_Cv and the preconditioner set up.  Uses d_t3, d_t4, d_t5, d_t6 as scratch.
+static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE_in, double *g, int *iters, double *rr,
                                   int *conv, int *bd, cudaStream_t s, int *n_conv = nullptr)
 {
     std::vector<int> flags(c.nProb, 1);
+    {
+        cudaError_t e = bary_rhs(c, dE_in, c.d_t5, s);
+        if (e != cudaSuccess) return e;
+    }
+    const double *dE = c.d_t5;
     if (edge_constraints(c)) {
         // y on null(R) cap N-perp (projector mode 2), then the translation that restores the barycenter
         cudaError_t e = edges_setup(c, 0, s);
@@ -750,6 +783,7 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
     // gradient_solve uses d_t3, d_t4, d_t6 as scratch before dir / z / x are written
     CK(pair_energy(c, gamma, 0, nullptr, E0, s));
     CK(pair_diff(c, gamma, 0, dE, s));
+    CK(penalties_add(c, 0, E0, dE, s));  // Sec. 8.1 penalties, if any
     // g~ = projected H^s gradient
     CK(constraints_jacobian(c, 0, s));
     st = precond_setup(ctx, gamma, s);
@@ -851,6 +885,7 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
         st = records(ctx, c.d_gam, 1, s);
         if (st) return st;
         CK(pair_energy(c, c.d_gam, 1, nullptr, E1, s));
+        CK(penalties_add(c, 1, E1, nullptr, s));
         std::vector<double> e1(nP);
         CK(cudaMemcpyAsync(e1.data(), E1, sizeof(double) * nP, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));

@@ -442,14 +442,25 @@ cudaError_t vec_scale_dev(Ctx &c, const double *x, const double *num_dev, int in
     return cudaGetLastError();
 }
 
-cudaError_t sum_problems(Ctx &c, const double *x, int per_vertex, double *out, cudaStream_t s)
+// out[q] (+)= sum of x over problem q's vertices (per_vertex) or edges, in the fixed chunk order.
+__global__ void k_sum_problems(RedArgs ra, const double *__restrict__ x, double *__restrict__ out, int add)
 {
-    (void)c;
-    (void)x;
-    (void)per_vertex;
-    (void)out;
-    (void)s;
-    return cudaSuccess;
+    double s[1] = {0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) s[0] += x[i];
+    if (reduce_phase<1>(s, ra))
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) out[q] = (add ? out[q] : 0.0) + ra.sums[q];
+}
+
+cudaError_t sum_problems(Ctx &c, const double *x, int per_vertex, double *out, cudaStream_t s, int add)
+{
+    SolverState &st = S(c);
+    if (per_vertex)
+        k_sum_problems<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 0), x, out, add);
+    else
+        k_sum_problems<<<st.e_n, kRedThreads, 0, s>>>(eargs(c, 0), x, out, add);
+    c.launches++;
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------- preconditioners
@@ -1035,6 +1046,51 @@ cudaError_t schur_gradient(Ctx &c, const double *y0, const double *y1, double *g
     k_schur_red<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_Cv, nullptr, g, red_out);
     k_schur_shift<<<nb, 256, 0, s>>>(c.nV, red_out, nullptr, 0.0, c.d_vprob, g);
     c.launches += 4;
+    return cudaGetLastError();
+}
+
+// Barycenter multiplier of Eq. 22: translations are in null(A-bar) and null(C_len), null(C_edges), so
+// N^T (A-bar g + C^T lambda) = N^T dE leaves (C_bary N)^T lambda_bary = N^T dE per problem.  rhs =
+// dE - C_bary^T lambda_bary is then consistent on the mean-free subspace.  lambda_bary = 0 when dE is
+// translation invariant (the tangent-point differential); penalties with a non-constant field are not.
+__global__ void k_bary_red(RedArgs ra, const double *__restrict__ C, const double *__restrict__ dE,
+                           double *__restrict__ out)
+{
+    double s[12] = {0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int v = lo + threadIdx.x; v < hi; v += blockDim.x) {
+        const double *cv = C + (size_t)v * 12;
+        for (int j = 0; j < 3; ++j) {
+            s[j] += dE[3 * (size_t)v + j];
+            for (int k = 0; k < 3; ++k) s[3 + 3 * k + j] += cv[3 * k + j];
+        }
+    }
+    if (reduce_phase<12>(s, ra))
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x)
+            for (int k = 0; k < 12; ++k) out[12 * q + k] = ra.sums[12 * q + k];
+}
+
+__global__ void k_bary_rhs(int nV, const double *__restrict__ red, const double *__restrict__ C,
+                           const double *__restrict__ dE, const int *__restrict__ vprob, double *__restrict__ rhs)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    const double *r = red + 12 * vprob[v];
+    double Mt[9], lam[3];
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) Mt[3 * j + k] = r[3 + 3 * k + j];  // (C_bary N)^T
+    solve3(Mt, r, lam);
+    const double *cv = C + (size_t)v * 12;
+    for (int j = 0; j < 3; ++j)
+        rhs[3 * (size_t)v + j] = dE[3 * (size_t)v + j] - (lam[0] * cv[j] + lam[1] * cv[3 + j] + lam[2] * cv[6 + j]);
+}
+
+cudaError_t bary_rhs(Ctx &c, const double *dE, double *rhs, cudaStream_t s)
+{
+    SolverState &st = S(c);
+    k_bary_red<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_Cv, dE, c.d_red);
+    k_bary_rhs<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_red, c.d_Cv, dE, c.d_vprob, rhs);
+    c.launches += 2;
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ struct CoarseState;
 struct GnnState;
 struct EdgeState;
 struct CcdState;
+struct PenState;
 
 // Precision of the pair arithmetic.
 enum Prec { P64 = 0, P32 = 1, PMIX = 2 };
@@ -173,6 +174,7 @@ struct Ctx {
     GnnState *gnn = nullptr;      // learned preconditioner term (contexts created with TP_PRECOND_LEARNED)
     EdgeState *edges = nullptr;   // edge-length constraint rows (edges.cu), allocated when first selected
     CcdState *ccd = nullptr;      // collision-time work list (ccd.cu), allocated when first used
+    PenState *pen = nullptr;      // penalties of Sec. 8.1 (penalties.cu), allocated by tp_set_penalties
     // captured CG iteration blocks
     cudaStream_t cg_stream = nullptr;
     cudaEvent_t cg_join[2] = {nullptr, nullptr};
@@ -247,6 +249,7 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
                      int proj_mode, int *conv_flags = nullptr);
 cudaError_t project_mean(Ctx &c, double *v, cudaStream_t s, const int *skip);
 cudaError_t schur_shift(Ctx &c, double *out, const double *phi, double phi_scale, cudaStream_t s);
+cudaError_t bary_rhs(Ctx &c, const double *dE, double *rhs, cudaStream_t s);
 // edge-length constraints (edges.cu)
 bool edges_chains_ok(const Ctx &c, std::string &why);
 cudaError_t edges_init(Ctx &c);
@@ -256,6 +259,11 @@ cudaError_t edges_setup(Ctx &c, int which, cudaStream_t s);
 cudaError_t edges_project(Ctx &c, double *v, cudaStream_t s, const int *skip);
 cudaError_t edges_pinv(Ctx &c, double *out, cudaStream_t s);
 cudaError_t edges_phi(Ctx &c, int which, double *phi, cudaStream_t s);
+// penalties of Sec. 8.1 (penalties.cu)
+cudaError_t penalties_set(Ctx &c, const tp_penalties *p);
+void penalties_free(Ctx &c);
+bool penalties_active(const Ctx &c);
+cudaError_t penalties_add(Ctx &c, int which, double *E, double *dE, cudaStream_t s);
 // first collision time along a direction (ccd.cu)
 cudaError_t ccd_init(Ctx &c);
 void ccd_free(Ctx &c);
@@ -272,7 +280,8 @@ cudaError_t vec_dot(Ctx &c, const double *a, const double *b, double *out_dev, c
 cudaError_t vec_axpby(Ctx &c, double a, const double *x, double b, const double *y, double *out, cudaStream_t s);
 cudaError_t vec_scale_dev(Ctx &c, const double *x, const double *num_dev, int invert_sqrt, double *out,
                           cudaStream_t s);
-cudaError_t sum_problems(Ctx &c, const double *per_edge_or_vertex, int per_vertex, double *out, cudaStream_t s);
+cudaError_t sum_problems(Ctx &c, const double *per_edge_or_vertex, int per_vertex, double *out, cudaStream_t s,
+                         int add = 0);
 
 // ------------------------------------------------------------------ learned preconditioner (gnn.cu)
 int gnn_num_params();

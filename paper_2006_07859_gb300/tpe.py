@@ -33,7 +33,8 @@ EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp
             "tp_spectral_symbols", "tp_gnn_num_params", "tp_gnn_set_params", "tp_gnn_get_params", "tp_gnn_bind",
             "tp_gnn_forward", "tp_gnn_backward", "tp_gnn_adam", "tp_gnn_g_apply", "tp_gnn_out_grad", "tp_cg_harvest",
             "tp_gnn_prepare_pairs", "tp_gnn_train_step", "tp_autotune", "tp_set_apply_variant",
-            "tp_set_energy_variant", "tp_last_solve", "tp_set_diff_variant", "tp_collision_time"]
+            "tp_set_energy_variant", "tp_last_solve", "tp_set_diff_variant", "tp_collision_time",
+            "tp_set_penalties", "tp_penalty"]
 
 
 class TpParams(ctypes.Structure):
@@ -45,6 +46,11 @@ class TpParams(ctypes.Structure):
                 ("independent", ctypes.c_int), ("coarse_dim", ctypes.c_int), ("far_cutoff", ctypes.c_double),
                 ("use_graphs", ctypes.c_int), ("precond_refresh", ctypes.c_int), ("constraint_set", ctypes.c_int),
                 ("line_search", ctypes.c_int), ("ccd_horizon", ctypes.c_double)]
+
+
+class TpPenalties(ctypes.Structure):
+    _fields_ = [("w_length", ctypes.c_double), ("w_length_diff", ctypes.c_double), ("w_field", ctypes.c_double),
+                ("field_M", ctypes.c_double * 9), ("field_b", ctypes.c_double * 3)]
 
 
 class TpSolveInfo(ctypes.Structure):
@@ -97,6 +103,8 @@ def library() -> ctypes.CDLL:
         L.tp_constraints.argtypes = [vp, vp, vp, vp]
         L.sobolev_gradient.argtypes = [vp, vp, vp, vp, ctypes.POINTER(TpSolveInfo), vp]
         L.tp_collision_time.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp]
+        L.tp_set_penalties.argtypes = [vp, ctypes.POINTER(TpPenalties)]
+        L.tp_penalty.argtypes = [vp, vp, vp, vp, vp]
         L.descent_step.argtypes = [vp, vp, ctypes.POINTER(TpStepInfo), vp]
         L.tp_launch_count.argtypes = [vp]
         L.tp_launch_count.restype = ctypes.c_int64
@@ -285,6 +293,32 @@ def tp_collision_time(ctx: Context, gamma, d, horizon: float, t=None):
     ctx._check(library().tp_collision_time(ctx.handle, _ptr(gamma), _ptr(d), ctypes.c_double(horizon), _ptr(t),
                                            _stream()))
     return t
+
+
+def tp_set_penalties(ctx: Context, w_length=0.0, w_length_diff=0.0, w_field=0.0, field_M=None, field_b=None,
+                     clear=False):
+    """Penalties of Sec. 8.1 that descent_step adds to the energy (clear=True removes them); the field is
+    X(x) = (M x + b) / |M x + b| (M 3 x 3, b 3-vector; default a constant field along z)."""
+    if clear:
+        ctx._check(library().tp_set_penalties(ctx.handle, None))
+        return
+    p = TpPenalties()
+    p.w_length, p.w_length_diff, p.w_field = w_length, w_length_diff, w_field
+    M = np.zeros(9) if field_M is None else np.asarray(field_M, dtype=np.float64).reshape(9)
+    b = np.array([0.0, 0.0, 1.0]) if field_b is None else np.asarray(field_b, dtype=np.float64).reshape(3)
+    for k in range(9):
+        p.field_M[k] = float(M[k])
+    for k in range(3):
+        p.field_b[k] = float(b[k])
+    ctx._check(library().tp_set_penalties(ctx.handle, ctypes.byref(p)))
+
+
+def tp_penalty(ctx: Context, gamma):
+    """(E [n_problems], dE [nV, 3]) of the penalties alone at gamma (device tensors)."""
+    E = _new(ctx.n_problems)
+    dE = _new((ctx.n_vertices, 3))
+    ctx._check(library().tp_penalty(ctx.handle, _ptr(gamma), _ptr(E), _ptr(dE), _stream()))
+    return E, dE
 
 
 def sobolev_gradient(ctx: Context, gamma, dE, g=None, allow_not_converged=False):
