@@ -39,9 +39,9 @@ MUFU_PER_PAIR = {"energy": 8, "diff": 8, "apply": 8}
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_NOMINAL = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6   # FLOP/s at the maximum SM clock
 L2_BYTES = 129 * 2 ** 20
-# DRAM bytes (read + write) of one apply launch on the 8 x 4096 workload, by targets per thread, from an
-# ncu capture of the current kernel (profiles/apply_pair_kernel_knots8x4096.md); other variants: unknown
-APPLY_TRAFFIC_BYTES = {2: 5.07e6}
+# DRAM bytes (read + write) of one apply launch on the 8 x 4096 workload, by (pass, targets per thread),
+# from ncu captures of the current kernels (profiles/apply_pair_kernel_knots8x4096.md); others: unknown
+APPLY_TRAFFIC_BYTES = {("gather", 2): 5.07e6}
 
 
 def parse():
@@ -596,6 +596,10 @@ def run_ours(args, rank, world, local_rank):
         rates, cores = oracle_rates(curves, args.cpu_seconds)
         cpu_val = oracle_step_rate(rates, pairs, passes)
     kernel_share = {k: prof[k][0] / 1e3 / total for k in prof}
+    sym_apply = tuned["tpt"].get("apply_symmetric", 0)
+    apply_variant = ("symmetric", sym_apply) if sym_apply else ("gather", tuned["tpt"]["apply"])
+    apply_kernel = (f"k_pairs_sym<TPT={sym_apply}> (symmetric Sobolev apply)" if sym_apply
+                    else f"k_pairs<PMIX, OP_APPLY, TPT={tuned['tpt']['apply']}> (Sobolev apply)")
     line = {
         "metric": "H^s descent steps/s at 262K edges; pair interactions/s vs FP32 roofline", "value": value, "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps,
@@ -611,12 +615,11 @@ def run_ours(args, rank, world, local_rank):
         "passes_per_step": passes,
         "kernel_time_share": kernel_share,
         "step_info": step_infos[-1],
-        "roofline": {"kernel": "k_pairs<PMIX, OP_APPLY> (Sobolev apply)", "bound": "alu",
+        "roofline": {"kernel": apply_kernel, "bound": "alu",
                      "achieved": achieved / 1e12 if achieved else None,
                      "peak": FP32_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / FP32_PEAK_NOMINAL if achieved else None,
-                     "traffic": (APPLY_TRAFFIC_BYTES.get(tuned["tpt"]["apply"])
-                                 if args.workload == "knots8x4096" else None),
+                     "traffic": (APPLY_TRAFFIC_BYTES.get(apply_variant) if args.workload == "knots8x4096" else None),
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "flop_per_pair": FLOP_PER_PAIR["apply"], "launches": n_a, "avg_launch_ms": avg_s * 1e3,
                      "peak_note": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal units and max clock)",
