@@ -266,7 +266,7 @@ void tp_destroy(tp_ctx *ctx)
     edges_free(c);
     ccd_free(c);
     penalties_free(c);
-    void *ptrs[] = {c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_voff,
+    void *ptrs[] = {c.d_esum, c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_voff,
                     c.plan_energy.d_items, c.plan_diff.d_items, c.plan_apply.d_items, c.plan_energy.d_eslots,
                     c.plan_diff.d_eslots, c.plan_apply.d_eslots, c.d_counter, c.d_recF, c.d_recF2, c.d_recLo,
                     c.d_recLo2, c.d_recD, c.d_recD2, c.d_ellw[0], c.d_ellw[1], c.d_Tw[0], c.d_Tw[1], c.d_xw[0],
@@ -426,6 +426,7 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
     c.part_elems = (size_t)ms * std::max(1, nE) * 6;
     CK(dalloc(&c.d_part, c.part_elems));
     CK(dalloc(&c.d_rows, nE));
+    CK(dalloc(&c.d_esum, 6 * (size_t)nE));
     CK(dalloc(&c.d_x0L0, 4 * (size_t)c.nProb));
     CK(dalloc(&c.d_Cv, 12 * (size_t)nV));
     CK(dalloc(&c.d_G, 16 * (size_t)c.nProb));

@@ -359,6 +359,70 @@ __global__ void k_vertex_gather(int nV, int nE, const int *__restrict__ inc_ptr,
     }
 }
 
+// Two-stage gather for many slots: each edge's slots are summed once (k_edge_slots), then every vertex
+// combines its edges' sums (k_vertex_from_edges).  The one-stage gather reads an edge's slots once per
+// endpoint, twice the traffic when an edge has tens of slots (the symmetric passes on long curves).
+template <int OP>
+__global__ void k_edge_slots(int nE, const int *__restrict__ eslots, const double *__restrict__ part,
+                             double *__restrict__ esum)
+{
+    constexpr int W = OP == OP_DIAG ? 1 : 6;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nE) return;
+    double o[W];
+    for (int c = 0; c < W; ++c) o[c] = 0.0;
+    for (int q = 0; q < eslots[I]; ++q) {
+        const double *p = part + ((size_t)q * nE + I) * W;
+        for (int c = 0; c < W; ++c) o[c] += p[c];
+    }
+    for (int c = 0; c < W; ++c) esum[(size_t)I * W + c] = o[c];
+}
+
+template <int OP>
+__global__ void k_vertex_from_edges(int nV, const int *__restrict__ inc_ptr, const int *__restrict__ inc,
+                                    const double *__restrict__ esum, double *__restrict__ out)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    double o[3] = {0, 0, 0};
+    for (int k = inc_ptr[v]; k < inc_ptr[v + 1]; ++k) {
+        const int I = inc[k] >> 1, sl = inc[k] & 1;
+        if constexpr (OP == OP_DIAG) {
+            o[0] += esum[I];
+        } else {
+            const double *p = esum + 6 * (size_t)I;
+            if constexpr (OP == OP_DIFF) {
+                for (int c = 0; c < 3; ++c) o[c] += p[3 * sl + c];
+            } else {
+                const double sg = sl ? 1.0 : -1.0;
+                for (int c = 0; c < 3; ++c) o[c] += sg * p[c] + p[3 + c];
+            }
+        }
+    }
+    if constexpr (OP == OP_DIAG) {
+        out[v] = o[0];
+    } else {
+        for (int c = 0; c < 3; ++c) out[3 * v + c] = o[c];
+    }
+}
+
+// Sum the partial slots of a pass into the per-vertex output, in one or two stages by slot count.
+template <int OP>
+static cudaError_t gather_slots(Ctx &c, const Ctx::Plan &pl, double *out, cudaStream_t s)
+{
+    if (c.nV == 0) return cudaSuccess;
+    if (pl.max_slots > 2 && c.d_esum) {
+        k_edge_slots<OP><<<(c.nE + 255) / 256, 256, 0, s>>>(c.nE, pl.d_eslots, c.d_part, c.d_esum);
+        k_vertex_from_edges<OP><<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_inc_ptr, c.d_inc, c.d_esum, out);
+        c.launches += 2;
+    } else {
+        k_vertex_gather<OP><<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.nE, c.d_inc_ptr, c.d_inc, pl.d_eslots, c.d_part,
+                                                              out);
+        c.launches++;
+    }
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------- planning
 
 // Build the (target block, source chunk) queue of one pass.  Items of big problems come first
@@ -831,12 +895,7 @@ cudaError_t pair_diff(Ctx &c, const double *gamma, int which, double *dE, cudaSt
         TPE_CHECK(sym_diff_pass(c, which, gamma, s));
     else
         TPE_CHECK(run_pairs<OP_DIFF>(c, which, gamma, nullptr, s));
-    if (c.nV > 0) {
-        k_vertex_gather<OP_DIFF><<<(c.nV + 255) / 256, 256, 0, s>>>(
-            c.nV, c.nE, c.d_inc_ptr, c.d_inc, sym ? c.plan_sym_d.d_eslots : c.plan_diff.d_eslots, c.d_part, dE);
-        c.launches++;
-    }
-    return cudaGetLastError();
+    return gather_slots<OP_DIFF>(c, sym ? c.plan_sym_d : c.plan_diff, dE, s);
 }
 
 cudaError_t pair_apply(Ctx &c, const double *gamma_geom, int which, const double *u, double *Au, cudaStream_t s)
@@ -847,23 +906,13 @@ cudaError_t pair_apply(Ctx &c, const double *gamma_geom, int which, const double
         TPE_CHECK(sym_apply_pass(c, which, gamma_geom, u, s));
     else
         TPE_CHECK(run_pairs<OP_APPLY>(c, which, gamma_geom, u, s));
-    if (c.nV > 0) {
-        k_vertex_gather<OP_APPLY><<<(c.nV + 255) / 256, 256, 0, s>>>(
-            c.nV, c.nE, c.d_inc_ptr, c.d_inc, sym ? c.plan_sym.d_eslots : c.plan_apply.d_eslots, c.d_part, Au);
-        c.launches++;
-    }
-    return cudaGetLastError();
+    return gather_slots<OP_APPLY>(c, sym ? c.plan_sym : c.plan_apply, Au, s);
 }
 
 cudaError_t pair_diag(Ctx &c, const double *gamma_geom, int which, double *diag, cudaStream_t s)
 {
     TPE_CHECK(run_pairs<OP_DIAG>(c, which, gamma_geom, nullptr, s));
-    if (c.nV > 0) {
-        k_vertex_gather<OP_DIAG><<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.nE, c.d_inc_ptr, c.d_inc, c.plan_apply.d_eslots,
-                                                                    c.d_part, diag);
-        c.launches++;
-    }
-    return cudaGetLastError();
+    return gather_slots<OP_DIAG>(c, c.plan_apply, diag, s);
 }
 
 }  // namespace tpe

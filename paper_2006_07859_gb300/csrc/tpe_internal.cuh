@@ -145,6 +145,7 @@ struct Ctx {
     double *d_part = nullptr;
     size_t part_elems = 0;
     double *d_rows = nullptr;  // [nE]
+    double *d_esum = nullptr;  // [nE][6] per-edge slot sums of the two-stage gather
     // constraints: per problem x0 (3) and L0
     double *d_x0L0 = nullptr;  // [nProb][4]
     int constraints_set = 0;
