@@ -545,19 +545,32 @@ __global__ void k_cg_init(RedArgs ra, const double *__restrict__ r, const double
     }
 }
 
-// alpha = rz / (p.q) per active problem.
+// alpha = rz / (p.q) per active problem.  fuse: q is not yet mean-free; its per-problem mean mq is
+// taken here and p.(q - mq) = p.q - mq.sum(p) is used (the mean-free projector folded into the CG
+// kernels: k_cg_update subtracts mq).
 __global__ void k_cg_alpha(RedArgs ra, const double *__restrict__ p, const double *__restrict__ q_,
-                           CGScalars *__restrict__ cg, int *__restrict__ done)
+                           CGScalars *__restrict__ cg, int *__restrict__ done, const int *__restrict__ prob_v,
+                           int fuse)
 {
-    double s[1] = {0};
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
     int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
-        s[0] += p[3 * i] * q_[3 * i] + p[3 * i + 1] * q_[3 * i + 1] + p[3 * i + 2] * q_[3 * i + 2];
-    if (reduce_phase<1>(s, ra)) {
+        for (int k = 0; k < 3; ++k) {
+            s[0] += p[3 * i + k] * q_[3 * i + k];
+            s[1 + k] += q_[3 * i + k];
+            s[4 + k] += p[3 * i + k];
+        }
+    if (reduce_phase<7>(s, ra)) {
         for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
             CGScalars &g = cg[q];
             if (g.done) continue;
-            double pq = ra.sums[q];
+            const double *S7 = ra.sums + 7 * q;
+            double pq = S7[0];
+            const double n = (double)(prob_v[q + 1] - prob_v[q]);
+            for (int k = 0; k < 3; ++k) {
+                g.mq[k] = (fuse && n > 0) ? S7[1 + k] / n : 0.0;
+                pq -= g.mq[k] * S7[4 + k];
+            }
             g.pq = pq;
             if (!(pq > 0.0)) {
                 g.breakdown = 1;
@@ -584,7 +597,7 @@ __global__ void k_cg_update(RedArgs ra, const int *__restrict__ vprob, const dou
         double a = cg[pr].alpha;
         for (int k = 0; k < 3; ++k) {
             y[3 * i + k] += a * p[3 * i + k];
-            double rv = r[3 * i + k] - a * q_[3 * i + k];
+            double rv = r[3 * i + k] - a * (q_[3 * i + k] - cg[pr].mq[k]);
             r[3 * i + k] = rv;
             s[0] += rv * rv;
         }
@@ -610,19 +623,31 @@ __global__ void k_cg_update(RedArgs ra, const int *__restrict__ vprob, const dou
     }
 }
 
-// rz_new = r.z; beta = rz_new / rz; rz = rz_new (active problems)
+// rz_new = r.z; beta = rz_new / rz; rz = rz_new (active problems).  fuse: z is not yet mean-free; its
+// mean mz is taken here, r.(z - mz) = r.z - mz.sum(r) is used, and k_cg_p subtracts mz.
 __global__ void k_cg_beta(RedArgs ra, const double *__restrict__ r, const double *__restrict__ z,
-                          CGScalars *__restrict__ cg, const int *__restrict__ done)
+                          CGScalars *__restrict__ cg, const int *__restrict__ done, const int *__restrict__ prob_v,
+                          int fuse)
 {
-    double s[1] = {0};
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
     int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
-        s[0] += r[3 * i] * z[3 * i] + r[3 * i + 1] * z[3 * i + 1] + r[3 * i + 2] * z[3 * i + 2];
-    if (reduce_phase<1>(s, ra)) {
+        for (int k = 0; k < 3; ++k) {
+            s[0] += r[3 * i + k] * z[3 * i + k];
+            s[1 + k] += z[3 * i + k];
+            s[4 + k] += r[3 * i + k];
+        }
+    if (reduce_phase<7>(s, ra)) {
         for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
             CGScalars &g = cg[q];
             if (g.done) continue;
-            double rzn = ra.sums[q];
+            const double *S7 = ra.sums + 7 * q;
+            double rzn = S7[0];
+            const double n = (double)(prob_v[q + 1] - prob_v[q]);
+            for (int k = 0; k < 3; ++k) {
+                g.mz[k] = (fuse && n > 0) ? S7[1 + k] / n : 0.0;
+                rzn -= g.mz[k] * S7[4 + k];
+            }
             g.beta = g.rz != 0.0 ? rzn / g.rz : 0.0;
             g.rz = rzn;
         }
@@ -638,7 +663,7 @@ __global__ void k_cg_p(int nV, const int *__restrict__ vprob, const double *__re
     int q = vprob[i];
     if (done[q]) return;
     double b = cg[q].beta;
-    for (int k = 0; k < 3; ++k) p[3 * i + k] = z[3 * i + k] + b * p[3 * i + k];
+    for (int k = 0; k < 3; ++k) p[3 * i + k] = (z[3 * i + k] - cg[q].mz[k]) + b * p[3 * i + k];
 }
 
 // Relative residual per problem: out[q] = sqrt(|r_true|^2 / |P rhs|^2)
@@ -667,6 +692,15 @@ static cudaError_t projector(Ctx &c, int mode, double *v, cudaStream_t s, const 
         return edges_project(c, v, s, skip);
     }
     return mode ? project_mean(c, v, s, skip) : project(c, v, s, skip);
+}
+
+// What the CG iteration still applies outside its kernels: mode 0 the whole constraint projector, mode 1
+// nothing, mode 2 the edge rows (their projector commutes with the mean removal).
+static cudaError_t projector_rest(Ctx &c, int mode, double *v, cudaStream_t s, const int *skip)
+{
+    if (mode == 0) return project(c, v, s, skip);
+    if (mode == 2) return edges_project(c, v, s, skip);
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------------- CUDA graphs of CG blocks
@@ -798,6 +832,7 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
     c.launches++;
     const double tol2 = rtol * rtol;
     const int every = std::max(1, c.prm.cg_check_every);
+    const int fuse = proj_mode != 0;  // projector modes 1, 2: their mean removal runs inside the CG kernels
     int it = 0;
     int *h_active = c.h_pinned_i;
     // one CG iteration enqueued on stream ss
@@ -807,15 +842,16 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
         cudaError_t ea = pair_apply(c, gamma_geom, which, p, q, ss);
         c.d_skip = nullptr;
         TPE_CHECK(ea);
-        TPE_CHECK(projector(c, proj_mode, q, ss, st.done));
-        k_cg_alpha<<<st.v_n, kRedThreads, 0, ss>>>(vargs(c, 5), p, q, c.d_cg, st.done);
+        // the mean-free part of the projector is folded into the CG kernels (fuse); the rest runs here
+        TPE_CHECK(projector_rest(c, proj_mode, q, ss, st.done));
+        k_cg_alpha<<<st.v_n, kRedThreads, 0, ss>>>(vargs(c, 5), p, q, c.d_cg, st.done, c.d_prob_v, fuse);
         k_cg_update<<<st.v_n, kRedThreads, 0, ss>>>(vargs(c, 6), c.d_vprob, p, q, y, r, c.d_cg, st.done, tol2,
                                                     st.active);
         c.launches += 2;
         TPE_CHECK(precond_apply(c, r, z, ss, st.done));
-        if (c.prm.precond != TP_PRECOND_NONE) TPE_CHECK(projector(c, proj_mode, z, ss, st.done));
+        if (c.prm.precond != TP_PRECOND_NONE) TPE_CHECK(projector_rest(c, proj_mode, z, ss, st.done));
         k_cg_beta<<<st.v_n, kRedThreads, 0, ss>>>(vargs(c, 7), r, c.prm.precond != TP_PRECOND_NONE ? z : r,
-                                                  c.d_cg, st.done);
+                                                  c.d_cg, st.done, c.d_prob_v, fuse);
         k_cg_p<<<nb, 256, 0, ss>>>(c.nV, c.d_vprob, c.prm.precond != TP_PRECOND_NONE ? z : r, p, c.d_cg, st.done);
         c.launches += 2;
         return cudaGetLastError();

@@ -75,6 +75,7 @@ struct KernelParams {
 // Device-side scalars of one CG solve (all FP64) - one block per problem.
 struct CGScalars {
     double rz, rz_new, pq, alpha, beta, bnorm2, rnorm2;
+    double mq[3], mz[3];  // per-component means of q = A-bar p and z = M^-1 r (mean-free projector fused)
     int done, breakdown, iters;
 };
 
