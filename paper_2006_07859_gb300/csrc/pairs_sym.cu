@@ -89,7 +89,7 @@ __device__ __forceinline__ void pair_apply_both(const Tgt<float> &t, const Src<P
 template <int TPT, bool FAST, bool CHECK, bool DF, bool SRC>
 __device__ __forceinline__ void sym_tile(const Tgt<float> (&tg)[TPT], const UVal<float> (&tu)[TPT],
                                          const bool (&valid)[TPT], const Tile<PMIX, true> &tl, int cnt,
-                                         Acc32<PMIX, OP_APPLY> (&a)[TPT], float (*sacc)[kTile], float (*scmp)[kTile],
+                                         Acc32<PMIX, OP_APPLY> (&a)[TPT], float2 (*sac)[kTile],
                                          const KernelParams &kp)
 {
     const int lane = threadIdx.x & 31;
@@ -119,15 +119,11 @@ __device__ __forceinline__ void sym_tile(const Tgt<float> (&tg)[TPT], const UVal
             if constexpr (SRC) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    float acc = sacc[q][j], cmp = scmp[q][j];
-                    kahan_add(acc, cmp, hs[q]);
-                    sacc[q][j] = acc;
-                    scmp[q][j] = cmp;
-                    acc = sacc[3 + q][j];
-                    cmp = scmp[3 + q][j];
-                    kahan_add(acc, cmp, ls[q]);
-                    sacc[3 + q][j] = acc;
-                    scmp[3 + q][j] = cmp;
+                    float2 h = sac[q][j], l = sac[3 + q][j];  // (sum, Kahan compensation)
+                    kahan_add(h.x, h.y, hs[q]);
+                    kahan_add(l.x, l.y, ls[q]);
+                    sac[q][j] = h;
+                    sac[3 + q][j] = l;
                 }
             }
         }
@@ -139,7 +135,7 @@ template <int TPT, bool FAST>
 __global__ void __launch_bounds__(kThreads, 2) k_pairs_sym(const PairArgs pa)
 {
     __shared__ Tile<PMIX, true> tl;
-    __shared__ float sacc[kSymWarps][6][kTile], scmp[kSymWarps][6][kTile];
+    __shared__ float2 sac[kSymWarps][6][kTile];  // per warp and source: (sum, Kahan compensation)
     __shared__ int s_item;
     __shared__ float s_box[2][kThreads / 32][6];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -197,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs_sym(const PairArgs pa)
                 box_add(sb, V3<float>{r.a.x, r.a.y, r.a.z}, V3<float>{r.b.x, r.b.y, r.b.z});
             }
             for (int t = lane; t < kTile; t += 32)
-                for (int q = 0; q < 6; ++q) sacc[wid][q][t] = scmp[wid][q][t] = 0.f;
+                for (int q = 0; q < 6; ++q) sac[wid][q][t] = make_float2(0.f, 0.f);
             block_box(sb, s_box[1]);  // contains the barrier that publishes the tile
             const bool check = !(s0 + cnt - 1 < w.nb_lo || s0 > w.nb_hi);
             float g2 = 0.f;
@@ -207,13 +203,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs_sym(const PairArgs pa)
             }
             const bool far = g2 >= pa.kp.mid2f;
             if (diag) {
-                sym_tile<TPT, FAST, true, true, false>(tg, tu, valid, tl, cnt, a, sacc[wid], scmp[wid], pa.kp);
+                sym_tile<TPT, FAST, true, true, false>(tg, tu, valid, tl, cnt, a, sac[wid], pa.kp);
             } else if (check) {
-                sym_tile<TPT, FAST, true, true, true>(tg, tu, valid, tl, cnt, a, sacc[wid], scmp[wid], pa.kp);
+                sym_tile<TPT, FAST, true, true, true>(tg, tu, valid, tl, cnt, a, sac[wid], pa.kp);
             } else if (!far) {
-                sym_tile<TPT, FAST, false, true, true>(tg, tu, valid, tl, cnt, a, sacc[wid], scmp[wid], pa.kp);
+                sym_tile<TPT, FAST, false, true, true>(tg, tu, valid, tl, cnt, a, sac[wid], pa.kp);
             } else {
-                sym_tile<TPT, FAST, false, false, true>(tg, tu, valid, tl, cnt, a, sacc[wid], scmp[wid], pa.kp);
+                sym_tile<TPT, FAST, false, false, true>(tg, tu, valid, tl, cnt, a, sac[wid], pa.kp);
             }
             // fold the target tile accumulators into FP64
 #pragma unroll
@@ -229,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_pairs_sym(const PairArgs pa)
                     for (int q = 0; q < 6; ++q) {
                         double x = 0.0;
                         for (int wv = 0; wv < kSymWarps; ++wv)
-                            x += (double)sacc[wv][q][threadIdx.x] - (double)scmp[wv][q][threadIdx.x];
+                            x += (double)sac[wv][q][threadIdx.x].x - (double)sac[wv][q][threadIdx.x].y;
                         v[q] = x;
                     }
                     const double l = pa.na.ell[J];
@@ -299,7 +295,7 @@ __device__ __forceinline__ void pair_energy_both(const Tgt<float> &t, const Src<
 template <int TPT, bool FAST, bool CHECK, int MODE, bool SRC>
 __device__ __forceinline__ void sym_energy_tile(const Tgt<float> (&tg)[TPT], const bool (&valid)[TPT],
                                                 const Tile<PMIX, false> &tl, int cnt, float (&at)[TPT],
-                                                float *sacc, float *scmp, const KernelParams &kp)
+                                                float2 *sac, const KernelParams &kp)
 {
     const int lane = threadIdx.x & 31;
     const int P = max(cnt, 32);
@@ -323,10 +319,9 @@ __device__ __forceinline__ void sym_energy_tile(const Tgt<float> (&tg)[TPT], con
                 pair_energy_both<FAST, (MODE >= 1)>(tg[k], s, keep, near, kp, at[k], as);
             }
             if constexpr (SRC) {
-                float acc = sacc[j], cmp = scmp[j];
-                kahan_add(acc, cmp, as);
-                sacc[j] = acc;
-                scmp[j] = cmp;
+                float2 ac = sac[j];  // (sum, Kahan compensation)
+                kahan_add(ac.x, ac.y, as);
+                sac[j] = ac;
             }
         }
         if constexpr (SRC) __syncwarp();
@@ -337,7 +332,7 @@ template <int TPT, bool FAST>
 __global__ void __launch_bounds__(kThreads, 3) k_energy_sym(const PairArgs pa)
 {
     __shared__ Tile<PMIX, false> tl;
-    __shared__ float sacc[kSymWarps][kTile], scmp[kSymWarps][kTile];
+    __shared__ float2 sac[kSymWarps][kTile];  // per warp and source: (sum, Kahan compensation)
     __shared__ int s_item;
     __shared__ float s_box[2][kThreads / 32][6];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -386,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_energy_sym(const PairArgs pa)
                 tl.lo[threadIdx.x] = pa.recLo[J];
                 box_add(sb, V3<float>{r.a.x, r.a.y, r.a.z}, V3<float>{r.b.x, r.b.y, r.b.z});
             }
-            for (int t = lane; t < kTile; t += 32) sacc[wid][t] = scmp[wid][t] = 0.f;
+            for (int t = lane; t < kTile; t += 32) sac[wid][t] = make_float2(0.f, 0.f);
             block_box(sb, s_box[1]);
             const bool check = !(s0 + cnt - 1 < w.nb_lo || s0 > w.nb_hi);
             float g2 = 0.f;
@@ -398,20 +393,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_energy_sym(const PairArgs pa)
 #pragma unroll
             for (int k = 0; k < TPT; ++k) at[k] = 0.f;
             if (diag)
-                sym_energy_tile<TPT, FAST, true, 2, false>(tg, valid, tl, cnt, at, sacc[wid], scmp[wid], pa.kp);
+                sym_energy_tile<TPT, FAST, true, 2, false>(tg, valid, tl, cnt, at, sac[wid], pa.kp);
             else if (check || mode == 2)
-                sym_energy_tile<TPT, FAST, true, 2, true>(tg, valid, tl, cnt, at, sacc[wid], scmp[wid], pa.kp);
+                sym_energy_tile<TPT, FAST, true, 2, true>(tg, valid, tl, cnt, at, sac[wid], pa.kp);
             else if (mode == 1)
-                sym_energy_tile<TPT, FAST, false, 1, true>(tg, valid, tl, cnt, at, sacc[wid], scmp[wid], pa.kp);
+                sym_energy_tile<TPT, FAST, false, 1, true>(tg, valid, tl, cnt, at, sac[wid], pa.kp);
             else
-                sym_energy_tile<TPT, FAST, false, 0, true>(tg, valid, tl, cnt, at, sacc[wid], scmp[wid], pa.kp);
+                sym_energy_tile<TPT, FAST, false, 0, true>(tg, valid, tl, cnt, at, sac[wid], pa.kp);
 #pragma unroll
             for (int k = 0; k < TPT; ++k) A[k] += (double)at[k];
             if (!diag) {
                 __syncthreads();
                 if (threadIdx.x < cnt) {
                     double x = 0.0;
-                    for (int wv = 0; wv < kSymWarps; ++wv) x += (double)sacc[wv][threadIdx.x] - (double)scmp[wv][threadIdx.x];
+                    for (int wv = 0; wv < kSymWarps; ++wv) x += (double)sac[wv][threadIdx.x].x - (double)sac[wv][threadIdx.x].y;
                     pa.part[(size_t)bslot * pa.nE + s0 + threadIdx.x] = x;
                 }
             }
