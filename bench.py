@@ -40,8 +40,9 @@ SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_NOMINAL = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6   # FLOP/s at the maximum SM clock
 L2_BYTES = 129 * 2 ** 20
 # DRAM bytes (read + write) of one apply launch on the 8 x 4096 workload, by (pass, targets per thread),
-# from ncu captures of the current kernels (profiles/apply_pair_kernel_knots8x4096.md); others: unknown
-APPLY_TRAFFIC_BYTES = {("gather", 2): 5.07e6}
+# from ncu captures of the current kernels (the profiles/ summaries named beside them); others: unknown
+APPLY_TRAFFIC_BYTES = {("gather", 2): 5.07e6,                   # apply_pair_kernel_knots8x4096.md
+                      ("symmetric", 1): 5.162240e6 + 0.249344e6}  # apply_symmetric_kernel_knots8x4096.md
 
 
 def parse():
@@ -66,6 +67,9 @@ def parse():
                          "a sample; batch: 1,024 independent knots of log-uniform size; learned: train the "
                          "learned preconditioner and compare times to 1e-6 against plain FP64 CG; "
                          "constraints: descent steps with the total-length and the edge-length constraint sets")
+    ap.add_argument("--apply-variant", type=int, default=-1,
+                    help="bench mode: after the autotuner, pin the apply pass (0 gather, 1 or 2 the symmetric "
+                         "pass with that many targets per thread); for launch lists taken under a profiler")
     ap.add_argument("--sym-tpt", type=int, default=0,
                     help="passes mode: run the symmetric energy / differential / apply passes with this many "
                          "targets per thread (0: the gather passes)")
@@ -529,6 +533,11 @@ def run_ours(args, rank, world, local_rank):
     gamma = torch.as_tensor(curves.gamma).cuda()
     pairs = ctx.pairs_per_pass()
     tuned = tpe.tp_autotune(ctx, gamma)   # targets per thread of each pair pass, timed on this workload
+    if args.apply_variant >= 0:
+        # profilers serialise every launch, which can tip the timing-based choice: pin the apply instead
+        tpe.tp_set_apply_variant(ctx, args.apply_variant)
+        tuned["tpt"]["apply_symmetric"] = args.apply_variant
+        tuned["pinned_apply_variant"] = args.apply_variant
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     ok_status = (tpe.TP_OK, tpe.TP_ERR_NOT_CONVERGED)
     infos = []
