@@ -176,8 +176,9 @@ TPE_API void tp_default_params(tp_params *p);
  * direction defines T_I.  vertex_offsets_host / edge_offsets_host: HOST int32 [n_curves + 1]
  * delimiting the curves (vertices and edges of curve c are contiguous); n_curves >= 1.
  * With p->independent = 1 every curve is its own problem.  Allocates all device scratch.
- * Errors: TP_ERR_INVALID_ARG (indices out of range, an edge outside its curve's vertex range,
- * bad parameters), TP_ERR_OOM, TP_ERR_CUDA. */
+ * Curves of fewer than 4 edges have no disjoint pair: their energy, differential and A-bar are 0.
+ * Errors: TP_ERR_INVALID_ARG (no edges at all, indices out of range, an edge outside its curve's
+ * vertex range, bad parameters), TP_ERR_OOM, TP_ERR_CUDA. */
 TPE_API tp_status tp_create(tp_ctx **ctx, int n_vertices, int n_edges, const int32_t *edges_host, int n_curves,
                     const int32_t *vertex_offsets_host, const int32_t *edge_offsets_host, const tp_params *p);
 TPE_API void tp_destroy(tp_ctx *ctx);

@@ -300,6 +300,7 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
     if (!params_ok(&prm, why)) return fail(ctx, TP_ERR_INVALID_ARG, why);
     if (nV < 1 || nE < 0 || n_curves < 1 || (nE > 0 && !edges_host) || !voff_host || !eoff_host)
         return fail(ctx, TP_ERR_INVALID_ARG, "bad graph sizes or null pointers");
+    if (nE == 0) return fail(ctx, TP_ERR_INVALID_ARG, "the graph has no edges (its energy is 0 and nothing moves)");
     if (voff_host[0] != 0 || eoff_host[0] != 0 || voff_host[n_curves] != nV || eoff_host[n_curves] != nE)
         return fail(ctx, TP_ERR_INVALID_ARG, "curve offsets must start at 0 and end at n_vertices / n_edges");
     for (int k = 0; k < n_curves; ++k)

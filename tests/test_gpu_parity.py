@@ -144,3 +144,31 @@ def test_mixed_precision_at_scale(torch, orc):
     assert cosine(dE[v_i], ref) >= 0.9999
     assert rel(dE[v_i], ref) <= 1e-5
     assert rel(Au[v_i], orc.gram_apply_at(c.gamma, c.edges, SIG, u, v_i)) <= 1e-6
+
+
+def test_graphs_without_disjoint_pairs(torch, orc):
+    """Edge cases of the pair set (Eq. 17 sums over edges that share no vertex): a triangle has no such
+    pair, so its energy, differential, A-bar u and diag(A) are exactly 0 (the oracle agrees); in an
+    independent batch the triangle's problem stays 0 while the knot next to it matches the oracle; a
+    graph without edges is rejected at creation."""
+    from paper_2006_07859_gb300 import tpe
+    tri = S.regular_polygon(3, 1.0)
+    c = S.single(tri)
+    assert orc.energy(c.gamma, c.edges) == 0.0
+    for prec in (0, 2):
+        ctx = make_ctx(c, precision=prec, precond=1)
+        g = dev(c.gamma)
+        assert host(tpe.tp_energy(ctx, g))[0] == 0.0
+        assert np.all(host(tpe.tp_differential(ctx, g)) == 0.0)
+        u = dev(np.random.default_rng(1).normal(size=(3, 3)))
+        assert np.all(host(tpe.sobolev_apply(ctx, g, u)) == 0.0)
+        assert np.all(host(tpe.tp_gram_diagonal(ctx, g)) == 0.0)
+    b = S.batch_of_knots([3, 64], 3, 5)
+    b.gamma[:3] = tri
+    ctx = make_ctx(b, precision=0, precond=1, independent=1)
+    E = host(tpe.tp_energy(ctx, dev(b.gamma)))
+    gk, ek = b.curve(1)
+    assert E[0] == 0.0 and abs(E[1] - orc.energy(gk, ek)) <= 1e-10 * E[1]
+    with pytest.raises(tpe.TpError) as ei:
+        tpe.Context(np.zeros((0, 2), dtype=np.int32), [0, 4], [0, 0], 4, precision=0, precond=1)
+    assert ei.value.status == tpe.TP_ERR_INVALID_ARG
