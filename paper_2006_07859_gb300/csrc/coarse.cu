@@ -27,7 +27,8 @@ namespace tpe {
         if (e_ != cudaSuccess) return e_; \
     } while (0)
 
-constexpr int kMaxCoarse = 64;
+constexpr int kMaxCoarse = 128;
+constexpr int kFactorSmem = (kMaxCoarse - 1) * (kMaxCoarse - 1) * (int)sizeof(double);  // 127^2 doubles
 
 struct CoarseCurve {
     int v0, n, m;  // hats j = 0 .. m-2 are the basis
@@ -120,7 +121,7 @@ __global__ void k_coarse_factor(const CoarseCurve *__restrict__ cc, double *__re
 {
     const CoarseCurve C = cc[blockIdx.x];
     const int mm = C.m - 1;
-    __shared__ double a[kMaxCoarse * kMaxCoarse];
+    extern __shared__ double a[];  // [mm][mm] (dynamic: up to 127^2 doubles)
     double *g = L + C.aoff;
     for (int t = threadIdx.x; t < mm * mm; t += blockDim.x) {
         int r = t / mm, col = t % mm;
@@ -187,7 +188,9 @@ __global__ void k_coarse_restrict(const CoarseCurve *__restrict__ cc, const doub
         for (int q = 0; q < 3; ++q) w[C.woff + 3 * j + q] = sh[q][0];
 }
 
-// y = (Z^T A Z)^-1 w per curve: one block per curve, one thread per (row, component)
+// y = (Z^T A Z)^-1 w per curve: one block per curve, one thread per row and its three components.  The
+// inverse is stored exactly symmetric (entry (r, c) and (c, r) are the same sum), so row r is read as
+// column r: consecutive threads read consecutive addresses.
 __global__ void k_coarse_solve(const CoarseCurve *__restrict__ cc, const double *__restrict__ Ainv,
                                double *__restrict__ w)
 {
@@ -198,11 +201,15 @@ __global__ void k_coarse_solve(const CoarseCurve *__restrict__ cc, const double 
     __shared__ double sw[3 * kMaxCoarse];
     for (int t = threadIdx.x; t < 3 * mm; t += blockDim.x) sw[t] = y[t];
     __syncthreads();
-    for (int t = threadIdx.x; t < 3 * mm; t += blockDim.x) {
-        const int r = t / 3, q = t % 3;
-        double s = 0.0;
-        for (int k = 0; k < mm; ++k) s += a[r * mm + k] * sw[3 * k + q];
-        y[t] = s;
+    for (int r = threadIdx.x; r < mm; r += blockDim.x) {
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < mm; ++k) {
+            const double v = a[(size_t)k * mm + r];
+            s[0] += v * sw[3 * k];
+            s[1] += v * sw[3 * k + 1];
+            s[2] += v * sw[3 * k + 2];
+        }
+        for (int q = 0; q < 3; ++q) y[3 * r + q] = s[q];
     }
 }
 
@@ -253,6 +260,7 @@ cudaError_t coarse_init(Ctx &c)
     TPE_CHECK(cudaMalloc(&S.d_L, sizeof(double) * std::max<long long>(1, aoff)));
     TPE_CHECK(cudaMalloc(&S.d_Li, sizeof(double) * std::max<long long>(1, aoff)));
     TPE_CHECK(cudaMalloc(&S.d_w, sizeof(double) * std::max<long long>(1, woff)));
+    TPE_CHECK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, kFactorSmem));
     return cudaSuccess;
 }
 
@@ -282,7 +290,8 @@ cudaError_t coarse_setup(Ctx &c, const double *gamma_geom, int which, cudaStream
         k_coarse_gram<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(b, S.d_curves, c.d_q, S.d_L);
         c.launches++;
     }
-    k_coarse_factor<<<c.nCurves, 256, 0, s>>>(S.d_curves, S.d_L, S.d_Li);
+    k_coarse_factor<<<c.nCurves, 256, (size_t)(S.max_m - 1) * (S.max_m - 1) * sizeof(double), s>>>(S.d_curves, S.d_L,
+                                                                                                 S.d_Li);
     c.launches++;
     S.ready = 1;
     return cudaGetLastError();
@@ -294,7 +303,7 @@ cudaError_t coarse_apply(Ctx &c, const double *r, double *z, cudaStream_t s)
     if (!c.coarse || !c.coarse->ready) return cudaSuccess;
     CoarseState &S = *c.coarse;
     k_coarse_restrict<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(S.d_curves, r, S.d_w);
-    k_coarse_solve<<<c.nCurves, 3 * kMaxCoarse, 0, s>>>(S.d_curves, S.d_L, S.d_w);
+    k_coarse_solve<<<c.nCurves, kMaxCoarse, 0, s>>>(S.d_curves, S.d_L, S.d_w);
     k_coarse_prolong<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_w, z);
     c.launches += 3;
     return cudaGetLastError();

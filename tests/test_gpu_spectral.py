@@ -149,18 +149,21 @@ def test_rq_symbol_halves_iterations(torch):
     assert its[3] < 0.75 * its[2], its
 
 
-@pytest.mark.parametrize("name", ["trefoil256", "knot300", "batch3"])
-def test_twolevel_apply(torch, orc, name):
+@pytest.mark.parametrize("name,m", [("trefoil256", 32), ("knot300", 32), ("batch3", 32), ("knot600", 128),
+                                    ("batch3", 128)])
+def test_twolevel_apply(torch, orc, name, m):
     """Two-level preconditioner (spectral RQ + coarse hats) against the oracle built from the dense
-    Gram matrix."""
+    Gram matrix; 128 hats is the largest coarse space (its factor uses opt-in shared memory)."""
     from paper_2006_07859_gb300 import tpe
     if name == "trefoil256":
         c, indep = S.trefoil_256(), 0
     elif name == "knot300":
         c, indep = S.single(S.fourier_knot(300, 5, 3)), 0
+    elif name == "knot600":
+        c, indep = S.single(S.fourier_knot(600, 6, 4)), 0
     else:
         c, indep = S.batch_of_knots([64, 129, 256], 5, 700), 1
-    ctx = make_ctx(c, precision=0, precond=4, independent=indep, coarse_dim=32)
+    ctx = make_ctx(c, precision=0, precond=4, independent=indep, coarse_dim=m)
     r = np.random.default_rng(6).normal(size=(c.n_vertices, 3))
     r -= r.mean(0)
     z = host(tpe.tp_precond_apply(ctx, dev(c.gamma), dev(r)))
@@ -170,7 +173,7 @@ def test_twolevel_apply(torch, orc, name):
         n = gk.shape[0]
         B, B0 = orc.gram_dense(gk, ek, SIG)
         v0, v1 = c.vertex_offsets[k], c.vertex_offsets[k + 1]
-        zo[v0:v1] = orc.twolevel_apply(B + B0, n, SIG, min(32, n // 4), r[v0:v1])
+        zo[v0:v1] = orc.twolevel_apply(B + B0, n, SIG, min(m, n // 4), r[v0:v1])
     # compare modulo the constant the mean-free projection removes (per curve)
     for k in range(c.n_curves):
         v0, v1 = c.vertex_offsets[k], c.vertex_offsets[k + 1]
