@@ -27,8 +27,9 @@ namespace tpe {
         if (e_ != cudaSuccess) return e_; \
     } while (0)
 
-constexpr int kMaxCoarse = 128;
-constexpr int kFactorSmem = (kMaxCoarse - 1) * (kMaxCoarse - 1) * (int)sizeof(double);  // 127^2 doubles
+constexpr int kMaxCoarse = 256;
+constexpr int kSmemCoarse = 128;  // coarse spaces up to this size factor in shared memory, larger ones in global
+constexpr int kFactorSmem = (kSmemCoarse - 1) * (kSmemCoarse - 1) * (int)sizeof(double);  // 127^2 doubles
 
 struct CoarseCurve {
     int v0, n, m;  // hats j = 0 .. m-2 are the basis
@@ -44,6 +45,7 @@ struct tpe::CoarseState {
     int *d_vcurve = nullptr;
     double *d_L = nullptr;   // per curve: (Z^T A Z)^-1, row-major (m-1) x (m-1)
     double *d_Li = nullptr;  // set-up scratch: L^-1 of the Cholesky factor, same layout
+    double *d_W = nullptr;   // set-up scratch: Cholesky work array of coarse spaces above 127 hats
     double *d_w = nullptr;  // coarse vectors
     int max_m = 0;
     int ready = 0;
@@ -117,11 +119,13 @@ __global__ void k_coarse_gram(int b, const CoarseCurve *__restrict__ cc, const d
 
 // symmetrise, Cholesky-factor and invert every curve's coarse matrix in place (one block per curve);
 // Li: scratch of the same layout for L^-1
-__global__ void k_coarse_factor(const CoarseCurve *__restrict__ cc, double *__restrict__ L, double *__restrict__ Li)
+__global__ void k_coarse_factor(const CoarseCurve *__restrict__ cc, double *__restrict__ L, double *__restrict__ Li,
+                                double *__restrict__ W)
 {
     const CoarseCurve C = cc[blockIdx.x];
     const int mm = C.m - 1;
-    extern __shared__ double a[];  // [mm][mm] (dynamic: up to 127^2 doubles)
+    extern __shared__ double sa[];  // [mm][mm] for mm <= 127 (dynamic shared memory)
+    double *a = mm <= kSmemCoarse - 1 ? sa : W + C.aoff;  // larger coarse spaces work in global memory
     double *g = L + C.aoff;
     for (int t = threadIdx.x; t < mm * mm; t += blockDim.x) {
         int r = t / mm, col = t % mm;
@@ -259,6 +263,7 @@ cudaError_t coarse_init(Ctx &c)
     TPE_CHECK(cudaMemcpy(S.d_vcurve, vc.data(), sizeof(int) * c.nV, cudaMemcpyHostToDevice));
     TPE_CHECK(cudaMalloc(&S.d_L, sizeof(double) * std::max<long long>(1, aoff)));
     TPE_CHECK(cudaMalloc(&S.d_Li, sizeof(double) * std::max<long long>(1, aoff)));
+    TPE_CHECK(cudaMalloc(&S.d_W, sizeof(double) * std::max<long long>(1, aoff)));
     TPE_CHECK(cudaMalloc(&S.d_w, sizeof(double) * std::max<long long>(1, woff)));
     TPE_CHECK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, kFactorSmem));
     return cudaSuccess;
@@ -271,6 +276,7 @@ void coarse_free(Ctx &c)
     cudaFree(c.coarse->d_vcurve);
     cudaFree(c.coarse->d_L);
     cudaFree(c.coarse->d_Li);
+    cudaFree(c.coarse->d_W);
     cudaFree(c.coarse->d_w);
     delete c.coarse;
     c.coarse = nullptr;
@@ -290,8 +296,8 @@ cudaError_t coarse_setup(Ctx &c, const double *gamma_geom, int which, cudaStream
         k_coarse_gram<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(b, S.d_curves, c.d_q, S.d_L);
         c.launches++;
     }
-    k_coarse_factor<<<c.nCurves, 256, (size_t)(S.max_m - 1) * (S.max_m - 1) * sizeof(double), s>>>(S.d_curves, S.d_L,
-                                                                                                 S.d_Li);
+    const int msm = std::min(S.max_m, kSmemCoarse) - 1;
+    k_coarse_factor<<<c.nCurves, 256, (size_t)msm * msm * sizeof(double), s>>>(S.d_curves, S.d_L, S.d_Li, S.d_W);
     c.launches++;
     S.ready = 1;
     return cudaGetLastError();

@@ -150,10 +150,10 @@ def test_rq_symbol_halves_iterations(torch):
 
 
 @pytest.mark.parametrize("name,m", [("trefoil256", 32), ("knot300", 32), ("batch3", 32), ("knot600", 128),
-                                    ("batch3", 128)])
+                                    ("batch3", 128), ("knot1200", 256)])
 def test_twolevel_apply(torch, orc, name, m):
     """Two-level preconditioner (spectral RQ + coarse hats) against the oracle built from the dense
-    Gram matrix; 128 hats is the largest coarse space (its factor uses opt-in shared memory)."""
+    Gram matrix; up to 128 hats the factor works in shared memory, 256 (the largest) in global memory."""
     from paper_2006_07859_gb300 import tpe
     if name == "trefoil256":
         c, indep = S.trefoil_256(), 0
@@ -161,6 +161,8 @@ def test_twolevel_apply(torch, orc, name, m):
         c, indep = S.single(S.fourier_knot(300, 5, 3)), 0
     elif name == "knot600":
         c, indep = S.single(S.fourier_knot(600, 6, 4)), 0
+    elif name == "knot1200":
+        c, indep = S.single(S.fourier_knot(1200, 8, 5)), 0
     else:
         c, indep = S.batch_of_knots([64, 129, 256], 5, 700), 1
     ctx = make_ctx(c, precision=0, precond=4, independent=indep, coarse_dim=m)
