@@ -67,7 +67,7 @@ def parse():
                          "a sample; batch: 1,024 independent knots of log-uniform size; learned: train the "
                          "learned preconditioner and compare times to 1e-6 against plain FP64 CG; "
                          "constraints: descent steps with the total-length and the edge-length constraint sets")
-    ap.add_argument("--coarse-dim", type=int, default=64, help="hat functions per curve of the coarse space")
+    ap.add_argument("--coarse-dim", type=int, default=128, help="hat functions per curve of the coarse space")
     ap.add_argument("--apply-variant", type=int, default=-1,
                     help="bench mode: after the autotuner, pin the apply pass (0 gather, 1 or 2 the symmetric "
                          "pass with that many targets per thread); for launch lists taken under a profiler")

@@ -129,7 +129,8 @@ typedef struct {
     int proj_maxit;
     int independent;      /* 1: every curve is its own problem (no cross-curve pairs, constraints per curve);
                              0: the whole graph is one problem (one barycenter + one total length) */
-    int coarse_dim;       /* TP_PRECOND_TWOLEVEL: hat functions per closed curve (<= 256, at most n / 4) */
+    int coarse_dim;       /* TP_PRECOND_TWOLEVEL: hat functions per closed curve (default 128; at most 256
+                             and n / 4) */
     double far_cutoff;    /* TP_MIXED: source tiles farther than far_cutoff * (extent of the curve) from a
                              warp's targets use single-float positions (faster, less accurate); >= 10
                              keeps double-float positions everywhere */

@@ -217,7 +217,7 @@ void tp_default_params(tp_params *p)
     p->constraint_set = TP_CONSTRAINTS_TOTAL_LENGTH;
     p->line_search = TP_LINESEARCH_UNIT;
     p->ccd_horizon = 1.5;
-    p->coarse_dim = 64;
+    p->coarse_dim = 128;
 }
 
 const char *tp_last_error(const tp_ctx *ctx) { return ctx ? ctx->c.err.c_str() : "null context"; }
