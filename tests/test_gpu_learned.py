@@ -162,12 +162,12 @@ def test_learned_preconditioner_gains(torch, orc, record_property):
     4 unseen knots: the trained G term on top of the two-level preconditioner versus the two-level
     preconditioner alone (and the loss before and after training).
 
-    What this shows on these curves: training lowers the loss by a few percent (0.425 -> 0.399 in the
-    measured run) while the learned term costs iterations (74 against 69).  The two-level preconditioner already
-    matches the local (diagonal and high-frequency) structure that an additive two-point stencil can
-    express.  So the test checks what must hold (the loss decreases; the learned PCG converges and its
-    true residual under the exact operator stays small; the iteration count stays within 15% of the
-    two-level count) and records the numbers."""
+    What this shows on these curves: training lowers the loss (0.352 -> 0.195 in the last measured
+    run), but with the default coarse space of 128 hats the learned term does not save iterations on
+    unseen knots (57 against 55): the two-level preconditioner already covers what a per-vertex
+    rescaling and a two-point stencil can express.  So the test checks what must hold (the loss
+    decreases; the learned PCG converges and its true residual under the exact operator stays small;
+    the iteration count stays within 15% of the two-level count) and records the numbers."""
     from paper_2006_07859_gb300 import learned, tpe
     sizes = [512, 700, 900, 1200]
     ctx, cs, gam, voff = setup(torch, orc, sizes, seed0=40, precision=2)
