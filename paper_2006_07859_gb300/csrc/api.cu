@@ -272,7 +272,7 @@ void tp_destroy(tp_ctx *ctx)
                     c.d_recLo2, c.d_recD, c.d_recD2, c.d_ellw[0], c.d_ellw[1], c.d_Tw[0], c.d_Tw[1], c.d_xw[0],
                     c.d_xw[1], c.d_urecF, c.d_urecD, c.d_part, c.d_rows, c.d_x0L0, c.d_Cv, c.d_G, c.d_Ginv,
                     c.d_red, c.d_phi, c.d_y, c.d_r, c.d_z, c.d_p, c.d_q, c.d_diag, c.d_t1, c.d_t2, c.d_t3, c.d_t4,
-                    c.d_t5, c.d_t6, c.d_gam, c.d_best, c.d_E, c.d_scal, c.d_cg, c.d_err};
+                    c.d_t5, c.d_t6, c.d_gam, c.d_best, c.d_yw0, c.d_yw1, c.d_E, c.d_scal, c.d_cg, c.d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     prof_harvest(c);
@@ -435,7 +435,7 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
     CK(dalloc(&c.d_red, 16 * (size_t)c.nProb));
     CK(dalloc(&c.d_phi, 4 * (size_t)c.nProb));
     double **vecs[] = {&c.d_y, &c.d_r, &c.d_z, &c.d_p, &c.d_q, &c.d_t1, &c.d_t2, &c.d_t3, &c.d_t4, &c.d_t5, &c.d_t6,
-                       &c.d_gam, &c.d_best};
+                       &c.d_gam, &c.d_best, &c.d_yw0, &c.d_yw1};
     for (double **v : vecs) CK(dalloc(v, 3 * (size_t)nV));
     CK(cudaMemset(c.d_z, 0, sizeof(double) * 3 * nV));
     CK(dalloc(&c.d_diag, nV));
@@ -677,8 +677,12 @@ static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE_
         // y on null(R) cap N-perp (projector mode 2), then the translation that restores the barycenter
         cudaError_t e = edges_setup(c, 0, s);
         if (e != cudaSuccess) return e;
-        e = cg_solve(c, gamma, 0, dE, g, c.prm.cg_rtol, c.prm.cg_maxit, iters, rr, conv, bd, s, 2, flags.data());
+        e = cg_solve(c, gamma, 0, dE, g, c.prm.cg_rtol, c.prm.cg_maxit, iters, rr, conv, bd, s, 2, flags.data(),
+                     c.warm_ok ? c.d_yw0 : nullptr);
         if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(c.d_yw0, g, sizeof(double) * 3 * c.nV, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+        c.warm_ok = 1;
         if (n_conv) {
             *n_conv = 0;
             for (int f : flags) *n_conv += f;
@@ -687,12 +691,19 @@ static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE_
     }
     int i0 = 0, i1 = 0, c0 = 0, c1 = 0, b0 = 0, b1 = 0;
     double r0 = 0, r1 = 0;
+    // both solves start from the previous step's solutions (the curve moves little between steps)
     cudaError_t e = cg_solve(c, gamma, 0, dE, c.d_t3, c.prm.cg_rtol, c.prm.cg_maxit, &i0, &r0, &c0, &b0, s, 1,
-                             flags.data());
+                             flags.data(), c.warm_ok ? c.d_yw0 : nullptr);
     if (e != cudaSuccess) return e;
     e = clen_rhs(c, c.d_t6, s);
     if (e != cudaSuccess) return e;
-    e = cg_solve(c, gamma, 0, c.d_t6, c.d_t4, c.prm.cg_rtol, c.prm.cg_maxit, &i1, &r1, &c1, &b1, s, 1, flags.data());
+    e = cg_solve(c, gamma, 0, c.d_t6, c.d_t4, c.prm.cg_rtol, c.prm.cg_maxit, &i1, &r1, &c1, &b1, s, 1, flags.data(),
+                 c.warm_ok ? c.d_yw1 : nullptr);
+    if (e != cudaSuccess) return e;
+    const size_t vb = sizeof(double) * 3 * c.nV;
+    if ((e = cudaMemcpyAsync(c.d_yw0, c.d_t3, vb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(c.d_yw1, c.d_t4, vb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+    c.warm_ok = 1;
     if (n_conv) {
         *n_conv = 0;
         for (int f : flags) *n_conv += f;
@@ -875,8 +886,10 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
                 CK(schur_shift(c, x, c.d_phi, -1.0, s));
             } else {
                 CK(clen_rhs(c, rhs, s));
+                // starts from z: A-bar^+ C_len^T of the pre-step curve (the gradient's second solve) or of
+                // the previous trial, both close to this trial's solution
                 CK(cg_solve(c, gamma, 0, rhs, z, c.prm.proj_cg_rtol, c.prm.cg_maxit, &pit_cg, &prr, &pconv, &pbd,
-                            s, 1));
+                            s, 1, nullptr, z));
                 CK(schur_projection(c, z, c.d_phi, -1.0, x, s));
             }
             proj_cg_total += pit_cg;

@@ -517,33 +517,70 @@ cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, co
 // ---------------------------------------------------------------------------------- CG
 
 // Initialise: bb = r.r (r = P rhs already), rz = r.z; done flags for problems with zero rhs.
+// Per problem |r|^2, r.z and |b|^2 (b = P rhs; r = b when the solve starts from zero).  A warm start
+// that already meets the tolerance is done at once.
 __global__ void k_cg_init(RedArgs ra, const double *__restrict__ r, const double *__restrict__ z,
-                          CGScalars *__restrict__ cg, int *__restrict__ done, int *__restrict__ active)
+                          const double *__restrict__ b, double tol2, CGScalars *__restrict__ cg,
+                          int *__restrict__ done, int *__restrict__ active)
+{
+    double s[3] = {0, 0, 0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        for (int k = 0; k < 3; ++k) {
+            s[0] += r[3 * i + k] * r[3 * i + k];
+            s[1] += r[3 * i + k] * z[3 * i + k];
+            s[2] += b[3 * i + k] * b[3 * i + k];
+        }
+    if (reduce_phase<3>(s, ra)) {
+        __shared__ int na;
+        if (threadIdx.x == 0) na = 0;
+        __syncthreads();
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+            CGScalars &g = cg[q];
+            g.bnorm2 = ra.sums[3 * q + 2];
+            g.rnorm2 = ra.sums[3 * q];
+            g.rz = ra.sums[3 * q + 1];
+            g.iters = 0;
+            g.breakdown = 0;
+            g.done = (g.bnorm2 == 0.0) || (g.rnorm2 <= tol2 * g.bnorm2);
+            done[q] = g.done;
+            if (!g.done) atomicAdd(&na, 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *active = na;
+    }
+}
+
+// Warm start safeguard: per problem |r0|^2 and |b|^2; where the guess does not reduce the residual the
+// problem restarts from y = 0, r = b.
+__global__ void k_warm_norms(RedArgs ra, const double *__restrict__ r, const double *__restrict__ b,
+                             double *__restrict__ out)
 {
     double s[2] = {0, 0};
     int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
         for (int k = 0; k < 3; ++k) {
             s[0] += r[3 * i + k] * r[3 * i + k];
-            s[1] += r[3 * i + k] * z[3 * i + k];
+            s[1] += b[3 * i + k] * b[3 * i + k];
         }
-    if (reduce_phase<2>(s, ra)) {
-        __shared__ int na;
-        if (threadIdx.x == 0) na = 0;
-        __syncthreads();
+    if (reduce_phase<2>(s, ra))
         for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
-            CGScalars &g = cg[q];
-            g.bnorm2 = ra.sums[2 * q];
-            g.rnorm2 = ra.sums[2 * q];
-            g.rz = ra.sums[2 * q + 1];
-            g.iters = 0;
-            g.breakdown = 0;
-            g.done = (g.bnorm2 == 0.0);
-            done[q] = g.done;
-            if (!g.done) atomicAdd(&na, 1);
+            out[2 * q] = ra.sums[2 * q];
+            out[2 * q + 1] = ra.sums[2 * q + 1];
         }
-        __syncthreads();
-        if (threadIdx.x == 0) *active = na;
+}
+
+__global__ void k_warm_reset(int nV, const int *__restrict__ vprob, const double *__restrict__ norms,
+                             const double *__restrict__ b, double *__restrict__ y, double *__restrict__ r)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    const int q = vprob[i];
+    if (!(norms[2 * q] < norms[2 * q + 1])) {
+        for (int k = 0; k < 3; ++k) {
+            y[3 * i + k] = 0.0;
+            r[3 * i + k] = b[3 * i + k];
+        }
     }
 }
 
@@ -817,22 +854,36 @@ static cudaError_t graph_block(Ctx &c, const double *gamma_geom, int which, int 
 
 cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
                      int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s,
-                     int proj_mode, int *conv_flags)
+                     int proj_mode, int *conv_flags, const double *x0)
 {
     SolverState &st = S(c);
     const size_t vb = sizeof(double) * 3 * c.nV;
     const int nb = (c.nV + 255) / 256;
     double *r = c.d_r, *z = c.d_z, *p = c.d_p, *q = c.d_q, *y = c.d_y;
-    // r = P rhs, y = 0
-    TPE_CHECK(cudaMemcpyAsync(r, rhs, vb, cudaMemcpyDeviceToDevice, s));
-    TPE_CHECK(projector(c, proj_mode, r, s, nullptr));
-    TPE_CHECK(cudaMemsetAsync(y, 0, vb, s));
+    const double tol2 = rtol * rtol;
+    // b = P rhs (kept in q until the iterations start)
+    TPE_CHECK(cudaMemcpyAsync(q, rhs, vb, cudaMemcpyDeviceToDevice, s));
+    TPE_CHECK(projector(c, proj_mode, q, s, nullptr));
+    if (x0) {
+        // y = P x0, r = b - P A-bar y; problems the guess does not help restart from zero
+        TPE_CHECK(cudaMemcpyAsync(y, x0, vb, cudaMemcpyDeviceToDevice, s));
+        TPE_CHECK(projector(c, proj_mode, y, s, nullptr));
+        TPE_CHECK(pair_apply(c, gamma_geom, which, y, z, s));
+        TPE_CHECK(projector(c, proj_mode, z, s, nullptr));
+        TPE_CHECK(vec_axpby(c, 1.0, q, -1.0, z, r, s));
+        double *norms = c.d_scal + 64 + 12 * (size_t)c.nProb;  // [nProb][2]
+        k_warm_norms<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 4), r, q, norms);
+        k_warm_reset<<<nb, 256, 0, s>>>(c.nV, c.d_vprob, norms, q, y, r);
+        c.launches += 2;
+    } else {
+        TPE_CHECK(cudaMemcpyAsync(r, q, vb, cudaMemcpyDeviceToDevice, s));
+        TPE_CHECK(cudaMemsetAsync(y, 0, vb, s));
+    }
     TPE_CHECK(precond_apply(c, r, z, s, nullptr));
     if (c.prm.precond != TP_PRECOND_NONE) TPE_CHECK(projector(c, proj_mode, z, s, nullptr));
     TPE_CHECK(cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, s));
-    k_cg_init<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 4), r, z, c.d_cg, st.done, st.active);
+    k_cg_init<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 4), r, z, q, tol2, c.d_cg, st.done, st.active);
     c.launches++;
-    const double tol2 = rtol * rtol;
     const int every = std::max(1, c.prm.cg_check_every);
     const int fuse = proj_mode != 0;  // projector modes 1, 2: their mean removal runs inside the CG kernels
     int it = 0;

@@ -170,6 +170,8 @@ struct Ctx {
     int sm_count = 0;
     SolverState *sol = nullptr;
     double *d_best = nullptr;  // [nV][3] line-search result
+    double *d_yw0 = nullptr, *d_yw1 = nullptr;  // [nV][3] last gradient solutions (warm starts of the next step)
+    int warm_ok = 0;                            // d_yw0 / d_yw1 hold solutions of an earlier step
     double *d_t5 = nullptr, *d_t6 = nullptr;
     int64_t pairs_per_pass = 0;
     const int *d_skip = nullptr;  // during a CG solve: per-problem converged flags (apply skips them)
@@ -246,9 +248,11 @@ cudaError_t precond_apply_base(Ctx &c, const double *r, double *z, cudaStream_t 
 cudaError_t coarse_init(Ctx &c);
 cudaError_t solver_setup(Ctx &c);
 void solver_free(Ctx &c);
+// x0 (optional, may alias x): initial guess; a problem whose initial residual is not below |P rhs| starts
+// from zero instead.  The tolerance is always relative to |P rhs|.
 cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
                      int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s,
-                     int proj_mode, int *conv_flags = nullptr);
+                     int proj_mode, int *conv_flags = nullptr, const double *x0 = nullptr);
 cudaError_t project_mean(Ctx &c, double *v, cudaStream_t s, const int *skip);
 cudaError_t schur_shift(Ctx &c, double *out, const double *phi, double phi_scale, cudaStream_t s);
 cudaError_t bary_rhs(Ctx &c, const double *dE, double *rhs, cudaStream_t s);
