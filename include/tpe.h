@@ -144,6 +144,10 @@ typedef struct {
     int line_search;      /* tp_line_search (default TP_LINESEARCH_UNIT) */
     double ccd_horizon;   /* TP_LINESEARCH_ISOTOPY: collision times are searched in (0, ccd_horizon]
                              (default 1.5, so that the start never exceeds tau = 1) */
+    int warm_start;       /* 1 (default): the gradient solves start from the context's previous gradient
+                             solutions and each projection solve from the previous one (a problem whose
+                             guess does not lower the residual starts from zero); 0: every solve starts
+                             from zero, so repeated calls on the same input give identical results */
 } tp_params;
 
 typedef struct {

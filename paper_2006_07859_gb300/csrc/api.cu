@@ -217,6 +217,7 @@ void tp_default_params(tp_params *p)
     p->constraint_set = TP_CONSTRAINTS_TOTAL_LENGTH;
     p->line_search = TP_LINESEARCH_UNIT;
     p->ccd_horizon = 1.5;
+    p->warm_start = 1;
     p->coarse_dim = 128;
 }
 
@@ -678,7 +679,7 @@ static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE_
         cudaError_t e = edges_setup(c, 0, s);
         if (e != cudaSuccess) return e;
         e = cg_solve(c, gamma, 0, dE, g, c.prm.cg_rtol, c.prm.cg_maxit, iters, rr, conv, bd, s, 2, flags.data(),
-                     c.warm_ok ? c.d_yw0 : nullptr);
+                     (c.warm_ok && c.prm.warm_start) ? c.d_yw0 : nullptr);
         if (e != cudaSuccess) return e;
         e = cudaMemcpyAsync(c.d_yw0, g, sizeof(double) * 3 * c.nV, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
@@ -693,12 +694,12 @@ static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE_
     double r0 = 0, r1 = 0;
     // both solves start from the previous step's solutions (the curve moves little between steps)
     cudaError_t e = cg_solve(c, gamma, 0, dE, c.d_t3, c.prm.cg_rtol, c.prm.cg_maxit, &i0, &r0, &c0, &b0, s, 1,
-                             flags.data(), c.warm_ok ? c.d_yw0 : nullptr);
+                             flags.data(), (c.warm_ok && c.prm.warm_start) ? c.d_yw0 : nullptr);
     if (e != cudaSuccess) return e;
     e = clen_rhs(c, c.d_t6, s);
     if (e != cudaSuccess) return e;
     e = cg_solve(c, gamma, 0, c.d_t6, c.d_t4, c.prm.cg_rtol, c.prm.cg_maxit, &i1, &r1, &c1, &b1, s, 1, flags.data(),
-                 c.warm_ok ? c.d_yw1 : nullptr);
+                 (c.warm_ok && c.prm.warm_start) ? c.d_yw1 : nullptr);
     if (e != cudaSuccess) return e;
     const size_t vb = sizeof(double) * 3 * c.nV;
     if ((e = cudaMemcpyAsync(c.d_yw0, c.d_t3, vb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
@@ -889,7 +890,7 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
                 // starts from z: A-bar^+ C_len^T of the pre-step curve (the gradient's second solve) or of
                 // the previous trial, both close to this trial's solution
                 CK(cg_solve(c, gamma, 0, rhs, z, c.prm.proj_cg_rtol, c.prm.cg_maxit, &pit_cg, &prr, &pconv, &pbd,
-                            s, 1, nullptr, z));
+                            s, 1, nullptr, c.prm.warm_start ? z : nullptr));
                 CK(schur_projection(c, z, c.d_phi, -1.0, x, s));
             }
             proj_cg_total += pit_cg;

@@ -45,7 +45,7 @@ class TpParams(ctypes.Structure):
                 ("max_halvings", ctypes.c_int), ("proj_tol", ctypes.c_double), ("proj_maxit", ctypes.c_int),
                 ("independent", ctypes.c_int), ("coarse_dim", ctypes.c_int), ("far_cutoff", ctypes.c_double),
                 ("use_graphs", ctypes.c_int), ("precond_refresh", ctypes.c_int), ("constraint_set", ctypes.c_int),
-                ("line_search", ctypes.c_int), ("ccd_horizon", ctypes.c_double)]
+                ("line_search", ctypes.c_int), ("ccd_horizon", ctypes.c_double), ("warm_start", ctypes.c_int)]
 
 
 class TpPenalties(ctypes.Structure):

@@ -56,7 +56,7 @@ def test_struct_layouts_match_header():
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(tp_params), offsetof(tp_params, independent),
          sizeof(tp_step_info), offsetof(tp_step_info, rel_res), sizeof(tp_solve_info),
-         offsetof(tp_params, constraint_set));
+         offsetof(tp_params, warm_start));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -66,4 +66,4 @@ int main(void) {
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [ctypes.sizeof(tpe.TpParams), tpe.TpParams.independent.offset, ctypes.sizeof(tpe.TpStepInfo),
-                    tpe.TpStepInfo.rel_res.offset, ctypes.sizeof(tpe.TpSolveInfo), tpe.TpParams.constraint_set.offset]
+                    tpe.TpStepInfo.rel_res.offset, ctypes.sizeof(tpe.TpSolveInfo), tpe.TpParams.warm_start.offset]

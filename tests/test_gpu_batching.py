@@ -37,7 +37,7 @@ def test_graph_replay_is_bitwise_identical(torch, precond, profile):
     out = {}
     for graphs in (0, 1):
         ctx = tpe.Context.from_curves(b, precision=tpe.TP_MIXED, precond=precond, independent=1, cg_rtol=1e-6,
-                                      cg_maxit=3000, cg_check_every=8, use_graphs=graphs)
+                                      cg_maxit=3000, cg_check_every=8, use_graphs=graphs, warm_start=0)
         g = dev(b.gamma)
         dE = tpe.tp_differential(ctx, g)
         ctx.profile(profile)
@@ -56,6 +56,31 @@ def test_graph_replay_is_bitwise_identical(torch, precond, profile):
     assert a[3] == g1[3]
     if profile:
         assert a[4] == g1[4] > 0
+
+
+def test_warm_start_repeats_a_solve_in_fewer_iterations(torch):
+    """With warm starts (the default) a second gradient solve on the same input starts from the first
+    one's solution: it stops after fewer iterations at the same tolerance and lands within that
+    tolerance of the first solution.  With warm_start = 0 the two solves are bitwise identical."""
+    from paper_2006_07859_gb300 import tpe
+    b = _batch()
+    res = {}
+    for warm in (0, 1):
+        ctx = tpe.Context.from_curves(b, precision=tpe.TP_MIXED, precond=4, independent=1, cg_rtol=1e-6,
+                                      cg_maxit=3000, warm_start=warm)
+        g = dev(b.gamma)
+        dE = tpe.tp_differential(ctx, g)
+        g1, i1 = tpe.sobolev_gradient(ctx, g, dE)
+        g2, i2 = tpe.sobolev_gradient(ctx, g, dE)
+        res[warm] = (host(g1), host(g2), i1, i2)
+        ctx.close()
+    c1, c2, ci1, ci2 = res[0]
+    assert np.array_equal(c1, c2) and ci1["iters"] == ci2["iters"]
+    w1, w2, wi1, wi2 = res[1]
+    assert np.array_equal(w1, c1)                        # nothing to start from on the first call
+    assert wi2["converged"] and wi2["iters"] < wi1["iters"]
+    assert wi2["rel_res"] <= 1e-4
+    assert rel(w2, w1) <= 1e-4
 
 
 def test_autotune_keeps_parity(torch, orc):

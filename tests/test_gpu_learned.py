@@ -185,7 +185,8 @@ def test_learned_preconditioner_gains(torch, orc, record_property):
     ctx2, cs2, gam2, _ = setup(torch, orc, [600, 800, 1000, 1400], seed0=90, precision=2)
     g2 = dev(gam2)
     dE2 = tpe.tp_differential(ctx2, g2)
-    ctx2.set_params(precond=tpe.TP_PRECOND_TWOLEVEL, cg_rtol=1e-6)
+    # both solves from zero: a warm start from the first would make the second look cheap
+    ctx2.set_params(precond=tpe.TP_PRECOND_TWOLEVEL, cg_rtol=1e-6, warm_start=0)
     _, i2l = tpe.sobolev_gradient(ctx2, g2, dE2)
     tpe.tp_gnn_set_params(ctx2, res["theta"])
     ctx2.set_params(precond=tpe.TP_PRECOND_LEARNED)
