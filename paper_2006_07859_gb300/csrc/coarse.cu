@@ -46,7 +46,8 @@ struct tpe::CoarseState {
     double *d_L = nullptr;   // per curve: (Z^T A Z)^-1, row-major (m-1) x (m-1)
     double *d_Li = nullptr;  // set-up scratch: L^-1 of the Cholesky factor, same layout
     double *d_W = nullptr;   // set-up scratch: Cholesky work array of coarse spaces above 127 hats
-    double *d_w = nullptr;  // coarse vectors
+    double *d_w = nullptr;  // coarse vectors: restriction Z^T r
+    double *d_w2 = nullptr; // coarse vectors: (Z^T A Z)^-1 Z^T r
     int max_m = 0;
     int ready = 0;
 };
@@ -192,29 +193,36 @@ __global__ void k_coarse_restrict(const CoarseCurve *__restrict__ cc, const doub
         for (int q = 0; q < 3; ++q) w[C.woff + 3 * j + q] = sh[q][0];
 }
 
-// y = (Z^T A Z)^-1 w per curve: one block per curve, one thread per row and its three components.  The
-// inverse is stored exactly symmetric (entry (r, c) and (c, r) are the same sum), so row r is read as
-// column r: consecutive threads read consecutive addresses.
-__global__ void k_coarse_solve(const CoarseCurve *__restrict__ cc, const double *__restrict__ Ainv,
-                               double *__restrict__ w)
+// y = (Z^T A Z)^-1 w per curve: one warp per row (8 rows per block, blockIdx.y the curve).  The lanes
+// split the row's entries (contiguous, so the loads coalesce) and a warp-shuffle sum finishes each of
+// the three components.  w and y are separate buffers: several blocks serve one curve.
+constexpr int kSolveRows = 8;
+__global__ void __launch_bounds__(32 * kSolveRows) k_coarse_solve(const CoarseCurve *__restrict__ cc,
+                                                                  const double *__restrict__ Ainv,
+                                                                  const double *__restrict__ w,
+                                                                  double *__restrict__ y)
 {
-    const CoarseCurve C = cc[blockIdx.x];
+    const CoarseCurve C = cc[blockIdx.y];
     const int mm = C.m - 1;
-    const double *a = Ainv + C.aoff;
-    double *y = w + C.woff;
+    const int r0 = blockIdx.x * kSolveRows;
+    if (r0 >= mm) return;  // uniform per block
     __shared__ double sw[3 * kMaxCoarse];
-    for (int t = threadIdx.x; t < 3 * mm; t += blockDim.x) sw[t] = y[t];
+    for (int t = threadIdx.x; t < 3 * mm; t += blockDim.x) sw[t] = w[C.woff + t];
     __syncthreads();
-    for (int r = threadIdx.x; r < mm; r += blockDim.x) {
-        double s[3] = {0.0, 0.0, 0.0};
-        for (int k = 0; k < mm; ++k) {
-            const double v = a[(size_t)k * mm + r];
-            s[0] += v * sw[3 * k];
-            s[1] += v * sw[3 * k + 1];
-            s[2] += v * sw[3 * k + 2];
-        }
-        for (int q = 0; q < 3; ++q) y[3 * r + q] = s[q];
+    const int r = r0 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= mm) return;  // whole warps leave; no barrier follows
+    const double *a = Ainv + C.aoff + (size_t)r * mm;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int k = lane; k < mm; k += 32) {
+        const double v = a[k];
+        s[0] += v * sw[3 * k];
+        s[1] += v * sw[3 * k + 1];
+        s[2] += v * sw[3 * k + 2];
     }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int q = 0; q < 3; ++q) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+    if (lane == 0)
+        for (int q = 0; q < 3; ++q) y[C.woff + 3 * r + q] = s[q];
 }
 
 // z[v] += sum_j Z_j(i) y_j (each vertex lies in at most two hats)
@@ -265,6 +273,7 @@ cudaError_t coarse_init(Ctx &c)
     TPE_CHECK(cudaMalloc(&S.d_Li, sizeof(double) * std::max<long long>(1, aoff)));
     TPE_CHECK(cudaMalloc(&S.d_W, sizeof(double) * std::max<long long>(1, aoff)));
     TPE_CHECK(cudaMalloc(&S.d_w, sizeof(double) * std::max<long long>(1, woff)));
+    TPE_CHECK(cudaMalloc(&S.d_w2, sizeof(double) * std::max<long long>(1, woff)));
     TPE_CHECK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, kFactorSmem));
     return cudaSuccess;
 }
@@ -278,6 +287,7 @@ void coarse_free(Ctx &c)
     cudaFree(c.coarse->d_Li);
     cudaFree(c.coarse->d_W);
     cudaFree(c.coarse->d_w);
+    cudaFree(c.coarse->d_w2);
     delete c.coarse;
     c.coarse = nullptr;
 }
@@ -309,8 +319,9 @@ cudaError_t coarse_apply(Ctx &c, const double *r, double *z, cudaStream_t s)
     if (!c.coarse || !c.coarse->ready) return cudaSuccess;
     CoarseState &S = *c.coarse;
     k_coarse_restrict<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(S.d_curves, r, S.d_w);
-    k_coarse_solve<<<c.nCurves, kMaxCoarse, 0, s>>>(S.d_curves, S.d_L, S.d_w);
-    k_coarse_prolong<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_w, z);
+    k_coarse_solve<<<dim3((S.max_m - 1 + kSolveRows - 1) / kSolveRows, c.nCurves), 32 * kSolveRows, 0, s>>>(
+        S.d_curves, S.d_L, S.d_w, S.d_w2);
+    k_coarse_prolong<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_w2, z);
     c.launches += 3;
     return cudaGetLastError();
 }
