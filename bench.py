@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--workload", choices=["knots8x4096", "scene8x4096", "knot262144"], default="knots8x4096")
     ap.add_argument("--cg-rtol", type=float, default=None)
     ap.add_argument("--cg-maxit", type=int, default=None)
+    ap.add_argument("--cg-check-every", type=int, default=8,
+                    help="CG iterations per captured block between convergence polls")
     ap.add_argument("--precond-refresh", type=int, default=8,
                     help="rebuild the fitted symbols and coarse space every k-th solve set-up (the timed "
                          "steps start with a full set-up, so they never hold less than their share)")
@@ -120,7 +122,7 @@ def solver_params(name, args):
     # rounding floor at that size is above 1e-6); the 8 x 4096 scene solves to 1e-6.
     rtol = args.cg_rtol if args.cg_rtol is not None else (1e-3 if name == "knot262144" else 1e-6)
     maxit = args.cg_maxit if args.cg_maxit is not None else 2000
-    return dict(cg_rtol=rtol, cg_maxit=maxit, proj_cg_rtol=1e-3, cg_check_every=8,
+    return dict(cg_rtol=rtol, cg_maxit=maxit, proj_cg_rtol=1e-3, cg_check_every=args.cg_check_every,
                 precond_refresh=max(1, args.precond_refresh), coarse_dim=args.coarse_dim)
 
 
