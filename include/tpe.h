@@ -395,7 +395,8 @@ TPE_API tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, con
  * powers ((alpha, beta) = (2, 4.5)) it times, on the curve gamma, every candidate number of target
  * edges per thread of the energy (1, 2, 4), differential (1, 2) and apply / diag (1, 2, 4) gather
  * passes, and the symmetric energy, differential and apply passes (each unordered pair evaluated once, 1 or 2
- * targets per thread, when their partial sums fit in 16 GB), one warm-up and three timed passes each
+ * targets per thread, when their partial sums fit in 32 GB and in half the free device memory), one
+ * warm-up and three timed passes each
  * (CUDA events on `stream`), and keeps the fastest, rebuilding that op's work queue; other contexts
  * keep their defaults and are left unchanged.
  *   tpt (HOST int32 [6], may be NULL): the chosen targets per thread of the energy, differential and

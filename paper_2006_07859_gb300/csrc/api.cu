@@ -1222,6 +1222,13 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
         return pair_apply(c, gamma, 0, gamma, c.d_t2, s);  // any u times the same
     };
     cudaError_t err = cudaSuccess;
+    // a symmetric variant is a candidate while its partial sums fit in 32 GB and in half the free memory
+    // (on top of what the partial buffer already holds); the buffer is shrunk to the winners' need below
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+    auto fits = [&](size_t bytes) {
+        return bytes <= ((size_t)32 << 30) && bytes <= c.part_elems * sizeof(double) + free_b / 2;
+    };
     for (int cls = 0; cls < 3 && err == cudaSuccess; ++cls) {
         int cand[4];
         const int nc = tpt_candidates(c, cls, cand);
@@ -1254,7 +1261,7 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
             int best_sym = 0;
             for (int t = 1; t <= 4 && err == cudaSuccess; ++t) {
                 const int tpt_t = (t == 2 || t == 4) ? 2 : 1;
-                if (sym_slots(c, tpt_t) * (size_t)c.nE * 6 * sizeof(double) > ((size_t)16 << 30)) continue;
+                if (!fits(sym_slots(c, tpt_t) * (size_t)c.nE * 6 * sizeof(double))) continue;
                 if ((err = sym_select_diff(c, t)) != cudaSuccess) break;
                 if ((err = run(cls)) != cudaSuccess) break;
                 cudaEventRecord(e0, s);
@@ -1277,7 +1284,7 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
         if (cls == 0 && nc > 1 && err == cudaSuccess) {
             int best_sym = 0;
             for (int t = 1; t <= 2 && err == cudaSuccess; ++t) {
-                if (sym_slots(c, t) * (size_t)c.nE * sizeof(double) > ((size_t)16 << 30)) continue;
+                if (!fits(sym_slots(c, t) * (size_t)c.nE * sizeof(double))) continue;
                 if ((err = sym_select_energy(c, t)) != cudaSuccess) break;
                 if ((err = run(cls)) != cudaSuccess) break;
                 cudaEventRecord(e0, s);
@@ -1300,7 +1307,7 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
         if (cls == 2 && nc > 1 && err == cudaSuccess) {
             int best_sym = 0;
             for (int t = 1; t <= 2 && err == cudaSuccess; ++t) {
-                if (sym_slots(c, t) * (size_t)c.nE * 6 * sizeof(double) > ((size_t)16 << 30)) continue;
+                if (!fits(sym_slots(c, t) * (size_t)c.nE * 6 * sizeof(double))) continue;
                 if ((err = sym_select(c, t)) != cudaSuccess) break;
                 if ((err = run(cls)) != cudaSuccess) break;
                 cudaEventRecord(e0, s);
@@ -1325,6 +1332,22 @@ tp_status tp_autotune(tp_ctx *ctx, const double *gamma, int32_t *tpt, double *ms
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(err);
+    // keep only the partial buffer the chosen passes need (the candidates may have grown it)
+    {
+        const size_t nE1 = (size_t)std::max(1, c.nE);
+        size_t need = (size_t)std::max(std::max(c.plan_energy.max_slots, c.plan_diff.max_slots), c.plan_apply.max_slots) *
+                      nE1 * 6;
+        if (c.apply_sym) need = std::max(need, (size_t)c.plan_sym.max_slots * nE1 * 6);
+        if (c.energy_sym) need = std::max(need, (size_t)c.plan_sym_e.max_slots * nE1);
+        if (c.diff_sym) need = std::max(need, (size_t)c.plan_sym_d.max_slots * nE1 * 6);
+        if (need < c.part_elems) {
+            graphs_reset(c);  // captured blocks hold the old buffer's address
+            CK(cudaStreamSynchronize(s));
+            CK(cudaFree(c.d_part));
+            CK(cudaMalloc(&c.d_part, sizeof(double) * need));
+            c.part_elems = need;
+        }
+    }
     return check_err_word(ctx, s);
 }
 
