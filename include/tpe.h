@@ -173,8 +173,11 @@ typedef struct {
 typedef struct tp_ctx tp_ctx;
 
 /* Fill p with the defaults: (alpha, beta) = (2, 4.5), sigma = NaN, FP32, cg_rtol 1e-6,
- * cg_maxit 20000, spectral preconditioner, Armijo c = 1e-4, shrink 0.5, 30 halvings,
- * proj_tol 1e-10, proj_maxit 5, near_cutoff 4. */
+ * cg_maxit 20000, cg_check_every 8, proj_cg_rtol 1e-6, spectral preconditioner,
+ * Armijo c = 1e-4, shrink 0.5, 30 halvings, proj_tol 1e-10, proj_maxit 5, near_cutoff 4,
+ * far_cutoff 10, independent 0, use_graphs 1, precond_refresh 1, coarse_dim 128,
+ * constraint_set TP_CONSTRAINTS_TOTAL_LENGTH, line_search TP_LINESEARCH_UNIT,
+ * ccd_horizon 1.5, warm_start 1. */
 TPE_API void tp_default_params(tp_params *p);
 
 /* Create a context for a fixed graph.  edges_host: HOST int32 [n_edges][2] (i1, i2), the edge
