@@ -7,7 +7,7 @@ file adds the linear algebra on top of them with numpy, one library primitive pe
 (a dense solve, an FFT), in the order the paper states it:
 
   * constraints Phi and their Jacobian C ........... Sec. 8.1 (barycenter; total length or
-                                                     every edge length)
+                                                     every edge length; pinned points)
   * gradient saddle-point problem .................. Sec. 5.3.1, Eq. 22 (dense solve)
   * projected system P^T A P y = P^T a, x = P y .... App. B.3.3 (solved by CG)
   * constraint projection via z = C^+ b, x = z - y . Sec. 5.3.2 Eq. 23, App. B.3.4
@@ -201,52 +201,78 @@ def bilinear(gamma, edges, sigma, u, v):
 
 @dataclass
 class ConstraintGroup:
-    """Constraints of Sec. 8.1 over the edges [e0, e1): the barycenter (3 rows) and either the total
-    length (1 row) or, when l0 is given, one edge-length row per edge (Phi_I = l0_I - l_I).  The
-    total-length row is the sum of the edge-length rows, so the two are never combined."""
+    """Constraints of Sec. 8.1 over the edges [e0, e1), rows in this order: the barycenter (3 rows,
+    unless bary is False); either the total length (1 row) or, when l0 is given, one edge-length row
+    per edge (Phi_I = l0_I - l_I); then, when pins is given, three rows per pinned vertex v,
+    Phi_v = gamma_v - p0_v (the point constraint).  The total-length row is the sum of the
+    edge-length rows, so the two are never combined."""
     e0: int
     e1: int
     x0: np.ndarray
     L0: float
     l0: Optional[np.ndarray] = None
+    bary: bool = True
+    pins: Optional[np.ndarray] = None   # global vertex indices
+    p0: Optional[np.ndarray] = None     # [len(pins), 3] target positions
+
+    @property
+    def n_bary(self) -> int:
+        return 3 if self.bary else 0
+
+    @property
+    def n_length(self) -> int:
+        return 1 if self.l0 is None else self.e1 - self.e0
 
     @property
     def n_rows(self) -> int:
-        return 4 if self.l0 is None else 3 + (self.e1 - self.e0)
+        return self.n_bary + self.n_length + (0 if self.pins is None else 3 * len(self.pins))
 
 
-def constraint_groups(gamma, edges, edge_offsets=None, edge_lengths=False):
+def constraint_groups(gamma, edges, edge_offsets=None, edge_lengths=False, pins=None, barycenter=True):
     """x0, L0 (and, with edge_lengths, every l0_I) fixed at their values on the given curve; one
-    group per curve if edge_offsets is given, else one group for the whole graph."""
+    group per curve if edge_offsets is given, else one group for the whole graph.  pins (optional):
+    one array of global vertex indices per group (a single array when there is one group); each
+    pinned vertex is held at its position on the given curve."""
+    gamma = np.asarray(gamma, dtype=np.float64)
     ell, T, x = edge_quantities(gamma, edges)
     offs = [0, len(edges)] if edge_offsets is None else list(edge_offsets)
+    if pins is not None and len(offs) == 2 and np.ndim(pins[0]) == 0:
+        pins = [pins]
     groups = []
     for c in range(len(offs) - 1):
         e0, e1 = offs[c], offs[c + 1]
         L = ell[e0:e1].sum()
         x0 = (ell[e0:e1, None] * x[e0:e1]).sum(0) / L
-        groups.append(ConstraintGroup(e0, e1, x0, L, ell[e0:e1].copy() if edge_lengths else None))
+        pv = None if pins is None else np.asarray(pins[c], dtype=np.int64)
+        groups.append(ConstraintGroup(e0, e1, x0, L, ell[e0:e1].copy() if edge_lengths else None,
+                                      bary=barycenter, pins=pv,
+                                      p0=None if pv is None else gamma[pv].copy()))
     return groups
 
 
 def phi(gamma, edges, groups):
-    """Per group: Phi_barycenter = sum_I l_I (x_I - x0) (3 rows), then Phi_length = L0 - sum_I l_I
-    (1 row) or Phi_length,I = l0_I - l_I (one row per edge, in edge order)."""
+    """Per group: Phi_barycenter = sum_I l_I (x_I - x0) (3 rows, if present), then Phi_length =
+    L0 - sum_I l_I (1 row) or Phi_length,I = l0_I - l_I (one row per edge, in edge order), then
+    gamma_v - p0_v for each pinned vertex (3 rows each, in pin order)."""
+    gamma = np.asarray(gamma, dtype=np.float64)
     ell, T, x = edge_quantities(gamma, edges)
     out = []
     for gr in groups:
         s = slice(gr.e0, gr.e1)
-        out.extend(list((ell[s, None] * (x[s] - gr.x0)).sum(0)))
+        if gr.bary:
+            out.extend(list((ell[s, None] * (x[s] - gr.x0)).sum(0)))
         if gr.l0 is None:
             out.append(gr.L0 - ell[s].sum())
         else:
             out.extend(list(gr.l0 - ell[s]))
+        if gr.pins is not None:
+            out.extend(list((gamma[gr.pins] - gr.p0).reshape(-1)))
     return np.array(out)
 
 
 def jacobian(gamma, edges, groups):
     """C = d Phi, shape [total rows, nV, 3] (vertex-major columns), rows in the order of phi.
-    d l_I / d g_i2 = T_I = -d l_I / d g_i1 and d x_I / d g_ia = Id / 2."""
+    d l_I / d g_i2 = T_I = -d l_I / d g_i1, d x_I / d g_ia = Id / 2, d g_v / d g_v = Id."""
     g, e = _geom(gamma, edges)
     ell, T, x = edge_quantities(g, e)
     C = np.zeros((sum(gr.n_rows for gr in groups), g.shape[0], 3))
@@ -254,15 +280,21 @@ def jacobian(gamma, edges, groups):
     for gr in groups:
         for I in range(gr.e0, gr.e1):
             i1, i2 = e[I]
-            for k in range(3):
-                r = r0 + k
-                C[r, i2] += T[I] * (x[I, k] - gr.x0[k])
-                C[r, i1] -= T[I] * (x[I, k] - gr.x0[k])
-                C[r, i1, k] += 0.5 * ell[I]
-                C[r, i2, k] += 0.5 * ell[I]
-            r = r0 + 3 + (0 if gr.l0 is None else I - gr.e0)
+            if gr.bary:
+                for k in range(3):
+                    r = r0 + k
+                    C[r, i2] += T[I] * (x[I, k] - gr.x0[k])
+                    C[r, i1] -= T[I] * (x[I, k] - gr.x0[k])
+                    C[r, i1, k] += 0.5 * ell[I]
+                    C[r, i2, k] += 0.5 * ell[I]
+            r = r0 + gr.n_bary + (0 if gr.l0 is None else I - gr.e0)
             C[r, i2] -= T[I]
             C[r, i1] += T[I]
+        if gr.pins is not None:
+            rp = r0 + gr.n_bary + gr.n_length
+            for a, v in enumerate(gr.pins):
+                for k in range(3):
+                    C[rp + 3 * a + k, v, k] = 1.0
         r0 += gr.n_rows
     return C
 
