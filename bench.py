@@ -69,7 +69,7 @@ def parse():
                          "precision: per-result error of the 262,144-edge passes against the FP64 oracle on "
                          "a sample; batch: 1,024 independent knots of log-uniform size; learned: train the "
                          "learned preconditioner and compare times to 1e-6 against plain FP64 CG; "
-                         "constraints: descent steps with the total-length and the edge-length constraint sets")
+                         "constraints: descent steps with the total-length, edge-length and pinned-point constraint sets")
     ap.add_argument("--coarse-dim", type=int, default=128, help="hat functions per curve of the coarse space")
     ap.add_argument("--apply-variant", type=int, default=-1,
                     help="bench mode: after the autotuner, pin the apply pass (0 gather, 1 or 2 the symmetric "
@@ -393,19 +393,25 @@ def run_batch(args):
 
 
 def run_constraints(args):
-    """Descent steps under the two constraint sets of Sec. 8.1 on the 8 x 4096 benchmark knots (mixed
-    precision, two-level preconditioner): barycenter + total length against barycenter + every edge
-    length.  Reports steps/s, CG iterations and the largest edge-length drift after the steps."""
+    """Descent steps under the three constraint sets of Sec. 8.1 on the 8 x 4096 benchmark knots (mixed
+    precision, two-level preconditioner): barycenter + total length, barycenter + every edge length, and
+    four pinned vertices per knot (at 0, n/4, n/2, 3n/4) + total length.  Reports steps/s, CG iterations,
+    the largest edge-length drift and the largest pin deviation after the steps."""
     import torch
     import synth as S
     from paper_2006_07859_gb300 import tpe
     curves = S.eight_knots_4096(as_scene=False)
     res = {"mode": "constraints", "workload": "8_independent_fourier_knots_K8_n4096_seeds1-8", "steps": args.steps,
            "warmup": args.warmup}
-    for name, cs in (("total_length", tpe.TP_CONSTRAINTS_TOTAL_LENGTH), ("edge_lengths", tpe.TP_CONSTRAINTS_EDGE_LENGTHS)):
+    vo = curves.vertex_offsets
+    pins = np.concatenate([vo[k] + (np.arange(4) * (vo[k + 1] - vo[k])) // 4 for k in range(len(vo) - 1)])
+    for name, cs in (("total_length", tpe.TP_CONSTRAINTS_TOTAL_LENGTH), ("edge_lengths", tpe.TP_CONSTRAINTS_EDGE_LENGTHS),
+                     ("points", tpe.TP_CONSTRAINTS_POINTS)):
         ctx = tpe.Context.from_curves(curves, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_TWOLEVEL, independent=1,
                                       cg_rtol=1e-6, cg_maxit=2000, proj_cg_rtol=1e-3, constraint_set=cs,
                                       precond_refresh=args.precond_refresh)
+        if cs == tpe.TP_CONSTRAINTS_POINTS:
+            tpe.tp_set_pins(ctx, pins, curves.gamma[pins])
         tpe.tp_autotune(ctx, torch.as_tensor(curves.gamma).cuda())
         g = torch.as_tensor(curves.gamma).cuda()
         ell0 = np.linalg.norm(curves.gamma[curves.edges[:, 1]] - curves.gamma[curves.edges[:, 0]], axis=1)
@@ -426,7 +432,8 @@ def run_constraints(args):
         res[name] = {"steps_per_s": 1.0 / t, "ms_per_step": 1e3 * t,
                      "cg_iters": [i["cg_iters"] for i in infos], "proj_cg_iters": [i["proj_cg_iters"] for i in infos],
                      "E_after": infos[-1]["E_after"], "accepted": infos[-1]["accepted"],
-                     "max_rel_edge_length_drift": float(np.max(np.abs(ell / ell0 - 1.0)))}
+                     "max_rel_edge_length_drift": float(np.max(np.abs(ell / ell0 - 1.0))),
+                     "max_pin_deviation": float(np.max(np.abs(gh[pins] - curves.gamma[pins])))}
         ctx.close()
     print(json.dumps(res), flush=True)
 

@@ -11,8 +11,8 @@
  *   - the projected H^s gradient g~ of Eq. 22, solved as P A-bar P y = P dE, g~ = P y (App. B.3.3);
  *   - one descent step with normalised gradient, backtracking from tau = 1 and constraint
  *     projection (Secs. 5.3.2 and 5.4, App. B.3.4).
- * Constraints are those of Sec. 8.1: the barycenter with either the total length or every edge length
- * (tp_params.constraint_set).
+ * Constraints are those of Sec. 8.1: the barycenter with either the total length or every edge length,
+ * or pinned vertices with the total length (tp_params.constraint_set).
  *
  * Conventions shared by every entry point
  *   - Vertex arrays (gamma, dE, u, ...) are DEVICE pointers to double, vertex-major [nV][3].
@@ -23,7 +23,7 @@
  *   - The caller owns every pointer it passes; the context owns its own scratch memory,
  *     allocated once in tp_create and sized for the graph it was created with.  Only
  *     tp_set_params (switching a preconditioner, a constraint set or the line search on),
- *     tp_autotune (a larger work queue), the first tp_set_penalties and the first
+ *     tp_autotune (a larger work queue), the first tp_set_penalties, tp_set_pins and the first
  *     tp_collision_time allocate device memory after tp_create.
  *   - Every call returns a tp_status; nothing aborts or traps.  tp_last_error() gives a
  *     human-readable message for the last failing call on a context.
@@ -84,10 +84,13 @@ typedef enum {
  * the first call). */
 typedef enum {
     TP_CONSTRAINTS_TOTAL_LENGTH = 0, /* barycenter (3 rows) + total length L0 - sum_I l_I (1 row) per problem */
-    TP_CONSTRAINTS_EDGE_LENGTHS = 1  /* barycenter + one row l0_I - l_I per edge (isometric motions only).
+    TP_CONSTRAINTS_EDGE_LENGTHS = 1, /* barycenter + one row l0_I - l_I per edge (isometric motions only).
                                         Every curve's edges must be one simple chain in storage order
                                         (i1 of edge I + 1 = i2 of edge I; closed when the last edge ends at
                                         the first one's start) and curves may not share vertices */
+    TP_CONSTRAINTS_POINTS = 2        /* total length (1 row) + gamma_v - p_v (3 rows) per pinned vertex v,
+                                        no barycenter row (the pins fix the translations); the pins are
+                                        set by tp_set_pins, at least one in every problem */
 } tp_constraint_set;
 
 /* Start of the backtracking line search (Sec. 5.4). */
@@ -231,8 +234,20 @@ TPE_API tp_status tp_set_constraints_from(tp_ctx *ctx, const double *gamma, tp_s
 
 /* Constraint values Phi (Sec. 8.1) of gamma into phi (device [4 * n_problems]):
  * rows 4q..4q+2 barycenter, row 4q+3 length of problem q: L0 - sum_I l_I, or with
- * TP_CONSTRAINTS_EDGE_LENGTHS max_I |l0_I - l_I| over the problem's edges. */
+ * TP_CONSTRAINTS_EDGE_LENGTHS max_I |l0_I - l_I| over the problem's edges.  With
+ * TP_CONSTRAINTS_POINTS rows 4q..4q+2 hold instead max_v |gamma_v,k - p_v,k| over the problem's
+ * pinned vertices, component k. */
 TPE_API tp_status tp_constraints(tp_ctx *ctx, const double *gamma, double *phi, tp_stream stream);
+
+/* Pinned vertices of TP_CONSTRAINTS_POINTS (Sec. 8.1, point constraints gamma_v = p_v):
+ *   vertices HOST int32 [n], distinct, in [0, n_vertices); targets HOST double [n][3], finite.
+ *   Every problem needs at least one pinned vertex and at most 24 (each vertex belongs to the problem
+ *   of its curve); n = 0 removes the pins.  Both arrays are copied.
+ * The gradient then takes one more mean-free CG solve per three pins of the most pinned problem
+ * (A-bar^+ e_v, reused by every constraint projection of the step) and a dense solve of
+ * 3 k + 4 unknowns per problem (k its pins).  The first call allocates the pins' scratch.
+ * Errors: TP_ERR_INVALID_ARG (the rules above). */
+TPE_API tp_status tp_set_pins(tp_ctx *ctx, int n, const int32_t *vertices, const double *targets);
 
 /* Set (pen non-NULL, copied) or clear (NULL) the penalties the descent step adds (Sec. 8.1).  The first
  * call allocates their scratch.  Errors: TP_ERR_INVALID_ARG (a non-finite weight). */
@@ -256,6 +271,9 @@ TPE_API tp_status tp_collision_time(tp_ctx *ctx, const double *gamma, const doub
  * With TP_CONSTRAINTS_EDGE_LENGTHS, P is the orthogonal projector onto the mean-free velocities that
  * keep every edge length (one tridiagonal solve per curve and iteration), and a translation then
  * restores the barycenter row; the result is the same KKT solution of Eq. 22.
+ * With TP_CONSTRAINTS_POINTS the KKT solution is formed from mean-free solves (A-bar^+ dE,
+ * A-bar^+ C_len^T and A-bar^+ e_v for every pinned vertex v) and the Schur complement of the
+ * constraint rows and the translations; info then sums the iterations of all of them.
  * info (host, may be NULL) is filled after a stream synchronisation.
  * Returns TP_ERR_NOT_CONVERGED (g holds the last iterate) or TP_ERR_BREAKDOWN on failure. */
 TPE_API tp_status sobolev_gradient(tp_ctx *ctx, const double *gamma, const double *dE, double *g, tp_solve_info *info,

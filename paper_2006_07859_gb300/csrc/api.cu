@@ -58,7 +58,8 @@ bool params_ok(const tp_params *p, std::string &why)
         why = "coarse_dim must be >= 2";
         return false;
     }
-    if (p->constraint_set != TP_CONSTRAINTS_TOTAL_LENGTH && p->constraint_set != TP_CONSTRAINTS_EDGE_LENGTHS) {
+    if (p->constraint_set != TP_CONSTRAINTS_TOTAL_LENGTH && p->constraint_set != TP_CONSTRAINTS_EDGE_LENGTHS &&
+        p->constraint_set != TP_CONSTRAINTS_POINTS) {
         why = "bad constraint_set";
         return false;
     }
@@ -267,6 +268,7 @@ void tp_destroy(tp_ctx *ctx)
     edges_free(c);
     ccd_free(c);
     penalties_free(c);
+    pins_free(c);
     void *ptrs[] = {c.d_esum, c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_voff,
                     c.plan_energy.d_items, c.plan_diff.d_items, c.plan_apply.d_items, c.plan_energy.d_eslots,
                     c.plan_diff.d_eslots, c.plan_apply.d_eslots, c.d_counter, c.d_recF, c.d_recF2, c.d_recLo,
@@ -565,11 +567,31 @@ tp_status tp_set_constraints_from(tp_ctx *ctx, const double *gamma, tp_stream st
     return TP_OK;
 }
 
+// TP_CONSTRAINTS_POINTS without pins has no constraint rows to solve with.
+static tp_status need_pins(tp_ctx *ctx)
+{
+    if (pin_constraints(ctx->c) && !pins_ready(ctx->c))
+        return fail(ctx, TP_ERR_INVALID_ARG, "TP_CONSTRAINTS_POINTS: no pinned vertices (tp_set_pins)");
+    return TP_OK;
+}
+
+tp_status tp_set_pins(tp_ctx *ctx, int n, const int32_t *vertices, const double *targets)
+{
+    if (!ctx) return TP_ERR_INVALID_ARG;
+    std::string why;
+    cudaError_t e = pins_set(ctx->c, n, vertices, targets, why);
+    if (e == cudaErrorInvalidValue && !why.empty()) return fail(ctx, TP_ERR_INVALID_ARG, why);
+    CK(e);
+    return TP_OK;
+}
+
 tp_status tp_constraints(tp_ctx *ctx, const double *gamma, double *phi, tp_stream stream)
 {
     if (!ctx || !gamma || !phi) return TP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    tp_status st = records(ctx, gamma, 0, s);
+    tp_status st = need_pins(ctx);
+    if (st) return st;
+    st = records(ctx, gamma, 0, s);
     if (st) return st;
     if (!ctx->c.constraints_set) {
         CK(constraints_targets(ctx->c, 0, s));
@@ -669,6 +691,43 @@ static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE_
                                   int *conv, int *bd, cudaStream_t s, int *n_conv = nullptr)
 {
     std::vector<int> flags(c.nProb, 1);
+    if (pin_constraints(c)) {
+        // y0 = A^+ dE, y1 = A^+ C_len^T, the pins' fields A^+ e_v, then the Schur complement (pins.cu); no
+        // barycenter multiplier: the pins' rows take up N^T dE
+        int it = 0, cv = 1, b = 0;
+        double r = 0.0;
+        int i0 = 0, c0 = 0, b0 = 0;
+        double r0 = 0.0;
+        cudaError_t e = cg_solve(c, gamma, 0, dE_in, c.d_t3, c.prm.cg_rtol, c.prm.cg_maxit, &i0, &r0, &c0, &b0, s, 1,
+                                 flags.data(), (c.warm_ok && c.prm.warm_start) ? c.d_yw0 : nullptr);
+        if (e != cudaSuccess) return e;
+        it += i0;
+        r = std::max(r, r0);
+        cv = cv && c0;
+        b = b || b0;
+        if ((e = clen_rhs(c, c.d_t6, s)) != cudaSuccess) return e;
+        e = cg_solve(c, gamma, 0, c.d_t6, c.d_t4, c.prm.cg_rtol, c.prm.cg_maxit, &i0, &r0, &c0, &b0, s, 1,
+                     flags.data(), (c.warm_ok && c.prm.warm_start) ? c.d_yw1 : nullptr);
+        if (e != cudaSuccess) return e;
+        it += i0;
+        r = std::max(r, r0);
+        cv = cv && c0;
+        b = b || b0;
+        if ((e = pins_fields(c, gamma, c.d_t6, &it, &r, &cv, &b, flags.data(), s)) != cudaSuccess) return e;
+        const size_t vb = sizeof(double) * 3 * c.nV;
+        if ((e = cudaMemcpyAsync(c.d_yw0, c.d_t3, vb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(c.d_yw1, c.d_t4, vb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+        c.warm_ok = 1;
+        if (n_conv) {
+            *n_conv = 0;
+            for (int f : flags) *n_conv += f;
+        }
+        *iters = it;
+        *rr = r;
+        *conv = cv;
+        *bd = b;
+        return pins_gradient(c, dE_in, c.d_t3, c.d_t4, g, s);
+    }
     {
         cudaError_t e = bary_rhs(c, dE_in, c.d_t5, s);
         if (e != cudaSuccess) return e;
@@ -724,7 +783,9 @@ tp_status sobolev_gradient(tp_ctx *ctx, const double *gamma, const double *dE, d
     if (!ctx || !gamma || !dE || !g) return TP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     Ctx &c = ctx->c;
-    tp_status st = records(ctx, gamma, 0, s);
+    tp_status st = need_pins(ctx);
+    if (st) return st;
+    st = records(ctx, gamma, 0, s);
     if (st) return st;
     if (!c.constraints_set) {
         CK(constraints_targets(c, 0, s));
@@ -784,7 +845,9 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
     const int nP = c.nProb, nV = c.nV;
     const size_t vb = sizeof(double) * 3 * nV;
     const int nb = (nV + 255) / 256;
-    tp_status st = records(ctx, gamma, 0, s);
+    tp_status st = need_pins(ctx);
+    if (st) return st;
+    st = records(ctx, gamma, 0, s);
     if (st) return st;
     if (!c.constraints_set) {
         CK(constraints_targets(c, 0, s));
@@ -885,6 +948,13 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
                             s, 2));
                 CK(vec_axpby(c, 1.0, z0, -1.0, z, x, s));
                 CK(schur_shift(c, x, c.d_phi, -1.0, s));
+            } else if (pin_constraints(c)) {
+                // y1 = A-bar(gamma)^+ C_len(trial)^T; the pins' fields of the gradient step stay valid (their
+                // rows do not depend on the curve); x from the Schur complement (pins.cu)
+                CK(clen_rhs(c, rhs, s));
+                CK(cg_solve(c, gamma, 0, rhs, z, c.prm.proj_cg_rtol, c.prm.cg_maxit, &pit_cg, &prr, &pconv, &pbd,
+                            s, 1, nullptr, c.prm.warm_start ? z : nullptr));
+                CK(pins_projection(c, z, c.d_gam, c.d_phi, x, s));
             } else {
                 CK(clen_rhs(c, rhs, s));
                 // starts from z: A-bar^+ C_len^T of the pre-step curve (the gradient's second solve) or of

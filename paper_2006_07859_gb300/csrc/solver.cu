@@ -343,13 +343,15 @@ __global__ void k_pinv(int nV, const double *__restrict__ C, const double *__res
 
 // With TP_CONSTRAINTS_EDGE_LENGTHS the slot of the total-length row holds max_I |l0_I - l_I| over the
 // problem's edges (edges.cu), so that one max over the four slots decides the projection's success.
-cudaError_t constraints_eval(Ctx &c, const double *, int which, double *phi, cudaStream_t s)
+// With TP_CONSTRAINTS_POINTS the barycenter slots hold the pins' largest deviation per component (pins.cu).
+cudaError_t constraints_eval(Ctx &c, const double *gamma, int which, double *phi, cudaStream_t s)
 {
     SolverState &st = S(c);
     k_phi<<<st.e_n, kRedThreads, 0, s>>>(eargs(c, 0), c.d_ellw[which], c.d_xw[which], c.d_x0L0, c.d_eprob, phi);
     c.launches++;
     TPE_CHECK(cudaGetLastError());
     if (edge_constraints(c)) TPE_CHECK(edges_phi(c, which, phi, s));
+    if (pin_constraints(c) && pins_ready(c)) TPE_CHECK(pins_phi(c, gamma, phi, s));
     return cudaSuccess;
 }
 
@@ -1207,6 +1209,34 @@ cudaError_t schur_projection(Ctx &c, const double *y1, const double *phi, double
     k_schur_red<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_Cv, nullptr, x, red_out);
     k_schur_shift<<<nb, 256, 0, s>>>(c.nV, red_out, phi, phi_scale, c.d_vprob, x);
     c.launches += 4;
+    return cudaGetLastError();
+}
+
+// Reductions per problem for the pinned-point route (pins.cu): out[5q] = <C_len, a> (0 if a is NULL),
+// out[5q + 1] = <C_len, b>, out[5q + 2..4] = sum over the problem's vertices of dE (0 if dE is NULL).
+__global__ void k_pin_red(RedArgs ra, const double *__restrict__ C, const double *__restrict__ a,
+                          const double *__restrict__ b, const double *__restrict__ dE, double *__restrict__ out)
+{
+    double s[5] = {0, 0, 0, 0, 0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double *cv = C + (size_t)i * 12 + 9;
+        for (int j = 0; j < 3; ++j) {
+            if (a) s[0] += cv[j] * a[3 * (size_t)i + j];
+            s[1] += cv[j] * b[3 * (size_t)i + j];
+            if (dE) s[2 + j] += dE[3 * (size_t)i + j];
+        }
+    }
+    if (reduce_phase<5>(s, ra))
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x)
+            for (int k = 0; k < 5; ++k) out[5 * q + k] = ra.sums[5 * q + k];
+}
+
+cudaError_t pin_reduce(Ctx &c, const double *a, const double *b, const double *dE, double *out, cudaStream_t s)
+{
+    SolverState &st = S(c);
+    k_pin_red<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_Cv, a, b, dE, out);
+    c.launches++;
     return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ struct GnnState;
 struct EdgeState;
 struct CcdState;
 struct PenState;
+struct PinState;
 
 // Precision of the pair arithmetic.
 enum Prec { P64 = 0, P32 = 1, PMIX = 2 };
@@ -179,6 +180,7 @@ struct Ctx {
     EdgeState *edges = nullptr;   // edge-length constraint rows (edges.cu), allocated when first selected
     CcdState *ccd = nullptr;      // collision-time work list (ccd.cu), allocated when first used
     PenState *pen = nullptr;      // penalties of Sec. 8.1 (penalties.cu), allocated by tp_set_penalties
+    PinState *pins = nullptr;     // pinned vertices of TP_CONSTRAINTS_POINTS (pins.cu), allocated by tp_set_pins
     // captured CG iteration blocks
     cudaStream_t cg_stream = nullptr;
     cudaEvent_t cg_join[2] = {nullptr, nullptr};
@@ -277,6 +279,20 @@ cudaError_t ccd_time(Ctx &c, const double *gamma, const double *d, double T, dou
 inline bool edge_constraints(const Ctx &c)
 {
     return c.edges && c.prm.constraint_set == TP_CONSTRAINTS_EDGE_LENGTHS;
+}
+// point constraints of Sec. 8.1 (pins.cu)
+bool pins_ready(const Ctx &c);
+cudaError_t pins_set(Ctx &c, int n, const int32_t *vertices, const double *targets, std::string &why);
+void pins_free(Ctx &c);
+cudaError_t pins_phi(Ctx &c, const double *gamma, double *phi, cudaStream_t s);
+cudaError_t pins_fields(Ctx &c, const double *gamma, double *rhs_scratch, int *iters, double *rr, int *conv,
+                        int *bd, int *flags, cudaStream_t s);
+cudaError_t pins_gradient(Ctx &c, const double *dE, const double *y0, const double *y1, double *g, cudaStream_t s);
+cudaError_t pins_projection(Ctx &c, const double *y1, const double *gamma_t, const double *phi, double *x,
+                            cudaStream_t s);
+inline bool pin_constraints(const Ctx &c)
+{
+    return c.prm.constraint_set == TP_CONSTRAINTS_POINTS;
 }
 cudaError_t clen_rhs(Ctx &c, double *out, cudaStream_t s);
 cudaError_t schur_gradient(Ctx &c, const double *y0, const double *y1, double *g, cudaStream_t s);

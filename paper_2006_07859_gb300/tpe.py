@@ -19,7 +19,7 @@ TP_FP64, TP_FP32, TP_MIXED = 0, 1, 2
 TP_PRECOND_NONE, TP_PRECOND_JACOBI, TP_PRECOND_SPECTRAL, TP_PRECOND_SPECTRAL_RQ, TP_PRECOND_TWOLEVEL = 0, 1, 2, 3, 4
 TP_PRECOND_LEARNED = 5
 TP_GNN_HIDDEN, TP_GNN_FEATURES = 64, 8
-TP_CONSTRAINTS_TOTAL_LENGTH, TP_CONSTRAINTS_EDGE_LENGTHS = 0, 1
+TP_CONSTRAINTS_TOTAL_LENGTH, TP_CONSTRAINTS_EDGE_LENGTHS, TP_CONSTRAINTS_POINTS = 0, 1, 2
 TP_LINESEARCH_UNIT, TP_LINESEARCH_ISOTOPY = 0, 1
 
 STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ERR_DEGENERATE_EDGE",
@@ -34,7 +34,7 @@ EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp
             "tp_gnn_forward", "tp_gnn_backward", "tp_gnn_adam", "tp_gnn_g_apply", "tp_gnn_out_grad", "tp_cg_harvest",
             "tp_gnn_prepare_pairs", "tp_gnn_train_step", "tp_autotune", "tp_set_apply_variant",
             "tp_set_energy_variant", "tp_last_solve", "tp_set_diff_variant", "tp_collision_time",
-            "tp_set_penalties", "tp_penalty"]
+            "tp_set_penalties", "tp_penalty", "tp_set_pins"]
 
 
 class TpParams(ctypes.Structure):
@@ -105,6 +105,7 @@ def library() -> ctypes.CDLL:
         L.tp_collision_time.argtypes = [vp, vp, vp, ctypes.c_double, vp, vp]
         L.tp_set_penalties.argtypes = [vp, ctypes.POINTER(TpPenalties)]
         L.tp_penalty.argtypes = [vp, vp, vp, vp, vp]
+        L.tp_set_pins.argtypes = [vp, i, vp, vp]
         L.descent_step.argtypes = [vp, vp, ctypes.POINTER(TpStepInfo), vp]
         L.tp_launch_count.argtypes = [vp]
         L.tp_launch_count.restype = ctypes.c_int64
@@ -311,6 +312,17 @@ def tp_set_penalties(ctx: Context, w_length=0.0, w_length_diff=0.0, w_field=0.0,
     for k in range(3):
         p.field_b[k] = float(b[k])
     ctx._check(library().tp_set_penalties(ctx.handle, ctypes.byref(p)))
+
+
+def tp_set_pins(ctx: Context, vertices, targets):
+    """Pinned vertices of TP_CONSTRAINTS_POINTS (Sec. 8.1): vertex indices and their target positions
+    [n, 3] (host arrays, copied); an empty list removes the pins."""
+    v = np.ascontiguousarray(np.asarray(vertices, dtype=np.int32).reshape(-1))
+    t = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).reshape(-1, 3))
+    if t.shape[0] != v.shape[0]:
+        raise ValueError("one target per pinned vertex")
+    ctx._check(library().tp_set_pins(ctx.handle, int(v.shape[0]), v.ctypes.data if v.size else None,
+                                      t.ctypes.data if t.size else None))
 
 
 def tp_penalty(ctx: Context, gamma):
