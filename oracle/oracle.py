@@ -7,7 +7,8 @@ file adds the linear algebra on top of them with numpy, one library primitive pe
 (a dense solve, an FFT), in the order the paper states it:
 
   * constraints Phi and their Jacobian C ........... Sec. 8.1 (barycenter; total length or
-                                                     every edge length; pinned points)
+                                                     every edge length; pinned points, tangents
+                                                     and quadric surfaces)
   * gradient saddle-point problem .................. Sec. 5.3.1, Eq. 22 (dense solve)
   * projected system P^T A P y = P^T a, x = P y .... App. B.3.3 (solved by CG)
   * constraint projection via z = C^+ b, x = z - y . Sec. 5.3.2 Eq. 23, App. B.3.4
@@ -22,6 +23,8 @@ the design notes of the repository):
     null(C)).
   * A-bar in the constraint projection is the one of the pre-step curve; C is evaluated
     at the current iterate.
+  * The tangent constraint T_I = X keeps the two rows b_a . T_I across X (the printed three
+    rows T_I - X have a Jacobian of rank 2); the surface constraint takes a quadric f.
   * Armijo constant 1e-4, halving, at most 30 halvings; projection tolerance on
     max|Phi| relative to max(1, L0).
 
@@ -199,13 +202,35 @@ def bilinear(gamma, edges, sigma, u, v):
 
 # ----------------------------------------------------------------------------- constraints
 
+def perp_basis(X):
+    """Two orthonormal vectors spanning the plane orthogonal to the unit vector X: b1 = X x e_k / |.|
+    with e_k the coordinate axis least aligned with X, and b2 = X x b1."""
+    X = np.asarray(X, dtype=np.float64)
+    k = int(np.argmin(np.abs(X)))
+    e = np.zeros(3)
+    e[k] = 1.0
+    b1 = np.cross(X, e)
+    b1 /= np.linalg.norm(b1)
+    return b1, np.cross(X, b1)
+
+
+def quadric(x, Q, b, c):
+    """f(x) = x^T Q x + b^T x + c and its gradient (Q + Q^T) x + b (x: [..., 3])."""
+    x = np.asarray(x)
+    f = np.einsum("...i,ij,...j->...", x, Q, x) + x @ b + c
+    return f, x @ (Q + Q.T).T + b
+
+
 @dataclass
 class ConstraintGroup:
     """Constraints of Sec. 8.1 over the edges [e0, e1), rows in this order: the barycenter (3 rows,
     unless bary is False); either the total length (1 row) or, when l0 is given, one edge-length row
     per edge (Phi_I = l0_I - l_I); then, when pins is given, three rows per pinned vertex v,
-    Phi_v = gamma_v - p0_v (the point constraint).  The total-length row is the sum of the
-    edge-length rows, so the two are never combined."""
+    Phi_v = gamma_v - p0_v (the point constraint); then two rows per tangent-constrained edge I,
+    b_a . T_I with (b_1, b_2) = perp_basis(X_I) (the tangent constraint T_I = X_I; the printed three
+    rows T_I - X_I have a Jacobian of rank 2, since |T_I| = 1, so the two rows across X_I are kept);
+    then one row f(gamma_v) per vertex held on the quadric surface f = 0 (the surface constraint).
+    The total-length row is the sum of the edge-length rows, so the two are never combined."""
     e0: int
     e1: int
     x0: np.ndarray
@@ -214,6 +239,10 @@ class ConstraintGroup:
     bary: bool = True
     pins: Optional[np.ndarray] = None   # global vertex indices
     p0: Optional[np.ndarray] = None     # [len(pins), 3] target positions
+    tangents: Optional[np.ndarray] = None   # global edge indices
+    X: Optional[np.ndarray] = None          # [len(tangents), 3] unit target tangents
+    surf: Optional[np.ndarray] = None       # global vertex indices held on the surface
+    quad: Optional[tuple] = None            # (Q [3, 3], b [3], c) of f(x) = x^T Q x + b^T x + c
 
     @property
     def n_bary(self) -> int:
@@ -224,29 +253,59 @@ class ConstraintGroup:
         return 1 if self.l0 is None else self.e1 - self.e0
 
     @property
+    def n_pin_rows(self) -> int:
+        return 0 if self.pins is None else 3 * len(self.pins)
+
+    @property
+    def n_tangent_rows(self) -> int:
+        return 0 if self.tangents is None else 2 * len(self.tangents)
+
+    @property
     def n_rows(self) -> int:
-        return self.n_bary + self.n_length + (0 if self.pins is None else 3 * len(self.pins))
+        return (self.n_bary + self.n_length + self.n_pin_rows + self.n_tangent_rows +
+                (0 if self.surf is None else len(self.surf)))
 
 
-def constraint_groups(gamma, edges, edge_offsets=None, edge_lengths=False, pins=None, barycenter=True):
+def constraint_groups(gamma, edges, edge_offsets=None, edge_lengths=False, pins=None, barycenter=True,
+                      tangents=None, X=None, surf=None, quad=None):
     """x0, L0 (and, with edge_lengths, every l0_I) fixed at their values on the given curve; one
-    group per curve if edge_offsets is given, else one group for the whole graph.  pins (optional):
-    one array of global vertex indices per group (a single array when there is one group); each
-    pinned vertex is held at its position on the given curve."""
+    group per curve if edge_offsets is given, else one group for the whole graph.  pins, tangents,
+    surf (optional): one array of global vertex (edge) indices per group, or a single array when
+    there is one group.  Each pinned vertex is held at its position on the given curve; X (same
+    nesting as tangents) gives the unit target tangent of each tangent edge (default: its tangent on
+    the given curve); quad = (Q, b, c) is the surface of every group's surf vertices."""
     gamma = np.asarray(gamma, dtype=np.float64)
     ell, T, x = edge_quantities(gamma, edges)
     offs = [0, len(edges)] if edge_offsets is None else list(edge_offsets)
-    if pins is not None and len(offs) == 2 and np.ndim(pins[0]) == 0:
-        pins = [pins]
+
+    def per_group(a):
+        if a is None:
+            return [None] * (len(offs) - 1)
+        if len(offs) == 2 and (len(a) == 0 or np.ndim(a[0]) == 0):
+            return [a]
+        return list(a)
+
+    pins, tangents, surf = per_group(pins), per_group(tangents), per_group(surf)
+    if X is not None and len(offs) == 2 and np.ndim(X) == 2:
+        X = [X]
     groups = []
     for c in range(len(offs) - 1):
         e0, e1 = offs[c], offs[c + 1]
         L = ell[e0:e1].sum()
         x0 = (ell[e0:e1, None] * x[e0:e1]).sum(0) / L
-        pv = None if pins is None else np.asarray(pins[c], dtype=np.int64)
+        pv = None if pins[c] is None else np.asarray(pins[c], dtype=np.int64)
+        tv = None if tangents[c] is None else np.asarray(tangents[c], dtype=np.int64)
+        Xc = None
+        if tv is not None:
+            Xc = T[tv].copy() if X is None else np.asarray(X[c], dtype=np.float64).reshape(-1, 3)
+            Xc = Xc / np.linalg.norm(Xc, axis=1, keepdims=True)
+        sv = None if surf[c] is None else np.asarray(surf[c], dtype=np.int64)
         groups.append(ConstraintGroup(e0, e1, x0, L, ell[e0:e1].copy() if edge_lengths else None,
                                       bary=barycenter, pins=pv,
-                                      p0=None if pv is None else gamma[pv].copy()))
+                                      p0=None if pv is None else gamma[pv].copy(),
+                                      tangents=tv, X=Xc, surf=sv,
+                                      quad=None if sv is None else tuple(np.asarray(q, dtype=np.float64)
+                                                                        for q in quad)))
     return groups
 
 
@@ -267,6 +326,12 @@ def phi(gamma, edges, groups):
             out.extend(list(gr.l0 - ell[s]))
         if gr.pins is not None:
             out.extend(list((gamma[gr.pins] - gr.p0).reshape(-1)))
+        if gr.tangents is not None:
+            for I, X in zip(gr.tangents, gr.X):
+                b1, b2 = perp_basis(X)
+                out.extend([b1 @ T[I], b2 @ T[I]])
+        if gr.surf is not None:
+            out.extend(list(quadric(gamma[gr.surf], *gr.quad)[0]))
     return np.array(out)
 
 
@@ -290,11 +355,25 @@ def jacobian(gamma, edges, groups):
             r = r0 + gr.n_bary + (0 if gr.l0 is None else I - gr.e0)
             C[r, i2] -= T[I]
             C[r, i1] += T[I]
+        rp = r0 + gr.n_bary + gr.n_length
         if gr.pins is not None:
-            rp = r0 + gr.n_bary + gr.n_length
             for a, v in enumerate(gr.pins):
                 for k in range(3):
                     C[rp + 3 * a + k, v, k] = 1.0
+        rp += gr.n_pin_rows
+        if gr.tangents is not None:
+            # d (b . T_I) / d g_i2 = (I - T T^T) b / l_I = -d (b . T_I) / d g_i1
+            for a, (I, X) in enumerate(zip(gr.tangents, gr.X)):
+                i1, i2 = e[I]
+                for k, bk in enumerate(perp_basis(X)):
+                    row = (bk - (bk @ T[I]) * T[I]) / ell[I]
+                    C[rp + 2 * a + k, i2] += row
+                    C[rp + 2 * a + k, i1] -= row
+        rp += gr.n_tangent_rows
+        if gr.surf is not None:
+            grads = quadric(g[gr.surf], *gr.quad)[1]
+            for a, v in enumerate(gr.surf):
+                C[rp + a, v] = grads[a]
         r0 += gr.n_rows
     return C
 

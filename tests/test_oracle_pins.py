@@ -1,10 +1,11 @@
-"""Pins of the oracle's point constraints (Sec. 8.1: a vertex held at a target position) combined with
-the total length and no barycenter row.  CPU only.
+"""Pins of the oracle's point, tangent and surface constraints (Sec. 8.1: a vertex held at a target
+position, an edge's tangent held at a unit vector, a vertex held on a quadric surface) combined with the
+total length and no barycenter row.  CPU only.
 
 The constrained gradient of Eq. 22 is checked against a route that shares nothing with the oracle's
 Jacobian: the velocity space is reduced by deleting the pinned vertices' coordinates and then taking
-the null space of the total-length gradient, computed here by complex-step differentiation of the
-length itself; on that space the gradient solves the reduced Gram system."""
+the null space of complex-step derivatives of the length, of the tangents themselves and of the
+surface function; on that space the gradient solves the reduced Gram system."""
 import numpy as np
 import pytest
 import scipy.linalg as sla
@@ -128,3 +129,141 @@ def test_descent_with_pins_keeps_them_and_lowers_energy(orc):
         E = info.E_after
         assert np.abs(cur[pins] - g[pins]).max() <= 1e-10
         assert abs(total_length(cur, e) - gr[0].L0) <= 1e-10 * gr[0].L0
+
+
+# ------------------------------------------------------------------ tangent and surface rows (Sec. 8.1)
+
+def _sphere(center, radius):
+    """Quadric (Q, b, c) of |x - center|^2 - radius^2."""
+    center = np.asarray(center, dtype=np.float64)
+    return np.eye(3), -2.0 * center, float(center @ center - radius * radius)
+
+
+def _plane_through(p, q, r):
+    n = np.cross(q - p, r - p)
+    n /= np.linalg.norm(n)
+    return np.zeros((3, 3)), n, -float(n @ p)
+
+
+def _complex_step_rows(fun, gamma):
+    """Jacobian [m, nV, 3] of fun (complex-safe, R^{nV x 3} -> R^m) by complex steps."""
+    h = 1e-30
+    m = len(fun(gamma.astype(np.complex128)))
+    J = np.zeros((m, gamma.shape[0], 3))
+    for v in range(gamma.shape[0]):
+        for k in range(3):
+            gc = gamma.astype(np.complex128)
+            gc[v, k] += 1j * h
+            J[:, v, k] = fun(gc).imag / h
+    return J
+
+
+def _tangent(gamma, edges, I):
+    d = gamma[edges[I, 1]] - gamma[edges[I, 0]]
+    return d / np.sqrt((d * d).sum())
+
+
+def test_tangent_and_surface_rows_match_differences(orc):
+    c = S.single(S.fourier_knot(14, 3, 21), closed=False)
+    g, e = c.gamma, c.edges
+    X = np.array([[0.3, -0.5, 0.8], [1.0, 0.2, -0.1]])
+    quad = _sphere(g.mean(0), 0.7)
+    gr = orc.constraint_groups(g, e, pins=np.array([0]), barycenter=False, tangents=np.array([0, 12]), X=X,
+                               surf=np.array([5, 9]), quad=quad)
+    assert gr[0].n_rows == 1 + 3 + 4 + 2
+    C = orc.jacobian(g, e, gr)
+    h = 1e-6
+    J = np.zeros_like(C)
+    for v in range(14):
+        for k in range(3):
+            gp, gm = g.copy(), g.copy()
+            gp[v, k] += h
+            gm[v, k] -= h
+            J[:, v, k] = (orc.phi(gp, e, gr) - orc.phi(gm, e, gr)) / (2 * h)
+    assert np.abs(J - C).max() <= 1e-8 * max(1.0, np.abs(C).max())
+    # the two tangent rows of an edge vanish exactly when T_I = X_I
+    gr0 = orc.constraint_groups(g, e, pins=np.array([0]), barycenter=False, tangents=np.array([3]))
+    assert np.abs(orc.phi(g, e, gr0)).max() <= 1e-15
+
+
+@pytest.mark.parametrize("closed", [True, False])
+def test_gradient_with_tangents_and_surface_matches_reduced_space_solve(orc, closed):
+    """The velocity space is {g : g = 0 at the pins, dL g = 0, dT_I g = 0, df(gamma_v) g = 0}, built
+    from complex-step derivatives of the length, of T_I itself (three rows of rank 2) and of f, not
+    from the oracle's rows; the oracle's KKT gradient must be the reduced solve on it."""
+    if closed:
+        c = S.single(S.trefoil(24, 0.01, 22))
+        pins, tans, surf = np.array([2]), np.array([6, 15]), np.array([10, 20])
+    else:
+        c = S.single(S.fourier_knot(22, 3, 23), closed=False)
+        pins, tans, surf = np.array([0, 21]), np.array([0, 20]), np.array([11])
+    g, e = c.gamma, c.edges
+    quad = _sphere(g[surf].mean(0) + np.array([0.1, -0.2, 0.05]), 0.9)
+    gr = orc.constraint_groups(g, e, pins=pins, barycenter=False, tangents=tans, surf=surf, quad=quad)
+    dE = orc.differential(g, e)
+    gk, _ = orc.sobolev_gradient(g, e, gr, dE, orc.Params(), dense=True)
+    Q, b, c0 = quad
+
+    def rows(x):
+        out = [total_length(x, e)]
+        for I in tans:
+            out.extend(list(_tangent(x, e, I)))
+        for v in surf:
+            out.append(x[v] @ Q @ x[v] + b @ x[v] + c0)
+        return np.array(out)
+
+    J = _complex_step_rows(rows, g)
+    n = g.shape[0]
+    Jcm = np.stack([J[r].T.reshape(-1) for r in range(J.shape[0])])
+    for v in pins:                      # pinned coordinates, component-major
+        for k in range(3):
+            row = np.zeros(3 * n)
+            row[k * n + v] = 1.0
+            Jcm = np.vstack([Jcm, row])
+    Z = sla.null_space(Jcm)
+    B, B0 = orc.gram_dense(g, e, SIG)
+    Ab = np.kron(np.eye(3), B + B0)
+    gz = Z @ np.linalg.solve(Z.T @ Ab @ Z, Z.T @ dE.T.reshape(-1))
+    ref = gz.reshape(3, n).T
+    np.testing.assert_allclose(gk, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+    assert Z.shape[1] == 3 * n - (1 + 2 * len(tans) + len(surf) + 3 * len(pins))
+
+
+def test_projection_reaches_tangent_and_surface_targets(orc):
+    """From a perturbed open curve the projection restores the end pins, rotates the end edges onto
+    their target tangents, and returns three vertices to the plane through them."""
+    c = S.single(S.fourier_knot(30, 3, 24), closed=False)
+    g, e = c.gamma, c.edges
+    pins, tans, surf = np.array([0, 29]), np.array([0, 28]), np.array([10, 15, 20])
+    quad = _plane_through(*g[surf])
+    T = orc.edge_quantities(g, e)[1]
+    X = np.array([T[0] + [0.0, 0.01, 0.0], T[28] + [0.01, 0.0, -0.01]])
+    X /= np.linalg.norm(X, axis=1, keepdims=True)
+    gr = orc.constraint_groups(g, e, pins=pins, barycenter=False, tangents=tans, X=X, surf=surf, quad=quad)
+    rng = np.random.default_rng(25)
+    moved = g + 1e-3 * rng.normal(size=g.shape)
+    out, it, ok = orc.constraint_projection(moved, e, gr, orc.make_apply(g, e, SIG), orc.Params(proj_cg_tol=1e-12))
+    assert ok and 1 <= it <= 5
+    assert np.abs(out[pins] - g[pins]).max() <= 1e-10
+    for I, x in zip(tans, X):
+        assert np.abs(_tangent(out, e, I) - x).max() <= 1e-10
+    f, _ = orc.quadric(out[surf], *quad)
+    assert np.abs(f).max() <= 1e-10
+    assert abs(total_length(out, e) - gr[0].L0) <= 1e-10 * gr[0].L0
+
+
+def test_descent_with_tangents_and_surface_keeps_them(orc):
+    c = S.single(S.fourier_knot(26, 3, 26), closed=False)
+    g, e = c.gamma, c.edges
+    pins, tans, surf = np.array([0, 25]), np.array([0, 24]), np.array([12])
+    quad = _sphere(np.zeros(3), float(np.linalg.norm(g[12])))
+    gr = orc.constraint_groups(g, e, pins=pins, barycenter=False, tangents=tans, surf=surf, quad=quad)
+    T0 = orc.edge_quantities(g, e)[1][tans]
+    prm = orc.Params(cg_tol=1e-10, proj_cg_tol=1e-10)
+    cur, E = g.copy(), orc.energy(g, e)
+    for _ in range(2):
+        cur, info = orc.descent_step(cur, e, gr, prm)
+        assert info.accepted and info.E_after < E
+        E = info.E_after
+        assert np.abs(orc.edge_quantities(cur, e)[1][tans] - T0).max() <= 1e-9
+        assert abs(np.linalg.norm(cur[12]) - np.linalg.norm(g[12])) <= 1e-10
