@@ -12,7 +12,7 @@
  *   - one descent step with normalised gradient, backtracking from tau = 1 and constraint
  *     projection (Secs. 5.3.2 and 5.4, App. B.3.4).
  * Constraints are those of Sec. 8.1: the barycenter with either the total length or every edge length,
- * or pinned vertices with the total length (tp_params.constraint_set).
+ * or the total length with pinned vertices, tangents and surface points (tp_params.constraint_set).
  *
  * Conventions shared by every entry point
  *   - Vertex arrays (gamma, dE, u, ...) are DEVICE pointers to double, vertex-major [nV][3].
@@ -23,8 +23,9 @@
  *   - The caller owns every pointer it passes; the context owns its own scratch memory,
  *     allocated once in tp_create and sized for the graph it was created with.  Only
  *     tp_set_params (switching a preconditioner, a constraint set or the line search on),
- *     tp_autotune (a larger work queue), the first tp_set_penalties, tp_set_pins and the first
- *     tp_collision_time allocate device memory after tp_create.
+ *     tp_autotune (a larger work queue), the first tp_set_penalties, the first tp_set_pins,
+ *     tp_set_tangents or tp_set_surface (and one that needs more solves than any before) and the
+ *     first tp_collision_time allocate device memory after tp_create.
  *   - Every call returns a tp_status; nothing aborts or traps.  tp_last_error() gives a
  *     human-readable message for the last failing call on a context.
  *   - A context is not thread-safe; use one context per host thread.
@@ -88,9 +89,10 @@ typedef enum {
                                         Every curve's edges must be one simple chain in storage order
                                         (i1 of edge I + 1 = i2 of edge I; closed when the last edge ends at
                                         the first one's start) and curves may not share vertices */
-    TP_CONSTRAINTS_POINTS = 2        /* total length (1 row) + gamma_v - p_v (3 rows) per pinned vertex v,
-                                        no barycenter row (the pins fix the translations); the pins are
-                                        set by tp_set_pins, at least one in every problem */
+    TP_CONSTRAINTS_POINTS = 2        /* total length (1 row) + gamma_v - p_v (3 rows) per pinned vertex v
+                                        (tp_set_pins, at least one in every problem), optional tangent rows
+                                        (tp_set_tangents) and surface rows (tp_set_surface); no barycenter
+                                        row (the pins fix the translations) */
 } tp_constraint_set;
 
 /* Start of the backtracking line search (Sec. 5.4). */
@@ -235,19 +237,33 @@ TPE_API tp_status tp_set_constraints_from(tp_ctx *ctx, const double *gamma, tp_s
 /* Constraint values Phi (Sec. 8.1) of gamma into phi (device [4 * n_problems]):
  * rows 4q..4q+2 barycenter, row 4q+3 length of problem q: L0 - sum_I l_I, or with
  * TP_CONSTRAINTS_EDGE_LENGTHS max_I |l0_I - l_I| over the problem's edges.  With
- * TP_CONSTRAINTS_POINTS rows 4q..4q+2 hold instead max_v |gamma_v,k - p_v,k| over the problem's
- * pinned vertices, component k. */
+ * TP_CONSTRAINTS_POINTS rows 4q..4q+2 hold instead, over the problem's constrained items, the largest
+ * |gamma_v,k - p_v,k| (pins), |T_I,k - X_I,k| (tangents) and |f(gamma_v)| (surface points). */
 TPE_API tp_status tp_constraints(tp_ctx *ctx, const double *gamma, double *phi, tp_stream stream);
 
-/* Pinned vertices of TP_CONSTRAINTS_POINTS (Sec. 8.1, point constraints gamma_v = p_v):
- *   vertices HOST int32 [n], distinct, in [0, n_vertices); targets HOST double [n][3], finite.
- *   Every problem needs at least one pinned vertex and at most 24 (each vertex belongs to the problem
- *   of its curve); n = 0 removes the pins.  Both arrays are copied.
- * The gradient then takes one more mean-free CG solve per three pins of the most pinned problem
- * (A-bar^+ e_v, reused by every constraint projection of the step) and a dense solve of
- * 3 k + 4 unknowns per problem (k its pins).  The first call allocates the pins' scratch.
- * Errors: TP_ERR_INVALID_ARG (the rules above). */
+/* Rows of TP_CONSTRAINTS_POINTS (Sec. 8.1).  All three calls copy their arrays, replace the previous
+ * list of their kind (n = 0 removes it) and may be made in any order; a call whose list breaks a rule
+ * returns TP_ERR_INVALID_ARG and leaves every list as it was.  Rules, per problem (each vertex or edge
+ * belongs to the problem of its curve): at most 24 distinct constrained vertices (pinned vertices,
+ * endpoints of tangent edges and surface vertices together) and at most 96 rows (3 per pin, 2 per
+ * tangent, 1 per surface vertex); no surface vertex pinned; no tangent edge with both ends pinned.
+ * The gradient takes one mean-free CG solve per three constrained vertices of the most constrained
+ * problem (A-bar^+ e_v, reused by every constraint projection of the step) and a dense solve of
+ * rows + 4 unknowns per problem.  The first call allocates the rows' scratch.
+ *
+ * Point constraints gamma_v = p_v: vertices HOST int32 [n], distinct, in [0, n_vertices); targets HOST
+ * double [n][3], finite.  Every problem needs at least one pinned vertex. */
 TPE_API tp_status tp_set_pins(tp_ctx *ctx, int n, const int32_t *vertices, const double *targets);
+
+/* Tangent constraints T_I = X_I: edges HOST int32 [n], distinct, in [0, n_edges); X HOST double [n][3],
+ * finite and nonzero (normalised by the library).  Each edge contributes the two rows b_a . T_I, with
+ * (b_1, b_2) an orthonormal basis across X_I (the three rows T_I - X_I have a Jacobian of rank 2). */
+TPE_API tp_status tp_set_tangents(tp_ctx *ctx, int n, const int32_t *edges, const double *X);
+
+/* Surface constraints f(gamma_v) = 0 for one quadric f(x) = x^T Q x + b^T x + c (planes, spheres,
+ * ellipsoids, cylinders, ...): quadric HOST double [13] = Q row-major (9), b (3), c, finite; vertices HOST
+ * int32 [n], distinct, in [0, n_vertices). */
+TPE_API tp_status tp_set_surface(tp_ctx *ctx, const double *quadric, int n, const int32_t *vertices);
 
 /* Set (pen non-NULL, copied) or clear (NULL) the penalties the descent step adds (Sec. 8.1).  The first
  * call allocates their scratch.  Errors: TP_ERR_INVALID_ARG (a non-finite weight). */
@@ -272,7 +288,7 @@ TPE_API tp_status tp_collision_time(tp_ctx *ctx, const double *gamma, const doub
  * keep every edge length (one tridiagonal solve per curve and iteration), and a translation then
  * restores the barycenter row; the result is the same KKT solution of Eq. 22.
  * With TP_CONSTRAINTS_POINTS the KKT solution is formed from mean-free solves (A-bar^+ dE,
- * A-bar^+ C_len^T and A-bar^+ e_v for every pinned vertex v) and the Schur complement of the
+ * A-bar^+ C_len^T and A-bar^+ e_v for every constrained vertex v) and the Schur complement of the
  * constraint rows and the translations; info then sums the iterations of all of them.
  * info (host, may be NULL) is filled after a stream synchronisation.
  * Returns TP_ERR_NOT_CONVERGED (g holds the last iterate) or TP_ERR_BREAKDOWN on failure. */

@@ -585,6 +585,26 @@ tp_status tp_set_pins(tp_ctx *ctx, int n, const int32_t *vertices, const double 
     return TP_OK;
 }
 
+tp_status tp_set_tangents(tp_ctx *ctx, int n, const int32_t *edges, const double *X)
+{
+    if (!ctx) return TP_ERR_INVALID_ARG;
+    std::string why;
+    cudaError_t e = tangents_set(ctx->c, n, edges, X, why);
+    if (e == cudaErrorInvalidValue && !why.empty()) return fail(ctx, TP_ERR_INVALID_ARG, why);
+    CK(e);
+    return TP_OK;
+}
+
+tp_status tp_set_surface(tp_ctx *ctx, const double *quadric, int n, const int32_t *vertices)
+{
+    if (!ctx) return TP_ERR_INVALID_ARG;
+    std::string why;
+    cudaError_t e = surface_set(ctx->c, quadric, n, vertices, why);
+    if (e == cudaErrorInvalidValue && !why.empty()) return fail(ctx, TP_ERR_INVALID_ARG, why);
+    CK(e);
+    return TP_OK;
+}
+
 tp_status tp_constraints(tp_ctx *ctx, const double *gamma, double *phi, tp_stream stream)
 {
     if (!ctx || !gamma || !phi) return TP_ERR_INVALID_ARG;
@@ -726,7 +746,7 @@ static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE_
         *rr = r;
         *conv = cv;
         *bd = b;
-        return pins_gradient(c, dE_in, c.d_t3, c.d_t4, g, s);
+        return pins_gradient(c, gamma, dE_in, c.d_t3, c.d_t4, g, s);
     }
     {
         cudaError_t e = bary_rhs(c, dE_in, c.d_t5, s);

@@ -343,7 +343,7 @@ __global__ void k_pinv(int nV, const double *__restrict__ C, const double *__res
 
 // With TP_CONSTRAINTS_EDGE_LENGTHS the slot of the total-length row holds max_I |l0_I - l_I| over the
 // problem's edges (edges.cu), so that one max over the four slots decides the projection's success.
-// With TP_CONSTRAINTS_POINTS the barycenter slots hold the pins' largest deviation per component (pins.cu).
+// With TP_CONSTRAINTS_POINTS the barycenter slots hold the largest pin, tangent and surface residuals (pins.cu).
 cudaError_t constraints_eval(Ctx &c, const double *gamma, int which, double *phi, cudaStream_t s)
 {
     SolverState &st = S(c);
@@ -351,7 +351,7 @@ cudaError_t constraints_eval(Ctx &c, const double *gamma, int which, double *phi
     c.launches++;
     TPE_CHECK(cudaGetLastError());
     if (edge_constraints(c)) TPE_CHECK(edges_phi(c, which, phi, s));
-    if (pin_constraints(c) && pins_ready(c)) TPE_CHECK(pins_phi(c, gamma, phi, s));
+    if (pin_constraints(c) && pins_ready(c)) TPE_CHECK(pins_phi(c, gamma, which, phi, s));
     return cudaSuccess;
 }
 

@@ -180,7 +180,7 @@ struct Ctx {
     EdgeState *edges = nullptr;   // edge-length constraint rows (edges.cu), allocated when first selected
     CcdState *ccd = nullptr;      // collision-time work list (ccd.cu), allocated when first used
     PenState *pen = nullptr;      // penalties of Sec. 8.1 (penalties.cu), allocated by tp_set_penalties
-    PinState *pins = nullptr;     // pinned vertices of TP_CONSTRAINTS_POINTS (pins.cu), allocated by tp_set_pins
+    PinState *pins = nullptr;     // point / tangent / surface rows of TP_CONSTRAINTS_POINTS (pins.cu)
     // captured CG iteration blocks
     cudaStream_t cg_stream = nullptr;
     cudaEvent_t cg_join[2] = {nullptr, nullptr};
@@ -280,14 +280,17 @@ inline bool edge_constraints(const Ctx &c)
 {
     return c.edges && c.prm.constraint_set == TP_CONSTRAINTS_EDGE_LENGTHS;
 }
-// point constraints of Sec. 8.1 (pins.cu)
+// point, tangent and surface constraints of Sec. 8.1 (pins.cu)
 bool pins_ready(const Ctx &c);
 cudaError_t pins_set(Ctx &c, int n, const int32_t *vertices, const double *targets, std::string &why);
+cudaError_t tangents_set(Ctx &c, int n, const int32_t *edges, const double *X, std::string &why);
+cudaError_t surface_set(Ctx &c, const double *quadric, int n, const int32_t *vertices, std::string &why);
 void pins_free(Ctx &c);
-cudaError_t pins_phi(Ctx &c, const double *gamma, double *phi, cudaStream_t s);
+cudaError_t pins_phi(Ctx &c, const double *gamma, int which, double *phi, cudaStream_t s);
 cudaError_t pins_fields(Ctx &c, const double *gamma, double *rhs_scratch, int *iters, double *rr, int *conv,
                         int *bd, int *flags, cudaStream_t s);
-cudaError_t pins_gradient(Ctx &c, const double *dE, const double *y0, const double *y1, double *g, cudaStream_t s);
+cudaError_t pins_gradient(Ctx &c, const double *gamma, const double *dE, const double *y0, const double *y1,
+                          double *g, cudaStream_t s);
 cudaError_t pins_projection(Ctx &c, const double *y1, const double *gamma_t, const double *phi, double *x,
                             cudaStream_t s);
 inline bool pin_constraints(const Ctx &c)

@@ -34,7 +34,8 @@ EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp
             "tp_gnn_forward", "tp_gnn_backward", "tp_gnn_adam", "tp_gnn_g_apply", "tp_gnn_out_grad", "tp_cg_harvest",
             "tp_gnn_prepare_pairs", "tp_gnn_train_step", "tp_autotune", "tp_set_apply_variant",
             "tp_set_energy_variant", "tp_last_solve", "tp_set_diff_variant", "tp_collision_time",
-            "tp_set_penalties", "tp_penalty", "tp_set_pins"]
+            "tp_set_penalties", "tp_penalty", "tp_set_pins",
+            "tp_set_tangents", "tp_set_surface"]
 
 
 class TpParams(ctypes.Structure):
@@ -106,6 +107,8 @@ def library() -> ctypes.CDLL:
         L.tp_set_penalties.argtypes = [vp, ctypes.POINTER(TpPenalties)]
         L.tp_penalty.argtypes = [vp, vp, vp, vp, vp]
         L.tp_set_pins.argtypes = [vp, i, vp, vp]
+        L.tp_set_tangents.argtypes = [vp, i, vp, vp]
+        L.tp_set_surface.argtypes = [vp, vp, i, vp]
         L.descent_step.argtypes = [vp, vp, ctypes.POINTER(TpStepInfo), vp]
         L.tp_launch_count.argtypes = [vp]
         L.tp_launch_count.restype = ctypes.c_int64
@@ -323,6 +326,28 @@ def tp_set_pins(ctx: Context, vertices, targets):
         raise ValueError("one target per pinned vertex")
     ctx._check(library().tp_set_pins(ctx.handle, int(v.shape[0]), v.ctypes.data if v.size else None,
                                       t.ctypes.data if t.size else None))
+
+
+def tp_set_tangents(ctx: Context, edges, X):
+    """Tangent constraints T_I = X_I of TP_CONSTRAINTS_POINTS (Sec. 8.1): edge indices and target
+    directions [n, 3] (normalised by the library); an empty list removes them."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1))
+    x = np.ascontiguousarray(np.asarray(X, dtype=np.float64).reshape(-1, 3))
+    if x.shape[0] != e.shape[0]:
+        raise ValueError("one target per tangent edge")
+    ctx._check(library().tp_set_tangents(ctx.handle, int(e.shape[0]), e.ctypes.data if e.size else None,
+                                          x.ctypes.data if x.size else None))
+
+
+def tp_set_surface(ctx: Context, vertices, Q=None, b=None, c=0.0):
+    """Surface constraints f(gamma_v) = 0 of TP_CONSTRAINTS_POINTS (Sec. 8.1) for the quadric
+    f(x) = x^T Q x + b^T x + c; an empty vertex list removes them."""
+    v = np.ascontiguousarray(np.asarray(vertices, dtype=np.int32).reshape(-1))
+    q = np.zeros(13)
+    q[:9] = np.zeros(9) if Q is None else np.asarray(Q, dtype=np.float64).reshape(9)
+    q[9:12] = np.zeros(3) if b is None else np.asarray(b, dtype=np.float64).reshape(3)
+    q[12] = float(c)
+    ctx._check(library().tp_set_surface(ctx.handle, q.ctypes.data, int(v.shape[0]), v.ctypes.data if v.size else None))
 
 
 def tp_penalty(ctx: Context, gamma):

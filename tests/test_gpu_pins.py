@@ -1,8 +1,9 @@
-"""Point constraints (Sec. 8.1, TP_CONSTRAINTS_POINTS: pinned vertices with the total length, no
-barycenter row) on the GPU against the oracle: the projected gradient against the dense KKT solve of
-Eq. 22 (one pin, more pins than one three-column solve holds, open curves pinned at both ends, an
-independent batch with ragged pin counts, two curves in one problem), descent steps against the oracle's,
-a mixed-precision run on a 4,096-vertex knot with the two-level preconditioner, and the argument checks."""
+"""Point, tangent and surface constraints (Sec. 8.1, TP_CONSTRAINTS_POINTS: pinned vertices, edges with
+a fixed tangent, vertices on a quadric, with the total length and no barycenter row) on the GPU against
+the oracle: the projected gradient against the dense KKT solve of Eq. 22 (one pin, more constrained
+vertices than one three-column solve holds, open curves pinned at both ends, an independent batch with
+ragged counts, two curves in one problem), descent steps against the oracle's, a mixed-precision run on a
+4,096-vertex knot with the two-level preconditioner, and the argument checks."""
 import numpy as np
 import pytest
 
@@ -139,12 +140,131 @@ def test_pin_arguments_are_checked(torch):
         tpe.tp_set_pins(ctx, [0, 45], np.array([[0.0, np.nan, 0.0], [0.0, 0.0, 0.0]]))
     tpe.tp_set_pins(ctx, [3, 45], b.gamma[[3, 45]])
     tpe.sobolev_gradient(ctx, g, tpe.tp_differential(ctx, g))
-    # the barycenter slots of tp_constraints report the pins' deviation per component
+    # the barycenter slots of tp_constraints report the largest pin, tangent and surface residuals
     moved = b.gamma.copy()
     moved[45] += np.array([0.0, 2e-3, -5e-4])
     phi = host(tpe.tp_constraints(ctx, dev(moved))).reshape(2, 4)
     np.testing.assert_allclose(phi[0, :3], 0.0, atol=0.0)
-    np.testing.assert_allclose(phi[1, :3], [0.0, 2e-3, 5e-4], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(phi[1, :3], [2e-3, 0.0, 0.0], rtol=1e-12, atol=1e-15)
     tpe.tp_set_pins(ctx, [], np.zeros((0, 3)))
     with pytest.raises(tpe.TpError):
         tpe.sobolev_gradient(ctx, g, tpe.tp_differential(ctx, g))
+
+
+def _sphere(center, radius):
+    center = np.asarray(center, dtype=np.float64)
+    return np.eye(3), -2.0 * center, float(center @ center - radius * radius)
+
+
+def _rows_case(name):
+    """(curves, independent, precond, pins, tangent edges, surface vertices) per problem, global indices."""
+    if name == "closed":
+        return S.single(S.trefoil(64, 0.01, 3)), 0, 2, [[2]], [[6, 30]], [[10, 40]]
+    if name == "open":
+        return S.single(S.fourier_knot(50, 4, 5), closed=False), 0, 1, [[0, 49]], [[0, 48]], [[25]]
+    if name == "batch":
+        b = S.batch_of_knots([40, 57, 64], 4, 71)
+        vo, eo = b.vertex_offsets, b.edge_offsets
+        return (b, 1, 1, [[vo[0] + 3], [vo[1] + 0, vo[1] + 30], [vo[2] + 8]],
+                [[eo[0] + 20], [eo[1] + 10, eo[1] + 40], [eo[2] + 1]], [[vo[0] + 30], [], [vo[2] + 50, vo[2] + 20]])
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["closed", "open", "batch"])
+def test_tangent_and_surface_gradient_matches_dense_kkt(torch, orc, name):
+    from paper_2006_07859_gb300 import tpe
+    c, indep, precond, pins, tans, surf = _rows_case(name)
+    ctx = make_ctx(c, precision=0, precond=precond, independent=indep, constraint_set=POINTS, cg_rtol=1e-11,
+                   cg_maxit=20000)
+    allp = np.concatenate([np.asarray(p, dtype=np.int64) for p in pins])
+    allt = np.concatenate([np.asarray(t, dtype=np.int64) for t in tans])
+    alls = np.concatenate([np.asarray(v, dtype=np.int64) for v in surf])
+    T = orc.edge_quantities(c.gamma, c.edges)[1]
+    quad = _sphere(c.gamma[alls].mean(0) + np.array([0.1, -0.2, 0.05]), 0.9)
+    tpe.tp_set_tangents(ctx, allt, T[allt])
+    tpe.tp_set_surface(ctx, alls, *quad)
+    tpe.tp_set_pins(ctx, allp, c.gamma[allp])
+    g = dev(c.gamma)
+    dE = tpe.tp_differential(ctx, g)
+    gt, info = tpe.sobolev_gradient(ctx, g, dE)
+    assert info["converged"]
+    gt = host(gt)
+    assert np.abs(gt[allp]).max() <= 1e-12 * np.abs(gt).max()
+    if indep:
+        parts = []
+        for k in range(c.n_curves):
+            gk, ek = c.curve(k)
+            v0, e0 = c.vertex_offsets[k], c.edge_offsets[k]
+            grk = orc.constraint_groups(gk, ek, pins=np.asarray(pins[k]) - v0, barycenter=False,
+                                        tangents=np.asarray(tans[k], dtype=np.int64) - e0,
+                                        surf=np.asarray(surf[k], dtype=np.int64) - v0, quad=quad)
+            parts.append(orc.sobolev_gradient(gk, ek, grk, orc.differential(gk, ek), orc.Params(), dense=True)[0])
+        ref = np.concatenate(parts)
+    else:
+        gr = orc.constraint_groups(c.gamma, c.edges, pins=allp, barycenter=False, tangents=allt, surf=alls, quad=quad)
+        ref = orc.sobolev_gradient(c.gamma, c.edges, gr, orc.differential(c.gamma, c.edges), orc.Params(),
+                                   dense=True)[0]
+    assert rel(gt, ref) <= 1e-7
+
+
+def test_tangent_and_surface_descent_steps_match_oracle(torch, orc):
+    """An open curve pinned at both ends with its end edges' tangents held and its middle vertex on a
+    sphere through it: every trial is projected back onto all of them."""
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.fourier_knot(40, 3, 8), closed=False)
+    pins, tans, surf = np.array([0, 39]), np.array([0, 38]), np.array([20])
+    X = orc.edge_quantities(c.gamma, c.edges)[1][tans]
+    quad = _sphere(np.zeros(3), float(np.linalg.norm(c.gamma[20])))
+    ctx = make_ctx(c, precision=0, precond=1, constraint_set=POINTS, cg_rtol=1e-11, proj_cg_rtol=1e-11,
+                   cg_maxit=20000)
+    tpe.tp_set_pins(ctx, pins, c.gamma[pins])
+    tpe.tp_set_tangents(ctx, tans, X)
+    tpe.tp_set_surface(ctx, surf, *quad)
+    g = dev(c.gamma)
+    gr = orc.constraint_groups(c.gamma, c.edges, pins=pins, barycenter=False, tangents=tans, X=X, surf=surf,
+                               quad=quad)
+    prm = orc.Params(cg_tol=1e-11, proj_cg_tol=1e-11)
+    go = c.gamma.copy()
+    for _ in range(2):
+        info = tpe.descent_step(ctx, g)
+        go, io = orc.descent_step(go, c.edges, gr, prm)
+        assert info["accepted"] == 1 and io.accepted
+        assert info["tau"] == io.tau
+        assert abs(info["E_after"] - io.E_after) <= 1e-9 * io.E_after
+        assert rel(host(g), go) <= 1e-7
+    gh = host(g)
+    Tn = orc.edge_quantities(gh, c.edges)[1]
+    tol = 1e-10 * max(1.0, gr[0].L0)   # the projection's stopping rule, max|Phi| <= proj_tol max(1, L0)
+    assert np.abs(Tn[tans] - X).max() <= tol
+    assert abs(orc.quadric(gh[surf], *quad)[0]).max() <= tol
+    phi = host(tpe.tp_constraints(ctx, g))
+    assert np.abs(phi).max() <= 1e-10 * max(1.0, gr[0].L0)
+
+
+def test_tangent_and_surface_arguments_are_checked(torch):
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.fourier_knot(60, 3, 9), closed=False)
+    ctx = make_ctx(c, precision=0, precond=1, constraint_set=POINTS, cg_rtol=1e-11, cg_maxit=20000)
+    tpe.tp_set_pins(ctx, [0, 59], c.gamma[[0, 59]])
+    bad = [lambda: tpe.tp_set_tangents(ctx, [60], [[1.0, 0, 0]]),            # edge out of range (59 edges)
+           lambda: tpe.tp_set_tangents(ctx, [3, 3], [[1.0, 0, 0]] * 2),      # repeated edge
+           lambda: tpe.tp_set_tangents(ctx, [3], [[0.0, 0, 0]]),             # zero target
+           lambda: tpe.tp_set_surface(ctx, [0], np.eye(3)),                  # a pinned vertex on the surface
+           lambda: tpe.tp_set_surface(ctx, list(range(1, 24)), np.eye(3)),   # 25 constrained vertices
+           lambda: tpe.tp_set_surface(ctx, [5], np.eye(3), [np.inf, 0, 0])]  # non-finite quadric
+    for call in bad:
+        with pytest.raises(tpe.TpError):
+            call()
+    two = make_ctx(S.single(S.fourier_knot(12, 2, 3), closed=False), precision=0, precond=1, constraint_set=POINTS)
+    tpe.tp_set_pins(two, [0, 1], np.zeros((2, 3)))
+    with pytest.raises(tpe.TpError):   # both ends of edge 0 pinned
+        tpe.tp_set_tangents(two, [0], [[1.0, 0, 0]])
+    # a rejected call leaves the lists as they were: the gradient matches the one before it
+    g = dev(c.gamma)
+    dE = tpe.tp_differential(ctx, g)
+    tpe.tp_set_tangents(ctx, [10], [c.gamma[11] - c.gamma[10]])
+    g1 = host(tpe.sobolev_gradient(ctx, g, dE)[0])
+    with pytest.raises(tpe.TpError):   # 25 constrained vertices: rejected after the lists were laid out
+        tpe.tp_set_surface(ctx, list(range(1, 24)), np.eye(3))
+    g2 = host(tpe.sobolev_gradient(ctx, g, dE)[0])
+    assert rel(g2, g1) <= 1e-8
