@@ -90,7 +90,10 @@ def test_autotune_keeps_parity(torch, orc):
     ctx = make_ctx(c, precision=tpe.TP_MIXED, precond=1)
     g = dev(c.gamma)
     res = tpe.tp_autotune(ctx, g)
-    assert set(res["tpt"].values()) <= {1, 2, 4}
+    # gather passes: targets per thread; symmetric passes: 0 (off) or the variant the timing picked
+    valid = {"energy": {1, 2, 4}, "diff": {1, 2, 4}, "apply": {1, 2, 4}, "apply_symmetric": {0, 1, 2},
+             "energy_symmetric": {0, 1, 2}, "diff_symmetric": {0, 1, 2, 3, 4}}
+    assert all(res["tpt"][k] in v for k, v in valid.items()), res["tpt"]
     assert all(len(v) >= 2 for v in res["ms"].values())
     rows = torch.empty(c.n_edges, dtype=torch.float64, device="cuda")
     tpe.tp_energy(ctx, g, rows=rows)
