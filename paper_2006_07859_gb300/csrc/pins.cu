@@ -466,7 +466,6 @@ static cudaError_t rebuild(Ctx &c, std::string &why)
     const int m = rmax + 4;
     const size_t smem = sizeof(double) * ((size_t)m * (m + 1) + m + (size_t)rmax * (kMaxTerms + 1)) +
                         sizeof(int) * (size_t)rmax * (2 * kMaxTerms + 1);
-    TPE_CHECK(cudaFuncSetAttribute(k_pin_system, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     auto up = [](void *d, const void *h, size_t bytes) {
         return bytes ? cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
     };
@@ -621,6 +620,8 @@ static cudaError_t pin_system(Ctx &c, int mode, int which, const double *y0, con
                               const double *gamma, const double *phi, cudaStream_t s)
 {
     PinState &p = *c.pins;
+    // the limit belongs to the kernel, not to this context: set it for this context's size every time
+    TPE_CHECK(cudaFuncSetAttribute(k_pin_system, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     k_pin_system<<<c.nProb, kSysThreads, p.smem, s>>>(mode, p.d_foff, p.d_fv, p.d_rows, p.d_roff, p.d_pt, p.d_te,
                                                       p.d_tB, p.d_quad, c.d_Tw[which], c.d_ellw[which], p.d_W,
                                                       3 * (size_t)c.nV, y0, y1, p.d_red, gamma, phi, p.d_coef,
