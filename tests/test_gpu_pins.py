@@ -268,3 +268,21 @@ def test_tangent_and_surface_arguments_are_checked(torch):
         tpe.tp_set_surface(ctx, list(range(1, 24)), np.eye(3))
     g2 = host(tpe.sobolev_gradient(ctx, g, dE)[0])
     assert rel(g2, g1) <= 1e-8
+
+
+def test_contexts_with_different_row_counts_interleave(torch, orc):
+    """24 pins (72 rows: the small system takes more than 48 KB of shared memory) in one context, one pin
+    in another set up after it: the first context's gradient still matches the dense KKT solve."""
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.trefoil(64, 0.01, 3))
+    big = make_ctx(c, precision=0, precond=2, constraint_set=POINTS, cg_rtol=1e-11, cg_maxit=20000)
+    pins = np.arange(0, 64, 64 // 24)[:24]
+    tpe.tp_set_pins(big, pins, c.gamma[pins])
+    small = make_ctx(c, precision=0, precond=2, constraint_set=POINTS, cg_rtol=1e-11, cg_maxit=20000)
+    tpe.tp_set_pins(small, [5], c.gamma[[5]])
+    g = dev(c.gamma)
+    tpe.sobolev_gradient(small, g, tpe.tp_differential(small, g))
+    gt = host(tpe.sobolev_gradient(big, g, tpe.tp_differential(big, g))[0])
+    gr = orc.constraint_groups(c.gamma, c.edges, pins=pins, barycenter=False)
+    ref = orc.sobolev_gradient(c.gamma, c.edges, gr, orc.differential(c.gamma, c.edges), orc.Params(), dense=True)[0]
+    assert rel(gt, ref) <= 1e-7
