@@ -80,15 +80,24 @@ def test_descent_steps_with_penalties_match_oracle(torch, orc):
         assert rel(host(g), go) <= 1e-7
 
 
-@pytest.mark.parametrize("cset", [0, 1])
+@pytest.mark.parametrize("cset", [0, 1, 2])
 def test_gradient_with_a_swirling_field_matches_dense_kkt(torch, orc, cset):
     """A non-constant field makes the differential translation-dependent (N^T dE != 0), so the
-    barycenter multiplier of Eq. 22 is no longer zero; the GPU route must still give the KKT
-    solution, for both constraint sets."""
+    barycenter multiplier of Eq. 22 is no longer zero (sets 0 and 1), and with pins, tangents and a
+    surface (set 2) the translation rows of the Schur system carry N^T dE; the GPU route must still give
+    the KKT solution."""
     from paper_2006_07859_gb300 import tpe
     c = S.single(S.trefoil(60, 0.01, 6))
     ctx = make_ctx(c, precision=0, precond=1, cg_rtol=1e-11, cg_maxit=20000, constraint_set=cset)
     tpe.tp_set_penalties(ctx, field_M=M, field_b=B, **W)
+    rows = {}
+    if cset == 2:
+        pins, tans, surf = np.array([4, 33]), np.array([10]), np.array([50])
+        quad = (np.eye(3), np.zeros(3), -float(c.gamma[50] @ c.gamma[50]))
+        tpe.tp_set_pins(ctx, pins, c.gamma[pins])
+        tpe.tp_set_tangents(ctx, tans, orc.edge_quantities(c.gamma, c.edges)[1][tans])
+        tpe.tp_set_surface(ctx, surf, *quad)
+        rows = dict(pins=pins, barycenter=False, tangents=tans, surf=surf, quad=quad)
     g = dev(c.gamma)
     dE = tpe.tp_differential(ctx, g)
     _, dP = tpe.tp_penalty(ctx, g)
@@ -98,6 +107,6 @@ def test_gradient_with_a_swirling_field_matches_dense_kkt(torch, orc, cset):
     pen = opens(orc)
     dEo = orc.differential(c.gamma, c.edges) + orc.penalty_gradient(c.gamma, c.edges, pen)
     assert np.abs(dEo.sum(0)).max() > 1e-3 * np.abs(dEo).max()   # really not translation invariant
-    gr = orc.constraint_groups(c.gamma, c.edges, edge_lengths=bool(cset))
+    gr = orc.constraint_groups(c.gamma, c.edges, edge_lengths=cset == 1, **rows)
     gk, _ = orc.sobolev_gradient(c.gamma, c.edges, gr, dEo, orc.Params(), dense=True)
     assert rel(host(gt), gk) <= 1e-7
