@@ -921,3 +921,26 @@ def twolevel_apply(A, n, sigma, m, r):
     Z = coarse_hats(n, m)
     Ac = Z.T @ A @ Z
     return z + Z @ np.linalg.solve(Ac, Z.T @ r)
+
+
+def balanced_apply(A, Z, spectral, r):
+    """Balancing two-level preconditioner (not from the paper; this library's design): with the
+    Galerkin coarse operator E = Z^T A Z and Q = Z E^-1 Z^T,
+        z = Q r + (I - Q A) S (I - A Q) r,
+    S the one-level term (a callable on [n, 3]).  It is symmetric when S is, reproduces A^-1 exactly
+    on range(A Z), and equals A^-1 when S does (on the complement of the null space).
+    A: [n, n]; Z: [n, k]; r: [n, 3]."""
+    E = Z.T @ A @ Z
+    Q = lambda v: Z @ np.linalg.solve(E, Z.T @ v)
+    y = spectral(r - A @ Q(r))
+    return Q(r) + y - Q(A @ y)
+
+
+def twolevel_balanced_apply(A, n, sigma, m, r):
+    """The balancing form of the two-level preconditioner of one closed curve: the Rayleigh-quotient
+    corrected spectral term of twolevel_apply as S, the m - 1 first of m periodic hats as Z.
+    r: [n, 3]; returns [n, 3] (before the mean-free projection)."""
+    ds = np.sqrt(np.diag(A))
+    lam = spectral_rq_symbol(A, n, sigma)
+    spec = lambda v: np.real(np.fft.ifft(np.fft.fft(v / ds[:, None], axis=0) / lam[:, None], axis=0)) / ds[:, None]
+    return balanced_apply(A, coarse_hats(n, m), spec, r)
