@@ -701,9 +701,11 @@ def sobolev_gradient(gamma, edges, groups, dE, prm: Params, dense=False, precond
     return res.x, res
 
 
-def constraint_projection(gamma_t, edges, groups, apply_abar, prm: Params, precond=None):
-    """Sec. 5.3.2 via App. B.3.4: repeat b = -Phi(g~); z = C^+ b; solve P A P y = P A z; x = z - y;
-    g~ += x; until max|Phi| <= tol.  Returns (curve, iterations, success)."""
+def constraint_projection(gamma_t, edges, groups, apply_abar, prm: Params, precond=None, A_dense=None):
+    """Sec. 5.3.2: repeat x = argmin x^T A-bar x / 2 subject to C x = -Phi(g~); g~ += x; until
+    max|Phi| <= tol.  With A_dense (the Gram matrix of the pre-step curve) x is the dense solve of the
+    saddle-point system of Eq. 23; otherwise App. B.3.4's route: z = C^+ b with b = -Phi, the
+    projected solve P A P y = P A z by CG, x = z - y.  Returns (curve, iterations, success)."""
     g = gamma_t.copy()
     scale = max(1.0, max(gr.L0 for gr in groups))
     for it in range(prm.proj_maxit + 1):
@@ -713,6 +715,10 @@ def constraint_projection(gamma_t, edges, groups, apply_abar, prm: Params, preco
         if it == prm.proj_maxit:
             break
         C = jacobian(g, edges, groups)
+        if A_dense is not None:
+            x, _ = kkt_solve(A_dense, C, np.zeros_like(g), -ph)
+            g = g + x
+            continue
         P = Projector(C)
         z = P.pinv(-ph).reshape(g.shape)
         res = projected_cg(apply_abar, P, apply_abar(z), prm.proj_cg_tol, prm.cg_maxit, precond)
@@ -750,12 +756,16 @@ def descent_step(gamma, edges, groups, prm: Params, dense=False, precond_factory
     d = g / gn
     slope = float(np.vdot(dE, d))
     apply_abar = make_apply(gamma, edges, prm.sigma)  # A-bar of the pre-step curve
+    A_dense = None
+    if dense:
+        B, B0 = gram_dense(gamma, edges, prm.sigma)
+        A_dense = B + B0
     tau = 1.0
     if prm.isotopy_safe:
         tau = 2.0 / 3.0 * float(first_collision_time(gamma, edges, d, prm.ccd_horizon)[0])
     for h in range(prm.max_halvings + 1):
         cand = gamma - tau * d
-        cand, pit, ok = constraint_projection(cand, edges, groups, apply_abar, prm, pc)
+        cand, pit, ok = constraint_projection(cand, edges, groups, apply_abar, prm, pc, A_dense)
         if ok:
             E1 = total(cand)
             if E1 <= E0 - prm.armijo_c * tau * slope:

@@ -101,7 +101,7 @@ extern "C" TPE_API tp_status tp_energy_static(const double *gamma, const int32_t
                                               int n_edges, double alpha, double beta, double *E,
                                               tp_stream stream)
 {
-    if (!gamma || !edges || !E || n_vertices < 1 || n_edges < 0) return TP_ERR_INVALID_ARG;
+    if (!gamma || !E || n_vertices < 1 || n_edges < 0 || (!edges && n_edges > 0)) return TP_ERR_INVALID_ARG;
     if (n_edges > kStaticMaxEdges) return TP_ERR_INVALID_ARG;  // beyond the fixed scratch
     if (!(alpha > 1.0) || !(beta >= alpha + 2.0 - 1e-12 && beta < 2.0 * alpha + 1.0)) return TP_ERR_INVALID_ARG;
     StaticPtrs *p = nullptr;

@@ -289,3 +289,21 @@ def test_edge_length_descent_step_keeps_every_edge_length(orc):
     ell1 = orc.edge_quantities(g1, e)[0]
     assert np.abs(ell1 - ell0).max() <= prm.proj_tol * max(1.0, gr[0].L0)
     assert np.abs(orc.phi(g1, e, gr)).max() <= prm.proj_tol * max(1.0, gr[0].L0)
+
+
+def test_dense_projection_matches_projected_route(orc):
+    """Eq. 23 solved as the dense saddle-point system agrees with App. B.3.4's route (z = C^+ b, the
+    projected solve, x = z - y) on a moved trefoil: the two formulations of the same projection."""
+    g = S.trefoil(96, 0.01, 4)
+    e = S.closed_edges(96)
+    gr = orc.constraint_groups(g, e)
+    prm = orc.Params(proj_cg_tol=1e-12, cg_maxit=200000)
+    sig = prm.sigma
+    B, B0 = orc.gram_dense(g, e, sig)
+    moved = g - 0.05 * orc.differential(g, e) / np.linalg.norm(orc.differential(g, e))
+    ap = orc.make_apply(g, e, sig)
+    a, ia, oka = orc.constraint_projection(moved, e, gr, ap, prm)
+    b, ib, okb = orc.constraint_projection(moved, e, gr, ap, prm, A_dense=B + B0)
+    assert oka and okb and ia == ib
+    assert np.abs(a - b).max() <= 1e-9 * np.abs(moved - g).max()
+    assert np.abs(orc.phi(b, e, gr)).max() <= 1e-10 * max(1.0, gr[0].L0)
