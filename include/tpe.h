@@ -77,8 +77,17 @@ typedef enum {
                                    operator at sampled frequencies, rebuilt at every set-up (not in the paper) */
     TP_PRECOND_TWOLEVEL = 4,    /* TP_PRECOND_SPECTRAL_RQ plus an additive coarse-space correction
                                    Z (Z^T A Z)^-1 Z^T with coarse_dim periodic hat functions per curve */
-    TP_PRECOND_LEARNED = 5      /* TP_PRECOND_TWOLEVEL plus a learned SPD local term G_theta (tp_gnn_*);
+    TP_PRECOND_LEARNED = 5,     /* TP_PRECOND_TWOLEVEL plus a learned SPD local term G_theta (tp_gnn_*);
                                    only for contexts created with it (not in the paper) */
+    TP_PRECOND_TWOLEVEL_BALANCED = 6, /* the same spectral term S and coarse space Z in the balancing
+                                   (multiplicative, symmetric) form Q r + (I - Q A) S (I - A Q) r,
+                                   Q = Z (Z^T A Z)^-1 Z^T: exact on range(A Z).  Keeps the set-up's
+                                   columns A Z (n (coarse_dim - 1) doubles per curve); every problem
+                                   must be one closed curve (independent curves, or a one-curve graph),
+                                   else TP_ERR_UNSUPPORTED (not in the paper) */
+    TP_PRECOND_LEARNED_BALANCED = 7  /* the balancing form with the learned smoother W S W + G (tp_gnn_*) in
+                                   place of S: Q r + (I - Q A)(W S W + G)(I - A Q) r; contexts created with
+                                   it, every problem one closed curve (not in the paper) */
 } tp_precond;
 
 /* Constraint sets of Sec. 8.1 (Phi of the descent step; targets fixed by tp_set_constraints_from or at
@@ -134,7 +143,7 @@ typedef struct {
     int proj_maxit;
     int independent;      /* 1: every curve is its own problem (no cross-curve pairs, constraints per curve);
                              0: the whole graph is one problem (one barycenter + one total length) */
-    int coarse_dim;       /* TP_PRECOND_TWOLEVEL: hat functions per closed curve (default 128; at most 256
+    int coarse_dim;       /* TP_PRECOND_TWOLEVEL: hat functions per closed curve (default 128; at most 2048
                              and n / 4) */
     double far_cutoff;    /* TP_MIXED: source tiles farther than far_cutoff * (extent of the curve) from a
                              warp's targets use single-float positions (faster, less accurate); >= 10
@@ -211,6 +220,14 @@ TPE_API tp_status tp_differential(tp_ctx *ctx, const double *gamma, double *dE, 
 
 /* Au = A-bar u with A = B + B0 of the curve gamma (Secs. 5.2.2-5.2.3, Eq. 19): u, Au device [nV][3]. */
 TPE_API tp_status sobolev_apply(tp_ctx *ctx, const double *gamma, const double *u, double *Au, tp_stream stream);
+
+/* The same product A-bar u in double-float arithmetic (every pair term as an unevaluated sum of two
+ * floats, ~48 bits, from the FP64 positions, tangents, lengths and u): the accurate operator with which
+ * the solves of TP_FP32 and TP_MIXED contexts judge their true residuals (FP64 contexts run their
+ * FP64 pass).  About an order of magnitude slower than sobolev_apply.  Builds its own work list at the
+ * first call (the only allocation, and it may grow the context's partial-sum buffer). */
+TPE_API tp_status sobolev_apply_accurate(tp_ctx *ctx, const double *gamma, const double *u, double *Au,
+                                         tp_stream stream);
 
 /* diag(A) of the curve gamma into diag [nV] (device). */
 TPE_API tp_status tp_gram_diagonal(tp_ctx *ctx, const double *gamma, double *diag, tp_stream stream);
@@ -329,7 +346,8 @@ TPE_API tp_status tp_profile_read(tp_ctx *ctx, int op, double *total_ms, int64_t
  * precision pair pass whose scratch (edge records, work items, partial sums; about 20 MB) lives in
  * fixed-size file-scope __device__ arrays that every GPU which loads the library keeps until exit.
  *   gamma  DEVICE double [n_vertices][3];  edges DEVICE int32 [n_edges][2] with indices in
- *          [0, n_vertices) (not checked: they are device data);  E DEVICE double [1].
+ *          [0, n_vertices) (not checked: they are device data; may be NULL when n_edges = 0, which
+ *          gives E = 0);  E DEVICE double [1].
  *   n_edges <= 65536, else TP_ERR_INVALID_ARG (the scratch has a fixed size).
  *   All pairs of disjoint edges of the whole graph form one problem (as independent = 0).
  * The first call on a device looks up the arrays' device addresses (cudaGetSymbolAddress); make
@@ -413,20 +431,26 @@ TPE_API tp_status tp_cg_harvest(tp_ctx *ctx, const double *gamma, const double *
  * applied to r_k and mean-projected, and AB[k] = A-bar B[k].  With ILAM (DEVICE double [nV], may be
  * NULL) the circulant is left to training (its scaling is learned): B[k] is the coarse term alone and
  * ILAM receives this curve's inverse circulant symbols; without it, B[k] is the whole two-level
- * preconditioner.  R, E, B, AB DEVICE double [n][nV][3]; B may be the same buffer as E (ER is taken
- * first).  Costs two A-bar applies per pair. */
+ * preconditioner.  When the context's preconditioner is a balancing form (TP_PRECOND_TWOLEVEL_BALANCED
+ * or TP_PRECOND_LEARNED_BALANCED), ILAM and R2 (DEVICE double [n][nV][3]) are required: B[k] = Q r_k and
+ * R2[k] = (I - A Q) r_k, the vector the learned smoother acts on (R2 is ignored otherwise and may be
+ * NULL).  R, E, B, AB DEVICE double [n][nV][3]; B may be the same buffer as E (ER is taken first).
+ * Costs two A-bar applies per pair. */
 TPE_API tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, double *R, double *E,
-                                       double *B, double *AB, double *ER, double *ILAM, tp_stream stream);
+                                       double *B, double *AB, double *ER, double *ILAM, double *R2,
+                                       tp_stream stream);
 
 /* One training step on n prepared pairs of the bound curve gamma, with the inverse symbols ILAM that
  * tp_gnn_prepare_pairs returned for it (NULL: the prepared B already holds the whole circulant):
- * z = B + W S W r + G r per pair, the loss at the current parameters, averaged over pairs and problems,
- * into *loss (host), the parameter gradient into grad (DEVICE float [P], may be NULL), then one Adam
- * step when lr > 0 (lr = 0: gradient only).  Costs one A-bar apply and two circulant applies per pair.
- * Synchronises the stream. */
+ * z = B + W S W r + G r per pair (R2 NULL), or in the balancing form z = B + (I - Q A)(W S W r2 + G r2)
+ * with r2 = R2[k] (the context's preconditioner must then be a balancing form, whose coarse space is the
+ * one the pairs were prepared with); the loss at the current parameters, averaged over pairs and
+ * problems, into *loss (host), the parameter gradient into grad (DEVICE float [P], may be NULL), then one
+ * Adam step when lr > 0 (lr = 0: gradient only).  Costs one A-bar apply and two circulant applies per
+ * pair.  Synchronises the stream. */
 TPE_API tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, const double *R, const double *B,
-                                    const double *AB, const double *ER, const double *ILAM, float lr,
-                                    double *loss, float *grad, tp_stream stream);
+                                    const double *AB, const double *ER, const double *ILAM, const double *R2,
+                                    float lr, double *loss, float *grad, tp_stream stream);
 
 /* Autotuner of the pair passes (not in the paper).  For TP_MIXED contexts with the specialised
  * powers ((alpha, beta) = (2, 4.5)) it times, on the curve gamma, every candidate number of target

@@ -194,3 +194,29 @@ def loss_and_grad(theta, f, diag, A, r, e, base_z, lam=None):
         dc_v = (gz * zs).sum(1) + (r * z2).sum(1)
         dout[:, 2] = 0.5 * (dc_v + np.roll(dc_v, -1))   # edge I feeds vertices I and I+1
     return L, backward(theta, cache, dout)
+
+
+def loss_and_grad_balanced(theta, f, diag, A, Z, r, e, lam):
+    """The same loss and gradient for the learned smoother inside the balancing two-level form:
+        z = Q r + (I - Q A) y,   y = G r2 + W S W r2,   r2 = (I - A Q) r,   Q = Z (Z^T A Z)^-1 Z^T.
+    The parameter-dependent part enters through y alone: dL/dy = (I - A Q) dL/dz (Q, A symmetric), and
+    y depends on the outputs exactly as z does in the additive form, with r2 in place of r."""
+    out, cache = forward(theta, f)
+    E = Z.T @ A @ Z
+    Q = lambda v: Z @ np.linalg.solve(E, Z.T @ v)
+    r2 = r - A @ Q(r)
+    zs = scaled_spectral(diag, vertex_log_scale(out), lam, r2)
+    y = g_apply(out, diag, r2) + zs
+    z = Q(r) + y - Q(A @ y)
+    Az = A @ z
+    er = float((e * r).sum())
+    s = float((z * r).sum())
+    q = float((z * Az).sum())
+    L = 1.0 - s * s / (q * er)
+    gz = -2.0 * s / (q * er) * (r - (s / q) * Az)
+    gy = gz - A @ Q(gz)
+    dout = g_out_grad(out, diag, r2, gy)
+    z2 = scaled_spectral(diag, vertex_log_scale(out), lam, gy)
+    dc_v = (gy * zs).sum(1) + (r2 * z2).sum(1)
+    dout[:, 2] = 0.5 * (dc_v + np.roll(dc_v, -1))
+    return L, backward(theta, cache, dout)

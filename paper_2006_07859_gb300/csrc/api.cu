@@ -50,7 +50,7 @@ bool params_ok(const tp_params *p, std::string &why)
         why = "bad precision";
         return false;
     }
-    if (p->precond < TP_PRECOND_NONE || p->precond > TP_PRECOND_LEARNED) {
+    if (p->precond < TP_PRECOND_NONE || p->precond > TP_PRECOND_LEARNED_BALANCED) {
         why = "bad preconditioner";
         return false;
     }
@@ -235,7 +235,7 @@ tp_status tp_profile(tp_ctx *ctx, int enable)
     if (!ctx) return TP_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     prof_harvest(c);
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 6; ++k) {
         c.prof_ms[k] = 0.0;
         c.prof_n[k] = 0;
     }
@@ -245,7 +245,7 @@ tp_status tp_profile(tp_ctx *ctx, int enable)
 
 tp_status tp_profile_read(tp_ctx *ctx, int op, double *total_ms, int64_t *launches)
 {
-    if (!ctx || op < 0 || op > 4) return TP_ERR_INVALID_ARG;
+    if (!ctx || op < 0 || op > 5) return TP_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     prof_harvest(c);
     if (total_ms) *total_ms = c.prof_ms[op];
@@ -275,7 +275,8 @@ void tp_destroy(tp_ctx *ctx)
                     c.d_recLo2, c.d_recD, c.d_recD2, c.d_ellw[0], c.d_ellw[1], c.d_Tw[0], c.d_Tw[1], c.d_xw[0],
                     c.d_xw[1], c.d_urecF, c.d_urecD, c.d_part, c.d_rows, c.d_x0L0, c.d_Cv, c.d_G, c.d_Ginv,
                     c.d_red, c.d_phi, c.d_y, c.d_r, c.d_z, c.d_p, c.d_q, c.d_diag, c.d_t1, c.d_t2, c.d_t3, c.d_t4,
-                    c.d_t5, c.d_t6, c.d_gam, c.d_best, c.d_yw0, c.d_yw1, c.d_E, c.d_scal, c.d_cg, c.d_err};
+                    c.d_t5, c.d_t6, c.d_gam, c.d_best, c.d_yw0, c.d_yw1, c.d_E, c.d_scal, c.d_cg, c.d_err,
+                    c.d_ell_lo[0], c.d_ell_lo[1], c.plan_df.d_items, c.plan_df.d_eslots, c.d_rf, c.d_ef};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     prof_harvest(c);
@@ -353,6 +354,8 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
     if ((prm.precond >= TP_PRECOND_SPECTRAL) && !c.spectral_ok)
         return fail(ctx, TP_ERR_UNSUPPORTED,
                     "the spectral preconditioner needs every curve to be a closed polygon (i, i+1 mod n) of >= 4 vertices");
+    if (precond_balanced(prm.precond) && c.nProb != n_curves)
+        return fail(ctx, TP_ERR_UNSUPPORTED, "the balancing two-level form needs every problem to be one curve");
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, dev));
@@ -416,10 +419,10 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
         CK(dalloc(&c.d_recF, nE));
         CK(dalloc(&c.d_recF2, nE));
         CK(dalloc(&c.d_urecF, nE));
-        if (mix) {
-            CK(dalloc(&c.d_recLo, nE));
-            CK(dalloc(&c.d_recLo2, nE));
-        }
+        CK(dalloc(&c.d_recLo, nE));
+        CK(dalloc(&c.d_recLo2, nE));
+        CK(dalloc(&c.d_ell_lo[0], nE));
+        CK(dalloc(&c.d_ell_lo[1], nE));
     }
     CK(dalloc(&c.d_counter, 8));
     CK(cudaMemset(c.d_counter, 0, sizeof(int) * 8));
@@ -438,7 +441,7 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
     CK(dalloc(&c.d_red, 16 * (size_t)c.nProb));
     CK(dalloc(&c.d_phi, 4 * (size_t)c.nProb));
     double **vecs[] = {&c.d_y, &c.d_r, &c.d_z, &c.d_p, &c.d_q, &c.d_t1, &c.d_t2, &c.d_t3, &c.d_t4, &c.d_t5, &c.d_t6,
-                       &c.d_gam, &c.d_best, &c.d_yw0, &c.d_yw1};
+                       &c.d_gam, &c.d_best, &c.d_yw0, &c.d_yw1, &c.d_rf, &c.d_ef};
     for (double **v : vecs) CK(dalloc(v, 3 * (size_t)nV));
     CK(cudaMemset(c.d_z, 0, sizeof(double) * 3 * nV));
     CK(dalloc(&c.d_diag, nV));
@@ -456,7 +459,7 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
         CK(e);
     }
     if (prm.precond >= TP_PRECOND_TWOLEVEL) CK(coarse_init(c));
-    if (prm.precond == TP_PRECOND_LEARNED) CK(gnn_alloc(c));
+    if (precond_learned(prm.precond)) CK(gnn_alloc(c));
     if (prm.constraint_set == TP_CONSTRAINTS_EDGE_LENGTHS) {
         if (!edges_chains_ok(c, why)) return fail(ctx, TP_ERR_INVALID_ARG, why);
         CK(edges_init(c));
@@ -475,8 +478,10 @@ tp_status tp_set_params(tp_ctx *ctx, const tp_params *p)
     if (p->precision != c.prm.precision) return fail(ctx, TP_ERR_INVALID_ARG, "precision is fixed at creation");
     if ((p->precond >= TP_PRECOND_SPECTRAL) && !c.spectral_ok)
         return fail(ctx, TP_ERR_UNSUPPORTED, "the spectral preconditioner needs closed polygons");
-    if (p->precond == TP_PRECOND_LEARNED && !c.gnn)
-        return fail(ctx, TP_ERR_UNSUPPORTED, "TP_PRECOND_LEARNED needs a context created with it");
+    if (precond_learned(p->precond) && !c.gnn)
+        return fail(ctx, TP_ERR_UNSUPPORTED, "the learned preconditioners need a context created with one of them");
+    if (precond_balanced(p->precond) && c.nProb != c.nCurves)
+        return fail(ctx, TP_ERR_UNSUPPORTED, "the balancing two-level form needs every problem to be one curve");
     if (p->constraint_set == TP_CONSTRAINTS_EDGE_LENGTHS && !c.edges) {
         if (!edges_chains_ok(c, why)) return fail(ctx, TP_ERR_INVALID_ARG, why);
         CK(edges_init(c));
@@ -544,6 +549,16 @@ tp_status sobolev_apply(tp_ctx *ctx, const double *gamma, const double *u, doubl
     if (st) return st;
     CK(pair_apply(ctx->c, gamma, 0, u, Au, s));
     return TP_OK;
+}
+
+tp_status sobolev_apply_accurate(tp_ctx *ctx, const double *gamma, const double *u, double *Au, tp_stream stream)
+{
+    if (!ctx || !gamma || !u || !Au) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    CK(pair_apply_acc(ctx->c, gamma, 0, u, Au, s));
+    return check_err_word(ctx, s);
 }
 
 tp_status tp_gram_diagonal(tp_ctx *ctx, const double *gamma, double *diag, tp_stream stream)
@@ -665,8 +680,8 @@ tp_status tp_collision_time(tp_ctx *ctx, const double *gamma, const double *d, d
 static tp_status precond_setup(tp_ctx *ctx, const double *gamma, cudaStream_t s)
 {
     Ctx &c = ctx->c;
-    if (c.prm.precond == TP_PRECOND_LEARNED && !gnn_ready(c))
-        return fail(ctx, TP_ERR_INVALID_ARG, "TP_PRECOND_LEARNED: no network parameters loaded (tp_gnn_set_params)");
+    if (precond_learned(c.prm.precond) && !gnn_ready(c))
+        return fail(ctx, TP_ERR_INVALID_ARG, "learned preconditioner: no network parameters loaded (tp_gnn_set_params)");
     if (c.prm.precond != TP_PRECOND_NONE) CK(pair_diag(c, gamma, 0, c.d_diag, s));
     // the fitted symbols and the coarse space are rebuilt every precond_refresh-th set-up (any SPD
     // preconditioner keeps PCG exact; the curve moves little between consecutive descent steps)
@@ -674,7 +689,7 @@ static tp_status precond_setup(tp_ctx *ctx, const double *gamma, cudaStream_t s)
     c.setups_since_full = full ? 0 : c.setups_since_full + 1;
     if (full && c.prm.precond >= TP_PRECOND_SPECTRAL_RQ) CK(spectral_rq_setup(c, gamma, 0, s));
     if (full && c.prm.precond >= TP_PRECOND_TWOLEVEL) CK(coarse_setup(c, gamma, 0, s));
-    if (c.prm.precond == TP_PRECOND_LEARNED) {
+    if (precond_learned(c.prm.precond)) {
         CK(gnn_bind(c, 0, c.d_diag, s));
         CK(gnn_forward(c, s));
     }
@@ -769,9 +784,28 @@ static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE_
         }
         return schur_shift(c, g, nullptr, 0.0, s);
     }
+    if (precond_balanced(c.prm.precond)) {
+        // One projected solve P A-bar P y = P dE with P = P_len P_N (the total-length row and the mean), then
+        // the translation that restores the barycenter rows: the KKT solution of Eq. 22 (App. B.3.3 with
+        // the translations handled apart).  It starts from the previous step's solution.  The balancing
+        // preconditioner resolves the smooth modes through its coarse space, where C_len lives; the
+        // one-level preconditioners amplify exactly those modes, and the projected operator then needs
+        // thousands of iterations, so they keep the two mean-free solves below.
+        cudaError_t e = cg_solve(c, gamma, 0, dE, g, c.prm.cg_rtol, c.prm.cg_maxit, iters, rr, conv, bd, s, 3,
+                                 flags.data(), (c.warm_ok && c.prm.warm_start) ? c.d_yw0 : nullptr);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(c.d_yw0, g, sizeof(double) * 3 * c.nV, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return e;
+        c.warm_ok = 1;
+        if (n_conv) {
+            *n_conv = 0;
+            for (int f : flags) *n_conv += f;
+        }
+        return schur_shift(c, g, nullptr, 0.0, s);
+    }
     int i0 = 0, i1 = 0, c0 = 0, c1 = 0, b0 = 0, b1 = 0;
     double r0 = 0, r1 = 0;
-    // both solves start from the previous step's solutions (the curve moves little between steps)
+    // y0 = A^+ dE, y1 = A^+ C_len^T (mean-free), both from the previous step's solutions
     cudaError_t e = cg_solve(c, gamma, 0, dE, c.d_t3, c.prm.cg_rtol, c.prm.cg_maxit, &i0, &r0, &c0, &b0, s, 1,
                              flags.data(), (c.warm_ok && c.prm.warm_start) ? c.d_yw0 : nullptr);
     if (e != cudaSuccess) return e;
@@ -784,11 +818,11 @@ static cudaError_t gradient_solve(Ctx &c, const double *gamma, const double *dE_
     if ((e = cudaMemcpyAsync(c.d_yw0, c.d_t3, vb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(c.d_yw1, c.d_t4, vb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
     c.warm_ok = 1;
+    c.warm1_ok = 1;
     if (n_conv) {
         *n_conv = 0;
         for (int f : flags) *n_conv += f;
     }
-    if (e != cudaSuccess) return e;
     e = schur_gradient(c, c.d_t3, c.d_t4, g, s);
     *iters = i0 + i1;
     *rr = std::max(r0, r1);
@@ -921,6 +955,13 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
         }
     int proj_cg_total = 0;
     int *mask_dev = reinterpret_cast<int *>(c.d_scal + 64 + 5 * nP);  // nP ints fit in 8 nP doubles
+    // the total-length route's projection solves start from the last projection solution of the previous
+    // step (A-bar^+ C_len^T at a nearby curve)
+    int have_z = 0;
+    if (!pin_constraints(c) && !edge_constraints(c) && c.warm1_ok) {
+        CK(cudaMemcpyAsync(z, c.d_yw1, vb, cudaMemcpyDeviceToDevice, s));
+        have_z = 1;
+    }
     CK(cudaMemcpyAsync(c.d_best, gamma, vb, cudaMemcpyDeviceToDevice, s));
     for (int h = 0; h <= c.prm.max_halvings; ++h) {
         int npend = 0;
@@ -977,10 +1018,11 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
                 CK(pins_projection(c, z, c.d_gam, c.d_phi, x, s));
             } else {
                 CK(clen_rhs(c, rhs, s));
-                // starts from z: A-bar^+ C_len^T of the pre-step curve (the gradient's second solve) or of
-                // the previous trial, both close to this trial's solution
+                // starts from z: A-bar^+ C_len^T of the previous trial or of the last step's projection, both
+                // close to this trial's solution
                 CK(cg_solve(c, gamma, 0, rhs, z, c.prm.proj_cg_rtol, c.prm.cg_maxit, &pit_cg, &prr, &pconv, &pbd,
-                            s, 1, nullptr, c.prm.warm_start ? z : nullptr));
+                            s, 1, nullptr, (c.prm.warm_start && have_z) ? z : nullptr));
+                have_z = 1;
                 CK(schur_projection(c, z, c.d_phi, -1.0, x, s));
             }
             proj_cg_total += pit_cg;
@@ -1019,6 +1061,10 @@ tp_status descent_step(tp_ctx *ctx, double *gamma, tp_step_info *info, tp_stream
         if (!accepted[q]) hE1[q] = hE0[q];
         nacc += accepted[q];
     }
+    if (have_z && !pin_constraints(c) && !edge_constraints(c)) {
+        CK(cudaMemcpyAsync(c.d_yw1, z, vb, cudaMemcpyDeviceToDevice, s));
+        c.warm1_ok = 1;
+    }
     CK(cudaMemcpyAsync(gamma, c.d_best, vb, cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
     if (info) {
@@ -1055,7 +1101,7 @@ int tp_gnn_num_params(void) { return gnn_num_params(); }
 static tp_status need_gnn(tp_ctx *ctx)
 {
     if (!ctx) return TP_ERR_INVALID_ARG;
-    if (!ctx->c.gnn) return fail(ctx, TP_ERR_UNSUPPORTED, "the context was not created with TP_PRECOND_LEARNED");
+    if (!ctx->c.gnn) return fail(ctx, TP_ERR_UNSUPPORTED, "the context was not created with a learned preconditioner");
     return TP_OK;
 }
 
@@ -1186,12 +1232,15 @@ tp_status tp_cg_harvest(tp_ctx *ctx, const double *gamma, const double *rhs, int
 }
 
 tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, double *R, double *E, double *B,
-                               double *AB, double *ER, double *ILAM, tp_stream stream)
+                               double *AB, double *ER, double *ILAM, double *R2, tp_stream stream)
 {
     if (!ctx || !gamma || n < 0 || (n > 0 && (!R || !E || !B || !AB || !ER)))
         return fail(ctx, TP_ERR_INVALID_ARG, "bad pair arguments");
     cudaStream_t s = (cudaStream_t)stream;
     Ctx &c = ctx->c;
+    const bool balanced = precond_balanced(c.prm.precond);
+    if (balanced && n > 0 && (!R2 || !ILAM || !c.spec))
+        return fail(ctx, TP_ERR_INVALID_ARG, "the balancing form needs R2 and ILAM");
     tp_status st = records(ctx, gamma, 0, s);
     if (st) return st;
     st = precond_setup(ctx, gamma, s);
@@ -1209,7 +1258,11 @@ tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, double *
         // operator, so only A-bar e is exactly consistent with e
         CK(pair_apply(c, gamma, 0, E + k * nv3, r, s));
         CK(gnn_problem_dot(c, E + k * nv3, r, ER + (size_t)k * c.nProb, s));  // before B may overwrite E
-        if (rescale) {
+        if (balanced) {
+            // z = Q r + (I - Q A) y with y the learned smoother of r2 = (I - A Q) r: B = Q r, R2 = r2
+            CK(coarse_balanced_part(c, 0, r, b, s));
+            CK(coarse_balanced_part(c, 1, r, R2 + k * nv3, s));
+        } else if (rescale) {
             CK(cudaMemsetAsync(b, 0, sizeof(double) * nv3, s));
             if (c.prm.precond >= TP_PRECOND_TWOLEVEL) CK(coarse_apply(c, r, b, s));
         } else {
@@ -1222,8 +1275,8 @@ tp_status tp_gnn_prepare_pairs(tp_ctx *ctx, const double *gamma, int n, double *
 }
 
 tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, const double *R, const double *B,
-                            const double *AB, const double *ER, const double *ILAM, float lr, double *loss,
-                            float *grad, tp_stream stream)
+                            const double *AB, const double *ER, const double *ILAM, const double *R2, float lr,
+                            double *loss, float *grad, tp_stream stream)
 {
     tp_status st = need_gnn(ctx);
     if (st) return st;
@@ -1235,7 +1288,9 @@ tp_status tp_gnn_train_step(tp_ctx *ctx, const double *gamma, int n, const doubl
     st = records(ctx, gamma, 0, s);
     if (st) return st;
     if (ILAM && !c.spec) return fail(ctx, TP_ERR_UNSUPPORTED, "no circulant preconditioner in this context");
-    CK(gnn_train_step(c, gamma, n, R, B, AB, ER, ILAM, lr, c.d_scal, s));
+    if (R2 && (!c.coarse || !precond_balanced(c.prm.precond)))
+        return fail(ctx, TP_ERR_INVALID_ARG, "R2 needs a context in a balancing two-level preconditioner");
+    CK(gnn_train_step(c, gamma, n, R, B, AB, ER, ILAM, R2, lr, c.d_scal, s));
     if (grad) CK(cudaMemcpyAsync(grad, gnn_last_grad(c), sizeof(float) * gnn_num_params(), cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(c.h_pinned, c.d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

@@ -12,6 +12,14 @@
 // component), Cholesky-factored per curve in FP64 and inverted explicitly (L^-T L^-1) at set-up.
 // Per CG iteration the term costs three small kernels: restriction Z^T r, the (m - 1) x (m - 1)
 // mat-vec with the inverse (all rows and components in parallel), prolongation Z y.
+//
+// Balancing form (TP_PRECOND_TWOLEVEL_BALANCED, when every problem is one closed curve): with
+// Q = Z E^-1 Z^T, E = Z^T A Z and S the spectral term,
+//   M^-1 r = Q r + (I - Q A) S (I - A Q) r,
+// the symmetric multiplicative combination: it is exact on range(A Z) and leaves S only the complement.
+// The probes of the set-up are the columns A Z themselves; they are kept (n (m - 1) doubles per curve)
+// so that A Q r = (A Z) E^-1 Z^T r and Q A y = Z E^-1 (A Z)^T y cost two dense passes over them and no
+// pair pass.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,7 +35,7 @@ namespace tpe {
         if (e_ != cudaSuccess) return e_; \
     } while (0)
 
-constexpr int kMaxCoarse = 256;
+constexpr int kMaxCoarse = 2048;
 constexpr int kSmemCoarse = 128;  // coarse spaces up to this size factor in shared memory, larger ones in global
 constexpr int kFactorSmem = (kSmemCoarse - 1) * (kSmemCoarse - 1) * (int)sizeof(double);  // 127^2 doubles
 
@@ -35,6 +43,7 @@ struct CoarseCurve {
     int v0, n, m;  // hats j = 0 .. m-2 are the basis
     int pad;
     long long aoff, woff;  // offsets of the factor [(m-1)^2] and of the coarse vectors [(m-1) x 3]
+    long long zoff;        // offset of the curve's A Z columns [(m-1)][n] (balancing form)
 };
 
 }  // namespace tpe
@@ -48,8 +57,12 @@ struct tpe::CoarseState {
     double *d_W = nullptr;   // set-up scratch: Cholesky work array of coarse spaces above 127 hats
     double *d_w = nullptr;  // coarse vectors: restriction Z^T r
     double *d_w2 = nullptr; // coarse vectors: (Z^T A Z)^-1 Z^T r
+    double *d_w3 = nullptr, *d_w4 = nullptr;  // balancing form: (A Z)^T y and its coarse solve
+    double *d_AZ = nullptr;  // balancing form: per curve the columns A z_j, [(m-1)][n] (column-major)
+    double *d_r2 = nullptr;  // balancing form: r - A Q r, [nV][3]
     int max_m = 0;
     int ready = 0;
+    int balanced = 0;        // the AZ columns are kept (every problem is one curve)
 };
 
 namespace tpe {
@@ -206,7 +219,7 @@ __global__ void __launch_bounds__(32 * kSolveRows) k_coarse_solve(const CoarseCu
     const int mm = C.m - 1;
     const int r0 = blockIdx.x * kSolveRows;
     if (r0 >= mm) return;  // uniform per block
-    __shared__ double sw[3 * kMaxCoarse];
+    extern __shared__ double sw[];  // [3 (max_m - 1)] the curve's coarse vector
     for (int t = threadIdx.x; t < 3 * mm; t += blockDim.x) sw[t] = w[C.woff + t];
     __syncthreads();
     const int r = r0 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
@@ -245,12 +258,102 @@ __global__ void k_coarse_prolong(int nV, const CoarseCurve *__restrict__ cc, con
     for (int q = 0; q < 3; ++q) z[3 * v + q] += acc[q];
 }
 
+// AZ[curve][3b + q][i] = (A z_{3b+q})(v0 + i): the probe of batch b carries hat 3b + q in component q
+__global__ void k_az_store(int nV, int b, const CoarseCurve *__restrict__ cc, const int *__restrict__ vcurve,
+                           const double *__restrict__ AY, double *__restrict__ AZ)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    const CoarseCurve C = cc[vcurve[v]];
+    const int i = v - C.v0;
+    for (int q = 0; q < 3; ++q) {
+        const int l = 3 * b + q;
+        if (l < C.m - 1) AZ[C.zoff + (long long)l * C.n + i] = AY[3 * v + q];
+    }
+}
+
+// out[v] = r[v] - sum_j AZ[j][v] w[j] (three components; each vertex reads its curve's column entries,
+// consecutive vertices read consecutive addresses of a column)
+__global__ void k_az_prolong_sub(int nV, const CoarseCurve *__restrict__ cc, const int *__restrict__ vcurve,
+                                 const double *__restrict__ AZ, const double *__restrict__ w,
+                                 const double *__restrict__ r, double *__restrict__ out)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nV) return;
+    const CoarseCurve C = cc[vcurve[v]];
+    const int i = v - C.v0, mm = C.m - 1;
+    const double *az = AZ + C.zoff + i;
+    const double *wc = w + C.woff;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int j = 0; j < mm; ++j) {
+        const double a = az[(long long)j * C.n];
+        s0 += a * wc[3 * j];
+        s1 += a * wc[3 * j + 1];
+        s2 += a * wc[3 * j + 2];
+    }
+    out[3 * v] = r[3 * v] - s0;
+    out[3 * v + 1] = r[3 * v + 1] - s1;
+    out[3 * v + 2] = r[3 * v + 2] - s2;
+}
+
+// w[j][q] = sum_i AZ[j][i] y[v0 + i][q]: one block per (curve, j), fixed-order tree sums
+__global__ void k_az_restrict(const CoarseCurve *__restrict__ cc, const double *__restrict__ AZ,
+                              const double *__restrict__ y, double *__restrict__ w)
+{
+    const CoarseCurve C = cc[blockIdx.x];
+    const int j = blockIdx.y;
+    if (j >= C.m - 1) return;
+    const double *az = AZ + C.zoff + (long long)j * C.n;
+    __shared__ double sh[3][256];
+    double s[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < C.n; i += blockDim.x) {
+        const double a = az[i];
+        const double *yy = y + 3 * (size_t)(C.v0 + i);
+        s[0] += a * yy[0];
+        s[1] += a * yy[1];
+        s[2] += a * yy[2];
+    }
+    for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] = s[q];
+    __syncthreads();
+    for (int wv = 128; wv > 0; wv >>= 1) {
+        if (threadIdx.x < wv)
+            for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + wv];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 3; ++q) w[C.woff + 3 * j + q] = sh[q][0];
+}
+
+__global__ void k_coarse_sub(long long n, const double *__restrict__ a, double *__restrict__ b)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i] - b[i];
+}
+
+// The balancing form's extra storage (the A Z columns and two coarse vectors), allocated when that
+// preconditioner is selected on a context whose problems are single curves.
+static cudaError_t coarse_balanced_alloc(Ctx &c)
+{
+    CoarseState &S = *c.coarse;
+    S.balanced = (c.prm.precond == TP_PRECOND_TWOLEVEL_BALANCED || c.prm.precond == TP_PRECOND_LEARNED_BALANCED) &&
+                 c.nCurves == c.nProb;
+    if (!S.balanced || S.d_AZ) return cudaSuccess;
+    const CoarseCurve &L = S.curves.back();
+    const long long woff = L.woff + 3LL * (L.m - 1), zoff = L.zoff + (long long)(L.m - 1) * L.n;
+    TPE_CHECK(cudaMalloc(&S.d_w3, sizeof(double) * std::max<long long>(1, woff)));
+    TPE_CHECK(cudaMalloc(&S.d_w4, sizeof(double) * std::max<long long>(1, woff)));
+    TPE_CHECK(cudaMalloc(&S.d_AZ, sizeof(double) * std::max<long long>(1, zoff)));
+    TPE_CHECK(cudaMalloc(&S.d_r2, sizeof(double) * 3 * (size_t)c.nV));
+    S.ready = 0;  // the next set-up fills the A Z columns
+    return cudaSuccess;
+}
+
 cudaError_t coarse_init(Ctx &c)
 {
-    if (c.coarse) return cudaSuccess;
+    if (c.coarse) return coarse_balanced_alloc(c);
     c.coarse = new CoarseState();
     CoarseState &S = *c.coarse;
-    long long aoff = 0, woff = 0;
+    long long aoff = 0, woff = 0, zoff = 0;
     std::vector<int> vc(c.nV);
     for (int k = 0; k < c.nCurves; ++k) {
         CoarseCurve C{};
@@ -259,8 +362,10 @@ cudaError_t coarse_init(Ctx &c)
         C.m = std::max(2, std::min(std::min(c.prm.coarse_dim, kMaxCoarse), C.n / 4));
         C.aoff = aoff;
         C.woff = woff;
+        C.zoff = zoff;
         aoff += (long long)(C.m - 1) * (C.m - 1);
         woff += 3LL * (C.m - 1);
+        zoff += (long long)(C.m - 1) * C.n;
         S.max_m = std::max(S.max_m, C.m);
         S.curves.push_back(C);
         for (int v = C.v0; v < C.v0 + C.n; ++v) vc[v] = k;
@@ -274,7 +379,11 @@ cudaError_t coarse_init(Ctx &c)
     TPE_CHECK(cudaMalloc(&S.d_W, sizeof(double) * std::max<long long>(1, aoff)));
     TPE_CHECK(cudaMalloc(&S.d_w, sizeof(double) * std::max<long long>(1, woff)));
     TPE_CHECK(cudaMalloc(&S.d_w2, sizeof(double) * std::max<long long>(1, woff)));
+    // balancing form: each problem must be one curve, so that E = Z^T A Z is the exact Galerkin matrix
+    TPE_CHECK(coarse_balanced_alloc(c));
     TPE_CHECK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, kFactorSmem));
+    TPE_CHECK(cudaFuncSetAttribute(k_coarse_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(double) * 3 * (kMaxCoarse - 1))));
     return cudaSuccess;
 }
 
@@ -288,6 +397,10 @@ void coarse_free(Ctx &c)
     cudaFree(c.coarse->d_W);
     cudaFree(c.coarse->d_w);
     cudaFree(c.coarse->d_w2);
+    cudaFree(c.coarse->d_w3);
+    cudaFree(c.coarse->d_w4);
+    cudaFree(c.coarse->d_AZ);
+    cudaFree(c.coarse->d_r2);
     delete c.coarse;
     c.coarse = nullptr;
 }
@@ -305,6 +418,10 @@ cudaError_t coarse_setup(Ctx &c, const double *gamma_geom, int which, cudaStream
         TPE_CHECK(pair_apply(c, gamma_geom, which, c.d_y, c.d_q, s));
         k_coarse_gram<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(b, S.d_curves, c.d_q, S.d_L);
         c.launches++;
+        if (S.balanced) {
+            k_az_store<<<nb, 256, 0, s>>>(c.nV, b, S.d_curves, S.d_vcurve, c.d_q, S.d_AZ);
+            c.launches++;
+        }
     }
     const int msm = std::min(S.max_m, kSmemCoarse) - 1;
     k_coarse_factor<<<c.nCurves, 256, (size_t)msm * msm * sizeof(double), s>>>(S.d_curves, S.d_L, S.d_Li, S.d_W);
@@ -319,10 +436,81 @@ cudaError_t coarse_apply(Ctx &c, const double *r, double *z, cudaStream_t s)
     if (!c.coarse || !c.coarse->ready) return cudaSuccess;
     CoarseState &S = *c.coarse;
     k_coarse_restrict<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(S.d_curves, r, S.d_w);
-    k_coarse_solve<<<dim3((S.max_m - 1 + kSolveRows - 1) / kSolveRows, c.nCurves), 32 * kSolveRows, 0, s>>>(
-        S.d_curves, S.d_L, S.d_w, S.d_w2);
+    k_coarse_solve<<<dim3((S.max_m - 1 + kSolveRows - 1) / kSolveRows, c.nCurves), 32 * kSolveRows,
+                     sizeof(double) * 3 * (S.max_m - 1), s>>>(S.d_curves, S.d_L, S.d_w, S.d_w2);
     k_coarse_prolong<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_w2, z);
     c.launches += 3;
+    return cudaGetLastError();
+}
+
+// z = Q r + (I - Q A) S (I - A Q) r (balancing form).  S = spectral_apply with the skip flags, or with
+// `learned` the learned smoother W S W + G of TP_PRECOND_LEARNED_BALANCED (the network's per-vertex
+// rescaling of the circulant and its local term).  r must not alias z.
+cudaError_t coarse_balanced_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip, bool learned)
+{
+    if (!c.coarse || !c.coarse->ready || !c.coarse->balanced) return cudaErrorNotReady;
+    CoarseState &S = *c.coarse;
+    const dim3 gsolve((S.max_m - 1 + kSolveRows - 1) / kSolveRows, c.nCurves);
+    const size_t smem = sizeof(double) * 3 * (S.max_m - 1);
+    const int nb = (c.nV + 255) / 256;
+    // c1 = E^-1 Z^T r,  r2 = r - (A Z) c1
+    k_coarse_restrict<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(S.d_curves, r, S.d_w);
+    k_coarse_solve<<<gsolve, 32 * kSolveRows, smem, s>>>(S.d_curves, S.d_L, S.d_w, S.d_w2);
+    k_az_prolong_sub<<<nb, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_AZ, S.d_w2, r, S.d_r2);
+    c.launches += 3;
+    // y = S r2 (into z)
+    if (learned) {
+        TPE_CHECK(spectral_apply_ex(c, S.d_r2, z, s, skip, c.d_diag, spectral_ilam(c, s), gnn_vlog(c)));
+        TPE_CHECK(gnn_gapply(c, S.d_r2, z, 1, s, skip));
+    } else {
+        TPE_CHECK(spectral_apply(c, S.d_r2, z, s, skip));
+    }
+    // c2 = E^-1 (A Z)^T y;  z = y + Z (c1 - c2)
+    k_az_restrict<<<dim3(c.nCurves, S.max_m), 256, 0, s>>>(S.d_curves, S.d_AZ, z, S.d_w3);
+    k_coarse_solve<<<gsolve, 32 * kSolveRows, smem, s>>>(S.d_curves, S.d_L, S.d_w3, S.d_w4);
+    const long long nw = (long long)S.curves.back().woff + 3LL * (S.curves.back().m - 1);
+    k_coarse_sub<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(nw, S.d_w2, S.d_w4);
+    k_coarse_prolong<<<nb, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_w4, z);
+    c.launches += 4;
+    return cudaGetLastError();
+}
+
+__global__ void k_coarse_neg(long long n, double *__restrict__ a)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = -a[i];
+}
+
+// The pieces of the balancing form that training needs, for the A Z columns and E of the last set-up:
+//   which 0: out = Q v = Z E^-1 Z^T v;   1: out = (I - A Q) v;   2: out = (I - Q A) v.
+// out may alias v for 1 and 2.
+cudaError_t coarse_balanced_part(Ctx &c, int which, const double *v, double *out, cudaStream_t s)
+{
+    if (!c.coarse || !c.coarse->ready || !c.coarse->balanced) return cudaErrorNotReady;
+    CoarseState &S = *c.coarse;
+    const dim3 gsolve((S.max_m - 1 + kSolveRows - 1) / kSolveRows, c.nCurves);
+    const size_t smem = sizeof(double) * 3 * (S.max_m - 1);
+    const int nb = (c.nV + 255) / 256;
+    const long long nw = (long long)S.curves.back().woff + 3LL * (S.curves.back().m - 1);
+    if (which == 2)
+        k_az_restrict<<<dim3(c.nCurves, S.max_m), 256, 0, s>>>(S.d_curves, S.d_AZ, v, S.d_w3);
+    else
+        k_coarse_restrict<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(S.d_curves, v, S.d_w3);
+    k_coarse_solve<<<gsolve, 32 * kSolveRows, smem, s>>>(S.d_curves, S.d_L, S.d_w3, S.d_w4);
+    c.launches += 2;
+    if (which == 0) {
+        TPE_CHECK(cudaMemsetAsync(out, 0, sizeof(double) * 3 * c.nV, s));
+        k_coarse_prolong<<<nb, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_w4, out);
+        c.launches++;
+    } else if (which == 1) {
+        k_az_prolong_sub<<<nb, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_AZ, S.d_w4, v, out);
+        c.launches++;
+    } else {
+        if (out != v) TPE_CHECK(cudaMemcpyAsync(out, v, sizeof(double) * 3 * c.nV, cudaMemcpyDeviceToDevice, s));
+        k_coarse_neg<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(nw, S.d_w4);
+        k_coarse_prolong<<<nb, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_w4, out);
+        c.launches += 2;
+    }
     return cudaGetLastError();
 }
 

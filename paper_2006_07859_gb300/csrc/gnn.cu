@@ -65,7 +65,7 @@ struct GnnState {
     float *wpart = nullptr;                                                 // [kWgBlocks][kWgMax]
     double *loss = nullptr;                                                 // [nProb]
     double *sq = nullptr;                                                   // [nProb][2]: z^T r, z^T A z
-    double *g = nullptr, *Ag = nullptr, *gz = nullptr;                      // [nV][3]
+    double *g = nullptr, *Ag = nullptr, *gz = nullptr, *gy = nullptr;       // [nV][3]
     int *eprev = nullptr, *enext = nullptr, *ecurve = nullptr;              // [nE]
     int loaded = 0, bound = 0, adam_t = 0;
 };
@@ -594,6 +594,7 @@ cudaError_t gnn_alloc(Ctx &c)
     TPE_CHECK(cudaMalloc(&G.g, sizeof(double) * 3 * nV));
     TPE_CHECK(cudaMalloc(&G.Ag, sizeof(double) * 3 * nV));
     TPE_CHECK(cudaMalloc(&G.gz, sizeof(double) * 3 * nV));
+    TPE_CHECK(cudaMalloc(&G.gy, sizeof(double) * 3 * nV));
     // neighbours along the closed curves: edge v0 + i = (v0 + i, v0 + (i + 1) mod n)
     std::vector<int> ep(nE), en(nE), ec(nE);
     for (int k = 0; k < c.nCurves; ++k) {
@@ -619,7 +620,7 @@ void gnn_free(Ctx &c)
     GnnState &G = *c.gnn;
     void *p[] = {G.master, G.m,     G.v,     G.grad, G.wb, G.feat, G.z1, G.z2,    G.z3,    G.bA,
                  G.bB,     G.bC,    G.out,   G.dout, G.ew, G.diag, G.cstat, G.wpart, G.loss, G.sq, G.vlog, G.zs, G.zg, G.w, G.dcv, G.g,
-                 G.Ag,     G.gz,    G.eprev, G.enext, G.ecurve};
+                 G.Ag,     G.gz,    G.gy,    G.eprev, G.enext, G.ecurve};
     for (void *q : p)
         if (q) cudaFree(q);
     delete c.gnn;
@@ -762,13 +763,15 @@ cudaError_t gnn_problem_dot(Ctx &c, const double *a, const double *b, double *ou
 // One training step over n_pairs prepared pairs of the bound geometry (edge records in slot 0):
 // r_i, b_i (the parameter-independent part of M^-1 r_i: the coarse term), Ab_i = A b_i, er_i = e_i . r_i
 // per problem, and ilam (the inverse circulant symbols of the geometry, [nV]; NULL: no rescaled
-// circulant).  Per pair: z = b + W S W r + G r, one A apply of the parameter-dependent part, the loss,
-// dL/dz, the output gradients of G and, through one more circulant apply, of the rescaling.  The loss
-// at the current parameters (mean over pairs and problems) goes to loss_dev; then, for lr > 0, one
-// Adam step.  The parameter gradient is left in the context (gnn_last_grad).
+// circulant).  Additive form (R2 NULL): z = b + W S W r + G r.  Balancing form (R2 given, r2_i =
+// (I - A Q) r_i, b_i = Q r_i): z = b + (I - Q A) y, y = W S W r2 + G r2, and dL/dy = (I - A Q) dL/dz.
+// Per pair: one A apply of the parameter-dependent part, the loss, dL/dz, the output gradients of G and,
+// through one more circulant apply, of the rescaling.  The loss at the current parameters (mean over
+// pairs and problems) goes to loss_dev; then, for lr > 0, one Adam step.  The parameter gradient is left
+// in the context (gnn_last_grad).
 cudaError_t gnn_train_step(Ctx &c, const double *gamma, int n_pairs, const double *R, const double *B,
-                           const double *AB, const double *ER, const double *ilam, float lr, double *loss_dev,
-                           cudaStream_t s)
+                           const double *AB, const double *ER, const double *ilam, const double *R2, float lr,
+                           double *loss_dev, cudaStream_t s)
 {
     GnnState &G = *c.gnn;
     const size_t nv3 = 3 * (size_t)c.nV;
@@ -778,21 +781,30 @@ cudaError_t gnn_train_step(Ctx &c, const double *gamma, int n_pairs, const doubl
     TPE_CHECK(cudaMemsetAsync(G.loss, 0, sizeof(double) * c.nProb, s));
     for (int i = 0; i < n_pairs; ++i) {
         const double *r = R + i * nv3, *b = B + i * nv3, *Ab = AB + i * nv3, *er = ER + (size_t)i * c.nProb;
-        TPE_CHECK(gnn_gapply(c, r, G.g, 0, s, nullptr));
+        const double *x = R2 ? R2 + i * nv3 : r;  // what the learned terms act on
+        TPE_CHECK(gnn_gapply(c, x, G.g, 0, s, nullptr));
         if (ilam) {
-            TPE_CHECK(spectral_apply_ex(c, r, G.zs, s, nullptr, G.diag, ilam, G.vlog));
+            TPE_CHECK(spectral_apply_ex(c, x, G.zs, s, nullptr, G.diag, ilam, G.vlog));
             k_gnn_add<<<nbv, 256, 0, s>>>((int)nv3, G.g, G.zs, G.w);
             c.launches++;
+        } else if (R2) {
+            TPE_CHECK(cudaMemcpyAsync(G.w, G.g, sizeof(double) * nv3, cudaMemcpyDeviceToDevice, s));
         }
-        const double *w = ilam ? G.w : G.g;
+        double *w = (ilam || R2) ? G.w : G.g;
+        if (R2) TPE_CHECK(coarse_balanced_part(c, 2, w, w, s));  // w = (I - Q A) y
         TPE_CHECK(pair_apply(c, gamma, 0, w, G.Ag, s));
         k_gnn_loss<<<c.nProb, 256, 0, s>>>(c.d_prob_v, r, b, w, Ab, G.Ag, er, scale, G.sq, G.loss);
         k_gnn_gz<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_vprob, r, Ab, G.Ag, er, G.sq, G.gz);
         c.launches += 2;
-        TPE_CHECK(gnn_out_grad(c, r, G.gz, scale, i > 0, G.dout, s));
+        const double *gy = G.gz;
+        if (R2) {
+            TPE_CHECK(coarse_balanced_part(c, 1, G.gz, G.gy, s));  // dL/dy = (I - A Q) dL/dz
+            gy = G.gy;
+        }
+        TPE_CHECK(gnn_out_grad(c, x, gy, scale, i > 0, G.dout, s));
         if (ilam) {
-            TPE_CHECK(spectral_apply_ex(c, G.gz, G.zg, s, nullptr, G.diag, ilam, G.vlog));
-            k_gnn_dcv<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, G.gz, G.zs, r, G.zg, G.dcv);
+            TPE_CHECK(spectral_apply_ex(c, gy, G.zg, s, nullptr, G.diag, ilam, G.vlog));
+            k_gnn_dcv<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, gy, G.zs, x, G.zg, G.dcv);
             k_gnn_dc_edges<<<(c.nE + 127) / 128, 128, 0, s>>>(c.nE, c.d_edges, G.dcv, scale, G.dout);
             c.launches += 2;
         }

@@ -43,7 +43,8 @@ namespace tpe {
 
 __global__ void k_records(int nE, const double *__restrict__ g, const int *__restrict__ E, RecF *__restrict__ recF,
                           RecLo *__restrict__ recLo, RecD *__restrict__ recD, double *__restrict__ ell,
-                          double *__restrict__ T, double *__restrict__ x, int *__restrict__ err)
+                          double *__restrict__ T, double *__restrict__ x, int *__restrict__ err,
+                          float *__restrict__ ell_lo)
 {
     int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nE) return;
@@ -65,6 +66,7 @@ __global__ void k_records(int nE, const double *__restrict__ g, const int *__res
     }
     double t[3] = {e[0] / l, e[1] / l, e[2] / l};
     ell[I] = l;
+    if (ell_lo) ell_lo[I] = (float)(l - (double)(float)l);
     for (int k = 0; k < 3; ++k) {
         T[3 * I + k] = t[k];
         x[3 * I + k] = 0.5 * (p1[k] + p2[k]);
@@ -423,11 +425,16 @@ static cudaError_t gather_slots(Ctx &c, const Ctx::Plan &pl, double *out, cudaSt
     return cudaGetLastError();
 }
 
+cudaError_t gather_apply(Ctx &c, const Ctx::Plan &pl, double *Au, cudaStream_t s)
+{
+    return gather_slots<OP_APPLY>(c, pl, Au, s);
+}
+
 // ---------------------------------------------------------------------------------- planning
 
 // Build the (target block, source chunk) queue of one pass.  Items of big problems come first
 // so the persistent grid ends with the small ones.
-static void plan_pass(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy)
+void plan_pass(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy)
 {
     const int tb = kThreads * tpt;
     std::vector<WorkItem> items;
@@ -728,7 +735,7 @@ cudaError_t static_energy_launch(const double *gamma, const int *edges, int nV, 
     *status = 0;
     if (nE == 0) return cudaMemsetAsync(E, 0, sizeof(double), s);
     TPE_CHECK(cudaMemsetAsync(err, 0, sizeof(int), s));
-    k_records<<<(nE + 255) / 256, 256, 0, s>>>(nE, gamma, edges, recF, recLo, nullptr, ell, T, x, err);
+    k_records<<<(nE + 255) / 256, 256, 0, s>>>(nE, gamma, edges, recF, recLo, nullptr, ell, T, x, err, nullptr);
     k_static_stats<<<1, 256, 0, s>>>(nV, nE, gamma, ell, scal);
     TPE_CHECK(cudaGetLastError());
     // the cutoffs are kernel arguments: read the two statistics and the error word (synchronises)
@@ -798,12 +805,14 @@ cudaError_t static_energy_launch(const double *gamma, const int *edges, int nV, 
 cudaError_t build_records(Ctx &c, const double *gamma, int which, cudaStream_t s)
 {
     int nb = (c.nE + 255) / 256;
-    const bool p64 = c.prm.precision == TP_FP64, mix = c.prm.precision == TP_MIXED;
+    const bool p64 = c.prm.precision == TP_FP64;
     RecF *rf = p64 ? nullptr : (which ? c.d_recF2 : c.d_recF);
-    RecLo *rl = mix ? (which ? c.d_recLo2 : c.d_recLo) : nullptr;
+    // the low parts serve the mixed pair passes and, in FP32 contexts too, the double-float apply
+    RecLo *rl = p64 ? nullptr : (which ? c.d_recLo2 : c.d_recLo);
     RecD *rd = p64 ? (which ? c.d_recD2 : c.d_recD) : nullptr;
     if (c.nE == 0) return cudaSuccess;
-    k_records<<<nb, 256, 0, s>>>(c.nE, gamma, c.d_edges, rf, rl, rd, c.d_ellw[which], c.d_Tw[which], c.d_xw[which], c.d_err);
+    k_records<<<nb, 256, 0, s>>>(c.nE, gamma, c.d_edges, rf, rl, rd, c.d_ellw[which], c.d_Tw[which], c.d_xw[which], c.d_err,
+                                 p64 ? nullptr : c.d_ell_lo[which]);
     c.launches++;
     return cudaGetLastError();
 }

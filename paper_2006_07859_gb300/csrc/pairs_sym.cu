@@ -752,7 +752,7 @@ static int sym_occupancy(int tpt)
 }
 
 // Edge blocks of 128 x tpt per problem; items (b, c >= b) sorted by problem size (large first).
-static void sym_plan_items(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy)
+void sym_plan_items(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy)
 {
     const int tb = kThreads * tpt;
     std::vector<int> vmin(c.nV, INT32_MAX), vmax(c.nV, -1);

@@ -499,6 +499,9 @@ cudaError_t precond_apply_base(Ctx &c, const double *r, double *z, cudaStream_t 
         if (e != cudaSuccess) return e;
         return coarse_apply(c, r, z, s);
     }
+    case TP_PRECOND_TWOLEVEL_BALANCED:
+    case TP_PRECOND_LEARNED_BALANCED:
+        return coarse_balanced_apply(c, r, z, s, skip, false);
     default:
         return cudaMemcpyAsync(z, r, sizeof(double) * 3 * c.nV, cudaMemcpyDeviceToDevice, s);
     }
@@ -508,8 +511,9 @@ cudaError_t precond_apply_base(Ctx &c, const double *r, double *z, cudaStream_t 
 // per-vertex rescaling, the coarse term and the learned local term G r.
 cudaError_t precond_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip)
 {
-    if (c.prm.precond != TP_PRECOND_LEARNED) return precond_apply_base(c, r, z, s, skip);
+    if (!precond_learned(c.prm.precond)) return precond_apply_base(c, r, z, s, skip);
     if (!gnn_ready(c) || !gnn_bound(c)) return cudaErrorNotReady;
+    if (c.prm.precond == TP_PRECOND_LEARNED_BALANCED) return coarse_balanced_apply(c, r, z, s, skip, true);
     cudaError_t e = spectral_apply_ex(c, r, z, s, skip, c.d_diag, spectral_ilam(c, s), gnn_vlog(c));
     if (e != cudaSuccess) return e;
     if ((e = coarse_apply(c, r, z, s)) != cudaSuccess) return e;
@@ -707,40 +711,99 @@ __global__ void k_cg_p(int nV, const int *__restrict__ vprob, const double *__re
     for (int k = 0; k < 3; ++k) p[3 * i + k] = (z[3 * i + k] - cg[q].mz[k]) + b * p[3 * i + k];
 }
 
-// Relative residual per problem: out[q] = sqrt(|r_true|^2 / |P rhs|^2)
+// Relative residual per problem: out[q] = sqrt(|r_true|^2 / |P rhs|^2), |P rhs|^2 from bn2[q] when given
+// (the refinement keeps the first solve's norms), else from the solve's scalars.  bn2_out (may be NULL)
+// receives the norms used.
 __global__ void k_relres(RedArgs ra, const double *__restrict__ r, const CGScalars *__restrict__ cg,
-                         double *__restrict__ out)
+                         double *__restrict__ out, const double *__restrict__ bn2, double *__restrict__ bn2_out)
 {
     double s[1] = {0};
     int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
     for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
         s[0] += r[3 * i] * r[3 * i] + r[3 * i + 1] * r[3 * i + 1] + r[3 * i + 2] * r[3 * i + 2];
     if (reduce_phase<1>(s, ra))
-        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x)
-            out[q] = cg[q].bnorm2 > 0.0 ? sqrt(ra.sums[q] / cg[q].bnorm2) : 0.0;
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x) {
+            const double b = bn2 ? bn2[q] : cg[q].bnorm2;
+            out[q] = b > 0.0 ? sqrt(ra.sums[q] / b) : 0.0;
+            if (bn2_out) bn2_out[q] = b;
+        }
+}
+
+// v[i] = 0 on the vertices of problems whose keep[q] is 0
+__global__ void k_zero_problems(int nV, const int *__restrict__ vprob, const int *__restrict__ keep,
+                                double *__restrict__ v)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV || keep[vprob[i]]) return;
+    v[3 * i] = v[3 * i + 1] = v[3 * i + 2] = 0.0;
 }
 
 // Solve P A-bar P y = P rhs (A-bar of the geometry `which`), x = P y.  The constraint Jacobian
 // (c.d_Cv, c.d_Ginv) must describe the projector to use.  rhs and x may not alias the CG scratch.
 cudaError_t project_mean(Ctx &c, double *v, cudaStream_t s, const int *skip);
 
+// v -= C_len (C_len . v) / (C_len . C_len) per problem (the total-length row of the Jacobian at the base
+// curve, row 3 of c.d_Cv); C_len sums to zero over every problem, so this commutes with the mean removal.
+__global__ void k_len_red(RedArgs ra, const double *__restrict__ C, const double *__restrict__ v,
+                          double *__restrict__ out)
+{
+    double s[2] = {0, 0};
+    int lo = ra.chunk_lo[blockIdx.x], hi = ra.chunk_lo[blockIdx.x + 1];
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        for (int k = 0; k < 3; ++k) {
+            const double cl = C[(size_t)i * 12 + 9 + k];
+            s[0] += cl * v[3 * i + k];
+            s[1] += cl * cl;
+        }
+    if (reduce_phase<2>(s, ra))
+        for (int q = threadIdx.x; q < ra.nprob; q += blockDim.x)
+            out[q] = ra.sums[2 * q + 1] > 0.0 ? ra.sums[2 * q] / ra.sums[2 * q + 1] : 0.0;
+}
+
+__global__ void k_len_sub(int nV, const double *__restrict__ C, const double *__restrict__ coef,
+                          const int *__restrict__ vprob, double *__restrict__ v, const int *__restrict__ skip)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nV) return;
+    const int q = vprob[i];
+    if (skip && skip[q]) return;
+    const double a = coef[q];
+    for (int k = 0; k < 3; ++k) v[3 * i + k] -= a * C[(size_t)i * 12 + 9 + k];
+}
+
+static cudaError_t project_len(Ctx &c, double *v, cudaStream_t s, const int *skip)
+{
+    SolverState &st = S(c);
+    k_len_red<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 2), c.d_Cv, v, st.mu);
+    k_len_sub<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_Cv, st.mu, c.d_vprob, v, skip);
+    c.launches += 2;
+    return cudaGetLastError();
+}
+
 // proj_mode 0: P = I - C^T (C C^T)^-1 C (constraint projector); 1: P = subtract the per-problem mean;
-// 2: the mean, then the edge-length rows (P = P_E P_N, the two commute; edges.cu, set up by edges_setup).
+// 2: the mean, then the edge-length rows (P = P_E P_N, the two commute; edges.cu, set up by edges_setup);
+// 3: the mean, then the total-length row (P = P_len P_N; the projected system of App. B.3.3 for the
+// total-length row, with the translations left to the barycenter shift).
 static cudaError_t projector(Ctx &c, int mode, double *v, cudaStream_t s, const int *skip)
 {
     if (mode == 2) {
         TPE_CHECK(project_mean(c, v, s, skip));
         return edges_project(c, v, s, skip);
     }
+    if (mode == 3) {
+        TPE_CHECK(project_mean(c, v, s, skip));
+        return project_len(c, v, s, skip);
+    }
     return mode ? project_mean(c, v, s, skip) : project(c, v, s, skip);
 }
 
 // What the CG iteration still applies outside its kernels: mode 0 the whole constraint projector, mode 1
-// nothing, mode 2 the edge rows (their projector commutes with the mean removal).
+// nothing, mode 2 the edge rows, mode 3 the length row (both commute with the mean removal).
 static cudaError_t projector_rest(Ctx &c, int mode, double *v, cudaStream_t s, const int *skip)
 {
     if (mode == 0) return project(c, v, s, skip);
     if (mode == 2) return edges_project(c, v, s, skip);
+    if (mode == 3) return project_len(c, v, s, skip);
     return cudaSuccess;
 }
 
@@ -854,9 +917,18 @@ static cudaError_t graph_block(Ctx &c, const double *gamma_geom, int which, int 
     return cudaSuccess;
 }
 
-cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
-                     int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s,
-                     int proj_mode, int *conv_flags, const double *x0)
+// Per-problem outcome of one preconditioned CG run.
+struct PcgOut {
+    std::vector<int> iters, done, bd;
+    std::vector<double> rr;  // true relative residual of x (when computed)
+};
+
+// Preconditioned CG on P A-bar P y = P rhs (the working-precision operator), x = P y.  residual: 0 none,
+// 1 with the working-precision operator, 2 with the accurate (double-float) one; r = P (rhs - A-bar x) is
+// then left in c.d_r and the norms |P rhs|^2 in bn2 (device [nProb], may be NULL).
+static cudaError_t pcg_run(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
+                           int maxit, cudaStream_t s, int proj_mode, const double *x0, int residual, PcgOut &out,
+                           double *bn2)
 {
     SolverState &st = S(c);
     const size_t vb = sizeof(double) * 3 * c.nV;
@@ -954,37 +1026,121 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
         TPE_CHECK(cudaEventRecord(c.cg_join[1], rs));
         TPE_CHECK(cudaStreamWaitEvent(s, c.cg_join[1], 0));
     }
-    // x = P y; true residual r = P (rhs - A-bar x) with the working-precision operator
+    // x = P y; true residual r = P (rhs - A-bar x)
     TPE_CHECK(cudaMemcpyAsync(x, y, vb, cudaMemcpyDeviceToDevice, s));
     TPE_CHECK(projector(c, proj_mode, x, s, nullptr));
-    TPE_CHECK(pair_apply(c, gamma_geom, which, x, q, s));
-    TPE_CHECK(vec_axpby(c, 1.0, rhs, -1.0, q, r, s));
-    TPE_CHECK(projector(c, proj_mode, r, s, nullptr));
     double *rr = c.d_scal + 64 + 10 * (size_t)c.nProb;  // [nProb]
-    k_relres<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), r, c.d_cg, rr);
-    c.launches++;
+    if (residual) {
+        if (residual == 2)
+            TPE_CHECK(pair_apply_acc(c, gamma_geom, which, x, q, s));
+        else
+            TPE_CHECK(pair_apply(c, gamma_geom, which, x, q, s));
+        TPE_CHECK(vec_axpby(c, 1.0, rhs, -1.0, q, r, s));
+        TPE_CHECK(projector(c, proj_mode, r, s, nullptr));
+        k_relres<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), r, c.d_cg, rr, nullptr, bn2);
+        c.launches++;
+    }
     std::vector<CGScalars> hcg(c.nProb);
-    std::vector<double> hrr(c.nProb);
+    out.rr.assign(c.nProb, 0.0);
     TPE_CHECK(cudaMemcpyAsync(hcg.data(), c.d_cg, sizeof(CGScalars) * c.nProb, cudaMemcpyDeviceToHost, s));
-    TPE_CHECK(cudaMemcpyAsync(hrr.data(), rr, sizeof(double) * c.nProb, cudaMemcpyDeviceToHost, s));
+    if (residual) TPE_CHECK(cudaMemcpyAsync(out.rr.data(), rr, sizeof(double) * c.nProb, cudaMemcpyDeviceToHost, s));
     TPE_CHECK(cudaStreamSynchronize(s));
-    c.last_rr = hrr;
-    c.last_iters.resize(c.nProb);
-    for (int qq = 0; qq < c.nProb; ++qq) c.last_iters[qq] = hcg[qq].iters;
-    int mx_it = 0, bd = 0, conv = 1;
-    double mx_rr = 0.0;
+    out.iters.resize(c.nProb);
+    out.done.resize(c.nProb);
+    out.bd.resize(c.nProb);
     for (int qq = 0; qq < c.nProb; ++qq) {
-        mx_it = std::max(mx_it, hcg[qq].iters);
-        bd |= hcg[qq].breakdown;
-        int ok = (hcg[qq].done && !hcg[qq].breakdown) ? 1 : 0;
+        out.iters[qq] = hcg[qq].iters;
+        out.done[qq] = hcg[qq].done;
+        out.bd[qq] = hcg[qq].breakdown;
+    }
+    return cudaSuccess;
+}
+
+// Solves below this relative tolerance in FP32 / mixed contexts are refined against the double-float
+// operator: the FP32 pair arithmetic's rounding sets a floor on the true residual (~1e-5 on curves of
+// 4,096 vertices, ~3e-4 on smooth vectors at 262,144, growing like n^2) that the recursive residual does
+// not see.  Looser solves (the constraint projections at 1e-3) keep the working-precision residual.
+constexpr double kRefineBelow = 5e-4;
+constexpr int kRefineMax = 4;        // correction solves at most
+constexpr double kCorrectionTol = 1e-2;
+
+cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
+                     int maxit, int *iters, double *rel_res, int *converged, int *breakdown, cudaStream_t s,
+                     int proj_mode, int *conv_flags, const double *x0)
+{
+    SolverState &st = S(c);
+    const bool refine = c.prm.precision != TP_FP64 && rtol < kRefineBelow && !c.hv.R;
+    double *bn2 = c.d_scal + 64 + 11 * (size_t)c.nProb;  // [nProb] |P rhs|^2 of this solve
+    PcgOut o;
+    TPE_CHECK(pcg_run(c, gamma_geom, which, rhs, x, rtol, maxit, s, proj_mode, x0, refine ? 2 : 1, o, bn2));
+    std::vector<int> it = o.iters, bd = o.bd, done = o.done;
+    std::vector<double> rr = o.rr;
+    int rounds = 0;
+    if (refine) {
+        // Iterative refinement: the residual r = P (rhs - A-bar_acc x) of the accurate operator is solved
+        // for a correction e with the working-precision PCG (to kCorrectionTol relative), x += e, and r
+        // is formed again, until every problem's true relative residual is within rtol.
+        const int nb = (c.nV + 255) / 256;
+        int *keep = reinterpret_cast<int *>(c.d_scal + 64 + 14 * (size_t)c.nProb);  // nProb ints
+        double *rr_d = c.d_scal + 64 + 10 * (size_t)c.nProb;
+        std::vector<double> prev(c.nProb, 0.0);
+        for (; rounds < kRefineMax; ++rounds) {
+            std::vector<int> need(c.nProb, 0);
+            int any = 0;
+            for (int q = 0; q < c.nProb; ++q) {
+                // a problem whose last correction did not halve its residual has reached the accurate
+                // operator's own evaluation floor: further rounds cannot help it
+                const bool stalled = rounds > 0 && rr[q] > 0.5 * prev[q];
+                need[q] = !bd[q] && rr[q] > rtol && !stalled;
+                any |= need[q];
+            }
+            if (!any) break;
+            prev = rr;
+            TPE_CHECK(cudaMemcpyAsync(keep, need.data(), sizeof(int) * c.nProb, cudaMemcpyHostToDevice, s));
+            TPE_CHECK(cudaMemcpyAsync(c.d_rf, c.d_r, sizeof(double) * 3 * c.nV, cudaMemcpyDeviceToDevice, s));
+            k_zero_problems<<<nb, 256, 0, s>>>(c.nV, c.d_vprob, keep, c.d_rf);
+            c.launches++;
+            PcgOut oc;
+            TPE_CHECK(pcg_run(c, gamma_geom, which, c.d_rf, c.d_ef, kCorrectionTol, maxit, s, proj_mode, nullptr, 0, oc,
+                              nullptr));
+            TPE_CHECK(vec_axpby(c, 1.0, x, 1.0, c.d_ef, x, s));
+            for (int q = 0; q < c.nProb; ++q)
+                if (need[q]) {
+                    it[q] += oc.iters[q];
+                    bd[q] |= oc.bd[q];
+                }
+            // r = P (rhs - A-bar_acc x), relative to the first solve's |P rhs|
+            TPE_CHECK(pair_apply_acc(c, gamma_geom, which, x, c.d_q, s));
+            TPE_CHECK(vec_axpby(c, 1.0, rhs, -1.0, c.d_q, c.d_r, s));
+            TPE_CHECK(projector(c, proj_mode, c.d_r, s, nullptr));
+            k_relres<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_r, c.d_cg, rr_d, bn2, nullptr);
+            c.launches++;
+            TPE_CHECK(cudaMemcpyAsync(rr.data(), rr_d, sizeof(double) * c.nProb, cudaMemcpyDeviceToHost, s));
+            TPE_CHECK(cudaStreamSynchronize(s));
+        }
+    }
+    c.last_rr = rr;
+    c.last_iters = it;
+    c.last_refinements = rounds;
+    // converged: CG met the tolerance and the true relative residual is within rtol when it was judged by
+    // the accurate operator (refined solves), or within 10 rtol when judged by the working-precision
+    // operator after CG stopped on its recursive residual (FP64 solves, whose rounding can leave the true
+    // residual a little above a tolerance near 1e-11; and the loose projection solves)
+    const double lim = refine ? rtol : 10.0 * rtol;
+    int mx_it = 0, b = 0, conv = 1;
+    double mx_rr = 0.0;
+    for (int q = 0; q < c.nProb; ++q) {
+        mx_it = std::max(mx_it, it[q]);
+        b |= bd[q];
+        const int ok = (done[q] || refine) && !bd[q] && rr[q] <= lim;
         conv &= ok;
-        if (conv_flags) conv_flags[qq] &= ok;
-        mx_rr = std::max(mx_rr, hrr[qq]);
+        if (conv_flags) conv_flags[q] &= ok;
+        mx_rr = std::max(mx_rr, rr[q]);
     }
     if (iters) *iters = mx_it;
     if (rel_res) *rel_res = mx_rr;
     if (converged) *converged = conv;
-    if (breakdown) *breakdown = bd;
+    if (breakdown) *breakdown = b;
     return cudaSuccess;
 }
 

@@ -132,11 +132,13 @@ struct Ctx {
     int energy_sym = 0;      // > 0: the energy runs the symmetric pass with this many targets per thread
     Plan plan_sym_d;         // symmetric differential (pairs_sym.cu)
     int diff_sym = 0;        // > 0: the differential runs the symmetric pass
+    Plan plan_df;            // double-float apply (pairs_df.cu), built at its first use
     int *d_counter = nullptr;  // persistent-queue counters [8]
     // edge records
     RecF *d_recF = nullptr, *d_recF2 = nullptr;
     RecLo *d_recLo = nullptr, *d_recLo2 = nullptr;
     RecD *d_recD = nullptr, *d_recD2 = nullptr;
+    float *d_ell_lo[2] = {nullptr, nullptr};  // low parts of the edge lengths (double-float apply)
     // FP64 edge quantities of the two geometries (0: base curve, 1: trial curve): [nE], [nE][3], [nE][3]
     double *d_ellw[2] = {nullptr, nullptr}, *d_Tw[2] = {nullptr, nullptr}, *d_xw[2] = {nullptr, nullptr};
     double mean_ell = 0.0;
@@ -173,6 +175,7 @@ struct Ctx {
     double *d_best = nullptr;  // [nV][3] line-search result
     double *d_yw0 = nullptr, *d_yw1 = nullptr;  // [nV][3] last gradient solutions (warm starts of the next step)
     int warm_ok = 0;                            // d_yw0 / d_yw1 hold solutions of an earlier step
+    int warm1_ok = 0;                           // total-length route: d_yw1 holds the last projection solution
     double *d_t5 = nullptr, *d_t6 = nullptr;
     int64_t pairs_per_pass = 0;
     const int *d_skip = nullptr;  // during a CG solve: per-problem converged flags (apply skips them)
@@ -190,6 +193,8 @@ struct Ctx {
     int graphs_broken = 0;         // a capture failed: direct launches from then on
     int setups_since_full = -1;    // preconditioner set-ups since the last full one (-1: none yet)
     std::vector<double> last_rr;   // per problem: true relative residual of the last CG solve
+    int last_refinements = 0;      // correction solves of the last CG solve (iterative refinement)
+    double *d_rf = nullptr, *d_ef = nullptr;  // [nV][3] refinement residual and correction
     std::vector<int> last_iters;   // per problem: its iterations
     // (residual, iterate) capture of a CG solve: every `every` iterations r -> R[n], y -> Y[n]
     struct Harvest {
@@ -200,8 +205,8 @@ struct Ctx {
     int profile = 0;
     std::vector<cudaEvent_t> prof_pool;
     std::vector<std::pair<int, int>> prof_pending;  // (op, slot)
-    double prof_ms[5] = {0, 0, 0, 0, 0};
-    int64_t prof_n[5] = {0, 0, 0, 0, 0};
+    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+    int64_t prof_n[6] = {0, 0, 0, 0, 0, 0};
 };
 
 int prof_begin(Ctx &c, int op, cudaStream_t s);
@@ -217,6 +222,11 @@ cudaError_t pair_energy(Ctx &c, const double *gamma, int which, double *rows_out
 cudaError_t pair_diff(Ctx &c, const double *gamma, int which, double *dE, cudaStream_t s);
 cudaError_t pair_apply(Ctx &c, const double *gamma_geom, int which, const double *u, double *Au, cudaStream_t s);
 cudaError_t pair_diag(Ctx &c, const double *gamma_geom, int which, double *diag, cudaStream_t s);
+// (pairs_df.cu) the apply in double-float arithmetic: the accurate operator of residual checks
+cudaError_t pair_apply_acc(Ctx &c, const double *gamma_geom, int which, const double *u, double *Au, cudaStream_t s);
+void plan_pass(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy);
+void sym_plan_items(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy);  // (pairs_sym.cu) items (b, c >= b)
+cudaError_t gather_apply(Ctx &c, const Ctx::Plan &pl, double *Au, cudaStream_t s);
 cudaError_t sym_select(Ctx &c, int tpt);  // (pairs_sym.cu) symmetric apply on (tpt 1, 2) or off (0)
 cudaError_t sym_apply_pass(Ctx &c, int which, const double *gamma, const double *u, cudaStream_t s);
 size_t sym_slots(const Ctx &c, int tpt);
@@ -239,6 +249,11 @@ cudaError_t spectral_setup(Ctx &c, cudaStream_t s);
 cudaError_t spectral_rq_setup(Ctx &c, const double *gamma_geom, int which, cudaStream_t s);
 cudaError_t coarse_setup(Ctx &c, const double *gamma_geom, int which, cudaStream_t s);
 cudaError_t coarse_apply(Ctx &c, const double *r, double *z, cudaStream_t s);
+cudaError_t coarse_balanced_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip, bool learned);
+cudaError_t coarse_balanced_part(Ctx &c, int which, const double *v, double *out, cudaStream_t s);
+inline bool precond_learned(int p) { return p == TP_PRECOND_LEARNED || p == TP_PRECOND_LEARNED_BALANCED; }
+inline bool precond_balanced(int p) { return p == TP_PRECOND_TWOLEVEL_BALANCED || p == TP_PRECOND_LEARNED_BALANCED; }
+cudaError_t spectral_apply(Ctx &c, const double *r, double *z, cudaStream_t s, const int *skip);
 void coarse_free(Ctx &c);
 cudaError_t spectral_symbol_copy(Ctx &c, int rq, double *out, cudaStream_t s);
 void spectral_free(Ctx &c);
@@ -329,8 +344,8 @@ cudaError_t gnn_out_grad(Ctx &c, const double *r, const double *gz, double scale
                          cudaStream_t s);
 cudaError_t gnn_problem_dot(Ctx &c, const double *a, const double *b, double *out, cudaStream_t s);
 cudaError_t gnn_train_step(Ctx &c, const double *gamma, int n_pairs, const double *R, const double *B,
-                           const double *AB, const double *ER, const double *ilam, float lr, double *loss_dev,
-                           cudaStream_t s);
+                           const double *AB, const double *ER, const double *ilam, const double *R2, float lr,
+                           double *loss_dev, cudaStream_t s);
 const double *gnn_vlog(const Ctx &c);
 
 }  // namespace tpe

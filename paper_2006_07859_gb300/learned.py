@@ -51,6 +51,7 @@ class PairSet:
     AB: object
     ER: object
     ILAM: object = None
+    R2: object = None     # balancing form: (I - A Q) r, what the learned smoother acts on
 
     @property
     def n(self) -> int:
@@ -59,7 +60,8 @@ class PairSet:
 
 def harvest(ctx: tpe.Context, gamma, rhs, every: int = 1, max_pairs: int = 32) -> PairSet:
     """Run the gradient-type CG solve A-bar y = P rhs on `gamma` with capture and prepare its pairs.
-    The context's preconditioner should be TP_PRECOND_TWOLEVEL (the base the learned term adds to)."""
+    The context's preconditioner should be the base the learned term shapes: TP_PRECOND_TWOLEVEL (for
+    TP_PRECOND_LEARNED) or TP_PRECOND_TWOLEVEL_BALANCED (for TP_PRECOND_LEARNED_BALANCED)."""
     import torch
     nV = ctx.n_vertices
     R = torch.empty((max_pairs, nV, 3), dtype=torch.float64, device="cuda")
@@ -69,9 +71,11 @@ def harvest(ctx: tpe.Context, gamma, rhs, every: int = 1, max_pairs: int = 32) -
     AB = torch.empty_like(R)
     ER = torch.empty((n, ctx.n_problems), dtype=torch.float64, device="cuda")
     ILAM = torch.empty(nV, dtype=torch.float64, device="cuda")
+    balanced = ctx.params.precond in (tpe.TP_PRECOND_TWOLEVEL_BALANCED, tpe.TP_PRECOND_LEARNED_BALANCED)
+    R2 = torch.empty_like(R) if balanced else None
     if n:
-        tpe.tp_gnn_prepare_pairs(ctx, gamma, R, E, E, AB, ER, ILAM)  # R := A-bar E; B overwrites E in place
-    return PairSet(gamma.clone(), R, E, AB, ER, ILAM)
+        tpe.tp_gnn_prepare_pairs(ctx, gamma, R, E, E, AB, ER, ILAM, R2)  # R := A-bar E; B overwrites E in place
+    return PairSet(gamma.clone(), R, E, AB, ER, ILAM, R2)
 
 
 def harvest_descent(ctx: tpe.Context, gamma, steps: int, every: int = 1, max_pairs: int = 32) -> list[PairSet]:
@@ -109,7 +113,8 @@ def train(ctx: tpe.Context, sets: list[PairSet], steps: int = 200, lr: float = 3
         b = min(batch, ps.n)
         j = int(rng.integers(ps.n - b + 1))          # a contiguous window of pairs: views, no copies
         loss = tpe.tp_gnn_train_step(ctx, ps.gamma, ps.R[j:j + b], ps.B[j:j + b], ps.AB[j:j + b],
-                                     ps.ER[j:j + b], lr, ILAM=ps.ILAM)
+                                     ps.ER[j:j + b], lr, ILAM=ps.ILAM,
+                                     R2=None if ps.R2 is None else ps.R2[j:j + b])
         losses.append(loss)
         if log_every and (it % log_every == 0 or it == steps - 1):
             print(f"step {it:5d}  loss {loss:.6f}", flush=True)
@@ -124,6 +129,6 @@ def evaluate_loss(ctx: tpe.Context, sets: list[PairSet], theta) -> float:
         if ps.n == 0:
             continue
         tpe.tp_gnn_bind(ctx, ps.gamma)
-        tot += tpe.tp_gnn_train_step(ctx, ps.gamma, ps.R, ps.B, ps.AB, ps.ER, 0.0, ILAM=ps.ILAM) * ps.n
+        tot += tpe.tp_gnn_train_step(ctx, ps.gamma, ps.R, ps.B, ps.AB, ps.ER, 0.0, ILAM=ps.ILAM, R2=ps.R2) * ps.n
         cnt += ps.n
     return tot / max(1, cnt)

@@ -18,6 +18,8 @@ TP_ERR_UNSUPPORTED = 10
 TP_FP64, TP_FP32, TP_MIXED = 0, 1, 2
 TP_PRECOND_NONE, TP_PRECOND_JACOBI, TP_PRECOND_SPECTRAL, TP_PRECOND_SPECTRAL_RQ, TP_PRECOND_TWOLEVEL = 0, 1, 2, 3, 4
 TP_PRECOND_LEARNED = 5
+TP_PRECOND_TWOLEVEL_BALANCED = 6
+TP_PRECOND_LEARNED_BALANCED = 7
 TP_GNN_HIDDEN, TP_GNN_FEATURES = 64, 8
 TP_CONSTRAINTS_TOTAL_LENGTH, TP_CONSTRAINTS_EDGE_LENGTHS, TP_CONSTRAINTS_POINTS = 0, 1, 2
 TP_LINESEARCH_UNIT, TP_LINESEARCH_ISOTOPY = 0, 1
@@ -27,7 +29,7 @@ STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ER
                 8: "TP_ERR_PROJECTION", 9: "TP_ERR_OOM", 10: "TP_ERR_UNSUPPORTED"}
 
 EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp_num_problems", "tp_set_params",
-            "tp_energy", "tp_differential", "sobolev_apply", "tp_gram_diagonal", "tp_precond_apply",
+            "tp_energy", "tp_differential", "sobolev_apply", "sobolev_apply_accurate", "tp_gram_diagonal", "tp_precond_apply",
             "tp_spectral_symbol", "tp_set_constraints_from", "tp_constraints", "sobolev_gradient", "descent_step",
             "tp_launch_count", "tp_pairs_per_pass", "tp_profile", "tp_profile_read", "tp_measure_peaks", "tp_energy_static",
             "tp_spectral_symbols", "tp_gnn_num_params", "tp_gnn_set_params", "tp_gnn_get_params", "tp_gnn_bind",
@@ -97,6 +99,7 @@ def library() -> ctypes.CDLL:
         L.tp_energy.argtypes = [vp, vp, vp, vp, vp]
         L.tp_differential.argtypes = [vp, vp, vp, vp, vp]
         L.sobolev_apply.argtypes = [vp, vp, vp, vp, vp]
+        L.sobolev_apply_accurate.argtypes = [vp, vp, vp, vp, vp]
         L.tp_gram_diagonal.argtypes = [vp, vp, vp, vp]
         L.tp_precond_apply.argtypes = [vp, vp, vp, vp, vp]
         L.tp_spectral_symbol.argtypes = [vp, i, vp, vp]
@@ -130,8 +133,8 @@ def library() -> ctypes.CDLL:
         L.tp_gnn_g_apply.argtypes = [vp, vp, vp, i, vp]
         L.tp_gnn_out_grad.argtypes = [vp, vp, vp, vp, i, vp]
         L.tp_cg_harvest.argtypes = [vp, vp, vp, i, i, vp, vp, ctypes.POINTER(i), ctypes.POINTER(TpSolveInfo), vp]
-        L.tp_gnn_prepare_pairs.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp]
-        L.tp_gnn_train_step.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, ctypes.c_float, pdd, vp, vp]
+        L.tp_gnn_prepare_pairs.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.tp_gnn_train_step.argtypes = [vp, vp, i, vp, vp, vp, vp, vp, vp, ctypes.c_float, pdd, vp, vp]
         L.tp_autotune.argtypes = [vp, vp, vp, vp, vp]
         L.tp_set_apply_variant.argtypes = [vp, i]
         L.tp_set_energy_variant.argtypes = [vp, i]
@@ -259,6 +262,12 @@ def tp_differential(ctx: Context, gamma, dE=None, E=None):
 def sobolev_apply(ctx: Context, gamma, u, Au=None):
     Au = _new((ctx.n_vertices, 3)) if Au is None else Au
     ctx._check(library().sobolev_apply(ctx.handle, _ptr(gamma), _ptr(u), _ptr(Au), _stream()))
+    return Au
+
+
+def sobolev_apply_accurate(ctx: Context, gamma, u, Au=None):
+    Au = _new((ctx.n_vertices, 3)) if Au is None else Au
+    ctx._check(library().sobolev_apply_accurate(ctx.handle, _ptr(gamma), _ptr(u), _ptr(Au), _stream()))
     return Au
 
 
@@ -468,18 +477,19 @@ def tp_cg_harvest(ctx: Context, gamma, rhs, every: int, R, E):
     return n.value, {"iters": info.iters, "rel_res": info.rel_res, "converged": info.converged}
 
 
-def tp_gnn_prepare_pairs(ctx: Context, gamma, R, E, B, AB, ER, ILAM=None):
+def tp_gnn_prepare_pairs(ctx: Context, gamma, R, E, B, AB, ER, ILAM=None, R2=None):
     """ER: CUDA float64 [n, n_problems]; B may be E (in place); ILAM (CUDA float64 [nV] or None)
-    receives the curve's inverse circulant symbols and leaves the circulant to training."""
+    receives the curve's inverse circulant symbols and leaves the circulant to training; R2 (like R)
+    receives (I - A Q) r in a balancing-form context (required there)."""
     ctx._check(library().tp_gnn_prepare_pairs(ctx.handle, _ptr(gamma), int(R.shape[0]), _ptr(R), _ptr(E), _ptr(B),
-                                              _ptr(AB), _ptr(ER), _ptr(ILAM), _stream()))
+                                              _ptr(AB), _ptr(ER), _ptr(ILAM), _ptr(R2), _stream()))
 
 
-def tp_gnn_train_step(ctx: Context, gamma, R, B, AB, ER, lr: float, grad=None, ILAM=None) -> float:
+def tp_gnn_train_step(ctx: Context, gamma, R, B, AB, ER, lr: float, grad=None, ILAM=None, R2=None) -> float:
     loss = ctypes.c_double()
     ctx._check(library().tp_gnn_train_step(ctx.handle, _ptr(gamma), int(R.shape[0]), _ptr(R), _ptr(B), _ptr(AB),
-                                           _ptr(ER), _ptr(ILAM), ctypes.c_float(lr), ctypes.byref(loss), _fptr(grad),
-                                           _stream()))
+                                           _ptr(ER), _ptr(ILAM), _ptr(R2), ctypes.c_float(lr), ctypes.byref(loss),
+                                           _fptr(grad), _stream()))
     return loss.value
 
 
