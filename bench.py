@@ -672,7 +672,7 @@ def run_ours(args, rank, world, local_rank):
         total_e2e += ev[0].elapsed_time(ev[3]) / 1e3
     clk = clocks.stop() if clocks else None
     launches = ctx.launch_count() - l0
-    ops = ["energy", "diff", "apply", "diag", "apply_cg", "apply_accurate"]
+    ops = ["energy", "diff", "apply", "diag", "apply_cg", "apply_accurate", "coarse_az"]
     prof = {op: ctx.profile_read(i) for i, op in enumerate(ops)}
     ctx.profile(False)
     tmax = max_over_ranks(total, dist, "cuda")
@@ -698,9 +698,11 @@ def run_ours(args, rank, world, local_rank):
     passes = {k: prof[k][1] / args.steps for k in ("energy", "diff", "apply")}
     passes["apply"] += prof["apply_cg"][1] / args.steps   # every apply launch (the CG ones may skip converged curves)
     passes["apply_accurate"] = prof["apply_accurate"][1] / args.steps
+    passes["coarse_az"] = prof["coarse_az"][1] / args.steps
     pps = {k: (pairs * prof[k][1] / (prof[k][0] / 1e3) if prof[k][1] else None) for k in prof}
     if not single:
         pps["apply_cg"] = None   # CG applies skip converged problems: their pair count is not a full pass
+        pps["coarse_az"] = None  # the coarse pass visits the pairs within each curve only
     big = None if (args.no_262k or args.workload == "knot262144") else pass_throughput_262k(tpe, torch)
     small = None if (args.no_small or args.workload == "knots8x4096") else short_run(tpe, torch, "knots8x4096", args, rank)
     # CPU oracle baseline on a bounded sample, extrapolated with the measured pass counts (the accurate
@@ -709,7 +711,8 @@ def run_ours(args, rank, world, local_rank):
         rates, cores, cpu_val = {}, 0, None
     else:
         rates, cores = oracle_rates(curves, args.cpu_seconds)
-        cpu_passes = dict(passes, apply=passes["apply"] + passes["apply_accurate"])
+        # the coarse A Z pass visits every ordered pair once with apply-like work: one apply's worth
+        cpu_passes = dict(passes, apply=passes["apply"] + passes["apply_accurate"] + passes["coarse_az"])
         cpu_val = oracle_step_rate(rates, pairs, cpu_passes)
     kernel_share = {k: prof[k][0] / 1e3 / total for k in prof}
     sym_apply = tuned["tpt"].get("apply_symmetric", 0)

@@ -143,8 +143,9 @@ typedef struct {
     int proj_maxit;
     int independent;      /* 1: every curve is its own problem (no cross-curve pairs, constraints per curve);
                              0: the whole graph is one problem (one barycenter + one total length) */
-    int coarse_dim;       /* TP_PRECOND_TWOLEVEL: hat functions per closed curve (default 128; at most 2048
-                             and n / 4) */
+    int coarse_dim;       /* TP_PRECOND_TWOLEVEL*: hat functions per closed curve (default 128; at most 8192
+                             and n / 4).  The set-up keeps n (m - 1) doubles of columns A Z per curve from
+                             8 hats on (every two-level form) and 3 (m - 1)^2 doubles of coarse matrices */
     double far_cutoff;    /* TP_MIXED: source tiles farther than far_cutoff * (extent of the curve) from a
                              warp's targets use single-float positions (faster, less accurate); >= 10
                              keeps double-float positions everywhere */
@@ -334,7 +335,9 @@ TPE_API int64_t tp_pairs_per_pass(const tp_ctx *ctx);
 
 /* Per-kernel timing with CUDA events recorded around every pair-kernel launch on its own stream.
  * enable = 1 starts (and clears) the record; op: 0 energy, 1 differential, 2 apply (full passes),
- * 3 diag, 4 apply inside CG solves (items of already converged problems skipped).
+ * 3 diag, 4 apply inside CG solves (items of already converged problems skipped), 5 double-float
+ * apply (tp_sobolev_apply_accurate and the refined solves' residuals), 6 the coarse-space pass that
+ * assembles A Z for the two-level preconditioners.
  * tp_profile_read synchronises the recorded events and returns the summed device time (ms) and
  * the number of launches of that pair kernel since profiling was enabled. */
 TPE_API tp_status tp_profile(tp_ctx *ctx, int enable);

@@ -235,7 +235,7 @@ tp_status tp_profile(tp_ctx *ctx, int enable)
     if (!ctx) return TP_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     prof_harvest(c);
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 7; ++k) {
         c.prof_ms[k] = 0.0;
         c.prof_n[k] = 0;
     }
@@ -245,7 +245,7 @@ tp_status tp_profile(tp_ctx *ctx, int enable)
 
 tp_status tp_profile_read(tp_ctx *ctx, int op, double *total_ms, int64_t *launches)
 {
-    if (!ctx || op < 0 || op > 5) return TP_ERR_INVALID_ARG;
+    if (!ctx || op < 0 || op > 6) return TP_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     prof_harvest(c);
     if (total_ms) *total_ms = c.prof_ms[op];

@@ -8,8 +8,10 @@
 //
 // Z = the m - 1 first of m periodic hat functions per closed curve (centres i = j n / m, support of
 // two hat widths; the m hats sum to 1, so the dropped one is implied on the mean-free subspace).
-// Z^T A Z is assembled with (m - 1) / 3 applies of the pair kernel (three hats per apply, one per
-// component), Cholesky-factored per curve in FP64 and inverted explicitly (L^-T L^-1) at set-up.
+// Z^T A Z comes from the columns A Z, which one dedicated pair pass assembles (coarse_az.cu); coarse
+// spaces below 8 hats are probed instead, with (m - 1) / 3 applies of the pair kernel (three hats per
+// apply, one per component).  It is Cholesky-factored per curve in FP64 and inverted explicitly
+// (L^-T L^-1) at set-up.
 // Per CG iteration the term costs three small kernels: restriction Z^T r, the (m - 1) x (m - 1)
 // mat-vec with the inverse (all rows and components in parallel), prolongation Z y.
 //
@@ -17,15 +19,14 @@
 // Q = Z E^-1 Z^T, E = Z^T A Z and S the spectral term,
 //   M^-1 r = Q r + (I - Q A) S (I - A Q) r,
 // the symmetric multiplicative combination: it is exact on range(A Z) and leaves S only the complement.
-// The probes of the set-up are the columns A Z themselves; they are kept (n (m - 1) doubles per curve)
-// so that A Q r = (A Z) E^-1 Z^T r and Q A y = Z E^-1 (A Z)^T y cost two dense passes over them and no
-// pair pass.
+// The columns A Z of the set-up are kept (n (m - 1) doubles per curve) so that A Q r = (A Z) E^-1 Z^T r
+// and Q A y = Z E^-1 (A Z)^T y cost two dense passes over them and no pair pass.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <vector>
 
-#include "tpe_internal.cuh"
+#include "coarse.cuh"
 
 namespace tpe {
 
@@ -34,58 +35,6 @@ namespace tpe {
         cudaError_t e_ = (x);             \
         if (e_ != cudaSuccess) return e_; \
     } while (0)
-
-constexpr int kMaxCoarse = 2048;
-constexpr int kSmemCoarse = 128;  // coarse spaces up to this size factor in shared memory, larger ones in global
-constexpr int kFactorSmem = (kSmemCoarse - 1) * (kSmemCoarse - 1) * (int)sizeof(double);  // 127^2 doubles
-
-struct CoarseCurve {
-    int v0, n, m;  // hats j = 0 .. m-2 are the basis
-    int pad;
-    long long aoff, woff;  // offsets of the factor [(m-1)^2] and of the coarse vectors [(m-1) x 3]
-    long long zoff;        // offset of the curve's A Z columns [(m-1)][n] (balancing form)
-};
-
-}  // namespace tpe
-
-struct tpe::CoarseState {
-    std::vector<CoarseCurve> curves;
-    CoarseCurve *d_curves = nullptr;
-    int *d_vcurve = nullptr;
-    double *d_L = nullptr;   // per curve: (Z^T A Z)^-1, row-major (m-1) x (m-1)
-    double *d_Li = nullptr;  // set-up scratch: L^-1 of the Cholesky factor, same layout
-    double *d_W = nullptr;   // set-up scratch: Cholesky work array of coarse spaces above 127 hats
-    double *d_w = nullptr;  // coarse vectors: restriction Z^T r
-    double *d_w2 = nullptr; // coarse vectors: (Z^T A Z)^-1 Z^T r
-    double *d_w3 = nullptr, *d_w4 = nullptr;  // balancing form: (A Z)^T y and its coarse solve
-    double *d_AZ = nullptr;  // balancing form: per curve the columns A z_j, [(m-1)][n] (column-major)
-    double *d_r2 = nullptr;  // balancing form: r - A Q r, [nV][3]
-    int max_m = 0;
-    int ready = 0;
-    int balanced = 0;        // the AZ columns are kept (every problem is one curve)
-};
-
-namespace tpe {
-
-// hat j of a curve with n vertices and m hats at local vertex i (periodic)
-__device__ __forceinline__ double hat(int i, int j, int n, int m)
-{
-    double t = (double)i * m / n;
-    double d = fabs(t - j);
-    d = fmin(d, m - d);
-    return fmax(0.0, 1.0 - d);
-}
-
-// local index range [lo, lo + len) (mod n) covering the support of hat j
-__device__ __forceinline__ void hat_support(int j, int n, int m, int &lo, int &len)
-{
-    lo = (int)floor((double)(j - 1) * n / m) - 1;
-    len = (int)ceil(2.0 * n / m) + 3;
-    if (len > n) {
-        lo = 0;
-        len = n;
-    }
-}
 
 __global__ void k_coarse_probe(int nV, int b, const CoarseCurve *__restrict__ cc, const int *__restrict__ vcurve,
                                double *__restrict__ y)
@@ -131,15 +80,15 @@ __global__ void k_coarse_gram(int b, const CoarseCurve *__restrict__ cc, const d
         }
 }
 
-// symmetrise, Cholesky-factor and invert every curve's coarse matrix in place (one block per curve);
+// symmetrise, Cholesky-factor and invert in place every curve's coarse matrix of at most 127 rows, in
+// shared memory (one block per curve; larger ones go to the tiled kernels of coarse_factor.cu);
 // Li: scratch of the same layout for L^-1
-__global__ void k_coarse_factor(const CoarseCurve *__restrict__ cc, double *__restrict__ L, double *__restrict__ Li,
-                                double *__restrict__ W)
+__global__ void k_coarse_factor(const CoarseCurve *__restrict__ cc, double *__restrict__ L, double *__restrict__ Li)
 {
     const CoarseCurve C = cc[blockIdx.x];
     const int mm = C.m - 1;
-    extern __shared__ double sa[];  // [mm][mm] for mm <= 127 (dynamic shared memory)
-    double *a = mm <= kSmemCoarse - 1 ? sa : W + C.aoff;  // larger coarse spaces work in global memory
+    if (mm > kSmemCoarse - 1) return;
+    extern __shared__ double a[];  // [mm][mm] (dynamic shared memory)
     double *g = L + C.aoff;
     for (int t = threadIdx.x; t < mm * mm; t += blockDim.x) {
         int r = t / mm, col = t % mm;
@@ -337,14 +286,39 @@ static cudaError_t coarse_balanced_alloc(Ctx &c)
     CoarseState &S = *c.coarse;
     S.balanced = (c.prm.precond == TP_PRECOND_TWOLEVEL_BALANCED || c.prm.precond == TP_PRECOND_LEARNED_BALANCED) &&
                  c.nCurves == c.nProb;
-    if (!S.balanced || S.d_AZ) return cudaSuccess;
+    if (!S.balanced || S.d_w3) return cudaSuccess;
     const CoarseCurve &L = S.curves.back();
     const long long woff = L.woff + 3LL * (L.m - 1), zoff = L.zoff + (long long)(L.m - 1) * L.n;
     TPE_CHECK(cudaMalloc(&S.d_w3, sizeof(double) * std::max<long long>(1, woff)));
     TPE_CHECK(cudaMalloc(&S.d_w4, sizeof(double) * std::max<long long>(1, woff)));
-    TPE_CHECK(cudaMalloc(&S.d_AZ, sizeof(double) * std::max<long long>(1, zoff)));
+    if (!S.d_AZ) TPE_CHECK(cudaMalloc(&S.d_AZ, sizeof(double) * std::max<long long>(1, zoff)));
     TPE_CHECK(cudaMalloc(&S.d_r2, sizeof(double) * 3 * (size_t)c.nV));
     S.ready = 0;  // the next set-up fills the A Z columns
+    return cudaSuccess;
+}
+
+// The A Z pass's per-edge hat records, its work items (blocks of 128 target rows, biggest curves
+// first) and the A Z columns it writes.
+static cudaError_t coarse_pass_alloc(Ctx &c)
+{
+    CoarseState &S = *c.coarse;
+    const CoarseCurve &L = S.curves.back();
+    const long long zoff = L.zoff + (long long)(L.m - 1) * L.n;
+    TPE_CHECK(cudaMalloc(&S.d_AZ, sizeof(double) * std::max<long long>(1, zoff)));
+    TPE_CHECK(cudaMalloc(&S.d_hbase, sizeof(int) * std::max(1, c.nE)));
+    if (c.prm.precision == TP_FP64)
+        TPE_CHECK(cudaMalloc(&S.d_hatD, sizeof(URecD) * std::max(1, c.nE)));
+    else
+        TPE_CHECK(cudaMalloc(&S.d_hatF, sizeof(URecF) * std::max(1, c.nE)));
+    std::vector<int> order(S.curves.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return S.curves[a].n > S.curves[b].n; });
+    std::vector<int2> items;
+    for (int k : order)
+        for (int r = 0; r < S.curves[k].n; r += kThreads) items.push_back(make_int2(k, r));
+    S.n_items = (int)items.size();
+    TPE_CHECK(cudaMalloc(&S.d_items, sizeof(int2) * std::max<size_t>(1, items.size())));
+    TPE_CHECK(cudaMemcpy(S.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
     return cudaSuccess;
 }
 
@@ -360,6 +334,7 @@ cudaError_t coarse_init(Ctx &c)
         C.v0 = c.h_voff[k];
         C.n = c.h_voff[k + 1] - C.v0;
         C.m = std::max(2, std::min(std::min(c.prm.coarse_dim, kMaxCoarse), C.n / 4));
+        C.e0 = c.h_eoff[k];
         C.aoff = aoff;
         C.woff = woff;
         C.zoff = zoff;
@@ -379,6 +354,11 @@ cudaError_t coarse_init(Ctx &c)
     TPE_CHECK(cudaMalloc(&S.d_W, sizeof(double) * std::max<long long>(1, aoff)));
     TPE_CHECK(cudaMalloc(&S.d_w, sizeof(double) * std::max<long long>(1, woff)));
     TPE_CHECK(cudaMalloc(&S.d_w2, sizeof(double) * std::max<long long>(1, woff)));
+    // the A Z pass needs hats of a few edges each on chain-ordered closed curves (which the spectral
+    // preconditioner under every two-level one already requires); small coarse spaces are probed
+    S.az_pass = c.spectral_ok && !S.curves.empty();
+    for (const CoarseCurve &C : S.curves) S.az_pass = S.az_pass && C.m >= kMinPassCoarse;
+    if (S.az_pass) TPE_CHECK(coarse_pass_alloc(c));
     // balancing form: each problem must be one curve, so that E = Z^T A Z is the exact Galerkin matrix
     TPE_CHECK(coarse_balanced_alloc(c));
     TPE_CHECK(cudaFuncSetAttribute(k_coarse_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, kFactorSmem));
@@ -401,6 +381,10 @@ void coarse_free(Ctx &c)
     cudaFree(c.coarse->d_w4);
     cudaFree(c.coarse->d_AZ);
     cudaFree(c.coarse->d_r2);
+    cudaFree(c.coarse->d_items);
+    cudaFree(c.coarse->d_hbase);
+    cudaFree(c.coarse->d_hatF);
+    cudaFree(c.coarse->d_hatD);
     delete c.coarse;
     c.coarse = nullptr;
 }
@@ -411,7 +395,8 @@ cudaError_t coarse_setup(Ctx &c, const double *gamma_geom, int which, cudaStream
     TPE_CHECK(coarse_init(c));
     CoarseState &S = *c.coarse;
     const int nb = (c.nV + 255) / 256;
-    const int nbatch = (S.max_m - 1 + 2) / 3;
+    const int nbatch = S.az_pass ? 0 : (S.max_m - 1 + 2) / 3;
+    if (S.az_pass) TPE_CHECK(coarse_az_pass(c, which, s));
     for (int b = 0; b < nbatch; ++b) {
         k_coarse_probe<<<nb, 256, 0, s>>>(c.nV, b, S.d_curves, S.d_vcurve, c.d_y);
         c.launches++;
@@ -424,8 +409,11 @@ cudaError_t coarse_setup(Ctx &c, const double *gamma_geom, int which, cudaStream
         }
     }
     const int msm = std::min(S.max_m, kSmemCoarse) - 1;
-    k_coarse_factor<<<c.nCurves, 256, (size_t)msm * msm * sizeof(double), s>>>(S.d_curves, S.d_L, S.d_Li, S.d_W);
+    k_coarse_factor<<<c.nCurves, 256, (size_t)msm * msm * sizeof(double), s>>>(S.d_curves, S.d_L, S.d_Li);
     c.launches++;
+    for (const CoarseCurve &C : S.curves)
+        if (C.m - 1 > kSmemCoarse - 1)
+            TPE_CHECK(coarse_factor_tiled(c, C.m - 1, S.d_L + C.aoff, S.d_W + C.aoff, S.d_Li + C.aoff, s));
     S.ready = 1;
     return cudaGetLastError();
 }

@@ -427,6 +427,54 @@ __device__ __forceinline__ float perp2_df(V3<float> d, V3<float> T, V3<float> Tl
     return dot3(dp, dp);
 }
 
+// The Gram weights of one pair: W = l_J sum_ab |d_ab|^-p and
+// W0 = l_J sum_ab (|T_I x d_ab|^2 + |T_J x d_ab|^2) |d_ab|^-(p+4), both zero when the edges share a vertex
+// (keep false); d2_11 = |d_11|^2.
+// Since g_i2 = g_i1 + l_I T_I, T_I x (g_ia - g_jb) does not depend on a and T_J x (g_ia - g_jb) does not
+// depend on b: two |T x d|^2 per tangent instead of four.  The chords come from d11 by increments that
+// mirror exactly between row I and row J (d12 = d11 - e_J, d21 = d11 + e_I, d22 = d11 + (e_I - e_J)), and
+// the four trapezoid terms are summed as (11 + 22) + (12 + 21): every quantity of the pair is bitwise the
+// same (up to sign) from row I and from row J, so W_IJ = W_JI and W0_IJ + W0_JI are exact and the FP32
+// operator stays exactly symmetric.
+template <bool FAST, bool DF, class R, class SR>
+__device__ __forceinline__ void gram_weights(const Tgt<R> &t, const SR &s, bool keep, R pp, R &W, R &W0, R &d2_11)
+{
+    V3<R> dd[4];
+    chords<DF>(t, s, dd);
+    R tt;
+    V3<R> dp;
+    const R cI1 = perp2(dd[0], t.T, tt, dp), cI2 = perp2(dd[1], t.T, tt, dp);  // |T_I x d_1b|^2
+    const R cJ1 = perp2(dd[0], s.T, tt, dp), cJ2 = perp2(dd[2], s.T, tt, dp);  // |T_J x d_a1|^2
+    const R c2s[4] = {cI1 + cJ1, cI2 + cJ1, cI1 + cJ2, cI2 + cJ2};
+    R tw[4], tw0[4];
+#pragma unroll
+    for (int ab = 0; ab < 4; ++ab) {
+        const R d2 = dot3(dd[ab], dd[ab]);
+        if (ab == 0) d2_11 = d2;
+        R r2;
+        R rp = inv_pow<R, FAST, 1>(d2, pp, r2);
+        tw[ab] = rp;
+        tw0[ab] = c2s[ab] * (rp * r2 * r2);
+    }
+    const R sw = (tw[0] + tw[3]) + (tw[1] + tw[2]);
+    const R sw0 = (tw0[0] + tw0[3]) + (tw0[1] + tw0[2]);
+    W = keep ? s.ell * sw : (R)0;
+    W0 = keep ? s.ell * sw0 : (R)0;
+}
+
+// |T_I - T_J|^2 / 2 = 1 - <T_I, T_J> (with the tangents' low parts when DF)
+template <bool DF, class R, class SR>
+__device__ __forceinline__ R tangent_gap(const Tgt<R> &t, const SR &s)
+{
+    V3<R> dT = {t.T.x - s.T.x, t.T.y - s.T.y, t.T.z - s.T.z};
+    if constexpr (DF) {
+        dT.x += t.Tl.x - s.Tm.x;
+        dT.y += t.Tl.y - s.Tm.y;
+        dT.z += t.Tl.z - s.Tm.z;
+    }
+    return (R)0.5 * dot3(dT, dT);
+}
+
 template <int PREC, int OP, bool FAST, bool DF = (PREC == PMIX)>
 __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type> &t, const Src<PREC> &s,
                                           Acc32<PREC, OP> &a, bool keep, const KernelParams &kp,
@@ -527,46 +575,14 @@ __device__ __forceinline__ void pair_eval(const Tgt<typename RealOf<PREC>::type>
             }
         }
     } else {  // OP_APPLY / OP_DIAG
-        // Since g_i2 = g_i1 + l_I T_I, T_I x (g_ia - g_jb) does not depend on a and T_J x (g_ia - g_jb)
-        // does not depend on b: two |T x d|^2 per tangent instead of four.  The chords come from d11
-        // by increments that mirror exactly between row I and row J (d12 = d11 - e_J,
-        // d21 = d11 + e_I, d22 = d11 + (e_I - e_J)), and the four trapezoid terms are summed as
-        // (11 + 22) + (12 + 21): every quantity of the pair is bitwise the same (up to sign) from
-        // row I and from row J, so W_IJ = W_JI and W0_IJ + W0_JI are exact and the FP32 operator
-        // stays exactly symmetric.
-        V3<R> dd[4];
-        chords<DF>(t, s, dd);
-        R tt;
-        V3<R> dp;
-        const R cI1 = perp2(dd[0], t.T, tt, dp), cI2 = perp2(dd[1], t.T, tt, dp);  // |T_I x d_1b|^2
-        const R cJ1 = perp2(dd[0], s.T, tt, dp), cJ2 = perp2(dd[2], s.T, tt, dp);  // |T_J x d_a1|^2
-        const R c2s[4] = {cI1 + cJ1, cI2 + cJ1, cI1 + cJ2, cI2 + cJ2};
-        R tw[4], tw0[4];
-#pragma unroll
-        for (int ab = 0; ab < 4; ++ab) {
-            const R d2 = dot3(dd[ab], dd[ab]);
-            if (ab == 0) d2_11 = d2;
-            R r2;
-            R rp = inv_pow<R, FAST, 1>(d2, pp, r2);
-            tw[ab] = rp;
-            tw0[ab] = c2s[ab] * (rp * r2 * r2);
-        }
-        R sw = (tw[0] + tw[3]) + (tw[1] + tw[2]);
-        R sw0 = (tw0[0] + tw0[3]) + (tw0[1] + tw0[2]);
-        R W = keep ? s.ell * sw : (R)0;
-        R W0 = keep ? s.ell * sw0 : (R)0;
+        R W, W0;
+        gram_weights<FAST, DF>(t, s, keep, pp, W, W0, d2_11);
         if constexpr (OP == OP_DIAG) {
             a.Sw += W;
             a.Sw0 += W0;
         } else {
             // (du_I - du_J) + (|T_I - T_J|^2 / 2) du_J  and  ub_I - ub_J, differences of double-floats
-            V3<R> dT = {t.T.x - s.T.x, t.T.y - s.T.y, t.T.z - s.T.z};
-            if constexpr (DF) {
-                dT.x += t.Tl.x - s.Tm.x;
-                dT.y += t.Tl.y - s.Tm.y;
-                dT.z += t.Tl.z - s.Tm.z;
-            }
-            R omt = (R)0.5 * dot3(dT, dT);
+            const R omt = tangent_gap<DF>(t, s);
             R ddx = (tu->dh.x - su->dh.x), ddy = (tu->dh.y - su->dh.y), ddz = (tu->dh.z - su->dh.z);
             R dbx = (tu->uh.x - su->uh.x), dby = (tu->uh.y - su->uh.y), dbz = (tu->uh.z - su->uh.z);
             // the differences of u always use the double-float parts in the mixed path: for smooth u

@@ -205,8 +205,8 @@ struct Ctx {
     int profile = 0;
     std::vector<cudaEvent_t> prof_pool;
     std::vector<std::pair<int, int>> prof_pending;  // (op, slot)
-    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
-    int64_t prof_n[6] = {0, 0, 0, 0, 0, 0};
+    double prof_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    int64_t prof_n[7] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 int prof_begin(Ctx &c, int op, cudaStream_t s);

@@ -26,8 +26,18 @@ def orc():
     return O
 
 
-@pytest.mark.parametrize("name,m", [("trefoil256", 32), ("knot600", 128), ("batch3", 32), ("knot1200", 256)])
-def test_balanced_apply_matches_oracle(torch, orc, name, m):
+# Coarse spaces of 8 hats and more are assembled by the A Z pass, smaller ones by probing (m = 4, 6);
+# in FP64 both agree with the oracle to ~1e-8.  In mixed precision the pass and the pair kernel work in
+# FP32 with double-float differences, and the coarse solve E^-1 amplifies the operator's rounding with
+# the coarse space's condition: measured 5e-6 (128 hats) and 3e-5 (256 hats) of the norm.  A wrong
+# index or sign anywhere in the pass moves the result by O(1).
+@pytest.mark.parametrize("name,m,prec,tol", [("trefoil256", 32, 0, 1e-6), ("knot600", 128, 0, 1e-6),
+                                             ("batch3", 32, 0, 1e-6), ("knot1200", 256, 0, 1e-6),
+                                             ("knot1200", 300, 0, 1e-6),
+                                             ("trefoil256", 4, 0, 1e-6), ("batch3", 6, 0, 1e-6),
+                                             ("knot600", 128, 2, 1e-4), ("knot1200", 256, 2, 1e-4),
+                                             ("batch3", 32, 2, 1e-4)])
+def test_balanced_apply_matches_oracle(torch, orc, name, m, prec, tol):
     from paper_2006_07859_gb300 import tpe
     if name == "trefoil256":
         c, indep = S.trefoil_256(), 0
@@ -37,7 +47,7 @@ def test_balanced_apply_matches_oracle(torch, orc, name, m):
         c, indep = S.single(S.fourier_knot(1200, 8, 5)), 0
     else:
         c, indep = S.batch_of_knots([64, 129, 256], 5, 700), 1
-    ctx = make_ctx(c, precision=0, precond=tpe.TP_PRECOND_TWOLEVEL_BALANCED, independent=indep, coarse_dim=m)
+    ctx = make_ctx(c, precision=prec, precond=tpe.TP_PRECOND_TWOLEVEL_BALANCED, independent=indep, coarse_dim=m)
     r = np.random.default_rng(6).normal(size=(c.n_vertices, 3))
     for k in range(c.n_curves):
         v0, v1 = c.vertex_offsets[k], c.vertex_offsets[k + 1]
@@ -50,7 +60,8 @@ def test_balanced_apply_matches_oracle(torch, orc, name, m):
         v0, v1 = c.vertex_offsets[k], c.vertex_offsets[k + 1]
         zo = orc.twolevel_balanced_apply(B + B0, n, SIG, min(m, n // 4), r[v0:v1])
         a, b = z[v0:v1] - z[v0:v1].mean(0), zo - zo.mean(0)
-        assert rel(a, b) <= 1e-6, k
+        print(name, m, prec, k, rel(a, b))
+        assert rel(a, b) <= tol, k
 
 
 def test_balanced_cuts_iterations(torch):

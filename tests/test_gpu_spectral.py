@@ -150,10 +150,13 @@ def test_rq_symbol_halves_iterations(torch):
 
 
 @pytest.mark.parametrize("name,m", [("trefoil256", 32), ("knot300", 32), ("batch3", 32), ("knot600", 128),
-                                    ("batch3", 128), ("knot1200", 256)])
+                                    ("batch3", 128), ("knot1200", 256), ("knot1200", 300), ("knot300", 6),
+                                    ("batch3", 4)])
 def test_twolevel_apply(torch, orc, name, m):
     """Two-level preconditioner (spectral RQ + coarse hats) against the oracle built from the dense
-    Gram matrix; up to 128 hats the factor works in shared memory, 256 (the largest) in global memory."""
+    Gram matrix.  Up to 128 hats one CTA factors the coarse matrix in shared memory; 256 and 300 hats
+    (255 and 299 rows: 8 and 10 tiles, ragged last tiles) take the tiled factorisation.  From 8 hats on
+    the columns A Z come from the coarse pair pass, below from probing applies."""
     from paper_2006_07859_gb300 import tpe
     if name == "trefoil256":
         c, indep = S.trefoil_256(), 0
