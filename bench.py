@@ -137,9 +137,11 @@ def solver_params(name, args):
     # projected curve meets the constraints for any solve accuracy).
     rtol = args.cg_rtol if args.cg_rtol is not None else (1e-4 if name == "knot262144" else 1e-6)
     maxit = args.cg_maxit if args.cg_maxit is not None else 2000
-    # the coarse space: 1,024 hats on the 262,144-vertex knot (measured: 47 CG iterations per step to the
-    # certified 1e-4 against 61 with 512 hats and ~100 with 128), 128 on 4,096 vertices
-    m = args.coarse_dim or (1024 if name == "knot262144" else 128)
+    # the coarse space: 8,192 hats (32 edges each) on the 262,144-vertex knot.  Measured CG iterations per
+    # step to the certified 1e-4 (gradient + projection solve) and seconds per step, set-up every two
+    # steps: 1,024 hats 47 + 18, 29.6 s; 2,048 37 + 13, 25.1 s; 4,096 27 + 10, 21.2 s; 8,192 21 + 7, 19.0 s.
+    # 128 hats on 4,096 vertices.
+    m = args.coarse_dim or (8192 if name == "knot262144" else 128)
     refresh = args.precond_refresh or max(1, args.steps)
     return dict(cg_rtol=rtol, cg_maxit=maxit, proj_cg_rtol=1e-3, cg_check_every=args.cg_check_every,
                 precond_refresh=refresh, coarse_dim=m)
@@ -278,15 +280,15 @@ def run_reference(args, rank, world):
 
 # Pass counts of one descent step, used only to extrapolate the CPU oracle (energy passes, differential
 # passes, Gram applies): the counts the GPU arm measured on the same workload and settings, so that both
-# arms are charged for the same passes.  262,144 edges (1,024 hats, gradient certified to 1e-4): 2 energy,
-# 1 differential and 85 applies per step (CG, projection, warm-start and residual applies, the 2
-# double-float residual checks counted as applies), plus 357 set-up applies (15 Rayleigh-quotient and
-# 341 coarse probes and the diagonal) once per timed window.  8 x 4096 knots (128 hats, certified 1e-6):
-# 2, 1 and 94 per step, plus 58 set-up applies per window.  The scene has no measured step and keeps a
-# nominal count.
-MEASURED_PASSES = {"knot262144": ({"energy": 2, "diff": 1, "apply": 85}, 357),
+# arms are charged for the same passes.  262,144 edges (8,192 hats, gradient certified to 1e-4): 2
+# energy, 1 differential and 37 applies per step (CG, projection, warm-start, correction and residual
+# applies, the 2 double-float residual checks counted as applies), plus 16 set-up applies (15
+# Rayleigh-quotient probes; the coarse pass visits every ordered pair once, one apply's worth) once per
+# timed window.  8 x 4096 knots (128 hats, certified 1e-6): 2, 1 and 104 per step, plus 16 set-up
+# applies per window.  The scene has no measured step and keeps a nominal count.
+MEASURED_PASSES = {"knot262144": ({"energy": 2, "diff": 1, "apply": 37}, 16),
                    "scene8x4096": ({"energy": 2, "diff": 1, "apply": 260}, 0),
-                   "knots8x4096": ({"energy": 2, "diff": 1, "apply": 94}, 58)}
+                   "knots8x4096": ({"energy": 2, "diff": 1, "apply": 104}, 16)}
 
 
 def passes_for(workload, steps):

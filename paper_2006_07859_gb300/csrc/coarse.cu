@@ -222,55 +222,97 @@ __global__ void k_az_store(int nV, int b, const CoarseCurve *__restrict__ cc, co
 }
 
 // out[v] = r[v] - sum_j AZ[j][v] w[j] (three components; each vertex reads its curve's column entries,
-// consecutive vertices read consecutive addresses of a column)
-__global__ void k_az_prolong_sub(int nV, const CoarseCurve *__restrict__ cc, const int *__restrict__ vcurve,
-                                 const double *__restrict__ AZ, const double *__restrict__ w,
-                                 const double *__restrict__ r, double *__restrict__ out)
+// consecutive vertices read consecutive addresses of a column).  The coefficients w of a chunk of
+// columns are staged in shared memory, and the column loop is unrolled so that every thread keeps
+// several independent loads in flight (the pass streams n (m - 1) doubles from memory).
+constexpr int kAzChunk = 512;
+__global__ void __launch_bounds__(256) k_az_prolong_sub(int nV, const CoarseCurve *__restrict__ cc,
+                                                        const int *__restrict__ vcurve, const double *__restrict__ AZ,
+                                                        const double *__restrict__ w, const double *__restrict__ r,
+                                                        double *__restrict__ out, int max_mm)
 {
+    __shared__ double sw[3 * kAzChunk];
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nV) return;
-    const CoarseCurve C = cc[vcurve[v]];
-    const int i = v - C.v0, mm = C.m - 1;
+    const int vc = min(v, nV - 1);
+    const CoarseCurve C = cc[vcurve[vc]];
+    const int i = vc - C.v0, mm = C.m - 1;
     const double *az = AZ + C.zoff + i;
+    // the block's vertices may span curves: each stages its own curve's coefficients chunk by chunk
+    const CoarseCurve C0 = cc[vcurve[min((int)(blockIdx.x * blockDim.x), nV - 1)]];
+    const bool uniform = C0.woff == C.woff;
     const double *wc = w + C.woff;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int j = 0; j < mm; ++j) {
-        const double a = az[(long long)j * C.n];
-        s0 += a * wc[3 * j];
-        s1 += a * wc[3 * j + 1];
-        s2 += a * wc[3 * j + 2];
+    for (int j0 = 0; j0 < max_mm; j0 += kAzChunk) {
+        const int cnt = min(kAzChunk, max(0, (C0.m - 1) - j0));
+        __syncthreads();
+        for (int t = threadIdx.x; t < 3 * cnt; t += blockDim.x) sw[t] = w[C0.woff + 3 * (long long)j0 + t];
+        __syncthreads();
+        const int hi = min(mm, j0 + kAzChunk);
+        if (uniform) {
+#pragma unroll 8
+            for (int j = j0; j < hi; ++j) {
+                const double a = az[(long long)j * C.n];
+                s0 += a * sw[3 * (j - j0)];
+                s1 += a * sw[3 * (j - j0) + 1];
+                s2 += a * sw[3 * (j - j0) + 2];
+            }
+        } else {
+            for (int j = j0; j < hi; ++j) {
+                const double a = az[(long long)j * C.n];
+                s0 += a * wc[3 * j];
+                s1 += a * wc[3 * j + 1];
+                s2 += a * wc[3 * j + 2];
+            }
+        }
     }
+    if (v >= nV) return;
     out[3 * v] = r[3 * v] - s0;
     out[3 * v + 1] = r[3 * v + 1] - s1;
     out[3 * v + 2] = r[3 * v + 2] - s2;
 }
 
-// w[j][q] = sum_i AZ[j][i] y[v0 + i][q]: one block per (curve, j), fixed-order tree sums
-__global__ void k_az_restrict(const CoarseCurve *__restrict__ cc, const double *__restrict__ AZ,
-                              const double *__restrict__ y, double *__restrict__ w)
+// w[j][q] = sum_i AZ[j][i] y[v0 + i][q]: one block per (curve, kAzCols consecutive columns), so that each
+// pass over y serves several columns; fixed-order sums (per thread, then warp shuffles, then warps)
+constexpr int kAzCols = 8;
+__global__ void __launch_bounds__(256) k_az_restrict(const CoarseCurve *__restrict__ cc, const double *__restrict__ AZ,
+                                                     const double *__restrict__ y, double *__restrict__ w)
 {
     const CoarseCurve C = cc[blockIdx.x];
-    const int j = blockIdx.y;
-    if (j >= C.m - 1) return;
-    const double *az = AZ + C.zoff + (long long)j * C.n;
-    __shared__ double sh[3][256];
-    double s[3] = {0, 0, 0};
+    const int j0 = blockIdx.y * kAzCols, mm = C.m - 1;
+    if (j0 >= mm) return;  // uniform per block
+    const int nc = min(kAzCols, mm - j0);
+    const double *az = AZ + C.zoff + (long long)j0 * C.n;
+    double s[kAzCols][3];
+#pragma unroll
+    for (int c = 0; c < kAzCols; ++c) s[c][0] = s[c][1] = s[c][2] = 0.0;
     for (int i = threadIdx.x; i < C.n; i += blockDim.x) {
-        const double a = az[i];
         const double *yy = y + 3 * (size_t)(C.v0 + i);
-        s[0] += a * yy[0];
-        s[1] += a * yy[1];
-        s[2] += a * yy[2];
+        const double y0 = yy[0], y1 = yy[1], y2 = yy[2];
+#pragma unroll
+        for (int c = 0; c < kAzCols; ++c)
+            if (c < nc) {
+                const double a = az[(long long)c * C.n + i];
+                s[c][0] += a * y0;
+                s[c][1] += a * y1;
+                s[c][2] += a * y2;
+            }
     }
-    for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] = s[q];
+    __shared__ double sh[8][kAzCols * 3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < kAzCols; ++c)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            double x = s[c][q];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) sh[warp][3 * c + q] = x;
+        }
     __syncthreads();
-    for (int wv = 128; wv > 0; wv >>= 1) {
-        if (threadIdx.x < wv)
-            for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + wv];
-        __syncthreads();
+    if (threadIdx.x < 3 * nc) {
+        double x = 0.0;
+        for (int k = 0; k < 8; ++k) x += sh[k][threadIdx.x];
+        w[C.woff + 3 * (long long)j0 + threadIdx.x] = x;
     }
-    if (threadIdx.x == 0)
-        for (int q = 0; q < 3; ++q) w[C.woff + 3 * j + q] = sh[q][0];
 }
 
 __global__ void k_coarse_sub(long long n, const double *__restrict__ a, double *__restrict__ b)
@@ -444,7 +486,7 @@ cudaError_t coarse_balanced_apply(Ctx &c, const double *r, double *z, cudaStream
     // c1 = E^-1 Z^T r,  r2 = r - (A Z) c1
     k_coarse_restrict<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(S.d_curves, r, S.d_w);
     k_coarse_solve<<<gsolve, 32 * kSolveRows, smem, s>>>(S.d_curves, S.d_L, S.d_w, S.d_w2);
-    k_az_prolong_sub<<<nb, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_AZ, S.d_w2, r, S.d_r2);
+    k_az_prolong_sub<<<nb, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_AZ, S.d_w2, r, S.d_r2, S.max_m - 1);
     c.launches += 3;
     // y = S r2 (into z)
     if (learned) {
@@ -454,7 +496,7 @@ cudaError_t coarse_balanced_apply(Ctx &c, const double *r, double *z, cudaStream
         TPE_CHECK(spectral_apply(c, S.d_r2, z, s, skip));
     }
     // c2 = E^-1 (A Z)^T y;  z = y + Z (c1 - c2)
-    k_az_restrict<<<dim3(c.nCurves, S.max_m), 256, 0, s>>>(S.d_curves, S.d_AZ, z, S.d_w3);
+    k_az_restrict<<<dim3(c.nCurves, (S.max_m - 1 + kAzCols - 1) / kAzCols), 256, 0, s>>>(S.d_curves, S.d_AZ, z, S.d_w3);
     k_coarse_solve<<<gsolve, 32 * kSolveRows, smem, s>>>(S.d_curves, S.d_L, S.d_w3, S.d_w4);
     const long long nw = (long long)S.curves.back().woff + 3LL * (S.curves.back().m - 1);
     k_coarse_sub<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(nw, S.d_w2, S.d_w4);
@@ -481,7 +523,7 @@ cudaError_t coarse_balanced_part(Ctx &c, int which, const double *v, double *out
     const int nb = (c.nV + 255) / 256;
     const long long nw = (long long)S.curves.back().woff + 3LL * (S.curves.back().m - 1);
     if (which == 2)
-        k_az_restrict<<<dim3(c.nCurves, S.max_m), 256, 0, s>>>(S.d_curves, S.d_AZ, v, S.d_w3);
+        k_az_restrict<<<dim3(c.nCurves, (S.max_m - 1 + kAzCols - 1) / kAzCols), 256, 0, s>>>(S.d_curves, S.d_AZ, v, S.d_w3);
     else
         k_coarse_restrict<<<dim3(c.nCurves, S.max_m), 128, 0, s>>>(S.d_curves, v, S.d_w3);
     k_coarse_solve<<<gsolve, 32 * kSolveRows, smem, s>>>(S.d_curves, S.d_L, S.d_w3, S.d_w4);
@@ -491,7 +533,7 @@ cudaError_t coarse_balanced_part(Ctx &c, int which, const double *v, double *out
         k_coarse_prolong<<<nb, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_w4, out);
         c.launches++;
     } else if (which == 1) {
-        k_az_prolong_sub<<<nb, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_AZ, S.d_w4, v, out);
+        k_az_prolong_sub<<<nb, 256, 0, s>>>(c.nV, S.d_curves, S.d_vcurve, S.d_AZ, S.d_w4, v, out, S.max_m - 1);
         c.launches++;
     } else {
         if (out != v) TPE_CHECK(cudaMemcpyAsync(out, v, sizeof(double) * 3 * c.nV, cudaMemcpyDeviceToDevice, s));
