@@ -41,6 +41,9 @@ import numpy as np  # noqa: E402
 # Canonical FP32 arithmetic per ordered disjoint pair interaction (one pair (I, J) with its 2x2
 # trapezoid), counted from the formulas each kernel evaluates (FMA = 2 FLOP); MUFU ops alongside.
 FLOP_PER_PAIR = {"energy": 122, "diff": 320, "apply": 255}
+# multi-field apply: the apply's weights (220) once per ordered pair plus 35 / 3 per scalar column, 12 columns
+MULTI_COLS = 12
+FLOP_PER_PAIR["apply_multi"] = 220 + 35 * MULTI_COLS // 3
 MUFU_PER_PAIR = {"energy": 8, "diff": 8, "apply": 8}
 FP32_LANES = 128   # FP32 FMA lanes per SM (Blackwell)
 L2_BYTES = 129 * 2 ** 20
@@ -202,13 +205,14 @@ class Clocks:
 # ------------------------------------------------------------------------------- CPU oracle timing
 
 def oracle_rates(curves, budget_s, alpha=2.0, beta=4.5):
-    """Seconds per ordered pair interaction of the FP64 oracle's energy rows, differential and Gram
-    apply, each timed on a bounded sample of target edges / vertices of the same workload."""
+    """Seconds per ordered pair interaction of the FP64 oracle's energy rows, differential, Gram apply
+    (3 columns) and 12-column Gram apply (the multi-field pass's width), each timed on a bounded sample
+    of target edges / vertices of the same workload."""
     from oracle import oracle as O
     O.build_library()
     nE = curves.n_edges
     rng = np.random.default_rng(42)
-    per = budget_s / 3.0
+    per = budget_s / 4.0
     out = {}
     sig = O.sigma_of(alpha, beta)
     # energy rows: each row visits ~nE pairs
@@ -225,7 +229,9 @@ def oracle_rates(curves, budget_s, alpha=2.0, beta=4.5):
     # differential / apply at vertices: each vertex visits 4 (nE - 3) ordered pairs (2 edges, 2 orders)
     for name, fn in (("diff", lambda v: O.differential_at(curves.gamma, curves.edges, v, alpha, beta)),
                      ("apply", lambda v: O.gram_apply_at(curves.gamma, curves.edges, sig,
-                                                         np.ones((curves.n_vertices, 3)), v))):
+                                                         np.ones((curves.n_vertices, 3)), v)),
+                     ("apply_multi", lambda v: O.gram_apply_at(curves.gamma, curves.edges, sig,
+                                                               np.ones((curves.n_vertices, MULTI_COLS)), v))):
         k = 1
         while True:
             v = rng.choice(curves.n_vertices, size=k, replace=False).astype(np.int32)
@@ -241,7 +247,7 @@ def oracle_rates(curves, budget_s, alpha=2.0, beta=4.5):
 
 def oracle_step_rate(rates, pairs, passes):
     """Oracle descent steps/s for the same pass counts per step (extrapolated from the samples)."""
-    t = sum(passes[k] * pairs * rates[k][0] for k in ("energy", "diff", "apply"))
+    t = sum(passes.get(k, 0.0) * pairs * rates[k][0] for k in ("energy", "diff", "apply", "apply_multi"))
     return 1.0 / t if t > 0 else None
 
 
@@ -279,26 +285,30 @@ def run_reference(args, rank, world):
 
 
 # Pass counts of one descent step, used only to extrapolate the CPU oracle (energy passes, differential
-# passes, Gram applies): the counts the GPU arm measured on the same workload and settings, so that both
-# arms are charged for the same passes.  262,144 edges (8,192 hats, gradient certified to 1e-4): 2
-# energy, 1 differential and 37 applies per step (CG, projection, warm-start, correction and residual
-# applies, the 2 double-float residual checks counted as applies), plus 16 set-up applies (15
-# Rayleigh-quotient probes; the coarse pass visits every ordered pair once, one apply's worth) once per
-# timed window.  8 x 4096 knots (128 hats, certified 1e-6): 2, 1 and 104 per step, plus 16 set-up
-# applies per window.  The scene has no measured step and keeps a nominal count.
-MEASURED_PASSES = {"knot262144": ({"energy": 2, "diff": 1, "apply": 37}, 16),
-                   "scene8x4096": ({"energy": 2, "diff": 1, "apply": 260}, 0),
-                   "knots8x4096": ({"energy": 2, "diff": 1, "apply": 104}, 16)}
+# passes, Gram applies, 12-column Gram applies): the counts the GPU arm measured on the same workload and
+# settings, so that both arms are charged for the same passes.  Per step, then per set-up (spread over
+# the timed window).  262,144 edges (8,192 hats, gradient certified to 1e-4): 2 energy, 1 differential
+# and 37 applies per step (CG, projection, warm-start, correction and residual applies, the 2
+# double-float residual checks counted as applies); per set-up one apply's worth for the coarse pass
+# (every ordered pair once) and 4 multi-field passes for the 15 Rayleigh-quotient probe fields.  8 x 4096
+# knots (128 hats, certified 1e-6): 2, 1 and 104 per step, the same set-up.  The scene has no measured
+# step and keeps a nominal count.
+MEASURED_PASSES = {"knot262144": ({"energy": 2, "diff": 1, "apply": 37}, {"apply": 1, "apply_multi": 4}),
+                   "scene8x4096": ({"energy": 2, "diff": 1, "apply": 260}, {}),
+                   "knots8x4096": ({"energy": 2, "diff": 1, "apply": 104}, {"apply": 1, "apply_multi": 4})}
 
 
 def passes_for(workload, steps):
     per, setup = MEASURED_PASSES[workload]
-    return dict(per, apply=per["apply"] + setup / max(1, steps))
+    out = dict(per)
+    for k, v in setup.items():
+        out[k] = out.get(k, 0.0) + v / max(1, steps)
+    return out
 
 
 def pass_throughput_262k(tpe, torch):
-    """Pair interactions/s of the energy, differential and apply passes on the 262,144-edge knot
-    (mixed precision), timed with CUDA events; also returns the per-launch apply time."""
+    """Pair interactions/s of the energy, differential, apply and 4-field apply passes on the
+    262,144-edge knot (mixed precision), timed with CUDA events; also returns the per-launch times."""
     import synth as S
     c = S.knot_262144()
     ctx = tpe.Context.from_curves(c, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_JACOBI)
@@ -306,19 +316,26 @@ def pass_throughput_262k(tpe, torch):
     u = torch.as_tensor(np.random.default_rng(1).normal(size=(c.n_vertices, 3))).cuda()
     tuned = tpe.tp_autotune(ctx, g)
     tpe.tp_energy(ctx, g)
+    U4 = torch.as_tensor(np.random.default_rng(2).normal(size=(4, c.n_vertices, 3))).cuda()
+    tpe.sobolev_apply_multi(ctx, g, U4)
     torch.cuda.synchronize()
     ctx.profile(True)
     tpe.tp_energy(ctx, g)
     tpe.tp_differential(ctx, g)
     tpe.sobolev_apply(ctx, g, u)
     tpe.sobolev_apply(ctx, g, u)
+    tpe.sobolev_apply_multi(ctx, g, U4)
+    tpe.sobolev_apply_multi(ctx, g, U4)
     torch.cuda.synchronize()
     pairs = ctx.pairs_per_pass()
     out = {"pairs_per_pass": pairs, "autotune": tuned["tpt"], "autotune_ms": tuned["ms"]}
-    for i, op in enumerate(["energy", "diff", "apply"]):
+    for i, op in [(0, "energy"), (1, "diff"), (2, "apply"), (7, "apply_multi")]:
         ms, n = ctx.profile_read(i)
         out[op] = {"pairs_per_s": pairs * n / (ms / 1e3), "ms_per_launch": ms / n,
                    "tflops": pairs * FLOP_PER_PAIR[op] * n / (ms / 1e3) / 1e12}
+    # scalar columns served per second: 3 per apply pass, 12 per multi-field pass
+    out["columns_x_pairs_per_s"] = {"apply": 3 * out["apply"]["pairs_per_s"],
+                                    "apply_multi": MULTI_COLS * out["apply_multi"]["pairs_per_s"]}
     ctx.profile(False)
     ctx.close()
     return out
@@ -674,7 +691,7 @@ def run_ours(args, rank, world, local_rank):
         total_e2e += ev[0].elapsed_time(ev[3]) / 1e3
     clk = clocks.stop() if clocks else None
     launches = ctx.launch_count() - l0
-    ops = ["energy", "diff", "apply", "diag", "apply_cg", "apply_accurate", "coarse_az"]
+    ops = ["energy", "diff", "apply", "diag", "apply_cg", "apply_accurate", "coarse_az", "apply_multi"]
     prof = {op: ctx.profile_read(i) for i, op in enumerate(ops)}
     ctx.profile(False)
     tmax = max_over_ranks(total, dist, "cuda")
@@ -701,6 +718,7 @@ def run_ours(args, rank, world, local_rank):
     passes["apply"] += prof["apply_cg"][1] / args.steps   # every apply launch (the CG ones may skip converged curves)
     passes["apply_accurate"] = prof["apply_accurate"][1] / args.steps
     passes["coarse_az"] = prof["coarse_az"][1] / args.steps
+    passes["apply_multi"] = prof["apply_multi"][1] / args.steps
     pps = {k: (pairs * prof[k][1] / (prof[k][0] / 1e3) if prof[k][1] else None) for k in prof}
     if not single:
         pps["apply_cg"] = None   # CG applies skip converged problems: their pair count is not a full pass
@@ -715,6 +733,7 @@ def run_ours(args, rank, world, local_rank):
         rates, cores = oracle_rates(curves, args.cpu_seconds)
         # the coarse A Z pass visits every ordered pair once with apply-like work: one apply's worth
         cpu_passes = dict(passes, apply=passes["apply"] + passes["apply_accurate"] + passes["coarse_az"])
+        # (apply_multi: the oracle's 12-column rate, measured on the same sample)
         cpu_val = oracle_step_rate(rates, pairs, cpu_passes)
     kernel_share = {k: prof[k][0] / 1e3 / total for k in prof}
     sym_apply = tuned["tpt"].get("apply_symmetric", 0)
@@ -729,9 +748,10 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": dict(cfg, alpha=2.0, beta=4.5, precision="mixed",
                        precond=f"{pname} (spectral RQ + {sp['coarse_dim']} coarse hats)", **sp,
-                       cg_rtol_meaning="true relative residual, double-float operator, residual refinement"
-                       + ("; 1e-4 at 262,144 edges: the operator's FP64-class evaluation floor there is ~2e-5"
-                          if args.workload == "knot262144" else ""),
+                       cg_rtol_meaning="true relative residual: the double-float operator's residual of the CG "
+                       "solution, updated by the working-precision product of each refinement correction"
+                       + ("; 1e-4 at 262,144 edges: the operator's FP64-class evaluation floor there is ~2e-5, "
+                          "and residuals reported below it are not resolved" if args.workload == "knot262144" else ""),
                        l2="flushed between timed steps (256 MiB write)",
                        parallelism=f"data-parallel shards x{world} (disjoint problems per rank, no collective)"),
         "autotune": tuned,

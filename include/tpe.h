@@ -222,6 +222,16 @@ TPE_API tp_status tp_differential(tp_ctx *ctx, const double *gamma, double *dE, 
 /* Au = A-bar u with A = B + B0 of the curve gamma (Secs. 5.2.2-5.2.3, Eq. 19): u, Au device [nV][3]. */
 TPE_API tp_status sobolev_apply(tp_ctx *ctx, const double *gamma, const double *u, double *Au, tp_stream stream);
 
+/* AU_f = A-bar U_f for m vector fields at once (Secs. 5.2.2-5.2.3, Eq. 19 per field): U, AU device
+ * double [m][nV][3] (field-major: field f starts at U + 3 nV f); m >= 0 (m = 0 does nothing).  Every
+ * pair's Gram weights and tangent gap (about 220 of the 255 canonical FLOP of an apply) are computed
+ * once per pass and applied to 4 fields (12 scalar columns); the per-column arithmetic is
+ * sobolev_apply's (same precision mode).  Builds its work list, per-field records and partial sums at
+ * the first call (about 4 nE records and slots x nE x 24 doubles).  U and AU must not overlap.
+ * Errors: TP_ERR_INVALID_ARG (NULL pointers with m > 0, m < 0), TP_ERR_CUDA. */
+TPE_API tp_status sobolev_apply_multi(tp_ctx *ctx, const double *gamma, const double *U, double *AU, int m,
+                                      tp_stream stream);
+
 /* The same product A-bar u in double-float arithmetic (every pair term as an unevaluated sum of two
  * floats, ~48 bits, from the FP64 positions, tangents, lengths and u): the accurate operator with which
  * the solves of TP_FP32 and TP_MIXED contexts judge their true residuals (FP64 contexts run their
@@ -337,7 +347,8 @@ TPE_API int64_t tp_pairs_per_pass(const tp_ctx *ctx);
  * enable = 1 starts (and clears) the record; op: 0 energy, 1 differential, 2 apply (full passes),
  * 3 diag, 4 apply inside CG solves (items of already converged problems skipped), 5 double-float
  * apply (tp_sobolev_apply_accurate and the refined solves' residuals), 6 the coarse-space pass that
- * assembles A Z for the two-level preconditioners.
+ * assembles A Z for the two-level preconditioners, 7 the multi-field apply (sobolev_apply_multi and
+ * the Rayleigh-quotient probes of the spectral set-up), one launch per 4 fields.
  * tp_profile_read synchronises the recorded events and returns the summed device time (ms) and
  * the number of launches of that pair kernel since profiling was enabled. */
 TPE_API tp_status tp_profile(tp_ctx *ctx, int enable);

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtpe.so")
-SOURCES = ["pairs.cu", "solver.cu", "spectral.cu", "api.cu", "peaks.cu", "static_energy.cu", "coarse.cu", "gnn.cu", "pairs_sym.cu", "edges.cu", "ccd.cu", "penalties.cu", "pins.cu", "pairs_df.cu", "coarse_az.cu", "coarse_factor.cu"]
+SOURCES = ["pairs.cu", "solver.cu", "spectral.cu", "api.cu", "peaks.cu", "static_energy.cu", "coarse.cu", "gnn.cu", "pairs_sym.cu", "edges.cu", "ccd.cu", "penalties.cu", "pins.cu", "pairs_df.cu", "coarse_az.cu", "coarse_factor.cu", "pairs_multi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

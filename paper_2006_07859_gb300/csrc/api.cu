@@ -235,7 +235,7 @@ tp_status tp_profile(tp_ctx *ctx, int enable)
     if (!ctx) return TP_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     prof_harvest(c);
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < 8; ++k) {
         c.prof_ms[k] = 0.0;
         c.prof_n[k] = 0;
     }
@@ -245,7 +245,7 @@ tp_status tp_profile(tp_ctx *ctx, int enable)
 
 tp_status tp_profile_read(tp_ctx *ctx, int op, double *total_ms, int64_t *launches)
 {
-    if (!ctx || op < 0 || op > 6) return TP_ERR_INVALID_ARG;
+    if (!ctx || op < 0 || op > 7) return TP_ERR_INVALID_ARG;
     Ctx &c = ctx->c;
     prof_harvest(c);
     if (total_ms) *total_ms = c.prof_ms[op];
@@ -269,6 +269,7 @@ void tp_destroy(tp_ctx *ctx)
     ccd_free(c);
     penalties_free(c);
     pins_free(c);
+    multi_free(c);
     void *ptrs[] = {c.d_esum, c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_voff,
                     c.plan_energy.d_items, c.plan_diff.d_items, c.plan_apply.d_items, c.plan_energy.d_eslots,
                     c.plan_diff.d_eslots, c.plan_apply.d_eslots, c.d_counter, c.d_recF, c.d_recF2, c.d_recLo,
@@ -276,7 +277,7 @@ void tp_destroy(tp_ctx *ctx)
                     c.d_xw[1], c.d_urecF, c.d_urecD, c.d_part, c.d_rows, c.d_x0L0, c.d_Cv, c.d_G, c.d_Ginv,
                     c.d_red, c.d_phi, c.d_y, c.d_r, c.d_z, c.d_p, c.d_q, c.d_diag, c.d_t1, c.d_t2, c.d_t3, c.d_t4,
                     c.d_t5, c.d_t6, c.d_gam, c.d_best, c.d_yw0, c.d_yw1, c.d_E, c.d_scal, c.d_cg, c.d_err,
-                    c.d_ell_lo[0], c.d_ell_lo[1], c.plan_df.d_items, c.plan_df.d_eslots, c.d_rf, c.d_ef};
+                    c.d_ell_lo[0], c.d_ell_lo[1], c.plan_df.d_items, c.plan_df.d_eslots, c.d_rf, c.d_ef, c.d_rs};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     prof_harvest(c);
@@ -424,8 +425,8 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
         CK(dalloc(&c.d_ell_lo[0], nE));
         CK(dalloc(&c.d_ell_lo[1], nE));
     }
-    CK(dalloc(&c.d_counter, 8));
-    CK(cudaMemset(c.d_counter, 0, sizeof(int) * 8));
+    CK(dalloc(&c.d_counter, 16));
+    CK(cudaMemset(c.d_counter, 0, sizeof(int) * 16));
     set_kernel_params(c);
     make_plans(c);
     CK(cudaGetLastError());
@@ -441,7 +442,7 @@ tp_status tp_create(tp_ctx **out, int nV, int nE, const int32_t *edges_host, int
     CK(dalloc(&c.d_red, 16 * (size_t)c.nProb));
     CK(dalloc(&c.d_phi, 4 * (size_t)c.nProb));
     double **vecs[] = {&c.d_y, &c.d_r, &c.d_z, &c.d_p, &c.d_q, &c.d_t1, &c.d_t2, &c.d_t3, &c.d_t4, &c.d_t5, &c.d_t6,
-                       &c.d_gam, &c.d_best, &c.d_yw0, &c.d_yw1, &c.d_rf, &c.d_ef};
+                       &c.d_gam, &c.d_best, &c.d_yw0, &c.d_yw1, &c.d_rf, &c.d_ef, &c.d_rs};
     for (double **v : vecs) CK(dalloc(v, 3 * (size_t)nV));
     CK(cudaMemset(c.d_z, 0, sizeof(double) * 3 * nV));
     CK(dalloc(&c.d_diag, nV));
@@ -548,6 +549,17 @@ tp_status sobolev_apply(tp_ctx *ctx, const double *gamma, const double *u, doubl
     tp_status st = records(ctx, gamma, 0, s);
     if (st) return st;
     CK(pair_apply(ctx->c, gamma, 0, u, Au, s));
+    return TP_OK;
+}
+
+tp_status sobolev_apply_multi(tp_ctx *ctx, const double *gamma, const double *U, double *AU, int m, tp_stream stream)
+{
+    if (!ctx || !gamma || m < 0 || (m > 0 && (!U || !AU))) return TP_ERR_INVALID_ARG;
+    if (m == 0) return TP_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    tp_status st = records(ctx, gamma, 0, s);
+    if (st) return st;
+    CK(pair_apply_multi(ctx->c, gamma, 0, U, AU, m, s));
     return TP_OK;
 }
 

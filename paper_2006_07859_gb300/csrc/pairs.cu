@@ -827,6 +827,14 @@ cudaError_t build_urecs(Ctx &c, const double *u, int which, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t build_urecs_into(Ctx &c, const double *u, int which, URecF *uf, URecD *ud, cudaStream_t s)
+{
+    if (c.nE == 0) return cudaSuccess;
+    k_urecs<<<(c.nE + 255) / 256, 256, 0, s>>>(c.nE, u, c.d_edges, c.d_ellw[which], uf, ud);
+    c.launches++;
+    return cudaGetLastError();
+}
+
 template <int OP>
 static cudaError_t run_pairs(Ctx &c, int which, const double *gamma, const double *u, cudaStream_t s)
 {

@@ -1062,6 +1062,7 @@ static cudaError_t pcg_run(Ctx &c, const double *gamma_geom, int which, const do
 // not see.  Looser solves (the constraint projections at 1e-3) keep the working-precision residual.
 constexpr double kRefineBelow = 5e-4;
 constexpr int kRefineMax = 4;        // correction solves at most
+constexpr double kUpdateBelow = 1e-2; // residuals below this are updated with the working-precision A-bar e
 constexpr double kCorrectionTol = 1e-2;
 
 cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *rhs, double *x, double rtol,
@@ -1078,8 +1079,13 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
     int rounds = 0;
     if (refine) {
         // Iterative refinement: the residual r = P (rhs - A-bar_acc x) of the accurate operator is solved
-        // for a correction e with the working-precision PCG (to kCorrectionTol relative), x += e, and r
-        // is formed again, until every problem's true relative residual is within rtol.
+        // for a correction e with the working-precision PCG (to kCorrectionTol relative), x += e, and the
+        // residual of the new x follows, until every problem's true relative residual is within rtol.
+        // The new residual is r - P A-bar_w e with the working-precision product when every residual
+        // was below kUpdateBelow: A-bar_w's relative error on e (its rounding floor, ~3e-4 on smooth
+        // vectors at 262,144 edges) then multiplies |A-bar e| ~ |r| <= kUpdateBelow |P rhs|, and adds at
+        // most ~3e-6 |P rhs| against the accurate evaluation of A-bar x it replaces.  Otherwise the
+        // accurate operator forms it again.
         const int nb = (c.nV + 255) / 256;
         int *keep = reinterpret_cast<int *>(c.d_scal + 64 + 14 * (size_t)c.nProb);  // nProb ints
         double *rr_d = c.d_scal + 64 + 10 * (size_t)c.nProb;
@@ -1096,8 +1102,12 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
             }
             if (!any) break;
             prev = rr;
+            double mx = 0.0;
+            for (int q = 0; q < c.nProb; ++q) mx = std::max(mx, rr[q]);
+            const bool update = mx <= kUpdateBelow;
             TPE_CHECK(cudaMemcpyAsync(keep, need.data(), sizeof(int) * c.nProb, cudaMemcpyHostToDevice, s));
             TPE_CHECK(cudaMemcpyAsync(c.d_rf, c.d_r, sizeof(double) * 3 * c.nV, cudaMemcpyDeviceToDevice, s));
+            if (update) TPE_CHECK(cudaMemcpyAsync(c.d_rs, c.d_r, sizeof(double) * 3 * c.nV, cudaMemcpyDeviceToDevice, s));
             k_zero_problems<<<nb, 256, 0, s>>>(c.nV, c.d_vprob, keep, c.d_rf);
             c.launches++;
             PcgOut oc;
@@ -1109,10 +1119,17 @@ cudaError_t cg_solve(Ctx &c, const double *gamma_geom, int which, const double *
                     it[q] += oc.iters[q];
                     bd[q] |= oc.bd[q];
                 }
-            // r = P (rhs - A-bar_acc x), relative to the first solve's |P rhs|
-            TPE_CHECK(pair_apply_acc(c, gamma_geom, which, x, c.d_q, s));
-            TPE_CHECK(vec_axpby(c, 1.0, rhs, -1.0, c.d_q, c.d_r, s));
-            TPE_CHECK(projector(c, proj_mode, c.d_r, s, nullptr));
+            // r = P (rhs - A-bar_acc x), relative to the first solve's |P rhs|: updated by the correction's
+            // working-precision product, or formed again with the accurate operator
+            if (update) {
+                TPE_CHECK(pair_apply(c, gamma_geom, which, c.d_ef, c.d_q, s));
+                TPE_CHECK(projector(c, proj_mode, c.d_q, s, nullptr));
+                TPE_CHECK(vec_axpby(c, 1.0, c.d_rs, -1.0, c.d_q, c.d_r, s));
+            } else {
+                TPE_CHECK(pair_apply_acc(c, gamma_geom, which, x, c.d_q, s));
+                TPE_CHECK(vec_axpby(c, 1.0, rhs, -1.0, c.d_q, c.d_r, s));
+                TPE_CHECK(projector(c, proj_mode, c.d_r, s, nullptr));
+            }
             k_relres<<<st.v_n, kRedThreads, 0, s>>>(vargs(c, 3), c.d_r, c.d_cg, rr_d, bn2, nullptr);
             c.launches++;
             TPE_CHECK(cudaMemcpyAsync(rr.data(), rr_d, sizeof(double) * c.nProb, cudaMemcpyDeviceToHost, s));

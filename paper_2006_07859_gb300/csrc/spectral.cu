@@ -68,6 +68,7 @@ struct tpe::SpecState {
     double *d_sym_rq = nullptr;  // [nV]
     int *d_klist = nullptr;      // [nCurves][kMaxRQ] sampled frequencies
     double *d_rq = nullptr;      // [nCurves][2 kMaxRQ] Rayleigh numerators (cos, sin)
+    double *d_probe = nullptr;   // [2][batches][nV][3] the probe fields and their products (set-up scratch)
     int *d_vcurve = nullptr;     // [nV] curve of each vertex
     int max_nk = 0;
     int rq_ready = 0;
@@ -636,7 +637,7 @@ void spectral_free(Ctx &c)
     if (!c.spec) return;
     SpecState &S = *c.spec;
     void *p[] = {S.d_curves, S.d_small_idx, S.d_sym, S.d_tw, S.d_chirp, S.d_bhat, S.d_buf0, S.d_buf1, S.d_dinv,
-                 S.d_sym_rq, S.d_klist, S.d_rq, S.d_vcurve, S.d_ilam, S.d_cluster_idx};
+                 S.d_sym_rq, S.d_klist, S.d_rq, S.d_vcurve, S.d_ilam, S.d_cluster_idx, S.d_probe};
     for (void *q : p)
         if (q) cudaFree(q);
     delete c.spec;
@@ -710,7 +711,7 @@ cudaError_t spectral_apply_ex(Ctx &c, const double *r, double *z, cudaStream_t s
 //
 // T. Chan's optimal circulant approximation of S = D^-1/2 A D^-1/2 has the eigenvalues
 // lambda_opt(k) = f_k^H S f_k / n (the Rayleigh quotients of S on the Fourier modes).  They are
-// sampled at <= 24 frequencies per curve with the apply kernel (cos and sin probes scaled by
+// sampled at <= 24 frequencies per curve with the multi-field apply (cos and sin probes scaled by
 // D^-1/2), the ratio rho(k) = lambda_opt(k) / lambda_ngon(k) is interpolated linearly in
 // (log k, log rho), and the preconditioner divides by lambda_ngon(k) rho(k).  On a regular polygon
 // rho = 1.  On knotted curves the low modes are far stiffer than the polygon's (rho up to ~1e4 at
@@ -804,18 +805,24 @@ __global__ void k_rq_symbol(const SpecCurve *__restrict__ curves, const int *__r
 }
 
 // Builds the corrected symbols of the curve `gamma_geom` (geometry slot `which`); needs diag(A) in
-// c.d_diag.  Uses c.d_y and c.d_q as scratch (free outside a CG solve).
+// c.d_diag.  The probe fields and their products live in a scratch of 2 x batches x 3 nV doubles.
 cudaError_t spectral_rq_setup(Ctx &c, const double *gamma_geom, int which, cudaStream_t s)
 {
     if (!c.spec) return cudaErrorNotSupported;
     SpecState &S = *c.spec;
     const int nb = (c.nV + 255) / 256;
     const int nbatch = (2 * S.max_nk + 2) / 3;
+    // every batch of three probes is one vector field: one multi-field apply serves all of them
+    const size_t nv3 = 3 * (size_t)c.nV;
+    if (!S.d_probe) TPE_CHECK(cudaMalloc(&S.d_probe, sizeof(double) * 2 * std::max(1, nbatch) * nv3));
+    double *Y = S.d_probe, *AY = S.d_probe + (size_t)nbatch * nv3;
     for (int b = 0; b < nbatch; ++b) {
-        k_rq_probe<<<nb, 256, 0, s>>>(c.nV, b, S.d_curves, S.d_vcurve, S.d_klist, c.d_diag, c.d_y);
+        k_rq_probe<<<nb, 256, 0, s>>>(c.nV, b, S.d_curves, S.d_vcurve, S.d_klist, c.d_diag, Y + b * nv3);
         c.launches++;
-        TPE_CHECK(pair_apply(c, gamma_geom, which, c.d_y, c.d_q, s));
-        k_rq_reduce<<<c.nCurves, 256, 0, s>>>(b, S.d_curves, c.d_y, c.d_q, S.d_rq);
+    }
+    TPE_CHECK(pair_apply_multi(c, gamma_geom, which, Y, AY, nbatch, s));
+    for (int b = 0; b < nbatch; ++b) {
+        k_rq_reduce<<<c.nCurves, 256, 0, s>>>(b, S.d_curves, Y + b * nv3, AY + b * nv3, S.d_rq);
         c.launches++;
     }
     k_rq_symbol<<<c.nCurves, 256, 0, s>>>(S.d_curves, S.d_klist, S.d_rq, S.d_sym, S.d_sym_rq);

@@ -133,7 +133,12 @@ struct Ctx {
     Plan plan_sym_d;         // symmetric differential (pairs_sym.cu)
     int diff_sym = 0;        // > 0: the differential runs the symmetric pass
     Plan plan_df;            // double-float apply (pairs_df.cu), built at its first use
-    int *d_counter = nullptr;  // persistent-queue counters [8]
+    Plan plan_multi;         // multi-field apply (pairs_multi.cu), built at its first use
+    URecF *d_urecMF = nullptr;  // multi-field apply: per-edge records of kMultiG fields (FP32 contexts)
+    URecD *d_urecMD = nullptr;  // the same in FP64 contexts
+    double *d_partM = nullptr;  // multi-field apply: partial sums [slot][nE][6 kMultiG]
+    int multi_ready = 0;
+    int *d_counter = nullptr;  // persistent-queue counters [16]
     // edge records
     RecF *d_recF = nullptr, *d_recF2 = nullptr;
     RecLo *d_recLo = nullptr, *d_recLo2 = nullptr;
@@ -195,6 +200,7 @@ struct Ctx {
     std::vector<double> last_rr;   // per problem: true relative residual of the last CG solve
     int last_refinements = 0;      // correction solves of the last CG solve (iterative refinement)
     double *d_rf = nullptr, *d_ef = nullptr;  // [nV][3] refinement residual and correction
+    double *d_rs = nullptr;                   // [nV][3] refinement: the accurate residual before a correction
     std::vector<int> last_iters;   // per problem: its iterations
     // (residual, iterate) capture of a CG solve: every `every` iterations r -> R[n], y -> Y[n]
     struct Harvest {
@@ -205,8 +211,8 @@ struct Ctx {
     int profile = 0;
     std::vector<cudaEvent_t> prof_pool;
     std::vector<std::pair<int, int>> prof_pending;  // (op, slot)
-    double prof_ms[7] = {0, 0, 0, 0, 0, 0, 0};
-    int64_t prof_n[7] = {0, 0, 0, 0, 0, 0, 0};
+    double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t prof_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 int prof_begin(Ctx &c, int op, cudaStream_t s);
@@ -218,12 +224,19 @@ void graphs_reset(Ctx &c);  // drop the captured blocks (their launches baked in
 // ------------------------------------------------------------------ pair passes (pairs.cu)
 cudaError_t build_records(Ctx &c, const double *gamma, int which, cudaStream_t s);
 cudaError_t build_urecs(Ctx &c, const double *u, int which_geom, cudaStream_t s);
+// per-edge records of u into the given arrays (one of them NULL) instead of the context's
+cudaError_t build_urecs_into(Ctx &c, const double *u, int which_geom, URecF *uf, URecD *ud, cudaStream_t s);
 cudaError_t pair_energy(Ctx &c, const double *gamma, int which, double *rows_out, double *E_out, cudaStream_t s);
 cudaError_t pair_diff(Ctx &c, const double *gamma, int which, double *dE, cudaStream_t s);
 cudaError_t pair_apply(Ctx &c, const double *gamma_geom, int which, const double *u, double *Au, cudaStream_t s);
 cudaError_t pair_diag(Ctx &c, const double *gamma_geom, int which, double *diag, cudaStream_t s);
 // (pairs_df.cu) the apply in double-float arithmetic: the accurate operator of residual checks
 cudaError_t pair_apply_acc(Ctx &c, const double *gamma_geom, int which, const double *u, double *Au, cudaStream_t s);
+// AU_f = A-bar U_f for m vector fields ([m][nV][3] each), kMultiG fields per pair pass
+constexpr int kMultiG = 4;
+cudaError_t pair_apply_multi(Ctx &c, const double *gamma_geom, int which, const double *U, double *AU, int m,
+                             cudaStream_t s);
+void multi_free(Ctx &c);
 void plan_pass(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy);
 void sym_plan_items(Ctx &c, Ctx::Plan &pl, int tpt, int occupancy);  // (pairs_sym.cu) items (b, c >= b)
 cudaError_t gather_apply(Ctx &c, const Ctx::Plan &pl, double *Au, cudaStream_t s);

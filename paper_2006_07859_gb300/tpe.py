@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ER
                 8: "TP_ERR_PROJECTION", 9: "TP_ERR_OOM", 10: "TP_ERR_UNSUPPORTED"}
 
 EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp_num_problems", "tp_set_params",
-            "tp_energy", "tp_differential", "sobolev_apply", "sobolev_apply_accurate", "tp_gram_diagonal", "tp_precond_apply",
+            "tp_energy", "tp_differential", "sobolev_apply", "sobolev_apply_accurate", "sobolev_apply_multi", "tp_gram_diagonal", "tp_precond_apply",
             "tp_spectral_symbol", "tp_set_constraints_from", "tp_constraints", "sobolev_gradient", "descent_step",
             "tp_launch_count", "tp_pairs_per_pass", "tp_profile", "tp_profile_read", "tp_measure_peaks", "tp_energy_static",
             "tp_spectral_symbols", "tp_gnn_num_params", "tp_gnn_set_params", "tp_gnn_get_params", "tp_gnn_bind",
@@ -100,6 +100,7 @@ def library() -> ctypes.CDLL:
         L.tp_differential.argtypes = [vp, vp, vp, vp, vp]
         L.sobolev_apply.argtypes = [vp, vp, vp, vp, vp]
         L.sobolev_apply_accurate.argtypes = [vp, vp, vp, vp, vp]
+        L.sobolev_apply_multi.argtypes = [vp, vp, vp, vp, i, vp]
         L.tp_gram_diagonal.argtypes = [vp, vp, vp, vp]
         L.tp_precond_apply.argtypes = [vp, vp, vp, vp, vp]
         L.tp_spectral_symbol.argtypes = [vp, i, vp, vp]
@@ -263,6 +264,14 @@ def sobolev_apply(ctx: Context, gamma, u, Au=None):
     Au = _new((ctx.n_vertices, 3)) if Au is None else Au
     ctx._check(library().sobolev_apply(ctx.handle, _ptr(gamma), _ptr(u), _ptr(Au), _stream()))
     return Au
+
+
+def sobolev_apply_multi(ctx: Context, gamma, U, AU=None):
+    """AU[f] = A-bar U[f] for the m vector fields of U, a CUDA float64 tensor [m, nV, 3]."""
+    m = int(U.shape[0])
+    AU = _new((m, ctx.n_vertices, 3)) if AU is None else AU
+    ctx._check(library().sobolev_apply_multi(ctx.handle, _ptr(gamma), _ptr(U), _ptr(AU), m, _stream()))
+    return AU
 
 
 def sobolev_apply_accurate(ctx: Context, gamma, u, Au=None):
