@@ -1,7 +1,7 @@
 // Learned preconditioner term (TP_PRECOND_LEARNED; this library's extension, not in the paper).
 //
 // A 3-layer network on the edge graph of the closed curves (width 64, BF16 weights, FP32
-// accumulation) maps local geometry to three values (a_I, b_I, c_I) per edge that shape an SPD
+// accumulation; the 64-wide layers on the tensor cores) maps local geometry to three values (a_I, b_I, c_I) per edge that shape an SPD
 // preconditioner around the two-level one:
 //   M^-1 r = W S W r + Z (Z^T A Z)^-1 Z^T r + G r,
 //   W = D^-1/2 diag(exp(c_v)), c_v = mean of c over the two edges at vertex v, S the circulant of the
@@ -152,48 +152,153 @@ __global__ void __launch_bounds__(128) k_gnn_l1(int nE, const float *__restrict_
     }
 }
 
-// zout = Ws relu(zin) + Wn avg(relu(zin[I-1]), relu(zin[I+1])) + b (one thread per edge)
-__global__ void __launch_bounds__(128) k_gnn_lmp(int nE, const int *__restrict__ eprev, const int *__restrict__ enext,
-                                                 const float *__restrict__ zin, const __nv_bfloat16 *__restrict__ w,
-                                                 int oWs, int oWn, int ob, float *__restrict__ zout)
+// ---------------------------------------------------------------------------------- tensor-core layers
+//
+// The two 64-wide contractions per layer run on the tensor cores with mma.sync m16n8k16 (BF16 operands,
+// FP32 accumulation): the forward message-passing layer z = [Ws | Wn] [h; m] + b (K = 128, N = 64) and
+// its data gradient [dh | dm] = dz [Ws | Wn] (K = 64, N = 128).  The weights are BF16 already; each FP32
+// activation is split into three BF16 terms (x = x1 + x2 + x3 to ~2^-24), so the products carry the
+// FP32 activations' digits and the layers compute what the CUDA-core form computes, up to the order of
+// the FP32 sums.  A block of 64 threads (two warps of 16 rows) takes 32 edges; the operand tiles sit in
+// shared memory with padded rows.
+constexpr int kTcRows = 32;
+
+__device__ __forceinline__ uint32_t bf_pack(__nv_bfloat16 lo, __nv_bfloat16 hi)
 {
-    __shared__ float Ws[kH * kH], Wn[kH * kH], b[kH];
-    for (int t = threadIdx.x; t < kH * kH; t += blockDim.x) {
-        Ws[t] = bf(w, oWs + t);
-        Wn[t] = bf(w, oWn + t);
-    }
-    for (int t = threadIdx.x; t < kH; t += blockDim.x) b[t] = bf(w, ob + t);
-    __syncthreads();
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nE) return;
-    const float4 *hs = reinterpret_cast<const float4 *>(zin + (size_t)I * kH);
-    const float4 *hp = reinterpret_cast<const float4 *>(zin + (size_t)eprev[I] * kH);
-    const float4 *hn = reinterpret_cast<const float4 *>(zin + (size_t)enext[I] * kH);
-    float h[kH], m[kH];
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// x = h + m + l in BF16 terms (each the rounding of the remainder)
+__device__ __forceinline__ void bf_split3(float x, __nv_bfloat16 (&t)[3])
+{
+    t[0] = __float2bfloat16_rn(x);
+    float r = x - __bfloat162float(t[0]);
+    t[1] = __float2bfloat16_rn(r);
+    r -= __bfloat162float(t[1]);
+    t[2] = __float2bfloat16_rn(r);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// acc[n-tile][4] += X[rows r0 .. r0 + 15][0 .. K) x B (B given transposed: Bt[n][k]), one warp.
+// Fragment layouts of m16n8k16 (g = lane / 4, q = lane % 4): A rows g and g + 8, columns 2q, 2q + 1 and
+// 2q + 8, 2q + 9; B column g, rows 2q, 2q + 1 and 2q + 8, 2q + 9; C rows g and g + 8, columns 2q, 2q + 1.
+template <int K, int N, int LDX, int LDB>
+__device__ __forceinline__ void tc_rows16(const float *X, int r0, const __nv_bfloat16 *Bt, float (&acc)[N / 8][4])
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
 #pragma unroll
-    for (int k = 0; k < kH / 4; ++k) {
-        const float4 a = hs[k], p = hp[k], n = hn[k];
-        h[4 * k] = fmaxf(a.x, 0.f);
-        h[4 * k + 1] = fmaxf(a.y, 0.f);
-        h[4 * k + 2] = fmaxf(a.z, 0.f);
-        h[4 * k + 3] = fmaxf(a.w, 0.f);
-        m[4 * k] = 0.5f * (fmaxf(p.x, 0.f) + fmaxf(n.x, 0.f));
-        m[4 * k + 1] = 0.5f * (fmaxf(p.y, 0.f) + fmaxf(n.y, 0.f));
-        m[4 * k + 2] = 0.5f * (fmaxf(p.z, 0.f) + fmaxf(n.z, 0.f));
-        m[4 * k + 3] = 0.5f * (fmaxf(p.w, 0.f) + fmaxf(n.w, 0.f));
-    }
-    float4 *zo = reinterpret_cast<float4 *>(zout + (size_t)I * kH);
-    for (int o = 0; o < kH; o += 4) {
-        float s[4];
+    for (int kk = 0; kk < K; kk += 16) {
+        const int c0 = kk + 2 * q;
+        const float x[8] = {X[(r0 + g) * LDX + c0],         X[(r0 + g) * LDX + c0 + 1],
+                            X[(r0 + g + 8) * LDX + c0],     X[(r0 + g + 8) * LDX + c0 + 1],
+                            X[(r0 + g) * LDX + c0 + 8],     X[(r0 + g) * LDX + c0 + 9],
+                            X[(r0 + g + 8) * LDX + c0 + 8], X[(r0 + g + 8) * LDX + c0 + 9]};
+        __nv_bfloat16 t[8][3];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float acc = b[o + q];
+        for (int e = 0; e < 8; ++e) bf_split3(x[e], t[e]);
+        uint32_t a[3][4];
 #pragma unroll
-            for (int k = 0; k < kH; ++k) acc = fmaf(Ws[(o + q) * kH + k], h[k], fmaf(Wn[(o + q) * kH + k], m[k], acc));
-            s[q] = acc;
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[p][r] = bf_pack(t[2 * r][p], t[2 * r + 1][p]);
+#pragma unroll
+        for (int nt = 0; nt < N / 8; ++nt) {
+            const __nv_bfloat16 *bc = Bt + (nt * 8 + g) * LDB + c0;
+            const uint32_t b0 = bf_pack(bc[0], bc[1]), b1 = bf_pack(bc[8], bc[9]);
+            // smallest terms first
+            mma_bf16_16816(acc[nt], a[2], b0, b1);
+            mma_bf16_16816(acc[nt], a[1], b0, b1);
+            mma_bf16_16816(acc[nt], a[0], b0, b1);
         }
-        zo[o / 4] = make_float4(s[0], s[1], s[2], s[3]);
     }
+}
+
+// zout = Ws relu(zin) + Wn avg(relu(zin[I-1]), relu(zin[I+1])) + b on the tensor cores
+__global__ void __launch_bounds__(64) k_gnn_lmp_tc(int nE, const int *__restrict__ eprev, const int *__restrict__ enext,
+                                                   const float *__restrict__ zin, const __nv_bfloat16 *__restrict__ w,
+                                                   int oWs, int oWn, int ob, float *__restrict__ zout)
+{
+    constexpr int K = 2 * kH, LDX = K + 4, LDB = K + 8;
+    __shared__ __align__(16) float X[kTcRows * LDX];
+    __shared__ __align__(16) __nv_bfloat16 Bt[kH * LDB];
+    __shared__ float bias[kH];
+    for (int t = threadIdx.x; t < kH * K; t += blockDim.x) {
+        const int n = t / K, k = t % K;
+        Bt[n * LDB + k] = k < kH ? w[oWs + n * kH + k] : w[oWn + n * kH + (k - kH)];
+    }
+    for (int t = threadIdx.x; t < kH; t += blockDim.x) bias[t] = bf(w, ob + t);
+    const int I0 = blockIdx.x * kTcRows;
+    for (int t = threadIdx.x; t < kTcRows * K; t += blockDim.x) {
+        const int r = t / K, k = t % K, I = I0 + r;
+        float v = 0.f;
+        if (I < nE) {
+            if (k < kH)
+                v = fmaxf(zin[(size_t)I * kH + k], 0.f);
+            else
+                v = 0.5f * (fmaxf(zin[(size_t)eprev[I] * kH + k - kH], 0.f) +
+                            fmaxf(zin[(size_t)enext[I] * kH + k - kH], 0.f));
+        }
+        X[r * LDX + k] = v;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    float acc[kH / 8][4];
+#pragma unroll
+    for (int nt = 0; nt < kH / 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+    tc_rows16<K, kH, LDX, LDB>(X, 16 * warp, Bt, acc);
+#pragma unroll
+    for (int nt = 0; nt < kH / 8; ++nt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int I = I0 + 16 * warp + g + 8 * h;
+            if (I >= nE) continue;
+            const int col = nt * 8 + 2 * q;
+            float2 o = make_float2(acc[nt][2 * h] + bias[col], acc[nt][2 * h + 1] + bias[col + 1]);
+            *reinterpret_cast<float2 *>(zout + (size_t)I * kH + col) = o;
+        }
+}
+
+// dh = dz Ws, dm = dz Wn on the tensor cores (dh[k] = sum_o dz[o] Ws[o][k])
+__global__ void __launch_bounds__(64) k_gnn_bmat_tc(int nE, const float *__restrict__ dz,
+                                                    const __nv_bfloat16 *__restrict__ w, int oWs, int oWn,
+                                                    float *__restrict__ dh, float *__restrict__ dm)
+{
+    constexpr int K = kH, N = 2 * kH, LDX = K + 4, LDB = K + 8;
+    __shared__ __align__(16) float X[kTcRows * LDX];
+    __shared__ __align__(16) __nv_bfloat16 Bt[N * LDB];
+    for (int t = threadIdx.x; t < N * K; t += blockDim.x) {
+        const int n = t / K, o = t % K;  // Bt[n][o] = Ws[o][n] (n < 64), Wn[o][n - 64]
+        Bt[n * LDB + o] = n < kH ? w[oWs + o * kH + n] : w[oWn + o * kH + (n - kH)];
+    }
+    const int I0 = blockIdx.x * kTcRows;
+    for (int t = threadIdx.x; t < kTcRows * K; t += blockDim.x) {
+        const int r = t / K, k = t % K, I = I0 + r;
+        X[r * LDX + k] = I < nE ? dz[(size_t)I * kH + k] : 0.f;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    float acc[N / 8][4];
+#pragma unroll
+    for (int nt = 0; nt < N / 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+    tc_rows16<K, N, LDX, LDB>(X, 16 * warp, Bt, acc);
+#pragma unroll
+    for (int nt = 0; nt < N / 8; ++nt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int I = I0 + 16 * warp + g + 8 * h;
+            if (I >= nE) continue;
+            const int col = nt * 8 + 2 * q;
+            float *out = col < kH ? dh + (size_t)I * kH + col : dm + (size_t)I * kH + (col - kH);
+            *reinterpret_cast<float2 *>(out) = make_float2(acc[nt][2 * h], acc[nt][2 * h + 1]);
+        }
 }
 
 // (a, b, c) = W4 relu(z3) + b4; also e^{2a}, e^{2b} in FP64 for the G term
@@ -325,41 +430,6 @@ __global__ void k_gnn_wreduce(int nW, int nB, int nblk, const float *__restrict_
         grad[oW + ent] = s;
     else
         grad[ob + ent - nW] = s;
-}
-
-// dh = dz Ws, dm = dz Wn (per edge: dh[k] = sum_o dz[o] Ws[o][k])
-__global__ void __launch_bounds__(128) k_gnn_bmat(int nE, const float *__restrict__ dz,
-                                                  const __nv_bfloat16 *__restrict__ w, int oWs, int oWn,
-                                                  float *__restrict__ dh, float *__restrict__ dm)
-{
-    __shared__ float Ws[kH * kH], Wn[kH * kH];
-    for (int t = threadIdx.x; t < kH * kH; t += blockDim.x) {
-        Ws[t] = bf(w, oWs + t);
-        Wn[t] = bf(w, oWn + t);
-    }
-    __syncthreads();
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nE) return;
-    float d[kH];
-    const float4 *dv = reinterpret_cast<const float4 *>(dz + (size_t)I * kH);
-#pragma unroll
-    for (int o = 0; o < kH / 4; ++o) {
-        const float4 v = dv[o];
-        d[4 * o] = v.x;
-        d[4 * o + 1] = v.y;
-        d[4 * o + 2] = v.z;
-        d[4 * o + 3] = v.w;
-    }
-    for (int k = 0; k < kH; ++k) {
-        float a = 0.f, m = 0.f;
-#pragma unroll
-        for (int o = 0; o < kH; ++o) {
-            a = fmaf(d[o], Ws[o * kH + k], a);
-            m = fmaf(d[o], Wn[o * kH + k], m);
-        }
-        dh[(size_t)I * kH + k] = a;
-        dm[(size_t)I * kH + k] = m;
-    }
 }
 
 // dzin = (dh + (dm[I+1] + dm[I-1]) / 2) * [zin > 0], written over dh (m[J] averages h[J-1], h[J+1])
@@ -675,8 +745,9 @@ cudaError_t gnn_forward(Ctx &c, cudaStream_t s)
     GnnState &G = *c.gnn;
     const int nb = (c.nE + 127) / 128;
     k_gnn_l1<<<nb, 128, 0, s>>>(c.nE, G.feat, G.wb, G.z1);
-    k_gnn_lmp<<<nb, 128, 0, s>>>(c.nE, G.eprev, G.enext, G.z1, G.wb, oW2s, oW2n, ob2, G.z2);
-    k_gnn_lmp<<<nb, 128, 0, s>>>(c.nE, G.eprev, G.enext, G.z2, G.wb, oW3s, oW3n, ob3, G.z3);
+    const int ntc = (c.nE + kTcRows - 1) / kTcRows;
+    k_gnn_lmp_tc<<<ntc, 64, 0, s>>>(c.nE, G.eprev, G.enext, G.z1, G.wb, oW2s, oW2n, ob2, G.z2);
+    k_gnn_lmp_tc<<<ntc, 64, 0, s>>>(c.nE, G.eprev, G.enext, G.z2, G.wb, oW3s, oW3n, ob3, G.z3);
     k_gnn_out<<<nb, 128, 0, s>>>(c.nE, G.z3, G.wb, G.out, G.ew);
     k_gnn_vlog<<<(c.nV + 255) / 256, 256, 0, s>>>(c.nV, c.d_inc_ptr, c.d_inc, G.out, G.vlog);
     c.launches += 5;
@@ -709,13 +780,13 @@ cudaError_t gnn_backward(Ctx &c, const float *dout, float *grad, cudaStream_t s)
     // layer 3: x = h2 (self) and avg h2 (neighbours)
     TPE_CHECK((wgrad<kH, kH>(c, G.bA, G.z2, 0, oW3s, ob3, grad, s)));
     TPE_CHECK((wgrad<kH, kH>(c, G.bA, G.z2, 1, oW3n, -1, grad, s)));
-    k_gnn_bmat<<<nb, 128, 0, s>>>(c.nE, G.bA, G.wb, oW3s, oW3n, G.bB, G.bC);
+    k_gnn_bmat_tc<<<(c.nE + kTcRows - 1) / kTcRows, 64, 0, s>>>(c.nE, G.bA, G.wb, oW3s, oW3n, G.bB, G.bC);
     k_gnn_bcombine<<<nb, 128, 0, s>>>(c.nE, G.eprev, G.enext, G.bC, G.z2, G.bB);  // dz2 in bB
     c.launches += 2;
     // layer 2
     TPE_CHECK((wgrad<kH, kH>(c, G.bB, G.z1, 0, oW2s, ob2, grad, s)));
     TPE_CHECK((wgrad<kH, kH>(c, G.bB, G.z1, 1, oW2n, -1, grad, s)));
-    k_gnn_bmat<<<nb, 128, 0, s>>>(c.nE, G.bB, G.wb, oW2s, oW2n, G.bA, G.bC);
+    k_gnn_bmat_tc<<<(c.nE + kTcRows - 1) / kTcRows, 64, 0, s>>>(c.nE, G.bB, G.wb, oW2s, oW2n, G.bA, G.bC);
     k_gnn_bcombine<<<nb, 128, 0, s>>>(c.nE, G.eprev, G.enext, G.bC, G.z1, G.bA);  // dz1 in bA
     c.launches += 2;
     // layer 1: x = the features
