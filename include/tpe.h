@@ -301,6 +301,32 @@ TPE_API tp_status tp_set_penalties(tp_ctx *ctx, const tp_penalties *pen);
  * [nV][3], may be NULL), both overwritten; zeros when none are set. */
 TPE_API tp_status tp_penalty(tp_ctx *ctx, const double *gamma, double *E, double *dE, tp_stream stream);
 
+/* Barnes-Hut comparator (App. B.1): the discrete energy and its differential approximated over a
+ * bounding volume hierarchy of tangent-points (T_I, x_I), one tree per problem, in FP64.  The tree is
+ * built on the host at every call (gamma is copied to the host; the call synchronises `stream`):
+ * nodes with more than leaf_size edges split by the plane that minimises the two children's summed
+ * squared 6-D box diameters; r_x, r_T are half the diagonals of a node's box of edge endpoints and of
+ * its box of tangents.  A node is admissible for target I when r_x < eps |x_I - x_N| and r_T < eps and
+ * it holds neither I nor an edge sharing a vertex with I; it then contributes
+ * l_I L_N |T_I x (x_I - x_N)|^alpha / |x_I - x_N|^beta (Eq. BVHNodeTPE) to the energy and
+ * L_N d/d gamma [l_I (k(x_I, x_N, T_I) + k(x_N, x_I, T_N))] to the target's endpoints in the
+ * differential; leaves contribute their disjoint pairs exactly (the trapezoid kernel of Eq. 18).
+ * eps = 0 gives the exact energy and differential.  A comparator for the exact tiled passes: the
+ * library's solves and descent steps do not use it.
+ *   eps >= 0, leaf_size in [1, 64] (else TP_ERR_INVALID_ARG).
+ *   tp_bh_energy: E DEVICE double [n_problems] and/or rows DEVICE double [n_edges] (the per-edge
+ *     sums), either may be NULL but not both.
+ *   tp_bh_differential: dE DEVICE double [nV][3] (overwritten).
+ *   TP_ERR_UNSUPPORTED when a vertex joins more than 15 edges or the tree is deeper than the
+ *   traversal stack (94 levels).
+ * tp_bh_stats reports the last pass's admissible nodes and leaf pairs summed over targets, and the
+ * tree depth. */
+TPE_API tp_status tp_bh_energy(tp_ctx *ctx, const double *gamma, double eps, int leaf_size, double *E, double *rows,
+                               tp_stream stream);
+TPE_API tp_status tp_bh_differential(tp_ctx *ctx, const double *gamma, double eps, int leaf_size, double *dE,
+                                     tp_stream stream);
+TPE_API tp_status tp_bh_stats(const tp_ctx *ctx, int64_t *admissible_nodes, int64_t *leaf_pairs, int32_t *depth);
+
 /* First collision time (Sec. 5.4): t (DEVICE double [n_problems]) receives, per problem, the first
  * tau in (0, horizon] at which two disjoint edges of gamma - tau d touch (segment distance at most
  * 1e-8 times the sum of their lengths), or horizon where none do.  gamma, d: DEVICE [nV][3].  Pairs

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtpe.so")
-SOURCES = ["pairs.cu", "solver.cu", "spectral.cu", "api.cu", "peaks.cu", "static_energy.cu", "coarse.cu", "gnn.cu", "pairs_sym.cu", "edges.cu", "ccd.cu", "penalties.cu", "pins.cu", "pairs_df.cu", "coarse_az.cu", "coarse_factor.cu", "pairs_multi.cu"]
+SOURCES = ["pairs.cu", "solver.cu", "spectral.cu", "api.cu", "peaks.cu", "static_energy.cu", "coarse.cu", "gnn.cu", "pairs_sym.cu", "edges.cu", "ccd.cu", "penalties.cu", "pins.cu", "pairs_df.cu", "coarse_az.cu", "coarse_factor.cu", "pairs_multi.cu", "bh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -27,8 +27,10 @@ def nvcc() -> str:
 
 
 def _flags():
+    # host code rounds every product and sum separately (no contraction into fma), as the oracle's numpy
+    # does: the Barnes-Hut hierarchy's split decisions compare such sums
     return ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-            "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
+            "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
 
 
 def _stale(out, deps):

@@ -270,6 +270,7 @@ void tp_destroy(tp_ctx *ctx)
     penalties_free(c);
     pins_free(c);
     multi_free(c);
+    bh_free(c);
     void *ptrs[] = {c.d_esum, c.d_edges, c.d_inc_ptr, c.d_inc, c.d_vprob, c.d_eprob, c.d_prob_v, c.d_prob_e, c.d_voff,
                     c.plan_energy.d_items, c.plan_diff.d_items, c.plan_apply.d_items, c.plan_energy.d_eslots,
                     c.plan_diff.d_eslots, c.plan_apply.d_eslots, c.d_counter, c.d_recF, c.d_recF2, c.d_recLo,
@@ -671,6 +672,47 @@ tp_status tp_penalty(tp_ctx *ctx, const double *gamma, double *E, double *dE, tp
     if (E) CK(cudaMemsetAsync(E, 0, sizeof(double) * c.nProb, s));
     if (dE) CK(cudaMemsetAsync(dE, 0, sizeof(double) * 3 * (size_t)c.nV, s));
     CK(penalties_add(c, 0, E, dE, s));
+    return TP_OK;
+}
+
+static tp_status bh_call(tp_ctx *ctx, const double *gamma, int op, double eps, int leaf_size, double *rows,
+                         double *E, double *dE, tp_stream stream)
+{
+    if (!(eps >= 0.0) || leaf_size < 1 || leaf_size > 64)
+        return fail(ctx, TP_ERR_INVALID_ARG, "Barnes-Hut: eps must be >= 0 and leaf_size in [1, 64]");
+    cudaStream_t s = (cudaStream_t)stream;
+    tp_status st = records(ctx, gamma, 0, s);  // the degenerate-edge check
+    if (st) return st;
+    int unsupported = 0;
+    CK(bh_pass(ctx->c, gamma, op, eps, leaf_size, rows, E, dE, s, unsupported));
+    if (unsupported)
+        return fail(ctx, TP_ERR_UNSUPPORTED, "Barnes-Hut: a vertex joins more than 15 edges, or the hierarchy is too deep");
+    return TP_OK;
+}
+
+tp_status tp_bh_energy(tp_ctx *ctx, const double *gamma, double eps, int leaf_size, double *E, double *rows,
+                       tp_stream stream)
+{
+    if (!ctx || !gamma || (!E && !rows)) return TP_ERR_INVALID_ARG;
+    return bh_call(ctx, gamma, OP_ENERGY, eps, leaf_size, rows, E, nullptr, stream);
+}
+
+tp_status tp_bh_differential(tp_ctx *ctx, const double *gamma, double eps, int leaf_size, double *dE,
+                             tp_stream stream)
+{
+    if (!ctx || !gamma || !dE) return TP_ERR_INVALID_ARG;
+    return bh_call(ctx, gamma, OP_DIFF, eps, leaf_size, nullptr, nullptr, dE, stream);
+}
+
+tp_status tp_bh_stats(const tp_ctx *ctx, int64_t *admissible_nodes, int64_t *leaf_pairs, int32_t *depth)
+{
+    if (!ctx) return TP_ERR_INVALID_ARG;
+    unsigned long long a = 0, p = 0;
+    int d = 0;
+    bh_stats(ctx->c, &a, &p, &d);
+    if (admissible_nodes) *admissible_nodes = (int64_t)a;
+    if (leaf_pairs) *leaf_pairs = (int64_t)p;
+    if (depth) *depth = d;
     return TP_OK;
 }
 

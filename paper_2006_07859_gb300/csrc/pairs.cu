@@ -827,6 +827,13 @@ cudaError_t build_urecs(Ctx &c, const double *u, int which, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t segment_sum(Ctx &c, const double *rows, double *E, cudaStream_t s)
+{
+    k_segment_sum<<<c.nProb, 256, 0, s>>>(c.d_prob_e, rows, E);
+    c.launches++;
+    return cudaGetLastError();
+}
+
 cudaError_t build_urecs_into(Ctx &c, const double *u, int which, URecF *uf, URecD *ud, cudaStream_t s)
 {
     if (c.nE == 0) return cudaSuccess;

@@ -19,6 +19,7 @@ struct EdgeState;
 struct CcdState;
 struct PenState;
 struct PinState;
+struct BhState;
 
 // Precision of the pair arithmetic.
 enum Prec { P64 = 0, P32 = 1, PMIX = 2 };
@@ -187,6 +188,7 @@ struct Ctx {
     GnnState *gnn = nullptr;      // learned preconditioner term (contexts created with TP_PRECOND_LEARNED)
     EdgeState *edges = nullptr;   // edge-length constraint rows (edges.cu), allocated when first selected
     CcdState *ccd = nullptr;      // collision-time work list (ccd.cu), allocated when first used
+    BhState *bh = nullptr;        // Barnes-Hut hierarchy (bh.cu), allocated when first used
     PenState *pen = nullptr;      // penalties of Sec. 8.1 (penalties.cu), allocated by tp_set_penalties
     PinState *pins = nullptr;     // point / tangent / surface rows of TP_CONSTRAINTS_POINTS (pins.cu)
     // captured CG iteration blocks
@@ -303,6 +305,13 @@ cudaError_t penalties_add(Ctx &c, int which, double *E, double *dE, cudaStream_t
 // first collision time along a direction (ccd.cu)
 cudaError_t ccd_init(Ctx &c);
 void ccd_free(Ctx &c);
+// Barnes-Hut comparator (bh.cu): op OP_ENERGY (rows, E) or OP_DIFF (dE)
+cudaError_t bh_pass(Ctx &c, const double *gamma, int op, double eps, int leaf_size, double *rows, double *E,
+                    double *dE, cudaStream_t s, int &unsupported);
+void bh_stats(const Ctx &c, unsigned long long *adm, unsigned long long *pairs, int *depth);
+void bh_free(Ctx &c);
+// E[q] = sum of rows over problem q's edges
+cudaError_t segment_sum(Ctx &c, const double *rows, double *E, cudaStream_t s);
 cudaError_t ccd_time(Ctx &c, const double *gamma, const double *d, double T, double *tmin, cudaStream_t s);
 inline bool edge_constraints(const Ctx &c)
 {

@@ -36,7 +36,7 @@ EXPORTED = ["tp_default_params", "tp_create", "tp_destroy", "tp_last_error", "tp
             "tp_gnn_forward", "tp_gnn_backward", "tp_gnn_adam", "tp_gnn_g_apply", "tp_gnn_out_grad", "tp_cg_harvest",
             "tp_gnn_prepare_pairs", "tp_gnn_train_step", "tp_autotune", "tp_set_apply_variant",
             "tp_set_energy_variant", "tp_last_solve", "tp_set_diff_variant", "tp_collision_time",
-            "tp_set_penalties", "tp_penalty", "tp_set_pins",
+            "tp_set_penalties", "tp_penalty", "tp_set_pins", "tp_bh_energy", "tp_bh_differential", "tp_bh_stats",
             "tp_set_tangents", "tp_set_surface"]
 
 
@@ -101,6 +101,10 @@ def library() -> ctypes.CDLL:
         L.sobolev_apply.argtypes = [vp, vp, vp, vp, vp]
         L.sobolev_apply_accurate.argtypes = [vp, vp, vp, vp, vp]
         L.sobolev_apply_multi.argtypes = [vp, vp, vp, vp, i, vp]
+        L.tp_bh_energy.argtypes = [vp, vp, d, i, vp, vp, vp]
+        L.tp_bh_differential.argtypes = [vp, vp, d, i, vp, vp]
+        L.tp_bh_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_int32)]
         L.tp_gram_diagonal.argtypes = [vp, vp, vp, vp]
         L.tp_precond_apply.argtypes = [vp, vp, vp, vp, vp]
         L.tp_spectral_symbol.argtypes = [vp, i, vp, vp]
@@ -272,6 +276,27 @@ def sobolev_apply_multi(ctx: Context, gamma, U, AU=None):
     AU = _new((m, ctx.n_vertices, 3)) if AU is None else AU
     ctx._check(library().sobolev_apply_multi(ctx.handle, _ptr(gamma), _ptr(U), _ptr(AU), m, _stream()))
     return AU
+
+
+def tp_bh_energy(ctx: Context, gamma, eps, leaf_size=8, E=None, rows=None):
+    """Barnes-Hut energy per problem (and optionally per edge); returns E."""
+    E = _new(ctx.n_problems) if E is None else E
+    ctx._check(library().tp_bh_energy(ctx.handle, _ptr(gamma), float(eps), int(leaf_size), _ptr(E), _ptr(rows),
+                                      _stream()))
+    return E
+
+
+def tp_bh_differential(ctx: Context, gamma, eps, leaf_size=8, dE=None):
+    dE = _new((ctx.n_vertices, 3)) if dE is None else dE
+    ctx._check(library().tp_bh_differential(ctx.handle, _ptr(gamma), float(eps), int(leaf_size), _ptr(dE), _stream()))
+    return dE
+
+
+def tp_bh_stats(ctx: Context):
+    """(admissible nodes, leaf pairs) of the last Barnes-Hut pass and the tree depth."""
+    a, p, dp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    ctx._check(library().tp_bh_stats(ctx.handle, ctypes.byref(a), ctypes.byref(p), ctypes.byref(dp)))
+    return a.value, p.value, dp.value
 
 
 def sobolev_apply_accurate(ctx: Context, gamma, u, Au=None):

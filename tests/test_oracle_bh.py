@@ -102,15 +102,16 @@ def test_hierarchy_partitions_edges_and_node_data(bh):
             l, r = nodes[nd["left"]], nodes[nd["right"]]
             assert (l["b"], l["e"], r["b"], r["e"]) == (nd["b"], l["e"], l["e"], nd["e"])
             assert abs(l["L"] + r["L"] - nd["L"]) <= 1e-12 * nd["L"]
-            # the split is the brute-force minimiser of the two children's squared 6-D diagonals
+            # halves, and the coordinate whose median split minimises the children's squared 6-D diagonals
+            assert l["e"] - l["b"] == len(items) // 2
             P = np.hstack([T, x])[items]
             best = np.inf
             for cc in range(6):
                 o = np.lexsort((items, P[:, cc]))
                 Q = P[o]
-                for k in range(1, len(items)):
-                    dl, dr = Q[:k].max(0) - Q[:k].min(0), Q[k:].max(0) - Q[k:].min(0)
-                    best = min(best, float(dl @ dl + dr @ dr))
+                k = len(items) // 2
+                dl, dr = Q[:k].max(0) - Q[:k].min(0), Q[k:].max(0) - Q[k:].min(0)
+                best = min(best, float(dl @ dl + dr @ dr))
             PL, PR = np.hstack([T, x])[perm[l["b"]:l["e"]]], np.hstack([T, x])[perm[r["b"]:r["e"]]]
             dl, dr = PL.max(0) - PL.min(0), PR.max(0) - PR.min(0)
             assert float(dl @ dl + dr @ dr) <= best * (1 + 1e-12)
