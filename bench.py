@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-262k", action="store_true", help="skip the 262,144-edge pair-pass timing")
     ap.add_argument("--no-small", action="store_true", help="skip the extra 8 x 4096 run")
-    ap.add_argument("--mode", choices=["bench", "passes", "precision", "batch", "learned", "constraints"],
+    ap.add_argument("--mode", choices=["bench", "passes", "precision", "batch", "learned", "constraints", "bh"],
                     default="bench",
                     help="passes: energy, differential and 3 applies of the workload (for ncu); "
                          "precision: per-result error of the 262,144-edge passes against the FP64 oracle on "
@@ -364,6 +364,62 @@ def run_passes(args):
             tpe.sobolev_apply_accurate(ctx, g, u)
     torch.cuda.synchronize()
     print(json.dumps({"mode": "passes", "workload": cfg["workload"], "pairs_per_pass": ctx.pairs_per_pass()}))
+
+
+def run_bh(args):
+    """The Barnes-Hut comparator (App. B.1) against the exact passes on the 262,144-edge knot: for each
+    eps, the wall time of tp_bh_energy and tp_bh_differential (host hierarchy build included; the calls
+    synchronise), their admissible nodes and leaf pairs, the energy's error against the exact mixed
+    pass and the differential's against the FP64 oracle at 64 sampled vertices; beside them the
+    exact mixed energy and differential passes (CUDA events)."""
+    import torch
+    import synth as S
+    from oracle import oracle as O
+    from paper_2006_07859_gb300 import tpe
+    O.build_library()
+    c = S.knot_262144()
+    g = torch.as_tensor(c.gamma).cuda()
+    v_idx = np.sort(np.random.default_rng(101).choice(c.n_vertices, size=64, replace=False)).astype(np.int32)
+    dEo = O.differential_at(c.gamma, c.edges, v_idx)
+    mixed = tpe.Context.from_curves(c, precision=tpe.TP_MIXED, precond=tpe.TP_PRECOND_JACOBI)
+    tpe.tp_autotune(mixed, g)
+    out = {"mode": "bh", "workload": "fourier_knot_K16_n262144_seed100", "pairs_exact": mixed.pairs_per_pass()}
+    E_ex = None
+    for name, fn in (("energy", lambda: tpe.tp_energy(mixed, g)), ("differential", lambda: tpe.tp_differential(mixed, g))):
+        r = fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out["exact_mixed_" + name + "_ms"] = e0.elapsed_time(e1)
+        if name == "energy":
+            E_ex = float(r.cpu()[0])
+    ctx = tpe.Context.from_curves(c, precision=tpe.TP_FP64, precond=tpe.TP_PRECOND_JACOBI)
+    rows = []
+    for eps in (0.4, 0.2, 0.1, 0.05):
+        rec = {"eps": eps}
+        for name in ("energy", "differential"):
+            fn = (lambda: tpe.tp_bh_energy(ctx, g, eps)) if name == "energy" else (lambda: tpe.tp_bh_differential(ctx, g, eps))
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = fn()
+            torch.cuda.synchronize()
+            rec[name + "_s"] = time.perf_counter() - t0
+            adm, pairs, depth, build_s = tpe.tp_bh_stats(ctx, with_build_time=True)
+            rec[name + "_admissible_nodes"], rec[name + "_leaf_pairs"], rec["depth"] = adm, pairs, depth
+            rec[name + "_host_build_s"] = build_s
+            if name == "energy":
+                rec["energy_rel_err"] = abs(float(r.cpu()[0]) / E_ex - 1.0)
+            else:
+                d = r.cpu().numpy()[v_idx]
+                rec["differential_err_rel_max"] = float(np.abs(d - dEo).max() / np.abs(dEo).max())
+        rows.append(rec)
+        print(json.dumps(rec), flush=True)
+    out["bh"] = rows
+    print(json.dumps(out), flush=True)
 
 
 def run_precision(args):
@@ -813,6 +869,8 @@ def main():
         run_batch(args)
     elif args.mode == "learned":
         run_learned(args)
+    elif args.mode == "bh":
+        run_bh(args)
     else:
         run_ours(args, rank, world, local_rank)
     if world > 1:

@@ -319,13 +319,15 @@ TPE_API tp_status tp_penalty(tp_ctx *ctx, const double *gamma, double *E, double
  *   tp_bh_differential: dE DEVICE double [nV][3] (overwritten).
  *   TP_ERR_UNSUPPORTED when a vertex joins more than 15 edges or the tree is deeper than the
  *   traversal stack (94 levels).
- * tp_bh_stats reports the last pass's admissible nodes and leaf pairs summed over targets, and the
- * tree depth. */
+ * tp_bh_stats reports the last pass's admissible nodes and leaf pairs summed over targets, the tree
+ * depth and the host seconds of its hierarchy (copy of gamma to the host, build, upload); each output
+ * may be NULL. */
 TPE_API tp_status tp_bh_energy(tp_ctx *ctx, const double *gamma, double eps, int leaf_size, double *E, double *rows,
                                tp_stream stream);
 TPE_API tp_status tp_bh_differential(tp_ctx *ctx, const double *gamma, double eps, int leaf_size, double *dE,
                                      tp_stream stream);
-TPE_API tp_status tp_bh_stats(const tp_ctx *ctx, int64_t *admissible_nodes, int64_t *leaf_pairs, int32_t *depth);
+TPE_API tp_status tp_bh_stats(const tp_ctx *ctx, int64_t *admissible_nodes, int64_t *leaf_pairs, int32_t *depth,
+                              double *build_seconds);
 
 /* First collision time (Sec. 5.4): t (DEVICE double [n_problems]) receives, per problem, the first
  * tau in (0, horizon] at which two disjoint edges of gamma - tau d touch (segment distance at most

@@ -704,15 +704,18 @@ tp_status tp_bh_differential(tp_ctx *ctx, const double *gamma, double eps, int l
     return bh_call(ctx, gamma, OP_DIFF, eps, leaf_size, nullptr, nullptr, dE, stream);
 }
 
-tp_status tp_bh_stats(const tp_ctx *ctx, int64_t *admissible_nodes, int64_t *leaf_pairs, int32_t *depth)
+tp_status tp_bh_stats(const tp_ctx *ctx, int64_t *admissible_nodes, int64_t *leaf_pairs, int32_t *depth,
+                      double *build_seconds)
 {
     if (!ctx) return TP_ERR_INVALID_ARG;
     unsigned long long a = 0, p = 0;
     int d = 0;
-    bh_stats(ctx->c, &a, &p, &d);
+    double bs = 0.0;
+    bh_stats(ctx->c, &a, &p, &d, &bs);
     if (admissible_nodes) *admissible_nodes = (int64_t)a;
     if (leaf_pairs) *leaf_pairs = (int64_t)p;
     if (depth) *depth = d;
+    if (build_seconds) *build_seconds = bs;
     return TP_OK;
 }
 

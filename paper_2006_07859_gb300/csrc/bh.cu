@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <numeric>
 #include <string>
@@ -365,6 +366,7 @@ struct tpe::BhState {
     size_t cap_nodes = 0;
     unsigned long long stats[2] = {0, 0};  // of the last pass
     int depth = 0;                          // of the last hierarchy
+    double build_s = 0.0;                   // host time of the last hierarchy: copy-out, build, upload
 };
 
 namespace tpe {
@@ -397,6 +399,7 @@ static cudaError_t bh_prepare(Ctx &c, const double *gamma, int leaf_size, cudaSt
     unsupported = 0;
     if (!c.bh) c.bh = new BhState();
     BhState &B = *c.bh;
+    const auto t0 = std::chrono::steady_clock::now();
     const int nV = c.nV, nE = c.nE;
     std::vector<double> g(3 * (size_t)nV);
     TPE_CHECK(cudaMemcpyAsync(g.data(), gamma, sizeof(double) * g.size(), cudaMemcpyDeviceToHost, s));
@@ -482,6 +485,7 @@ static cudaError_t bh_prepare(Ctx &c, const double *gamma, int leaf_size, cudaSt
     TPE_CHECK(cudaMemcpy(B.d_near_ptr, near_ptr.data(), sizeof(int) * (nE + 1), cudaMemcpyHostToDevice));
     if (!near_pos.empty())
         TPE_CHECK(cudaMemcpy(B.d_near_pos, near_pos.data(), sizeof(int) * near_pos.size(), cudaMemcpyHostToDevice));
+    B.build_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return cudaSuccess;
 }
 
@@ -526,11 +530,12 @@ cudaError_t bh_pass(Ctx &c, const double *gamma, int op, double eps, int leaf_si
     return cudaGetLastError();
 }
 
-void bh_stats(const Ctx &c, unsigned long long *adm, unsigned long long *pairs, int *depth)
+void bh_stats(const Ctx &c, unsigned long long *adm, unsigned long long *pairs, int *depth, double *build_s)
 {
     *adm = c.bh ? c.bh->stats[0] : 0;
     *pairs = c.bh ? c.bh->stats[1] : 0;
     if (depth) *depth = c.bh ? c.bh->depth : 0;
+    if (build_s) *build_s = c.bh ? c.bh->build_s : 0.0;
 }
 
 void bh_free(Ctx &c)

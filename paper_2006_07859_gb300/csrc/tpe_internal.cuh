@@ -308,7 +308,7 @@ void ccd_free(Ctx &c);
 // Barnes-Hut comparator (bh.cu): op OP_ENERGY (rows, E) or OP_DIFF (dE)
 cudaError_t bh_pass(Ctx &c, const double *gamma, int op, double eps, int leaf_size, double *rows, double *E,
                     double *dE, cudaStream_t s, int &unsupported);
-void bh_stats(const Ctx &c, unsigned long long *adm, unsigned long long *pairs, int *depth);
+void bh_stats(const Ctx &c, unsigned long long *adm, unsigned long long *pairs, int *depth, double *build_s);
 void bh_free(Ctx &c);
 // E[q] = sum of rows over problem q's edges
 cudaError_t segment_sum(Ctx &c, const double *rows, double *E, cudaStream_t s);

@@ -104,7 +104,7 @@ def library() -> ctypes.CDLL:
         L.tp_bh_energy.argtypes = [vp, vp, d, i, vp, vp, vp]
         L.tp_bh_differential.argtypes = [vp, vp, d, i, vp, vp]
         L.tp_bh_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
-                                  ctypes.POINTER(ctypes.c_int32)]
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]
         L.tp_gram_diagonal.argtypes = [vp, vp, vp, vp]
         L.tp_precond_apply.argtypes = [vp, vp, vp, vp, vp]
         L.tp_spectral_symbol.argtypes = [vp, i, vp, vp]
@@ -292,11 +292,12 @@ def tp_bh_differential(ctx: Context, gamma, eps, leaf_size=8, dE=None):
     return dE
 
 
-def tp_bh_stats(ctx: Context):
-    """(admissible nodes, leaf pairs) of the last Barnes-Hut pass and the tree depth."""
-    a, p, dp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
-    ctx._check(library().tp_bh_stats(ctx.handle, ctypes.byref(a), ctypes.byref(p), ctypes.byref(dp)))
-    return a.value, p.value, dp.value
+def tp_bh_stats(ctx: Context, with_build_time=False):
+    """(admissible nodes, leaf pairs, tree depth) of the last Barnes-Hut pass, and with
+    with_build_time the host seconds of its hierarchy."""
+    a, p, dp, bs = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_double()
+    ctx._check(library().tp_bh_stats(ctx.handle, ctypes.byref(a), ctypes.byref(p), ctypes.byref(dp), ctypes.byref(bs)))
+    return (a.value, p.value, dp.value, bs.value) if with_build_time else (a.value, p.value, dp.value)
 
 
 def sobolev_apply_accurate(ctx: Context, gamma, u, Au=None):
