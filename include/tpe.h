@@ -392,8 +392,8 @@ TPE_API tp_status tp_profile_read(tp_ctx *ctx, int op, double *total_ms, int64_t
  *          gives E = 0);  E DEVICE double [1].
  *   n_edges <= 65536, else TP_ERR_INVALID_ARG (the scratch has a fixed size).
  *   All pairs of disjoint edges of the whole graph form one problem (as independent = 0).
- * The first call on a device looks up the arrays' device addresses (cudaGetSymbolAddress); make
- * it before any stream capture.  Every call synchronises `stream` once (to read the edge-length
+ * The first call on a device looks up the arrays' device addresses (cudaGetSymbolAddress).  Every
+ * call synchronises `stream` once (to read the edge-length
  * statistics that set the near-pair cutoff) and then enqueues the pair pass.  All calls share the
  * same scratch and it keeps the last call's contents: calls that overlap on the GPU (other streams,
  * other host threads) race and must be serialised by the caller.
