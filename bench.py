@@ -59,7 +59,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["knots8x4096", "scene8x4096", "knot262144"], default="knot262144")
+    ap.add_argument("--workload", choices=["knots8x4096", "scene8x4096", "knot262144", "knot65536"], default="knot262144",
+                    help="knot65536: the same knot family at a quarter of the size, for ncu captures whose "
+                         "device memory must stay small")
     ap.add_argument("--cg-rtol", type=float, default=None)
     ap.add_argument("--cg-maxit", type=int, default=None)
     ap.add_argument("--cg-check-every", type=int, default=8,
@@ -113,6 +115,9 @@ def workload(name, rank=0):
     if name == "knot262144":
         return S.knot_262144(), {"workload": "fourier_knot_K16_n262144_seed100", "n_vertices": 262144,
                                  "n_edges": 262144, "curves": 1}, 0
+    if name == "knot65536":
+        return S.single(S.fourier_knot(65536, 16, 100)), {"workload": "fourier_knot_K16_n65536_seed100",
+                                                          "n_vertices": 65536, "n_edges": 65536, "curves": 1}, 0
     f = shard_first_seed(rank)
     if name == "scene8x4096":
         return S.eight_knots_4096(True, f), {"workload": f"scene_of_8_fourier_knots_K8_n4096_seeds{f}-{f + 7}",
@@ -139,12 +144,14 @@ def solver_params(name, args):
     # there) and the certified residual stalls near 2.6e-5.  The projection solves stop at 1e-3 (the
     # projected curve meets the constraints for any solve accuracy).
     rtol = args.cg_rtol if args.cg_rtol is not None else (1e-4 if name == "knot262144" else 1e-6)
-    maxit = args.cg_maxit if args.cg_maxit is not None else 2000
+    # at 262,144 edges the solves take 21 + 7 iterations (0.27 s each): a cap of 400 ends a stalled run
+    # in minutes instead of hours
+    maxit = args.cg_maxit if args.cg_maxit is not None else (400 if name == "knot262144" else 2000)
     # the coarse space: 8,192 hats (32 edges each) on the 262,144-vertex knot.  Measured CG iterations per
     # step to the certified 1e-4 (gradient + projection solve) and seconds per step, set-up every two
     # steps: 1,024 hats 47 + 18, 29.6 s; 2,048 37 + 13, 25.1 s; 4,096 27 + 10, 21.2 s; 8,192 21 + 7, 19.0 s.
     # 128 hats on 4,096 vertices.
-    m = args.coarse_dim or (8192 if name == "knot262144" else 128)
+    m = args.coarse_dim or {"knot262144": 8192, "knot65536": 2048}.get(name, 128)
     refresh = args.precond_refresh or max(1, args.steps)
     return dict(cg_rtol=rtol, cg_maxit=maxit, proj_cg_rtol=1e-3, cg_check_every=args.cg_check_every,
                 precond_refresh=refresh, coarse_dim=m)
@@ -291,11 +298,12 @@ def run_reference(args, rank, world):
 # and 37 applies per step (CG, projection, warm-start, correction and residual applies, the 2
 # double-float residual checks counted as applies); per set-up one apply's worth for the coarse pass
 # (every ordered pair once) and 4 multi-field passes for the 15 Rayleigh-quotient probe fields.  8 x 4096
-# knots (128 hats, certified 1e-6): 2, 1 and 104 per step, the same set-up.  The scene has no measured
-# step and keeps a nominal count.
+# knots (128 hats, certified 1e-6): 2, 1 and 104 per step, the same set-up.  The scene and the
+# 65,536-edge knot (a profiling workload) have no measured step and keep nominal counts.
 MEASURED_PASSES = {"knot262144": ({"energy": 2, "diff": 1, "apply": 37}, {"apply": 1, "apply_multi": 4}),
                    "scene8x4096": ({"energy": 2, "diff": 1, "apply": 260}, {}),
-                   "knots8x4096": ({"energy": 2, "diff": 1, "apply": 104}, {"apply": 1, "apply_multi": 4})}
+                   "knots8x4096": ({"energy": 2, "diff": 1, "apply": 104}, {"apply": 1, "apply_multi": 4}),
+                   "knot65536": ({"energy": 2, "diff": 1, "apply": 40}, {"apply": 1, "apply_multi": 4})}
 
 
 def passes_for(workload, steps):
