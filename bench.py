@@ -49,8 +49,11 @@ FP32_LANES = 128   # FP32 FMA lanes per SM (Blackwell)
 L2_BYTES = 129 * 2 ** 20
 # DRAM bytes (read + write) of one apply launch on the 8 x 4096 workload, by (pass, targets per thread),
 # from ncu captures of the current kernels (the profiles/ summaries named beside them); others: unknown
-APPLY_TRAFFIC_BYTES = {("gather", 2): 5.07e6,                   # apply_pair_kernel_knots8x4096.md
-                      ("symmetric", 1): 5.162240e6 + 0.249344e6}  # apply_symmetric_kernel_knots8x4096.md
+APPLY_TRAFFIC_BYTES = {("knots8x4096", "gather", 2): 5.07e6,                   # apply_pair_kernel_knots8x4096.md
+                      ("knots8x4096", "symmetric", 1): 5.162240e6 + 0.249344e6,  # apply_symmetric_kernel_knots8x4096.md
+                      # captured at 65,536 edges and scaled by the pairs (x16):
+                      # apply_symmetric_kernel_traffic_knot65536.md
+                      ("knot262144", "symmetric", 1): 16.0 * (19161856 + 1550644736)}
 
 
 def parse():
@@ -834,7 +837,7 @@ def run_ours(args, rank, world, local_rank):
                      "achieved": achieved / 1e12 if achieved else None,
                      "peak": peak / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / peak if achieved else None,
-                     "traffic": (APPLY_TRAFFIC_BYTES.get(apply_variant) if args.workload == "knots8x4096" else None),
+                     "traffic": APPLY_TRAFFIC_BYTES.get((args.workload,) + apply_variant),
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "flop_per_pair": FLOP_PER_PAIR["apply"], "launches": n_a, "avg_launch_ms": avg_s * 1e3,
                      "peak_note": f"{sms} SMs (device attribute) x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz "
