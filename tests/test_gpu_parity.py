@@ -172,3 +172,36 @@ def test_graphs_without_disjoint_pairs(torch, orc):
     with pytest.raises(tpe.TpError) as ei:
         tpe.Context(np.zeros((0, 2), dtype=np.int32), [0, 4], [0, 0], 4, precision=0, precond=1)
     assert ei.value.status == tpe.TP_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("n,K", [(4096, 8), (16384, 12)])
+def test_fp32_at_size(torch, orc, n, K, capsys):
+    """Plain FP32 (single-float positions, tangents and u; FP32 tile sums folded into FP64) on knots of
+    4,096 and 16,384 edges against the FP64 oracle: energy, the differential on sampled vertices and the
+    apply of a smooth vector on sampled vertices.  FP32 loses log2(|d| / eps) bits on near pairs and
+    the differential's vertex values are differences of edge rows ~1 / (kappa l) larger, so its error
+    grows with n.  Measured: energy 1.6e-8 and 1.6e-6, smooth apply 2.4e-5 and 8.7e-3; the differential
+    has cosine 0.99976 at 4,096 edges and breaks down at 16,384 (cosine 0.935, the mixed mode's job).
+    The bars sit 3-10x above the measured errors, far below the O(1) error of a wrong index or sign."""
+    from paper_2006_07859_gb300 import tpe
+    c = S.single(S.fourier_knot(n, K, 100 + K))
+    rng = np.random.default_rng(7)
+    v_i = np.sort(rng.choice(c.n_vertices, 48, replace=False)).astype(np.int32)
+    t = np.linspace(0, 2 * np.pi, n, endpoint=False)
+    U = np.stack([np.cos(t), np.sin(2 * t), np.cos(3 * t)], 1)
+    ctx = make_ctx(c, precision=1, precond=1)
+    g = dev(c.gamma)
+    E = float(host(tpe.tp_energy(ctx, g))[0])
+    dE = host(tpe.tp_differential(ctx, g))[v_i]
+    Au = host(tpe.sobolev_apply(ctx, g, dev(U)))[v_i]
+    Eo = orc.energy(c.gamma, c.edges)
+    dEo = orc.differential_at(c.gamma, c.edges, v_i)
+    Auo = orc.gram_apply_at(c.gamma, c.edges, SIG, U, v_i)
+    e_E, e_d, e_a = abs(E / Eo - 1.0), rel(dE, dEo), rel(Au, Auo)
+    with capsys.disabled():
+        print(f"\nFP32 at {n} edges: energy {e_E:.2e}, differential {e_d:.2e} (cos {cosine(dE, dEo):.8f}), "
+              f"smooth apply {e_a:.2e}")
+    assert e_E <= {4096: 1e-7, 16384: 1e-5}[n]
+    assert e_a <= {4096: 2e-4, 16384: 3e-2}[n]
+    if n == 4096:
+        assert cosine(dE, dEo) >= 0.999 and e_d <= 0.1
